@@ -1,0 +1,234 @@
+/*
+ * hfcr.h - C ABI of the GB300 implementation of history-free collision
+ * response between two triangle meshes (J. Ye, "History-free Collision
+ * Response for Deformable Surfaces", arXiv 1409.2081).
+ *
+ * The library finds every edge-face (E-F) intersection between two meshes,
+ * at least one of them oriented (Sec. 3), turns the crossings into
+ * penetration stencils (Sec. 4, Fig. 3), and moves the stencil vertices by
+ * the global displacement minimizer (Sec. 4, Eq. 3, solved through the
+ * normal equations Eq. 7 / Eq. 8).  The repair loop repeats the three
+ * steps until no intersection remains (Sec. 3).
+ *
+ * Conventions shared by every entry point:
+ *  - All array pointers are DEVICE pointers unless a parameter says "host".
+ *    The caller owns every input and output buffer; the library only reads
+ *    inputs and writes outputs.  A context owns its scratch memory, which
+ *    hfcr_reserve allocates; no other call allocates device memory.
+ *  - Work is enqueued on the given CUDA stream (NULL = legacy default).
+ *    Entry points that return a count (detect, build_stencils, resolve)
+ *    synchronise that stream before returning; respond does not.
+ *  - Positions are structure-of-arrays x[], y[], z[] of the mesh's dtype.
+ *    float32 coordinates must be finite with magnitude at most 2^38;
+ *    float64 coordinates must be finite and either 0 or of magnitude in
+ *    [2^-200, 2^38].  Outside that range the exactness argument of the
+ *    predicates does not hold and the call returns HFCR_ERR_RANGE (or
+ *    HFCR_ERR_NONFINITE) without producing output.
+ *  - Triangles are int32 [n_tris][3], counter-clockwise seen from the
+ *    front side of an oriented mesh (the normal (b-a) x (c-a) points to
+ *    the front).
+ *  - Vertex and face ids in pairs and stencils are local to their mesh.
+ *  - Errors are returned as hfcr_status; no C++ exception crosses the ABI.
+ *    hfcr_last_error(ctx) gives a human-readable message.
+ *
+ * Readings of the paper fixed by this interface:
+ *  - An E-F intersection is a strict crossing of the face's plane by the
+ *    edge inside the closed triangle: an endpoint on the plane, a coplanar
+ *    edge, a zero-area face or a zero-length edge gives no pair; a crossing
+ *    through a shared triangle edge or vertex is reported for every face
+ *    containing that point.
+ *  - Direction 0 pairs an edge of A with a face of B (needs B oriented);
+ *    direction 1 an edge of B with a face of A (needs A oriented).
+ *  - n is the unit face normal of the pre-response positions, alpha = 1/3
+ *    (Eq. 1), x' = x - M^-1 grad(D)^T lambda with
+ *    grad(D) M^-1 grad(D)^T lambda = grad(D) x - d (Eq. 8; d = 0 is Eq. 7).
+ */
+#ifndef HFCR_H
+#define HFCR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HFCR_OK = 0,
+    HFCR_ERR_ARG = 1,           /* invalid argument (NULL, negative size, no oriented mesh) */
+    HFCR_ERR_CAPACITY = 2,      /* output or reserved scratch too small; *n_out holds the size needed */
+    HFCR_ERR_CUDA = 3,          /* a CUDA call failed (see hfcr_last_error) */
+    HFCR_ERR_NONFINITE = 4,     /* a position is NaN or infinite */
+    HFCR_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    HFCR_ERR_NOT_CONVERGED = 6, /* the solver or the repair loop stopped at its iteration limit */
+    HFCR_ERR_UNSUPPORTED = 7,   /* option combination not implemented */
+    HFCR_ERR_RANGE = 8          /* a coordinate is outside the range the exact predicates cover */
+} hfcr_status;
+
+typedef enum { HFCR_F32 = 0, HFCR_F64 = 1 } hfcr_dtype;
+
+/* Solver of Eq. 7/8.  MIXED: conjugate gradients in float32 with float64
+ * iterative refinement of the residual against the float64 constraint
+ * gradients; FP64: conjugate gradients in float64 throughout. */
+typedef enum { HFCR_SOLVER_MIXED = 0, HFCR_SOLVER_FP64 = 1 } hfcr_solver;
+
+/* Role schedule of the repair loop when both meshes are oriented (Sec. 4:
+ * "one is regarded as oriented and the other as un-oriented" in the
+ * iterations).  ALTERNATE: iteration i tests direction i mod 2; BOTH: both
+ * directions every iteration. */
+typedef enum { HFCR_ROLES_ALTERNATE = 0, HFCR_ROLES_BOTH = 1 } hfcr_roles;
+
+typedef struct {
+    int32_t dtype;          /* hfcr_dtype of x, y, z */
+    int32_t n_verts;
+    void *x, *y, *z;        /* device [n_verts] each; resolve updates them in place */
+    int32_t n_tris;
+    const int32_t *tris;    /* device [n_tris][3] */
+    int32_t n_edges;        /* 0 with edges == NULL: the library derives them */
+    const int32_t *edges;   /* device [n_edges][2], unique, v0 < v1, lexicographic (see hfcr_build_edges) */
+    int32_t oriented;       /* 1 = faces have a front side (closed outward surface) */
+    const float *inv_mass;  /* device [n_verts] inverse masses M^-1, or NULL for all 1 (Sec. 4) */
+} hfcr_mesh;
+
+/* One E-F intersection: edge (v0 < v1) of the edge mesh crossing `face` of
+ * the oriented mesh; dir 0 = edge of A / face of B, dir 1 = edge of B /
+ * face of A. */
+typedef struct { uint32_t dir, v0, v1, face; } hfcr_pair;
+
+/* One penetration stencil {x0; face} (Sec. 4): x0 is the endpoint of a
+ * crossing edge on the back side of `face`; mesh of x0 and of the face
+ * follow `dir` as in hfcr_pair. */
+typedef struct { uint32_t dir, x0, face, pad; } hfcr_stencil;
+
+typedef struct {
+    int32_t solver;         /* hfcr_solver (default MIXED) */
+    int32_t f32_filter;     /* 1 (default): float32 meshes try the float32 filter first */
+    int32_t roles;          /* hfcr_roles (default ALTERNATE) */
+    int32_t max_cg_iters;   /* per float32 run of MIXED (default 500); FP64 runs once with max_cg_iters * max_refine */
+    int32_t max_refine;     /* refinement rounds of the MIXED solver (default 6) */
+    double rel_tol;         /* target |b - A lambda| / |b| (default 1e-12) */
+    double inner_tol;       /* MIXED: residual reduction of one float32 run (default 1e-5) */
+} hfcr_options;
+
+typedef struct {
+    int32_t cg_iters;        /* conjugate-gradient iterations, all runs */
+    int32_t refine_rounds;   /* MIXED: float64 residual evaluations after the first */
+    double rel_residual;     /* |b - A lambda| / |b| at exit, float64 */
+    int32_t converged;       /* rel_residual <= rel_tol */
+    int32_t n_stencils;
+    int32_t n_touched;       /* distinct vertices in the stencils */
+} hfcr_solve_info;
+
+typedef struct {
+    int64_t narrow_tests;    /* segment-triangle tests run at BVH leaves */
+    int64_t f64_fallbacks;   /* orientation signs the float32 filter left open */
+    int64_t exact_fallbacks; /* signs the float64 filter left open (exact expansion arithmetic) */
+    int64_t brute_force_equiv; /* |E| x |F| summed over the tested directions */
+} hfcr_detect_stats;
+
+typedef struct {
+    int32_t iters;                 /* detections run */
+    int32_t converged;             /* the last detections of every active direction found no pair */
+    int64_t pairs_first;           /* pairs of the first detection */
+    int64_t pairs_last;            /* pairs of the last detection */
+    int64_t total_pairs;           /* pairs over all detections */
+    int64_t total_stencils;
+    int32_t cg_iters;              /* all solves */
+    double worst_rel_residual;     /* largest solver residual over the iterations */
+    hfcr_detect_stats stats;       /* summed over the detections */
+} hfcr_resolve_info;
+
+/* Stages timed by the optional profiler (instrumentation; the paper has no
+ * counterpart). */
+typedef enum {
+    HFCR_STAGE_VALIDATE = 0,  /* input range / finiteness checks */
+    HFCR_STAGE_BVH = 1,       /* hierarchy build and refit */
+    HFCR_STAGE_TRAVERSE = 2,  /* the traversal + exact narrow-phase kernel, one interval per launch */
+    HFCR_STAGE_STENCILS = 3,  /* pair sort, pair records, stencil keys, sort, unique */
+    HFCR_STAGE_ASSEMBLE = 4,  /* constraint rows and the vertex CSR */
+    HFCR_STAGE_SOLVE = 5,     /* Eq. 7 / Eq. 8 solve */
+    HFCR_STAGE_DISPLACE = 6,  /* x' - x and its application */
+    HFCR_N_STAGES = 7
+} hfcr_stage;
+
+typedef struct {
+    double ms[HFCR_N_STAGES];          /* summed CUDA-event time per stage */
+    int64_t intervals[HFCR_N_STAGES];  /* timed intervals per stage */
+} hfcr_profile;
+
+typedef struct hfcr_ctx hfcr_ctx;
+
+/* Create a context.  opt may be NULL (defaults above).  Allocates nothing
+ * on the device.  Returns HFCR_ERR_ARG for a NULL ctx pointer. */
+hfcr_status hfcr_create(hfcr_ctx **ctx, const hfcr_options *opt);
+
+/* Destroy a context and free its scratch.  NULL is accepted. */
+hfcr_status hfcr_destroy(hfcr_ctx *ctx);
+
+/* Allocate the context's device scratch for meshes of up to max_verts
+ * vertices and max_tris triangles each and up to max_pairs E-F pairs per
+ * detection (stencils <= pairs).  May be called again to grow; calls that
+ * exceed the reserved sizes return HFCR_ERR_CAPACITY.  Synchronous. */
+hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int64_t max_pairs);
+
+/* Unique undirected edges (v0 < v1, lexicographic) of a triangle list: the
+ * primitives of the detection (every face-face contact decomposes into two
+ * E-F contacts, Sec. 4).  out: device int32 [cap][2]; *n_out (host) gets
+ * the edge count, HFCR_ERR_CAPACITY if it exceeds cap.  Synchronises. */
+hfcr_status hfcr_build_edges(hfcr_ctx *ctx, const int32_t *tris, int32_t n_tris, int32_t n_verts,
+                             int32_t *out, int64_t cap, int64_t *n_out, void *stream);
+
+/* Exact discrete collision detection (Sec. 3): every E-F pair of the
+ * active directions (0 when B is oriented, 1 when A is), sorted by
+ * (dir, v0, v1, face).  out: device [cap]; *n_out (host) gets the pair
+ * count (HFCR_ERR_CAPACITY when above cap, out then holds the first cap in
+ * unspecified order).  stats may be NULL.  Synchronises. */
+hfcr_status hfcr_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
+                        hfcr_pair *out, int64_t cap, int64_t *n_out,
+                        hfcr_detect_stats *stats, void *stream);
+
+/* Penetration stencils from sorted pairs (Sec. 3 and Sec. 4, Fig. 3):
+ * x0 = the endpoint on the back side of the face (exact sign), identical
+ * (dir, x0, face) merged, sorted.  out: device [cap]; *n_out (host) gets
+ * the count.  Synchronises. */
+hfcr_status hfcr_build_stencils(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
+                                const hfcr_pair *pairs, int64_t n_pairs,
+                                hfcr_stencil *out, int64_t cap, int64_t *n_out, void *stream);
+
+/* Global displacement minimizer (Sec. 4, Eq. 3 via Eq. 8): for k stencils
+ * on the current positions, writes dxA [A.n_verts], dxB [B.n_verts]
+ * (device SoA pairs of three arrays each, in the mesh's dtype: dx?[0]=x,
+ * [1]=y, [2]=z) with x' = x + dx; untouched vertices get 0.  info (host,
+ * may be NULL) is filled after the stream is synchronised when non-NULL. */
+hfcr_status hfcr_respond(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
+                         const hfcr_stencil *st, int64_t k, double d,
+                         void *const *dxA, void *const *dxB, hfcr_solve_info *info, void *stream);
+
+/* The repair loop (Sec. 3): detect, build stencils, displace, repeated
+ * until no E-F intersection remains or max_iters detections ran.  Updates
+ * A and B's positions in place.  info (host) may be NULL.  Returns
+ * HFCR_ERR_NOT_CONVERGED when the loop stopped at max_iters.
+ * Synchronises. */
+hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, int32_t max_iters,
+                         hfcr_resolve_info *info, void *stream);
+
+/* Profiler (instrumentation, no counterpart in the paper).  When enabled,
+ * every later call records CUDA events on its stream around each stage;
+ * enabling resets the sums.  hfcr_profile_read waits for the recorded
+ * events and returns the sums. */
+hfcr_status hfcr_profile_enable(hfcr_ctx *ctx, int32_t on);
+hfcr_status hfcr_profile_read(hfcr_ctx *ctx, hfcr_profile *out);
+
+/* Kernel launches made by this library in this process so far
+ * (instrumentation, no counterpart in the paper). */
+int64_t hfcr_launch_count(void);
+
+/* Message of the last failing call on this context ("" if none). */
+const char *hfcr_last_error(const hfcr_ctx *ctx);
+
+/* Static name of a status code. */
+const char *hfcr_status_string(hfcr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HFCR_H */

@@ -1,0 +1,730 @@
+// C ABI of libhfcr: context, scratch reservation and the entry points that
+// chain the detection (Sec. 3), the stencils (Sec. 4) and the minimizer
+// (Sec. 4, Eqs. 3-8) into the repair loop (Sec. 3).
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace hfcr;
+
+std::atomic<long long> hfcr::g_launches{0};
+
+struct ProfInterval {
+    int stage;
+    cudaEvent_t a, b;
+};
+
+struct hfcr_ctx {
+    hfcr_options opt;
+    std::string err;
+    int64_t max_verts = 0, max_tris = 0, max_pairs = 0;
+    int device = 0;
+    uint32_t *d_status = nullptr;
+    DevStats *d_stats = nullptr;
+    int *d_cnt = nullptr;         // [16] device counters
+    uint32_t *h_status = nullptr; // pinned
+    int *h_cnt = nullptr;         // pinned [16]
+    DevStats *h_stats = nullptr;  // pinned
+    SortTemp sort;
+    Bvh bvh[2];                   // [0]: faces of B (direction 0), [1]: faces of A (direction 1)
+    int *edges[2] = {nullptr, nullptr};
+    unsigned long long *ekeys = nullptr, *ekeys_alt = nullptr;
+    unsigned *eflags = nullptr;
+    unsigned long long *pkeys = nullptr, *pkeys_alt = nullptr;
+    hfcr_pair *pairs = nullptr;
+    unsigned long long *skeys = nullptr, *skeys_alt = nullptr;
+    unsigned *sflags = nullptr;
+    hfcr_stencil *stencils = nullptr;
+    SolveBuffers sb;
+    // profiler
+    bool prof_on = false;
+    double prof_ms[HFCR_N_STAGES] = {0};
+    long long prof_n[HFCR_N_STAGES] = {0};
+    std::vector<ProfInterval> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+};
+
+// device counter slots
+enum { C_PAIRS = 0, C_STENCILS = 1, C_EDGES_A = 2, C_EDGES_B = 3, C_N4 = 4, C_NPAIRS_IN = 5 };
+
+namespace {
+
+hfcr_status fail(hfcr_ctx *c, hfcr_status s, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(ctx, HFCR_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc((void **)p, sizeof(T) * n);
+}
+
+void free_all(hfcr_ctx *c) {
+    void *ptrs[] = {c->d_status, c->d_stats, c->d_cnt, c->sort.hist, c->edges[0], c->edges[1],
+                    c->ekeys, c->ekeys_alt, c->eflags, c->pkeys, c->pkeys_alt, c->pairs,
+                    c->skeys, c->skeys_alt, c->sflags, c->stencils,
+                    c->sb.ids, c->sb.n64, c->sb.n32, c->sb.b, c->sb.lam, c->sb.r64, c->sb.r32,
+                    c->sb.x32, c->sb.p32, c->sb.q32, c->sb.p64, c->sb.q64, c->sb.vidx, c->sb.ckey,
+                    c->sb.ckey_alt, c->sb.cval, c->sb.cval_alt, c->sb.cflag, c->sb.seg, c->sb.gvert,
+                    c->sb.winv, c->sb.u64, c->sb.u32, c->sb.red, c->sb.d_U, c->sb.iwork,
+                    c->sb.dwork};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < 2; ++i) {
+        Bvh &b = c->bvh[i];
+        void *bp[] = {b.nodes, b.parent, b.flags, b.leaf_face, b.leaf_tri, b.keys, b.keys_alt,
+                      b.vals_alt, b.bounds, b.bounds_part};
+        for (void *p : bp)
+            if (p) cudaFree(p);
+        b = Bvh();
+    }
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->h_cnt) cudaFreeHost(c->h_cnt);
+    if (c->h_stats) cudaFreeHost(c->h_stats);
+    c->d_status = nullptr; c->d_stats = nullptr; c->d_cnt = nullptr; c->sort = SortTemp();
+    c->edges[0] = c->edges[1] = nullptr;
+    c->ekeys = c->ekeys_alt = nullptr; c->eflags = nullptr;
+    c->pkeys = c->pkeys_alt = nullptr; c->pairs = nullptr;
+    c->skeys = c->skeys_alt = nullptr; c->sflags = nullptr; c->stencils = nullptr;
+    c->sb = SolveBuffers();
+    c->h_status = nullptr; c->h_cnt = nullptr; c->h_stats = nullptr;
+    c->max_verts = c->max_tris = c->max_pairs = 0;
+}
+
+cudaEvent_t prof_event(hfcr_ctx *c) {
+    cudaEvent_t e = nullptr;
+    if (!c->prof_pool.empty()) {
+        e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+    } else {
+        cudaEventCreate(&e);
+    }
+    return e;
+}
+
+void prof_begin(hfcr_ctx *c, int stage, cudaStream_t s) {
+    if (!c->prof_on) return;
+    ProfInterval iv{stage, prof_event(c), nullptr};
+    cudaEventRecord(iv.a, s);
+    c->prof_pending.push_back(iv);
+}
+
+void prof_end(hfcr_ctx *c, int stage, cudaStream_t s) {
+    if (!c->prof_on) return;
+    for (auto it = c->prof_pending.rbegin(); it != c->prof_pending.rend(); ++it)
+        if (it->stage == stage && !it->b) {
+            it->b = prof_event(c);
+            cudaEventRecord(it->b, s);
+            return;
+        }
+}
+
+// accumulates every closed interval (waits for its end event)
+void prof_collect(hfcr_ctx *c) {
+    std::vector<ProfInterval> keep;
+    for (auto &iv : c->prof_pending) {
+        if (!iv.b) { keep.push_back(iv); continue; }
+        float ms = 0.f;
+        cudaEventSynchronize(iv.b);
+        if (cudaEventElapsedTime(&ms, iv.a, iv.b) == cudaSuccess) {
+            c->prof_ms[iv.stage] += ms;
+            c->prof_n[iv.stage] += 1;
+        }
+        c->prof_pool.push_back(iv.a);
+        c->prof_pool.push_back(iv.b);
+    }
+    c->prof_pending.swap(keep);
+}
+
+hfcr_status device_status(hfcr_ctx *ctx, uint32_t st) {
+    if (st & ST_NONFINITE) return fail(ctx, HFCR_ERR_NONFINITE, "a position is NaN or infinite");
+    if (st & ST_RANGE)
+        return fail(ctx, HFCR_ERR_RANGE,
+                    "a coordinate is outside the exact-predicate range (|c| <= 2^38; float64 "
+                    "nonzero |c| >= 2^-200)");
+    if (st & ST_BAD_INDEX) return fail(ctx, HFCR_ERR_ARG, "a vertex or face index is out of range");
+    if (st & ST_TIMEOUT) return fail(ctx, HFCR_ERR_TIMEOUT, "a device-side wait gave up");
+    return HFCR_OK;
+}
+
+hfcr_status check_mesh(hfcr_ctx *ctx, const hfcr_mesh *m, const char *name) {
+    if (!m) return fail(ctx, HFCR_ERR_ARG, "mesh %s is NULL", name);
+    if (m->dtype != HFCR_F32 && m->dtype != HFCR_F64)
+        return fail(ctx, HFCR_ERR_ARG, "mesh %s: unknown dtype %d", name, m->dtype);
+    if (m->n_verts < 0 || m->n_tris < 0 || m->n_edges < 0)
+        return fail(ctx, HFCR_ERR_ARG, "mesh %s: negative size", name);
+    if (m->n_verts > 0 && (!m->x || !m->y || !m->z))
+        return fail(ctx, HFCR_ERR_ARG, "mesh %s: NULL positions", name);
+    if (m->n_tris > 0 && !m->tris) return fail(ctx, HFCR_ERR_ARG, "mesh %s: NULL tris", name);
+    if (m->n_edges > 0 && !m->edges) return fail(ctx, HFCR_ERR_ARG, "mesh %s: NULL edges", name);
+    if (m->n_verts > ctx->max_verts || m->n_tris > ctx->max_tris)
+        return fail(ctx, HFCR_ERR_CAPACITY,
+                    "mesh %s (%d verts, %d tris) exceeds the reserved %lld verts / %lld tris", name,
+                    m->n_verts, m->n_tris, (long long)ctx->max_verts, (long long)ctx->max_tris);
+    if (m->n_edges > 3 * ctx->max_tris)
+        return fail(ctx, HFCR_ERR_CAPACITY, "mesh %s: too many edges", name);
+    return HFCR_OK;
+}
+
+hfcr_status check_pair(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B) {
+    if (!ctx) return HFCR_ERR_ARG;
+    if (ctx->max_tris == 0) return fail(ctx, HFCR_ERR_CAPACITY, "hfcr_reserve was not called");
+    hfcr_status s = check_mesh(ctx, A, "A");
+    if (s) return s;
+    if ((s = check_mesh(ctx, B, "B"))) return s;
+    if (A->dtype != B->dtype) return fail(ctx, HFCR_ERR_UNSUPPORTED, "A and B differ in dtype");
+    if (!A->oriented && !B->oriented)
+        return fail(ctx, HFCR_ERR_ARG, "at least one mesh must be oriented (Sec. 3)");
+    return HFCR_OK;
+}
+
+// Edges of mesh `which` (0 = A, 1 = B): the caller's, or built into the
+// context (synchronises to learn the count).
+hfcr_status mesh_edges(hfcr_ctx *ctx, const hfcr_mesh *m, int which, const int **edges, int *ne,
+                       cudaStream_t s) {
+    if (m->edges) {
+        *edges = m->edges;
+        *ne = m->n_edges;
+        return HFCR_OK;
+    }
+    int slot = which ? C_EDGES_B : C_EDGES_A;
+    build_edges(m->tris, m->n_tris, m->n_verts, ctx->edges[which], ctx->d_cnt + slot, ctx->ekeys,
+                ctx->ekeys_alt, ctx->eflags, ctx->sort, ctx->d_status, s);
+    CK(cudaMemcpyAsync(ctx->h_cnt + slot, ctx->d_cnt + slot, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *edges = ctx->edges[which];
+    *ne = ctx->h_cnt[slot];
+    return HFCR_OK;
+}
+
+struct DetectPlan {
+    const int *edges[2] = {nullptr, nullptr};  // edges of A, of B
+    int ne[2] = {0, 0};
+    int edge_bits = 1, face_bits = 1;
+};
+
+hfcr_status plan_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool dir0, bool dir1,
+                        DetectPlan &pl, cudaStream_t s) {
+    hfcr_status st;
+    if (dir0 && A->n_tris > 0 && (st = mesh_edges(ctx, A, 0, &pl.edges[0], &pl.ne[0], s))) return st;
+    if (dir1 && B->n_tris > 0 && (st = mesh_edges(ctx, B, 1, &pl.edges[1], &pl.ne[1], s))) return st;
+    int maxe = pl.ne[0] > pl.ne[1] ? pl.ne[0] : pl.ne[1];
+    int maxf = A->n_tris > B->n_tris ? A->n_tris : B->n_tris;
+    pl.edge_bits = bits_for(maxe > 1 ? maxe : 2);
+    pl.face_bits = bits_for(maxf > 1 ? maxf : 2);
+    return HFCR_OK;
+}
+
+// Launches the traversal of the active directions; positions validated and
+// the BVHs refitted (built first when `build`).  Pair keys -> ctx->pkeys.
+void launch_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool dir0, bool dir1,
+                   const DetectPlan &pl, bool *built, cudaStream_t s) {
+    prof_begin(ctx, HFCR_STAGE_VALIDATE, s);
+    validate_positions(*A, ctx->d_status, s);
+    validate_positions(*B, ctx->d_status, s);
+    prof_end(ctx, HFCR_STAGE_VALIDATE, s);
+    for (int d = 0; d < 2; ++d) {
+        if (!(d == 0 ? dir0 : dir1)) continue;
+        const hfcr_mesh &F = d == 0 ? *B : *A;
+        const hfcr_mesh &E = d == 0 ? *A : *B;
+        if (F.n_tris <= 0 || pl.ne[d] <= 0) continue;
+        Bvh &b = ctx->bvh[d];
+        prof_begin(ctx, HFCR_STAGE_BVH, s);
+        if (!built[d] || b.n != F.n_tris) {
+            bvh_build(b, F, ctx->sort, ctx->d_status, s);
+            built[d] = true;
+        }
+        bvh_refit(b, F, ctx->d_status, s);
+        prof_end(ctx, HFCR_STAGE_BVH, s);
+        DetectArgs a;
+        a.edge_mesh = &E;
+        a.edges = pl.edges[d];
+        a.n_edges = pl.ne[d];
+        a.bvh = &b;
+        a.dir = d;
+        a.f32_filter = ctx->opt.f32_filter;
+        a.edge_bits = pl.edge_bits;
+        a.face_bits = pl.face_bits;
+        a.keys = ctx->pkeys;
+        a.d_count = ctx->d_cnt + C_PAIRS;
+        a.cap = (int)ctx->max_pairs;
+        a.stats = ctx->d_stats;
+        prof_begin(ctx, HFCR_STAGE_TRAVERSE, s);
+        detect_launch(a, s, ctx->d_status);
+        prof_end(ctx, HFCR_STAGE_TRAVERSE, s);
+    }
+}
+
+hfcr_status read_back(hfcr_ctx *ctx, cudaStream_t s) {
+    CK(cudaMemcpyAsync(ctx->h_cnt, ctx->d_cnt, sizeof(int) * 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    prof_collect(ctx);
+    return device_status(ctx, *ctx->h_status);
+}
+
+void add_stats(hfcr_detect_stats *o, const DevStats &d, long long bf) {
+    o->narrow_tests += (int64_t)d.narrow_tests;
+    o->f64_fallbacks += (int64_t)d.f64_fallbacks;
+    o->exact_fallbacks += (int64_t)d.exact_fallbacks;
+    o->brute_force_equiv += bf;
+}
+
+// sorted pair keys (count P on the host) -> hfcr_pair records in out
+hfcr_status finish_pairs(hfcr_ctx *ctx, int P, const DetectPlan &pl, hfcr_pair *out,
+                         cudaStream_t s) {
+    if (P <= 0) return HFCR_OK;
+    int bits = 1 + pl.edge_bits + pl.face_bits;
+    prof_begin(ctx, HFCR_STAGE_STENCILS, s);
+    bool flip = radix_sort_u64(ctx->pkeys, nullptr, ctx->pkeys_alt, nullptr, P, bits, ctx->sort, s);
+    unsigned long long *sorted = flip ? ctx->pkeys_alt : ctx->pkeys;
+    keys_to_pairs(sorted, ctx->d_cnt + C_PAIRS, P, pl.edges[0], pl.edges[1], pl.edge_bits,
+                  pl.face_bits, out, s);
+    prof_end(ctx, HFCR_STAGE_STENCILS, s);
+    CK(cudaGetLastError());
+    return HFCR_OK;
+}
+
+// pairs (count in d_cnt[slot]) -> unique stencils in out; returns k on the host
+hfcr_status make_stencils(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
+                          const hfcr_pair *pairs, int P, int slot, hfcr_stencil *out, int64_t *k,
+                          cudaStream_t s) {
+    *k = 0;
+    if (P <= 0) return HFCR_OK;
+    MeshPair mp{*A, *B};
+    int maxv = A->n_verts > B->n_verts ? A->n_verts : B->n_verts;
+    int maxf = A->n_tris > B->n_tris ? A->n_tris : B->n_tris;
+    int vb = bits_for(maxv > 1 ? maxv : 2), fb = bits_for(maxf > 1 ? maxf : 2);
+    prof_begin(ctx, HFCR_STAGE_STENCILS, s);
+    stencil_keys(mp, pairs, ctx->d_cnt + slot, P, vb, fb, ctx->opt.f32_filter, ctx->skeys,
+                 ctx->d_stats, ctx->d_status, s);
+    bool flip = radix_sort_u64(ctx->skeys, nullptr, ctx->skeys_alt, nullptr, P, 1 + vb + fb,
+                               ctx->sort, s);
+    unsigned long long *sorted = flip ? ctx->skeys_alt : ctx->skeys;
+    stencil_unique(sorted, ctx->d_cnt + slot, P, vb, fb, ctx->sflags, out, ctx->d_cnt + C_STENCILS, s);
+    prof_end(ctx, HFCR_STAGE_STENCILS, s);
+    hfcr_status st = read_back(ctx, s);
+    if (st) return st;
+    *k = ctx->h_cnt[C_STENCILS];
+    return HFCR_OK;
+}
+
+SolveParams params_of(const hfcr_options &o) {
+    SolveParams p;
+    p.solver = o.solver;
+    p.max_cg_iters = o.max_cg_iters;
+    p.max_refine = o.max_refine;
+    p.rel_tol = o.rel_tol;
+    p.inner_tol = o.inner_tol;
+    return p;
+}
+
+// assemble, solve and displace k stencils (count in d_cnt[C_STENCILS])
+hfcr_status run_response(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
+                         const hfcr_stencil *st, int k, double d, int apply, void *const *dxA,
+                         void *const *dxB, cudaStream_t s) {
+    if (k <= 0) return HFCR_OK;
+    MeshPair mp{*A, *B};
+    prof_begin(ctx, HFCR_STAGE_ASSEMBLE, s);
+    assemble(mp, st, ctx->d_cnt + C_STENCILS, k, d, ctx->sb, ctx->d_status, s);
+    build_vertex_csr(mp, ctx->d_cnt + C_STENCILS, k, ctx->sb, ctx->sort, ctx->d_cnt + C_N4, s);
+    prof_end(ctx, HFCR_STAGE_ASSEMBLE, s);
+    prof_begin(ctx, HFCR_STAGE_SOLVE, s);
+    solve(params_of(ctx->opt), ctx->d_cnt + C_STENCILS, k, ctx->sb, ctx->d_status, s);
+    prof_end(ctx, HFCR_STAGE_SOLVE, s);
+    prof_begin(ctx, HFCR_STAGE_DISPLACE, s);
+    displacement(mp, k, ctx->sb, apply, dxA, dxB, s);
+    prof_end(ctx, HFCR_STAGE_DISPLACE, s);
+    CK(cudaGetLastError());
+    return HFCR_OK;
+}
+
+hfcr_status solve_info(hfcr_ctx *ctx, int k, hfcr_solve_info *info, cudaStream_t s) {
+    int iw[16] = {0};
+    double dw[1] = {0};
+    if (k > 0) {
+        CK(cudaMemcpyAsync(iw, ctx->sb.iwork, sizeof(int) * 16, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(dw, ctx->sb.dwork, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(ctx->h_cnt + 8, ctx->sb.d_U, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    info->cg_iters = iw[1];
+    info->refine_rounds = iw[3];
+    info->rel_residual = dw[0];
+    info->converged = k == 0 || dw[0] <= ctx->opt.rel_tol;
+    info->n_stencils = k;
+    info->n_touched = k > 0 ? ctx->h_cnt[8] : 0;
+    return HFCR_OK;
+}
+
+hfcr_status reset_words(hfcr_ctx *ctx, cudaStream_t s) {
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s));
+    CK(cudaMemsetAsync(ctx->d_stats, 0, sizeof(DevStats), s));
+    CK(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(int) * 16, s));
+    return HFCR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
+    if (!out) return HFCR_ERR_ARG;
+    hfcr_ctx *c = new (std::nothrow) hfcr_ctx();
+    if (!c) return HFCR_ERR_ARG;
+    c->opt.solver = HFCR_SOLVER_MIXED;
+    c->opt.f32_filter = 1;
+    c->opt.roles = HFCR_ROLES_ALTERNATE;
+    c->opt.max_cg_iters = 500;
+    c->opt.max_refine = 6;
+    c->opt.rel_tol = 1e-12;
+    c->opt.inner_tol = 1e-5;
+    if (opt) {
+        c->opt = *opt;
+        if (c->opt.max_cg_iters <= 0) c->opt.max_cg_iters = 500;
+        if (c->opt.max_refine <= 0) c->opt.max_refine = 6;
+        if (!(c->opt.rel_tol > 0)) c->opt.rel_tol = 1e-12;
+        if (!(c->opt.inner_tol > 0)) c->opt.inner_tol = 1e-5;
+        if (c->opt.solver != HFCR_SOLVER_FP64) c->opt.solver = HFCR_SOLVER_MIXED;
+        if (c->opt.roles != HFCR_ROLES_BOTH) c->opt.roles = HFCR_ROLES_ALTERNATE;
+    }
+    cudaGetDevice(&c->device);
+    *out = c;
+    return HFCR_OK;
+}
+
+hfcr_status hfcr_destroy(hfcr_ctx *ctx) {
+    if (!ctx) return HFCR_OK;
+    prof_collect(ctx);
+    for (auto &iv : ctx->prof_pending) {
+        if (iv.a) cudaEventDestroy(iv.a);
+        if (iv.b) cudaEventDestroy(iv.b);
+    }
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    free_all(ctx);
+    delete ctx;
+    return HFCR_OK;
+}
+
+hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int64_t max_pairs) {
+    if (!ctx) return HFCR_ERR_ARG;
+    if (max_verts < 0 || max_tris < 0 || max_pairs < 0 || max_verts > (1ll << 30) ||
+        max_tris > (1ll << 29) || max_pairs > (1ll << 28))
+        return fail(ctx, HFCR_ERR_ARG, "reserve sizes out of range");
+    if (max_verts <= ctx->max_verts && max_tris <= ctx->max_tris && max_pairs <= ctx->max_pairs)
+        return HFCR_OK;
+    if (max_verts < ctx->max_verts) max_verts = ctx->max_verts;
+    if (max_tris < ctx->max_tris) max_tris = ctx->max_tris;
+    if (max_pairs < ctx->max_pairs) max_pairs = ctx->max_pairs;
+    CK(cudaDeviceSynchronize());
+    free_all(ctx);
+    if (max_tris < 1) max_tris = 1;
+    if (max_pairs < 1) max_pairs = 1;
+    const size_t T = (size_t)max_tris, P = (size_t)max_pairs, E3 = 3 * T;
+    CK(dalloc(&ctx->d_status, 1));
+    CK(dalloc(&ctx->d_stats, 1));
+    CK(dalloc(&ctx->d_cnt, 16));
+    CK(cudaMallocHost((void **)&ctx->h_status, sizeof(uint32_t)));
+    CK(cudaMallocHost((void **)&ctx->h_cnt, sizeof(int) * 16));
+    CK(cudaMallocHost((void **)&ctx->h_stats, sizeof(DevStats)));
+    size_t maxn = E3 > 4 * P ? E3 : 4 * P;
+    ctx->sort.max_blocks = sort_blocks_for((int)maxn) + 1;
+    CK(dalloc(&ctx->sort.hist, 256 * (size_t)ctx->sort.max_blocks));
+    for (int i = 0; i < 2; ++i) {
+        Bvh &b = ctx->bvh[i];
+        b.cap = (int)T;
+        CK(dalloc(&b.nodes, 4 * T));
+        CK(dalloc(&b.parent, 2 * T));
+        CK(dalloc(&b.flags, T));
+        CK(dalloc(&b.leaf_face, T));
+        CK(cudaMalloc(&b.leaf_tri, 80 * T));
+        CK(dalloc(&b.keys, T));
+        CK(dalloc(&b.keys_alt, T));
+        CK(dalloc(&b.vals_alt, T));
+        CK(dalloc(&b.bounds, 8));
+        CK(dalloc(&b.bounds_part, 6 * 1024));
+        CK(dalloc(&ctx->edges[i], 2 * E3));
+    }
+    CK(dalloc(&ctx->ekeys, E3));
+    CK(dalloc(&ctx->ekeys_alt, E3));
+    CK(dalloc(&ctx->eflags, E3));
+    CK(dalloc(&ctx->pkeys, P));
+    CK(dalloc(&ctx->pkeys_alt, P));
+    CK(dalloc(&ctx->pairs, P));
+    CK(dalloc(&ctx->skeys, P));
+    CK(dalloc(&ctx->skeys_alt, P));
+    CK(dalloc(&ctx->sflags, P));
+    CK(dalloc(&ctx->stencils, P));
+    SolveBuffers &sb = ctx->sb;
+    sb.cap_k = (int)P;
+    CK(dalloc(&sb.ids, P));
+    CK(dalloc(&sb.n64, P));
+    CK(dalloc(&sb.n32, P));
+    CK(dalloc(&sb.b, P));
+    CK(dalloc(&sb.lam, P));
+    CK(dalloc(&sb.r64, P));
+    CK(dalloc(&sb.r32, P));
+    CK(dalloc(&sb.x32, P));
+    CK(dalloc(&sb.p32, P));
+    CK(dalloc(&sb.q32, P));
+    CK(dalloc(&sb.p64, 2 * P));
+    CK(dalloc(&sb.q64, P));
+    CK(dalloc(&sb.vidx, P));
+    CK(dalloc(&sb.ckey, 4 * P));
+    CK(dalloc(&sb.ckey_alt, 4 * P));
+    CK(dalloc(&sb.cval, 4 * P));
+    CK(dalloc(&sb.cval_alt, 4 * P));
+    CK(dalloc(&sb.cflag, 4 * P));
+    CK(dalloc(&sb.seg, 4 * P + 1));
+    CK(dalloc(&sb.gvert, 4 * P));
+    CK(dalloc(&sb.winv, 4 * P));
+    CK(dalloc(&sb.u64, 12 * P));
+    CK(dalloc(&sb.u32, 12 * P));
+    CK(dalloc(&sb.red, 1024));
+    CK(dalloc(&sb.d_U, 1));
+    CK(dalloc(&sb.iwork, 16));
+    CK(dalloc(&sb.dwork, 16));
+    ctx->max_verts = max_verts;
+    ctx->max_tris = max_tris;
+    ctx->max_pairs = max_pairs;
+    return HFCR_OK;
+}
+
+hfcr_status hfcr_build_edges(hfcr_ctx *ctx, const int32_t *tris, int32_t n_tris, int32_t n_verts,
+                             int32_t *out, int64_t cap, int64_t *n_out, void *stream) {
+    if (!ctx) return HFCR_ERR_ARG;
+    if (n_tris < 0 || n_verts < 0 || !n_out || (n_tris > 0 && (!tris || !out)))
+        return fail(ctx, HFCR_ERR_ARG, "hfcr_build_edges: bad arguments");
+    if (n_tris > ctx->max_tris) return fail(ctx, HFCR_ERR_CAPACITY, "n_tris exceeds the reservation");
+    cudaStream_t s = (cudaStream_t)stream;
+    *n_out = 0;
+    if (n_tris == 0) return HFCR_OK;
+    hfcr_status st = reset_words(ctx, s);
+    if (st) return st;
+    build_edges(tris, n_tris, n_verts, ctx->edges[0], ctx->d_cnt + C_EDGES_A, ctx->ekeys,
+                ctx->ekeys_alt, ctx->eflags, ctx->sort, ctx->d_status, s);
+    if ((st = read_back(ctx, s))) return st;
+    int ne = ctx->h_cnt[C_EDGES_A];
+    *n_out = ne;
+    if (ne > cap) return fail(ctx, HFCR_ERR_CAPACITY, "%d edges exceed cap %lld", ne, (long long)cap);
+    CK(cudaMemcpyAsync(out, ctx->edges[0], sizeof(int) * 2 * (size_t)ne, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return HFCR_OK;
+}
+
+hfcr_status hfcr_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, hfcr_pair *out,
+                        int64_t cap, int64_t *n_out, hfcr_detect_stats *stats, void *stream) {
+    hfcr_status st = check_pair(ctx, A, B);
+    if (st) return st;
+    if (!n_out || cap < 0 || (cap > 0 && !out)) return fail(ctx, HFCR_ERR_ARG, "hfcr_detect: bad output");
+    cudaStream_t s = (cudaStream_t)stream;
+    *n_out = 0;
+    if (stats) memset(stats, 0, sizeof *stats);
+    if ((st = reset_words(ctx, s))) return st;
+    bool dir0 = B->oriented != 0, dir1 = A->oriented != 0;
+    DetectPlan pl;
+    if ((st = plan_detect(ctx, A, B, dir0, dir1, pl, s))) return st;
+    bool built[2] = {false, false};
+    launch_detect(ctx, A, B, dir0, dir1, pl, built, s);
+    if ((st = read_back(ctx, s))) return st;
+    int P = ctx->h_cnt[C_PAIRS];
+    *n_out = P;
+    if (stats)
+        add_stats(stats, *ctx->h_stats,
+                  (dir0 ? (long long)pl.ne[0] * B->n_tris : 0) + (dir1 ? (long long)pl.ne[1] * A->n_tris : 0));
+    if (P > ctx->max_pairs)
+        return fail(ctx, HFCR_ERR_CAPACITY, "%d pairs exceed the reserved %lld", P,
+                    (long long)ctx->max_pairs);
+    if (P > cap) return fail(ctx, HFCR_ERR_CAPACITY, "%d pairs exceed cap %lld", P, (long long)cap);
+    if ((st = finish_pairs(ctx, P, pl, out, s))) return st;
+    CK(cudaStreamSynchronize(s));
+    return HFCR_OK;
+}
+
+hfcr_status hfcr_build_stencils(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
+                                const hfcr_pair *pairs, int64_t n_pairs, hfcr_stencil *out,
+                                int64_t cap, int64_t *n_out, void *stream) {
+    hfcr_status st = check_pair(ctx, A, B);
+    if (st) return st;
+    if (!n_out || n_pairs < 0 || (n_pairs > 0 && !pairs) || cap < 0 || (cap > 0 && !out))
+        return fail(ctx, HFCR_ERR_ARG, "hfcr_build_stencils: bad arguments");
+    if (n_pairs > ctx->max_pairs)
+        return fail(ctx, HFCR_ERR_CAPACITY, "%lld pairs exceed the reservation", (long long)n_pairs);
+    cudaStream_t s = (cudaStream_t)stream;
+    *n_out = 0;
+    if (n_pairs == 0) return HFCR_OK;
+    if ((st = reset_words(ctx, s))) return st;
+    ctx->h_cnt[C_NPAIRS_IN] = (int)n_pairs;
+    CK(cudaMemcpyAsync(ctx->d_cnt + C_NPAIRS_IN, ctx->h_cnt + C_NPAIRS_IN, sizeof(int),
+                       cudaMemcpyHostToDevice, s));
+    validate_positions(*A, ctx->d_status, s);
+    validate_positions(*B, ctx->d_status, s);
+    int64_t k = 0;
+    if ((st = make_stencils(ctx, A, B, pairs, (int)n_pairs, C_NPAIRS_IN, ctx->stencils, &k, s)))
+        return st;
+    *n_out = k;
+    if (k > cap) return fail(ctx, HFCR_ERR_CAPACITY, "%lld stencils exceed cap %lld", (long long)k, (long long)cap);
+    if (k > 0)
+        CK(cudaMemcpyAsync(out, ctx->stencils, sizeof(hfcr_stencil) * (size_t)k,
+                           cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return HFCR_OK;
+}
+
+hfcr_status hfcr_respond(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
+                         const hfcr_stencil *st_in, int64_t k, double d, void *const *dxA,
+                         void *const *dxB, hfcr_solve_info *info, void *stream) {
+    hfcr_status st = check_pair(ctx, A, B);
+    if (st) return st;
+    if (k < 0 || (k > 0 && !st_in) || !dxA || !dxB || !(d == d))
+        return fail(ctx, HFCR_ERR_ARG, "hfcr_respond: bad arguments");
+    for (int c = 0; c < 3; ++c)
+        if ((A->n_verts > 0 && !dxA[c]) || (B->n_verts > 0 && !dxB[c]))
+            return fail(ctx, HFCR_ERR_ARG, "hfcr_respond: NULL displacement array");
+    if (k > ctx->max_pairs)
+        return fail(ctx, HFCR_ERR_CAPACITY, "%lld stencils exceed the reservation", (long long)k);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = reset_words(ctx, s))) return st;
+    size_t es = A->dtype == HFCR_F32 ? 4 : 8;
+    for (int c = 0; c < 3; ++c) {
+        if (A->n_verts > 0) CK(cudaMemsetAsync(dxA[c], 0, es * (size_t)A->n_verts, s));
+        if (B->n_verts > 0) CK(cudaMemsetAsync(dxB[c], 0, es * (size_t)B->n_verts, s));
+    }
+    ctx->h_cnt[C_STENCILS] = (int)k;
+    CK(cudaMemcpyAsync(ctx->d_cnt + C_STENCILS, ctx->h_cnt + C_STENCILS, sizeof(int),
+                       cudaMemcpyHostToDevice, s));
+    validate_positions(*A, ctx->d_status, s);
+    validate_positions(*B, ctx->d_status, s);
+    if ((st = run_response(ctx, A, B, st_in, (int)k, d, 0, dxA, dxB, s))) return st;
+    if (info) {
+        memset(info, 0, sizeof *info);
+        if ((st = solve_info(ctx, (int)k, info, s))) return st;
+        CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if ((st = device_status(ctx, *ctx->h_status))) return st;
+    }
+    return HFCR_OK;
+}
+
+hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, int32_t max_iters,
+                         hfcr_resolve_info *info, void *stream) {
+    hfcr_status st = check_pair(ctx, A, B);
+    if (st) return st;
+    if (max_iters < 0 || !(d == d)) return fail(ctx, HFCR_ERR_ARG, "hfcr_resolve: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    hfcr_resolve_info loc;
+    memset(&loc, 0, sizeof loc);
+    const bool has0 = B->oriented != 0, has1 = A->oriented != 0;
+    const int n_dirs = (int)has0 + (int)has1;
+    const bool alternate = n_dirs == 2 && ctx->opt.roles == HFCR_ROLES_ALTERNATE;
+    const int need_quiet = alternate ? 2 : 1;
+    if ((st = reset_words(ctx, s))) return st;
+    DetectPlan pl;
+    if ((st = plan_detect(ctx, A, B, has0, has1, pl, s))) return st;
+    bool built[2] = {false, false};
+    int quiet = 0;
+    for (int it = 0; it < max_iters; ++it) {
+        bool d0 = has0, d1 = has1;
+        if (alternate) { d0 = (it % 2) == 0; d1 = !d0; }
+        if ((st = reset_words(ctx, s))) return st;
+        launch_detect(ctx, A, B, d0, d1, pl, built, s);
+        if ((st = read_back(ctx, s))) { loc.iters = it + 1; if (info) *info = loc; return st; }
+        int P = ctx->h_cnt[C_PAIRS];
+        add_stats(&loc.stats, *ctx->h_stats,
+                  (d0 ? (long long)pl.ne[0] * B->n_tris : 0) + (d1 ? (long long)pl.ne[1] * A->n_tris : 0));
+        loc.iters = it + 1;
+        if (it == 0) loc.pairs_first = P;
+        loc.pairs_last = P;
+        loc.total_pairs += P;
+        if (P > ctx->max_pairs) {
+            if (info) *info = loc;
+            return fail(ctx, HFCR_ERR_CAPACITY, "%d pairs exceed the reserved %lld", P,
+                        (long long)ctx->max_pairs);
+        }
+        if (P == 0) {
+            if (++quiet >= need_quiet) { loc.converged = 1; break; }
+            continue;
+        }
+        quiet = 0;
+        if ((st = finish_pairs(ctx, P, pl, ctx->pairs, s))) return st;
+        int64_t k = 0;
+        if ((st = make_stencils(ctx, A, B, ctx->pairs, P, C_PAIRS, ctx->stencils, &k, s))) return st;
+        loc.total_stencils += k;
+        if ((st = run_response(ctx, A, B, ctx->stencils, (int)k, d, 1, nullptr, nullptr, s))) return st;
+        hfcr_solve_info si;
+        if ((st = solve_info(ctx, (int)k, &si, s))) return st;
+        loc.cg_iters += si.cg_iters;
+        if (si.rel_residual > loc.worst_rel_residual) loc.worst_rel_residual = si.rel_residual;
+    }
+    if (info) *info = loc;
+    CK(cudaStreamSynchronize(s));
+    if (!loc.converged) return fail(ctx, HFCR_ERR_NOT_CONVERGED, "repair loop stopped after %d detections", loc.iters);
+    return HFCR_OK;
+}
+
+hfcr_status hfcr_profile_enable(hfcr_ctx *ctx, int32_t on) {
+    if (!ctx) return HFCR_ERR_ARG;
+    prof_collect(ctx);
+    for (int i = 0; i < HFCR_N_STAGES; ++i) {
+        ctx->prof_ms[i] = 0;
+        ctx->prof_n[i] = 0;
+    }
+    ctx->prof_on = on != 0;
+    return HFCR_OK;
+}
+
+hfcr_status hfcr_profile_read(hfcr_ctx *ctx, hfcr_profile *out) {
+    if (!ctx || !out) return HFCR_ERR_ARG;
+    prof_collect(ctx);
+    for (int i = 0; i < HFCR_N_STAGES; ++i) {
+        out->ms[i] = ctx->prof_ms[i];
+        out->intervals[i] = ctx->prof_n[i];
+    }
+    return HFCR_OK;
+}
+
+int64_t hfcr_launch_count(void) { return (int64_t)g_launches.load(); }
+
+const char *hfcr_last_error(const hfcr_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+const char *hfcr_status_string(hfcr_status s) {
+    switch (s) {
+        case HFCR_OK: return "HFCR_OK";
+        case HFCR_ERR_ARG: return "HFCR_ERR_ARG";
+        case HFCR_ERR_CAPACITY: return "HFCR_ERR_CAPACITY";
+        case HFCR_ERR_CUDA: return "HFCR_ERR_CUDA";
+        case HFCR_ERR_NONFINITE: return "HFCR_ERR_NONFINITE";
+        case HFCR_ERR_TIMEOUT: return "HFCR_ERR_TIMEOUT";
+        case HFCR_ERR_NOT_CONVERGED: return "HFCR_ERR_NOT_CONVERGED";
+        case HFCR_ERR_UNSUPPORTED: return "HFCR_ERR_UNSUPPORTED";
+        case HFCR_ERR_RANGE: return "HFCR_ERR_RANGE";
+    }
+    return "HFCR_UNKNOWN";
+}
+
+}  // extern "C"

@@ -1,0 +1,350 @@
+// Topology (edges), input validation and the linear BVH over the faces of
+// an oriented mesh.
+//
+// The paper only says that detection uses tight bounding volumes (Sec. 1);
+// the hierarchy here is a binary radix tree over 30-bit Morton codes of the
+// face centroids (Karras 2012), refitted bottom-up with arrival counters.
+// Boxes are float32 and conservative: for float32 coordinates min/max are
+// exact, for float64 they are rounded outward, so box rejection never drops
+// a true intersection.
+#include <cuda_runtime.h>
+#include <float.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace hfcr {
+
+namespace {
+
+// index into [0, n): out-of-range ids read element 0 and raise ST_BAD_INDEX
+__device__ __forceinline__ int chk(int i, int n, uint32_t *st) {
+    if ((unsigned)i < (unsigned)n) return i;
+    atomicOr(st, ST_BAD_INDEX);
+    return 0;
+}
+
+template <typename T>
+__global__ void k_validate(const T *x, const T *y, const T *z, int n, uint32_t *status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t bad = 0;
+    if (i < n) {
+        T c[3] = {x[i], y[i], z[i]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T v = c[k];
+            if (!isfinite(v)) {
+                bad |= ST_NONFINITE;
+            } else {
+                T a = fabs(v);
+                if (a > (T)0x1p38) bad |= ST_RANGE;
+                if (sizeof(T) == 8 && a != (T)0 && a < (T)0x1p-200) bad |= ST_RANGE;
+            }
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (bad && (threadIdx.x & 31) == 0) atomicOr(status, bad);
+}
+
+__global__ void k_edge_keys(const int *tris, int nt, int vb, unsigned long long *keys,
+                            uint32_t *status, int nv) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int a = v[k], b = v[(k + 1) % 3];
+        if ((unsigned)a >= (unsigned)nv || (unsigned)b >= (unsigned)nv) {
+            atomicOr(status, ST_BAD_INDEX);
+            a = b = 0;
+        }
+        unsigned long long lo = (unsigned)min(a, b), hi = (unsigned)max(a, b);
+        keys[3 * t + k] = (lo << vb) | hi;
+    }
+}
+
+__global__ void k_unique_flags(const unsigned long long *keys, int n, unsigned *flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_write_edges(const unsigned long long *keys, const unsigned *pos, int n, int vb,
+                              int *edges) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (i == 0 || keys[i] != keys[i - 1]) {
+        unsigned long long k = keys[i];
+        unsigned p = pos[i];
+        edges[2 * p] = (int)(k >> vb);
+        edges[2 * p + 1] = (int)(k & ((1ull << vb) - 1));
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load3(const T *x, const T *y, const T *z, int i, T *o) {
+    o[0] = x[i];
+    o[1] = y[i];
+    o[2] = z[i];
+}
+
+__device__ __forceinline__ float lo_f(float v) { return v; }
+__device__ __forceinline__ float hi_f(float v) { return v; }
+__device__ __forceinline__ float lo_f(double v) { return __double2float_rd(v); }
+__device__ __forceinline__ float hi_f(double v) { return __double2float_ru(v); }
+
+// per-block min/max of face centroids (float32 approximations suffice: the
+// codes only order the leaves)
+template <typename T>
+__global__ void k_centroid_bounds(const T *x, const T *y, const T *z, int nv, const int *tris,
+                                  int nt, float *part, uint32_t *st) {
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        T a[3], b[3], c[3];
+        load3(x, y, z, chk(tris[3 * t], nv, st), a);
+        load3(x, y, z, chk(tris[3 * t + 1], nv, st), b);
+        load3(x, y, z, chk(tris[3 * t + 2], nv, st), c);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float m = (float)((a[k] + b[k] + c[k]) / (T)3);
+            lo[k] = fminf(lo[k], m);
+            hi[k] = fmaxf(hi[k], m);
+        }
+    }
+    __shared__ float s[6][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+        if (lane == 0) { s[k][w] = lo[k]; s[3 + k][w] = hi[k]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        int nw = blockDim.x >> 5;
+        float v = s[threadIdx.x][0];
+        for (int i = 1; i < nw; ++i)
+            v = threadIdx.x < 3 ? fminf(v, s[threadIdx.x][i]) : fmaxf(v, s[threadIdx.x][i]);
+        part[6 * blockIdx.x + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_bounds_final(const float *part, int nb, float *bounds) {
+    int k = threadIdx.x;
+    if (k >= 6) return;
+    float v = part[k];
+    for (int i = 1; i < nb; ++i) v = k < 3 ? fminf(v, part[6 * i + k]) : fmaxf(v, part[6 * i + k]);
+    bounds[k] = v;
+}
+
+__device__ __forceinline__ unsigned spread10(unsigned v) {
+    v = (v * 0x00010001u) & 0xFF0000FFu;
+    v = (v * 0x00000101u) & 0x0F00F00Fu;
+    v = (v * 0x00000011u) & 0xC30C30C3u;
+    v = (v * 0x00000005u) & 0x49249249u;
+    return v;
+}
+
+template <typename T>
+__global__ void k_morton(const T *x, const T *y, const T *z, int nv, const int *tris, int nt,
+                         const float *bounds, unsigned *keys, int *vals, uint32_t *st) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    T a[3], b[3], c[3];
+    load3(x, y, z, chk(tris[3 * t], nv, st), a);
+    load3(x, y, z, chk(tris[3 * t + 1], nv, st), b);
+    load3(x, y, z, chk(tris[3 * t + 2], nv, st), c);
+    unsigned q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float m = (float)((a[k] + b[k] + c[k]) / (T)3);
+        float ext = bounds[3 + k] - bounds[k];
+        float u = ext > 0.f ? (m - bounds[k]) / ext : 0.f;
+        u = fminf(fmaxf(u * 1024.f, 0.f), 1023.f);
+        q[k] = (unsigned)u;
+    }
+    keys[t] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+    vals[t] = t;
+}
+
+__device__ __forceinline__ int kdelta(const unsigned *keys, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    unsigned long long ki = ((unsigned long long)keys[i] << 32) | (unsigned)i;
+    unsigned long long kj = ((unsigned long long)keys[j] << 32) | (unsigned)j;
+    return __clzll(ki ^ kj);
+}
+
+// Karras 2012: internal node i covers a key range found from the common
+// prefix lengths of its neighbours; keys made unique by appending i.
+__global__ void k_karras(const unsigned *keys, int n, float4 *nodes, int *iparent, int *lparent) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (kdelta(keys, n, i, i + 1) - kdelta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = kdelta(keys, n, i, i - d);
+    int lmax = 2;
+    while (kdelta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (kdelta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = kdelta(keys, n, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (kdelta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int gamma = i + s * d + min(d, 0);
+    int left = (min(i, j) == gamma) ? ~gamma : gamma;
+    int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    nodes[4 * i + 3] = make_float4(__int_as_float(left), __int_as_float(right), 0.f, 0.f);
+    if (left < 0) lparent[~left] = i; else iparent[left] = i;
+    if (right < 0) lparent[~right] = i; else iparent[right] = i;
+    if (i == 0) iparent[0] = -1;
+}
+
+template <typename T>
+__device__ __forceinline__ void pack_leaf(void *leaf_tri, int j, const T *a, const T *b,
+                                          const T *c, int f);
+template <>
+__device__ __forceinline__ void pack_leaf<float>(void *leaf_tri, int j, const float *a,
+                                                 const float *b, const float *c, int f) {
+    float4 *L = (float4 *)leaf_tri + 3 * j;
+    L[0] = make_float4(a[0], a[1], a[2], b[0]);
+    L[1] = make_float4(b[1], b[2], c[0], c[1]);
+    L[2] = make_float4(c[2], __int_as_float(f), 0.f, 0.f);
+}
+template <>
+__device__ __forceinline__ void pack_leaf<double>(void *leaf_tri, int j, const double *a,
+                                                  const double *b, const double *c, int f) {
+    double2 *L = (double2 *)leaf_tri + 5 * j;
+    L[0] = make_double2(a[0], a[1]);
+    L[1] = make_double2(a[2], b[0]);
+    L[2] = make_double2(b[1], b[2]);
+    L[3] = make_double2(c[0], c[1]);
+    L[4] = make_double2(c[2], __longlong_as_double((long long)f));
+}
+
+template <typename T>
+__global__ void k_refit(const T *x, const T *y, const T *z, int nv, const int *tris,
+                        const int *leaf_face, int n, float4 *nodes, const int *iparent,
+                        const int *lparent, unsigned *flags, void *leaf_tri, uint32_t *st) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int f = leaf_face[j];
+    T a[3], b[3], c[3];
+    load3(x, y, z, chk(tris[3 * f], nv, st), a);
+    load3(x, y, z, chk(tris[3 * f + 1], nv, st), b);
+    load3(x, y, z, chk(tris[3 * f + 2], nv, st), c);
+    pack_leaf<T>(leaf_tri, j, a, b, c, f);
+    if (n == 1) return;
+    float lo[3], hi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = lo_f(fmin(fmin(a[k], b[k]), c[k]));
+        hi[k] = hi_f(fmax(fmax(a[k], b[k]), c[k]));
+    }
+    int node = lparent[j];
+    int child = ~j;
+    // bounded by the tree depth (< 64 for unique 62-bit keys); the guard
+    // only keeps a corrupted parent array from looping
+    for (int guard = 0; guard < 128 && node >= 0; ++guard) {
+        float *nf = (float *)(nodes + 4 * node);
+        int c0 = __float_as_int(nf[12]);
+        int slot = (c0 == child) ? 0 : 6;
+        nf[slot + 0] = lo[0];
+        nf[slot + 1] = lo[1];
+        nf[slot + 2] = lo[2];
+        nf[slot + 3] = hi[0];
+        nf[slot + 4] = hi[1];
+        nf[slot + 5] = hi[2];
+        __threadfence();
+        unsigned old = atomicAdd(&flags[node], 1u);
+        if (old == 0) return;
+        __threadfence();
+        int sib = 6 - slot;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(lo[k], __ldcg(nf + sib + k));
+            hi[k] = fmaxf(hi[k], __ldcg(nf + sib + 3 + k));
+        }
+        child = node;
+        node = iparent[node];
+    }
+}
+
+}  // namespace
+
+void validate_positions(const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s) {
+    if (m.n_verts <= 0) return;
+    int nb = (m.n_verts + 255) / 256;
+    if (m.dtype == HFCR_F32)
+        { k_validate<float><<<nb, 256, 0, s>>>((const float *)m.x, (const float *)m.y,
+                                             (const float *)m.z, m.n_verts, d_status); note_launch(); }
+    else
+        { k_validate<double><<<nb, 256, 0, s>>>((const double *)m.x, (const double *)m.y,
+                                              (const double *)m.z, m.n_verts, d_status); note_launch(); }
+}
+
+void build_edges(const int *tris, int n_tris, int n_verts, int *edges_out, int *d_count,
+                 unsigned long long *keys, unsigned long long *keys_alt, unsigned *flags,
+                 SortTemp &t, uint32_t *d_status, cudaStream_t s) {
+    int n = 3 * n_tris;
+    if (n == 0) {
+        cudaMemsetAsync(d_count, 0, sizeof(int), s);
+        return;
+    }
+    int vb = bits_for(n_verts > 1 ? n_verts : 2);
+    { k_edge_keys<<<(n_tris + 255) / 256, 256, 0, s>>>(tris, n_tris, vb, keys, d_status, n_verts); note_launch(); }
+    bool flip = radix_sort_u64(keys, nullptr, keys_alt, nullptr, n, 2 * vb, t, s);
+    unsigned long long *sorted = flip ? keys_alt : keys;
+    { k_unique_flags<<<(n + 255) / 256, 256, 0, s>>>(sorted, n, flags); note_launch(); }
+    scan_flags_dev(flags, nullptr, n, d_count, s);
+    { k_write_edges<<<(n + 255) / 256, 256, 0, s>>>(sorted, flags, n, vb, edges_out); note_launch(); }
+}
+
+void bvh_build(Bvh &b, const hfcr_mesh &m, SortTemp &t, uint32_t *d_status, cudaStream_t s) {
+    int nv = m.n_verts;
+    int n = m.n_tris;
+    b.n = n;
+    b.dtype = m.dtype;
+    if (n <= 0) return;
+    int nb = (n + 255) / 256;
+    int nbb = nb < 1024 ? nb : 1024;
+    if (m.dtype == HFCR_F32) {
+        const float *x = (const float *)m.x, *y = (const float *)m.y, *z = (const float *)m.z;
+        { k_centroid_bounds<float><<<nbb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds_part, d_status); note_launch(); }
+        { k_bounds_final<<<1, 32, 0, s>>>(b.bounds_part, nbb, b.bounds); note_launch(); }
+        { k_morton<float><<<nb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds, b.keys, b.leaf_face, d_status); note_launch(); }
+    } else {
+        const double *x = (const double *)m.x, *y = (const double *)m.y, *z = (const double *)m.z;
+        { k_centroid_bounds<double><<<nbb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds_part, d_status); note_launch(); }
+        { k_bounds_final<<<1, 32, 0, s>>>(b.bounds_part, nbb, b.bounds); note_launch(); }
+        { k_morton<double><<<nb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds, b.keys, b.leaf_face, d_status); note_launch(); }
+    }
+    bool flip = radix_sort_u32(b.keys, b.leaf_face, b.keys_alt, b.vals_alt, n, 30, t, s);
+    if (flip) {
+        cudaMemcpyAsync(b.keys, b.keys_alt, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(b.leaf_face, b.vals_alt, sizeof(int) * n, cudaMemcpyDeviceToDevice, s);
+    }
+    if (n > 1)
+        { k_karras<<<(n - 1 + 255) / 256, 256, 0, s>>>(b.keys, n, b.nodes, b.parent, b.parent + b.cap); note_launch(); }
+}
+
+void bvh_refit(Bvh &b, const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s) {
+    int n = b.n;
+    if (n <= 0) return;
+    if (n > 1) cudaMemsetAsync(b.flags, 0, sizeof(unsigned) * (n - 1), s);
+    int nb = (n + 255) / 256;
+    if (m.dtype == HFCR_F32)
+        { k_refit<float><<<nb, 256, 0, s>>>((const float *)m.x, (const float *)m.y, (const float *)m.z,
+                                          m.n_verts, m.tris, b.leaf_face, n, b.nodes, b.parent,
+                                          b.parent + b.cap, b.flags, b.leaf_tri, d_status); note_launch(); }
+    else
+        { k_refit<double><<<nb, 256, 0, s>>>((const double *)m.x, (const double *)m.y,
+                                           (const double *)m.z, m.n_verts, m.tris, b.leaf_face, n,
+                                           b.nodes, b.parent, b.parent + b.cap, b.flags, b.leaf_tri,
+                                           d_status); note_launch(); }
+}
+
+}  // namespace hfcr

@@ -1,0 +1,286 @@
+// Narrow and broad phase of the edge-face detection (Sec. 3) and the
+// penetration stencils (Sec. 4, Fig. 3).
+//
+// One thread per edge of the edge mesh walks the BVH of the oriented mesh's
+// faces with the edge's box, testing both children of a node with one
+// 64-byte node load; at a leaf the exact segment-triangle test decides.
+// Hits are appended (one atomic per hit) as 64-bit keys
+// (dir | edge | face), which a radix sort turns into the lexicographic
+// (dir, v0, v1, face) order because the edges are sorted by (v0, v1).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "predicates.cuh"
+
+namespace hfcr {
+
+namespace {
+
+constexpr int STACK = 64;
+
+__device__ __forceinline__ int chk(int i, int n, uint32_t *st) {
+    if ((unsigned)i < (unsigned)n) return i;
+    atomicOr(st, ST_BAD_INDEX);
+    return 0;
+}
+
+__device__ __forceinline__ bool overlap(const float *lo, const float *hi, float l0, float l1,
+                                        float l2, float h0, float h1, float h2) {
+    return lo[0] <= h0 && l0 <= hi[0] && lo[1] <= h1 && l1 <= hi[1] && lo[2] <= h2 && l2 <= hi[2];
+}
+
+__device__ __forceinline__ float lo_f(float v) { return v; }
+__device__ __forceinline__ float hi_f(float v) { return v; }
+__device__ __forceinline__ float lo_f(double v) { return __double2float_rd(v); }
+__device__ __forceinline__ float hi_f(double v) { return __double2float_ru(v); }
+
+template <typename T>
+struct Leaf;
+template <>
+struct Leaf<float> {
+    float a[3], b[3], c[3];
+    int face;
+    __device__ __forceinline__ void load(const void *base, int j) {
+        const float4 *L = (const float4 *)base + 3 * j;
+        float4 l0 = __ldg(L), l1 = __ldg(L + 1), l2 = __ldg(L + 2);
+        a[0] = l0.x; a[1] = l0.y; a[2] = l0.z; b[0] = l0.w;
+        b[1] = l1.x; b[2] = l1.y; c[0] = l1.z; c[1] = l1.w;
+        c[2] = l2.x; face = __float_as_int(l2.y);
+    }
+};
+template <>
+struct Leaf<double> {
+    double a[3], b[3], c[3];
+    int face;
+    __device__ __forceinline__ void load(const void *base, int j) {
+        const double2 *L = (const double2 *)base + 5 * j;
+        double2 l0 = __ldg(L), l1 = __ldg(L + 1), l2 = __ldg(L + 2), l3 = __ldg(L + 3),
+                l4 = __ldg(L + 4);
+        a[0] = l0.x; a[1] = l0.y; a[2] = l1.x; b[0] = l1.y;
+        b[1] = l2.x; b[2] = l2.y; c[0] = l3.x; c[1] = l3.y;
+        c[2] = l4.x; face = (int)__double_as_longlong(l4.y);
+    }
+};
+
+template <typename T, bool F32F>
+__device__ __forceinline__ bool leaf_test(const T *p, const T *q, const Leaf<T> &L, DevStats *st) {
+    int side;
+    if constexpr (F32F && sizeof(T) == 4) {
+        f3 P = {(float)p[0], (float)p[1], (float)p[2]}, Q = {(float)q[0], (float)q[1], (float)q[2]};
+        f3 A = {(float)L.a[0], (float)L.a[1], (float)L.a[2]};
+        f3 B = {(float)L.b[0], (float)L.b[1], (float)L.b[2]};
+        f3 C = {(float)L.c[0], (float)L.c[1], (float)L.c[2]};
+        return segtri_f32(P, Q, A, B, C, side, st);
+    } else {
+        return segtri_f64<T>(p, q, L.a, L.b, L.c, side, st);
+    }
+}
+
+template <typename T, bool F32F>
+__global__ void __launch_bounds__(256) k_traverse(
+    const int2 *edges, int ne, const T *ex, const T *ey, const T *ez, int nv, const float4 *nodes,
+    const void *leaf_tri, int nleaf, unsigned long long dirbit, int face_bits,
+    unsigned long long *out, int *count, int cap, DevStats *st, uint32_t *status) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned tests = 0;
+    if (e < ne && nleaf > 0) {
+        int2 ev = edges[e];
+        int i0 = chk(ev.x, nv, status), i1 = chk(ev.y, nv, status);
+        T p[3] = {ex[i0], ey[i0], ez[i0]}, q[3] = {ex[i1], ey[i1], ez[i1]};
+        float lo[3], hi[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = lo_f(p[k] < q[k] ? p[k] : q[k]);
+            hi[k] = hi_f(p[k] < q[k] ? q[k] : p[k]);
+        }
+        const unsigned long long ebits = ((unsigned long long)e) << face_bits;
+        int stack[STACK];
+        int sp = 0;
+        int node = nleaf == 1 ? ~0 : 0;
+        // a tree of nleaf leaves has 2 nleaf - 1 nodes; each is visited at
+        // most once per edge, so the bound only guards a corrupted tree
+        int visits = 0;
+        const int max_visits = 2 * nleaf + 8;
+        while (true) {
+            if (++visits > max_visits) {
+                atomicOr(status, ST_BAD_INDEX);
+                break;
+            }
+            int leaf0 = -1, leaf1 = -1;
+            int next = -1, push = -1;
+            if (node < 0) {
+                leaf0 = ~node;
+            } else {
+                const float4 *nd = nodes + 4 * node;
+                float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+                int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+                bool h0 = overlap(lo, hi, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
+                bool h1 = overlap(lo, hi, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
+                if (h0) { if (c0 < 0) leaf0 = ~c0; else next = c0; }
+                if (h1) {
+                    if (c1 < 0) leaf1 = ~c1;
+                    else if (next < 0) next = c1;
+                    else push = c1;
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                int lf = w ? leaf1 : leaf0;
+                if (lf >= 0) {
+                    Leaf<T> L;
+                    L.load(leaf_tri, lf);
+                    ++tests;
+                    if (leaf_test<T, F32F>(p, q, L, st)) {
+                        int pos = atomicAdd(count, 1);
+                        if (pos < cap) out[pos] = dirbit | ebits | (unsigned)L.face;
+                    }
+                }
+            }
+            if (push >= 0) {
+                if (sp < STACK) stack[sp++] = push;
+                else atomicOr(status, ST_BAD_INDEX);  // unreachable: depth < 64
+            }
+            if (next >= 0) {
+                node = next;
+                continue;
+            }
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    unsigned tot = __reduce_add_sync(0xffffffffu, tests);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&st->narrow_tests, (unsigned long long)tot);
+}
+
+__global__ void k_keys_to_pairs(const unsigned long long *keys, const int *d_n, int cap,
+                                const int2 *edgesA, const int2 *edgesB, int edge_bits,
+                                int face_bits, hfcr_pair *out) {
+    int n = min(*d_n, cap);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long k = keys[i];
+    unsigned dir = (unsigned)(k >> (edge_bits + face_bits));
+    unsigned e = (unsigned)((k >> face_bits) & ((1ull << edge_bits) - 1));
+    unsigned f = (unsigned)(k & ((1ull << face_bits) - 1));
+    int2 ev = dir ? edgesB[e] : edgesA[e];
+    out[i] = hfcr_pair{dir, (unsigned)ev.x, (unsigned)ev.y, f};
+}
+
+template <typename T>
+__device__ __forceinline__ void ld3(const hfcr_mesh &m, int i, T *o) {
+    o[0] = ((const T *)m.x)[i];
+    o[1] = ((const T *)m.y)[i];
+    o[2] = ((const T *)m.z)[i];
+}
+
+// x0 = the endpoint of the pair's edge on the back side of its face
+template <typename T>
+__global__ void k_stencil_keys(hfcr_mesh A, hfcr_mesh B, const hfcr_pair *pairs, const int *d_n,
+                               int cap, int vert_bits, int face_bits, int f32_filter,
+                               unsigned long long *keys, DevStats *st, uint32_t *status) {
+    int n = min(*d_n, cap);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    hfcr_pair pr = pairs[i];
+    unsigned dir = pr.dir ? 1u : 0u;
+    if (pr.dir > 1u) atomicOr(status, ST_BAD_INDEX);
+    const hfcr_mesh &E = dir ? B : A;
+    const hfcr_mesh &F = dir ? A : B;
+    int v0 = chk((int)pr.v0, E.n_verts, status), v1 = chk((int)pr.v1, E.n_verts, status);
+    int f = chk((int)pr.face, F.n_tris, status);
+    int ia = chk(F.tris[3 * f], F.n_verts, status), ib = chk(F.tris[3 * f + 1], F.n_verts, status),
+        ic = chk(F.tris[3 * f + 2], F.n_verts, status);
+    T a[3], b[3], c[3], p[3];
+    ld3<T>(F, ia, a);
+    ld3<T>(F, ib, b);
+    ld3<T>(F, ic, c);
+    ld3<T>(E, v0, p);
+    int s = orient_full<T>(a, b, c, p, f32_filter, st);
+    // a crossing pair has s != 0; a pair given by the caller with the first
+    // endpoint on the plane keeps v1 (the crossing test would reject it)
+    unsigned x0 = s < 0 ? (unsigned)v0 : (unsigned)v1;
+    keys[i] = ((unsigned long long)dir << (vert_bits + face_bits)) |
+              ((unsigned long long)x0 << face_bits) | (unsigned long long)(unsigned)f;
+}
+
+__global__ void k_stencil_flags(const unsigned long long *keys, const int *d_n, int cap,
+                                unsigned *flags) {
+    int n = min(*d_n, cap);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_stencil_write(const unsigned long long *keys, const unsigned *pos,
+                                const int *d_n, int cap, int vert_bits, int face_bits,
+                                hfcr_stencil *out) {
+    int n = min(*d_n, cap);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (i == 0 || keys[i] != keys[i - 1]) {
+        unsigned long long k = keys[i];
+        hfcr_stencil s;
+        s.dir = (unsigned)(k >> (vert_bits + face_bits));
+        s.x0 = (unsigned)((k >> face_bits) & ((1ull << vert_bits) - 1));
+        s.face = (unsigned)(k & ((1ull << face_bits) - 1));
+        s.pad = 0;
+        out[pos[i]] = s;
+    }
+}
+
+}  // namespace
+
+void detect_launch(const DetectArgs &a, cudaStream_t s, uint32_t *d_status) {
+    if (a.n_edges <= 0 || a.bvh->n <= 0) return;
+    const hfcr_mesh &m = *a.edge_mesh;
+    int nb = (a.n_edges + 255) / 256;
+    unsigned long long dirbit = (unsigned long long)a.dir << (a.edge_bits + a.face_bits);
+    const int2 *E = (const int2 *)a.edges;
+    if (m.dtype == HFCR_F32) {
+        const float *x = (const float *)m.x, *y = (const float *)m.y, *z = (const float *)m.z;
+        if (a.f32_filter)
+            { k_traverse<float, true><<<nb, 256, 0, s>>>(E, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes,
+                                                       a.bvh->leaf_tri, a.bvh->n, dirbit, a.face_bits,
+                                                       a.keys, a.d_count, a.cap, a.stats, d_status); note_launch(); }
+        else
+            { k_traverse<float, false><<<nb, 256, 0, s>>>(E, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes,
+                                                        a.bvh->leaf_tri, a.bvh->n, dirbit, a.face_bits,
+                                                        a.keys, a.d_count, a.cap, a.stats, d_status); note_launch(); }
+    } else {
+        const double *x = (const double *)m.x, *y = (const double *)m.y, *z = (const double *)m.z;
+        { k_traverse<double, false><<<nb, 256, 0, s>>>(E, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes,
+                                                     a.bvh->leaf_tri, a.bvh->n, dirbit, a.face_bits,
+                                                     a.keys, a.d_count, a.cap, a.stats, d_status); note_launch(); }
+    }
+}
+
+void keys_to_pairs(const unsigned long long *keys, const int *d_n, int cap, const int *edgesA,
+                   const int *edgesB, int edge_bits, int face_bits, hfcr_pair *out, cudaStream_t s) {
+    if (cap <= 0) return;
+    { k_keys_to_pairs<<<(cap + 255) / 256, 256, 0, s>>>(keys, d_n, cap, (const int2 *)edgesA,
+                                                      (const int2 *)edgesB, edge_bits, face_bits, out); note_launch(); }
+}
+
+void stencil_keys(const MeshPair &mp, const hfcr_pair *pairs, const int *d_n, int cap,
+                  int vert_bits, int face_bits, int f32_filter, unsigned long long *keys,
+                  DevStats *stats, uint32_t *d_status, cudaStream_t s) {
+    if (cap <= 0) return;
+    int nb = (cap + 255) / 256;
+    if (mp.A.dtype == HFCR_F32)
+        { k_stencil_keys<float><<<nb, 256, 0, s>>>(mp.A, mp.B, pairs, d_n, cap, vert_bits, face_bits,
+                                                 f32_filter, keys, stats, d_status); note_launch(); }
+    else
+        { k_stencil_keys<double><<<nb, 256, 0, s>>>(mp.A, mp.B, pairs, d_n, cap, vert_bits, face_bits,
+                                                  f32_filter, keys, stats, d_status); note_launch(); }
+}
+
+void stencil_unique(const unsigned long long *keys, const int *d_n, int cap, int vert_bits,
+                    int face_bits, unsigned *flags, hfcr_stencil *out, int *d_k, cudaStream_t s) {
+    if (cap <= 0) return;
+    int nb = (cap + 255) / 256;
+    { k_stencil_flags<<<nb, 256, 0, s>>>(keys, d_n, cap, flags); note_launch(); }
+    scan_flags_dev(flags, d_n, cap, d_k, s);
+    { k_stencil_write<<<nb, 256, 0, s>>>(keys, flags, d_n, cap, vert_bits, face_bits, out); note_launch(); }
+}
+
+}  // namespace hfcr

@@ -1,0 +1,177 @@
+// Internal declarations shared by the translation units of libhfcr.
+// Host-side launch wrappers only; every device function a kernel needs is
+// defined in the translation unit (or the .cuh header) that launches it.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <atomic>
+#include <string>
+
+#include "../../include/hfcr.h"
+
+namespace hfcr {
+
+// Process-wide count of kernel launches made by this library.
+extern std::atomic<long long> g_launches;
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Device-side status bits (one 32-bit word per context, OR-ed by kernels).
+enum : uint32_t {
+    ST_NONFINITE = 1u << 0,
+    ST_RANGE = 1u << 1,
+    ST_CAPACITY = 1u << 2,
+    ST_TIMEOUT = 1u << 3,
+    ST_BAD_INDEX = 1u << 4,
+};
+
+// Counters a detection accumulates on the device.
+struct DevStats {
+    unsigned long long narrow_tests;
+    unsigned long long f64_fallbacks;
+    unsigned long long exact_fallbacks;
+    unsigned long long pad;
+};
+
+// A BVH over the faces of one mesh (Karras 2012 binary radix tree).
+// Internal node i (0 <= i < n-1) is stored as 4 x 16 bytes:
+//   [c0.lo.xyz, c0.hi.x] [c0.hi.yz, c1.lo.xy] [c1.lo.z, c1.hi.xyz] [child0, child1, -, -]
+// child >= 0 is an internal node, child < 0 the leaf ~child.  Leaf j holds
+// face leaf_face[j]; its triangle is packed (in leaf order) for the
+// narrow phase: float32 meshes 3 x float4 (a.xyz b.x | b.yz c.xy | c.z face - -),
+// float64 meshes 5 x double2 (a.xy | a.z b.x | b.yz | c.xy | c.z face).
+struct Bvh {
+    int n = 0;                  // leaves (faces)
+    int cap = 0;
+    float4 *nodes = nullptr;    // [4 * (cap - 1)]
+    int *parent = nullptr;      // [2 * cap - 1]: parent of internal i at [i], of leaf j at [cap - 1 + j]
+    unsigned *flags = nullptr;  // [cap - 1] arrival counters of the refit
+    int *leaf_face = nullptr;   // [cap]
+    void *leaf_tri = nullptr;   // [cap] packed triangles
+    unsigned *keys = nullptr;   // [cap] Morton codes (sort scratch)
+    unsigned *keys_alt = nullptr;
+    int *vals_alt = nullptr;
+    float *bounds = nullptr;    // [6] scene bounds of the centroids
+    float *bounds_part = nullptr;  // per-block partial bounds
+    int dtype = 0;
+};
+
+struct SortTemp {
+    unsigned *hist = nullptr;   // [256 * max_blocks]
+    int max_blocks = 0;
+};
+
+// Radix sort (stable LSD, 8-bit digits) of keys with optional int values.
+// Sorts bits [0, bits).  Ping-pongs between (k0, v0) and (k1, v1); returns
+// true when the result ended in (k1, v1).  n is read from the host.
+bool radix_sort_u32(unsigned *k0, int *v0, unsigned *k1, int *v1, int n, int bits,
+                    SortTemp &t, cudaStream_t s);
+bool radix_sort_u64(unsigned long long *k0, int *v0, unsigned long long *k1, int *v1, int n,
+                    int bits, SortTemp &t, cudaStream_t s);
+// Same with the element count read from a device word (launch sized by cap).
+bool radix_sort_u64_dev(unsigned long long *k0, unsigned long long *k1, const int *d_n, int cap,
+                        int bits, SortTemp &t, cudaStream_t s);
+bool radix_sort_u32_dev(unsigned *k0, int *v0, unsigned *k1, int *v1, const int *d_n, int cap,
+                        int bits, SortTemp &t, cudaStream_t s);
+int sort_blocks_for(int n);
+
+// Exclusive scan of n unsigned flags (in place), total written to *d_total.
+// n read from a device word, cap bounds it.
+void scan_flags_dev(unsigned *flags, const int *d_n, int cap, int *d_total, cudaStream_t s);
+
+// ---- topology ----
+// Unique sorted edges of a triangle list.  Scratch: keys/keys_alt of
+// 3 * n_tris u64 and flags of 3 * n_tris unsigned.
+void build_edges(const int *tris, int n_tris, int n_verts, int *edges_out, int *d_count,
+                 unsigned long long *keys, unsigned long long *keys_alt, unsigned *flags,
+                 SortTemp &t, uint32_t *d_status, cudaStream_t s);
+
+// ---- BVH ----
+void bvh_build(Bvh &b, const hfcr_mesh &m, SortTemp &t, uint32_t *d_status, cudaStream_t s);
+void bvh_refit(Bvh &b, const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s);
+
+// ---- validation ----
+void validate_positions(const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s);
+
+// ---- detection ----
+struct DetectArgs {
+    const hfcr_mesh *edge_mesh;
+    const int *edges;   // [n_edges][2]
+    int n_edges;
+    const Bvh *bvh;     // over the faces of the other mesh
+    int dir;
+    int f32_filter;
+    int edge_bits, face_bits;  // key layout
+    unsigned long long *keys;  // output keys (dir | edge | face)
+    int *d_count;
+    int cap;
+    DevStats *stats;
+};
+void detect_launch(const DetectArgs &a, cudaStream_t s, uint32_t *d_status);
+// keys (sorted) -> hfcr_pair records
+void keys_to_pairs(const unsigned long long *keys, const int *d_n, int cap, const int *edgesA,
+                   const int *edgesB, int edge_bits, int face_bits, hfcr_pair *out, cudaStream_t s);
+
+// ---- stencils ----
+struct MeshPair {
+    hfcr_mesh A, B;
+};
+// one stencil key per pair (dir | x0 | face); n pairs from host count
+void stencil_keys(const MeshPair &mp, const hfcr_pair *pairs, const int *d_n, int cap,
+                  int vert_bits, int face_bits, int f32_filter, unsigned long long *keys,
+                  DevStats *stats, uint32_t *d_status, cudaStream_t s);
+// sorted keys -> unique stencils, count to d_k
+void stencil_unique(const unsigned long long *keys, const int *d_n, int cap, int vert_bits,
+                    int face_bits, unsigned *flags, hfcr_stencil *out, int *d_k, cudaStream_t s);
+
+// ---- solver ----
+struct SolveBuffers {
+    int cap_k = 0;       // stencils
+    int4 *ids = nullptr;         // [cap_k] global vertex ids
+    double4_32a *n64 = nullptr;      // [cap_k] unit normal (w unused)
+    float4 *n32 = nullptr;       // [cap_k]
+    double *b = nullptr;         // [cap_k] D - d
+    double *lam = nullptr;       // [cap_k]
+    double *r64 = nullptr;       // [cap_k]
+    float *r32 = nullptr, *x32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // [cap_k]
+    double *p64 = nullptr, *q64 = nullptr;   // p64 [2 cap_k] (x and p), q64 [cap_k] (FP64 solver)
+    int4 *vidx = nullptr;        // [cap_k] compact vertex index of each stencil role
+    // vertex CSR over 4k entries
+    unsigned *ckey = nullptr, *ckey_alt = nullptr;   // [4 cap_k]
+    int *cval = nullptr, *cval_alt = nullptr;        // [4 cap_k]
+    unsigned *cflag = nullptr;                       // [4 cap_k]
+    int *seg = nullptr;          // [4 cap_k + 1]
+    int *gvert = nullptr;        // [4 cap_k]
+    float *winv = nullptr;       // [4 cap_k]
+    double *u64 = nullptr;       // [3 * 4 cap_k]
+    float *u32 = nullptr;        // [3 * 4 cap_k]
+    double *red = nullptr;       // reduction partials [1024]
+    int *d_U = nullptr;          // touched vertex count (device)
+    int *iwork = nullptr;        // [16] solver control words
+    double *dwork = nullptr;     // [16]
+};
+
+struct SolveParams {
+    int solver;
+    int max_cg_iters;
+    int max_refine;
+    double rel_tol;
+    double inner_tol;
+};
+
+void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int cap, double d,
+              SolveBuffers &sb, uint32_t *d_status, cudaStream_t s);
+// d_n4: device word receiving 4k (the CSR entry count)
+void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers &sb, SortTemp &t,
+                      int *d_n4, cudaStream_t s);
+// Solves and leaves lambda in sb.lam; results (iters, residual) in sb.iwork / sb.dwork.
+void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint32_t *d_status,
+           cudaStream_t s);
+// dx = -M^-1 J^T lambda for the touched vertices; apply to positions (apply=1)
+// or write full dx arrays (zeroed first).
+void displacement(const MeshPair &mp, int cap, SolveBuffers &sb, int apply, void *const *dxA,
+                  void *const *dxB, cudaStream_t s);
+
+int bits_for(long long n);  // smallest b with n <= 2^b (at least 1)
+
+}  // namespace hfcr

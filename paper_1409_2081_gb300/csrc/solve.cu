@@ -1,0 +1,432 @@
+// Constraint assembly and the global displacement minimizer (Sec. 4).
+//
+// Stencil s = {x0; x1, x2, x3} gives the row of grad(D) (Eq. 2): +n^T at x0
+// and -n^T/3 at x1, x2, x3, n the unit normal of the face on the
+// pre-response positions; D = n . (x0 - (x1 + x2 + x3)/3) (Eq. 1) and the
+// right-hand side of Eq. 8 is b = D - d.  The system
+// grad(D) M^-1 grad(D)^T lambda = b (Eq. 7 / Eq. 8) is solved matrix-free:
+//   u = M^-1 grad(D)^T p   (per touched vertex: a fixed-order sum over the
+//                           vertex's stencil entries, a CSR built by a
+//                           stable sort, hence deterministic)
+//   q = grad(D) u          (per stencil: gather of four vertices).
+// Displacement x' - x = -M^-1 grad(D)^T lambda (Eq. 5).
+//
+// MIXED: conjugate gradients in float32 on float32 normals solve for a
+// correction of lambda; the residual b - A lambda is recomputed in float64
+// with the float64 normals after every run (iterative refinement), until
+// |r| <= rel_tol |b|.  FP64: conjugate gradients in float64.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace hfcr {
+
+namespace {
+
+constexpr int CG_THREADS = 1024;
+constexpr int RES_BLOCKS = 512;
+
+__device__ __forceinline__ int chk(int i, int n, uint32_t *st) {
+    if ((unsigned)i < (unsigned)n) return i;
+    atomicOr(st, ST_BAD_INDEX);
+    return 0;
+}
+
+template <typename T>
+__device__ __forceinline__ double ldd(const void *p, int i) {
+    return (double)((const T *)p)[i];
+}
+
+__device__ __forceinline__ void ld_pos(const hfcr_mesh &m, int i, double *o) {
+    if (m.dtype == HFCR_F32) {
+        o[0] = ldd<float>(m.x, i); o[1] = ldd<float>(m.y, i); o[2] = ldd<float>(m.z, i);
+    } else {
+        o[0] = ldd<double>(m.x, i); o[1] = ldd<double>(m.y, i); o[2] = ldd<double>(m.z, i);
+    }
+}
+
+__global__ void k_assemble(hfcr_mesh A, hfcr_mesh B, const hfcr_stencil *st, const int *d_k,
+                           int cap, double d, int4 *ids, double4_32a *n64, float4 *n32, double *b,
+                           uint32_t *status) {
+    int k = min(*d_k, cap);
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k) return;
+    hfcr_stencil S = st[s];
+    const int nA = A.n_verts;
+    const hfcr_mesh &E = S.dir ? B : A;  // mesh of x0
+    const hfcr_mesh &F = S.dir ? A : B;  // mesh of the face
+    if (S.dir > 1u) atomicOr(status, ST_BAD_INDEX);
+    int x0 = chk((int)S.x0, E.n_verts, status);
+    int f = chk((int)S.face, F.n_tris, status);
+    int v1 = chk(F.tris[3 * f], F.n_verts, status), v2 = chk(F.tris[3 * f + 1], F.n_verts, status),
+        v3 = chk(F.tris[3 * f + 2], F.n_verts, status);
+    double p0[3], p1[3], p2[3], p3[3];
+    ld_pos(E, x0, p0);
+    ld_pos(F, v1, p1);
+    ld_pos(F, v2, p2);
+    ld_pos(F, v3, p3);
+    double e1[3] = {p2[0] - p1[0], p2[1] - p1[1], p2[2] - p1[2]};
+    double e2[3] = {p3[0] - p1[0], p3[1] - p1[1], p3[2] - p1[2]};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                   e1[0] * e2[1] - e1[1] * e2[0]};
+    double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    double D = 0.0;
+    if (nn > 0.0) {
+        n[0] /= nn; n[1] /= nn; n[2] /= nn;
+        double c[3];
+        for (int q = 0; q < 3; ++q) c[q] = p0[q] - (p1[q] + p2[q] + p3[q]) / 3.0;
+        D = n[0] * c[0] + n[1] * c[1] + n[2] * c[2];
+    } else {
+        n[0] = n[1] = n[2] = 0.0;  // zero-area face: an empty row, b = 0 (only from caller input)
+    }
+    int o = S.dir ? 0 : nA;  // offset of the face mesh in the global numbering
+    int g0 = S.dir ? nA + x0 : x0;
+    ids[s] = make_int4(g0, o + v1, o + v2, o + v3);
+    n64[s] = make_double4_32a(n[0], n[1], n[2], 0.0);
+    n32[s] = make_float4((float)n[0], (float)n[1], (float)n[2], 0.f);
+    b[s] = nn > 0.0 ? D - d : 0.0;
+}
+
+__global__ void k_csr_entries(const int4 *ids, const int *d_k, int cap, unsigned *key, int *val) {
+    int k = min(*d_k, cap);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4 * k) return;
+    int s = i >> 2, role = i & 3;
+    key[i] = (unsigned)((const int *)ids)[4 * s + role];
+    val[i] = i;  // s * 4 + role
+}
+
+__global__ void k_csr_flags(const unsigned *key, const int *d_k, int cap, unsigned *flag,
+                            int *d_n4) {
+    int n = 4 * min(*d_k, cap);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *d_n4 = n;
+    if (i < n) flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_csr_build(const unsigned *key, const int *val, const unsigned *excl,
+                            const int *d_k, int cap, int nA, const float *wA, const float *wB,
+                            int4 *vidx, int *seg, int *gvert, float *winv) {
+    int n = 4 * min(*d_k, cap);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned f = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
+    int j = (int)(excl[i] + f) - 1;
+    ((int *)vidx)[val[i]] = j;
+    if (f) {
+        int g = (int)key[i];
+        seg[j] = i;
+        gvert[j] = g;
+        const float *w = g < nA ? wA : wB;
+        int lv = g < nA ? g : g - nA;
+        winv[j] = w ? w[lv] : 1.0f;
+    }
+    if (i == n - 1) seg[j + 1] = n;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        T x = lane < (int)(blockDim.x >> 5) ? sh[lane] : (T)0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[32] = x;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+template <typename T>
+struct NrmT;
+template <>
+struct NrmT<float> { typedef float4 type; };
+template <>
+struct NrmT<double> { typedef double4_32a type; };
+
+// Conjugate gradients on A x = rhs, A = J M^-1 J^T, by one CTA.
+// mode 0 (MIXED inner run): rhs = r64, skipped when ctl[0] (done) is set,
+//   on exit lam += x.  mode 1 (FP64): rhs = b, on exit lam = x.
+// ctl[0] done flag, ctl[1] total iterations, ctl[2] inner runs.
+template <typename T>
+__global__ void __launch_bounds__(CG_THREADS) k_cg(
+    int mode, const int *d_k, const int *d_U, const int *seg, const int *cval, const float *winv,
+    const typename NrmT<T>::type *nrm, const int4 *vidx, const double *rhs64, double *lam, T *x,
+    T *r, T *p, T *q, T *u, int maxit, double tol, int *ctl) {
+    __shared__ T sh[33];
+    if (mode == 0 && ctl[0]) return;
+    const int k = *d_k, U = *d_U, tid = threadIdx.x;
+    T rr_loc = 0;
+    for (int s = tid; s < k; s += CG_THREADS) {
+        T v = (T)rhs64[s];
+        r[s] = v;
+        p[s] = v;
+        x[s] = 0;
+        rr_loc += v * v;
+    }
+    T rr = block_sum(rr_loc, sh);
+    const T rr0 = rr;
+    const T third = (T)1 / (T)3;
+    const T stop = (T)(tol * tol) * rr0;
+    int it = 0;
+    while (it < maxit && rr > stop && rr > (T)0) {
+        // u = M^-1 J^T p
+        for (int j = tid; j < U; j += CG_THREADS) {
+            T a0 = 0, a1 = 0, a2 = 0;
+            for (int e = seg[j]; e < seg[j + 1]; ++e) {
+                int v = cval[e];
+                int s = v >> 2;
+                T c = (v & 3) ? -third : (T)1;
+                T ps = c * p[s];
+                typename NrmT<T>::type n = nrm[s];
+                a0 += ps * (T)n.x;
+                a1 += ps * (T)n.y;
+                a2 += ps * (T)n.z;
+            }
+            T w = (T)winv[j];
+            u[3 * j] = w * a0;
+            u[3 * j + 1] = w * a1;
+            u[3 * j + 2] = w * a2;
+        }
+        __syncthreads();
+        // q = J u, pq = p . q
+        T pq_loc = 0;
+        for (int s = tid; s < k; s += CG_THREADS) {
+            int4 vi = vidx[s];
+            typename NrmT<T>::type n = nrm[s];
+            T d0 = u[3 * vi.x] - (u[3 * vi.y] + u[3 * vi.z] + u[3 * vi.w]) * third;
+            T d1 = u[3 * vi.x + 1] - (u[3 * vi.y + 1] + u[3 * vi.z + 1] + u[3 * vi.w + 1]) * third;
+            T d2 = u[3 * vi.x + 2] - (u[3 * vi.y + 2] + u[3 * vi.z + 2] + u[3 * vi.w + 2]) * third;
+            T qs = (T)n.x * d0 + (T)n.y * d1 + (T)n.z * d2;
+            q[s] = qs;
+            pq_loc += p[s] * qs;
+        }
+        T pq = block_sum(pq_loc, sh);
+        if (!(pq > (T)0)) break;  // breakdown: A is singular on p
+        T alpha = rr / pq;
+        T rn_loc = 0;
+        for (int s = tid; s < k; s += CG_THREADS) {
+            x[s] += alpha * p[s];
+            T rs = r[s] - alpha * q[s];
+            r[s] = rs;
+            rn_loc += rs * rs;
+        }
+        T rn = block_sum(rn_loc, sh);
+        T beta = rn / rr;
+        rr = rn;
+        for (int s = tid; s < k; s += CG_THREADS) p[s] = r[s] + beta * p[s];
+        __syncthreads();
+        ++it;
+    }
+    for (int s = tid; s < k; s += CG_THREADS) {
+        if (mode == 0) lam[s] += (double)x[s];
+        else lam[s] = (double)x[s];
+    }
+    if (tid == 0) {
+        ctl[1] += it;
+        ctl[2] += 1;
+    }
+}
+
+// float64 residual, vertex half: u = M^-1 J^T lam
+__global__ void k_res_vertex(const int *d_U, const int *seg, const int *cval, const float *winv,
+                             const double4_32a *n64, const double *lam, double *u, const int *ctl) {
+    if (ctl[0]) return;
+    const int U = *d_U;
+    const double third = 1.0 / 3.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < U; j += gridDim.x * blockDim.x) {
+        double a0 = 0, a1 = 0, a2 = 0;
+        for (int e = seg[j]; e < seg[j + 1]; ++e) {
+            int v = cval[e];
+            int s = v >> 2;
+            double ps = ((v & 3) ? -third : 1.0) * lam[s];
+            double4_32a n = n64[s];
+            a0 += ps * n.x;
+            a1 += ps * n.y;
+            a2 += ps * n.z;
+        }
+        double w = (double)winv[j];
+        u[3 * j] = w * a0;
+        u[3 * j + 1] = w * a1;
+        u[3 * j + 2] = w * a2;
+    }
+}
+
+// float64 residual, stencil half: r = b - J u; per-block partial sums of
+// r^2 and b^2 to red[blk] and red[RES_BLOCKS + blk]
+__global__ void k_res_stencil(const int *d_k, const int4 *vidx, const double4_32a *n64,
+                              const double *b, const double *u, double *r, double *red,
+                              const int *ctl) {
+    __shared__ double sh[33];
+    if (ctl[0]) return;
+    const int k = *d_k;
+    const double third = 1.0 / 3.0;
+    double rr = 0, bb = 0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < k; s += gridDim.x * blockDim.x) {
+        int4 vi = vidx[s];
+        double4_32a n = n64[s];
+        double d0 = u[3 * vi.x] - (u[3 * vi.y] + u[3 * vi.z] + u[3 * vi.w]) * third;
+        double d1 = u[3 * vi.x + 1] - (u[3 * vi.y + 1] + u[3 * vi.z + 1] + u[3 * vi.w + 1]) * third;
+        double d2 = u[3 * vi.x + 2] - (u[3 * vi.y + 2] + u[3 * vi.z + 2] + u[3 * vi.w + 2]) * third;
+        double rs = b[s] - (n.x * d0 + n.y * d1 + n.z * d2);
+        r[s] = rs;
+        rr += rs * rs;
+        bb += b[s] * b[s];
+    }
+    rr = block_sum(rr, sh);
+    bb = block_sum(bb, sh);
+    if (threadIdx.x == 0) {
+        red[blockIdx.x] = rr;
+        red[RES_BLOCKS + blockIdx.x] = bb;
+    }
+}
+
+// Sums the partials in a fixed order, records |r|/|b| and sets the done
+// flag when it meets rel_tol.  ctl[0] done, ctl[3] refinement rounds.
+__global__ void k_res_check(const double *red, int nblk, double rel_tol, int *ctl, double *dres,
+                            int count_round) {
+    if (threadIdx.x != 0 || ctl[0]) return;
+    double rr = 0, bb = 0;
+    for (int i = 0; i < nblk; ++i) {
+        rr += red[i];
+        bb += red[RES_BLOCKS + i];
+    }
+    double rel = bb > 0 ? sqrt(rr / bb) : 0.0;
+    dres[0] = rel;
+    if (rel <= rel_tol) ctl[0] = 1;
+    if (count_round) ctl[3] += 1;
+}
+
+__global__ void k_init_lam(const int *d_k, const double *b, double *lam, double *r) {
+    const int k = *d_k;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < k; s += gridDim.x * blockDim.x) {
+        lam[s] = 0.0;
+        r[s] = b[s];
+    }
+}
+
+// displacement of the touched vertices: dx = -M^-1 J^T lam (float64)
+__global__ void k_displace(const int *d_U, const int *seg, const int *cval, const float *winv,
+                           const double4_32a *n64, const double *lam, const int *gvert, hfcr_mesh A,
+                           hfcr_mesh B, int apply, void *dA0, void *dA1, void *dA2, void *dB0,
+                           void *dB1, void *dB2) {
+    const int U = *d_U;
+    const double third = 1.0 / 3.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < U; j += gridDim.x * blockDim.x) {
+        double a0 = 0, a1 = 0, a2 = 0;
+        for (int e = seg[j]; e < seg[j + 1]; ++e) {
+            int v = cval[e];
+            int s = v >> 2;
+            double ps = ((v & 3) ? -third : 1.0) * lam[s];
+            double4_32a n = n64[s];
+            a0 += ps * n.x;
+            a1 += ps * n.y;
+            a2 += ps * n.z;
+        }
+        double w = (double)winv[j];
+        double dx[3] = {-w * a0, -w * a1, -w * a2};
+        int g = gvert[j];
+        const bool inA = g < A.n_verts;
+        const hfcr_mesh &m = inA ? A : B;
+        int lv = inA ? g : g - A.n_verts;
+        if (apply) {
+            void *P[3] = {m.x, m.y, m.z};
+            for (int c = 0; c < 3; ++c) {
+                if (m.dtype == HFCR_F32) {
+                    float *pp = (float *)P[c] + lv;
+                    *pp = (float)((double)*pp + dx[c]);
+                } else {
+                    double *pp = (double *)P[c] + lv;
+                    *pp = *pp + dx[c];
+                }
+            }
+        } else {
+            void *O[3] = {inA ? dA0 : dB0, inA ? dA1 : dB1, inA ? dA2 : dB2};
+            for (int c = 0; c < 3; ++c) {
+                if (m.dtype == HFCR_F32) ((float *)O[c])[lv] = (float)dx[c];
+                else ((double *)O[c])[lv] = dx[c];
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int cap, double d,
+              SolveBuffers &sb, uint32_t *d_status, cudaStream_t s) {
+    if (cap <= 0) return;
+    { k_assemble<<<(cap + 255) / 256, 256, 0, s>>>(mp.A, mp.B, st, d_k, cap, d, sb.ids, sb.n64,
+                                                 sb.n32, sb.b, d_status); note_launch(); }
+}
+
+void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers &sb, SortTemp &t,
+                      int *d_n4, cudaStream_t s) {
+    if (cap <= 0) return;
+    int n4 = 4 * cap;
+    int nb = (n4 + 255) / 256;
+    { k_csr_entries<<<nb, 256, 0, s>>>(sb.ids, d_k, cap, sb.ckey, sb.cval); note_launch(); }
+    { k_csr_flags<<<1, 1, 0, s>>>(sb.ckey, d_k, cap, sb.cflag, d_n4); note_launch(); }  // count only
+    int vb = bits_for((long long)mp.A.n_verts + mp.B.n_verts);
+    bool flip = radix_sort_u32_dev(sb.ckey, sb.cval, sb.ckey_alt, sb.cval_alt, d_n4, n4, vb, t, s);
+    if (flip) {
+        cudaMemcpyAsync(sb.ckey, sb.ckey_alt, sizeof(unsigned) * n4, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(sb.cval, sb.cval_alt, sizeof(int) * n4, cudaMemcpyDeviceToDevice, s);
+    }
+    { k_csr_flags<<<nb, 256, 0, s>>>(sb.ckey, d_k, cap, sb.cflag, d_n4); note_launch(); }
+    scan_flags_dev(sb.cflag, d_n4, n4, sb.d_U, s);
+    { k_csr_build<<<nb, 256, 0, s>>>(sb.ckey, sb.cval, sb.cflag, d_k, cap, mp.A.n_verts,
+                                   mp.A.inv_mass, mp.B.inv_mass, sb.vidx, sb.seg, sb.gvert, sb.winv); note_launch(); }
+}
+
+void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint32_t *d_status,
+           cudaStream_t s) {
+    (void)d_status;
+    if (cap <= 0) return;
+    int rb = (cap + 255) / 256;
+    if (rb > RES_BLOCKS) rb = RES_BLOCKS;
+    cudaMemsetAsync(sb.iwork, 0, sizeof(int) * 16, s);
+    { k_init_lam<<<rb, 256, 0, s>>>(d_k, sb.b, sb.lam, sb.r64); note_launch(); }
+    if (p.solver == HFCR_SOLVER_FP64) {
+        // one float64 run with the whole iteration budget of the mixed solver
+        { k_cg<double><<<1, CG_THREADS, 0, s>>>(1, d_k, sb.d_U, sb.seg, sb.cval, sb.winv, sb.n64,
+                                              sb.vidx, sb.b, sb.lam, sb.p64 + 0, sb.r64, sb.p64 + cap,
+                                              sb.q64, sb.u64, p.max_cg_iters * p.max_refine,
+                                              p.rel_tol, sb.iwork); note_launch(); }
+        { k_res_vertex<<<rb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval, sb.winv, sb.n64, sb.lam, sb.u64,
+                                         sb.iwork); note_launch(); }
+        { k_res_stencil<<<rb, 256, 0, s>>>(d_k, sb.vidx, sb.n64, sb.b, sb.u64, sb.r64, sb.red,
+                                          sb.iwork); note_launch(); }
+        { k_res_check<<<1, 32, 0, s>>>(sb.red, rb, p.rel_tol, sb.iwork, sb.dwork, 0); note_launch(); }
+        return;
+    }
+    // MIXED: float32 runs on the float64 residual (r = b to start)
+    for (int round = 0; round < p.max_refine; ++round) {
+        { k_cg<float><<<1, CG_THREADS, 0, s>>>(0, d_k, sb.d_U, sb.seg, sb.cval, sb.winv, sb.n32,
+                                             sb.vidx, sb.r64, sb.lam, sb.x32, sb.r32, sb.p32,
+                                             sb.q32, sb.u32, p.max_cg_iters, p.inner_tol, sb.iwork); note_launch(); }
+        { k_res_vertex<<<rb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval, sb.winv, sb.n64, sb.lam, sb.u64,
+                                         sb.iwork); note_launch(); }
+        { k_res_stencil<<<rb, 256, 0, s>>>(d_k, sb.vidx, sb.n64, sb.b, sb.u64, sb.r64, sb.red,
+                                          sb.iwork); note_launch(); }
+        { k_res_check<<<1, 32, 0, s>>>(sb.red, rb, p.rel_tol, sb.iwork, sb.dwork, 1); note_launch(); }
+    }
+}
+
+void displacement(const MeshPair &mp, int cap, SolveBuffers &sb, int apply, void *const *dxA,
+                  void *const *dxB, cudaStream_t s) {
+    if (cap <= 0) return;
+    int nb = (4 * cap + 255) / 256;
+    if (nb > 1024) nb = 1024;
+    void *a0 = dxA ? dxA[0] : nullptr, *a1 = dxA ? dxA[1] : nullptr, *a2 = dxA ? dxA[2] : nullptr;
+    void *b0 = dxB ? dxB[0] : nullptr, *b1 = dxB ? dxB[1] : nullptr, *b2 = dxB ? dxB[2] : nullptr;
+    { k_displace<<<nb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval, sb.winv, sb.n64, sb.lam, sb.gvert, mp.A,
+                                  mp.B, apply, a0, a1, a2, b0, b1, b2); note_launch(); }
+}
+
+}  // namespace hfcr

@@ -1,0 +1,272 @@
+// Stable LSD radix sort (8-bit digits) and exclusive scans.
+//
+// Tile = 256 threads x 8 rounds of 32 keys = 2048 keys.  Within a tile each
+// warp owns 256 consecutive keys and ranks them round by round: lanes with
+// the same digit are found with __match_any_sync, a lane's rank is the
+// number of equal-digit lanes before it plus the warp's running count of
+// that digit (kept in shared memory), which preserves input order.  Per-
+// warp counts are then prefix-summed across the 8 warps, and a tile's
+// global offset for a digit comes from the digit-major scan of all tiles'
+// histograms.  Inputs of up to SMALL_N keys are sorted by one CTA that
+// walks its tiles in order (one launch for all passes).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace hfcr {
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int ROUNDS = 8;
+constexpr int TILE = TPB * ROUNDS;  // 2048
+constexpr int SMALL_N = 16 * TILE;  // single-CTA sort up to 32768 keys
+
+template <typename K>
+__device__ __forceinline__ unsigned digit_of(K k, int shift) {
+    return (unsigned)((k >> shift) & (K)0xff);
+}
+
+// Ranks one tile.  wh must be zero on entry; on exit wh[w][d] holds the
+// exclusive prefix over warps of digit d's count and tot[d] (if non-null)
+// the tile's count of digit d.  Invalid slots get digit 256.
+template <typename K, bool HV>
+__device__ __forceinline__ void rank_tile(const K *kin, const int *vin, int n, int tile_base,
+                                          unsigned (*wh)[256], K *key, int *val, unsigned *dig,
+                                          unsigned *rank, int shift) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int base = tile_base + warp * 256;
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        int idx = base + r * 32 + lane;
+        bool valid = idx < n;
+        key[r] = valid ? kin[idx] : (K)0;
+        if (HV) val[r] = valid ? vin[idx] : 0;
+        unsigned d = valid ? digit_of(key[r], shift) : 256u;
+        dig[r] = d;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned lt = peers & ((1u << lane) - 1u);
+        unsigned before = d < 256 ? wh[warp][d] : 0u;
+        rank[r] = before + __popc(lt);
+        __syncwarp();
+        if (d < 256 && lt == 0) wh[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(TPB) k_hist(const K *keys, int n, const int *d_n, int shift,
+                                              unsigned *hist, int nblocks) {
+    if (d_n) n = min(n, *d_n);
+    __shared__ unsigned h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * TILE;
+    for (int i = threadIdx.x; i < TILE; i += TPB) {
+        int idx = base + i;
+        if (idx < n) atomicAdd(&h[digit_of(keys[idx], shift)], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of a[0..m) in place by one CTA of 1024 threads; total to *d_total
+__global__ void __launch_bounds__(1024) k_scan1(unsigned *a, int m, const int *d_m, int *d_total) {
+    if (d_m) m = min(m, *d_m);
+    __shared__ unsigned ws[32];
+    const int t = threadIdx.x;
+    int chunk = (m + 1023) / 1024;
+    int beg = min(m, t * chunk), end = min(m, beg + chunk);
+    unsigned sum = 0;
+    for (int i = beg; i < end; ++i) sum += a[i];
+    // block exclusive scan of per-thread sums
+    unsigned v = sum;
+    const int lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) ws[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        unsigned x = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        ws[lane] = x;
+    }
+    __syncthreads();
+    unsigned excl = v - sum + (w ? ws[w - 1] : 0u);
+    for (int i = beg; i < end; ++i) {
+        unsigned x = a[i];
+        a[i] = excl;
+        excl += x;
+    }
+    if (t == 1023 && d_total) *d_total = (int)(ws[31]);
+}
+
+template <typename K, bool HV>
+__global__ void __launch_bounds__(TPB) k_scatter(const K *kin, const int *vin, K *kout, int *vout,
+                                                 int n, const int *d_n, int shift,
+                                                 const unsigned *hist, int nblocks) {
+    if (d_n) n = min(n, *d_n);
+    __shared__ unsigned wh[TPB / 32][256];
+    for (int i = threadIdx.x; i < (TPB / 32) * 256; i += TPB) (&wh[0][0])[i] = 0;
+    __syncthreads();
+    K key[ROUNDS];
+    int val[ROUNDS];
+    unsigned dig[ROUNDS], rank[ROUNDS];
+    rank_tile<K, HV>(kin, vin, n, blockIdx.x * TILE, wh, key, val, dig, rank, shift);
+    __syncthreads();
+    unsigned run = 0;
+    for (int w = 0; w < TPB / 32; ++w) {
+        unsigned c = wh[w][threadIdx.x];
+        wh[w][threadIdx.x] = run;
+        run += c;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        unsigned d = dig[r];
+        if (d < 256) {
+            unsigned pos = hist[d * nblocks + blockIdx.x] + wh[warp][d] + rank[r];
+            kout[pos] = key[r];
+            if (HV) vout[pos] = val[r];
+        }
+    }
+}
+
+// One CTA sorts all passes.  Returns (via *d_flip) nothing: the caller
+// knows the pass count and hence the buffer holding the result.
+template <typename K, bool HV>
+__global__ void __launch_bounds__(TPB) k_sort_small(K *k0, int *v0, K *k1, int *v1, int n,
+                                                    const int *d_n, int bits) {
+    if (d_n) n = min(n, *d_n);
+    __shared__ unsigned wh[TPB / 32][256];
+    __shared__ unsigned off[256];
+    __shared__ unsigned cnt[256];
+    K *kin = k0, *kout = k1;
+    int *vin = v0, *vout = v1;
+    for (int shift = 0; shift < bits; shift += 8) {
+        // digit totals over the whole input
+        cnt[threadIdx.x] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += TPB) atomicAdd(&cnt[digit_of(kin[i], shift)], 1u);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // exclusive scan of 256 counts by one warp (8 per lane)
+            const int lane = threadIdx.x;
+            unsigned loc[8], s = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) { loc[q] = cnt[lane * 8 + q]; s += loc[q]; }
+            unsigned v = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            unsigned e = v - s;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) { off[lane * 8 + q] = e; e += loc[q]; }
+        }
+        __syncthreads();
+        for (int tb = 0; tb < n; tb += TILE) {
+            for (int i = threadIdx.x; i < (TPB / 32) * 256; i += TPB) (&wh[0][0])[i] = 0;
+            __syncthreads();
+            K key[ROUNDS];
+            int val[ROUNDS];
+            unsigned dig[ROUNDS], rank[ROUNDS];
+            rank_tile<K, HV>(kin, vin, n, tb, wh, key, val, dig, rank, shift);
+            __syncthreads();
+            unsigned run = 0;
+            for (int w = 0; w < TPB / 32; ++w) {
+                unsigned c = wh[w][threadIdx.x];
+                wh[w][threadIdx.x] = run;
+                run += c;
+            }
+            cnt[threadIdx.x] = run;  // tile total of this digit
+            __syncthreads();
+            const int warp = threadIdx.x >> 5;
+#pragma unroll
+            for (int r = 0; r < ROUNDS; ++r) {
+                unsigned d = dig[r];
+                if (d < 256) {
+                    unsigned pos = off[d] + wh[warp][d] + rank[r];
+                    kout[pos] = key[r];
+                    if (HV) vout[pos] = val[r];
+                }
+            }
+            __syncthreads();
+            off[threadIdx.x] += cnt[threadIdx.x];
+            __syncthreads();
+        }
+        K *tk = kin; kin = kout; kout = tk;
+        int *tv = vin; vin = vout; vout = tv;
+        __syncthreads();
+    }
+}
+
+template <typename K, bool HV>
+bool radix_sort_impl(K *k0, int *v0, K *k1, int *v1, int n, const int *d_n, int bits,
+                     SortTemp &t, cudaStream_t s) {
+    int passes = (bits + 7) / 8;
+    if (n <= 0 || passes == 0) return false;
+    if (n <= SMALL_N) {
+        { k_sort_small<K, HV><<<1, TPB, 0, s>>>(k0, v0, k1, v1, n, d_n, passes * 8); note_launch(); }
+        return passes & 1;
+    }
+    int nb = (n + TILE - 1) / TILE;
+    K *kin = k0, *kout = k1;
+    int *vin = v0, *vout = v1;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        { k_hist<K><<<nb, TPB, 0, s>>>(kin, n, d_n, shift, t.hist, nb); note_launch(); }
+        { k_scan1<<<1, 1024, 0, s>>>(t.hist, 256 * nb, nullptr, nullptr); note_launch(); }
+        { k_scatter<K, HV><<<nb, TPB, 0, s>>>(kin, vin, kout, vout, n, d_n, shift, t.hist, nb); note_launch(); }
+        K *tk = kin; kin = kout; kout = tk;
+        int *tv = vin; vin = vout; vout = tv;
+    }
+    return passes & 1;
+}
+
+}  // namespace
+
+int sort_blocks_for(int n) { return (n + TILE - 1) / TILE; }
+
+bool radix_sort_u32(unsigned *k0, int *v0, unsigned *k1, int *v1, int n, int bits, SortTemp &t,
+                    cudaStream_t s) {
+    if (v0) return radix_sort_impl<unsigned, true>(k0, v0, k1, v1, n, nullptr, bits, t, s);
+    return radix_sort_impl<unsigned, false>(k0, nullptr, k1, nullptr, n, nullptr, bits, t, s);
+}
+bool radix_sort_u64(unsigned long long *k0, int *v0, unsigned long long *k1, int *v1, int n,
+                    int bits, SortTemp &t, cudaStream_t s) {
+    if (v0)
+        return radix_sort_impl<unsigned long long, true>(k0, v0, k1, v1, n, nullptr, bits, t, s);
+    return radix_sort_impl<unsigned long long, false>(k0, nullptr, k1, nullptr, n, nullptr, bits, t,
+                                                      s);
+}
+bool radix_sort_u64_dev(unsigned long long *k0, unsigned long long *k1, const int *d_n, int cap,
+                        int bits, SortTemp &t, cudaStream_t s) {
+    return radix_sort_impl<unsigned long long, false>(k0, nullptr, k1, nullptr, cap, d_n, bits, t, s);
+}
+bool radix_sort_u32_dev(unsigned *k0, int *v0, unsigned *k1, int *v1, const int *d_n, int cap,
+                        int bits, SortTemp &t, cudaStream_t s) {
+    return radix_sort_impl<unsigned, true>(k0, v0, k1, v1, cap, d_n, bits, t, s);
+}
+
+void scan_flags_dev(unsigned *flags, const int *d_n, int cap, int *d_total, cudaStream_t s) {
+    { k_scan1<<<1, 1024, 0, s>>>(flags, cap, d_n, d_total); note_launch(); }
+}
+
+int bits_for(long long n) {
+    int b = 1;
+    while ((1ll << b) < n) ++b;
+    return b;
+}
+
+}  // namespace hfcr
