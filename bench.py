@@ -40,7 +40,7 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_traverse_cloth_torus.md")
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -72,7 +72,7 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -223,7 +223,8 @@ def main():
     sc = scene()
 
     def dev_mesh(m, dtype):
-        P = np.ascontiguousarray(m.V.astype(dtype))
+        # the float64 form computes on the exact widening of the same float32 data
+        P = np.ascontiguousarray(m.V.astype(np.float32).astype(dtype))
         tdt = torch.float32 if dtype == np.float32 else torch.float64
         xyz = [torch.tensor(np.ascontiguousarray(P[:, c]), dtype=tdt, device=dev) for c in range(3)]
         return xyz, torch.tensor(m.T, device=dev)
@@ -363,7 +364,8 @@ def main():
             "ef_tests_per_s_executed": round(narrow / (per_frame / 1e3), 1),
             "filter": {"narrow_tests": narrow, "f64_fallbacks": int(info.stats.f64_fallbacks),
                        "exact_fallbacks": int(info.stats.exact_fallbacks)},
-            "solver": {"cg_iters": int(info.cg_iters), "rel_residual": info.worst_rel_residual},
+            "solver": {"cg_iters": int(info.cg_iters), "rel_residual": info.worst_rel_residual,
+                       "float32_cg_in_shared_memory": bool(info.solver_path & 1)},
             "stage_ms_per_frame": stage_ms,
             "roofline": {"kernel": "k_traverse (BVH traversal + exact narrow phase)",
                          "bound": "hbm", "achieved": round(achieved, 2), "peak": peak,

@@ -135,6 +135,7 @@ typedef struct {
     int32_t cg_iters;              /* all solves */
     double worst_rel_residual;     /* largest solver residual over the iterations */
     hfcr_detect_stats stats;       /* summed over the detections */
+    int32_t solver_path;           /* bit 0: the float32 CG ran in shared memory, bit 1: in global memory */
 } hfcr_resolve_info;
 
 /* Stages timed by the optional profiler (instrumentation; the paper has no

@@ -73,7 +73,7 @@ class hfcr_resolve_info(ctypes.Structure):
                 ("pairs_first", ctypes.c_int64), ("pairs_last", ctypes.c_int64),
                 ("total_pairs", ctypes.c_int64), ("total_stencils", ctypes.c_int64),
                 ("cg_iters", ctypes.c_int32), ("worst_rel_residual", ctypes.c_double),
-                ("stats", hfcr_detect_stats)]
+                ("stats", hfcr_detect_stats), ("solver_path", ctypes.c_int32)]
 
 
 HFCR_N_STAGES = 7

@@ -32,6 +32,8 @@ struct hfcr_ctx {
     uint32_t *h_status = nullptr; // pinned
     int *h_cnt = nullptr;         // pinned [16]
     DevStats *h_stats = nullptr;  // pinned
+    double *h_dw = nullptr;       // pinned [4] solver words
+    int *h_iw = nullptr;          // pinned [8] solver control words
     SortTemp sort;
     Bvh bvh[2];                   // [0]: faces of B (direction 0), [1]: faces of A (direction 1)
     int *edges[2] = {nullptr, nullptr};
@@ -52,7 +54,7 @@ struct hfcr_ctx {
 };
 
 // device counter slots
-enum { C_PAIRS = 0, C_STENCILS = 1, C_EDGES_A = 2, C_EDGES_B = 3, C_N4 = 4, C_NPAIRS_IN = 5 };
+enum { C_PAIRS = 0, C_STENCILS = 1, C_EDGES_A = 2, C_EDGES_B = 3, C_N4 = 4, C_NPAIRS_IN = 5, C_PEFF = 6 };
 
 namespace {
 
@@ -87,7 +89,7 @@ void free_all(hfcr_ctx *c) {
                     c->ekeys, c->ekeys_alt, c->eflags, c->pkeys, c->pkeys_alt, c->pairs,
                     c->skeys, c->skeys_alt, c->sflags, c->stencils,
                     c->sb.ids, c->sb.n64, c->sb.n32, c->sb.b, c->sb.lam, c->sb.r64, c->sb.r32,
-                    c->sb.x32, c->sb.p32, c->sb.q32, c->sb.p64, c->sb.q64, c->sb.vidx, c->sb.ckey,
+                    c->sb.x32, c->sb.p32, c->sb.q32, c->sb.w32, c->sb.p64, c->sb.q64, c->sb.vidx, c->sb.ckey,
                     c->sb.ckey_alt, c->sb.cval, c->sb.cval_alt, c->sb.cflag, c->sb.seg, c->sb.gvert,
                     c->sb.winv, c->sb.u64, c->sb.u32, c->sb.red, c->sb.d_U, c->sb.iwork,
                     c->sb.dwork};
@@ -104,13 +106,15 @@ void free_all(hfcr_ctx *c) {
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->h_cnt) cudaFreeHost(c->h_cnt);
     if (c->h_stats) cudaFreeHost(c->h_stats);
+    if (c->h_dw) cudaFreeHost(c->h_dw);
+    if (c->h_iw) cudaFreeHost(c->h_iw);
     c->d_status = nullptr; c->d_stats = nullptr; c->d_cnt = nullptr; c->sort = SortTemp();
     c->edges[0] = c->edges[1] = nullptr;
     c->ekeys = c->ekeys_alt = nullptr; c->eflags = nullptr;
     c->pkeys = c->pkeys_alt = nullptr; c->pairs = nullptr;
     c->skeys = c->skeys_alt = nullptr; c->sflags = nullptr; c->stencils = nullptr;
     c->sb = SolveBuffers();
-    c->h_status = nullptr; c->h_cnt = nullptr; c->h_stats = nullptr;
+    c->h_status = nullptr; c->h_cnt = nullptr; c->h_stats = nullptr; c->h_dw = nullptr; c->h_iw = nullptr;
     c->max_verts = c->max_tris = c->max_pairs = 0;
 }
 
@@ -364,6 +368,44 @@ hfcr_status run_response(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     return HFCR_OK;
 }
 
+// One repair iteration enqueued on device counts only: detection, clamped
+// pair count, pair sort and records, stencils, assembly, solve, applied
+// displacement.  Grids are sized by the reserved capacity; kernels read
+// the live counts.  Nothing is read back.
+void enqueue_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d0, bool d1,
+                       const DetectPlan &pl, bool *built, double d, cudaStream_t s) {
+    const int cap = (int)ctx->max_pairs;
+    launch_detect(ctx, A, B, d0, d1, pl, built, s);
+    prof_begin(ctx, HFCR_STAGE_STENCILS, s);
+    clamp_count(ctx->d_cnt + C_PAIRS, cap, ctx->d_cnt + C_PEFF, ctx->d_status, s);
+    int bits = 1 + pl.edge_bits + pl.face_bits;
+    bool flip = radix_sort_u64_dev(ctx->pkeys, ctx->pkeys_alt, ctx->d_cnt + C_PEFF, cap, bits,
+                                   ctx->sort, s);
+    keys_to_pairs(flip ? ctx->pkeys_alt : ctx->pkeys, ctx->d_cnt + C_PEFF, cap, pl.edges[0],
+                  pl.edges[1], pl.edge_bits, pl.face_bits, ctx->pairs, s);
+    MeshPair mp{*A, *B};
+    int maxv = A->n_verts > B->n_verts ? A->n_verts : B->n_verts;
+    int maxf = A->n_tris > B->n_tris ? A->n_tris : B->n_tris;
+    int vb = bits_for(maxv > 1 ? maxv : 2), fb = bits_for(maxf > 1 ? maxf : 2);
+    stencil_keys(mp, ctx->pairs, ctx->d_cnt + C_PEFF, cap, vb, fb, ctx->opt.f32_filter, ctx->skeys,
+                 ctx->d_stats, ctx->d_status, s);
+    flip = radix_sort_u64_dev(ctx->skeys, ctx->skeys_alt, ctx->d_cnt + C_PEFF, cap, 1 + vb + fb,
+                              ctx->sort, s);
+    stencil_unique(flip ? ctx->skeys_alt : ctx->skeys, ctx->d_cnt + C_PEFF, cap, vb, fb, ctx->sflags,
+                   ctx->stencils, ctx->d_cnt + C_STENCILS, s);
+    prof_end(ctx, HFCR_STAGE_STENCILS, s);
+    run_response(ctx, A, B, ctx->stencils, cap, d, 1, nullptr, nullptr, s);
+}
+
+// Reads the counters, status, statistics and solver words of the last
+// iteration in one batch and synchronises.
+hfcr_status read_iteration(hfcr_ctx *ctx, cudaStream_t s) {
+    CK(cudaMemcpyAsync(ctx->h_iw, ctx->sb.iwork, sizeof(int) * 6, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_iw + 6, ctx->sb.d_U, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_dw, ctx->sb.dwork, sizeof(double), cudaMemcpyDeviceToHost, s));
+    return read_back(ctx, s);
+}
+
 hfcr_status solve_info(hfcr_ctx *ctx, int k, hfcr_solve_info *info, cudaStream_t s) {
     int iw[16] = {0};
     double dw[1] = {0};
@@ -452,6 +494,8 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(cudaMallocHost((void **)&ctx->h_status, sizeof(uint32_t)));
     CK(cudaMallocHost((void **)&ctx->h_cnt, sizeof(int) * 16));
     CK(cudaMallocHost((void **)&ctx->h_stats, sizeof(DevStats)));
+    CK(cudaMallocHost((void **)&ctx->h_dw, sizeof(double) * 4));
+    CK(cudaMallocHost((void **)&ctx->h_iw, sizeof(int) * 8));
     size_t maxn = E3 > 4 * P ? E3 : 4 * P;
     ctx->sort.max_blocks = sort_blocks_for((int)maxn) + 1;
     CK(dalloc(&ctx->sort.hist, 256 * (size_t)ctx->sort.max_blocks));
@@ -492,6 +536,7 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(dalloc(&sb.x32, P));
     CK(dalloc(&sb.p32, P));
     CK(dalloc(&sb.q32, P));
+    CK(dalloc(&sb.w32, P));
     CK(dalloc(&sb.p64, 2 * P));
     CK(dalloc(&sb.q64, P));
     CK(dalloc(&sb.vidx, P));
@@ -652,34 +697,33 @@ hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, in
         bool d0 = has0, d1 = has1;
         if (alternate) { d0 = (it % 2) == 0; d1 = !d0; }
         if ((st = reset_words(ctx, s))) return st;
-        launch_detect(ctx, A, B, d0, d1, pl, built, s);
-        if ((st = read_back(ctx, s))) { loc.iters = it + 1; if (info) *info = loc; return st; }
+        CK(cudaMemsetAsync(ctx->sb.iwork, 0, sizeof(int) * 16, s));
+        CK(cudaMemsetAsync(ctx->sb.dwork, 0, sizeof(double), s));
+        CK(cudaMemsetAsync(ctx->sb.d_U, 0, sizeof(int), s));
+        enqueue_iteration(ctx, A, B, d0, d1, pl, built, d, s);
+        CK(cudaGetLastError());
+        st = read_iteration(ctx, s);
         int P = ctx->h_cnt[C_PAIRS];
+        int64_t k = ctx->h_cnt[C_STENCILS];
+        loc.iters = it + 1;
+        if (st) {
+            if (info) *info = loc;
+            return st;
+        }
         add_stats(&loc.stats, *ctx->h_stats,
                   (d0 ? (long long)pl.ne[0] * B->n_tris : 0) + (d1 ? (long long)pl.ne[1] * A->n_tris : 0));
-        loc.iters = it + 1;
         if (it == 0) loc.pairs_first = P;
         loc.pairs_last = P;
         loc.total_pairs += P;
-        if (P > ctx->max_pairs) {
-            if (info) *info = loc;
-            return fail(ctx, HFCR_ERR_CAPACITY, "%d pairs exceed the reserved %lld", P,
-                        (long long)ctx->max_pairs);
-        }
+        loc.total_stencils += k;
         if (P == 0) {
             if (++quiet >= need_quiet) { loc.converged = 1; break; }
             continue;
         }
         quiet = 0;
-        if ((st = finish_pairs(ctx, P, pl, ctx->pairs, s))) return st;
-        int64_t k = 0;
-        if ((st = make_stencils(ctx, A, B, ctx->pairs, P, C_PAIRS, ctx->stencils, &k, s))) return st;
-        loc.total_stencils += k;
-        if ((st = run_response(ctx, A, B, ctx->stencils, (int)k, d, 1, nullptr, nullptr, s))) return st;
-        hfcr_solve_info si;
-        if ((st = solve_info(ctx, (int)k, &si, s))) return st;
-        loc.cg_iters += si.cg_iters;
-        if (si.rel_residual > loc.worst_rel_residual) loc.worst_rel_residual = si.rel_residual;
+        loc.cg_iters += ctx->h_iw[1];
+        loc.solver_path |= ctx->h_iw[4];
+        if (ctx->h_dw[0] > loc.worst_rel_residual) loc.worst_rel_residual = ctx->h_dw[0];
     }
     if (info) *info = loc;
     CK(cudaStreamSynchronize(s));

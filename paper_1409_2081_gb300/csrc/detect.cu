@@ -228,7 +228,22 @@ __global__ void k_stencil_write(const unsigned long long *keys, const unsigned *
     }
 }
 
+// effective count = count when it fits the capacity, else 0 with
+// ST_CAPACITY raised (so nothing downstream runs on a truncated set)
+__global__ void k_clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *status) {
+    int n = *d_n;
+    if (n > cap) {
+        atomicOr(status, ST_CAPACITY);
+        n = 0;
+    }
+    *d_eff = n;
+}
+
 }  // namespace
+
+void clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *d_status, cudaStream_t s) {
+    { k_clamp_count<<<1, 1, 0, s>>>(d_n, cap, d_eff, d_status); note_launch(); }
+}
 
 void detect_launch(const DetectArgs &a, cudaStream_t s, uint32_t *d_status) {
     if (a.n_edges <= 0 || a.bvh->n <= 0) return;

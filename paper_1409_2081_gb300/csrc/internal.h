@@ -108,6 +108,8 @@ struct DetectArgs {
     DevStats *stats;
 };
 void detect_launch(const DetectArgs &a, cudaStream_t s, uint32_t *d_status);
+// d_eff = *d_n if it is at most cap, else 0 and ST_CAPACITY
+void clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *d_status, cudaStream_t s);
 // keys (sorted) -> hfcr_pair records
 void keys_to_pairs(const unsigned long long *keys, const int *d_n, int cap, const int *edgesA,
                    const int *edgesB, int edge_bits, int face_bits, hfcr_pair *out, cudaStream_t s);
@@ -133,12 +135,14 @@ struct SolveBuffers {
     double *b = nullptr;         // [cap_k] D - d
     double *lam = nullptr;       // [cap_k]
     double *r64 = nullptr;       // [cap_k]
-    float *r32 = nullptr, *x32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // [cap_k]
+    float *r32 = nullptr, *x32 = nullptr, *p32 = nullptr, *q32 = nullptr, *w32 = nullptr;  // [cap_k]
     double *p64 = nullptr, *q64 = nullptr;   // p64 [2 cap_k] (x and p), q64 [cap_k] (FP64 solver)
     int4 *vidx = nullptr;        // [cap_k] compact vertex index of each stencil role
     // vertex CSR over 4k entries
     unsigned *ckey = nullptr, *ckey_alt = nullptr;   // [4 cap_k]
     int *cval = nullptr, *cval_alt = nullptr;        // [4 cap_k]
+    unsigned *ckey_s = nullptr;  // the sorted key buffer (ckey or ckey_alt)
+    int *cval_s = nullptr;       // the sorted entry buffer (cval or cval_alt)
     unsigned *cflag = nullptr;                       // [4 cap_k]
     int *seg = nullptr;          // [4 cap_k + 1]
     int *gvert = nullptr;        // [4 cap_k]

@@ -234,6 +234,201 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg(
     }
 }
 
+// ---------------------------------------------------------------------------
+// float32 CG of the mixed solver, one CTA, single reduction per iteration
+// (Chronopoulos-Gear form: s = A p is carried by a recurrence, so each
+// iteration needs one product w = A r and one fused reduction of (r, r) and
+// (w, r)).  Everything the iteration touches is staged in shared memory
+// when it fits (64 k + 20 U bytes, k stencils, U touched vertices);
+// otherwise the same loop runs on global scratch.
+// ---------------------------------------------------------------------------
+
+constexpr int FAST_SMEM = 231424;  // 226 KB dynamic (+256 B static) under the 227 KB per-CTA limit
+
+struct CgView {
+    float *r, *p, *x, *sv, *w;   // [k]
+    float *ux, *uy, *uz;         // [U]
+    const float *nx, *ny, *nz;   // [k] (shared-memory copy) or null
+    const float4 *n4;            // [k] (global) when nx is null
+    const int4 *vidx;            // [k]
+    const int *seg;              // [U + 1]
+    const int *cval;             // [4 k]
+    const float *winv;           // [U]
+    __device__ __forceinline__ float3 nrm(int s) const {
+        if (nx) return make_float3(nx[s], ny[s], nz[s]);
+        float4 v = n4[s];
+        return make_float3(v.x, v.y, v.z);
+    }
+};
+
+// deterministic block reduction of two sums with a single barrier: warp
+// partials go to red[2 * warp]; after the barrier every warp loads the
+// partials lane-parallel, folds them with the same shuffle tree and takes
+// lane 0's result, so all threads obtain bit-identical sums
+__device__ __forceinline__ void block_sum2(float a, float b, float *red, float &sa, float &sb_) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[2 * w] = a;
+        red[2 * w + 1] = b;
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    float x = lane < nw ? red[2 * lane] : 0.f;
+    float y = lane < nw ? red[2 * lane + 1] : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    // lanes of a butterfly may differ in the last bit; lane 0's value is
+    // the same in every warp (same inputs, same operations)
+    sa = __shfl_sync(0xffffffffu, x, 0);
+    sb_ = __shfl_sync(0xffffffffu, y, 0);
+}
+
+__device__ __forceinline__ void cg_matvec_vertex(const CgView &v, int U) {
+    const float third = 1.0f / 3.0f;
+    for (int j = threadIdx.x; j < U; j += blockDim.x) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        const int e1 = v.seg[j + 1];
+        for (int e = v.seg[j]; e < e1; ++e) {
+            int c = v.cval[e];
+            int s = c >> 2;
+            float ps = ((c & 3) ? -third : 1.0f) * v.r[s];
+            float3 n = v.nrm(s);
+            a0 += ps * n.x;
+            a1 += ps * n.y;
+            a2 += ps * n.z;
+        }
+        float w = v.winv[j];
+        v.ux[j] = w * a0;
+        v.uy[j] = w * a1;
+        v.uz[j] = w * a2;
+    }
+}
+
+__device__ __forceinline__ float cg_matvec_stencil(const CgView &v, int s) {
+    const float third = 1.0f / 3.0f;
+    int4 g = v.vidx[s];
+    float3 n = v.nrm(s);
+    float d0 = v.ux[g.x] - (v.ux[g.y] + v.ux[g.z] + v.ux[g.w]) * third;
+    float d1 = v.uy[g.x] - (v.uy[g.y] + v.uy[g.z] + v.uy[g.w]) * third;
+    float d2 = v.uz[g.x] - (v.uz[g.y] + v.uz[g.z] + v.uz[g.w]) * third;
+    return n.x * d0 + n.y * d1 + n.z * d2;
+}
+
+// returns the iteration count; x holds the solution of A x = r0
+__device__ __forceinline__ int cg_cg_loop(const CgView &v, int k, int U, int maxit, float tol,
+                                          float *red) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // w = A r, gamma = (r, r), delta = (w, r)
+    cg_matvec_vertex(v, U);
+    __syncthreads();
+    float ga = 0.f, de = 0.f;
+    for (int s = tid; s < k; s += nt) {
+        float ws = cg_matvec_stencil(v, s);
+        float rs = v.r[s];
+        v.w[s] = ws;
+        ga += rs * rs;
+        de += ws * rs;
+    }
+    float gamma, delta;
+    block_sum2(ga, de, red, gamma, delta);
+    const float stop = tol * tol * gamma;
+    float alpha = gamma / delta, beta = 0.f;
+    int it = 0;
+    while (it < maxit && gamma > stop && gamma > 0.f && alpha > 0.f && isfinite(alpha)) {
+        for (int s = tid; s < k; s += nt) {
+            float ps = v.r[s] + beta * v.p[s];
+            float ss = v.w[s] + beta * v.sv[s];
+            v.p[s] = ps;
+            v.sv[s] = ss;
+            v.x[s] += alpha * ps;
+            v.r[s] -= alpha * ss;
+        }
+        __syncthreads();
+        cg_matvec_vertex(v, U);
+        __syncthreads();
+        ga = 0.f;
+        de = 0.f;
+        for (int s = tid; s < k; s += nt) {
+            float ws = cg_matvec_stencil(v, s);
+            float rs = v.r[s];
+            v.w[s] = ws;
+            ga += rs * rs;
+            de += ws * rs;
+        }
+        float gn, dn;
+        block_sum2(ga, de, red, gn, dn);
+        beta = gn / gamma;
+        alpha = gn / (dn - beta * gn / alpha);
+        gamma = gn;
+        ++it;
+    }
+    return it;
+}
+
+// One float32 run of the mixed solver: rhs = r64 (the float64 residual),
+// on exit lam += x.  Skipped once ctl[0] (converged) is set.
+__global__ void __launch_bounds__(CG_THREADS) k_cg_fast(
+    const int *d_k, const int *d_U, const int *seg_g, const int *cval_g, const float *winv_g,
+    const float4 *n32, const int4 *vidx_g, const double *rhs64, double *lam, float *x_g, float *r_g,
+    float *p_g, float *s_g, float *w_g, float *u_g, int cap4, int maxit, double tol, int *ctl,
+    int smem_bytes) {
+    extern __shared__ float4 smem4[];
+    __shared__ float red[64];
+    if (ctl[0]) return;
+    const int k = *d_k, U = *d_U, tid = threadIdx.x, nt = blockDim.x;
+    CgView v;
+    const long long need = 64ll * k + 20ll * U + 16;
+    if (need <= smem_bytes) {
+        // layout: vidx | r p x sv w | nx ny nz | ux uy uz | seg | cval | winv
+        char *base = (char *)smem4;
+        int4 *vidx = (int4 *)base;
+        float *f = (float *)(vidx + k);
+        v.r = f; v.p = f + k; v.x = f + 2 * k; v.sv = f + 3 * k; v.w = f + 4 * k;
+        float *nx = f + 5 * k, *ny = f + 6 * k, *nz = f + 7 * k;
+        v.ux = f + 8 * k; v.uy = v.ux + U; v.uz = v.uy + U;
+        int *seg = (int *)(v.uz + U);
+        int *cval = seg + U + 1;
+        float *winv = (float *)(cval + 4 * k);
+        for (int s = tid; s < k; s += nt) {
+            vidx[s] = vidx_g[s];
+            float4 n = n32[s];
+            nx[s] = n.x; ny[s] = n.y; nz[s] = n.z;
+        }
+        for (int j = tid; j <= U; j += nt) seg[j] = seg_g[j];
+        for (int j = tid; j < U; j += nt) winv[j] = winv_g[j];
+        for (int e = tid; e < 4 * k; e += nt) cval[e] = cval_g[e];
+        v.nx = nx; v.ny = ny; v.nz = nz; v.n4 = nullptr;
+        v.vidx = vidx; v.seg = seg; v.cval = cval; v.winv = winv;
+    } else {
+        v.r = r_g; v.p = p_g; v.x = x_g; v.sv = s_g; v.w = w_g;
+        v.ux = u_g; v.uy = u_g + cap4; v.uz = u_g + 2 * cap4;
+        v.nx = v.ny = v.nz = nullptr; v.n4 = n32;
+        v.vidx = vidx_g; v.seg = seg_g; v.cval = cval_g; v.winv = winv_g;
+    }
+    for (int s = tid; s < k; s += nt) {
+        v.r[s] = (float)rhs64[s];
+        v.p[s] = 0.f;
+        v.sv[s] = 0.f;
+        v.x[s] = 0.f;
+    }
+    __syncthreads();
+    int it = cg_cg_loop(v, k, U, maxit, (float)tol, red);
+    for (int s = tid; s < k; s += nt) lam[s] += (double)v.x[s];
+    if (tid == 0) {
+        ctl[1] += it;
+        ctl[2] += 1;
+        ctl[4] |= need <= smem_bytes ? 1 : 2;  // 1: shared-memory path ran, 2: global path ran
+    }
+}
+
 // float64 residual, vertex half: u = M^-1 J^T lam
 __global__ void k_res_vertex(const int *d_U, const int *seg, const int *cval, const float *winv,
                              const double4_32a *n64, const double *lam, double *u, const int *ctl) {
@@ -374,13 +569,11 @@ void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers 
     { k_csr_flags<<<1, 1, 0, s>>>(sb.ckey, d_k, cap, sb.cflag, d_n4); note_launch(); }  // count only
     int vb = bits_for((long long)mp.A.n_verts + mp.B.n_verts);
     bool flip = radix_sort_u32_dev(sb.ckey, sb.cval, sb.ckey_alt, sb.cval_alt, d_n4, n4, vb, t, s);
-    if (flip) {
-        cudaMemcpyAsync(sb.ckey, sb.ckey_alt, sizeof(unsigned) * n4, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(sb.cval, sb.cval_alt, sizeof(int) * n4, cudaMemcpyDeviceToDevice, s);
-    }
-    { k_csr_flags<<<nb, 256, 0, s>>>(sb.ckey, d_k, cap, sb.cflag, d_n4); note_launch(); }
+    sb.ckey_s = flip ? sb.ckey_alt : sb.ckey;
+    sb.cval_s = flip ? sb.cval_alt : sb.cval;
+    { k_csr_flags<<<nb, 256, 0, s>>>(sb.ckey_s, d_k, cap, sb.cflag, d_n4); note_launch(); }
     scan_flags_dev(sb.cflag, d_n4, n4, sb.d_U, s);
-    { k_csr_build<<<nb, 256, 0, s>>>(sb.ckey, sb.cval, sb.cflag, d_k, cap, mp.A.n_verts,
+    { k_csr_build<<<nb, 256, 0, s>>>(sb.ckey_s, sb.cval_s, sb.cflag, d_k, cap, mp.A.n_verts,
                                    mp.A.inv_mass, mp.B.inv_mass, sb.vidx, sb.seg, sb.gvert, sb.winv); note_launch(); }
 }
 
@@ -388,17 +581,24 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
            cudaStream_t s) {
     (void)d_status;
     if (cap <= 0) return;
+    // dynamic shared memory granted to the fast CG kernel (0 until set)
+    static int fast_smem = -1;
+    if (fast_smem < 0) {
+        fast_smem = cudaFuncSetAttribute(k_cg_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         FAST_SMEM) == cudaSuccess ? FAST_SMEM : 0;
+        if (!fast_smem) cudaGetLastError();  // refused: the global-memory path runs
+    }
     int rb = (cap + 255) / 256;
     if (rb > RES_BLOCKS) rb = RES_BLOCKS;
     cudaMemsetAsync(sb.iwork, 0, sizeof(int) * 16, s);
     { k_init_lam<<<rb, 256, 0, s>>>(d_k, sb.b, sb.lam, sb.r64); note_launch(); }
     if (p.solver == HFCR_SOLVER_FP64) {
         // one float64 run with the whole iteration budget of the mixed solver
-        { k_cg<double><<<1, CG_THREADS, 0, s>>>(1, d_k, sb.d_U, sb.seg, sb.cval, sb.winv, sb.n64,
+        { k_cg<double><<<1, CG_THREADS, 0, s>>>(1, d_k, sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64,
                                               sb.vidx, sb.b, sb.lam, sb.p64 + 0, sb.r64, sb.p64 + cap,
                                               sb.q64, sb.u64, p.max_cg_iters * p.max_refine,
                                               p.rel_tol, sb.iwork); note_launch(); }
-        { k_res_vertex<<<rb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval, sb.winv, sb.n64, sb.lam, sb.u64,
+        { k_res_vertex<<<rb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64, sb.lam, sb.u64,
                                          sb.iwork); note_launch(); }
         { k_res_stencil<<<rb, 256, 0, s>>>(d_k, sb.vidx, sb.n64, sb.b, sb.u64, sb.r64, sb.red,
                                           sb.iwork); note_launch(); }
@@ -407,10 +607,12 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
     }
     // MIXED: float32 runs on the float64 residual (r = b to start)
     for (int round = 0; round < p.max_refine; ++round) {
-        { k_cg<float><<<1, CG_THREADS, 0, s>>>(0, d_k, sb.d_U, sb.seg, sb.cval, sb.winv, sb.n32,
-                                             sb.vidx, sb.r64, sb.lam, sb.x32, sb.r32, sb.p32,
-                                             sb.q32, sb.u32, p.max_cg_iters, p.inner_tol, sb.iwork); note_launch(); }
-        { k_res_vertex<<<rb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval, sb.winv, sb.n64, sb.lam, sb.u64,
+        { k_cg_fast<<<1, CG_THREADS, fast_smem, s>>>(d_k, sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n32,
+                                                    sb.vidx, sb.r64, sb.lam, sb.x32, sb.r32, sb.p32,
+                                                    sb.q32, sb.w32, sb.u32, 4 * sb.cap_k,
+                                                    p.max_cg_iters, p.inner_tol, sb.iwork,
+                                                    fast_smem); note_launch(); }
+        { k_res_vertex<<<rb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64, sb.lam, sb.u64,
                                          sb.iwork); note_launch(); }
         { k_res_stencil<<<rb, 256, 0, s>>>(d_k, sb.vidx, sb.n64, sb.b, sb.u64, sb.r64, sb.red,
                                           sb.iwork); note_launch(); }
@@ -425,7 +627,7 @@ void displacement(const MeshPair &mp, int cap, SolveBuffers &sb, int apply, void
     if (nb > 1024) nb = 1024;
     void *a0 = dxA ? dxA[0] : nullptr, *a1 = dxA ? dxA[1] : nullptr, *a2 = dxA ? dxA[2] : nullptr;
     void *b0 = dxB ? dxB[0] : nullptr, *b1 = dxB ? dxB[1] : nullptr, *b2 = dxB ? dxB[2] : nullptr;
-    { k_displace<<<nb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval, sb.winv, sb.n64, sb.lam, sb.gvert, mp.A,
+    { k_displace<<<nb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64, sb.lam, sb.gvert, mp.A,
                                   mp.B, apply, a0, a1, a2, b0, b1, b2); note_launch(); }
 }
 

@@ -58,7 +58,10 @@ __device__ __forceinline__ void rank_tile(const K *kin, const int *vin, int n, i
 template <typename K>
 __global__ void __launch_bounds__(TPB) k_hist(const K *keys, int n, const int *d_n, int shift,
                                               unsigned *hist, int nblocks) {
-    if (d_n) n = min(n, *d_n);
+    if (d_n) {
+        n = min(n, *d_n);
+        if (n <= SMALL_N) return;  // the single-CTA kernel sorts it
+    }
     __shared__ unsigned h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -72,7 +75,9 @@ __global__ void __launch_bounds__(TPB) k_hist(const K *keys, int n, const int *d
 }
 
 // exclusive scan of a[0..m) in place by one CTA of 1024 threads; total to *d_total
-__global__ void __launch_bounds__(1024) k_scan1(unsigned *a, int m, const int *d_m, int *d_total) {
+__global__ void __launch_bounds__(1024) k_scan1(unsigned *a, int m, const int *d_m, int *d_total,
+                                               const int *d_gate = nullptr) {
+    if (d_gate && *d_gate <= SMALL_N) return;  // histogram scan of a sort the single CTA handled
     if (d_m) m = min(m, *d_m);
     __shared__ unsigned ws[32];
     const int t = threadIdx.x;
@@ -113,7 +118,10 @@ template <typename K, bool HV>
 __global__ void __launch_bounds__(TPB) k_scatter(const K *kin, const int *vin, K *kout, int *vout,
                                                  int n, const int *d_n, int shift,
                                                  const unsigned *hist, int nblocks) {
-    if (d_n) n = min(n, *d_n);
+    if (d_n) {
+        n = min(n, *d_n);
+        if (n <= SMALL_N) return;
+    }
     __shared__ unsigned wh[TPB / 32][256];
     for (int i = threadIdx.x; i < (TPB / 32) * 256; i += TPB) (&wh[0][0])[i] = 0;
     __syncthreads();
@@ -147,6 +155,7 @@ template <typename K, bool HV>
 __global__ void __launch_bounds__(TPB) k_sort_small(K *k0, int *v0, K *k1, int *v1, int n,
                                                     const int *d_n, int bits) {
     if (d_n) n = min(n, *d_n);
+    if (n > SMALL_N) return;  // the multi-CTA kernels sort it
     __shared__ unsigned wh[TPB / 32][256];
     __shared__ unsigned off[256];
     __shared__ unsigned cnt[256];
@@ -214,11 +223,14 @@ __global__ void __launch_bounds__(TPB) k_sort_small(K *k0, int *v0, K *k1, int *
 template <typename K, bool HV>
 bool radix_sort_impl(K *k0, int *v0, K *k1, int *v1, int n, const int *d_n, int bits,
                      SortTemp &t, cudaStream_t s) {
+    // n: the element count (d_n == null) or an upper bound of *d_n
     int passes = (bits + 7) / 8;
     if (n <= 0 || passes == 0) return false;
-    if (n <= SMALL_N) {
+    if (n <= SMALL_N || d_n) {
+        // with a device count the single CTA sorts whenever *d_n <= SMALL_N
+        // and the multi-CTA kernels below return at once; otherwise the reverse
         { k_sort_small<K, HV><<<1, TPB, 0, s>>>(k0, v0, k1, v1, n, d_n, passes * 8); note_launch(); }
-        return passes & 1;
+        if (n <= SMALL_N) return passes & 1;
     }
     int nb = (n + TILE - 1) / TILE;
     K *kin = k0, *kout = k1;
@@ -226,7 +238,7 @@ bool radix_sort_impl(K *k0, int *v0, K *k1, int *v1, int n, const int *d_n, int 
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
         { k_hist<K><<<nb, TPB, 0, s>>>(kin, n, d_n, shift, t.hist, nb); note_launch(); }
-        { k_scan1<<<1, 1024, 0, s>>>(t.hist, 256 * nb, nullptr, nullptr); note_launch(); }
+        { k_scan1<<<1, 1024, 0, s>>>(t.hist, 256 * nb, nullptr, nullptr, d_n); note_launch(); }
         { k_scatter<K, HV><<<nb, TPB, 0, s>>>(kin, vin, kout, vout, n, d_n, shift, t.hist, nb); note_launch(); }
         K *tk = kin; kin = kout; kout = tk;
         int *tv = vin; vin = vout; vout = tv;
