@@ -88,6 +88,9 @@ void free_all(hfcr_ctx *c) {
     void *ptrs[] = {c->d_status, c->d_stats, c->d_cnt, c->sort.hist, c->edges[0], c->edges[1],
                     c->ekeys, c->ekeys_alt, c->eflags, c->pkeys, c->pkeys_alt, c->pairs,
                     c->skeys, c->skeys_alt, c->sflags, c->stencils,
+                    c->sb.ids_raw, c->sb.n64_raw, c->sb.n32_raw, c->sb.b_raw, c->sb.parent,
+                    c->sb.zkey, c->sb.zkey_alt, c->sb.szone, c->sb.zs, c->sb.zv, c->sb.d_nz,
+                    c->sb.ck64, c->sb.ck64_alt,
                     c->sb.ids, c->sb.n64, c->sb.n32, c->sb.b, c->sb.lam, c->sb.r64, c->sb.r32,
                     c->sb.x32, c->sb.p32, c->sb.q32, c->sb.w32, c->sb.p64, c->sb.q64, c->sb.vidx, c->sb.ckey,
                     c->sb.ckey_alt, c->sb.cval, c->sb.cval_alt, c->sb.cflag, c->sb.seg, c->sb.gvert,
@@ -356,7 +359,8 @@ hfcr_status run_response(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     MeshPair mp{*A, *B};
     prof_begin(ctx, HFCR_STAGE_ASSEMBLE, s);
     assemble(mp, st, ctx->d_cnt + C_STENCILS, k, d, ctx->sb, ctx->d_status, s);
-    build_vertex_csr(mp, ctx->d_cnt + C_STENCILS, k, ctx->sb, ctx->sort, ctx->d_cnt + C_N4, s);
+    build_vertex_csr(mp, ctx->d_cnt + C_STENCILS, k, ctx->sb, ctx->sort, ctx->d_cnt + C_N4,
+                     ctx->d_status, s);
     prof_end(ctx, HFCR_STAGE_ASSEMBLE, s);
     prof_begin(ctx, HFCR_STAGE_SOLVE, s);
     solve(params_of(ctx->opt), ctx->d_cnt + C_STENCILS, k, ctx->sb, ctx->d_status, s);
@@ -526,6 +530,19 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(dalloc(&ctx->stencils, P));
     SolveBuffers &sb = ctx->sb;
     sb.cap_k = (int)P;
+    CK(dalloc(&sb.ids_raw, P));
+    CK(dalloc(&sb.n64_raw, P));
+    CK(dalloc(&sb.n32_raw, P));
+    CK(dalloc(&sb.b_raw, P));
+    CK(dalloc(&sb.parent, P));
+    CK(dalloc(&sb.zkey, P));
+    CK(dalloc(&sb.zkey_alt, P));
+    CK(dalloc(&sb.szone, P));
+    CK(dalloc(&sb.zs, P + 1));
+    CK(dalloc(&sb.zv, 4 * P + 1));
+    CK(dalloc(&sb.d_nz, 1));
+    CK(dalloc(&sb.ck64, 4 * P));
+    CK(dalloc(&sb.ck64_alt, 4 * P));
     CK(dalloc(&sb.ids, P));
     CK(dalloc(&sb.n64, P));
     CK(dalloc(&sb.n32, P));

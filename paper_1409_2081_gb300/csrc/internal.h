@@ -73,6 +73,8 @@ bool radix_sort_u64_dev(unsigned long long *k0, unsigned long long *k1, const in
                         int bits, SortTemp &t, cudaStream_t s);
 bool radix_sort_u32_dev(unsigned *k0, int *v0, unsigned *k1, int *v1, const int *d_n, int cap,
                         int bits, SortTemp &t, cudaStream_t s);
+bool radix_sort_u64v_dev(unsigned long long *k0, int *v0, unsigned long long *k1, int *v1,
+                         const int *d_n, int cap, int bits, SortTemp &t, cudaStream_t s);
 int sort_blocks_for(int n);
 
 // Exclusive scan of n unsigned flags (in place), total written to *d_total.
@@ -129,6 +131,19 @@ void stencil_unique(const unsigned long long *keys, const int *d_n, int cap, int
 // ---- solver ----
 struct SolveBuffers {
     int cap_k = 0;       // stencils
+    // rows as assembled (stencil order) ...
+    int4 *ids_raw = nullptr;
+    double4_32a *n64_raw = nullptr;
+    float4 *n32_raw = nullptr;
+    double *b_raw = nullptr;
+    // ... and regrouped by impact zone (the arrays below are zone-ordered)
+    int *parent = nullptr;       // [cap_k] union-find forest over stencils
+    unsigned long long *zkey = nullptr, *zkey_alt = nullptr;  // [cap_k] (zone label, stencil)
+    int *szone = nullptr;        // [cap_k] zone of each zone-ordered stencil
+    int *zs = nullptr;           // [cap_k + 1] first stencil of each zone
+    int *zv = nullptr;           // [4 cap_k + 1] first touched vertex of each zone
+    int *d_nz = nullptr;         // zone count (device)
+    unsigned long long *ck64 = nullptr, *ck64_alt = nullptr;  // [4 cap_k] (zone, vertex) keys
     int4 *ids = nullptr;         // [cap_k] global vertex ids
     double4_32a *n64 = nullptr;      // [cap_k] unit normal (w unused)
     float4 *n32 = nullptr;       // [cap_k]
@@ -167,7 +182,7 @@ void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int ca
               SolveBuffers &sb, uint32_t *d_status, cudaStream_t s);
 // d_n4: device word receiving 4k (the CSR entry count)
 void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers &sb, SortTemp &t,
-                      int *d_n4, cudaStream_t s);
+                      int *d_n4, uint32_t *d_status, cudaStream_t s);
 // Solves and leaves lambda in sb.lam; results (iters, residual) in sb.iwork / sb.dwork.
 void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint32_t *d_status,
            cudaStream_t s);

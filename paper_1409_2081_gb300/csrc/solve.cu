@@ -244,6 +244,8 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg(
 // ---------------------------------------------------------------------------
 
 constexpr int FAST_SMEM = 231424;  // 226 KB dynamic (+256 B static) under the 227 KB per-CTA limit
+constexpr int ZONE_SMALL_SMEM = 56 * 1024;  // small zones: up to 4 CTAs per SM
+constexpr int ZONE_BIG = 1024;  // zones with at least this many stencils get a 1024-thread CTA
 
 struct CgView {
     float *r, *p, *x, *sv, *w;   // [k]
@@ -254,6 +256,7 @@ struct CgView {
     const int *seg;              // [U + 1]
     const int *cval;             // [4 k]
     const float *winv;           // [U]
+    int voff = 0, coff = 0, eoff = 0;  // subtracted from vidx, cval and seg values (global path)
     __device__ __forceinline__ float3 nrm(int s) const {
         if (nx) return make_float3(nx[s], ny[s], nz[s]);
         float4 v = n4[s];
@@ -295,9 +298,9 @@ __device__ __forceinline__ void cg_matvec_vertex(const CgView &v, int U) {
     const float third = 1.0f / 3.0f;
     for (int j = threadIdx.x; j < U; j += blockDim.x) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        const int e1 = v.seg[j + 1];
-        for (int e = v.seg[j]; e < e1; ++e) {
-            int c = v.cval[e];
+        const int e1 = v.seg[j + 1] - v.eoff;
+        for (int e = v.seg[j] - v.eoff; e < e1; ++e) {
+            int c = v.cval[e] - v.coff;
             int s = c >> 2;
             float ps = ((c & 3) ? -third : 1.0f) * v.r[s];
             float3 n = v.nrm(s);
@@ -315,6 +318,7 @@ __device__ __forceinline__ void cg_matvec_vertex(const CgView &v, int U) {
 __device__ __forceinline__ float cg_matvec_stencil(const CgView &v, int s) {
     const float third = 1.0f / 3.0f;
     int4 g = v.vidx[s];
+    g.x -= v.voff; g.y -= v.voff; g.z -= v.voff; g.w -= v.voff;
     float3 n = v.nrm(s);
     float d0 = v.ux[g.x] - (v.ux[g.y] + v.ux[g.z] + v.ux[g.w]) * third;
     float d1 = v.uy[g.x] - (v.uy[g.y] + v.uy[g.z] + v.uy[g.w]) * third;
@@ -373,59 +377,232 @@ __device__ __forceinline__ int cg_cg_loop(const CgView &v, int k, int U, int max
     return it;
 }
 
-// One float32 run of the mixed solver: rhs = r64 (the float64 residual),
-// on exit lam += x.  Skipped once ctl[0] (converged) is set.
-__global__ void __launch_bounds__(CG_THREADS) k_cg_fast(
-    const int *d_k, const int *d_U, const int *seg_g, const int *cval_g, const float *winv_g,
-    const float4 *n32, const int4 *vidx_g, const double *rhs64, double *lam, float *x_g, float *r_g,
-    float *p_g, float *s_g, float *w_g, float *u_g, int cap4, int maxit, double tol, int *ctl,
+// ---------------------------------------------------------------------------
+// impact zones (Sec. 4: constraints with overlapping stencils form one
+// zone, and each zone is one linear system).  Lock-free union-find over the
+// stencils that share a vertex: a root is only ever hooked under a smaller
+// root (atomicCAS), so each zone ends with its smallest stencil index as
+// root; path halving only rewrites non-root entries with an ancestor.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int uf_find(int *parent, int x) {
+    while (true) {
+        int p = __ldcg(parent + x);
+        if (p == x) return x;
+        int gp = __ldcg(parent + p);
+        if (gp != p) parent[x] = gp;
+        x = p;
+    }
+}
+
+__global__ void k_uf_init(const int *d_k, int *parent) {
+    const int k = *d_k;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
+        parent[i] = i;
+}
+
+// unions the stencils of every touched vertex (CSR by vertex)
+__global__ void k_uf_union(const int *d_U, const int *seg, const int *cval, int *parent,
+                           uint32_t *status) {
+    const int U = *d_U;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < U; j += gridDim.x * blockDim.x) {
+        const int e0 = seg[j], e1 = seg[j + 1];
+        const int s0 = cval[e0] >> 2;
+        for (int e = e0 + 1; e < e1; ++e) {
+            int a = s0, b = cval[e] >> 2;
+            // every failed exchange means another thread hooked that root:
+            // the count of roots falls, so the loop ends; the bound is a guard
+            int guard = 0;
+            while (true) {
+                a = uf_find(parent, a);
+                b = uf_find(parent, b);
+                if (a == b) break;
+                if (a < b) { int t = a; a = b; b = t; }
+                int old = atomicCAS(parent + a, a, b);
+                if (old == a) break;
+                a = old;
+                if (++guard > (1 << 24)) { atomicOr(status, ST_TIMEOUT); break; }
+            }
+        }
+    }
+}
+
+__global__ void k_zone_keys(const int *d_k, int *parent, int kb, unsigned long long *zkey) {
+    const int k = *d_k;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
+        zkey[i] = ((unsigned long long)uf_find(parent, i) << kb) | (unsigned)i;
+}
+
+__global__ void k_zone_flags(const int *d_k, const unsigned long long *zkey, int kb,
+                             unsigned *flags) {
+    const int k = *d_k;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x)
+        flags[t] = (t == 0 || (zkey[t] >> kb) != (zkey[t - 1] >> kb)) ? 1u : 0u;
+}
+
+// regroups the rows zone by zone (zone order = order of the smallest stencil)
+__global__ void k_zone_gather(const int *d_k, const unsigned long long *zkey, int kb,
+                              const unsigned *excl, const int4 *ids_raw,
+                              const double4_32a *n64_raw, const float4 *n32_raw,
+                              const double *b_raw, int4 *ids, double4_32a *n64, float4 *n32,
+                              double *b, int *szone, int *zs) {
+    const int k = *d_k;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
+        unsigned long long key = zkey[t];
+        int src = (int)(key & ((1ull << kb) - 1));
+        unsigned f = (t == 0 || (key >> kb) != (zkey[t - 1] >> kb)) ? 1u : 0u;
+        int z = (int)(excl[t] + f) - 1;
+        szone[t] = z;
+        if (f) zs[z] = t;
+        if (t == k - 1) zs[z + 1] = k;
+        ids[t] = ids_raw[src];
+        n64[t] = n64_raw[src];
+        n32[t] = n32_raw[src];
+        b[t] = b_raw[src];
+    }
+}
+
+// CSR entries keyed (zone, vertex): vertices come out grouped by zone
+__global__ void k_csr2_entries(const int4 *ids, const int *szone, const int *d_k, int cap, int vb,
+                               unsigned long long *key, int *val) {
+    int k = min(*d_k, cap);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4 * k) return;
+    int t = i >> 2, role = i & 3;
+    key[i] = ((unsigned long long)szone[t] << vb) | (unsigned)((const int *)ids)[4 * t + role];
+    val[i] = i;
+}
+
+__global__ void k_csr2_flags(const unsigned long long *key, const int *d_k, int cap,
+                             unsigned *flag) {
+    int n = 4 * min(*d_k, cap);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_csr2_build(const unsigned long long *key, const int *val, const unsigned *excl,
+                             const int *d_k, int cap, int vb, int nA, const float *wA,
+                             const float *wB, int4 *vidx, int *seg, int *gvert, float *winv,
+                             int *zv, const int *d_nz) {
+    int n = 4 * min(*d_k, cap);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long kk = key[i];
+    unsigned f = (i == 0 || kk != key[i - 1]) ? 1u : 0u;
+    int j = (int)(excl[i] + f) - 1;
+    ((int *)vidx)[val[i]] = j;
+    if (f) {
+        int g = (int)(kk & ((1ull << vb) - 1));
+        seg[j] = i;
+        gvert[j] = g;
+        const float *w = g < nA ? wA : wB;
+        int lv = g < nA ? g : g - nA;
+        winv[j] = w ? w[lv] : 1.0f;
+        if (i == 0 || (kk >> vb) != (key[i - 1] >> vb)) zv[(int)(kk >> vb)] = j;
+    }
+    if (i == n - 1) {
+        seg[j + 1] = n;
+        zv[*d_nz] = j + 1;
+    }
+}
+
+// One float32 CG run per impact zone of the mixed solver (rhs = the float64
+// residual restricted to the zone, lam += x on exit).  Zones with at least
+// `big_min` stencils go to the launch with is_big = 1 (1024 threads, all of
+// shared memory), the others to is_big = 0 (256 threads, a quarter); a zone
+// whose residual is already below rel_tol |b| / sqrt(#zones) is skipped.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
+    const int *d_nz, const int *zs, const int *zv, int big_min, int is_big, const int *seg_g,
+    const int *cval_g, const float *winv_g, const float4 *n32, const int4 *vidx_g,
+    const double *rhs64, double *lam, float *x_g, float *r_g, float *p_g, float *s_g, float *w_g,
+    float *u_g, int cap4, int maxit, double tol, double rel_tol, const double *bnorm2, int *ctl,
     int smem_bytes) {
     extern __shared__ float4 smem4[];
     __shared__ float red[64];
+    __shared__ double redd[THREADS / 32];
     if (ctl[0]) return;
-    const int k = *d_k, U = *d_U, tid = threadIdx.x, nt = blockDim.x;
-    CgView v;
-    const long long need = 64ll * k + 20ll * U + 16;
-    if (need <= smem_bytes) {
-        // layout: vidx | r p x sv w | nx ny nz | ux uy uz | seg | cval | winv
-        char *base = (char *)smem4;
-        int4 *vidx = (int4 *)base;
-        float *f = (float *)(vidx + k);
-        v.r = f; v.p = f + k; v.x = f + 2 * k; v.sv = f + 3 * k; v.w = f + 4 * k;
-        float *nx = f + 5 * k, *ny = f + 6 * k, *nz = f + 7 * k;
-        v.ux = f + 8 * k; v.uy = v.ux + U; v.uz = v.uy + U;
-        int *seg = (int *)(v.uz + U);
-        int *cval = seg + U + 1;
-        float *winv = (float *)(cval + 4 * k);
-        for (int s = tid; s < k; s += nt) {
-            vidx[s] = vidx_g[s];
-            float4 n = n32[s];
-            nx[s] = n.x; ny[s] = n.y; nz[s] = n.z;
+    const int nz = *d_nz, tid = threadIdx.x, nt = blockDim.x;
+    const double zone_tol2 = rel_tol * rel_tol * (*bnorm2) / (double)(nz > 0 ? nz : 1);
+    for (int z = blockIdx.x; z < nz; z += gridDim.x) {
+        const int s0 = zs[z], k = zs[z + 1] - s0;
+        const int j0 = zv[z], U = zv[z + 1] - j0;
+        if ((k >= big_min) != (is_big != 0)) continue;
+        // skip a zone that already meets its share of the tolerance
+        double rz = 0.0;
+        for (int t = tid; t < k; t += nt) rz += rhs64[s0 + t] * rhs64[s0 + t];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) rz += __shfl_xor_sync(0xffffffffu, rz, o);
+        if ((tid & 31) == 0) redd[tid >> 5] = rz;
+        __syncthreads();
+        double rzs = 0.0;
+        for (int w = 0; w < nt / 32; ++w) rzs += redd[w];
+        __syncthreads();
+        if (rzs <= 0.5 * zone_tol2) continue;
+        const int e0 = seg_g[j0];
+        CgView v;
+        const long long need = 64ll * k + 20ll * U + 16;
+        if (need <= smem_bytes) {
+            char *base = (char *)smem4;
+            int4 *vidx = (int4 *)base;
+            float *f = (float *)(vidx + k);
+            v.r = f; v.p = f + k; v.x = f + 2 * k; v.sv = f + 3 * k; v.w = f + 4 * k;
+            float *nx = f + 5 * k, *ny = f + 6 * k, *nz_ = f + 7 * k;
+            v.ux = f + 8 * k; v.uy = v.ux + U; v.uz = v.uy + U;
+            int *seg = (int *)(v.uz + U);
+            int *cval = seg + U + 1;
+            float *winv = (float *)(cval + 4 * k);
+            for (int t = tid; t < k; t += nt) {
+                int4 g = vidx_g[s0 + t];
+                vidx[t] = make_int4(g.x - j0, g.y - j0, g.z - j0, g.w - j0);
+                float4 n = n32[s0 + t];
+                nx[t] = n.x; ny[t] = n.y; nz_[t] = n.z;
+            }
+            for (int j = tid; j <= U; j += nt) seg[j] = seg_g[j0 + j] - e0;
+            for (int j = tid; j < U; j += nt) winv[j] = winv_g[j0 + j];
+            for (int e = tid; e < 4 * k; e += nt) cval[e] = cval_g[e0 + e] - 4 * s0;
+            v.nx = nx; v.ny = ny; v.nz = nz_; v.n4 = nullptr;
+            v.vidx = vidx; v.seg = seg; v.cval = cval; v.winv = winv;
+            v.voff = 0; v.coff = 0; v.eoff = 0;
+        } else {
+            v.r = r_g + s0; v.p = p_g + s0; v.x = x_g + s0; v.sv = s_g + s0; v.w = w_g + s0;
+            v.ux = u_g + j0; v.uy = u_g + cap4 + j0; v.uz = u_g + 2 * cap4 + j0;
+            v.nx = v.ny = v.nz = nullptr; v.n4 = n32 + s0;
+            v.vidx = vidx_g + s0; v.seg = seg_g + j0; v.cval = cval_g; v.winv = winv_g + j0;
+            v.voff = j0; v.coff = 4 * s0; v.eoff = 0;
         }
-        for (int j = tid; j <= U; j += nt) seg[j] = seg_g[j];
-        for (int j = tid; j < U; j += nt) winv[j] = winv_g[j];
-        for (int e = tid; e < 4 * k; e += nt) cval[e] = cval_g[e];
-        v.nx = nx; v.ny = ny; v.nz = nz; v.n4 = nullptr;
-        v.vidx = vidx; v.seg = seg; v.cval = cval; v.winv = winv;
-    } else {
-        v.r = r_g; v.p = p_g; v.x = x_g; v.sv = s_g; v.w = w_g;
-        v.ux = u_g; v.uy = u_g + cap4; v.uz = u_g + 2 * cap4;
-        v.nx = v.ny = v.nz = nullptr; v.n4 = n32;
-        v.vidx = vidx_g; v.seg = seg_g; v.cval = cval_g; v.winv = winv_g;
+        for (int t = tid; t < k; t += nt) {
+            v.r[t] = (float)rhs64[s0 + t];
+            v.p[t] = 0.f;
+            v.sv[t] = 0.f;
+            v.x[t] = 0.f;
+        }
+        __syncthreads();
+        int it = cg_cg_loop(v, k, U, maxit, (float)tol, red);
+        for (int t = tid; t < k; t += nt) lam[s0 + t] += (double)v.x[t];
+        if (tid == 0) {
+            atomicAdd(&ctl[1], it);
+            atomicAdd(&ctl[2], 1);
+            atomicOr(&ctl[4], need <= smem_bytes ? 1 : 2);
+        }
+        __syncthreads();  // shared memory is reused by the next zone
     }
-    for (int s = tid; s < k; s += nt) {
-        v.r[s] = (float)rhs64[s];
-        v.p[s] = 0.f;
-        v.sv[s] = 0.f;
-        v.x[s] = 0.f;
+}
+
+// ||b||^2 partials and r = b, lam = 0 (the first residual of the mixed solver)
+__global__ void k_init_res(const int *d_k, const double *b, double *lam, double *r, double *red) {
+    __shared__ double sh[33];
+    const int k = *d_k;
+    double bb = 0.0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < k; s += gridDim.x * blockDim.x) {
+        lam[s] = 0.0;
+        r[s] = b[s];
+        bb += b[s] * b[s];
     }
-    __syncthreads();
-    int it = cg_cg_loop(v, k, U, maxit, (float)tol, red);
-    for (int s = tid; s < k; s += nt) lam[s] += (double)v.x[s];
-    if (tid == 0) {
-        ctl[1] += it;
-        ctl[2] += 1;
-        ctl[4] |= need <= smem_bytes ? 1 : 2;  // 1: shared-memory path ran, 2: global path ran
+    bb = block_sum(bb, sh);
+    if (threadIdx.x == 0) {
+        red[blockIdx.x] = bb;
+        red[RES_BLOCKS + blockIdx.x] = bb;
     }
 }
 
@@ -494,6 +671,7 @@ __global__ void k_res_check(const double *red, int nblk, double rel_tol, int *ct
     }
     double rel = bb > 0 ? sqrt(rr / bb) : 0.0;
     dres[0] = rel;
+    dres[1] = bb;
     if (rel <= rel_tol) ctl[0] = 1;
     if (count_round) ctl[3] += 1;
 }
@@ -556,25 +734,50 @@ __global__ void k_displace(const int *d_U, const int *seg, const int *cval, cons
 void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int cap, double d,
               SolveBuffers &sb, uint32_t *d_status, cudaStream_t s) {
     if (cap <= 0) return;
-    { k_assemble<<<(cap + 255) / 256, 256, 0, s>>>(mp.A, mp.B, st, d_k, cap, d, sb.ids, sb.n64,
-                                                 sb.n32, sb.b, d_status); note_launch(); }
+    { k_assemble<<<(cap + 255) / 256, 256, 0, s>>>(mp.A, mp.B, st, d_k, cap, d, sb.ids_raw,
+                                                 sb.n64_raw, sb.n32_raw, sb.b_raw, d_status); note_launch(); }
 }
 
 void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers &sb, SortTemp &t,
-                      int *d_n4, cudaStream_t s) {
+                      int *d_n4, uint32_t *d_status, cudaStream_t s) {
     if (cap <= 0) return;
     int n4 = 4 * cap;
     int nb = (n4 + 255) / 256;
-    { k_csr_entries<<<nb, 256, 0, s>>>(sb.ids, d_k, cap, sb.ckey, sb.cval); note_launch(); }
+    int gb = (cap + 255) / 256;
+    if (gb > 1024) gb = 1024;
+    // vertex -> stencils of the rows as assembled (for the impact zones)
+    { k_csr_entries<<<nb, 256, 0, s>>>(sb.ids_raw, d_k, cap, sb.ckey, sb.cval); note_launch(); }
     { k_csr_flags<<<1, 1, 0, s>>>(sb.ckey, d_k, cap, sb.cflag, d_n4); note_launch(); }  // count only
     int vb = bits_for((long long)mp.A.n_verts + mp.B.n_verts);
     bool flip = radix_sort_u32_dev(sb.ckey, sb.cval, sb.ckey_alt, sb.cval_alt, d_n4, n4, vb, t, s);
-    sb.ckey_s = flip ? sb.ckey_alt : sb.ckey;
-    sb.cval_s = flip ? sb.cval_alt : sb.cval;
-    { k_csr_flags<<<nb, 256, 0, s>>>(sb.ckey_s, d_k, cap, sb.cflag, d_n4); note_launch(); }
+    unsigned *ck1 = flip ? sb.ckey_alt : sb.ckey;
+    int *cv1 = flip ? sb.cval_alt : sb.cval;
+    { k_csr_flags<<<nb, 256, 0, s>>>(ck1, d_k, cap, sb.cflag, d_n4); note_launch(); }
     scan_flags_dev(sb.cflag, d_n4, n4, sb.d_U, s);
-    { k_csr_build<<<nb, 256, 0, s>>>(sb.ckey_s, sb.cval_s, sb.cflag, d_k, cap, mp.A.n_verts,
-                                   mp.A.inv_mass, mp.B.inv_mass, sb.vidx, sb.seg, sb.gvert, sb.winv); note_launch(); }
+    { k_csr_build<<<nb, 256, 0, s>>>(ck1, cv1, sb.cflag, d_k, cap, mp.A.n_verts, mp.A.inv_mass,
+                                   mp.B.inv_mass, sb.vidx, sb.seg, sb.gvert, sb.winv); note_launch(); }
+    // impact zones and the zone-ordered rows
+    int kb = bits_for((long long)cap + 1);
+    { k_uf_init<<<gb, 256, 0, s>>>(d_k, sb.parent); note_launch(); }
+    { k_uf_union<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(sb.d_U, sb.seg, cv1, sb.parent, d_status); note_launch(); }
+    { k_zone_keys<<<gb, 256, 0, s>>>(d_k, sb.parent, kb, sb.zkey); note_launch(); }
+    bool zflip = radix_sort_u64_dev(sb.zkey, sb.zkey_alt, d_k, cap, 2 * kb, t, s);
+    unsigned long long *zk = zflip ? sb.zkey_alt : sb.zkey;
+    { k_zone_flags<<<gb, 256, 0, s>>>(d_k, zk, kb, sb.cflag); note_launch(); }
+    scan_flags_dev(sb.cflag, d_k, cap, sb.d_nz, s);
+    { k_zone_gather<<<gb, 256, 0, s>>>(d_k, zk, kb, sb.cflag, sb.ids_raw, sb.n64_raw, sb.n32_raw,
+                                     sb.b_raw, sb.ids, sb.n64, sb.n32, sb.b, sb.szone, sb.zs); note_launch(); }
+    // vertex -> stencils again, keyed (zone, vertex): zone-contiguous numbering
+    int zb = bits_for((long long)cap + 1);
+    { k_csr2_entries<<<nb, 256, 0, s>>>(sb.ids, sb.szone, d_k, cap, vb, sb.ck64, sb.cval); note_launch(); }
+    bool flip2 = radix_sort_u64v_dev(sb.ck64, sb.cval, sb.ck64_alt, sb.cval_alt, d_n4, n4, zb + vb, t, s);
+    unsigned long long *ck2 = flip2 ? sb.ck64_alt : sb.ck64;
+    sb.cval_s = flip2 ? sb.cval_alt : sb.cval;
+    { k_csr2_flags<<<nb, 256, 0, s>>>(ck2, d_k, cap, sb.cflag); note_launch(); }
+    scan_flags_dev(sb.cflag, d_n4, n4, sb.d_U, s);
+    { k_csr2_build<<<nb, 256, 0, s>>>(ck2, sb.cval_s, sb.cflag, d_k, cap, vb, mp.A.n_verts,
+                                    mp.A.inv_mass, mp.B.inv_mass, sb.vidx, sb.seg, sb.gvert, sb.winv,
+                                    sb.zv, sb.d_nz); note_launch(); }
 }
 
 void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint32_t *d_status,
@@ -582,11 +785,14 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
     (void)d_status;
     if (cap <= 0) return;
     // dynamic shared memory granted to the fast CG kernel (0 until set)
-    static int fast_smem = -1;
+    static int fast_smem = -1, zone_small_smem = 0;
     if (fast_smem < 0) {
-        fast_smem = cudaFuncSetAttribute(k_cg_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        fast_smem = cudaFuncSetAttribute(k_cg_zone<CG_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          FAST_SMEM) == cudaSuccess ? FAST_SMEM : 0;
         if (!fast_smem) cudaGetLastError();  // refused: the global-memory path runs
+        zone_small_smem = cudaFuncSetAttribute(k_cg_zone<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               ZONE_SMALL_SMEM) == cudaSuccess ? ZONE_SMALL_SMEM : 0;
+        if (!zone_small_smem) cudaGetLastError();
     }
     int rb = (cap + 255) / 256;
     if (rb > RES_BLOCKS) rb = RES_BLOCKS;
@@ -605,13 +811,22 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
         { k_res_check<<<1, 32, 0, s>>>(sb.red, rb, p.rel_tol, sb.iwork, sb.dwork, 0); note_launch(); }
         return;
     }
-    // MIXED: float32 runs on the float64 residual (r = b to start)
+    // MIXED: float32 runs per impact zone on the float64 residual (r = b to start)
+    { k_init_res<<<rb, 256, 0, s>>>(d_k, sb.b, sb.lam, sb.r64, sb.red); note_launch(); }
+    { k_res_check<<<1, 32, 0, s>>>(sb.red, rb, p.rel_tol, sb.iwork, sb.dwork, 0); note_launch(); }
+    int zsmall = (cap + 1023) / 1024 * 4;  // blocks of the small-zone launch (grid-stride over zones)
+    if (zsmall > 2048) zsmall = 2048;
+    int zbig = (cap + ZONE_BIG - 1) / ZONE_BIG;
+    if (zbig > 152) zbig = 152;
     for (int round = 0; round < p.max_refine; ++round) {
-        { k_cg_fast<<<1, CG_THREADS, fast_smem, s>>>(d_k, sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n32,
-                                                    sb.vidx, sb.r64, sb.lam, sb.x32, sb.r32, sb.p32,
-                                                    sb.q32, sb.w32, sb.u32, 4 * sb.cap_k,
-                                                    p.max_cg_iters, p.inner_tol, sb.iwork,
-                                                    fast_smem); note_launch(); }
+        { k_cg_zone<256><<<zsmall, 256, zone_small_smem, s>>>(
+              sb.d_nz, sb.zs, sb.zv, ZONE_BIG, 0, sb.seg, sb.cval_s, sb.winv, sb.n32, sb.vidx, sb.r64,
+              sb.lam, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.u32, 4 * sb.cap_k, p.max_cg_iters,
+              p.inner_tol, p.rel_tol, sb.dwork + 1, sb.iwork, zone_small_smem); note_launch(); }
+        { k_cg_zone<CG_THREADS><<<zbig, CG_THREADS, fast_smem, s>>>(
+              sb.d_nz, sb.zs, sb.zv, ZONE_BIG, 1, sb.seg, sb.cval_s, sb.winv, sb.n32, sb.vidx, sb.r64,
+              sb.lam, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.u32, 4 * sb.cap_k, p.max_cg_iters,
+              p.inner_tol, p.rel_tol, sb.dwork + 1, sb.iwork, fast_smem); note_launch(); }
         { k_res_vertex<<<rb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64, sb.lam, sb.u64,
                                          sb.iwork); note_launch(); }
         { k_res_stencil<<<rb, 256, 0, s>>>(d_k, sb.vidx, sb.n64, sb.b, sb.u64, sb.r64, sb.red,

@@ -266,6 +266,10 @@ bool radix_sort_u64_dev(unsigned long long *k0, unsigned long long *k1, const in
                         int bits, SortTemp &t, cudaStream_t s) {
     return radix_sort_impl<unsigned long long, false>(k0, nullptr, k1, nullptr, cap, d_n, bits, t, s);
 }
+bool radix_sort_u64v_dev(unsigned long long *k0, int *v0, unsigned long long *k1, int *v1,
+                         const int *d_n, int cap, int bits, SortTemp &t, cudaStream_t s) {
+    return radix_sort_impl<unsigned long long, true>(k0, v0, k1, v1, cap, d_n, bits, t, s);
+}
 bool radix_sort_u32_dev(unsigned *k0, int *v0, unsigned *k1, int *v1, const int *d_n, int cap,
                         int bits, SortTemp &t, cudaStream_t s) {
     return radix_sort_impl<unsigned, true>(k0, v0, k1, v1, cap, d_n, bits, t, s);
