@@ -54,7 +54,7 @@ class hfcr_options(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int32), ("f32_filter", ctypes.c_int32),
                 ("roles", ctypes.c_int32), ("max_cg_iters", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("rel_tol", ctypes.c_double),
-                ("inner_tol", ctypes.c_double)]
+                ("inner_tol", ctypes.c_double), ("graphs", ctypes.c_int32)]
 
 
 class hfcr_solve_info(ctypes.Structure):
@@ -162,11 +162,12 @@ class Context:
 
     def __init__(self, solver: int = HFCR_SOLVER_MIXED, f32_filter: bool = True,
                  roles: int = HFCR_ROLES_ALTERNATE, max_cg_iters: int = 500, max_refine: int = 6,
-                 rel_tol: float = 1e-12, inner_tol: float = 1e-5):
+                 rel_tol: float = 1e-12, inner_tol: float = 1e-5, graphs: bool = True):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("hfcr needs a CUDA device")
-        opt = hfcr_options(solver, int(f32_filter), roles, max_cg_iters, max_refine, rel_tol, inner_tol)
+        opt = hfcr_options(solver, int(f32_filter), roles, max_cg_iters, max_refine, rel_tol, inner_tol,
+                           int(graphs))
         h = ctypes.c_void_p()
         self._check(lib().hfcr_create(ctypes.byref(h), ctypes.byref(opt)), None)
         self.handle = h

@@ -19,6 +19,16 @@ std::atomic<long long> hfcr::g_launches{0};
 struct ProfInterval {
     int stage;
     cudaEvent_t a, b;
+    bool pooled = true;  // false: the events belong to a captured graph
+};
+
+// A captured repair iteration: the exact launch sequence of one set of
+// arguments, replayed with cudaGraphLaunch.
+struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+    unsigned long long last_use = 0;
 };
 
 struct hfcr_ctx {
@@ -51,6 +61,11 @@ struct hfcr_ctx {
     long long prof_n[HFCR_N_STAGES] = {0};
     std::vector<ProfInterval> prof_pending;
     std::vector<cudaEvent_t> prof_pool;
+    // graph replay
+    std::vector<GraphEntry> graphs;
+    unsigned long long graph_clock = 0;
+    cudaStream_t own = nullptr;          // used when the caller passes the legacy default stream
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 // device counter slots
@@ -160,8 +175,10 @@ void prof_collect(hfcr_ctx *c) {
             c->prof_ms[iv.stage] += ms;
             c->prof_n[iv.stage] += 1;
         }
-        c->prof_pool.push_back(iv.a);
-        c->prof_pool.push_back(iv.b);
+        if (iv.pooled) {
+            c->prof_pool.push_back(iv.a);
+            c->prof_pool.push_back(iv.b);
+        }
     }
     c->prof_pending.swap(keep);
 }
@@ -410,6 +427,92 @@ hfcr_status read_iteration(hfcr_ctx *ctx, cudaStream_t s) {
     return read_back(ctx, s);
 }
 
+hfcr_status reset_words(hfcr_ctx *ctx, cudaStream_t s);
+
+void clear_graphs(hfcr_ctx *c) {
+    for (auto &g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
+template <typename T>
+void key_add(std::string &k, const T &v) {
+    k.append(reinterpret_cast<const char *>(&v), sizeof(T));
+}
+
+// Resets the per-iteration words and enqueues one repair iteration,
+// directly or through a cached CUDA graph of the same arguments.
+hfcr_status run_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d0, bool d1,
+                          const DetectPlan &pl, bool *built, double d, cudaStream_t s) {
+    auto body = [&]() -> hfcr_status {
+        hfcr_status st = reset_words(ctx, s);
+        if (st) return st;
+        CK(cudaMemsetAsync(ctx->sb.iwork, 0, sizeof(int) * 16, s));
+        CK(cudaMemsetAsync(ctx->sb.dwork, 0, sizeof(double) * 2, s));
+        CK(cudaMemsetAsync(ctx->sb.d_U, 0, sizeof(int), s));
+        enqueue_iteration(ctx, A, B, d0, d1, pl, built, d, s);
+        return HFCR_OK;
+    };
+    if (!ctx->opt.graphs || ctx->prof_on || !s) return body();
+    std::string key;
+    key_add(key, *A);
+    key_add(key, *B);
+    key_add(key, d);
+    key_add(key, d0);
+    key_add(key, d1);
+    key_add(key, built[0]);
+    key_add(key, built[1]);
+    key_add(key, ctx->opt);
+    key_add(key, ctx->max_pairs);
+    key_add(key, pl.edges[0]);
+    key_add(key, pl.edges[1]);
+    key_add(key, pl.ne[0]);
+    key_add(key, pl.ne[1]);
+    key_add(key, s);
+    GraphEntry *g = nullptr;
+    for (auto &e : ctx->graphs)
+        if (e.key == key) g = &e;
+    if (!g) {
+        if (ctx->graphs.size() >= 8) {  // evict the least recently used
+            size_t lru = 0;
+            for (size_t i = 1; i < ctx->graphs.size(); ++i)
+                if (ctx->graphs[i].last_use < ctx->graphs[lru].last_use) lru = i;
+            cudaGraphExecDestroy(ctx->graphs[lru].exec);
+            ctx->graphs.erase(ctx->graphs.begin() + lru);
+        }
+        long long l0 = g_launches.load();
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        hfcr_status st = body();
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (st) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess)
+            return fail(ctx, HFCR_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+        GraphEntry ne;
+        ne.key = key;
+        e = cudaGraphInstantiate(&ne.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess)
+            return fail(ctx, HFCR_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        ne.launches = g_launches.load() - l0;
+        g_launches.fetch_sub(ne.launches);  // counted when replayed
+        ctx->graphs.push_back(ne);
+        g = &ctx->graphs.back();
+    } else {
+        // the captured sequence builds exactly the hierarchies the body would
+        for (int dd = 0; dd < 2; ++dd)
+            if ((dd == 0 ? d0 : d1) && (dd == 0 ? B : A)->n_tris > 0 && pl.ne[dd] > 0)
+                built[dd] = true;
+    }
+    g->last_use = ++ctx->graph_clock;
+    CK(cudaGraphLaunch(g->exec, s));
+    g_launches.fetch_add(g->launches);
+    return HFCR_OK;
+}
+
 hfcr_status solve_info(hfcr_ctx *ctx, int k, hfcr_solve_info *info, cudaStream_t s) {
     int iw[16] = {0};
     double dw[1] = {0};
@@ -450,6 +553,7 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
     c->opt.max_refine = 6;
     c->opt.rel_tol = 1e-12;
     c->opt.inner_tol = 1e-5;
+    c->opt.graphs = 1;
     if (opt) {
         c->opt = *opt;
         if (c->opt.max_cg_iters <= 0) c->opt.max_cg_iters = 500;
@@ -472,6 +576,10 @@ hfcr_status hfcr_destroy(hfcr_ctx *ctx) {
         if (iv.b) cudaEventDestroy(iv.b);
     }
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    clear_graphs(ctx);
+    if (ctx->own) cudaStreamDestroy(ctx->own);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     free_all(ctx);
     delete ctx;
     return HFCR_OK;
@@ -488,7 +596,9 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     if (max_tris < ctx->max_tris) max_tris = ctx->max_tris;
     if (max_pairs < ctx->max_pairs) max_pairs = ctx->max_pairs;
     CK(cudaDeviceSynchronize());
+    clear_graphs(ctx);
     free_all(ctx);
+    solver_init();
     if (max_tris < 1) max_tris = 1;
     if (max_pairs < 1) max_pairs = 1;
     const size_t T = (size_t)max_tris, P = (size_t)max_pairs, E3 = 3 * T;
@@ -698,7 +808,19 @@ hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, in
     hfcr_status st = check_pair(ctx, A, B);
     if (st) return st;
     if (max_iters < 0 || !(d == d)) return fail(ctx, HFCR_ERR_ARG, "hfcr_resolve: bad arguments");
-    cudaStream_t s = (cudaStream_t)stream;
+    cudaStream_t user = (cudaStream_t)stream, s = user;
+    if (!user && ctx->opt.graphs && !ctx->prof_on) {
+        // the legacy default stream cannot be captured: work on an own
+        // stream ordered after everything the caller queued before
+        if (!ctx->own) {
+            CK(cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
+        }
+        CK(cudaEventRecord(ctx->ev_in, user));
+        CK(cudaStreamWaitEvent(ctx->own, ctx->ev_in, 0));
+        s = ctx->own;
+    }
     hfcr_resolve_info loc;
     memset(&loc, 0, sizeof loc);
     const bool has0 = B->oriented != 0, has1 = A->oriented != 0;
@@ -713,11 +835,7 @@ hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, in
     for (int it = 0; it < max_iters; ++it) {
         bool d0 = has0, d1 = has1;
         if (alternate) { d0 = (it % 2) == 0; d1 = !d0; }
-        if ((st = reset_words(ctx, s))) return st;
-        CK(cudaMemsetAsync(ctx->sb.iwork, 0, sizeof(int) * 16, s));
-        CK(cudaMemsetAsync(ctx->sb.dwork, 0, sizeof(double), s));
-        CK(cudaMemsetAsync(ctx->sb.d_U, 0, sizeof(int), s));
-        enqueue_iteration(ctx, A, B, d0, d1, pl, built, d, s);
+        if ((st = run_iteration(ctx, A, B, d0, d1, pl, built, d, s))) return st;
         CK(cudaGetLastError());
         st = read_iteration(ctx, s);
         int P = ctx->h_cnt[C_PAIRS];
@@ -744,6 +862,10 @@ hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, in
     }
     if (info) *info = loc;
     CK(cudaStreamSynchronize(s));
+    if (s != user) {
+        CK(cudaEventRecord(ctx->ev_out, s));
+        CK(cudaStreamWaitEvent(user, ctx->ev_out, 0));
+    }
     if (!loc.converged) return fail(ctx, HFCR_ERR_NOT_CONVERGED, "repair loop stopped after %d detections", loc.iters);
     return HFCR_OK;
 }

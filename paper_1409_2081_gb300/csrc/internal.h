@@ -183,6 +183,8 @@ void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int ca
 // d_n4: device word receiving 4k (the CSR entry count)
 void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers &sb, SortTemp &t,
                       int *d_n4, uint32_t *d_status, cudaStream_t s);
+// One-time kernel attributes (shared-memory opt-in); call outside stream capture.
+void solver_init();
 // Solves and leaves lambda in sb.lam; results (iters, residual) in sb.iwork / sb.dwork.
 void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint32_t *d_status,
            cudaStream_t s);

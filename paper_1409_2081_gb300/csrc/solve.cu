@@ -427,32 +427,35 @@ __global__ void k_uf_union(const int *d_U, const int *seg, const int *cval, int 
     }
 }
 
-__global__ void k_zone_keys(const int *d_k, int *parent, int kb, unsigned long long *zkey) {
+// zone label of every stencil (its root = the smallest stencil of its zone)
+__global__ void k_zone_keys(const int *d_k, int *parent, unsigned *zlab, int *zsrc) {
     const int k = *d_k;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
-        zkey[i] = ((unsigned long long)uf_find(parent, i) << kb) | (unsigned)i;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+        zlab[i] = (unsigned)uf_find(parent, i);
+        zsrc[i] = i;
+    }
 }
 
-__global__ void k_zone_flags(const int *d_k, const unsigned long long *zkey, int kb,
-                             unsigned *flags) {
+__global__ void k_zone_flags(const int *d_k, const unsigned *zlab, unsigned *flags) {
     const int k = *d_k;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x)
-        flags[t] = (t == 0 || (zkey[t] >> kb) != (zkey[t - 1] >> kb)) ? 1u : 0u;
+        flags[t] = (t == 0 || zlab[t] != zlab[t - 1]) ? 1u : 0u;
 }
 
-// regroups the rows zone by zone (zone order = order of the smallest stencil)
-__global__ void k_zone_gather(const int *d_k, const unsigned long long *zkey, int kb,
+// regroups the rows zone by zone (zones in the order of their smallest
+// stencil, stencils ascending inside a zone: the label sort is stable)
+__global__ void k_zone_gather(const int *d_k, const unsigned *zlab, const int *zsrc,
                               const unsigned *excl, const int4 *ids_raw,
                               const double4_32a *n64_raw, const float4 *n32_raw,
                               const double *b_raw, int4 *ids, double4_32a *n64, float4 *n32,
-                              double *b, int *szone, int *zs) {
+                              double *b, int *szone, int *zs, int *pos_of) {
     const int k = *d_k;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
-        unsigned long long key = zkey[t];
-        int src = (int)(key & ((1ull << kb) - 1));
-        unsigned f = (t == 0 || (key >> kb) != (zkey[t - 1] >> kb)) ? 1u : 0u;
+        int src = zsrc[t];
+        unsigned f = (t == 0 || zlab[t] != zlab[t - 1]) ? 1u : 0u;
         int z = (int)(excl[t] + f) - 1;
         szone[t] = z;
+        pos_of[src] = t;
         if (f) zs[z] = t;
         if (t == k - 1) zs[z + 1] = k;
         ids[t] = ids_raw[src];
@@ -462,43 +465,46 @@ __global__ void k_zone_gather(const int *d_k, const unsigned long long *zkey, in
     }
 }
 
-// CSR entries keyed (zone, vertex): vertices come out grouped by zone
-__global__ void k_csr2_entries(const int4 *ids, const int *szone, const int *d_k, int cap, int vb,
-                               unsigned long long *key, int *val) {
+// Zone-ordered CSR: the vertex-ordered entries (s * 4 + role) are re-sorted
+// stably by the zone of their stencil, so vertices come out grouped by zone
+// (vertex order kept inside a zone) and entries renumbered to zone order.
+__global__ void k_csr2_entries(const int *cv1, const int *pos_of, const int *szone,
+                               const int *d_k, int cap, unsigned *key, int *val) {
     int k = min(*d_k, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 4 * k) return;
-    int t = i >> 2, role = i & 3;
-    key[i] = ((unsigned long long)szone[t] << vb) | (unsigned)((const int *)ids)[4 * t + role];
-    val[i] = i;
+    int e = cv1[i];
+    int t = pos_of[e >> 2];
+    key[i] = (unsigned)szone[t];
+    val[i] = 4 * t + (e & 3);
 }
 
-__global__ void k_csr2_flags(const unsigned long long *key, const int *d_k, int cap,
+__global__ void k_csr2_flags(const int *val, const int4 *ids, const int *d_k, int cap,
                              unsigned *flag) {
     int n = 4 * min(*d_k, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
+    if (i < n)
+        flag[i] = (i == 0 || ((const int *)ids)[val[i]] != ((const int *)ids)[val[i - 1]]) ? 1u : 0u;
 }
 
-__global__ void k_csr2_build(const unsigned long long *key, const int *val, const unsigned *excl,
-                             const int *d_k, int cap, int vb, int nA, const float *wA,
+__global__ void k_csr2_build(const unsigned *zkey, const int *val, const unsigned *excl,
+                             const int4 *ids, const int *d_k, int cap, int nA, const float *wA,
                              const float *wB, int4 *vidx, int *seg, int *gvert, float *winv,
                              int *zv, const int *d_nz) {
     int n = 4 * min(*d_k, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    unsigned long long kk = key[i];
-    unsigned f = (i == 0 || kk != key[i - 1]) ? 1u : 0u;
+    const int g = ((const int *)ids)[val[i]];
+    unsigned f = (i == 0 || g != ((const int *)ids)[val[i - 1]]) ? 1u : 0u;
     int j = (int)(excl[i] + f) - 1;
     ((int *)vidx)[val[i]] = j;
     if (f) {
-        int g = (int)(kk & ((1ull << vb) - 1));
         seg[j] = i;
         gvert[j] = g;
         const float *w = g < nA ? wA : wB;
         int lv = g < nA ? g : g - nA;
         winv[j] = w ? w[lv] : 1.0f;
-        if (i == 0 || (kk >> vb) != (key[i - 1] >> vb)) zv[(int)(kk >> vb)] = j;
+        if (i == 0 || zkey[i] != zkey[i - 1]) zv[zkey[i]] = j;
     }
     if (i == n - 1) {
         seg[j + 1] = n;
@@ -589,9 +595,13 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
     }
 }
 
-// ||b||^2 partials and r = b, lam = 0 (the first residual of the mixed solver)
-__global__ void k_init_res(const int *d_k, const double *b, double *lam, double *r, double *red) {
+// r = b, lam = 0 (the first residual of the mixed solver); the last block
+// (ticket counter) sums the |b|^2 partials in block order into dres[1],
+// records |r| / |b| = 1 in dres[0] and sets ctl[0] when b = 0.
+__global__ void k_init_res(const int *d_k, const double *b, double *lam, double *r, double *red,
+                           int *ctl, unsigned *ticket, double *dres) {
     __shared__ double sh[33];
+    __shared__ bool last;
     const int k = *d_k;
     double bb = 0.0;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < k; s += gridDim.x * blockDim.x) {
@@ -601,9 +611,19 @@ __global__ void k_init_res(const int *d_k, const double *b, double *lam, double 
     }
     bb = block_sum(bb, sh);
     if (threadIdx.x == 0) {
-        red[blockIdx.x] = bb;
         red[RES_BLOCKS + blockIdx.x] = bb;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double Bn = 0;
+    for (int i = 0; i < (int)gridDim.x; ++i) Bn += __ldcg(red + RES_BLOCKS + i);
+    dres[0] = Bn > 0 ? 1.0 : 0.0;
+    dres[1] = Bn;
+    if (!(Bn > 0)) ctl[0] = 1;
+    *ticket = 0;
 }
 
 // float64 residual, vertex half: u = M^-1 J^T lam
@@ -631,11 +651,16 @@ __global__ void k_res_vertex(const int *d_U, const int *seg, const int *cval, co
 }
 
 // float64 residual, stencil half: r = b - J u; per-block partial sums of
-// r^2 and b^2 to red[blk] and red[RES_BLOCKS + blk]
+// r^2 and b^2 to red[blk] and red[RES_BLOCKS + blk].  The last block to
+// finish (ticket counter) adds the partials in block order, records
+// |r| / |b| in dres[0] and |b|^2 in dres[1], and sets ctl[0] when the
+// relative residual meets rel_tol.
 __global__ void k_res_stencil(const int *d_k, const int4 *vidx, const double4_32a *n64,
                               const double *b, const double *u, double *r, double *red,
-                              const int *ctl) {
+                              int *ctl, unsigned *ticket, double rel_tol, double *dres,
+                              int count_round) {
     __shared__ double sh[33];
+    __shared__ bool last;
     if (ctl[0]) return;
     const int k = *d_k;
     const double third = 1.0 / 3.0;
@@ -656,24 +681,23 @@ __global__ void k_res_stencil(const int *d_k, const int4 *vidx, const double4_32
     if (threadIdx.x == 0) {
         red[blockIdx.x] = rr;
         red[RES_BLOCKS + blockIdx.x] = bb;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
-}
-
-// Sums the partials in a fixed order, records |r|/|b| and sets the done
-// flag when it meets rel_tol.  ctl[0] done, ctl[3] refinement rounds.
-__global__ void k_res_check(const double *red, int nblk, double rel_tol, int *ctl, double *dres,
-                            int count_round) {
-    if (threadIdx.x != 0 || ctl[0]) return;
-    double rr = 0, bb = 0;
-    for (int i = 0; i < nblk; ++i) {
-        rr += red[i];
-        bb += red[RES_BLOCKS + i];
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double R = 0, Bn = 0;
+    for (int i = 0; i < (int)gridDim.x; ++i) {
+        R += __ldcg(red + i);
+        Bn += __ldcg(red + RES_BLOCKS + i);
     }
-    double rel = bb > 0 ? sqrt(rr / bb) : 0.0;
+    double rel = Bn > 0 ? sqrt(R / Bn) : 0.0;
     dres[0] = rel;
-    dres[1] = bb;
+    dres[1] = Bn;
     if (rel <= rel_tol) ctl[0] = 1;
     if (count_round) ctl[3] += 1;
+    *ticket = 0;
 }
 
 __global__ void k_init_lam(const int *d_k, const double *b, double *lam, double *r) {
@@ -738,6 +762,20 @@ void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int ca
                                                  sb.n64_raw, sb.n32_raw, sb.b_raw, d_status); note_launch(); }
 }
 
+// dynamic shared memory granted to the zone CG kernels (0: the global-memory
+// path runs); set once per process, outside any stream capture
+static int g_fast_smem = -1, g_zone_small_smem = 0;
+
+void solver_init() {
+    if (g_fast_smem >= 0) return;
+    g_fast_smem = cudaFuncSetAttribute(k_cg_zone<CG_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       FAST_SMEM) == cudaSuccess ? FAST_SMEM : 0;
+    if (!g_fast_smem) cudaGetLastError();
+    g_zone_small_smem = cudaFuncSetAttribute(k_cg_zone<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             ZONE_SMALL_SMEM) == cudaSuccess ? ZONE_SMALL_SMEM : 0;
+    if (!g_zone_small_smem) cudaGetLastError();
+}
+
 void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers &sb, SortTemp &t,
                       int *d_n4, uint32_t *d_status, cudaStream_t s) {
     if (cap <= 0) return;
@@ -756,26 +794,34 @@ void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers 
     scan_flags_dev(sb.cflag, d_n4, n4, sb.d_U, s);
     { k_csr_build<<<nb, 256, 0, s>>>(ck1, cv1, sb.cflag, d_k, cap, mp.A.n_verts, mp.A.inv_mass,
                                    mp.B.inv_mass, sb.vidx, sb.seg, sb.gvert, sb.winv); note_launch(); }
-    // impact zones and the zone-ordered rows
+    // impact zones and the zone-ordered rows.  The 64-bit scratch arrays
+    // are used as pairs of 32-bit arrays: (label, stencil) for the zone sort,
+    // (zone, entry) for the zone-ordered CSR.
     int kb = bits_for((long long)cap + 1);
+    unsigned *zlab = (unsigned *)sb.zkey, *zlab_alt = (unsigned *)sb.zkey_alt;
+    int *zsrc = (int *)sb.zkey + cap, *zsrc_alt = (int *)sb.zkey_alt + cap;
     { k_uf_init<<<gb, 256, 0, s>>>(d_k, sb.parent); note_launch(); }
     { k_uf_union<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(sb.d_U, sb.seg, cv1, sb.parent, d_status); note_launch(); }
-    { k_zone_keys<<<gb, 256, 0, s>>>(d_k, sb.parent, kb, sb.zkey); note_launch(); }
-    bool zflip = radix_sort_u64_dev(sb.zkey, sb.zkey_alt, d_k, cap, 2 * kb, t, s);
-    unsigned long long *zk = zflip ? sb.zkey_alt : sb.zkey;
-    { k_zone_flags<<<gb, 256, 0, s>>>(d_k, zk, kb, sb.cflag); note_launch(); }
+    { k_zone_keys<<<gb, 256, 0, s>>>(d_k, sb.parent, zlab, zsrc); note_launch(); }
+    bool zflip = radix_sort_u32_dev(zlab, zsrc, zlab_alt, zsrc_alt, d_k, cap, kb, t, s);
+    unsigned *zl = zflip ? zlab_alt : zlab;
+    int *zr = zflip ? zsrc_alt : zsrc;
+    { k_zone_flags<<<gb, 256, 0, s>>>(d_k, zl, sb.cflag); note_launch(); }
     scan_flags_dev(sb.cflag, d_k, cap, sb.d_nz, s);
-    { k_zone_gather<<<gb, 256, 0, s>>>(d_k, zk, kb, sb.cflag, sb.ids_raw, sb.n64_raw, sb.n32_raw,
-                                     sb.b_raw, sb.ids, sb.n64, sb.n32, sb.b, sb.szone, sb.zs); note_launch(); }
-    // vertex -> stencils again, keyed (zone, vertex): zone-contiguous numbering
-    int zb = bits_for((long long)cap + 1);
-    { k_csr2_entries<<<nb, 256, 0, s>>>(sb.ids, sb.szone, d_k, cap, vb, sb.ck64, sb.cval); note_launch(); }
-    bool flip2 = radix_sort_u64v_dev(sb.ck64, sb.cval, sb.ck64_alt, sb.cval_alt, d_n4, n4, zb + vb, t, s);
-    unsigned long long *ck2 = flip2 ? sb.ck64_alt : sb.ck64;
-    sb.cval_s = flip2 ? sb.cval_alt : sb.cval;
-    { k_csr2_flags<<<nb, 256, 0, s>>>(ck2, d_k, cap, sb.cflag); note_launch(); }
+    int *pos_of = sb.parent;  // the forest is no longer needed
+    { k_zone_gather<<<gb, 256, 0, s>>>(d_k, zl, zr, sb.cflag, sb.ids_raw, sb.n64_raw, sb.n32_raw,
+                                     sb.b_raw, sb.ids, sb.n64, sb.n32, sb.b, sb.szone, sb.zs,
+                                     pos_of); note_launch(); }
+    // vertex-ordered entries re-sorted stably by zone: zone-contiguous numbering
+    unsigned *k2 = (unsigned *)sb.ck64, *k2_alt = (unsigned *)sb.ck64_alt;
+    int *v2 = (int *)sb.ck64 + n4, *v2_alt = (int *)sb.ck64_alt + n4;
+    { k_csr2_entries<<<nb, 256, 0, s>>>(cv1, pos_of, sb.szone, d_k, cap, k2, v2); note_launch(); }
+    bool flip2 = radix_sort_u32_dev(k2, v2, k2_alt, v2_alt, d_n4, n4, kb, t, s);
+    unsigned *zk2 = flip2 ? k2_alt : k2;
+    sb.cval_s = flip2 ? v2_alt : v2;
+    { k_csr2_flags<<<nb, 256, 0, s>>>(sb.cval_s, sb.ids, d_k, cap, sb.cflag); note_launch(); }
     scan_flags_dev(sb.cflag, d_n4, n4, sb.d_U, s);
-    { k_csr2_build<<<nb, 256, 0, s>>>(ck2, sb.cval_s, sb.cflag, d_k, cap, vb, mp.A.n_verts,
+    { k_csr2_build<<<nb, 256, 0, s>>>(zk2, sb.cval_s, sb.cflag, sb.ids, d_k, cap, mp.A.n_verts,
                                     mp.A.inv_mass, mp.B.inv_mass, sb.vidx, sb.seg, sb.gvert, sb.winv,
                                     sb.zv, sb.d_nz); note_launch(); }
 }
@@ -784,16 +830,8 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
            cudaStream_t s) {
     (void)d_status;
     if (cap <= 0) return;
-    // dynamic shared memory granted to the fast CG kernel (0 until set)
-    static int fast_smem = -1, zone_small_smem = 0;
-    if (fast_smem < 0) {
-        fast_smem = cudaFuncSetAttribute(k_cg_zone<CG_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         FAST_SMEM) == cudaSuccess ? FAST_SMEM : 0;
-        if (!fast_smem) cudaGetLastError();  // refused: the global-memory path runs
-        zone_small_smem = cudaFuncSetAttribute(k_cg_zone<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               ZONE_SMALL_SMEM) == cudaSuccess ? ZONE_SMALL_SMEM : 0;
-        if (!zone_small_smem) cudaGetLastError();
-    }
+    solver_init();
+    const int fast_smem = g_fast_smem, zone_small_smem = g_zone_small_smem;
     int rb = (cap + 255) / 256;
     if (rb > RES_BLOCKS) rb = RES_BLOCKS;
     cudaMemsetAsync(sb.iwork, 0, sizeof(int) * 16, s);
@@ -807,13 +845,13 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
         { k_res_vertex<<<rb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64, sb.lam, sb.u64,
                                          sb.iwork); note_launch(); }
         { k_res_stencil<<<rb, 256, 0, s>>>(d_k, sb.vidx, sb.n64, sb.b, sb.u64, sb.r64, sb.red,
-                                          sb.iwork); note_launch(); }
-        { k_res_check<<<1, 32, 0, s>>>(sb.red, rb, p.rel_tol, sb.iwork, sb.dwork, 0); note_launch(); }
+                                          sb.iwork, (unsigned *)(sb.iwork + 12), p.rel_tol,
+                                          sb.dwork, 0); note_launch(); }
         return;
     }
     // MIXED: float32 runs per impact zone on the float64 residual (r = b to start)
-    { k_init_res<<<rb, 256, 0, s>>>(d_k, sb.b, sb.lam, sb.r64, sb.red); note_launch(); }
-    { k_res_check<<<1, 32, 0, s>>>(sb.red, rb, p.rel_tol, sb.iwork, sb.dwork, 0); note_launch(); }
+    { k_init_res<<<rb, 256, 0, s>>>(d_k, sb.b, sb.lam, sb.r64, sb.red, sb.iwork,
+                                   (unsigned *)(sb.iwork + 12), sb.dwork); note_launch(); }
     int zsmall = (cap + 1023) / 1024 * 4;  // blocks of the small-zone launch (grid-stride over zones)
     if (zsmall > 2048) zsmall = 2048;
     int zbig = (cap + ZONE_BIG - 1) / ZONE_BIG;
@@ -830,8 +868,8 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
         { k_res_vertex<<<rb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64, sb.lam, sb.u64,
                                          sb.iwork); note_launch(); }
         { k_res_stencil<<<rb, 256, 0, s>>>(d_k, sb.vidx, sb.n64, sb.b, sb.u64, sb.r64, sb.red,
-                                          sb.iwork); note_launch(); }
-        { k_res_check<<<1, 32, 0, s>>>(sb.red, rb, p.rel_tol, sb.iwork, sb.dwork, 1); note_launch(); }
+                                          sb.iwork, (unsigned *)(sb.iwork + 12), p.rel_tol,
+                                          sb.dwork, 1); note_launch(); }
     }
 }
 

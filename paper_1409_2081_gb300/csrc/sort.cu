@@ -74,44 +74,51 @@ __global__ void __launch_bounds__(TPB) k_hist(const K *keys, int n, const int *d
     hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of a[0..m) in place by one CTA of 1024 threads; total to *d_total
+// exclusive scan of a[0..m) in place by one CTA of 1024 threads; total to
+// *d_total.  Tiles of 4096: each thread loads 4 consecutive elements
+// (coalesced across the warp), the CTA scans the per-thread sums, and a
+// running carry links the tiles.
 __global__ void __launch_bounds__(1024) k_scan1(unsigned *a, int m, const int *d_m, int *d_total,
                                                const int *d_gate = nullptr) {
     if (d_gate && *d_gate <= SMALL_N) return;  // histogram scan of a sort the single CTA handled
     if (d_m) m = min(m, *d_m);
     __shared__ unsigned ws[32];
-    const int t = threadIdx.x;
-    int chunk = (m + 1023) / 1024;
-    int beg = min(m, t * chunk), end = min(m, beg + chunk);
-    unsigned sum = 0;
-    for (int i = beg; i < end; ++i) sum += a[i];
-    // block exclusive scan of per-thread sums
-    unsigned v = sum;
-    const int lane = t & 31, w = t >> 5;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    unsigned carry = 0;
+    for (int base = 0; base < m; base += 4096) {
+        const int i0 = base + 4 * t;
+        unsigned v[4];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-    }
-    if (lane == 31) ws[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        unsigned x = ws[lane];
+        for (int q = 0; q < 4; ++q) v[q] = i0 + q < m ? a[i0 + q] : 0u;
+        const unsigned sum = v[0] + v[1] + v[2] + v[3];
+        unsigned x = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             unsigned y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        ws[lane] = x;
+        if (lane == 31) ws[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            unsigned y = ws[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned z = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += z;
+            }
+            ws[lane] = y;
+        }
+        __syncthreads();
+        unsigned e = carry + x - sum + (w ? ws[w - 1] : 0u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (i0 + q < m) a[i0 + q] = e;
+            e += v[q];
+        }
+        carry += ws[31];
+        __syncthreads();  // ws is rewritten by the next tile
     }
-    __syncthreads();
-    unsigned excl = v - sum + (w ? ws[w - 1] : 0u);
-    for (int i = beg; i < end; ++i) {
-        unsigned x = a[i];
-        a[i] = excl;
-        excl += x;
-    }
-    if (t == 1023 && d_total) *d_total = (int)(ws[31]);
+    if (t == 0 && d_total) *d_total = (int)carry;
 }
 
 template <typename K, bool HV>
