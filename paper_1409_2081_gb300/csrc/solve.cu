@@ -546,9 +546,14 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
         __syncthreads();
         if (rzs <= 0.5 * zone_tol2) continue;
         const int e0 = seg_g[j0];
-        CgView v;
         const long long need = 64ll * k + 20ll * U + 16;
-        if (need <= smem_bytes) {
+        const bool in_smem = need <= smem_bytes;
+        int it;
+        // the two paths are instantiated separately so that the shared-memory
+        // one sees pointers derived only from the shared array (LDS/STS, not
+        // generic loads)
+        if (in_smem) {
+            CgView v;
             char *base = (char *)smem4;
             int4 *vidx = (int4 *)base;
             float *f = (float *)(vidx + k);
@@ -570,26 +575,36 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
             v.nx = nx; v.ny = ny; v.nz = nz_; v.n4 = nullptr;
             v.vidx = vidx; v.seg = seg; v.cval = cval; v.winv = winv;
             v.voff = 0; v.coff = 0; v.eoff = 0;
+            for (int t = tid; t < k; t += nt) {
+                v.r[t] = (float)rhs64[s0 + t];
+                v.p[t] = 0.f;
+                v.sv[t] = 0.f;
+                v.x[t] = 0.f;
+            }
+            __syncthreads();
+            it = cg_cg_loop(v, k, U, maxit, (float)tol, red);
+            for (int t = tid; t < k; t += nt) lam[s0 + t] += (double)v.x[t];
         } else {
+            CgView v;
             v.r = r_g + s0; v.p = p_g + s0; v.x = x_g + s0; v.sv = s_g + s0; v.w = w_g + s0;
             v.ux = u_g + j0; v.uy = u_g + cap4 + j0; v.uz = u_g + 2 * cap4 + j0;
             v.nx = v.ny = v.nz = nullptr; v.n4 = n32 + s0;
             v.vidx = vidx_g + s0; v.seg = seg_g + j0; v.cval = cval_g; v.winv = winv_g + j0;
             v.voff = j0; v.coff = 4 * s0; v.eoff = 0;
+            for (int t = tid; t < k; t += nt) {
+                v.r[t] = (float)rhs64[s0 + t];
+                v.p[t] = 0.f;
+                v.sv[t] = 0.f;
+                v.x[t] = 0.f;
+            }
+            __syncthreads();
+            it = cg_cg_loop(v, k, U, maxit, (float)tol, red);
+            for (int t = tid; t < k; t += nt) lam[s0 + t] += (double)v.x[t];
         }
-        for (int t = tid; t < k; t += nt) {
-            v.r[t] = (float)rhs64[s0 + t];
-            v.p[t] = 0.f;
-            v.sv[t] = 0.f;
-            v.x[t] = 0.f;
-        }
-        __syncthreads();
-        int it = cg_cg_loop(v, k, U, maxit, (float)tol, red);
-        for (int t = tid; t < k; t += nt) lam[s0 + t] += (double)v.x[t];
         if (tid == 0) {
             atomicAdd(&ctl[1], it);
             atomicAdd(&ctl[2], 1);
-            atomicOr(&ctl[4], need <= smem_bytes ? 1 : 2);
+            atomicOr(&ctl[4], in_smem ? 1 : 2);
         }
         __syncthreads();  // shared memory is reused by the next zone
     }
