@@ -181,6 +181,30 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
 hfcr_status hfcr_build_edges(hfcr_ctx *ctx, const int32_t *tris, int32_t n_tris, int32_t n_verts,
                              int32_t *out, int64_t cap, int64_t *n_out, void *stream);
 
+/* hfcr_build_edges for callers that cannot allocate device memory: the
+ * same sorted unique edges, computed without a context and without any
+ * cudaMalloc, cudaFree or other allocating call.  The paper has no
+ * counterpart; this exists for code that may not allocate on the device
+ * while it runs - for example a host application whose device memory is
+ * owned by its own pool or budget, a plugin that is given device buffers
+ * but no right to allocate, or a latency-critical loop that cannot afford
+ * cudaMalloc's implicit synchronisation.
+ *
+ * Its scratch is one fixed device array inside the library (about 3.9 MB,
+ * enough for n_tris <= 65,536), which every GPU that loads the library
+ * holds until the process exits.  Larger inputs return HFCR_ERR_CAPACITY
+ * (message in hfcr_last_error(NULL)), as does cap < 3 * n_tris: out must
+ * have room for the largest possible edge count.  The first call on a
+ * device looks up that device's address of the array (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (different streams, or different
+ * host threads) race and give undefined results; calls in sequence are
+ * fine, since each call clears the words it needs cleared.
+ * tris, out: device; *n_out (host) gets the edge count.  Synchronises
+ * `stream`. */
+hfcr_status hfcr_build_edges_noalloc(const int32_t *tris, int32_t n_tris, int32_t n_verts,
+                                     int32_t *out, int64_t cap, int64_t *n_out, void *stream);
+
 /* Exact discrete collision detection (Sec. 3): every E-F pair of the
  * active directions (0 when B is oriented, 1 when A is), sorted by
  * (dir, v0, v1, face).  out: device [cap]; *n_out (host) gets the pair
@@ -226,7 +250,8 @@ hfcr_status hfcr_profile_read(hfcr_ctx *ctx, hfcr_profile *out);
  * (instrumentation, no counterpart in the paper). */
 int64_t hfcr_launch_count(void);
 
-/* Message of the last failing call on this context ("" if none). */
+/* Message of the last failing call on this context ("" if none); with
+ * ctx == NULL, of the last failing context-free call of this thread. */
 const char *hfcr_last_error(const hfcr_ctx *ctx);
 
 /* Static name of a status code. */

@@ -93,6 +93,9 @@ _SIGS = {
     "hfcr_build_edges": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                           ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                           ctypes.c_void_p], ctypes.c_int),
+    "hfcr_build_edges_noalloc": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                  ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p],
+                                 ctypes.c_int),
     "hfcr_detect": ([ctypes.c_void_p, ctypes.POINTER(hfcr_mesh), ctypes.POINTER(hfcr_mesh),
                      ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                      ctypes.POINTER(hfcr_detect_stats), ctypes.c_void_p], ctypes.c_int),
@@ -140,6 +143,18 @@ class HfcrError(RuntimeError):
 
 def hfcr_launch_count() -> int:
     return int(lib().hfcr_launch_count())
+
+
+def hfcr_build_edges_noalloc(tris, n_verts: int, out, stream=None) -> int:
+    """hfcr_build_edges without a context or any device allocation (fixed
+    scratch inside the library, n_tris <= 65,536; out must hold 3 * n_tris
+    edges)."""
+    n = ctypes.c_int64()
+    st = lib().hfcr_build_edges_noalloc(_ptr(tris), int(tris.shape[0]), n_verts, _ptr(out),
+                                        int(out.shape[0]), ctypes.byref(n), _stream_ptr(stream))
+    if st != HFCR_OK:
+        raise HfcrError(st, (lib().hfcr_last_error(None) or b"").decode())
+    return int(n.value)
 
 
 def status_string(s: int) -> str:

@@ -16,6 +16,12 @@ using namespace hfcr;
 
 std::atomic<long long> hfcr::g_launches{0};
 
+namespace hfcr {
+// message of the last failing context-free call of this thread
+static thread_local std::string g_noctx_err;
+void set_noctx_error(const std::string &msg) { g_noctx_err = msg; }
+}  // namespace hfcr
+
 struct ProfInterval {
     int stage;
     cudaEvent_t a, b;
@@ -893,7 +899,9 @@ hfcr_status hfcr_profile_read(hfcr_ctx *ctx, hfcr_profile *out) {
 
 int64_t hfcr_launch_count(void) { return (int64_t)g_launches.load(); }
 
-const char *hfcr_last_error(const hfcr_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+const char *hfcr_last_error(const hfcr_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : hfcr::g_noctx_err.c_str();
+}
 
 const char *hfcr_status_string(hfcr_status s) {
     switch (s) {
