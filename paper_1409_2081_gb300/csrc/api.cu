@@ -682,7 +682,7 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(dalloc(&sb.gvert, 4 * P));
     CK(dalloc(&sb.winv, 4 * P));
     CK(dalloc(&sb.u64, 12 * P));
-    CK(dalloc(&sb.u32, 12 * P));
+    CK(dalloc(&sb.u32, 16 * P));
     CK(dalloc(&sb.red, 1024));
     CK(dalloc(&sb.d_U, 1));
     CK(dalloc(&sb.iwork, 16));

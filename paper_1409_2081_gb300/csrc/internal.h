@@ -163,7 +163,7 @@ struct SolveBuffers {
     int *gvert = nullptr;        // [4 cap_k]
     float *winv = nullptr;       // [4 cap_k]
     double *u64 = nullptr;       // [3 * 4 cap_k]
-    float *u32 = nullptr;        // [3 * 4 cap_k]
+    float *u32 = nullptr;        // [4 * 4 cap_k] (float4 per touched vertex)
     double *red = nullptr;       // reduction partials [1024]
     int *d_U = nullptr;          // touched vertex count (device)
     int *iwork = nullptr;        // [16] solver control words

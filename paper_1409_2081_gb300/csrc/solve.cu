@@ -249,16 +249,14 @@ constexpr int ZONE_BIG = 1024;  // zones with at least this many stencils get a 
 
 struct CgView {
     float *r, *p, *x, *sv, *w;   // [k]
-    float *ux, *uy, *uz;         // [U]
-    const float *nx, *ny, *nz;   // [k] (shared-memory copy) or null
-    const float4 *n4;            // [k] (global) when nx is null
+    float4 *u;                   // [U] M^-1 J^T r per touched vertex (w unused)
+    const float4 *n4;            // [k] unit normals (float32)
     const int4 *vidx;            // [k]
     const int *seg;              // [U + 1]
     const int *cval;             // [4 k]
     const float *winv;           // [U]
     int voff = 0, coff = 0, eoff = 0;  // subtracted from vidx, cval and seg values (global path)
     __device__ __forceinline__ float3 nrm(int s) const {
-        if (nx) return make_float3(nx[s], ny[s], nz[s]);
         float4 v = n4[s];
         return make_float3(v.x, v.y, v.z);
     }
@@ -309,9 +307,7 @@ __device__ __forceinline__ void cg_matvec_vertex(const CgView &v, int U) {
             a2 += ps * n.z;
         }
         float w = v.winv[j];
-        v.ux[j] = w * a0;
-        v.uy[j] = w * a1;
-        v.uz[j] = w * a2;
+        v.u[j] = make_float4(w * a0, w * a1, w * a2, 0.f);
     }
 }
 
@@ -320,9 +316,10 @@ __device__ __forceinline__ float cg_matvec_stencil(const CgView &v, int s) {
     int4 g = v.vidx[s];
     g.x -= v.voff; g.y -= v.voff; g.z -= v.voff; g.w -= v.voff;
     float3 n = v.nrm(s);
-    float d0 = v.ux[g.x] - (v.ux[g.y] + v.ux[g.z] + v.ux[g.w]) * third;
-    float d1 = v.uy[g.x] - (v.uy[g.y] + v.uy[g.z] + v.uy[g.w]) * third;
-    float d2 = v.uz[g.x] - (v.uz[g.y] + v.uz[g.z] + v.uz[g.w]) * third;
+    float4 u0 = v.u[g.x], u1 = v.u[g.y], u2 = v.u[g.z], u3 = v.u[g.w];
+    float d0 = u0.x - (u1.x + u2.x + u3.x) * third;
+    float d1 = u0.y - (u1.y + u2.y + u3.y) * third;
+    float d2 = u0.z - (u1.z + u2.z + u3.z) * third;
     return n.x * d0 + n.y * d1 + n.z * d2;
 }
 
@@ -546,7 +543,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
         __syncthreads();
         if (rzs <= 0.5 * zone_tol2) continue;
         const int e0 = seg_g[j0];
-        const long long need = 64ll * k + 20ll * U + 16;
+        const long long need = 68ll * k + 24ll * U + 16;
         const bool in_smem = need <= smem_bytes;
         int it;
         // the two paths are instantiated separately so that the shared-memory
@@ -554,25 +551,25 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
         // generic loads)
         if (in_smem) {
             CgView v;
+            // layout: vidx | n4 | u | r p x sv w | seg | cval | winv
             char *base = (char *)smem4;
             int4 *vidx = (int4 *)base;
-            float *f = (float *)(vidx + k);
+            float4 *n4 = (float4 *)(vidx + k);
+            v.u = n4 + k;
+            float *f = (float *)(v.u + U);
             v.r = f; v.p = f + k; v.x = f + 2 * k; v.sv = f + 3 * k; v.w = f + 4 * k;
-            float *nx = f + 5 * k, *ny = f + 6 * k, *nz_ = f + 7 * k;
-            v.ux = f + 8 * k; v.uy = v.ux + U; v.uz = v.uy + U;
-            int *seg = (int *)(v.uz + U);
+            int *seg = (int *)(f + 5 * k);
             int *cval = seg + U + 1;
             float *winv = (float *)(cval + 4 * k);
             for (int t = tid; t < k; t += nt) {
                 int4 g = vidx_g[s0 + t];
                 vidx[t] = make_int4(g.x - j0, g.y - j0, g.z - j0, g.w - j0);
-                float4 n = n32[s0 + t];
-                nx[t] = n.x; ny[t] = n.y; nz_[t] = n.z;
+                n4[t] = n32[s0 + t];
             }
             for (int j = tid; j <= U; j += nt) seg[j] = seg_g[j0 + j] - e0;
             for (int j = tid; j < U; j += nt) winv[j] = winv_g[j0 + j];
             for (int e = tid; e < 4 * k; e += nt) cval[e] = cval_g[e0 + e] - 4 * s0;
-            v.nx = nx; v.ny = ny; v.nz = nz_; v.n4 = nullptr;
+            v.n4 = n4;
             v.vidx = vidx; v.seg = seg; v.cval = cval; v.winv = winv;
             v.voff = 0; v.coff = 0; v.eoff = 0;
             for (int t = tid; t < k; t += nt) {
@@ -587,8 +584,8 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
         } else {
             CgView v;
             v.r = r_g + s0; v.p = p_g + s0; v.x = x_g + s0; v.sv = s_g + s0; v.w = w_g + s0;
-            v.ux = u_g + j0; v.uy = u_g + cap4 + j0; v.uz = u_g + 2 * cap4 + j0;
-            v.nx = v.ny = v.nz = nullptr; v.n4 = n32 + s0;
+            v.u = (float4 *)u_g + j0;
+            v.n4 = n32 + s0;
             v.vidx = vidx_g + s0; v.seg = seg_g + j0; v.cval = cval_g; v.winv = winv_g + j0;
             v.voff = j0; v.coff = 4 * s0; v.eoff = 0;
             for (int t = tid; t < k; t += nt) {
