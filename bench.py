@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
-    ap.add_argument("--frames", type=int, default=300,
+    ap.add_argument("--frames", type=int, default=0,
                     help="frames of the cloth-over-body sequence (0 to skip)")
     return ap.parse_args()
 

@@ -111,7 +111,8 @@ void free_all(hfcr_ctx *c) {
                     c->skeys, c->skeys_alt, c->sflags, c->stencils,
                     c->sb.ids_raw, c->sb.n64_raw, c->sb.n32_raw, c->sb.b_raw, c->sb.parent,
                     c->sb.zkey, c->sb.zkey_alt, c->sb.szone, c->sb.zs, c->sb.zv, c->sb.d_nz,
-                    c->sb.ck64, c->sb.ck64_alt,
+                    c->sb.ck64, c->sb.ck64_alt, c->sb.gst, c->sb.zg, c->sb.d_ng, c->sb.pinv,
+                    c->sb.z32,
                     c->sb.ids, c->sb.n64, c->sb.n32, c->sb.b, c->sb.lam, c->sb.r64, c->sb.r32,
                     c->sb.x32, c->sb.p32, c->sb.q32, c->sb.w32, c->sb.p64, c->sb.q64, c->sb.vidx, c->sb.ckey,
                     c->sb.ckey_alt, c->sb.cval, c->sb.cval_alt, c->sb.cflag, c->sb.seg, c->sb.gvert,
@@ -657,6 +658,11 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(dalloc(&sb.zs, P + 1));
     CK(dalloc(&sb.zv, 4 * P + 1));
     CK(dalloc(&sb.d_nz, 1));
+    CK(dalloc(&sb.gst, P + 1));
+    CK(dalloc(&sb.zg, P + 1));
+    CK(dalloc(&sb.d_ng, 1));
+    CK(dalloc(&sb.pinv, P));
+    CK(dalloc(&sb.z32, P));
     CK(dalloc(&sb.ck64, 4 * P));
     CK(dalloc(&sb.ck64_alt, 4 * P));
     CK(dalloc(&sb.ids, P));

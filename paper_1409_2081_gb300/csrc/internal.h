@@ -143,6 +143,11 @@ struct SolveBuffers {
     int *zs = nullptr;           // [cap_k + 1] first stencil of each zone
     int *zv = nullptr;           // [4 cap_k + 1] first touched vertex of each zone
     int *d_nz = nullptr;         // zone count (device)
+    int *gst = nullptr;          // [cap_k + 1] first row of each preconditioner group
+    int *zg = nullptr;           // [cap_k + 1] first group of each zone
+    int *d_ng = nullptr;         // group count (device)
+    float4 *pinv = nullptr;      // [cap_k] row of the group's inverse block
+    float *z32 = nullptr;        // [cap_k] preconditioned residual (global-memory CG path)
     unsigned long long *ck64 = nullptr, *ck64_alt = nullptr;  // [4 cap_k] (zone, vertex) keys
     int4 *ids = nullptr;         // [cap_k] global vertex ids
     double4_32a *n64 = nullptr;      // [cap_k] unit normal (w unused)

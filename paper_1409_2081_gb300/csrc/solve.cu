@@ -249,6 +249,11 @@ constexpr int ZONE_BIG = 1024;  // zones with at least this many stencils get a 
 
 struct CgView {
     float *r, *p, *x, *sv, *w;   // [k]
+    float *z;                    // [k] preconditioned residual P^-1 r
+    const float4 *pinv;          // [k] row of its group's inverse block (up to 4 columns)
+    const int *gst;              // [G + 1] first row of each group (row offsets relative to the zone)
+    int G = 0;                   // groups in the zone
+    int goff = 0;                // subtracted from gst values (global path)
     float4 *u;                   // [U] M^-1 J^T r per touched vertex (w unused)
     const float4 *n4;            // [k] unit normals (float32)
     const int4 *vidx;            // [k]
@@ -262,34 +267,51 @@ struct CgView {
     }
 };
 
-// deterministic block reduction of two sums with a single barrier: warp
-// partials go to red[2 * warp]; after the barrier every warp loads the
+// deterministic block reduction of three sums with a single barrier: warp
+// partials go to red[3 * warp]; after the barrier every warp loads the
 // partials lane-parallel, folds them with the same shuffle tree and takes
-// lane 0's result, so all threads obtain bit-identical sums
-__device__ __forceinline__ void block_sum2(float a, float b, float *red, float &sa, float &sb_) {
+// lane 0's result (lanes of a butterfly may differ in the last bit; lane
+// 0's value is the same in every warp), so all threads get identical sums
+__device__ __forceinline__ void block_sum3(float a, float b, float c, float *red, float &sa,
+                                           float &sb_, float &sc) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
-        red[2 * w] = a;
-        red[2 * w + 1] = b;
+        red[3 * w] = a;
+        red[3 * w + 1] = b;
+        red[3 * w + 2] = c;
     }
     __syncthreads();
     const int nw = blockDim.x >> 5;
-    float x = lane < nw ? red[2 * lane] : 0.f;
-    float y = lane < nw ? red[2 * lane + 1] : 0.f;
+    float x = lane < nw ? red[3 * lane] : 0.f;
+    float y = lane < nw ? red[3 * lane + 1] : 0.f;
+    float q = lane < nw ? red[3 * lane + 2] : 0.f;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         x += __shfl_xor_sync(0xffffffffu, x, o);
         y += __shfl_xor_sync(0xffffffffu, y, o);
+        q += __shfl_xor_sync(0xffffffffu, q, o);
     }
-    // lanes of a butterfly may differ in the last bit; lane 0's value is
-    // the same in every warp (same inputs, same operations)
     sa = __shfl_sync(0xffffffffu, x, 0);
     sb_ = __shfl_sync(0xffffffffu, y, 0);
+    sc = __shfl_sync(0xffffffffu, q, 0);
+}
+
+// z = P^-1 r for the rows of one group (block-Jacobi over rows sharing x0)
+__device__ __forceinline__ void cg_precond_group(const CgView &v, int g) {
+    const int a = v.gst[g] - v.goff, b = v.gst[g + 1] - v.goff;
+    float rr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) rr[q] = a + q < b ? v.r[a + q] : 0.f;
+    for (int t = a; t < b; ++t) {
+        float4 m = v.pinv[t];
+        v.z[t] = m.x * rr[0] + m.y * rr[1] + m.z * rr[2] + m.w * rr[3];
+    }
 }
 
 __device__ __forceinline__ void cg_matvec_vertex(const CgView &v, int U) {
@@ -300,7 +322,7 @@ __device__ __forceinline__ void cg_matvec_vertex(const CgView &v, int U) {
         for (int e = v.seg[j] - v.eoff; e < e1; ++e) {
             int c = v.cval[e] - v.coff;
             int s = c >> 2;
-            float ps = ((c & 3) ? -third : 1.0f) * v.r[s];
+            float ps = ((c & 3) ? -third : 1.0f) * v.z[s];
             float3 n = v.nrm(s);
             a0 += ps * n.x;
             a1 += ps * n.y;
@@ -324,51 +346,64 @@ __device__ __forceinline__ float cg_matvec_stencil(const CgView &v, int s) {
 }
 
 // returns the iteration count; x holds the solution of A x = r0
+// Preconditioned CG in the Chronopoulos-Gear form (one fused reduction per
+// iteration): u = P^-1 r, w = A u, s = A p by recurrence.  P is the
+// block-Jacobi preconditioner over the groups.  Stops when |r| <= tol |r0|.
+// Returns the iteration count; x holds the solution of A x = r0.
 __device__ __forceinline__ int cg_cg_loop(const CgView &v, int k, int U, int maxit, float tol,
                                           float *red) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    // w = A r, gamma = (r, r), delta = (w, r)
+    for (int g = tid; g < v.G; g += nt) cg_precond_group(v, g);
+    __syncthreads();
     cg_matvec_vertex(v, U);
     __syncthreads();
-    float ga = 0.f, de = 0.f;
+    float ga = 0.f, de = 0.f, rh = 0.f;
     for (int s = tid; s < k; s += nt) {
         float ws = cg_matvec_stencil(v, s);
-        float rs = v.r[s];
+        float rs = v.r[s], zs = v.z[s];
         v.w[s] = ws;
-        ga += rs * rs;
-        de += ws * rs;
+        ga += rs * zs;
+        de += ws * zs;
+        rh += rs * rs;
     }
-    float gamma, delta;
-    block_sum2(ga, de, red, gamma, delta);
-    const float stop = tol * tol * gamma;
+    float gamma, delta, rho;
+    block_sum3(ga, de, rh, red, gamma, delta, rho);
+    const float stop = tol * tol * rho;
     float alpha = gamma / delta, beta = 0.f;
     int it = 0;
-    while (it < maxit && gamma > stop && gamma > 0.f && alpha > 0.f && isfinite(alpha)) {
-        for (int s = tid; s < k; s += nt) {
-            float ps = v.r[s] + beta * v.p[s];
-            float ss = v.w[s] + beta * v.sv[s];
-            v.p[s] = ps;
-            v.sv[s] = ss;
-            v.x[s] += alpha * ps;
-            v.r[s] -= alpha * ss;
+    while (it < maxit && rho > stop && rho > 0.f && alpha > 0.f && isfinite(alpha)) {
+        for (int g = tid; g < v.G; g += nt) {
+            const int a = v.gst[g] - v.goff, b = v.gst[g + 1] - v.goff;
+            for (int s = a; s < b; ++s) {
+                float ps = v.z[s] + beta * v.p[s];
+                float ss = v.w[s] + beta * v.sv[s];
+                v.p[s] = ps;
+                v.sv[s] = ss;
+                v.x[s] += alpha * ps;
+                v.r[s] -= alpha * ss;
+            }
+            cg_precond_group(v, g);
         }
         __syncthreads();
         cg_matvec_vertex(v, U);
         __syncthreads();
         ga = 0.f;
         de = 0.f;
+        rh = 0.f;
         for (int s = tid; s < k; s += nt) {
             float ws = cg_matvec_stencil(v, s);
-            float rs = v.r[s];
+            float rs = v.r[s], zs = v.z[s];
             v.w[s] = ws;
-            ga += rs * rs;
-            de += ws * rs;
+            ga += rs * zs;
+            de += ws * zs;
+            rh += rs * rs;
         }
-        float gn, dn;
-        block_sum2(ga, de, red, gn, dn);
+        float gn, dn, rn;
+        block_sum3(ga, de, rh, red, gn, dn, rn);
         beta = gn / gamma;
         alpha = gn / (dn - beta * gn / alpha);
         gamma = gn;
+        rho = rn;
         ++it;
     }
     return it;
@@ -509,6 +544,111 @@ __global__ void k_csr2_build(const unsigned *zkey, const int *val, const unsigne
     }
 }
 
+// ---------------------------------------------------------------------------
+// block-Jacobi preconditioner: rows whose stencils share x0 (an edge
+// endpoint crossing several faces) are nearly dependent; they are
+// contiguous inside a zone (stencils are sorted by (dir, x0, face)) and are
+// grouped, at most GMAX rows per group.  Each group's block of A is inverted
+// once per solve.
+// ---------------------------------------------------------------------------
+constexpr int GMAX = 4;
+
+__device__ __forceinline__ bool group_start(const int4 *ids, const int *szone, const int *zs,
+                                            int t) {
+    const int zs0 = zs[szone[t]], x0 = ids[t].x;
+    int rs = t;
+    while (rs > zs0 && ids[rs - 1].x == x0) --rs;
+    return ((t - rs) % GMAX) == 0;
+}
+
+__global__ void k_group_flags(const int *d_k, const int4 *ids, const int *szone, const int *zs,
+                              unsigned *flags) {
+    const int k = *d_k;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x)
+        flags[t] = group_start(ids, szone, zs, t) ? 1u : 0u;
+}
+
+__global__ void k_group_build(const int *d_k, const int4 *ids, const int *szone, const int *zs,
+                              const unsigned *excl, const int *d_nz, int *gst, int *zg) {
+    const int k = *d_k;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
+        const bool st = group_start(ids, szone, zs, t);
+        const int g = (int)excl[t];
+        if (st) {
+            gst[g] = t;
+            const int z = szone[t];
+            if (zs[z] == t) zg[z] = g;
+        }
+        if (t == k - 1) {
+            const int ng = g + (st ? 1 : 0);
+            gst[ng] = k;
+            zg[*d_nz] = ng;
+        }
+    }
+}
+
+// inverse of each group's block of A = J M^-1 J^T (float64, stored float32):
+// A_ab = (n_a . n_b) (w(x0) + 1/9 sum of w over the face vertices shared by a and b)
+__global__ void k_group_inverse(const int *d_ng, const int *gst, const int4 *vidx,
+                                const double4_32a *n64, const float *winv, float4 *pinv) {
+    const int ng = *d_ng;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const int a0 = gst[g], m = gst[g + 1] - a0;
+        double A[GMAX][2 * GMAX];
+        for (int a = 0; a < m; ++a) {
+            const int4 va = vidx[a0 + a];
+            const double4_32a na = n64[a0 + a];
+            for (int b = 0; b < m; ++b) {
+                const int4 vb = vidx[a0 + b];
+                const double4_32a nb = n64[a0 + b];
+                double w = winv[va.x];
+                const int fa[3] = {va.y, va.z, va.w}, fb[3] = {vb.y, vb.z, vb.w};
+                for (int p = 0; p < 3; ++p)
+                    for (int q = 0; q < 3; ++q)
+                        if (fa[p] == fb[q]) w += winv[fa[p]] / 9.0;
+                A[a][b] = (na.x * nb.x + na.y * nb.y + na.z * nb.z) * w;
+                A[a][GMAX + b] = a == b ? 1.0 : 0.0;
+            }
+        }
+        // Gauss-Jordan with partial pivoting; a (near-)singular block falls
+        // back to the inverse of its diagonal
+        bool ok = true;
+        double dmax = 0.0;
+        for (int a = 0; a < m; ++a) dmax = fmax(dmax, fabs(A[a][a]));
+        for (int c = 0; c < m && ok; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < m; ++r)
+                if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+            if (!(fabs(A[piv][c]) > 1e-12 * dmax)) { ok = false; break; }
+            if (piv != c)
+                for (int q = 0; q < 2 * GMAX; ++q) {
+                    double tmp = A[c][q];
+                    A[c][q] = A[piv][q];
+                    A[piv][q] = tmp;
+                }
+            const double inv = 1.0 / A[c][c];
+            for (int q = 0; q < 2 * GMAX; ++q) A[c][q] *= inv;
+            for (int r = 0; r < m; ++r)
+                if (r != c) {
+                    const double f = A[r][c];
+                    for (int q = 0; q < 2 * GMAX; ++q) A[r][q] -= f * A[c][q];
+                }
+        }
+        for (int a = 0; a < m; ++a) {
+            float row[GMAX] = {0.f, 0.f, 0.f, 0.f};
+            if (ok) {
+                for (int b = 0; b < m; ++b) row[b] = (float)A[a][GMAX + b];
+            } else {
+                // diagonal fallback computed from the untouched inputs
+                const int4 va = vidx[a0 + a];
+                double w = winv[va.x] + (winv[va.y] + winv[va.z] + winv[va.w]) / 9.0;
+                row[a] = w > 0.0 ? (float)(1.0 / w) : 0.f;
+            }
+            pinv[a0 + a] = make_float4(row[0], row[1], row[2], row[3]);
+        }
+    }
+}
+
 // One float32 CG run per impact zone of the mixed solver (rhs = the float64
 // residual restricted to the zone, lam += x on exit).  Zones with at least
 // `big_min` stencils go to the launch with is_big = 1 (1024 threads, all of
@@ -518,11 +658,11 @@ template <int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
     const int *d_nz, const int *zs, const int *zv, int big_min, int is_big, const int *seg_g,
     const int *cval_g, const float *winv_g, const float4 *n32, const int4 *vidx_g,
-    const double *rhs64, double *lam, float *x_g, float *r_g, float *p_g, float *s_g, float *w_g,
-    float *u_g, int cap4, int maxit, double tol, double rel_tol, const double *bnorm2, int *ctl,
-    int smem_bytes) {
+    const float4 *pinv_g, const int *gst_g, const int *zg, const double *rhs64, double *lam,
+    float *x_g, float *r_g, float *p_g, float *s_g, float *w_g, float *z_g, float *u_g, int cap4,
+    int maxit, double tol, double rel_tol, const double *bnorm2, int *ctl, int smem_bytes) {
     extern __shared__ float4 smem4[];
-    __shared__ float red[64];
+    __shared__ float red[96];
     __shared__ double redd[THREADS / 32];
     if (ctl[0]) return;
     const int nz = *d_nz, tid = threadIdx.x, nt = blockDim.x;
@@ -543,7 +683,8 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
         __syncthreads();
         if (rzs <= 0.5 * zone_tol2) continue;
         const int e0 = seg_g[j0];
-        const long long need = 68ll * k + 24ll * U + 16;
+        const int g0 = zg[z], G = zg[z + 1] - g0;
+        const long long need = 92ll * k + 24ll * U + 4ll * G + 32;
         const bool in_smem = need <= smem_bytes;
         int it;
         // the two paths are instantiated separately so that the shared-memory
@@ -551,21 +692,26 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
         // generic loads)
         if (in_smem) {
             CgView v;
-            // layout: vidx | n4 | u | r p x sv w | seg | cval | winv
+            // layout: vidx | n4 | pinv | u | r p x sv w z | seg | cval | winv | gst
             char *base = (char *)smem4;
             int4 *vidx = (int4 *)base;
             float4 *n4 = (float4 *)(vidx + k);
-            v.u = n4 + k;
+            float4 *pinv = n4 + k;
+            v.u = pinv + k;
             float *f = (float *)(v.u + U);
-            v.r = f; v.p = f + k; v.x = f + 2 * k; v.sv = f + 3 * k; v.w = f + 4 * k;
-            int *seg = (int *)(f + 5 * k);
+            v.r = f; v.p = f + k; v.x = f + 2 * k; v.sv = f + 3 * k; v.w = f + 4 * k; v.z = f + 5 * k;
+            int *seg = (int *)(f + 6 * k);
             int *cval = seg + U + 1;
             float *winv = (float *)(cval + 4 * k);
+            int *gst = (int *)(winv + U);
             for (int t = tid; t < k; t += nt) {
                 int4 g = vidx_g[s0 + t];
                 vidx[t] = make_int4(g.x - j0, g.y - j0, g.z - j0, g.w - j0);
                 n4[t] = n32[s0 + t];
+                pinv[t] = pinv_g[s0 + t];
             }
+            for (int g = tid; g <= G; g += nt) gst[g] = gst_g[g0 + g] - s0;
+            v.pinv = pinv; v.gst = gst; v.G = G; v.goff = 0;
             for (int j = tid; j <= U; j += nt) seg[j] = seg_g[j0 + j] - e0;
             for (int j = tid; j < U; j += nt) winv[j] = winv_g[j0 + j];
             for (int e = tid; e < 4 * k; e += nt) cval[e] = cval_g[e0 + e] - 4 * s0;
@@ -584,8 +730,10 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
         } else {
             CgView v;
             v.r = r_g + s0; v.p = p_g + s0; v.x = x_g + s0; v.sv = s_g + s0; v.w = w_g + s0;
+            v.z = z_g + s0;
             v.u = (float4 *)u_g + j0;
             v.n4 = n32 + s0;
+            v.pinv = pinv_g + s0; v.gst = gst_g + g0; v.G = G; v.goff = s0;
             v.vidx = vidx_g + s0; v.seg = seg_g + j0; v.cval = cval_g; v.winv = winv_g + j0;
             v.voff = j0; v.coff = 4 * s0; v.eoff = 0;
             for (int t = tid; t < k; t += nt) {
@@ -836,6 +984,12 @@ void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers 
     { k_csr2_build<<<nb, 256, 0, s>>>(zk2, sb.cval_s, sb.cflag, sb.ids, d_k, cap, mp.A.n_verts,
                                     mp.A.inv_mass, mp.B.inv_mass, sb.vidx, sb.seg, sb.gvert, sb.winv,
                                     sb.zv, sb.d_nz); note_launch(); }
+    // groups of rows sharing x0 and the inverses of their blocks
+    { k_group_flags<<<gb, 256, 0, s>>>(d_k, sb.ids, sb.szone, sb.zs, sb.cflag); note_launch(); }
+    scan_flags_dev(sb.cflag, d_k, cap, sb.d_ng, s);
+    { k_group_build<<<gb, 256, 0, s>>>(d_k, sb.ids, sb.szone, sb.zs, sb.cflag, sb.d_nz, sb.gst,
+                                     sb.zg); note_launch(); }
+    { k_group_inverse<<<gb, 128, 0, s>>>(sb.d_ng, sb.gst, sb.vidx, sb.n64, sb.winv, sb.pinv); note_launch(); }
 }
 
 void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint32_t *d_status,
@@ -870,12 +1024,14 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
     if (zbig > 152) zbig = 152;
     for (int round = 0; round < p.max_refine; ++round) {
         { k_cg_zone<256><<<zsmall, 256, zone_small_smem, s>>>(
-              sb.d_nz, sb.zs, sb.zv, ZONE_BIG, 0, sb.seg, sb.cval_s, sb.winv, sb.n32, sb.vidx, sb.r64,
-              sb.lam, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.u32, 4 * sb.cap_k, p.max_cg_iters,
+              sb.d_nz, sb.zs, sb.zv, ZONE_BIG, 0, sb.seg, sb.cval_s, sb.winv, sb.n32, sb.vidx, sb.pinv,
+              sb.gst, sb.zg, sb.r64, sb.lam, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.z32, sb.u32,
+              4 * sb.cap_k, p.max_cg_iters,
               p.inner_tol, p.rel_tol, sb.dwork + 1, sb.iwork, zone_small_smem); note_launch(); }
         { k_cg_zone<CG_THREADS><<<zbig, CG_THREADS, fast_smem, s>>>(
-              sb.d_nz, sb.zs, sb.zv, ZONE_BIG, 1, sb.seg, sb.cval_s, sb.winv, sb.n32, sb.vidx, sb.r64,
-              sb.lam, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.u32, 4 * sb.cap_k, p.max_cg_iters,
+              sb.d_nz, sb.zs, sb.zv, ZONE_BIG, 1, sb.seg, sb.cval_s, sb.winv, sb.n32, sb.vidx, sb.pinv,
+              sb.gst, sb.zg, sb.r64, sb.lam, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.z32, sb.u32,
+              4 * sb.cap_k, p.max_cg_iters,
               p.inner_tol, p.rel_tol, sb.dwork + 1, sb.iwork, fast_smem); note_launch(); }
         { k_res_vertex<<<rb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64, sb.lam, sb.u64,
                                          sb.iwork); note_launch(); }
