@@ -214,6 +214,21 @@ hfcr_status hfcr_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
                         hfcr_pair *out, int64_t cap, int64_t *n_out,
                         hfcr_detect_stats *stats, void *stream);
 
+/* hfcr_detect over a batch of independent mesh pairs (A_i, B_i), i <
+ * n_pairs, in one set of launches: each edge of A_i is tested against the
+ * faces of B_i only (and each edge of B_i against A_i's faces).  A and B
+ * are the concatenations of the A_i and of the B_i: positions and faces
+ * back to back, triangle vertex ids global within the concatenation.
+ * segs: device int32 [(n_pairs + 1)][4], row i = first vertex of A_i, first
+ * face of A_i, first vertex of B_i, first face of B_i; row n_pairs =
+ * (A.n_verts, A.n_tris, B.n_verts, B.n_tris); rows non-decreasing (checked:
+ * HFCR_ERR_ARG otherwise).  The oriented flags of A and B apply to every
+ * pair.  Pairs are reported with global ids, sorted by (dir, v0, v1,
+ * face); a pair's mesh index follows from the offsets.  Synchronises. */
+hfcr_status hfcr_detect_batch(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
+                              int32_t n_pairs, const int32_t *segs, hfcr_pair *out, int64_t cap,
+                              int64_t *n_out, hfcr_detect_stats *stats, void *stream);
+
 /* Penetration stencils from sorted pairs (Sec. 3 and Sec. 4, Fig. 3):
  * x0 = the endpoint on the back side of the face (exact sign), identical
  * (dir, x0, face) merged, sorted.  out: device [cap]; *n_out (host) gets
@@ -249,6 +264,16 @@ hfcr_status hfcr_profile_read(hfcr_ctx *ctx, hfcr_profile *out);
 /* Kernel launches made by this library in this process so far
  * (instrumentation, no counterpart in the paper). */
 int64_t hfcr_launch_count(void);
+
+/* hfcr_resolve over a batch of independent mesh pairs laid out as in
+ * hfcr_detect_batch: one repair loop for all pairs (each iteration detects
+ * every pair, and the minimizer's impact zones never span two pairs, so
+ * the result equals resolving the pairs one by one with the same iteration
+ * schedule); the loop ends when no pair has an intersection or after
+ * max_iters detections.  Positions are updated in place.  Synchronises. */
+hfcr_status hfcr_resolve_batch(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, int32_t n_pairs,
+                               const int32_t *segs, double d, int32_t max_iters,
+                               hfcr_resolve_info *info, void *stream);
 
 /* Message of the last failing call on this context ("" if none); with
  * ctx == NULL, of the last failing context-free call of this thread. */

@@ -325,7 +325,7 @@ def scene_c3(seed: int = BASE_SEED + 2, nu: int = 512, nv: int = 256,
 
 
 def scene_c4(seed: int = BASE_SEED + 3, n_pairs: int = 1024, lmin: int = 1,
-             lmax: int = 5) -> List[Scene]:
+             lmax: int = 5, rho_lo: float = 0.5, rho_hi: float = 1.8) -> List[Scene]:
     """Batch of independent pairs of oriented icospheres (radius 1), each
     level uniform in {1..5} (80 to 20,480 triangles per mesh), B under a
     uniform random rotation and offset rho*u, rho ~ U(0.5, 1.8), u uniform
@@ -339,7 +339,7 @@ def scene_c4(seed: int = BASE_SEED + 3, n_pairs: int = 1024, lmin: int = 1,
             if L not in cache:
                 cache[L] = icosphere(L, 1.0)
         Rm = random_rotation(rng)
-        rho = rng.uniform(0.5, 1.8)
+        rho = rng.uniform(rho_lo, rho_hi)
         off = rho * random_unit(rng)
         VA, TA = cache[la]
         VB, TB = cache[lb]
@@ -425,3 +425,27 @@ def soa(V: np.ndarray, dtype) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
     W = np.ascontiguousarray(V.astype(dtype))
     return (np.ascontiguousarray(W[:, 0]), np.ascontiguousarray(W[:, 1]),
             np.ascontiguousarray(W[:, 2]))
+
+
+def concat_batch(scenes: List[Scene]):
+    """Lays a batch of independent mesh pairs out as two concatenated meshes
+    and a segment table: returns (VA, TA, VB, TB, segs) with triangle ids
+    global within each concatenation and segs int32 [(n + 1), 4], row i =
+    (first vertex of A_i, first face of A_i, first vertex of B_i, first face
+    of B_i), last row the totals."""
+    VA, TA, VB, TB = [], [], [], []
+    segs = np.zeros((len(scenes) + 1, 4), np.int64)
+    va = ta = vb = tb = 0
+    for i, sc in enumerate(scenes):
+        segs[i] = [va, ta, vb, tb]
+        VA.append(sc.A.V)
+        TA.append(sc.A.T.astype(np.int64) + va)
+        VB.append(sc.B.V)
+        TB.append(sc.B.T.astype(np.int64) + vb)
+        va += sc.A.n_verts
+        ta += sc.A.n_tris
+        vb += sc.B.n_verts
+        tb += sc.B.n_tris
+    segs[-1] = [va, ta, vb, tb]
+    return (np.concatenate(VA), np.concatenate(TA).astype(np.int32), np.concatenate(VB),
+            np.concatenate(TB).astype(np.int32), segs.astype(np.int32))

@@ -393,6 +393,62 @@ def respond(st: np.ndarray, PA, TA, PB, TB, d: float, inv_mass=None):
     return sol.dx[:nA], sol.dx[nA:], asm, sol
 
 
+# ----------------------------------------------------------------------------
+# diffusion of displacement vectors (Sec. 5)
+# ----------------------------------------------------------------------------
+
+def vertex_adjacency(E: np.ndarray, n_verts: int):
+    """Neighbours of every vertex over the mesh edges, as CSR (indptr,
+    indices), indices ascending within a vertex."""
+    E = np.asarray(E, np.int64)
+    src = np.concatenate([E[:, 0], E[:, 1]])
+    dst = np.concatenate([E[:, 1], E[:, 0]])
+    order = np.lexsort((dst, src))
+    src, dst = src[order], dst[order]
+    indptr = np.zeros(n_verts + 1, np.int64)
+    np.add.at(indptr, src + 1, 1)
+    return np.cumsum(indptr), dst
+
+
+def diffuse(dx: np.ndarray, E: np.ndarray, rings: int, sweeps: int) -> np.ndarray:
+    """Spreads the displacement of the vertices the minimizer moved to their
+    vicinity as a discrete harmonic field (Sec. 5 names constrained
+    diffusion without equations; this is the reading used here): the moved
+    vertices keep their displacement (Dirichlet), vertices more than `rings`
+    edges away keep zero, and each vertex in between takes the mean of its
+    neighbours, `sweeps` Jacobi sweeps starting from zero.  dx: [n, 3]."""
+    n = dx.shape[0]
+    C = np.any(dx != 0.0, axis=1)
+    if rings <= 0 or sweeps <= 0 or not C.any():
+        return dx.copy()
+    indptr, nbr = vertex_adjacency(E, n)
+    deg = np.diff(indptr)
+    # ring distance from the moved vertices (breadth-first, `rings` levels)
+    dist = np.full(n, rings + 1, np.int64)
+    dist[C] = 0
+    frontier = np.nonzero(C)[0]
+    for r in range(1, rings + 1):
+        nxt = []
+        for v in frontier:
+            for w in nbr[indptr[v]:indptr[v + 1]]:
+                if dist[w] > r:
+                    dist[w] = r
+                    nxt.append(w)
+        frontier = np.array(sorted(set(nxt)), np.int64)
+    free = (dist >= 1) & (dist <= rings)
+    u = np.where(C[:, None], dx, 0.0)
+    fv = np.nonzero(free)[0]
+    for _ in range(sweeps):
+        new = u.copy()
+        for v in fv:
+            acc = np.zeros(3)
+            for w in nbr[indptr[v]:indptr[v + 1]]:
+                acc += u[w]
+            new[v] = acc / deg[v]
+        u = new
+    return u
+
+
 @dataclass
 class ResolveResult:
     PA: np.ndarray

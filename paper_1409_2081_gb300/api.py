@@ -99,6 +99,13 @@ _SIGS = {
     "hfcr_detect": ([ctypes.c_void_p, ctypes.POINTER(hfcr_mesh), ctypes.POINTER(hfcr_mesh),
                      ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                      ctypes.POINTER(hfcr_detect_stats), ctypes.c_void_p], ctypes.c_int),
+    "hfcr_detect_batch": ([ctypes.c_void_p, ctypes.POINTER(hfcr_mesh), ctypes.POINTER(hfcr_mesh),
+                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(hfcr_detect_stats),
+                           ctypes.c_void_p], ctypes.c_int),
+    "hfcr_resolve_batch": ([ctypes.c_void_p, ctypes.POINTER(hfcr_mesh), ctypes.POINTER(hfcr_mesh),
+                            ctypes.c_int32, ctypes.c_void_p, ctypes.c_double, ctypes.c_int32,
+                            ctypes.POINTER(hfcr_resolve_info), ctypes.c_void_p], ctypes.c_int),
     "hfcr_build_stencils": ([ctypes.c_void_p, ctypes.POINTER(hfcr_mesh), ctypes.POINTER(hfcr_mesh),
                              ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                              ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p], ctypes.c_int),
@@ -229,6 +236,25 @@ class Context:
                                       int(out.shape[0]), ctypes.byref(n), ctypes.byref(st),
                                       _stream_ptr(stream)))
         return (int(n.value), st) if stats else int(n.value)
+
+    def hfcr_detect_batch(self, A: "Mesh", B: "Mesh", segs, out, stream=None, stats: bool = False):
+        """segs: int32 CUDA tensor [n_pairs + 1, 4] (see include/hfcr.h)."""
+        n = ctypes.c_int64()
+        st = hfcr_detect_stats()
+        self._check(lib().hfcr_detect_batch(self.handle, ctypes.byref(A.c), ctypes.byref(B.c),
+                                            int(segs.shape[0]) - 1, _ptr(segs), _ptr(out),
+                                            int(out.shape[0]), ctypes.byref(n), ctypes.byref(st),
+                                            _stream_ptr(stream)))
+        return (int(n.value), st) if stats else int(n.value)
+
+    def hfcr_resolve_batch(self, A: "Mesh", B: "Mesh", segs, d: float, max_iters: int, stream=None,
+                           raise_not_converged: bool = False):
+        info = hfcr_resolve_info()
+        allow = () if raise_not_converged else (HFCR_ERR_NOT_CONVERGED,)
+        self._check(lib().hfcr_resolve_batch(self.handle, ctypes.byref(A.c), ctypes.byref(B.c),
+                                             int(segs.shape[0]) - 1, _ptr(segs), d, max_iters,
+                                             ctypes.byref(info), _stream_ptr(stream)), allow=allow)
+        return info
 
     def hfcr_build_stencils(self, A: "Mesh", B: "Mesh", pairs, n_pairs: int, out, stream=None) -> int:
         n = ctypes.c_int64()

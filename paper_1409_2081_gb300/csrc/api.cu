@@ -49,6 +49,8 @@ struct hfcr_ctx {
     int *h_cnt = nullptr;         // pinned [16]
     DevStats *h_stats = nullptr;  // pinned
     double *h_dw = nullptr;       // pinned [4] solver words
+    int *d_segs = nullptr;        // [8] segment table of a single mesh pair
+    int *h_segs = nullptr;        // pinned [8]
     int *h_iw = nullptr;          // pinned [8] solver control words
     SortTemp sort;
     Bvh bvh[2];                   // [0]: faces of B (direction 0), [1]: faces of A (direction 1)
@@ -132,6 +134,8 @@ void free_all(hfcr_ctx *c) {
     if (c->h_cnt) cudaFreeHost(c->h_cnt);
     if (c->h_stats) cudaFreeHost(c->h_stats);
     if (c->h_dw) cudaFreeHost(c->h_dw);
+    if (c->h_segs) cudaFreeHost(c->h_segs);
+    if (c->d_segs) cudaFree(c->d_segs);
     if (c->h_iw) cudaFreeHost(c->h_iw);
     c->d_status = nullptr; c->d_stats = nullptr; c->d_cnt = nullptr; c->sort = SortTemp();
     c->edges[0] = c->edges[1] = nullptr;
@@ -140,6 +144,7 @@ void free_all(hfcr_ctx *c) {
     c->skeys = c->skeys_alt = nullptr; c->sflags = nullptr; c->stencils = nullptr;
     c->sb = SolveBuffers();
     c->h_status = nullptr; c->h_cnt = nullptr; c->h_stats = nullptr; c->h_dw = nullptr; c->h_iw = nullptr;
+    c->h_segs = nullptr; c->d_segs = nullptr;
     c->max_verts = c->max_tris = c->max_pairs = 0;
 }
 
@@ -255,11 +260,24 @@ struct DetectPlan {
     const int *edges[2] = {nullptr, nullptr};  // edges of A, of B
     int ne[2] = {0, 0};
     int edge_bits = 1, face_bits = 1;
+    const int *segs = nullptr;  // segment table (one row per mesh pair + a closing row)
+    int nseg = 1;
 };
 
 hfcr_status plan_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool dir0, bool dir1,
-                        DetectPlan &pl, cudaStream_t s) {
+                        DetectPlan &pl, cudaStream_t s, const int *segs = nullptr, int nseg = 1) {
     hfcr_status st;
+    if (segs) {
+        pl.segs = segs;
+        pl.nseg = nseg;
+    } else {
+        // a single pair: one segment covering both meshes
+        const int one[8] = {0, 0, 0, 0, A->n_verts, A->n_tris, B->n_verts, B->n_tris};
+        memcpy(ctx->h_segs, one, sizeof one);
+        CK(cudaMemcpyAsync(ctx->d_segs, ctx->h_segs, sizeof one, cudaMemcpyHostToDevice, s));
+        pl.segs = ctx->d_segs;
+        pl.nseg = 1;
+    }
     if (dir0 && A->n_tris > 0 && (st = mesh_edges(ctx, A, 0, &pl.edges[0], &pl.ne[0], s))) return st;
     if (dir1 && B->n_tris > 0 && (st = mesh_edges(ctx, B, 1, &pl.edges[1], &pl.ne[1], s))) return st;
     int maxe = pl.ne[0] > pl.ne[1] ? pl.ne[0] : pl.ne[1];
@@ -276,6 +294,7 @@ void launch_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d
     prof_begin(ctx, HFCR_STAGE_VALIDATE, s);
     validate_positions(*A, ctx->d_status, s);
     validate_positions(*B, ctx->d_status, s);
+    check_segments(pl.segs, pl.nseg, *A, *B, ctx->d_status, s);
     prof_end(ctx, HFCR_STAGE_VALIDATE, s);
     for (int d = 0; d < 2; ++d) {
         if (!(d == 0 ? dir0 : dir1)) continue;
@@ -285,12 +304,17 @@ void launch_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d
         Bvh &b = ctx->bvh[d];
         prof_begin(ctx, HFCR_STAGE_BVH, s);
         if (!built[d] || b.n != F.n_tris) {
-            bvh_build(b, F, ctx->sort, ctx->d_status, s);
+            // direction 0 builds over B's faces (column 3), direction 1 over A's (column 1)
+            bvh_build(b, F, pl.segs, d == 0 ? 3 : 1, pl.nseg, ctx->sort, ctx->d_status, s);
             built[d] = true;
         }
         bvh_refit(b, F, ctx->d_status, s);
         prof_end(ctx, HFCR_STAGE_BVH, s);
         DetectArgs a;
+        a.segs = pl.segs;
+        a.nseg = pl.nseg;
+        a.ecol = d == 0 ? 0 : 2;  // edge mesh A (vertex column 0) or B (column 2)
+        a.fcol = d == 0 ? 3 : 1;
         a.edge_mesh = &E;
         a.edges = pl.edges[d];
         a.n_edges = pl.ne[d];
@@ -306,6 +330,7 @@ void launch_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d
         prof_begin(ctx, HFCR_STAGE_TRAVERSE, s);
         detect_launch(a, s, ctx->d_status);
         prof_end(ctx, HFCR_STAGE_TRAVERSE, s);
+        pair_products(a.edges, a.n_edges, pl.segs, pl.nseg, a.ecol, a.fcol, F.n_tris, ctx->d_stats, s);
     }
 }
 
@@ -319,11 +344,11 @@ hfcr_status read_back(hfcr_ctx *ctx, cudaStream_t s) {
     return device_status(ctx, *ctx->h_status);
 }
 
-void add_stats(hfcr_detect_stats *o, const DevStats &d, long long bf) {
+void add_stats(hfcr_detect_stats *o, const DevStats &d) {
     o->narrow_tests += (int64_t)d.narrow_tests;
     o->f64_fallbacks += (int64_t)d.f64_fallbacks;
     o->exact_fallbacks += (int64_t)d.exact_fallbacks;
-    o->brute_force_equiv += bf;
+    o->brute_force_equiv += (int64_t)d.bf;
 }
 
 // sorted pair keys (count P on the host) -> hfcr_pair records in out
@@ -476,6 +501,8 @@ hfcr_status run_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     key_add(key, pl.ne[0]);
     key_add(key, pl.ne[1]);
     key_add(key, s);
+    key_add(key, pl.segs);
+    key_add(key, pl.nseg);
     GraphEntry *g = nullptr;
     for (auto &e : ctx->graphs)
         if (e.key == key) g = &e;
@@ -617,6 +644,8 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(cudaMallocHost((void **)&ctx->h_stats, sizeof(DevStats)));
     CK(cudaMallocHost((void **)&ctx->h_dw, sizeof(double) * 4));
     CK(cudaMallocHost((void **)&ctx->h_iw, sizeof(int) * 8));
+    CK(cudaMallocHost((void **)&ctx->h_segs, sizeof(int) * 8));
+    CK(dalloc(&ctx->d_segs, 8));
     size_t maxn = E3 > 4 * P ? E3 : 4 * P;
     ctx->sort.max_blocks = sort_blocks_for((int)maxn) + 1;
     CK(dalloc(&ctx->sort.hist, 256 * (size_t)ctx->sort.max_blocks));
@@ -721,8 +750,9 @@ hfcr_status hfcr_build_edges(hfcr_ctx *ctx, const int32_t *tris, int32_t n_tris,
     return HFCR_OK;
 }
 
-hfcr_status hfcr_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, hfcr_pair *out,
-                        int64_t cap, int64_t *n_out, hfcr_detect_stats *stats, void *stream) {
+static hfcr_status detect_impl(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
+                               const int *segs, int nseg, hfcr_pair *out, int64_t cap,
+                               int64_t *n_out, hfcr_detect_stats *stats, void *stream) {
     hfcr_status st = check_pair(ctx, A, B);
     if (st) return st;
     if (!n_out || cap < 0 || (cap > 0 && !out)) return fail(ctx, HFCR_ERR_ARG, "hfcr_detect: bad output");
@@ -732,15 +762,13 @@ hfcr_status hfcr_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, h
     if ((st = reset_words(ctx, s))) return st;
     bool dir0 = B->oriented != 0, dir1 = A->oriented != 0;
     DetectPlan pl;
-    if ((st = plan_detect(ctx, A, B, dir0, dir1, pl, s))) return st;
+    if ((st = plan_detect(ctx, A, B, dir0, dir1, pl, s, segs, nseg))) return st;
     bool built[2] = {false, false};
     launch_detect(ctx, A, B, dir0, dir1, pl, built, s);
     if ((st = read_back(ctx, s))) return st;
     int P = ctx->h_cnt[C_PAIRS];
     *n_out = P;
-    if (stats)
-        add_stats(stats, *ctx->h_stats,
-                  (dir0 ? (long long)pl.ne[0] * B->n_tris : 0) + (dir1 ? (long long)pl.ne[1] * A->n_tris : 0));
+    if (stats) add_stats(stats, *ctx->h_stats);
     if (P > ctx->max_pairs)
         return fail(ctx, HFCR_ERR_CAPACITY, "%d pairs exceed the reserved %lld", P,
                     (long long)ctx->max_pairs);
@@ -748,6 +776,19 @@ hfcr_status hfcr_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, h
     if ((st = finish_pairs(ctx, P, pl, out, s))) return st;
     CK(cudaStreamSynchronize(s));
     return HFCR_OK;
+}
+
+hfcr_status hfcr_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, hfcr_pair *out,
+                        int64_t cap, int64_t *n_out, hfcr_detect_stats *stats, void *stream) {
+    return detect_impl(ctx, A, B, nullptr, 1, out, cap, n_out, stats, stream);
+}
+
+hfcr_status hfcr_detect_batch(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
+                              int32_t n_pairs, const int32_t *segs, hfcr_pair *out, int64_t cap,
+                              int64_t *n_out, hfcr_detect_stats *stats, void *stream) {
+    if (!ctx) return HFCR_ERR_ARG;
+    if (n_pairs < 1 || !segs) return fail(ctx, HFCR_ERR_ARG, "hfcr_detect_batch: need n_pairs >= 1 and a segment table");
+    return detect_impl(ctx, A, B, segs, n_pairs, out, cap, n_out, stats, stream);
 }
 
 hfcr_status hfcr_build_stencils(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
@@ -815,8 +856,9 @@ hfcr_status hfcr_respond(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     return HFCR_OK;
 }
 
-hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, int32_t max_iters,
-                         hfcr_resolve_info *info, void *stream) {
+static hfcr_status resolve_impl(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, const int *segs,
+                                int nseg, double d, int32_t max_iters, hfcr_resolve_info *info,
+                                void *stream) {
     hfcr_status st = check_pair(ctx, A, B);
     if (st) return st;
     if (max_iters < 0 || !(d == d)) return fail(ctx, HFCR_ERR_ARG, "hfcr_resolve: bad arguments");
@@ -841,7 +883,7 @@ hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, in
     const int need_quiet = alternate ? 2 : 1;
     if ((st = reset_words(ctx, s))) return st;
     DetectPlan pl;
-    if ((st = plan_detect(ctx, A, B, has0, has1, pl, s))) return st;
+    if ((st = plan_detect(ctx, A, B, has0, has1, pl, s, segs, nseg))) return st;
     bool built[2] = {false, false};
     int quiet = 0;
     for (int it = 0; it < max_iters; ++it) {
@@ -857,8 +899,7 @@ hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, in
             if (info) *info = loc;
             return st;
         }
-        add_stats(&loc.stats, *ctx->h_stats,
-                  (d0 ? (long long)pl.ne[0] * B->n_tris : 0) + (d1 ? (long long)pl.ne[1] * A->n_tris : 0));
+        add_stats(&loc.stats, *ctx->h_stats);
         if (it == 0) loc.pairs_first = P;
         loc.pairs_last = P;
         loc.total_pairs += P;
@@ -880,6 +921,19 @@ hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, in
     }
     if (!loc.converged) return fail(ctx, HFCR_ERR_NOT_CONVERGED, "repair loop stopped after %d detections", loc.iters);
     return HFCR_OK;
+}
+
+hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, int32_t max_iters,
+                         hfcr_resolve_info *info, void *stream) {
+    return resolve_impl(ctx, A, B, nullptr, 1, d, max_iters, info, stream);
+}
+
+hfcr_status hfcr_resolve_batch(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, int32_t n_pairs,
+                               const int32_t *segs, double d, int32_t max_iters,
+                               hfcr_resolve_info *info, void *stream) {
+    if (!ctx) return HFCR_ERR_ARG;
+    if (n_pairs < 1 || !segs) return fail(ctx, HFCR_ERR_ARG, "hfcr_resolve_batch: need n_pairs >= 1 and a segment table");
+    return resolve_impl(ctx, A, B, segs, n_pairs, d, max_iters, info, stream);
 }
 
 hfcr_status hfcr_profile_enable(hfcr_ctx *ctx, int32_t on) {

@@ -17,6 +17,21 @@ namespace hfcr {
 
 namespace {
 
+// segment table sanity: rows non-decreasing, first row 0, last row equal to
+// the mesh sizes (the concatenated A and B)
+__global__ void k_check_segs(const int *segs, int nseg, int nva, int nta, int nvb, int ntb,
+                             uint32_t *st) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > nseg) return;
+    const int tot[4] = {nva, nta, nvb, ntb};
+    for (int c = 0; c < 4; ++c) {
+        int v = segs[4 * i + c];
+        bool bad = (i == 0 && v != 0) || (i == nseg && v != tot[c]) ||
+                   (i > 0 && v < segs[4 * (i - 1) + c]) || v < 0 || v > tot[c];
+        if (bad) atomicOr(st, ST_BAD_INDEX);
+    }
+}
+
 // index into [0, n): out-of-range ids read element 0 and raise ST_BAD_INDEX
 __device__ __forceinline__ int chk(int i, int n, uint32_t *st) {
     if ((unsigned)i < (unsigned)n) return i;
@@ -148,7 +163,8 @@ __device__ __forceinline__ unsigned spread10(unsigned v) {
 
 template <typename T>
 __global__ void k_morton(const T *x, const T *y, const T *z, int nv, const int *tris, int nt,
-                         const float *bounds, unsigned *keys, int *vals, uint32_t *st) {
+                         const float *bounds, const int *segs, int col, int nseg,
+                         unsigned long long *keys, int *vals, uint32_t *st) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     T a[3], b[3], c[3];
@@ -164,43 +180,55 @@ __global__ void k_morton(const T *x, const T *y, const T *z, int nv, const int *
         u = fminf(fmaxf(u * 1024.f, 0.f), 1023.f);
         q[k] = (unsigned)u;
     }
-    keys[t] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+    const unsigned long long seg = (unsigned long long)seg_of(segs, col, nseg, t);
+    keys[t] = (seg << 30) | (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
     vals[t] = t;
 }
 
-__device__ __forceinline__ int kdelta(const unsigned *keys, int n, int i, int j) {
+// common-prefix length of the keys of leaves i and j of one segment (its
+// sorted keys start at K); keys made unique by appending the local index
+__device__ __forceinline__ int kdelta(const unsigned long long *K, int n, int i, int j) {
     if (j < 0 || j >= n) return -1;
-    unsigned long long ki = ((unsigned long long)keys[i] << 32) | (unsigned)i;
-    unsigned long long kj = ((unsigned long long)keys[j] << 32) | (unsigned)j;
+    unsigned long long ki = ((K[i] & 0x3fffffffull) << 32) | (unsigned)i;
+    unsigned long long kj = ((K[j] & 0x3fffffffull) << 32) | (unsigned)j;
     return __clzll(ki ^ kj);
 }
 
-// Karras 2012: internal node i covers a key range found from the common
-// prefix lengths of its neighbours; keys made unique by appending i.
-__global__ void k_karras(const unsigned *keys, int n, float4 *nodes, int *iparent, int *lparent) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
-    int d = (kdelta(keys, n, i, i + 1) - kdelta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
-    int dmin = kdelta(keys, n, i, i - d);
+// Karras 2012, one tree per segment: internal node l of the segment whose
+// faces start at t0 covers a key range found from the common-prefix lengths
+// of its neighbours.  Segment-local node l is stored at t0 + l, leaf c at
+// t0 + c (encoded ~(t0 + c)); each segment's root (l = 0) has parent -1.
+__global__ void k_karras(const unsigned long long *keys, int n_total, const int *segs, int col,
+                         int nseg, float4 *nodes, int *iparent, int *lparent) {
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= n_total) return;
+    const int sgi = seg_of(segs, col, nseg, gi);
+    int t0, n;
+    seg_range(segs, col, sgi, n_total, t0, n);
+    const int i = gi - t0;
+    if (i < 0 || i >= n - 1) return;
+    const unsigned long long *K = keys + t0;
+    int d = (kdelta(K, n, i, i + 1) - kdelta(K, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = kdelta(K, n, i, i - d);
     int lmax = 2;
-    while (kdelta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    while (kdelta(K, n, i, i + lmax * d) > dmin) lmax <<= 1;
     int l = 0;
     for (int t = lmax >> 1; t >= 1; t >>= 1)
-        if (kdelta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+        if (kdelta(K, n, i, i + (l + t) * d) > dmin) l += t;
     int j = i + l * d;
-    int dnode = kdelta(keys, n, i, j);
+    int dnode = kdelta(K, n, i, j);
     int s = 0, t = l;
     do {
         t = (t + 1) >> 1;
-        if (kdelta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+        if (kdelta(K, n, i, i + (s + t) * d) > dnode) s += t;
     } while (t > 1);
     int gamma = i + s * d + min(d, 0);
-    int left = (min(i, j) == gamma) ? ~gamma : gamma;
-    int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
-    nodes[4 * i + 3] = make_float4(__int_as_float(left), __int_as_float(right), 0.f, 0.f);
-    if (left < 0) lparent[~left] = i; else iparent[left] = i;
-    if (right < 0) lparent[~right] = i; else iparent[right] = i;
-    if (i == 0) iparent[0] = -1;
+    int left = (min(i, j) == gamma) ? ~(t0 + gamma) : t0 + gamma;
+    int right = (max(i, j) == gamma + 1) ? ~(t0 + gamma + 1) : t0 + gamma + 1;
+    nodes[4 * gi + 3] = make_float4(__int_as_float(left), __int_as_float(right), 0.f, 0.f);
+    if (left < 0) lparent[~left] = gi; else iparent[left] = gi;
+    if (right < 0) lparent[~right] = gi; else iparent[right] = gi;
+    if (i == 0) iparent[gi] = -1;
 }
 
 template <typename T>
@@ -237,7 +265,6 @@ __global__ void k_refit(const T *x, const T *y, const T *z, int nv, const int *t
     load3(x, y, z, chk(tris[3 * f + 1], nv, st), b);
     load3(x, y, z, chk(tris[3 * f + 2], nv, st), c);
     pack_leaf<T>(leaf_tri, j, a, b, c, f);
-    if (n == 1) return;
     float lo[3], hi[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -303,11 +330,21 @@ void build_edges(const int *tris, int n_tris, int n_verts, int *edges_out, int *
     { k_write_edges<<<(n + 255) / 256, 256, 0, s>>>(sorted, flags, n, vb, edges_out); note_launch(); }
 }
 
-void bvh_build(Bvh &b, const hfcr_mesh &m, SortTemp &t, uint32_t *d_status, cudaStream_t s) {
+void check_segments(const int *segs, int nseg, const hfcr_mesh &A, const hfcr_mesh &B,
+                    uint32_t *d_status, cudaStream_t s) {
+    { k_check_segs<<<(nseg + 1 + 127) / 128, 128, 0, s>>>(segs, nseg, A.n_verts, A.n_tris, B.n_verts,
+                                                        B.n_tris, d_status); note_launch(); }
+}
+
+void bvh_build(Bvh &b, const hfcr_mesh &m, const int *segs, int col, int nseg, SortTemp &t,
+               uint32_t *d_status, cudaStream_t s) {
     int nv = m.n_verts;
     int n = m.n_tris;
     b.n = n;
     b.dtype = m.dtype;
+    b.segs = segs;
+    b.col = col;
+    b.nseg = nseg;
     if (n <= 0) return;
     int nb = (n + 255) / 256;
     int nbb = nb < 1024 ? nb : 1024;
@@ -315,26 +352,30 @@ void bvh_build(Bvh &b, const hfcr_mesh &m, SortTemp &t, uint32_t *d_status, cuda
         const float *x = (const float *)m.x, *y = (const float *)m.y, *z = (const float *)m.z;
         { k_centroid_bounds<float><<<nbb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds_part, d_status); note_launch(); }
         { k_bounds_final<<<1, 32, 0, s>>>(b.bounds_part, nbb, b.bounds); note_launch(); }
-        { k_morton<float><<<nb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds, b.keys, b.leaf_face, d_status); note_launch(); }
+        { k_morton<float><<<nb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds, segs, col, nseg, b.keys,
+                                           b.leaf_face, d_status); note_launch(); }
     } else {
         const double *x = (const double *)m.x, *y = (const double *)m.y, *z = (const double *)m.z;
         { k_centroid_bounds<double><<<nbb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds_part, d_status); note_launch(); }
         { k_bounds_final<<<1, 32, 0, s>>>(b.bounds_part, nbb, b.bounds); note_launch(); }
-        { k_morton<double><<<nb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds, b.keys, b.leaf_face, d_status); note_launch(); }
+        { k_morton<double><<<nb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds, segs, col, nseg, b.keys,
+                                            b.leaf_face, d_status); note_launch(); }
     }
-    bool flip = radix_sort_u32(b.keys, b.leaf_face, b.keys_alt, b.vals_alt, n, 30, t, s);
+    bool flip = radix_sort_u64(b.keys, b.leaf_face, b.keys_alt, b.vals_alt, n, 30 + bits_for(nseg + 1),
+                               t, s);
     if (flip) {
-        cudaMemcpyAsync(b.keys, b.keys_alt, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(b.keys, b.keys_alt, sizeof(unsigned long long) * n, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(b.leaf_face, b.vals_alt, sizeof(int) * n, cudaMemcpyDeviceToDevice, s);
     }
-    if (n > 1)
-        { k_karras<<<(n - 1 + 255) / 256, 256, 0, s>>>(b.keys, n, b.nodes, b.parent, b.parent + b.cap); note_launch(); }
+    // leaves of one-face segments keep parent -1
+    cudaMemsetAsync(b.parent + b.cap, 0xff, sizeof(int) * n, s);
+    { k_karras<<<nb, 256, 0, s>>>(b.keys, n, segs, col, nseg, b.nodes, b.parent, b.parent + b.cap); note_launch(); }
 }
 
 void bvh_refit(Bvh &b, const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s) {
     int n = b.n;
     if (n <= 0) return;
-    if (n > 1) cudaMemsetAsync(b.flags, 0, sizeof(unsigned) * (n - 1), s);
+    cudaMemsetAsync(b.flags, 0, sizeof(unsigned) * n, s);
     int nb = (n + 255) / 256;
     if (m.dtype == HFCR_F32)
         { k_refit<float><<<nb, 256, 0, s>>>((const float *)m.x, (const float *)m.y, (const float *)m.z,

@@ -80,12 +80,20 @@ __device__ __forceinline__ bool leaf_test(const T *p, const T *q, const Leaf<T> 
 template <typename T, bool F32F>
 __global__ void __launch_bounds__(256) k_traverse(
     const int2 *edges, int ne, const T *ex, const T *ey, const T *ez, int nv, const float4 *nodes,
-    const void *leaf_tri, int nleaf, unsigned long long dirbit, int face_bits,
-    unsigned long long *out, int *count, int cap, DevStats *st, uint32_t *status) {
+    const void *leaf_tri, int nfaces, const int *segs, int nseg, int ecol, int fcol,
+    unsigned long long dirbit, int face_bits, unsigned long long *out, int *count, int cap,
+    DevStats *st, uint32_t *status) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned tests = 0;
+    int2 ev = make_int2(0, 0);
+    int pair = 0, t0 = 0, nleaf = 0;
+    if (e < ne) {
+        ev = edges[e];
+        // the faces of this edge's own mesh pair form one tree
+        pair = seg_of(segs, ecol, nseg, ev.x);
+        seg_range(segs, fcol, pair, nfaces, t0, nleaf);
+    }
     if (e < ne && nleaf > 0) {
-        int2 ev = edges[e];
         int i0 = chk(ev.x, nv, status), i1 = chk(ev.y, nv, status);
         T p[3] = {ex[i0], ey[i0], ez[i0]}, q[3] = {ex[i1], ey[i1], ez[i1]};
         float lo[3], hi[3];
@@ -97,7 +105,7 @@ __global__ void __launch_bounds__(256) k_traverse(
         const unsigned long long ebits = ((unsigned long long)e) << face_bits;
         int stack[STACK];
         int sp = 0;
-        int node = nleaf == 1 ? ~0 : 0;
+        int node = nleaf == 1 ? ~t0 : t0;
         // a tree of nleaf leaves has 2 nleaf - 1 nodes; each is visited at
         // most once per edge, so the bound only guards a corrupted tree
         int visits = 0;
@@ -239,7 +247,39 @@ __global__ void k_clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *sta
     *d_eff = n;
 }
 
+__device__ __forceinline__ int first_edge_from(const int2 *E, int ne, int v) {
+    int lo = 0, hi = ne;  // first edge whose first vertex is >= v
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (E[mid].x < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_pair_products(const int2 *E, int ne, const int *segs, int nseg, int ecol, int fcol,
+                                int nfaces, DevStats *st) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < nseg) {
+        int e0 = first_edge_from(E, ne, segs[4 * i + ecol]);
+        int e1 = first_edge_from(E, ne, segs[4 * (i + 1) + ecol]);
+        int f0, nf;
+        seg_range(segs, fcol, i, nfaces, f0, nf);
+        v = (unsigned long long)max(e1 - e0, 0) * (unsigned long long)nf;
+    }
+    v = __reduce_add_sync(0xffffffffu, (unsigned)(v & 0xffffffffu)) +
+        ((unsigned long long)__reduce_add_sync(0xffffffffu, (unsigned)(v >> 32)) << 32);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&st->bf, v);
+}
+
 }  // namespace
+
+void pair_products(const int *edges, int ne, const int *segs, int nseg, int ecol, int fcol,
+                   int nfaces, DevStats *stats, cudaStream_t s) {
+    if (ne <= 0 || nseg <= 0) return;
+    { k_pair_products<<<(nseg + 255) / 256, 256, 0, s>>>((const int2 *)edges, ne, segs, nseg, ecol,
+                                                        fcol, nfaces, stats); note_launch(); }
+}
 
 void clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *d_status, cudaStream_t s) {
     { k_clamp_count<<<1, 1, 0, s>>>(d_n, cap, d_eff, d_status); note_launch(); }
@@ -255,17 +295,20 @@ void detect_launch(const DetectArgs &a, cudaStream_t s, uint32_t *d_status) {
         const float *x = (const float *)m.x, *y = (const float *)m.y, *z = (const float *)m.z;
         if (a.f32_filter)
             { k_traverse<float, true><<<nb, 256, 0, s>>>(E, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes,
-                                                       a.bvh->leaf_tri, a.bvh->n, dirbit, a.face_bits,
-                                                       a.keys, a.d_count, a.cap, a.stats, d_status); note_launch(); }
+                                                       a.bvh->leaf_tri, a.bvh->n, a.segs, a.nseg, a.ecol, a.fcol,
+                                                       dirbit, a.face_bits, a.keys, a.d_count, a.cap,
+                                                       a.stats, d_status); note_launch(); }
         else
             { k_traverse<float, false><<<nb, 256, 0, s>>>(E, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes,
-                                                        a.bvh->leaf_tri, a.bvh->n, dirbit, a.face_bits,
-                                                        a.keys, a.d_count, a.cap, a.stats, d_status); note_launch(); }
+                                                        a.bvh->leaf_tri, a.bvh->n, a.segs, a.nseg, a.ecol, a.fcol,
+                                                        dirbit, a.face_bits, a.keys, a.d_count, a.cap,
+                                                        a.stats, d_status); note_launch(); }
     } else {
         const double *x = (const double *)m.x, *y = (const double *)m.y, *z = (const double *)m.z;
         { k_traverse<double, false><<<nb, 256, 0, s>>>(E, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes,
-                                                     a.bvh->leaf_tri, a.bvh->n, dirbit, a.face_bits,
-                                                     a.keys, a.d_count, a.cap, a.stats, d_status); note_launch(); }
+                                                     a.bvh->leaf_tri, a.bvh->n, a.segs, a.nseg, a.ecol, a.fcol,
+                                                     dirbit, a.face_bits, a.keys, a.d_count, a.cap,
+                                                     a.stats, d_status); note_launch(); }
     }
 }
 

@@ -25,16 +25,44 @@ enum : uint32_t {
     ST_BAD_INDEX = 1u << 4,
 };
 
+#ifdef __CUDACC__
+// Segment of element idx in a batch: the largest i < nseg with
+// segs[4 i + col] <= idx.  Segment table rows hold the offsets of one mesh
+// pair in the concatenated meshes: (A vertex, A face, B vertex, B face).
+__device__ __forceinline__ int seg_of(const int *segs, int col, int nseg, int idx) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (segs[4 * mid + col] <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// [first, first + count) of segment i in column col, clamped into [0, total)
+// (a malformed table is reported by check_segments; this keeps every index
+// in range meanwhile)
+__device__ __forceinline__ void seg_range(const int *segs, int col, int i, int total, int &first,
+                                          int &count) {
+    int a = min(max(segs[4 * i + col], 0), total);
+    int b = min(max(segs[4 * (i + 1) + col], a), total);
+    first = a;
+    count = b - a;
+}
+#endif
+
 // Counters a detection accumulates on the device.
 struct DevStats {
     unsigned long long narrow_tests;
     unsigned long long f64_fallbacks;
     unsigned long long exact_fallbacks;
-    unsigned long long pad;
+    unsigned long long bf;  // sum over mesh pairs of |edges| x |faces| tested
 };
 
 // A BVH over the faces of one mesh (Karras 2012 binary radix tree).
-// Internal node i (0 <= i < n-1) is stored as 4 x 16 bytes:
+// A batch of independent mesh pairs builds one tree per pair (segment) in the
+// same arrays: the internal nodes of the segment whose faces start at t0 are
+// stored at t0 .. t0 + n_seg - 2, its leaves at t0 .. t0 + n_seg - 1.
+// Internal node i is stored as 4 x 16 bytes:
 //   [c0.lo.xyz, c0.hi.x] [c0.hi.yz, c1.lo.xy] [c1.lo.z, c1.hi.xyz] [child0, child1, -, -]
 // child >= 0 is an internal node, child < 0 the leaf ~child.  Leaf j holds
 // face leaf_face[j]; its triangle is packed (in leaf order) for the
@@ -48,12 +76,15 @@ struct Bvh {
     unsigned *flags = nullptr;  // [cap - 1] arrival counters of the refit
     int *leaf_face = nullptr;   // [cap]
     void *leaf_tri = nullptr;   // [cap] packed triangles
-    unsigned *keys = nullptr;   // [cap] Morton codes (sort scratch)
-    unsigned *keys_alt = nullptr;
+    unsigned long long *keys = nullptr;      // [cap] (segment, Morton code) sort keys
+    unsigned long long *keys_alt = nullptr;
     int *vals_alt = nullptr;
     float *bounds = nullptr;    // [6] scene bounds of the centroids
     float *bounds_part = nullptr;  // per-block partial bounds
     int dtype = 0;
+    // one tree per segment: segment i owns faces [segs[4 i + col], segs[4 (i + 1) + col])
+    const int *segs = nullptr;
+    int col = 0, nseg = 1;
 };
 
 struct SortTemp {
@@ -89,7 +120,12 @@ void build_edges(const int *tris, int n_tris, int n_verts, int *edges_out, int *
                  SortTemp &t, uint32_t *d_status, cudaStream_t s);
 
 // ---- BVH ----
-void bvh_build(Bvh &b, const hfcr_mesh &m, SortTemp &t, uint32_t *d_status, cudaStream_t s);
+// segs: device [(nseg + 1)][4] rows (A vertex, A face, B vertex, B face)
+// offsets; col selects the face column of the mesh the tree is built over
+void bvh_build(Bvh &b, const hfcr_mesh &m, const int *segs, int col, int nseg, SortTemp &t,
+               uint32_t *d_status, cudaStream_t s);
+void check_segments(const int *segs, int nseg, const hfcr_mesh &A, const hfcr_mesh &B,
+                    uint32_t *d_status, cudaStream_t s);
 void bvh_refit(Bvh &b, const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s);
 
 // ---- validation ----
@@ -97,6 +133,9 @@ void validate_positions(const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s);
 
 // ---- detection ----
 struct DetectArgs {
+    const int *segs;    // segment table of the batch (one row per mesh pair + a closing row)
+    int nseg;
+    int ecol, fcol;     // vertex column of the edge mesh, face column of the face mesh
     const hfcr_mesh *edge_mesh;
     const int *edges;   // [n_edges][2]
     int n_edges;
@@ -110,6 +149,10 @@ struct DetectArgs {
     DevStats *stats;
 };
 void detect_launch(const DetectArgs &a, cudaStream_t s, uint32_t *d_status);
+// adds sum_i |edges of pair i| x |faces of pair i| to stats->bf (edges are
+// sorted by first vertex, so each pair's edges are contiguous)
+void pair_products(const int *edges, int ne, const int *segs, int nseg, int ecol, int fcol,
+                   int nfaces, DevStats *stats, cudaStream_t s);
 // d_eff = *d_n if it is at most cap, else 0 and ST_CAPACITY
 void clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *d_status, cudaStream_t s);
 // keys (sorted) -> hfcr_pair records
