@@ -140,6 +140,22 @@ def profiled_traffic():
         return None
 
 
+def whole_job(local_total_ms: float, steps: int, dist=None, device=None):
+    """Replicas only: every rank runs the same workload on its own GPU; the
+    job's time is the slowest rank's, and the whole-job ms per frame is
+    that time over all frames of all ranks.  Returns (max total ms, ms per
+    frame)."""
+    ws = 1
+    t = local_total_ms
+    if dist is not None and dist.is_initialized():
+        import torch
+        ws = dist.get_world_size()
+        x = torch.tensor([local_total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return t, t / (steps * ws)
+
+
 def scene():
     import meshgen
     return meshgen.scene_c2()
@@ -256,6 +272,7 @@ def batched(api, torch, dev, steps, warmup, timed_fn):
             t.copy_(t0, non_blocking=True)
         return ctx.hfcr_resolve_batch(A, B, dsegs, D_POST, 1)
 
+    variant, variant_ms = ctx.hfcr_autotune(A, B, dsegs)
     for _ in range(warmup):
         step()
     ctx.hfcr_profile_enable(True)
@@ -280,7 +297,8 @@ def batched(api, torch, dev, steps, warmup, timed_fn):
             "roofline": {"kernel": "k_traverse", "bound": "hbm", "achieved": round(ach, 2),
                          "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": round(ach / peak, 5),
                          "alg_bytes_per_launch": alg,
-                         "avg_launch_ms": round(trav_ms / max(1, trav_n), 5)}}
+                         "avg_launch_ms": round(trav_ms / max(1, trav_n), 5),
+                         "traverse_variant": variant, "variant_ms": variant_ms}}
 
 
 def run_reference(args, ws, rank):
@@ -393,6 +411,8 @@ def main():
 
     # ---- optimized form: float32 filter, mixed-precision solver ----
     ctx, A, B, init, ne = build(np.float32, api.HFCR_SOLVER_MIXED, True)
+    # traversal variant chosen by the library's autotuner on this scene
+    variant, variant_ms = ctx.hfcr_autotune(A, B)
     for _ in range(args.warmup):
         frame(ctx, A, B, init)
     # profiled pass: CUDA events around every stage on the launching stream
@@ -409,12 +429,7 @@ def main():
     ms, infos = timed(lambda: frame(ctx, A, B, init), args.steps, 2)
     clocks = sampler.stop()
     launches = api.hfcr_launch_count() - launches0
-    total_ms = sum(ms)
-    if pg:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    per_frame = total_ms / (args.steps * ws)       # whole-job ms per frame
+    total_ms, per_frame = whole_job(sum(ms), args.steps, pg, dev)
     info = infos[-1]
     bf = int(info.stats.brute_force_equiv)
     narrow = int(info.stats.narrow_tests)
@@ -444,11 +459,7 @@ def main():
         return info
 
     e2e_ms, _ = timed(e2e_frame, args.steps, 2)
-    e2e_total = sum(e2e_ms)
-    if pg:
-        t = torch.tensor([e2e_total], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total, _ = whole_job(sum(e2e_ms), args.steps, pg, dev)
     io_bytes = sum(h.numel() * h.element_size() for h in host_in)
 
     # ---- the plain float64 GPU form on the same frame ----
@@ -504,7 +515,8 @@ def main():
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 5),
                          "traffic": profiled_traffic(), "alg_bytes_per_launch": alg_bytes,
                          "avg_launch_ms": round(trav_avg_ms, 5), "launches_timed": trav_n,
-                         "dominant_stage": dominant},
+                         "dominant_stage": dominant, "traverse_variant": variant,
+                         "variant_ms": variant_ms},
             "e2e": {"value": round(e2e_total / (args.steps * ws), 4), "unit": "ms/frame",
                     "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
             "fp64_form": fp64,

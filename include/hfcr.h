@@ -254,6 +254,19 @@ hfcr_status hfcr_respond(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
 hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, int32_t max_iters,
                          hfcr_resolve_info *info, void *stream);
 
+/* Autotuner of the traversal kernel (no counterpart in the paper): builds
+ * the hierarchies for A and B (a batch laid out as in hfcr_detect_batch
+ * when segs is given, one pair when segs is NULL and n_pairs is ignored),
+ * times every traversal variant (register
+ * budget for 2, 3 or 4 CTAs of 256 threads per SM, exact narrow phase
+ * inline or out of line) three times on this scene, and makes the fastest
+ * the context's choice for every later call.  *chosen (host, may be NULL)
+ * gets its index; ms (host [n_ms], may be NULL) the best time of each
+ * variant.  Synchronises. */
+hfcr_status hfcr_autotune(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, int32_t n_pairs,
+                          const int32_t *segs, int32_t *chosen, double *ms, int32_t n_ms,
+                          void *stream);
+
 /* Profiler (instrumentation, no counterpart in the paper).  When enabled,
  * every later call records CUDA events on its stream around each stage;
  * enabling resets the sums.  hfcr_profile_read waits for the recorded

@@ -116,6 +116,9 @@ _SIGS = {
     "hfcr_resolve": ([ctypes.c_void_p, ctypes.POINTER(hfcr_mesh), ctypes.POINTER(hfcr_mesh),
                       ctypes.c_double, ctypes.c_int32, ctypes.POINTER(hfcr_resolve_info),
                       ctypes.c_void_p], ctypes.c_int),
+    "hfcr_autotune": ([ctypes.c_void_p, ctypes.POINTER(hfcr_mesh), ctypes.POINTER(hfcr_mesh),
+                       ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                       ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_void_p], ctypes.c_int),
     "hfcr_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     "hfcr_profile_read": ([ctypes.c_void_p, ctypes.POINTER(hfcr_profile)], ctypes.c_int),
     "hfcr_launch_count": ([], ctypes.c_int64),
@@ -210,6 +213,17 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def hfcr_autotune(self, A: "Mesh", B: "Mesh", segs=None, stream=None):
+        """Times the traversal variants on this scene (a batch when segs is
+        given) and keeps the fastest; returns (chosen index, [ms per variant])."""
+        chosen = ctypes.c_int32()
+        ms = (ctypes.c_double * 8)()
+        n_pairs = 0 if segs is None else int(segs.shape[0]) - 1
+        self._check(lib().hfcr_autotune(self.handle, ctypes.byref(A.c), ctypes.byref(B.c), n_pairs,
+                                        _ptr(segs), ctypes.byref(chosen), ms, 8,
+                                        _stream_ptr(stream)))
+        return int(chosen.value), [round(ms[i], 5) for i in range(3)]
 
     def hfcr_profile_enable(self, on: bool = True):
         self._check(lib().hfcr_profile_enable(self.handle, int(on)))

@@ -49,6 +49,7 @@ struct hfcr_ctx {
     int *h_cnt = nullptr;         // pinned [16]
     DevStats *h_stats = nullptr;  // pinned
     double *h_dw = nullptr;       // pinned [4] solver words
+    int trav_variant = 0;         // traversal variant (hfcr_autotune)
     int *d_segs = nullptr;        // [8] segment table of a single mesh pair
     int *h_segs = nullptr;        // pinned [8]
     int *h_iw = nullptr;          // pinned [8] solver control words
@@ -290,7 +291,37 @@ hfcr_status plan_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, b
 // Launches the traversal of the active directions; positions validated and
 // the BVHs refitted (built first when `build`).  Pair keys -> ctx->pkeys.
 void launch_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool dir0, bool dir1,
-                   const DetectPlan &pl, bool *built, cudaStream_t s) {
+                   const DetectPlan &pl, bool *built, cudaStream_t s, bool traverse_only = false,
+                   int variant = -1) {
+    if (traverse_only) {
+        // timing of the traversal alone (hierarchies already built and refitted)
+        for (int d = 0; d < 2; ++d) {
+            if (!(d == 0 ? dir0 : dir1)) continue;
+            const hfcr_mesh &F = d == 0 ? *B : *A;
+            const hfcr_mesh &E = d == 0 ? *A : *B;
+            if (F.n_tris <= 0 || pl.ne[d] <= 0) continue;
+            DetectArgs a;
+            a.segs = pl.segs;
+            a.nseg = pl.nseg;
+            a.ecol = d == 0 ? 0 : 2;
+            a.fcol = d == 0 ? 3 : 1;
+            a.edge_mesh = &E;
+            a.edges = pl.edges[d];
+            a.n_edges = pl.ne[d];
+            a.bvh = &ctx->bvh[d];
+            a.dir = d;
+            a.f32_filter = ctx->opt.f32_filter;
+            a.edge_bits = pl.edge_bits;
+            a.face_bits = pl.face_bits;
+            a.keys = ctx->pkeys;
+            a.d_count = ctx->d_cnt + C_PAIRS;
+            a.cap = (int)ctx->max_pairs;
+            a.stats = ctx->d_stats;
+            a.variant = variant;
+            detect_launch(a, s, ctx->d_status);
+        }
+        return;
+    }
     prof_begin(ctx, HFCR_STAGE_VALIDATE, s);
     validate_positions(*A, ctx->d_status, s);
     validate_positions(*B, ctx->d_status, s);
@@ -327,6 +358,7 @@ void launch_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d
         a.d_count = ctx->d_cnt + C_PAIRS;
         a.cap = (int)ctx->max_pairs;
         a.stats = ctx->d_stats;
+        a.variant = ctx->trav_variant;
         prof_begin(ctx, HFCR_STAGE_TRAVERSE, s);
         detect_launch(a, s, ctx->d_status);
         prof_end(ctx, HFCR_STAGE_TRAVERSE, s);
@@ -503,6 +535,7 @@ hfcr_status run_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     key_add(key, s);
     key_add(key, pl.segs);
     key_add(key, pl.nseg);
+    key_add(key, ctx->trav_variant);
     GraphEntry *g = nullptr;
     for (auto &e : ctx->graphs)
         if (e.key == key) g = &e;
@@ -934,6 +967,51 @@ hfcr_status hfcr_resolve_batch(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, int32_
     if (!ctx) return HFCR_ERR_ARG;
     if (n_pairs < 1 || !segs) return fail(ctx, HFCR_ERR_ARG, "hfcr_resolve_batch: need n_pairs >= 1 and a segment table");
     return resolve_impl(ctx, A, B, segs, n_pairs, d, max_iters, info, stream);
+}
+
+hfcr_status hfcr_autotune(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, int32_t n_pairs,
+                          const int32_t *segs, int32_t *chosen, double *ms, int32_t n_ms,
+                          void *stream) {
+    hfcr_status st = check_pair(ctx, A, B);
+    if (st) return st;
+    if (segs && n_pairs < 1) return fail(ctx, HFCR_ERR_ARG, "hfcr_autotune: n_pairs must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = reset_words(ctx, s))) return st;
+    bool dir0 = B->oriented != 0, dir1 = A->oriented != 0;
+    DetectPlan pl;
+    if ((st = plan_detect(ctx, A, B, dir0, dir1, pl, s, segs, segs ? n_pairs : 1))) return st;
+    bool built[2] = {false, false};
+    launch_detect(ctx, A, B, dir0, dir1, pl, built, s);  // builds and refits the hierarchies
+    if ((st = read_back(ctx, s))) return st;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = 0;
+    double best_ms = 1e300;
+    for (int v = 0; v < N_TRAVERSE_VARIANTS; ++v) {
+        double vbest = 1e300;
+        for (int rep = 0; rep < 3; ++rep) {
+            CK(cudaMemsetAsync(ctx->d_cnt + C_PAIRS, 0, sizeof(int), s));
+            CK(cudaEventRecord(e0, s));
+            launch_detect(ctx, A, B, dir0, dir1, pl, built, s, true, v);
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            if (t < vbest) vbest = t;
+        }
+        if (ms && v < n_ms) ms[v] = vbest;
+        if (vbest < best_ms) {
+            best_ms = vbest;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if ((st = read_back(ctx, s))) return st;
+    ctx->trav_variant = best;
+    if (chosen) *chosen = best;
+    return HFCR_OK;
 }
 
 hfcr_status hfcr_profile_enable(hfcr_ctx *ctx, int32_t on) {

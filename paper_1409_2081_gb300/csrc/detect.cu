@@ -64,7 +64,7 @@ struct Leaf<double> {
 };
 
 template <typename T, bool F32F>
-__device__ __forceinline__ bool leaf_test(const T *p, const T *q, const Leaf<T> &L, DevStats *st) {
+__device__ __forceinline__ bool leaf_test_body(const T *p, const T *q, const Leaf<T> &L, DevStats *st) {
     int side;
     if constexpr (F32F && sizeof(T) == 4) {
         f3 P = {(float)p[0], (float)p[1], (float)p[2]}, Q = {(float)q[0], (float)q[1], (float)q[2]};
@@ -77,8 +77,18 @@ __device__ __forceinline__ bool leaf_test(const T *p, const T *q, const Leaf<T> 
     }
 }
 
+// the exact narrow phase out of line: the traversal loop then needs far
+// fewer registers (leaf tests are rare next to node visits)
 template <typename T, bool F32F>
-__global__ void __launch_bounds__(256) k_traverse(
+__device__ __noinline__ bool leaf_test_call(const T *p, const T *q, const Leaf<T> &L, DevStats *st) {
+    return leaf_test_body<T, F32F>(p, q, L, st);
+}
+
+// Traversal variants (picked by hfcr_autotune): MINB = CTAs of 256 threads
+// the compiler must fit per SM (register budget), NOINL = narrow phase out
+// of line.
+template <typename T, bool F32F, int MINB, bool NOINL>
+__global__ void __launch_bounds__(256, MINB) k_traverse(
     const int2 *edges, int ne, const T *ex, const T *ey, const T *ez, int nv, const float4 *nodes,
     const void *leaf_tri, int nfaces, const int *segs, int nseg, int ecol, int fcol,
     unsigned long long dirbit, int face_bits, unsigned long long *out, int *count, int cap,
@@ -139,7 +149,10 @@ __global__ void __launch_bounds__(256) k_traverse(
                     Leaf<T> L;
                     L.load(leaf_tri, lf);
                     ++tests;
-                    if (leaf_test<T, F32F>(p, q, L, st)) {
+                    bool hit;
+                    if constexpr (NOINL) hit = leaf_test_call<T, F32F>(p, q, L, st);
+                    else hit = leaf_test_body<T, F32F>(p, q, L, st);
+                    if (hit) {
                         int pos = atomicAdd(count, 1);
                         if (pos < cap) out[pos] = dirbit | ebits | (unsigned)L.face;
                     }
@@ -285,30 +298,38 @@ void clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *d_status, cudaSt
     { k_clamp_count<<<1, 1, 0, s>>>(d_n, cap, d_eff, d_status); note_launch(); }
 }
 
+template <typename T, bool F32F, int MINB, bool NOINL>
+static void launch_traverse(const DetectArgs &a, const T *x, const T *y, const T *z, int nb,
+                            unsigned long long dirbit, cudaStream_t s, uint32_t *d_status) {
+    const hfcr_mesh &m = *a.edge_mesh;
+    { k_traverse<T, F32F, MINB, NOINL><<<nb, 256, 0, s>>>(
+          (const int2 *)a.edges, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes, a.bvh->leaf_tri,
+          a.bvh->n, a.segs, a.nseg, a.ecol, a.fcol, dirbit, a.face_bits, a.keys, a.d_count, a.cap,
+          a.stats, d_status); note_launch(); }
+}
+
+template <typename T, bool F32F>
+static void launch_variant(const DetectArgs &a, const T *x, const T *y, const T *z, int nb,
+                           unsigned long long dirbit, cudaStream_t s, uint32_t *d_status) {
+    switch (a.variant) {
+        case 1: launch_traverse<T, F32F, 4, true>(a, x, y, z, nb, dirbit, s, d_status); break;
+        case 2: launch_traverse<T, F32F, 3, true>(a, x, y, z, nb, dirbit, s, d_status); break;
+        default: launch_traverse<T, F32F, 2, false>(a, x, y, z, nb, dirbit, s, d_status); break;
+    }
+}
+
 void detect_launch(const DetectArgs &a, cudaStream_t s, uint32_t *d_status) {
     if (a.n_edges <= 0 || a.bvh->n <= 0) return;
     const hfcr_mesh &m = *a.edge_mesh;
     int nb = (a.n_edges + 255) / 256;
     unsigned long long dirbit = (unsigned long long)a.dir << (a.edge_bits + a.face_bits);
-    const int2 *E = (const int2 *)a.edges;
     if (m.dtype == HFCR_F32) {
         const float *x = (const float *)m.x, *y = (const float *)m.y, *z = (const float *)m.z;
-        if (a.f32_filter)
-            { k_traverse<float, true><<<nb, 256, 0, s>>>(E, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes,
-                                                       a.bvh->leaf_tri, a.bvh->n, a.segs, a.nseg, a.ecol, a.fcol,
-                                                       dirbit, a.face_bits, a.keys, a.d_count, a.cap,
-                                                       a.stats, d_status); note_launch(); }
-        else
-            { k_traverse<float, false><<<nb, 256, 0, s>>>(E, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes,
-                                                        a.bvh->leaf_tri, a.bvh->n, a.segs, a.nseg, a.ecol, a.fcol,
-                                                        dirbit, a.face_bits, a.keys, a.d_count, a.cap,
-                                                        a.stats, d_status); note_launch(); }
+        if (a.f32_filter) launch_variant<float, true>(a, x, y, z, nb, dirbit, s, d_status);
+        else launch_variant<float, false>(a, x, y, z, nb, dirbit, s, d_status);
     } else {
         const double *x = (const double *)m.x, *y = (const double *)m.y, *z = (const double *)m.z;
-        { k_traverse<double, false><<<nb, 256, 0, s>>>(E, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes,
-                                                     a.bvh->leaf_tri, a.bvh->n, a.segs, a.nseg, a.ecol, a.fcol,
-                                                     dirbit, a.face_bits, a.keys, a.d_count, a.cap,
-                                                     a.stats, d_status); note_launch(); }
+        launch_variant<double, false>(a, x, y, z, nb, dirbit, s, d_status);
     }
 }
 

@@ -352,3 +352,16 @@ def test_graph_replay_matches_plain_launches(api):
     for r in results[1:]:
         assert np.array_equal(r[0], results[0][0]) and np.array_equal(r[1], results[0][1])
         assert r[2:] == results[0][2:]
+
+
+def test_autotuned_variants_give_identical_pairs(api):
+    """Every traversal variant finds the same exact pair set."""
+    sc = meshgen.scene_c2()
+    A, PA = dev_mesh(api, sc.A.V, sc.A.T, False, np.float32)
+    B, PB = dev_mesh(api, sc.B.V, sc.B.T, True, np.float32)
+    ctx = make_ctx(api, sc.A.n_verts, sc.A.n_tris)
+    chosen, ms = ctx.hfcr_autotune(A, B)
+    assert 0 <= chosen < 3 and all(t > 0 for t in ms)
+    _, n, got, _ = detect(ctx, A, B)
+    ref = oracle.detect(PA, sc.A.T, False, PB, sc.B.T, True)
+    assert np.array_equal(got, ref.rec)
