@@ -185,17 +185,18 @@ def cpu_oracle_frame(sc, edge_fraction=1.0):
     return (t2 - t0), oracle.num_threads(), (t1 - t0) / frac + (t2 - t1)
 
 
-def frame_sequence(api, torch, dev, n_frames, max_iters=8):
+def frame_sequence(api, torch, dev, n_frames, max_iters=8, rings=4, sweeps=16):
     """Cloth 512 x 512 (side 3.0, float32, un-oriented) falling onto an
     oriented body (icosphere level 7 with spherical-harmonic radius noise of
     amplitude 0.1): each frame moves the cloth by the seeded velocity field
     (torch ops on the device, outside the timed region), then one repair
-    loop (resolve, up to max_iters iterations, graph-replayed) is timed."""
+    loop (resolve, up to max_iters iterations, graph-replayed, with the
+    diffusion of Sec. 5 over `rings` rings and `sweeps` sweeps) is timed."""
     import numpy as np
     import meshgen
     sc = meshgen.scene_c5()
     mot = sc.meta["motion"]
-    ctx = api.Context()
+    ctx = api.Context(diffuse_rings=rings, diffuse_sweeps=sweeps)
     ctx.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), 1 << 18)
 
     def dev_xyz(V):
@@ -232,7 +233,8 @@ def frame_sequence(api, torch, dev, n_frames, max_iters=8):
     ctx.close()
     srt = sorted(ms)
     return {"workload": "cloth 512x512 (784,385 edges) falling on SH body (icosphere L7, 327,680 faces), "
-                        "float32, one resolve (<= %d iterations) per frame" % max_iters,
+                        "float32, one resolve (<= %d iterations, diffusion R=%d S=%d) per frame"
+                        % (max_iters, rings, sweeps),
             "frames": n_frames, "ms_p50": round(statistics.median(ms), 4),
             "ms_p99": round(srt[min(len(srt) - 1, int(0.99 * len(srt)))], 4),
             "ms_mean": round(statistics.mean(ms), 4), "max_pairs_first": max(pairs),

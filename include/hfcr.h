@@ -104,18 +104,23 @@ typedef struct {
     int32_t f32_filter;     /* 1 (default): float32 meshes try the float32 filter first */
     int32_t roles;          /* hfcr_roles (default ALTERNATE) */
     int32_t max_cg_iters;   /* per float32 run of MIXED (default 500); FP64 runs once with max_cg_iters * max_refine */
-    int32_t max_refine;     /* refinement rounds of the MIXED solver (default 6) */
+    int32_t max_refine;     /* MIXED: float32 runs per impact zone, each followed by the zone's
+                               float64 residual (default 6) */
     double rel_tol;         /* target |b - A lambda| / |b| (default 1e-12) */
     double inner_tol;       /* MIXED: residual reduction of one float32 run (default 1e-5) */
     int32_t graphs;         /* 1 (default): resolve replays each repair iteration as a captured
                                CUDA graph (re-captured when any argument changes); 0: plain launches.
                                Graphs are not used while the profiler is enabled. */
+    int32_t diffuse_rings;  /* Sec. 5 diffusion in hfcr_resolve (see hfcr_diffuse): rings R of the */
+    int32_t diffuse_sweeps; /* band and Jacobi sweeps S; 0 (default) in either: no diffusion, the
+                               minimizer's displacement is applied as it is */
 } hfcr_options;
 
 typedef struct {
     int32_t cg_iters;        /* conjugate-gradient iterations, all runs */
-    int32_t refine_rounds;   /* MIXED: float64 residual evaluations after the first */
-    double rel_residual;     /* |b - A lambda| / |b| at exit, float64 */
+    int32_t refine_rounds;   /* MIXED: the most float32 runs any impact zone needed */
+    double rel_residual;     /* |b - A lambda| / |b| at exit, float64 (MIXED: every zone stops
+                                at |r_zone| <= rel_tol |b_zone|, which bounds the whole) */
     int32_t converged;       /* rel_residual <= rel_tol */
     int32_t n_stencils;
     int32_t n_touched;       /* distinct vertices in the stencils */
@@ -246,11 +251,28 @@ hfcr_status hfcr_respond(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
                          const hfcr_stencil *st, int64_t k, double d,
                          void *const *dxA, void *const *dxB, hfcr_solve_info *info, void *stream);
 
+/* Diffusion of a displacement field over one mesh (Sec. 5: the
+ * correction is propagated from the penetrating vertices to their vicinity
+ * as a harmonic vector field; the paper gives no equations, this is the
+ * reading implemented): vertices with a nonzero displacement keep it,
+ * vertices more than `rings` edges from all of them, and kinematic
+ * vertices (M.inv_mass 0), get 0, and every vertex in between takes
+ * `sweeps` Jacobi sweeps of the mean of its neighbours, starting from 0.
+ * The neighbours come from M's edge list (M.edges, or derived from the
+ * triangles); each mean sums them in ascending vertex order in float64.
+ * dx, dy, dz: device float64 [M.n_verts], read and overwritten.  rings in
+ * [0, 1024], sweeps in [0, 100000]; either 0 leaves the field as it is.
+ * Synchronises. */
+hfcr_status hfcr_diffuse(hfcr_ctx *ctx, const hfcr_mesh *M, double *dx, double *dy, double *dz,
+                         int32_t rings, int32_t sweeps, void *stream);
+
 /* The repair loop (Sec. 3): detect, build stencils, displace, repeated
  * until no E-F intersection remains or max_iters detections ran.  Updates
- * A and B's positions in place.  info (host) may be NULL.  Returns
- * HFCR_ERR_NOT_CONVERGED when the loop stopped at max_iters.
- * Synchronises. */
+ * A and B's positions in place.  With options diffuse_rings and
+ * diffuse_sweeps > 0, each iteration's displacement is first spread over
+ * both meshes as by hfcr_diffuse (Sec. 5), then applied.  info (host) may
+ * be NULL.  Returns HFCR_ERR_NOT_CONVERGED when the loop stopped at
+ * max_iters.  Synchronises. */
 hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, int32_t max_iters,
                          hfcr_resolve_info *info, void *stream);
 

@@ -410,13 +410,16 @@ def vertex_adjacency(E: np.ndarray, n_verts: int):
     return np.cumsum(indptr), dst
 
 
-def diffuse(dx: np.ndarray, E: np.ndarray, rings: int, sweeps: int) -> np.ndarray:
+def diffuse(dx: np.ndarray, E: np.ndarray, rings: int, sweeps: int,
+            fixed: Optional[np.ndarray] = None) -> np.ndarray:
     """Spreads the displacement of the vertices the minimizer moved to their
     vicinity as a discrete harmonic field (Sec. 5 names constrained
     diffusion without equations; this is the reading used here): the moved
-    vertices keep their displacement (Dirichlet), vertices more than `rings`
-    edges away keep zero, and each vertex in between takes the mean of its
-    neighbours, `sweeps` Jacobi sweeps starting from zero.  dx: [n, 3]."""
+    vertices (nonzero dx) keep their displacement (Dirichlet), vertices more
+    than `rings` edges away and `fixed` (kinematic) vertices keep zero, and
+    each vertex in between takes the mean of its neighbours, `sweeps` Jacobi
+    sweeps starting from zero.  The ring distance is the edge-count distance
+    to the nearest moved vertex over the whole mesh.  dx: [n, 3]."""
     n = dx.shape[0]
     C = np.any(dx != 0.0, axis=1)
     if rings <= 0 or sweeps <= 0 or not C.any():
@@ -436,6 +439,8 @@ def diffuse(dx: np.ndarray, E: np.ndarray, rings: int, sweeps: int) -> np.ndarra
                     nxt.append(w)
         frontier = np.array(sorted(set(nxt)), np.int64)
     free = (dist >= 1) & (dist <= rings)
+    if fixed is not None:
+        free &= ~np.asarray(fixed, bool)
     u = np.where(C[:, None], dx, 0.0)
     fv = np.nonzero(free)[0]
     for _ in range(sweeps):
@@ -474,12 +479,16 @@ def role_schedule(orientedA: bool, orientedB: bool, it: int, mode: str) -> List[
 
 def resolve(PA, TA, orientedA, PB, TB, orientedB, d: float = 1e-4, max_iters: int = 64,
             store_dtype=np.float64, inv_mass=None, n_threads: int = 0,
-            mode: str = "alternate") -> ResolveResult:
+            mode: str = "alternate", diffuse_rings: int = 0,
+            diffuse_sweeps: int = 0) -> ResolveResult:
     """The repair loop of Sec. 3: detect, build stencils, displace by the
     minimizer, repeated until no edge-face intersection remains.  It stops
     when the most recent detections covering every active direction found
     no pair, or after `max_iters` detections.  Positions are rounded to
-    `store_dtype` after each displacement (the storage type of the scene)."""
+    `store_dtype` after each displacement (the storage type of the scene).
+    With diffuse_rings and diffuse_sweeps > 0, each mesh's displacement is
+    spread by `diffuse` (Sec. 5) before it is applied; vertices of inverse
+    mass 0 are held fixed."""
     if mode not in ("alternate", "both"):
         raise ValueError(mode)
     PA = np.asarray(PA, np.float64).astype(store_dtype).astype(np.float64)
@@ -504,6 +513,11 @@ def resolve(PA, TA, orientedA, PB, TB, orientedB, d: float = 1e-4, max_iters: in
         st = stencils(pr)
         sc.append(len(st))
         dA, dB, _, _ = respond(st, PA, TA, PB, TB, d, inv_mass)
+        if diffuse_rings > 0 and diffuse_sweeps > 0:
+            nA = PA.shape[0]
+            fx = None if inv_mass is None else np.asarray(inv_mass) == 0.0
+            dA = diffuse(dA, EA, diffuse_rings, diffuse_sweeps, None if fx is None else fx[:nA])
+            dB = diffuse(dB, EB, diffuse_rings, diffuse_sweeps, None if fx is None else fx[nA:])
         PA = (PA + dA).astype(store_dtype).astype(np.float64)
         PB = (PB + dB).astype(store_dtype).astype(np.float64)
     return ResolveResult(PA, PB, max_iters, pc, sc, dl, False)

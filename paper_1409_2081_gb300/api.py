@@ -54,7 +54,8 @@ class hfcr_options(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int32), ("f32_filter", ctypes.c_int32),
                 ("roles", ctypes.c_int32), ("max_cg_iters", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("rel_tol", ctypes.c_double),
-                ("inner_tol", ctypes.c_double), ("graphs", ctypes.c_int32)]
+                ("inner_tol", ctypes.c_double), ("graphs", ctypes.c_int32),
+                ("diffuse_rings", ctypes.c_int32), ("diffuse_sweeps", ctypes.c_int32)]
 
 
 class hfcr_solve_info(ctypes.Structure):
@@ -113,6 +114,8 @@ _SIGS = {
                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                       ctypes.POINTER(hfcr_solve_info), ctypes.c_void_p], ctypes.c_int),
+    "hfcr_diffuse": ([ctypes.c_void_p, ctypes.POINTER(hfcr_mesh), ctypes.c_void_p, ctypes.c_void_p,
+                      ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p], ctypes.c_int),
     "hfcr_resolve": ([ctypes.c_void_p, ctypes.POINTER(hfcr_mesh), ctypes.POINTER(hfcr_mesh),
                       ctypes.c_double, ctypes.c_int32, ctypes.POINTER(hfcr_resolve_info),
                       ctypes.c_void_p], ctypes.c_int),
@@ -187,12 +190,13 @@ class Context:
 
     def __init__(self, solver: int = HFCR_SOLVER_MIXED, f32_filter: bool = True,
                  roles: int = HFCR_ROLES_ALTERNATE, max_cg_iters: int = 500, max_refine: int = 6,
-                 rel_tol: float = 1e-12, inner_tol: float = 1e-5, graphs: bool = True):
+                 rel_tol: float = 1e-12, inner_tol: float = 1e-5, graphs: bool = True,
+                 diffuse_rings: int = 0, diffuse_sweeps: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("hfcr needs a CUDA device")
         opt = hfcr_options(solver, int(f32_filter), roles, max_cg_iters, max_refine, rel_tol, inner_tol,
-                           int(graphs))
+                           int(graphs), diffuse_rings, diffuse_sweeps)
         h = ctypes.c_void_p()
         self._check(lib().hfcr_create(ctypes.byref(h), ctypes.byref(opt)), None)
         self.handle = h
@@ -286,6 +290,11 @@ class Context:
                                        _ptr(stencils), k, d, pa, pb,
                                        ctypes.byref(si) if info else None, _stream_ptr(stream)))
         return si
+
+    def hfcr_diffuse(self, M: "Mesh", dx, rings: int, sweeps: int, stream=None):
+        """dx: three float64 CUDA tensors [n] (x, y, z), overwritten."""
+        self._check(lib().hfcr_diffuse(self.handle, ctypes.byref(M.c), _ptr(dx[0]), _ptr(dx[1]),
+                                       _ptr(dx[2]), rings, sweeps, _stream_ptr(stream)))
 
     def hfcr_resolve(self, A: "Mesh", B: "Mesh", d: float, max_iters: int, stream=None,
                      raise_not_converged: bool = False):

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhfcr.so")
-SOURCES = ["api.cu", "bvh.cu", "detect.cu", "noalloc.cu", "solve.cu", "sort.cu"]
+SOURCES = ["api.cu", "bvh.cu", "detect.cu", "diffuse.cu", "noalloc.cu", "solve.cu", "sort.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -64,6 +64,11 @@ struct hfcr_ctx {
     unsigned *sflags = nullptr;
     hfcr_stencil *stencils = nullptr;
     SolveBuffers sb;
+    // diffusion (Sec. 5): vertex adjacency per mesh, float64 field ping-pong
+    // over both meshes' vertices (AoS), ring distances
+    int *adj_ptr[2] = {nullptr, nullptr}, *adj_nbr[2] = {nullptr, nullptr}, *adj_cur = nullptr;
+    double *field = nullptr, *field_alt = nullptr;
+    int *ring = nullptr;
     // profiler
     bool prof_on = false;
     double prof_ms[HFCR_N_STAGES] = {0};
@@ -123,6 +128,13 @@ void free_all(hfcr_ctx *c) {
                     c->sb.dwork};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    void *dp[] = {c->adj_ptr[0], c->adj_ptr[1], c->adj_nbr[0], c->adj_nbr[1], c->adj_cur, c->field,
+                  c->field_alt, c->ring};
+    for (void *p : dp)
+        if (p) cudaFree(p);
+    c->adj_ptr[0] = c->adj_ptr[1] = c->adj_nbr[0] = c->adj_nbr[1] = c->adj_cur = nullptr;
+    c->field = c->field_alt = nullptr;
+    c->ring = nullptr;
     for (int i = 0; i < 2; ++i) {
         Bvh &b = c->bvh[i];
         void *bp[] = {b.nodes, b.parent, b.flags, b.leaf_face, b.leaf_tri, b.keys, b.keys_alt,
@@ -414,7 +426,8 @@ hfcr_status make_stencils(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     bool flip = radix_sort_u64(ctx->skeys, nullptr, ctx->skeys_alt, nullptr, P, 1 + vb + fb,
                                ctx->sort, s);
     unsigned long long *sorted = flip ? ctx->skeys_alt : ctx->skeys;
-    stencil_unique(sorted, ctx->d_cnt + slot, P, vb, fb, ctx->sflags, out, ctx->d_cnt + C_STENCILS, s);
+    stencil_unique(sorted, ctx->d_cnt + slot, P, vb, fb, ctx->sflags, out, ctx->d_cnt + C_STENCILS,
+                   ctx->sort, s);
     prof_end(ctx, HFCR_STAGE_STENCILS, s);
     hfcr_status st = read_back(ctx, s);
     if (st) return st;
@@ -453,6 +466,30 @@ hfcr_status run_response(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     return HFCR_OK;
 }
 
+bool diffusing(const hfcr_ctx *ctx) {
+    return ctx->opt.diffuse_rings > 0 && ctx->opt.diffuse_sweeps > 0;
+}
+
+// vertex adjacency of both meshes for the diffusion, from their edge lists
+// (the plan's, or derived from the triangles)
+hfcr_status prepare_diffusion(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
+                              DetectPlan &pl, cudaStream_t s) {
+    const hfcr_mesh *M[2] = {A, B};
+    for (int i = 0; i < 2; ++i) {
+        if (M[i]->n_verts <= 0) continue;
+        const int *e = pl.edges[i];
+        int ne = pl.ne[i];
+        if (!e && M[i]->n_tris > 0) {
+            hfcr_status st = mesh_edges(ctx, M[i], i, &e, &ne, s);
+            if (st) return st;
+        }
+        build_adjacency(e, e ? ne : 0, M[i]->n_verts, ctx->adj_ptr[i], ctx->adj_nbr[i], ctx->adj_cur,
+                        ctx->sort, ctx->d_status, s);
+    }
+    CK(cudaGetLastError());
+    return HFCR_OK;
+}
+
 // One repair iteration enqueued on device counts only: detection, clamped
 // pair count, pair sort and records, stencils, assembly, solve, applied
 // displacement.  Grids are sized by the reserved capacity; kernels read
@@ -477,9 +514,26 @@ void enqueue_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bo
     flip = radix_sort_u64_dev(ctx->skeys, ctx->skeys_alt, ctx->d_cnt + C_PEFF, cap, 1 + vb + fb,
                               ctx->sort, s);
     stencil_unique(flip ? ctx->skeys_alt : ctx->skeys, ctx->d_cnt + C_PEFF, cap, vb, fb, ctx->sflags,
-                   ctx->stencils, ctx->d_cnt + C_STENCILS, s);
+                   ctx->stencils, ctx->d_cnt + C_STENCILS, ctx->sort, s);
     prof_end(ctx, HFCR_STAGE_STENCILS, s);
-    run_response(ctx, A, B, ctx->stencils, cap, d, 1, nullptr, nullptr, s);
+    if (!diffusing(ctx)) {
+        run_response(ctx, A, B, ctx->stencils, cap, d, 1, nullptr, nullptr, s);
+        return;
+    }
+    // Sec. 5: the minimizer's displacement into the float64 field, spread
+    // over each mesh, then applied
+    const int ntot = A->n_verts + B->n_verts;
+    cudaMemsetAsync(ctx->field, 0, sizeof(double) * 3 * (size_t)ntot, s);
+    void *fld[3] = {ctx->field, nullptr, nullptr};
+    run_response(ctx, A, B, ctx->stencils, cap, d, 2, fld, nullptr, s);
+    prof_begin(ctx, HFCR_STAGE_DISPLACE, s);
+    DiffMeshArgs da, db;
+    da.ptr = ctx->adj_ptr[0]; da.nbr = ctx->adj_nbr[0]; da.inv_mass = A->inv_mass; da.n = A->n_verts;
+    db.ptr = ctx->adj_ptr[1]; db.nbr = ctx->adj_nbr[1]; db.inv_mass = B->inv_mass; db.n = B->n_verts;
+    const double *u = diffuse_field(da, db, ctx->field, ctx->field_alt, ctx->ring,
+                                    ctx->opt.diffuse_rings, ctx->opt.diffuse_sweeps, s);
+    apply_field(*A, *B, ctx->ring, ctx->opt.diffuse_rings, u, s);
+    prof_end(ctx, HFCR_STAGE_DISPLACE, s);
 }
 
 // Reads the counters, status, statistics and solver words of the last
@@ -621,6 +675,8 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
     c->opt.rel_tol = 1e-12;
     c->opt.inner_tol = 1e-5;
     c->opt.graphs = 1;
+    c->opt.diffuse_rings = 0;
+    c->opt.diffuse_sweeps = 0;
     if (opt) {
         c->opt = *opt;
         if (c->opt.max_cg_iters <= 0) c->opt.max_cg_iters = 500;
@@ -629,6 +685,12 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
         if (!(c->opt.inner_tol > 0)) c->opt.inner_tol = 1e-5;
         if (c->opt.solver != HFCR_SOLVER_FP64) c->opt.solver = HFCR_SOLVER_MIXED;
         if (c->opt.roles != HFCR_ROLES_BOTH) c->opt.roles = HFCR_ROLES_ALTERNATE;
+        if (c->opt.diffuse_rings < 0 || c->opt.diffuse_sweeps < 0 || c->opt.diffuse_rings > 1024 ||
+            c->opt.diffuse_sweeps > 100000) {
+            delete c;
+            set_noctx_error("hfcr_create: diffuse_rings must be in [0, 1024] and diffuse_sweeps in [0, 100000]");
+            return HFCR_ERR_ARG;
+        }
     }
     cudaGetDevice(&c->device);
     *out = c;
@@ -707,6 +769,17 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(dalloc(&ctx->skeys_alt, P));
     CK(dalloc(&ctx->sflags, P));
     CK(dalloc(&ctx->stencils, P));
+    {
+        const size_t V = (size_t)max_verts;
+        for (int i = 0; i < 2; ++i) {
+            CK(dalloc(&ctx->adj_ptr[i], V + 1));
+            CK(dalloc(&ctx->adj_nbr[i], 2 * E3));
+        }
+        CK(dalloc(&ctx->adj_cur, V));
+        CK(dalloc(&ctx->field, 6 * V));
+        CK(dalloc(&ctx->field_alt, 6 * V));
+        CK(dalloc(&ctx->ring, 2 * V));
+    }
     SolveBuffers &sb = ctx->sb;
     sb.cap_k = (int)P;
     CK(dalloc(&sb.ids_raw, P));
@@ -889,6 +962,34 @@ hfcr_status hfcr_respond(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     return HFCR_OK;
 }
 
+hfcr_status hfcr_diffuse(hfcr_ctx *ctx, const hfcr_mesh *M, double *dx, double *dy, double *dz,
+                         int32_t rings, int32_t sweeps, void *stream) {
+    if (!ctx) return HFCR_ERR_ARG;
+    hfcr_status st = check_mesh(ctx, M, "M");
+    if (st) return st;
+    if (rings < 0 || sweeps < 0 || rings > 1024 || sweeps > 100000)
+        return fail(ctx, HFCR_ERR_ARG, "hfcr_diffuse: rings must be in [0, 1024], sweeps in [0, 100000]");
+    if (M->n_verts > 0 && (!dx || !dy || !dz))
+        return fail(ctx, HFCR_ERR_ARG, "hfcr_diffuse: NULL displacement array");
+    if (M->n_verts == 0 || rings == 0 || sweeps == 0) return HFCR_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = reset_words(ctx, s))) return st;
+    const int *e = M->edges;
+    int ne = M->n_edges;
+    if (!e && M->n_tris > 0 && (st = mesh_edges(ctx, M, 0, &e, &ne, s))) return st;
+    build_adjacency(e, e ? ne : 0, M->n_verts, ctx->adj_ptr[0], ctx->adj_nbr[0], ctx->adj_cur,
+                    ctx->sort, ctx->d_status, s);
+    field_from_soa(dx, dy, dz, M->n_verts, ctx->field, s);
+    DiffMeshArgs a, none;
+    a.ptr = ctx->adj_ptr[0]; a.nbr = ctx->adj_nbr[0]; a.inv_mass = M->inv_mass; a.n = M->n_verts;
+    const double *u = diffuse_field(a, none, ctx->field, ctx->field_alt, ctx->ring, rings, sweeps, s);
+    field_to_soa(u, M->n_verts, dx, dy, dz, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return device_status(ctx, *ctx->h_status);
+}
+
 static hfcr_status resolve_impl(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, const int *segs,
                                 int nseg, double d, int32_t max_iters, hfcr_resolve_info *info,
                                 void *stream) {
@@ -917,6 +1018,7 @@ static hfcr_status resolve_impl(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, const
     if ((st = reset_words(ctx, s))) return st;
     DetectPlan pl;
     if ((st = plan_detect(ctx, A, B, has0, has1, pl, s, segs, nseg))) return st;
+    if (diffusing(ctx) && (st = prepare_diffusion(ctx, A, B, pl, s))) return st;
     bool built[2] = {false, false};
     int quiet = 0;
     for (int it = 0; it < max_iters; ++it) {

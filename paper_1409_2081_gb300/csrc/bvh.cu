@@ -107,22 +107,18 @@ __device__ __forceinline__ float hi_f(float v) { return v; }
 __device__ __forceinline__ float lo_f(double v) { return __double2float_rd(v); }
 __device__ __forceinline__ float hi_f(double v) { return __double2float_ru(v); }
 
-// per-block min/max of face centroids (float32 approximations suffice: the
-// codes only order the leaves)
+// per-block min/max of the vertex positions (coalesced; they contain every
+// face centroid, and float32 approximations suffice: the codes only order
+// the leaves)
 template <typename T>
-__global__ void k_centroid_bounds(const T *x, const T *y, const T *z, int nv, const int *tris,
-                                  int nt, float *part, uint32_t *st) {
+__global__ void k_vertex_bounds(const T *x, const T *y, const T *z, int nv, float *part) {
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-        T a[3], b[3], c[3];
-        load3(x, y, z, chk(tris[3 * t], nv, st), a);
-        load3(x, y, z, chk(tris[3 * t + 1], nv, st), b);
-        load3(x, y, z, chk(tris[3 * t + 2], nv, st), c);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+        const float c[3] = {(float)x[v], (float)y[v], (float)z[v]};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            float m = (float)((a[k] + b[k] + c[k]) / (T)3);
-            lo[k] = fminf(lo[k], m);
-            hi[k] = fmaxf(hi[k], m);
+            lo[k] = fminf(lo[k], c[k]);
+            hi[k] = fmaxf(hi[k], c[k]);
         }
     }
     __shared__ float s[6][32];
@@ -145,12 +141,32 @@ __global__ void k_centroid_bounds(const T *x, const T *y, const T *z, int nv, co
     }
 }
 
-__global__ void k_bounds_final(const float *part, int nb, float *bounds) {
-    int k = threadIdx.x;
-    if (k >= 6) return;
-    float v = part[k];
-    for (int i = 1; i < nb; ++i) v = k < 3 ? fminf(v, part[6 * i + k]) : fmaxf(v, part[6 * i + k]);
-    bounds[k] = v;
+// the nb per-block partials folded by one CTA of 256 threads
+__global__ void __launch_bounds__(256) k_bounds_final(const float *part, int nb, float *bounds) {
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(lo[k], part[6 * i + k]);
+            hi[k] = fmaxf(hi[k], part[6 * i + 3 + k]);
+        }
+    __shared__ float sh[6][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+        if (lane == 0) { sh[k][w] = lo[k]; sh[3 + k][w] = hi[k]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        float v = sh[k][0];
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) v = k < 3 ? fminf(v, sh[k][q]) : fmaxf(v, sh[k][q]);
+        bounds[k] = v;
+    }
 }
 
 __device__ __forceinline__ unsigned spread10(unsigned v) {
@@ -326,7 +342,7 @@ void build_edges(const int *tris, int n_tris, int n_verts, int *edges_out, int *
     bool flip = radix_sort_u64(keys, nullptr, keys_alt, nullptr, n, 2 * vb, t, s);
     unsigned long long *sorted = flip ? keys_alt : keys;
     { k_unique_flags<<<(n + 255) / 256, 256, 0, s>>>(sorted, n, flags); note_launch(); }
-    scan_flags_dev(flags, nullptr, n, d_count, s);
+    scan_flags_dev(flags, nullptr, n, d_count, t, s);
     { k_write_edges<<<(n + 255) / 256, 256, 0, s>>>(sorted, flags, n, vb, edges_out); note_launch(); }
 }
 
@@ -347,17 +363,19 @@ void bvh_build(Bvh &b, const hfcr_mesh &m, const int *segs, int col, int nseg, S
     b.nseg = nseg;
     if (n <= 0) return;
     int nb = (n + 255) / 256;
-    int nbb = nb < 1024 ? nb : 1024;
+    int vbk = (nv + 255) / 256;
+    if (vbk > 1024) vbk = 1024;
+    if (vbk < 1) vbk = 1;
     if (m.dtype == HFCR_F32) {
         const float *x = (const float *)m.x, *y = (const float *)m.y, *z = (const float *)m.z;
-        { k_centroid_bounds<float><<<nbb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds_part, d_status); note_launch(); }
-        { k_bounds_final<<<1, 32, 0, s>>>(b.bounds_part, nbb, b.bounds); note_launch(); }
+        { k_vertex_bounds<float><<<vbk, 256, 0, s>>>(x, y, z, nv, b.bounds_part); note_launch(); }
+        { k_bounds_final<<<1, 256, 0, s>>>(b.bounds_part, vbk, b.bounds); note_launch(); }
         { k_morton<float><<<nb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds, segs, col, nseg, b.keys,
                                            b.leaf_face, d_status); note_launch(); }
     } else {
         const double *x = (const double *)m.x, *y = (const double *)m.y, *z = (const double *)m.z;
-        { k_centroid_bounds<double><<<nbb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds_part, d_status); note_launch(); }
-        { k_bounds_final<<<1, 32, 0, s>>>(b.bounds_part, nbb, b.bounds); note_launch(); }
+        { k_vertex_bounds<double><<<vbk, 256, 0, s>>>(x, y, z, nv, b.bounds_part); note_launch(); }
+        { k_bounds_final<<<1, 256, 0, s>>>(b.bounds_part, vbk, b.bounds); note_launch(); }
         { k_morton<double><<<nb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds, segs, col, nseg, b.keys,
                                             b.leaf_face, d_status); note_launch(); }
     }

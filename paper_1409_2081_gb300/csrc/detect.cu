@@ -354,11 +354,12 @@ void stencil_keys(const MeshPair &mp, const hfcr_pair *pairs, const int *d_n, in
 }
 
 void stencil_unique(const unsigned long long *keys, const int *d_n, int cap, int vert_bits,
-                    int face_bits, unsigned *flags, hfcr_stencil *out, int *d_k, cudaStream_t s) {
+                    int face_bits, unsigned *flags, hfcr_stencil *out, int *d_k, SortTemp &t,
+                    cudaStream_t s) {
     if (cap <= 0) return;
     int nb = (cap + 255) / 256;
     { k_stencil_flags<<<nb, 256, 0, s>>>(keys, d_n, cap, flags); note_launch(); }
-    scan_flags_dev(flags, d_n, cap, d_k, s);
+    scan_flags_dev(flags, d_n, cap, d_k, t, s);
     { k_stencil_write<<<nb, 256, 0, s>>>(keys, flags, d_n, cap, vert_bits, face_bits, out); note_launch(); }
 }
 

@@ -75,7 +75,7 @@ struct Bvh {
     int *parent = nullptr;      // [2 * cap - 1]: parent of internal i at [i], of leaf j at [cap - 1 + j]
     unsigned *flags = nullptr;  // [cap - 1] arrival counters of the refit
     int *leaf_face = nullptr;   // [cap]
-    void *leaf_tri = nullptr;   // [cap] packed triangles
+    void *leaf_tri = nullptr;   // [cap] packed triangles in leaf order
     unsigned long long *keys = nullptr;      // [cap] (segment, Morton code) sort keys
     unsigned long long *keys_alt = nullptr;
     int *vals_alt = nullptr;
@@ -110,7 +110,8 @@ int sort_blocks_for(int n);
 
 // Exclusive scan of n unsigned flags (in place), total written to *d_total.
 // n read from a device word, cap bounds it.
-void scan_flags_dev(unsigned *flags, const int *d_n, int cap, int *d_total, cudaStream_t s);
+void scan_flags_dev(unsigned *flags, const int *d_n, int cap, int *d_total, SortTemp &t,
+                    cudaStream_t s);
 
 // ---- topology ----
 // Unique sorted edges of a triangle list.  Scratch: keys/keys_alt of
@@ -171,7 +172,8 @@ void stencil_keys(const MeshPair &mp, const hfcr_pair *pairs, const int *d_n, in
                   DevStats *stats, uint32_t *d_status, cudaStream_t s);
 // sorted keys -> unique stencils, count to d_k
 void stencil_unique(const unsigned long long *keys, const int *d_n, int cap, int vert_bits,
-                    int face_bits, unsigned *flags, hfcr_stencil *out, int *d_k, cudaStream_t s);
+                    int face_bits, unsigned *flags, hfcr_stencil *out, int *d_k, SortTemp &t,
+                    cudaStream_t s);
 
 // ---- solver ----
 struct SolveBuffers {
@@ -240,9 +242,31 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
            cudaStream_t s);
 // dx = -M^-1 J^T lambda for the touched vertices; apply to positions (apply=1)
 // or write full dx arrays (zeroed first).
+// apply 1: x += dx; 0: dx to dxA / dxB (three arrays each, mesh dtype);
+// 2: dx to the float64 field dxA[0] (AoS over global vertex ids)
 void displacement(const MeshPair &mp, int cap, SolveBuffers &sb, int apply, void *const *dxA,
                   void *const *dxB, cudaStream_t s);
 
 int bits_for(long long n);  // smallest b with n <= 2^b (at least 1)
+
+// diffusion of displacement vectors (diffuse.cu)
+struct DiffMeshArgs {
+    const int *ptr = nullptr, *nbr = nullptr;  // vertex adjacency CSR, ascending neighbours
+    const float *inv_mass = nullptr;           // null: no kinematic vertices
+    int n = 0;                                 // vertices
+};
+// CSR of an edge list: ptr [nv + 1], nbr [2 ne], cur [nv] scratch
+void build_adjacency(const int *edges, int ne, int nv, int *ptr, int *nbr, int *cur, SortTemp &t,
+                     uint32_t *d_status, cudaStream_t s);
+// rings and sweeps over u (AoS float64 over A's then B's vertices); returns
+// the buffer holding the result (u or u_alt); ring [a.n + b.n] gets the
+// ring distances (0: moved, rings + 1: beyond)
+const double *diffuse_field(const DiffMeshArgs &a, const DiffMeshArgs &b, double *u, double *u_alt,
+                            int *ring, int rings, int sweeps, cudaStream_t s);
+void apply_field(const hfcr_mesh &A, const hfcr_mesh &B, const int *ring, int rings,
+                 const double *u, cudaStream_t s);
+void field_from_soa(const double *x, const double *y, const double *z, int n, double *u,
+                    cudaStream_t s);
+void field_to_soa(const double *u, int n, double *x, double *y, double *z, cudaStream_t s);
 
 }  // namespace hfcr

@@ -649,44 +649,106 @@ __global__ void k_group_inverse(const int *d_ng, const int *gst, const int4 *vid
     }
 }
 
-// One float32 CG run per impact zone of the mixed solver (rhs = the float64
-// residual restricted to the zone, lam += x on exit).  Zones with at least
-// `big_min` stencils go to the launch with is_big = 1 (1024 threads, all of
-// shared memory), the others to is_big = 0 (256 threads, a quarter); a zone
-// whose residual is already below rel_tol |b| / sqrt(#zones) is skipped.
+// sum over the block, identical in every thread: each warp folds its values
+// with a butterfly and keeps lane 0's result, and every thread adds the warp
+// results in warp order
+__device__ __forceinline__ double block_sum_uniform(double x, double *redd) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    x = __shfl_sync(0xffffffffu, x, 0);
+    if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = x;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += redd[w];
+    __syncthreads();
+    return s;
+}
+
+// float64 residual r = b - J M^-1 J^T lam of one zone (the float64 normals;
+// Eq. 7), written to v.r in float32 as the next right-hand side.  The
+// vertex half goes through u64 (global scratch, this zone's rows only).
+// Returns |r|^2, identical in every thread.
+__device__ __forceinline__ double zone_residual(const CgView &v, int k, int U, int s0, int j0,
+                                                const double4_32a *n64, const double *b64,
+                                                const double *lam, double *u64, double *redd) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const double third = 1.0 / 3.0;
+    for (int j = tid; j < U; j += nt) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        const int e1 = v.seg[j + 1] - v.eoff;
+        for (int e = v.seg[j] - v.eoff; e < e1; ++e) {
+            const int c = v.cval[e] - v.coff;
+            const int sl = c >> 2;
+            const double ps = ((c & 3) ? -third : 1.0) * lam[s0 + sl];
+            const double4_32a n = n64[s0 + sl];
+            a0 += ps * n.x;
+            a1 += ps * n.y;
+            a2 += ps * n.z;
+        }
+        const double w = (double)v.winv[j];
+        double *u = u64 + 3 * (size_t)(j0 + j);
+        u[0] = w * a0;
+        u[1] = w * a1;
+        u[2] = w * a2;
+    }
+    __syncthreads();
+    double rr = 0.0;
+    for (int t = tid; t < k; t += nt) {
+        const int4 g = v.vidx[t];
+        const double *ux = u64 + 3 * (size_t)(j0 + g.x - v.voff);
+        const double *ua = u64 + 3 * (size_t)(j0 + g.y - v.voff);
+        const double *ub = u64 + 3 * (size_t)(j0 + g.z - v.voff);
+        const double *uc = u64 + 3 * (size_t)(j0 + g.w - v.voff);
+        const double4_32a n = n64[s0 + t];
+        const double d0 = ux[0] - (ua[0] + ub[0] + uc[0]) * third;
+        const double d1 = ux[1] - (ua[1] + ub[1] + uc[1]) * third;
+        const double d2 = ux[2] - (ua[2] + ub[2] + uc[2]) * third;
+        const double r = b64[s0 + t] - (n.x * d0 + n.y * d1 + n.z * d2);
+        v.r[t] = (float)r;
+        rr += r * r;
+    }
+    return block_sum_uniform(rr, redd);
+}
+
+// The mixed solver, one CTA per impact zone (zones with at least `big_min`
+// stencils go to the launch with is_big = 1: 1024 threads and all of shared
+// memory; the others to is_big = 0: 256 threads and a quarter).  Per zone:
+// lam = 0, r = b; then rounds of iterative refinement, each a float32 PCG
+// solve of A x = r (relative tolerance tol), lam += x and the float64
+// residual, until |r|^2 <= rel_tol^2 |b_zone|^2 or max_refine rounds.
+// Meeting that in every zone meets |r| <= rel_tol |b| for the whole
+// system, whose matrix is block-diagonal by zone.  The zone's final |r|^2
+// and |b|^2 go to zres[z] and zbb[z].
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
     const int *d_nz, const int *zs, const int *zv, int big_min, int is_big, const int *seg_g,
-    const int *cval_g, const float *winv_g, const float4 *n32, const int4 *vidx_g,
-    const float4 *pinv_g, const int *gst_g, const int *zg, const double *rhs64, double *lam,
-    float *x_g, float *r_g, float *p_g, float *s_g, float *w_g, float *z_g, float *u_g, int cap4,
-    int maxit, double tol, double rel_tol, const double *bnorm2, int *ctl, int smem_bytes) {
+    const int *cval_g, const float *winv_g, const float4 *n32, const double4_32a *n64,
+    const int4 *vidx_g, const float4 *pinv_g, const int *gst_g, const int *zg, const double *b64,
+    double *lam, double *u64, double *zres, double *zbb, float *x_g, float *r_g, float *p_g,
+    float *s_g, float *w_g, float *z_g, float *u_g, int maxit, int max_refine, double tol,
+    double rel_tol, int *ctl, int smem_bytes) {
     extern __shared__ float4 smem4[];
     __shared__ float red[96];
     __shared__ double redd[THREADS / 32];
-    if (ctl[0]) return;
     const int nz = *d_nz, tid = threadIdx.x, nt = blockDim.x;
-    const double zone_tol2 = rel_tol * rel_tol * (*bnorm2) / (double)(nz > 0 ? nz : 1);
     for (int z = blockIdx.x; z < nz; z += gridDim.x) {
         const int s0 = zs[z], k = zs[z + 1] - s0;
         const int j0 = zv[z], U = zv[z + 1] - j0;
         if ((k >= big_min) != (is_big != 0)) continue;
-        // skip a zone that already meets its share of the tolerance
-        double rz = 0.0;
-        for (int t = tid; t < k; t += nt) rz += rhs64[s0 + t] * rhs64[s0 + t];
-#pragma unroll
-        for (int o = 16; o; o >>= 1) rz += __shfl_xor_sync(0xffffffffu, rz, o);
-        if ((tid & 31) == 0) redd[tid >> 5] = rz;
-        __syncthreads();
-        double rzs = 0.0;
-        for (int w = 0; w < nt / 32; ++w) rzs += redd[w];
-        __syncthreads();
-        if (rzs <= 0.5 * zone_tol2) continue;
+        double bb = 0.0;
+        for (int t = tid; t < k; t += nt) {
+            const double bv = b64[s0 + t];
+            bb += bv * bv;
+            lam[s0 + t] = 0.0;
+        }
+        bb = block_sum_uniform(bb, redd);
+        const double target = rel_tol * rel_tol * bb;
         const int e0 = seg_g[j0];
         const int g0 = zg[z], G = zg[z + 1] - g0;
         const long long need = 92ll * k + 24ll * U + 4ll * G + 32;
         const bool in_smem = need <= smem_bytes;
-        int it;
+        double rr = bb;
+        int its = 0, rounds = 0;
         // the two paths are instantiated separately so that the shared-memory
         // one sees pointers derived only from the shared array (LDS/STS, not
         // generic loads)
@@ -709,6 +771,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
                 vidx[t] = make_int4(g.x - j0, g.y - j0, g.z - j0, g.w - j0);
                 n4[t] = n32[s0 + t];
                 pinv[t] = pinv_g[s0 + t];
+                v.r[t] = (float)b64[s0 + t];
             }
             for (int g = tid; g <= G; g += nt) gst[g] = gst_g[g0 + g] - s0;
             v.pinv = pinv; v.gst = gst; v.G = G; v.goff = 0;
@@ -718,15 +781,19 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
             v.n4 = n4;
             v.vidx = vidx; v.seg = seg; v.cval = cval; v.winv = winv;
             v.voff = 0; v.coff = 0; v.eoff = 0;
-            for (int t = tid; t < k; t += nt) {
-                v.r[t] = (float)rhs64[s0 + t];
-                v.p[t] = 0.f;
-                v.sv[t] = 0.f;
-                v.x[t] = 0.f;
+            while (rr > target && rounds < max_refine) {
+                for (int t = tid; t < k; t += nt) {
+                    v.p[t] = 0.f;
+                    v.sv[t] = 0.f;
+                    v.x[t] = 0.f;
+                }
+                __syncthreads();
+                its += cg_cg_loop(v, k, U, maxit, (float)tol, red);
+                for (int t = tid; t < k; t += nt) lam[s0 + t] += (double)v.x[t];
+                __syncthreads();
+                rr = zone_residual(v, k, U, s0, j0, n64, b64, lam, u64, redd);
+                ++rounds;
             }
-            __syncthreads();
-            it = cg_cg_loop(v, k, U, maxit, (float)tol, red);
-            for (int t = tid; t < k; t += nt) lam[s0 + t] += (double)v.x[t];
         } else {
             CgView v;
             v.r = r_g + s0; v.p = p_g + s0; v.x = x_g + s0; v.sv = s_g + s0; v.w = w_g + s0;
@@ -736,54 +803,53 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
             v.pinv = pinv_g + s0; v.gst = gst_g + g0; v.G = G; v.goff = s0;
             v.vidx = vidx_g + s0; v.seg = seg_g + j0; v.cval = cval_g; v.winv = winv_g + j0;
             v.voff = j0; v.coff = 4 * s0; v.eoff = 0;
-            for (int t = tid; t < k; t += nt) {
-                v.r[t] = (float)rhs64[s0 + t];
-                v.p[t] = 0.f;
-                v.sv[t] = 0.f;
-                v.x[t] = 0.f;
+            for (int t = tid; t < k; t += nt) v.r[t] = (float)b64[s0 + t];
+            while (rr > target && rounds < max_refine) {
+                for (int t = tid; t < k; t += nt) {
+                    v.p[t] = 0.f;
+                    v.sv[t] = 0.f;
+                    v.x[t] = 0.f;
+                }
+                __syncthreads();
+                its += cg_cg_loop(v, k, U, maxit, (float)tol, red);
+                for (int t = tid; t < k; t += nt) lam[s0 + t] += (double)v.x[t];
+                __syncthreads();
+                rr = zone_residual(v, k, U, s0, j0, n64, b64, lam, u64, redd);
+                ++rounds;
             }
-            __syncthreads();
-            it = cg_cg_loop(v, k, U, maxit, (float)tol, red);
-            for (int t = tid; t < k; t += nt) lam[s0 + t] += (double)v.x[t];
         }
         if (tid == 0) {
-            atomicAdd(&ctl[1], it);
-            atomicAdd(&ctl[2], 1);
+            zres[z] = rr;
+            zbb[z] = bb;
+            atomicAdd(&ctl[1], its);
+            atomicAdd(&ctl[2], rounds);
+            atomicMax(&ctl[3], rounds);
             atomicOr(&ctl[4], in_smem ? 1 : 2);
         }
         __syncthreads();  // shared memory is reused by the next zone
     }
 }
 
-// r = b, lam = 0 (the first residual of the mixed solver); the last block
-// (ticket counter) sums the |b|^2 partials in block order into dres[1],
-// records |r| / |b| = 1 in dres[0] and sets ctl[0] when b = 0.
-__global__ void k_init_res(const int *d_k, const double *b, double *lam, double *r, double *red,
-                           int *ctl, unsigned *ticket, double *dres) {
-    __shared__ double sh[33];
-    __shared__ bool last;
-    const int k = *d_k;
-    double bb = 0.0;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < k; s += gridDim.x * blockDim.x) {
-        lam[s] = 0.0;
-        r[s] = b[s];
-        bb += b[s] * b[s];
+// |r| / |b| of the whole system from the zones' |r|^2 and |b|^2 (fixed
+// summation order) to dres[0], |b|^2 to dres[1]; ctl[0] = converged
+__global__ void __launch_bounds__(256) k_zone_final(const int *d_nz, const double *zres,
+                                                    const double *zbb, double rel_tol,
+                                                    double *dres, int *ctl) {
+    __shared__ double redd[8];
+    const int nz = *d_nz;
+    double R = 0.0, Bn = 0.0;
+    for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+        R += zres[z];
+        Bn += zbb[z];
     }
-    bb = block_sum(bb, sh);
+    R = block_sum_uniform(R, redd);
+    Bn = block_sum_uniform(Bn, redd);
     if (threadIdx.x == 0) {
-        red[RES_BLOCKS + blockIdx.x] = bb;
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        const double rel = Bn > 0.0 ? sqrt(R / Bn) : (R > 0.0 ? INFINITY : 0.0);
+        dres[0] = rel;
+        dres[1] = Bn;
+        ctl[0] = rel <= rel_tol;
     }
-    __syncthreads();
-    if (!last || threadIdx.x != 0) return;
-    __threadfence();
-    double Bn = 0;
-    for (int i = 0; i < (int)gridDim.x; ++i) Bn += __ldcg(red + RES_BLOCKS + i);
-    dres[0] = Bn > 0 ? 1.0 : 0.0;
-    dres[1] = Bn;
-    if (!(Bn > 0)) ctl[0] = 1;
-    *ticket = 0;
 }
 
 // float64 residual, vertex half: u = M^-1 J^T lam
@@ -868,7 +934,9 @@ __global__ void k_init_lam(const int *d_k, const double *b, double *lam, double 
     }
 }
 
-// displacement of the touched vertices: dx = -M^-1 J^T lam (float64)
+// displacement of the touched vertices: dx = -M^-1 J^T lam (float64).
+// apply 1: added to the positions; 0: written to the caller's arrays (mesh
+// dtype); 2: written to the float64 field dA0 (x, y, z per global vertex)
 __global__ void k_displace(const int *d_U, const int *seg, const int *cval, const float *winv,
                            const double4_32a *n64, const double *lam, const int *gvert, hfcr_mesh A,
                            hfcr_mesh B, int apply, void *dA0, void *dA1, void *dA2, void *dB0,
@@ -889,6 +957,13 @@ __global__ void k_displace(const int *d_U, const int *seg, const int *cval, cons
         double w = (double)winv[j];
         double dx[3] = {-w * a0, -w * a1, -w * a2};
         int g = gvert[j];
+        if (apply == 2) {  // into the float64 field of the diffusion (AoS, global ids)
+            double *f = (double *)dA0 + 3 * (size_t)g;
+            f[0] = dx[0];
+            f[1] = dx[1];
+            f[2] = dx[2];
+            continue;
+        }
         const bool inA = g < A.n_verts;
         const hfcr_mesh &m = inA ? A : B;
         int lv = inA ? g : g - A.n_verts;
@@ -951,7 +1026,7 @@ void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers 
     unsigned *ck1 = flip ? sb.ckey_alt : sb.ckey;
     int *cv1 = flip ? sb.cval_alt : sb.cval;
     { k_csr_flags<<<nb, 256, 0, s>>>(ck1, d_k, cap, sb.cflag, d_n4); note_launch(); }
-    scan_flags_dev(sb.cflag, d_n4, n4, sb.d_U, s);
+    scan_flags_dev(sb.cflag, d_n4, n4, sb.d_U, t, s);
     { k_csr_build<<<nb, 256, 0, s>>>(ck1, cv1, sb.cflag, d_k, cap, mp.A.n_verts, mp.A.inv_mass,
                                    mp.B.inv_mass, sb.vidx, sb.seg, sb.gvert, sb.winv); note_launch(); }
     // impact zones and the zone-ordered rows.  The 64-bit scratch arrays
@@ -967,7 +1042,7 @@ void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers 
     unsigned *zl = zflip ? zlab_alt : zlab;
     int *zr = zflip ? zsrc_alt : zsrc;
     { k_zone_flags<<<gb, 256, 0, s>>>(d_k, zl, sb.cflag); note_launch(); }
-    scan_flags_dev(sb.cflag, d_k, cap, sb.d_nz, s);
+    scan_flags_dev(sb.cflag, d_k, cap, sb.d_nz, t, s);
     int *pos_of = sb.parent;  // the forest is no longer needed
     { k_zone_gather<<<gb, 256, 0, s>>>(d_k, zl, zr, sb.cflag, sb.ids_raw, sb.n64_raw, sb.n32_raw,
                                      sb.b_raw, sb.ids, sb.n64, sb.n32, sb.b, sb.szone, sb.zs,
@@ -980,13 +1055,13 @@ void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers 
     unsigned *zk2 = flip2 ? k2_alt : k2;
     sb.cval_s = flip2 ? v2_alt : v2;
     { k_csr2_flags<<<nb, 256, 0, s>>>(sb.cval_s, sb.ids, d_k, cap, sb.cflag); note_launch(); }
-    scan_flags_dev(sb.cflag, d_n4, n4, sb.d_U, s);
+    scan_flags_dev(sb.cflag, d_n4, n4, sb.d_U, t, s);
     { k_csr2_build<<<nb, 256, 0, s>>>(zk2, sb.cval_s, sb.cflag, sb.ids, d_k, cap, mp.A.n_verts,
                                     mp.A.inv_mass, mp.B.inv_mass, sb.vidx, sb.seg, sb.gvert, sb.winv,
                                     sb.zv, sb.d_nz); note_launch(); }
     // groups of rows sharing x0 and the inverses of their blocks
     { k_group_flags<<<gb, 256, 0, s>>>(d_k, sb.ids, sb.szone, sb.zs, sb.cflag); note_launch(); }
-    scan_flags_dev(sb.cflag, d_k, cap, sb.d_ng, s);
+    scan_flags_dev(sb.cflag, d_k, cap, sb.d_ng, t, s);
     { k_group_build<<<gb, 256, 0, s>>>(d_k, sb.ids, sb.szone, sb.zs, sb.cflag, sb.d_nz, sb.gst,
                                      sb.zg); note_launch(); }
     { k_group_inverse<<<gb, 128, 0, s>>>(sb.d_ng, sb.gst, sb.vidx, sb.n64, sb.winv, sb.pinv); note_launch(); }
@@ -1001,9 +1076,9 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
     int rb = (cap + 255) / 256;
     if (rb > RES_BLOCKS) rb = RES_BLOCKS;
     cudaMemsetAsync(sb.iwork, 0, sizeof(int) * 16, s);
-    { k_init_lam<<<rb, 256, 0, s>>>(d_k, sb.b, sb.lam, sb.r64); note_launch(); }
     if (p.solver == HFCR_SOLVER_FP64) {
         // one float64 run with the whole iteration budget of the mixed solver
+        { k_init_lam<<<rb, 256, 0, s>>>(d_k, sb.b, sb.lam, sb.r64); note_launch(); }
         { k_cg<double><<<1, CG_THREADS, 0, s>>>(1, d_k, sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64,
                                               sb.vidx, sb.b, sb.lam, sb.p64 + 0, sb.r64, sb.p64 + cap,
                                               sb.q64, sb.u64, p.max_cg_iters * p.max_refine,
@@ -1015,30 +1090,24 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
                                           sb.dwork, 0); note_launch(); }
         return;
     }
-    // MIXED: float32 runs per impact zone on the float64 residual (r = b to start)
-    { k_init_res<<<rb, 256, 0, s>>>(d_k, sb.b, sb.lam, sb.r64, sb.red, sb.iwork,
-                                   (unsigned *)(sb.iwork + 12), sb.dwork); note_launch(); }
+    // MIXED: float32 PCG with float64 refinement, each zone to convergence
+    // in its own CTA.  r64 and q64 (float64 scratch of the FP64 solver) hold
+    // the zones' final |r|^2 and |b|^2.
     int zsmall = (cap + 1023) / 1024 * 4;  // blocks of the small-zone launch (grid-stride over zones)
     if (zsmall > 2048) zsmall = 2048;
     int zbig = (cap + ZONE_BIG - 1) / ZONE_BIG;
     if (zbig > 152) zbig = 152;
-    for (int round = 0; round < p.max_refine; ++round) {
-        { k_cg_zone<256><<<zsmall, 256, zone_small_smem, s>>>(
-              sb.d_nz, sb.zs, sb.zv, ZONE_BIG, 0, sb.seg, sb.cval_s, sb.winv, sb.n32, sb.vidx, sb.pinv,
-              sb.gst, sb.zg, sb.r64, sb.lam, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.z32, sb.u32,
-              4 * sb.cap_k, p.max_cg_iters,
-              p.inner_tol, p.rel_tol, sb.dwork + 1, sb.iwork, zone_small_smem); note_launch(); }
-        { k_cg_zone<CG_THREADS><<<zbig, CG_THREADS, fast_smem, s>>>(
-              sb.d_nz, sb.zs, sb.zv, ZONE_BIG, 1, sb.seg, sb.cval_s, sb.winv, sb.n32, sb.vidx, sb.pinv,
-              sb.gst, sb.zg, sb.r64, sb.lam, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.z32, sb.u32,
-              4 * sb.cap_k, p.max_cg_iters,
-              p.inner_tol, p.rel_tol, sb.dwork + 1, sb.iwork, fast_smem); note_launch(); }
-        { k_res_vertex<<<rb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64, sb.lam, sb.u64,
-                                         sb.iwork); note_launch(); }
-        { k_res_stencil<<<rb, 256, 0, s>>>(d_k, sb.vidx, sb.n64, sb.b, sb.u64, sb.r64, sb.red,
-                                          sb.iwork, (unsigned *)(sb.iwork + 12), p.rel_tol,
-                                          sb.dwork, 1); note_launch(); }
-    }
+    { k_cg_zone<256><<<zsmall, 256, zone_small_smem, s>>>(
+          sb.d_nz, sb.zs, sb.zv, ZONE_BIG, 0, sb.seg, sb.cval_s, sb.winv, sb.n32, sb.n64, sb.vidx,
+          sb.pinv, sb.gst, sb.zg, sb.b, sb.lam, sb.u64, sb.r64, sb.q64, sb.x32, sb.r32, sb.p32,
+          sb.q32, sb.w32, sb.z32, sb.u32, p.max_cg_iters, p.max_refine, p.inner_tol, p.rel_tol,
+          sb.iwork, zone_small_smem); note_launch(); }
+    { k_cg_zone<CG_THREADS><<<zbig, CG_THREADS, fast_smem, s>>>(
+          sb.d_nz, sb.zs, sb.zv, ZONE_BIG, 1, sb.seg, sb.cval_s, sb.winv, sb.n32, sb.n64, sb.vidx,
+          sb.pinv, sb.gst, sb.zg, sb.b, sb.lam, sb.u64, sb.r64, sb.q64, sb.x32, sb.r32, sb.p32,
+          sb.q32, sb.w32, sb.z32, sb.u32, p.max_cg_iters, p.max_refine, p.inner_tol, p.rel_tol,
+          sb.iwork, fast_smem); note_launch(); }
+    { k_zone_final<<<1, 256, 0, s>>>(sb.d_nz, sb.r64, sb.q64, p.rel_tol, sb.dwork, sb.iwork); note_launch(); }
 }
 
 void displacement(const MeshPair &mp, int cap, SolveBuffers &sb, int apply, void *const *dxA,

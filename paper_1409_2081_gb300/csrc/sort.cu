@@ -55,13 +55,24 @@ __device__ __forceinline__ void rank_tile(const K *kin, const int *vin, int n, i
     }
 }
 
-template <typename K>
-__global__ void __launch_bounds__(TPB) k_hist(const K *keys, int n, const int *d_n, int shift,
-                                              unsigned *hist, int nblocks) {
+// tiles of the live input: n, or *d_n (clamped to n) when a device count is
+// given.  Returns 0 when the single-CTA kernel sorts the input instead.
+__device__ __forceinline__ int live_tiles(int n, const int *d_n) {
     if (d_n) {
         n = min(n, *d_n);
-        if (n <= SMALL_N) return;  // the single-CTA kernel sorts it
+        if (n <= SMALL_N) return 0;
     }
+    return (n + TILE - 1) / TILE;
+}
+
+// per-tile digit counts, digit-major with rows as long as the live tile
+// count (tiles past the live input neither count nor get scanned)
+template <typename K>
+__global__ void __launch_bounds__(TPB) k_hist(const K *keys, int n, const int *d_n, int shift,
+                                              unsigned *hist) {
+    const int nba = live_tiles(n, d_n);
+    if ((int)blockIdx.x >= nba) return;
+    if (d_n) n = min(n, *d_n);
     __shared__ unsigned h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -71,21 +82,19 @@ __global__ void __launch_bounds__(TPB) k_hist(const K *keys, int n, const int *d
         if (idx < n) atomicAdd(&h[digit_of(keys[idx], shift)], 1u);
     }
     __syncthreads();
-    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    hist[threadIdx.x * nba + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of a[0..m) in place by one CTA of 1024 threads; total to
-// *d_total.  Tiles of 4096: each thread loads 4 consecutive elements
-// (coalesced across the warp), the CTA scans the per-thread sums, and a
-// running carry links the tiles.
-__global__ void __launch_bounds__(1024) k_scan1(unsigned *a, int m, const int *d_m, int *d_total,
-                                               const int *d_gate = nullptr) {
-    if (d_gate && *d_gate <= SMALL_N) return;  // histogram scan of a sort the single CTA handled
-    if (d_m) m = min(m, *d_m);
+// exclusive scan of a[0..m) in place by the calling CTA (NT threads),
+// starting from carry; returns carry + the sum to every thread.  Chunks of 4 NT: each thread loads 4
+// consecutive elements (coalesced across the warp), the CTA scans the
+// per-thread sums, and a running carry links the chunks.
+template <int NT>
+__device__ __forceinline__ unsigned block_scan_excl(unsigned *a, int m, unsigned carry = 0) {
     __shared__ unsigned ws[32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    unsigned carry = 0;
-    for (int base = 0; base < m; base += 4096) {
+    constexpr int NW = NT / 32;
+    for (int base = 0; base < m; base += 4 * NT) {
         const int i0 = base + 4 * t;
         unsigned v[4];
 #pragma unroll
@@ -100,13 +109,13 @@ __global__ void __launch_bounds__(1024) k_scan1(unsigned *a, int m, const int *d
         if (lane == 31) ws[w] = x;
         __syncthreads();
         if (w == 0) {
-            unsigned y = ws[lane];
+            unsigned y = lane < NW ? ws[lane] : 0u;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 unsigned z = __shfl_up_sync(0xffffffffu, y, o);
                 if (lane >= o) y += z;
             }
-            ws[lane] = y;
+            if (lane < NW) ws[lane] = y;
         }
         __syncthreads();
         unsigned e = carry + x - sum + (w ? ws[w - 1] : 0u);
@@ -115,21 +124,103 @@ __global__ void __launch_bounds__(1024) k_scan1(unsigned *a, int m, const int *d
             if (i0 + q < m) a[i0 + q] = e;
             e += v[q];
         }
-        carry += ws[31];
-        __syncthreads();  // ws is rewritten by the next tile
+        carry += ws[NW - 1];
+        __syncthreads();  // ws is rewritten by the next chunk
     }
-    if (t == 0 && d_total) *d_total = (int)carry;
+    return carry;
+}
+
+// exclusive scan of a[0..m) (m clamped to *d_m) by one CTA; total to *d_total
+__global__ void __launch_bounds__(1024) k_scan1(unsigned *a, int m, const int *d_m, int *d_total) {
+    if (d_m) m = min(m, *d_m);
+    unsigned total = block_scan_excl<1024>(a, m);
+    if (threadIdx.x == 0 && d_total) *d_total = (int)total;
+}
+
+// the histogram scan of one pass: CTA d scans digit d's row of tile counts
+// in place and writes the digit's total to tot[d]
+__global__ void __launch_bounds__(TPB) k_scan_rows(unsigned *hist, int n, const int *d_n,
+                                                   unsigned *tot) {
+    const int nba = live_tiles(n, d_n);
+    if (!nba) return;
+    unsigned total = block_scan_excl<TPB>(hist + blockIdx.x * nba, nba);
+    if (threadIdx.x == 0) tot[blockIdx.x] = total;
+}
+
+// Multi-CTA exclusive scan of a[0..m) (m clamped to *d_m), for the flag
+// scans: CTA b owns chunk b of SCAN_CHUNK elements.  The first kernel
+// writes each chunk's sum to part[b]; the second adds up part[0..b) in each
+// CTA (at most a few thousand values) and scans its chunk from there.
+constexpr int SCAN_CHUNK = 4096;
+
+__global__ void __launch_bounds__(TPB) k_scan_reduce(const unsigned *a, int m, const int *d_m,
+                                                     unsigned *part) {
+    __shared__ unsigned ws[TPB / 32];
+    if (d_m) m = min(m, *d_m);
+    const int base = blockIdx.x * SCAN_CHUNK;
+    if (base >= m) return;
+    const int end = min(m, base + SCAN_CHUNK);
+    unsigned x = 0;
+    for (int i = base + threadIdx.x; i < end; i += TPB) x += a[i];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tsum = 0;
+        for (int w = 0; w < TPB / 32; ++w) tsum += ws[w];
+        part[blockIdx.x] = tsum;
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_scan_down(unsigned *a, int m, const int *d_m,
+                                                   const unsigned *part, int *d_total) {
+    __shared__ unsigned ws[TPB / 32];
+    if (d_m) m = min(m, *d_m);
+    const int base = blockIdx.x * SCAN_CHUNK;
+    const int nlive = (m + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    if (m == 0 && blockIdx.x == 0 && threadIdx.x == 0 && d_total) *d_total = 0;
+    if (base >= m) return;
+    unsigned x = 0;
+    for (int i = threadIdx.x; i < (int)blockIdx.x; i += TPB) x += part[i];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = x;
+    __syncthreads();
+    unsigned off = 0;
+    for (int w = 0; w < TPB / 32; ++w) off += ws[w];
+    __syncthreads();  // ws is reused by the scan below
+    const int len = min(m - base, SCAN_CHUNK);
+    unsigned total = block_scan_excl<TPB>(a + base, len, off);
+    if ((int)blockIdx.x == nlive - 1 && threadIdx.x == 0 && d_total) *d_total = (int)total;
 }
 
 template <typename K, bool HV>
 __global__ void __launch_bounds__(TPB) k_scatter(const K *kin, const int *vin, K *kout, int *vout,
                                                  int n, const int *d_n, int shift,
-                                                 const unsigned *hist, int nblocks) {
-    if (d_n) {
-        n = min(n, *d_n);
-        if (n <= SMALL_N) return;
-    }
+                                                 const unsigned *hist, const unsigned *tot) {
+    const int nba = live_tiles(n, d_n);
+    if ((int)blockIdx.x >= nba) return;
+    if (d_n) n = min(n, *d_n);
     __shared__ unsigned wh[TPB / 32][256];
+    __shared__ unsigned dbase[256];
+    __shared__ unsigned wsum[TPB / 32];
+    // first output position of each digit: exclusive scan of the digit totals
+    {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        const unsigned c = tot[threadIdx.x];
+        unsigned x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        unsigned before = 0;
+        for (int q = 0; q < w; ++q) before += wsum[q];
+        dbase[threadIdx.x] = before + x - c;
+    }
     for (int i = threadIdx.x; i < (TPB / 32) * 256; i += TPB) (&wh[0][0])[i] = 0;
     __syncthreads();
     K key[ROUNDS];
@@ -149,7 +240,7 @@ __global__ void __launch_bounds__(TPB) k_scatter(const K *kin, const int *vin, K
     for (int r = 0; r < ROUNDS; ++r) {
         unsigned d = dig[r];
         if (d < 256) {
-            unsigned pos = hist[d * nblocks + blockIdx.x] + wh[warp][d] + rank[r];
+            unsigned pos = dbase[d] + hist[d * nba + blockIdx.x] + wh[warp][d] + rank[r];
             kout[pos] = key[r];
             if (HV) vout[pos] = val[r];
         }
@@ -240,13 +331,15 @@ bool radix_sort_impl(K *k0, int *v0, K *k1, int *v1, int n, const int *d_n, int 
         if (n <= SMALL_N) return passes & 1;
     }
     int nb = (n + TILE - 1) / TILE;
+    // the digit totals sit in the spare row after the largest histogram
+    unsigned *tot = t.hist + 256 * (size_t)(t.max_blocks - 1);
     K *kin = k0, *kout = k1;
     int *vin = v0, *vout = v1;
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
-        { k_hist<K><<<nb, TPB, 0, s>>>(kin, n, d_n, shift, t.hist, nb); note_launch(); }
-        { k_scan1<<<1, 1024, 0, s>>>(t.hist, 256 * nb, nullptr, nullptr, d_n); note_launch(); }
-        { k_scatter<K, HV><<<nb, TPB, 0, s>>>(kin, vin, kout, vout, n, d_n, shift, t.hist, nb); note_launch(); }
+        { k_hist<K><<<nb, TPB, 0, s>>>(kin, n, d_n, shift, t.hist); note_launch(); }
+        { k_scan_rows<<<256, TPB, 0, s>>>(t.hist, n, d_n, tot); note_launch(); }
+        { k_scatter<K, HV><<<nb, TPB, 0, s>>>(kin, vin, kout, vout, n, d_n, shift, t.hist, tot); note_launch(); }
         K *tk = kin; kin = kout; kout = tk;
         int *tv = vin; vin = vout; vout = tv;
     }
@@ -282,8 +375,15 @@ bool radix_sort_u32_dev(unsigned *k0, int *v0, unsigned *k1, int *v1, const int 
     return radix_sort_impl<unsigned, true>(k0, v0, k1, v1, cap, d_n, bits, t, s);
 }
 
-void scan_flags_dev(unsigned *flags, const int *d_n, int cap, int *d_total, cudaStream_t s) {
-    { k_scan1<<<1, 1024, 0, s>>>(flags, cap, d_n, d_total); note_launch(); }
+void scan_flags_dev(unsigned *flags, const int *d_n, int cap, int *d_total, SortTemp &t,
+                    cudaStream_t s) {
+    if (cap <= SCAN_CHUNK) {
+        { k_scan1<<<1, 1024, 0, s>>>(flags, cap, d_n, d_total); note_launch(); }
+        return;
+    }
+    const int nc = (cap + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    { k_scan_reduce<<<nc, TPB, 0, s>>>(flags, cap, d_n, t.hist); note_launch(); }
+    { k_scan_down<<<nc, TPB, 0, s>>>(flags, cap, d_n, t.hist, d_total); note_launch(); }
 }
 
 int bits_for(long long n) {

@@ -1,0 +1,144 @@
+"""Diffusion of displacement vectors (Sec. 5) on the GPU against the oracle.
+
+hfcr_diffuse runs the same sweeps as oracle.diffuse in the same float64
+summation order, so on the same input field the results are bit-identical.
+Inside hfcr_resolve the field comes from the GPU's own minimizer; there the
+check is the oracle's response + diffusion on the GPU's positions before the
+iteration, within the solver tolerance, and exact detection on the positions
+after it."""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+from gpu_util import dev_mesh, detect, positions
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_2081_gb300 import api as a
+    a.lib()
+    return a
+
+
+def _field(n, moved, rng, scale=1e-3):
+    dx = np.zeros((n, 3))
+    dx[moved] = rng.normal(size=(len(moved), 3)) * scale
+    return dx
+
+
+def _gpu_diffuse(api, ctx, M, dx, R, S):
+    import torch
+    t = [torch.tensor(np.ascontiguousarray(dx[:, c]), dtype=torch.float64, device="cuda:0")
+         for c in range(3)]
+    ctx.hfcr_diffuse(M, t, R, S)
+    return np.stack([x.cpu().numpy() for x in t], 1)
+
+
+@pytest.mark.parametrize("kind", ["cloth", "sphere", "torus"])
+def test_diffuse_bit_exact(api, kind):
+    rng = np.random.default_rng({"cloth": 1, "sphere": 2, "torus": 3}[kind])
+    if kind == "cloth":
+        V, T = meshgen.cloth(97, 2.0)           # 9,409 vertices: a ragged tail of the 256-thread grid
+    elif kind == "sphere":
+        V, T = meshgen.icosphere(4, 1.0)
+    else:
+        V, T = meshgen.torus(61, 29, 1.0, 0.3)
+    n = len(V)
+    ctx = api.Context()
+    ctx.hfcr_reserve(n, len(T), 16)
+    for edges in (False, True):                 # the caller's edge list, or derived from the faces
+        M, _ = dev_mesh(api, V, T, False, np.float32, edges=edges)
+        for R, S in ((1, 1), (4, 8), (7, 33)):
+            dx = _field(n, rng.choice(n, 40, replace=False), rng)
+            got = _gpu_diffuse(api, ctx, M, dx, R, S)
+            ref = oracle.diffuse(dx, oracle.edges(T), R, S)
+            assert np.array_equal(got, ref), (kind, edges, R, S)
+
+
+def test_diffuse_kinematic_vertices_and_disabled(api):
+    rng = np.random.default_rng(9)
+    V, T = meshgen.cloth(40, 1.0)
+    n = len(V)
+    moved = rng.choice(n, 12, replace=False)
+    w = np.ones(n, np.float32)
+    fixed = rng.choice(np.setdiff1d(np.arange(n), moved), 150, replace=False)
+    w[fixed] = 0.0
+    ctx = api.Context()
+    ctx.hfcr_reserve(n, len(T), 16)
+    M, _ = dev_mesh(api, V, T, False, np.float32, inv_mass=w)
+    dx = _field(n, moved, rng)
+    got = _gpu_diffuse(api, ctx, M, dx, 5, 12)
+    ref = oracle.diffuse(dx, oracle.edges(T), 5, 12, w == 0)
+    assert np.array_equal(got, ref) and np.all(got[fixed] == 0)
+    for R, S in ((0, 5), (5, 0)):
+        assert np.array_equal(_gpu_diffuse(api, ctx, M, dx, R, S), dx)
+    # an all-zero field stays zero
+    assert np.all(_gpu_diffuse(api, ctx, M, np.zeros((n, 3)), 3, 3) == 0)
+    with pytest.raises(api.HfcrError):
+        _gpu_diffuse(api, ctx, M, dx, -1, 3)
+
+
+def _resolve_step_parity(api, sc, R, S, iters, d=1e-4):
+    """One repair iteration at a time with diffusion: the GPU's pairs equal
+    the oracle's on the GPU positions (exact), and the GPU's new positions
+    equal the oracle's response + diffusion from the same positions within
+    the solver tolerance (a few float32 ulps)."""
+    A, _ = dev_mesh(api, sc.A.V, sc.A.T, sc.A.oriented, np.float32)
+    B, _ = dev_mesh(api, sc.B.V, sc.B.T, sc.B.oriented, np.float32)
+    ctx = api.Context(diffuse_rings=R, diffuse_sweeps=S)
+    ctx.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), 1 << 16)
+    EA, EB = oracle.edges(sc.A.T), oracle.edges(sc.B.T)
+    nA = sc.A.n_verts
+    converged = False
+    for it in range(iters):
+        PA, PB = positions(A), positions(B)
+        _, n, got, _ = detect(ctx, A, B)
+        ref = oracle.detect(PA, sc.A.T, sc.A.oriented, PB, sc.B.T, sc.B.oriented)
+        assert np.array_equal(got, ref.rec), f"iteration {it}"
+        if n == 0:
+            converged = True
+            break
+        st = oracle.stencils(ref)
+        dA, dB, _, _ = oracle.respond(st, PA, sc.A.T, PB, sc.B.T, d)
+        eA = (PA + oracle.diffuse(dA, EA, R, S)).astype(np.float32).astype(np.float64)
+        eB = (PB + oracle.diffuse(dB, EB, R, S)).astype(np.float32).astype(np.float64)
+        info = ctx.hfcr_resolve(A, B, d, 1)
+        assert info.pairs_first == n
+        gA, gB = positions(A), positions(B)
+        scale = max(np.abs(dA).max(), np.abs(dB).max())
+        tol = 1e-6 * scale + 4 * np.spacing(np.float32(max(np.abs(PA).max(), np.abs(PB).max())))
+        assert np.abs(gA - eA).max() <= tol and np.abs(gB - eB).max() <= tol, f"iteration {it}"
+        # diffusion moved vertices beyond the stencils
+        moved = np.any(gA != PA, axis=1)
+        assert moved.sum() > len(np.unique(np.concatenate([st[:, 1][st[:, 0] == 0]])))
+    return converged
+
+
+def test_resolve_with_diffusion_step_parity(api):
+    sc = meshgen.scene_random_small(23, "cloth_sphere")
+    _resolve_step_parity(api, sc, 4, 8, 6)
+
+
+def test_resolve_with_diffusion_converges(api):
+    # the small cloth/sphere scene: the literal loop (no diffusion) does not
+    # converge in 40 iterations, the loop with diffusion does; the final
+    # positions have no E-F intersection under the oracle's exact detection
+    sc = meshgen.scene_random_small(23, "cloth_sphere")
+    res = {}
+    for R, S in ((0, 0), (4, 16)):
+        A, _ = dev_mesh(api, sc.A.V, sc.A.T, sc.A.oriented, np.float32)
+        B, _ = dev_mesh(api, sc.B.V, sc.B.T, sc.B.oriented, np.float32)
+        ctx = api.Context(diffuse_rings=R, diffuse_sweeps=S)
+        ctx.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), 1 << 17)
+        info = ctx.hfcr_resolve(A, B, 1e-4, 40)
+        res[R] = info
+        if info.converged:
+            left = oracle.detect(positions(A), sc.A.T, sc.A.oriented, positions(B), sc.B.T, sc.B.oriented)
+            assert len(left) == 0
+    assert res[4].converged
