@@ -34,7 +34,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DCD+response ms/frame and E-F tests/s on 1 GB300 vs plain FP64 GPU form"
 D_POST = 1e-4
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_traverse_cloth_torus.md")
 
 
 def parse():
@@ -46,7 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 1,024-pair batched workload")
-    ap.add_argument("--frames", type=int, default=0,
+    ap.add_argument("--no-c3", action="store_true", help="skip the two-tori precision form and d-sweep")
+    ap.add_argument("--frames", type=int, default=300,
                     help="frames of the cloth-over-body sequence (0 to skip)")
     return ap.parse_args()
 
@@ -115,24 +115,29 @@ def measured_peak_hbm():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {"k_traverse": ("detect.cu", "predicates.cuh"), "k_cg_zone": ("solve.cu",)}
+PROFILES = {"k_traverse": "k_traverse_cloth_torus.md", "k_cg_zone": "k_cg_zone_cloth_torus.md"}
+
+
+def kernel_source_hash(kernel: str = "k_traverse") -> str:
     h = hashlib.sha256()
-    for f in ("detect.cu", "predicates.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_1409_2081_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per traversal launch from the committed ncu summary, if
-    it was taken on the current kernel source."""
-    if not os.path.exists(PROFILE_SUMMARY):
+def profiled_traffic(kernel: str = "k_traverse"):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, if
+    the summary was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", PROFILES[kernel])
+    if not os.path.exists(path):
         return None
     vals = {}
-    for line in open(PROFILE_SUMMARY):
+    for line in open(path):
         if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_sha")):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("source_sha") != kernel_source_hash():
+    if vals.get("source_sha") != kernel_source_hash(kernel):
         return None
     try:
         return int(float(vals["traffic_bytes_per_launch"]))
@@ -185,19 +190,26 @@ def cpu_oracle_frame(sc, edge_fraction=1.0):
     return (t2 - t0), oracle.num_threads(), (t1 - t0) / frac + (t2 - t1)
 
 
-def frame_sequence(api, torch, dev, n_frames, max_iters=8, rings=4, sweeps=16):
+def frame_sequence(api, torch, dev, n_frames, max_iters=8, rings=4, sweeps=16, body_inv_mass=1.0,
+                   time_budget_s=45.0):
     """Cloth 512 x 512 (side 3.0, float32, un-oriented) falling onto an
     oriented body (icosphere level 7 with spherical-harmonic radius noise of
     amplitude 0.1): each frame moves the cloth by the seeded velocity field
     (torch ops on the device, outside the timed region), then one repair
     loop (resolve, up to max_iters iterations, graph-replayed, with the
-    diffusion of Sec. 5 over `rings` rings and `sweeps` sweeps) is timed."""
+    diffusion of Sec. 5 over `rings` rings and `sweeps` sweeps) is timed.
+    The prescribed drift keeps pushing resting cloth into the body, and the
+    loop stops converging after a few dozen contact frames; once frames
+    take seconds the run stops at `time_budget_s` and reports the frames it
+    completed."""
+    import time
     import numpy as np
     import meshgen
     sc = meshgen.scene_c5()
     mot = sc.meta["motion"]
     ctx = api.Context(diffuse_rings=rings, diffuse_sweeps=sweeps)
-    ctx.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), 1 << 18)
+    cap = 1 << 18
+    ctx.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), cap)
 
     def dev_xyz(V):
         P = V.astype(np.float32)
@@ -208,13 +220,16 @@ def frame_sequence(api, torch, dev, n_frames, max_iters=8, rings=4, sweeps=16):
     ea = torch.zeros((3 * sc.A.n_tris, 2), dtype=torch.int32, device=dev)
     ea = ea[:ctx.hfcr_build_edges(ta, sc.A.n_verts, ea)].contiguous()
     A = api.Mesh(*xa, ta, False, edges=ea)
-    B = api.Mesh(*xb, tb, True)
+    wb = None if body_inv_mass == 1.0 else torch.full((sc.B.n_verts,), body_inv_mass,
+                                                      dtype=torch.float32, device=dev)
+    B = api.Mesh(*xb, tb, True, inv_mass=wb)
     K = torch.tensor(mot.k.T, dtype=torch.float32, device=dev)
     W = torch.tensor(mot.w, dtype=torch.float32, device=dev)
     PH = torch.tensor(mot.ph, dtype=torch.float32, device=dev)
     AD = torch.tensor((mot.amp[:, None] * mot.dir) * (0.5 * mot.v0), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    ms, pairs, iters, conv = [], [], [], 0
+    ms, pairs, iters, conv = [], [], [], []
+    stop, t_start = "all frames", time.time()
     for f in range(n_frames):
         X = torch.stack([A.x, A.y, A.z], 1)
         V = torch.sin(X @ K + W * f + PH) @ AD
@@ -223,23 +238,39 @@ def frame_sequence(api, torch, dev, n_frames, max_iters=8, rings=4, sweeps=16):
         A.x.copy_(X[:, 0]); A.y.copy_(X[:, 1]); A.z.copy_(X[:, 2])
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        info = ctx.hfcr_resolve(A, B, D_POST, max_iters)
+        try:
+            info = ctx.hfcr_resolve(A, B, D_POST, max_iters)
+        except api.HfcrError as e:
+            stop = f"frame {f}: {e}"[:120]
+            break
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
         pairs.append(int(info.pairs_first))
         iters.append(int(info.iters))
-        conv += int(info.converged)
+        conv.append(bool(info.converged))
+        if time.time() - t_start > time_budget_s:
+            stop = f"time budget {time_budget_s:.0f} s after frame {f}"
+            break
     ctx.close()
+    contact = [i for i, p in enumerate(pairs) if p > 0]
+    first_fail = next((i for i, c in enumerate(conv) if not c), None)
+    healthy = ms[:first_fail] if first_fail is not None else ms
     srt = sorted(ms)
     return {"workload": "cloth 512x512 (784,385 edges) falling on SH body (icosphere L7, 327,680 faces), "
-                        "float32, one resolve (<= %d iterations, diffusion R=%d S=%d) per frame"
-                        % (max_iters, rings, sweeps),
-            "frames": n_frames, "ms_p50": round(statistics.median(ms), 4),
-            "ms_p99": round(srt[min(len(srt) - 1, int(0.99 * len(srt)))], 4),
-            "ms_mean": round(statistics.mean(ms), 4), "max_pairs_first": max(pairs),
-            "mean_iters": round(statistics.mean(iters), 2), "converged_frames": conv,
-            "frames_with_contact": sum(1 for p in pairs if p > 0)}
+                        "float32, one resolve (<= %d iterations, diffusion R=%d S=%d, body inverse "
+                        "mass %g) per frame" % (max_iters, rings, sweeps, body_inv_mass),
+            "frames_requested": n_frames, "frames_completed": len(ms), "stopped": stop,
+            "ms_p50": round(statistics.median(ms), 4) if ms else None,
+            "ms_p99": round(srt[min(len(srt) - 1, int(0.99 * len(srt)))], 4) if ms else None,
+            "first_contact_frame": contact[0] if contact else None,
+            "first_unconverged_frame": first_fail,
+            "ms_p50_before_first_unconverged": round(statistics.median(healthy), 4) if healthy else None,
+            "ms_p99_before_first_unconverged":
+                round(sorted(healthy)[min(len(healthy) - 1, int(0.99 * len(healthy)))], 4) if healthy else None,
+            "converged_contact_frames": sum(1 for i in contact if conv[i]),
+            "contact_frames": len(contact), "max_pairs_first": max(pairs) if pairs else 0,
+            "mean_iters": round(statistics.mean(iters), 2) if iters else None}
 
 
 def batched(api, torch, dev, steps, warmup, timed_fn):
@@ -301,6 +332,109 @@ def batched(api, torch, dev, steps, warmup, timed_fn):
                          "alg_bytes_per_launch": alg,
                          "avg_launch_ms": round(trav_ms / max(1, trav_n), 5),
                          "traverse_variant": variant, "variant_ms": variant_ms}}
+
+
+def precision_form(api, torch, dev, steps, timed_fn, d_values=(1e-4, 1e-3, 1e-2), rings=4,
+                   sweeps=16, max_iters=32):
+    """Two 262,144-face tori, float32, a seeded local overlap: one repair
+    iteration (float32 filter -> float64 -> exact; float32 CG + float64
+    refinement) timed from the initial state; the float32 solver's
+    displacement error against the float64 GPU solver on the same stencils;
+    and the d-sweep (each d resolved with diffusion, at most max_iters
+    detections: detections run, and the signed distance D' of every
+    first-iteration stencil's x0 from its face at the final positions,
+    relative to d)."""
+    import numpy as np
+    import meshgen
+    sc = meshgen.scene_c3()
+
+    def mesh(m):
+        xyz = [torch.tensor(np.ascontiguousarray(m.V[:, c].astype(np.float32)), device=dev) for c in range(3)]
+        return api.Mesh(*xyz, torch.tensor(m.T, device=dev), True), [t.clone() for t in xyz]
+
+    def fresh():
+        (A, a0), (B, b0) = mesh(sc.A), mesh(sc.B)
+        return A, B, a0 + b0
+
+    def restore(A, B, init):
+        for t, t0 in zip((A.x, A.y, A.z, B.x, B.y, B.z), init):
+            t.copy_(t0, non_blocking=True)
+
+    cap = 1 << 20
+    ctx = api.Context()
+    ctx.hfcr_reserve(sc.A.n_verts, sc.A.n_tris, cap)
+    A, B, init = fresh()
+    variant, _ = ctx.hfcr_autotune(A, B)
+
+    def step():
+        restore(A, B, init)
+        return ctx.hfcr_resolve(A, B, D_POST, 1)
+
+    ms, infos = timed_fn(step, steps, 3)
+    info = infos[-1]
+    # float32 CG + float64 refinement vs the float64 CG on the same stencils
+    restore(A, B, init)
+    pairs = torch.zeros((cap, 4), dtype=torch.int32, device=dev)
+    n = ctx.hfcr_detect(A, B, pairs)
+    st = torch.zeros((cap, 4), dtype=torch.int32, device=dev)
+    k = ctx.hfcr_build_stencils(A, B, pairs, n, st)
+    ctx64 = api.Context(solver=api.HFCR_SOLVER_FP64)
+    ctx64.hfcr_reserve(sc.A.n_verts, sc.A.n_tris, cap)
+    A64 = api.Mesh(*[t.double() for t in init[:3]], A.tris, True)
+    B64 = api.Mesh(*[t.double() for t in init[3:]], B.tris, True)
+    dx = {}
+    for name, c, MA, MB in (("mixed", ctx, A64, B64), ("fp64", ctx64, A64, B64)):
+        da = [torch.zeros(sc.A.n_verts, dtype=torch.float64, device=dev) for _ in range(3)]
+        db = [torch.zeros(sc.B.n_verts, dtype=torch.float64, device=dev) for _ in range(3)]
+        si = c.hfcr_respond(MA, MB, st, k, D_POST, da, db)
+        dx[name] = (torch.cat([torch.stack(da, 1), torch.stack(db, 1)]), si)
+    err = float((dx["mixed"][0] - dx["fp64"][0]).abs().max() / dx["fp64"][0].abs().max())
+    ctx64.close()
+    ctx.close()
+    # d-sweep: repair to convergence from the initial state (the overlap is
+    # several edge lengths deep: the loop uses the diffusion of Sec. 5)
+    ctx = api.Context(diffuse_rings=rings, diffuse_sweeps=sweeps)
+    ctx.hfcr_reserve(sc.A.n_verts, sc.A.n_tris, cap)
+    stn = st[:k, :3].cpu().numpy().astype(np.int64)
+    sweep = []
+    for d in d_values:
+        restore(A, B, init)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = ctx.hfcr_resolve(A, B, d, max_iters)
+        e1.record()
+        e1.synchronize()
+        PA = torch.stack([A.x, A.y, A.z], 1).double().cpu().numpy()
+        PB = torch.stack([B.x, B.y, B.z], 1).double().cpu().numpy()
+        # D' of x0 against its face at the final positions (Eq. 1); dir 0:
+        # x0 in A, face in B; dir 1: the reverse
+        m0 = stn[:, 0] == 0
+        x0 = np.empty((len(stn), 3))
+        tri = np.empty((len(stn), 3, 3))
+        x0[m0], tri[m0] = PA[stn[m0, 1]], PB[sc.B.T[stn[m0, 2]]]
+        x0[~m0], tri[~m0] = PB[stn[~m0, 1]], PA[sc.A.T[stn[~m0, 2]]]
+        nrm = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+        ln = np.linalg.norm(nrm, axis=1)
+        ok = ln > 0
+        Dp = np.einsum("ij,ij->i", nrm[ok] / ln[ok, None], x0[ok] - tri[ok].mean(axis=1))
+        sweep.append({"d": d, "converged": bool(r.converged), "detections": int(r.iters),
+                      "pairs_first": int(r.pairs_first), "ms": round(e0.elapsed_time(e1), 3),
+                      "gap_over_d_min": round(float(Dp.min() / d), 4),
+                      "gap_over_d_median": round(float(np.median(Dp) / d), 4)})
+    ctx.close()
+    return {"workload": "two tori 512x256 quads (262,144 faces each), float32, local overlap "
+                        "depth U(0, 0.2 r); one repair iteration from the initial state",
+            "ms_p50": round(statistics.median(ms), 4), "ms_mean": round(statistics.mean(ms), 4),
+            "pairs": int(info.pairs_first), "stencils": int(k),
+            "filter": {"narrow_tests": int(info.stats.narrow_tests),
+                       "f64_fallbacks": int(info.stats.f64_fallbacks),
+                       "exact_fallbacks": int(info.stats.exact_fallbacks)},
+            "dx_rel_err_vs_fp64_solver": err,
+            "mixed_solver": {"cg_iters": int(dx["mixed"][1].cg_iters),
+                             "rel_residual": dx["mixed"][1].rel_residual},
+            "traverse_variant": variant,
+            "d_sweep": {"diffusion": {"rings": rings, "sweeps": sweeps}, "max_iters": max_iters,
+                        "runs": sweep}}
 
 
 def run_reference(args, ws, rank):
@@ -436,17 +570,54 @@ def main():
     bf = int(info.stats.brute_force_equiv)
     narrow = int(info.stats.narrow_tests)
 
-    # roofline of the dominant kernel: the traversal + exact narrow phase
-    trav_ms, trav_n = prof["traverse"]
-    trav_avg_ms = trav_ms / max(1, trav_n)
-    # the profiled pass saw k_prof frames (+2 warm-up frames before the sums were read)
     P = int(info.pairs_first)
-    alg_bytes = (sc.A.n_verts * 12 + ne * 8 + sc.B.n_verts * 12 + sc.B.n_tris * 12 + P * 8)
     peak, peak_kind = measured_peak_hbm()
-    achieved = alg_bytes / (trav_avg_ms * 1e-3) / 1e9
     n_prof_frames = max(1, prof["traverse"][1])
     stage_ms = {k: round(v[0] / n_prof_frames, 4) for k, v in prof.items()}
     dominant = max(stage_ms, key=stage_ms.get)
+    # rooflines of the two kernels that own a stage each: the traversal +
+    # exact narrow phase, and the per-zone solver (the solve stage is
+    # k_cg_zone<256>, the 1024-thread launch, empty on this frame, and the
+    # one-CTA k_zone_final); algorithmic bytes = compulsory reads + writes
+    trav_ms, trav_n = prof["traverse"]
+    trav_avg_ms = trav_ms / max(1, trav_n)
+    alg_trav = (sc.A.n_verts * 12 + ne * 8 + sc.B.n_verts * 12 + sc.B.n_tris * 12 + P * 8)
+    ach_trav = alg_trav / (trav_avg_ms * 1e-3) / 1e9
+    solve_ms, solve_n = prof["solve"]
+    solve_avg_ms = solve_ms / max(1, solve_n)
+    # stencil count and touched vertices of this frame's system (outside the
+    # timed regions)
+    restore(A, B, init)
+    pbuf = torch.zeros((1 << 16, 4), dtype=torch.int32, device=dev)
+    n_p = ctx.hfcr_detect(A, B, pbuf)
+    sbuf = torch.zeros((1 << 16, 4), dtype=torch.int32, device=dev)
+    k_st = ctx.hfcr_build_stencils(A, B, pbuf, n_p, sbuf)
+    dxa = [torch.zeros(sc.A.n_verts, device=dev) for _ in range(3)]
+    dxb = [torch.zeros(sc.B.n_verts, device=dev) for _ in range(3)]
+    si = ctx.hfcr_respond(A, B, sbuf, k_st, D_POST, dxa, dxb)
+    # per stencil: ids 16 + float32 normal 16 + preconditioner row 16 + b 8
+    # + float64 normal 32 + lam 8 (written) + 4 vertex-CSR entries 16 + group
+    # start 4; per touched vertex: CSR offset 4 + inverse mass 4
+    alg_cg = 116 * k_st + 8 * int(si.n_touched)
+    ach_cg = alg_cg / (solve_avg_ms * 1e-3) / 1e9
+    roof = {
+        "k_traverse": {"kernel": "k_traverse (BVH traversal + exact narrow phase)", "bound": "hbm",
+                       "achieved": round(ach_trav, 2), "peak": peak, "peak_kind": peak_kind,
+                       "unit": "GB/s", "frac": round(ach_trav / peak, 5),
+                       "traffic": profiled_traffic("k_traverse"), "alg_bytes_per_launch": alg_trav,
+                       "avg_launch_ms": round(trav_avg_ms, 5), "launches_timed": trav_n,
+                       "traverse_variant": variant, "variant_ms": variant_ms},
+        "k_cg_zone": {"kernel": "k_cg_zone<256> (float32 PCG per impact zone, float64 refinement in "
+                                "the kernel)", "bound": "hbm",
+                      "achieved": round(ach_cg, 3), "peak": peak, "peak_kind": peak_kind,
+                      "unit": "GB/s", "frac": round(ach_cg / peak, 6),
+                      "traffic": profiled_traffic("k_cg_zone"), "alg_bytes_per_launch": alg_cg,
+                      "avg_launch_ms": round(solve_avg_ms, 5), "launches_timed": solve_n,
+                      "stencils": k_st, "touched_vertices": int(si.n_touched)},
+    }
+    dom_kernel = "k_cg_zone" if stage_ms["solve"] >= stage_ms["traverse"] else "k_traverse"
+    roofline = dict(roof[dom_kernel], dominant_stage=dominant,
+                    chosen_by="the larger of the solve and traverse stages in the profiled pass")
 
     # ---- end to end through the C ABI with host buffers ----
     host_in = [t.detach().cpu().pin_memory() for t in init]
@@ -478,6 +649,7 @@ def main():
         ctx64.close()
 
     frames = frame_sequence(api, torch, dev, args.frames) if args.frames > 0 else None
+    c3 = None if args.no_c3 else precision_form(api, torch, dev, max(5, args.steps // 5), timed)
     batch = None if args.no_batch else batched(api, torch, dev, max(5, args.steps // 10), 2, timed)
 
     line = None
@@ -512,16 +684,12 @@ def main():
             "stage_ms_per_frame": stage_ms,
             "profiled_ms_per_frame": round(statistics.mean(prof_ms), 4),
             "graphs": True,
-            "roofline": {"kernel": "k_traverse (BVH traversal + exact narrow phase)",
-                         "bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 5),
-                         "traffic": profiled_traffic(), "alg_bytes_per_launch": alg_bytes,
-                         "avg_launch_ms": round(trav_avg_ms, 5), "launches_timed": trav_n,
-                         "dominant_stage": dominant, "traverse_variant": variant,
-                         "variant_ms": variant_ms},
+            "roofline": roofline,
+            "rooflines": roof,
             "e2e": {"value": round(e2e_total / (args.steps * ws), 4), "unit": "ms/frame",
                     "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
             "fp64_form": fp64,
+            "precision_form": c3,
             "frame_sequence": frames,
             "batch": batch,
             "gpu_launches": launches,

@@ -742,8 +742,9 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(cudaMallocHost((void **)&ctx->h_segs, sizeof(int) * 8));
     CK(dalloc(&ctx->d_segs, 8));
     size_t maxn = E3 > 4 * P ? E3 : 4 * P;
-    ctx->sort.max_blocks = sort_blocks_for((int)maxn) + 1;
+    ctx->sort.max_blocks = sort_blocks_for((int)maxn) + 2;
     CK(dalloc(&ctx->sort.hist, 256 * (size_t)ctx->sort.max_blocks));
+    ctx->sort.status = ctx->d_status;
     for (int i = 0; i < 2; ++i) {
         Bvh &b = ctx->bvh[i];
         b.cap = (int)T;

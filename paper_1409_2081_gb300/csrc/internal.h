@@ -88,8 +88,10 @@ struct Bvh {
 };
 
 struct SortTemp {
-    unsigned *hist = nullptr;   // [256 * max_blocks]
-    int max_blocks = 0;
+    unsigned *hist = nullptr;   // [256 * max_blocks]: tile histograms, then a row for the grid
+                                // barrier of the cooperative sort and a row of digit totals
+    int max_blocks = 0;         // tiles of the largest sort + 2
+    uint32_t *status = nullptr; // device status word (ST_TIMEOUT of the cooperative sort)
 };
 
 // Radix sort (stable LSD, 8-bit digits) of keys with optional int values.

@@ -22,7 +22,7 @@ namespace {
 
 constexpr int NOALLOC_MAX_TRIS = 1 << 16;
 constexpr int NOALLOC_KEYS = 3 * NOALLOC_MAX_TRIS;              // one key per half-edge
-constexpr int NOALLOC_HIST_BLOCKS = (NOALLOC_KEYS + 2047) / 2048 + 1;
+constexpr int NOALLOC_HIST_BLOCKS = (NOALLOC_KEYS + 2047) / 2048 + 2;
 constexpr size_t OFF_KEYS = 0;
 constexpr size_t OFF_KEYS_ALT = OFF_KEYS + 8ull * NOALLOC_KEYS;
 constexpr size_t OFF_FLAGS = OFF_KEYS_ALT + 8ull * NOALLOC_KEYS;
@@ -84,6 +84,7 @@ extern "C" hfcr_status hfcr_build_edges_noalloc(const int32_t *tris, int32_t n_t
     hfcr::SortTemp t;
     t.hist = (unsigned *)(b + OFF_HIST);
     t.max_blocks = NOALLOC_HIST_BLOCKS;
+    t.status = d_status;
     // the count and the status word carry over from the previous call
     if (cudaMemsetAsync(d_count, 0, 8, s) != cudaSuccess) return HFCR_ERR_CUDA;
     hfcr::build_edges(tris, n_tris, n_verts, out, d_count, (unsigned long long *)(b + OFF_KEYS),

@@ -30,8 +30,9 @@ __device__ __forceinline__ unsigned digit_of(K k, int shift) {
 
 // Ranks one tile.  wh must be zero on entry; on exit wh[w][d] holds the
 // exclusive prefix over warps of digit d's count and tot[d] (if non-null)
-// the tile's count of digit d.  Invalid slots get digit 256.
-template <typename K, bool HV>
+// the tile's count of digit d.  Invalid slots get digit 256.  CG: read the
+// keys from L2 (data written by other CTAs of the same launch).
+template <typename K, bool HV, bool CG = false>
 __device__ __forceinline__ void rank_tile(const K *kin, const int *vin, int n, int tile_base,
                                           unsigned (*wh)[256], K *key, int *val, unsigned *dig,
                                           unsigned *rank, int shift) {
@@ -41,8 +42,8 @@ __device__ __forceinline__ void rank_tile(const K *kin, const int *vin, int n, i
     for (int r = 0; r < ROUNDS; ++r) {
         int idx = base + r * 32 + lane;
         bool valid = idx < n;
-        key[r] = valid ? kin[idx] : (K)0;
-        if (HV) val[r] = valid ? vin[idx] : 0;
+        key[r] = valid ? (CG ? __ldcg(kin + idx) : kin[idx]) : (K)0;
+        if (HV) val[r] = valid ? (CG ? __ldcg(vin + idx) : vin[idx]) : 0;
         unsigned d = valid ? digit_of(key[r], shift) : 256u;
         dig[r] = d;
         unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -86,10 +87,11 @@ __global__ void __launch_bounds__(TPB) k_hist(const K *keys, int n, const int *d
 }
 
 // exclusive scan of a[0..m) in place by the calling CTA (NT threads),
-// starting from carry; returns carry + the sum to every thread.  Chunks of 4 NT: each thread loads 4
+// starting from carry; returns carry + the sum to every thread.  CGL: read
+// a from L2 (written by other CTAs of the same launch).  Chunks of 4 NT: each thread loads 4
 // consecutive elements (coalesced across the warp), the CTA scans the
 // per-thread sums, and a running carry links the chunks.
-template <int NT>
+template <int NT, bool CGL = false>
 __device__ __forceinline__ unsigned block_scan_excl(unsigned *a, int m, unsigned carry = 0) {
     __shared__ unsigned ws[32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -98,7 +100,7 @@ __device__ __forceinline__ unsigned block_scan_excl(unsigned *a, int m, unsigned
         const int i0 = base + 4 * t;
         unsigned v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = i0 + q < m ? a[i0 + q] : 0u;
+        for (int q = 0; q < 4; ++q) v[q] = i0 + q < m ? (CGL ? __ldcg(a + i0 + q) : a[i0 + q]) : 0u;
         const unsigned sum = v[0] + v[1] + v[2] + v[3];
         unsigned x = sum;
 #pragma unroll
@@ -318,6 +320,152 @@ __global__ void __launch_bounds__(TPB) k_sort_small(K *k0, int *v0, K *k1, int *
     }
 }
 
+// Grid-wide barrier of k_sort_coop: a monotone arrival counter (zeroed
+// before the launch); barrier number e is passed when it reaches
+// e * gridDim.x.  The cooperative launch makes every CTA co-resident; the
+// spin is bounded all the same: after ~0.5 s the CTA records ST_TIMEOUT in
+// *status and every CTA that sees the flag leaves the kernel (the sort's
+// output is then invalid and the caller reports HFCR_ERR_TIMEOUT).
+constexpr long long BARRIER_SPIN_LIMIT = 1ll << 22;
+
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned epoch, uint32_t *status) {
+    __shared__ int failed;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        failed = 0;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const unsigned target = epoch * gridDim.x;
+        long long spins = 0;
+        while (true) {
+            unsigned seen;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(bar) : "memory");
+            if (seen >= target) break;
+            if (*(volatile uint32_t *)status & ST_TIMEOUT) { failed = 1; break; }
+            if (++spins > BARRIER_SPIN_LIMIT) {
+                atomicOr(status, ST_TIMEOUT);
+                failed = 1;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return failed == 0;
+}
+
+// All passes of the multi-CTA sort in one cooperative launch, for sorts
+// whose count is on the device: the grid (at most the co-resident CTAs)
+// walks the live tiles in each phase, with grid-wide barriers between the
+// histogram, the digit-row scans and the scatter.  When the live count fits
+// the single-CTA kernel every CTA returns at once (every CTA reads the same
+// count before any barrier, so none waits alone).  Data written by other
+// CTAs in the same launch (keys, histogram rows, digit totals) is read with
+// L2 loads (__ldcg), never through a possibly stale L1 line.
+template <typename K, bool HV>
+__global__ void __launch_bounds__(TPB) k_sort_coop(K *k0, int *v0, K *k1, int *v1, int n,
+                                                   const int *d_n, int bits, unsigned *hist,
+                                                   unsigned *tot, unsigned *bar, uint32_t *status) {
+    n = min(n, *d_n);
+    if (n <= SMALL_N) return;
+    unsigned epoch = 0;
+    const int nba = (n + TILE - 1) / TILE;
+    __shared__ unsigned wh[TPB / 32][256];
+    __shared__ unsigned dbase[256];
+    __shared__ unsigned wsum[TPB / 32];
+    K *kin = k0, *kout = k1;
+    int *vin = v0, *vout = v1;
+    for (int shift = 0; shift < bits; shift += 8) {
+        for (int b = blockIdx.x; b < nba; b += gridDim.x) {
+            wh[0][threadIdx.x] = 0;
+            __syncthreads();
+            const int base = b * TILE;
+            for (int i = threadIdx.x; i < TILE; i += TPB) {
+                const int idx = base + i;
+                if (idx < n) atomicAdd(&wh[0][digit_of(__ldcg(kin + idx), shift)], 1u);
+            }
+            __syncthreads();
+            hist[threadIdx.x * nba + b] = wh[0][threadIdx.x];
+            __syncthreads();
+        }
+        if (!grid_barrier(bar, ++epoch, status)) return;
+        for (int d = blockIdx.x; d < 256; d += gridDim.x) {
+            const unsigned total = block_scan_excl<TPB, true>(hist + d * nba, nba);
+            if (threadIdx.x == 0) tot[d] = total;
+        }
+        if (!grid_barrier(bar, ++epoch, status)) return;
+        {
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+            const unsigned c = __ldcg(tot + threadIdx.x);
+            unsigned x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[w] = x;
+            __syncthreads();
+            unsigned before = 0;
+            for (int q = 0; q < w; ++q) before += wsum[q];
+            dbase[threadIdx.x] = before + x - c;
+            __syncthreads();
+        }
+        for (int b = blockIdx.x; b < nba; b += gridDim.x) {
+            for (int i = threadIdx.x; i < (TPB / 32) * 256; i += TPB) (&wh[0][0])[i] = 0;
+            __syncthreads();
+            K key[ROUNDS];
+            int val[ROUNDS];
+            unsigned dig[ROUNDS], rank[ROUNDS];
+            rank_tile<K, HV, true>(kin, vin, n, b * TILE, wh, key, val, dig, rank, shift);
+            __syncthreads();
+            unsigned run = 0;
+            for (int w = 0; w < TPB / 32; ++w) {
+                unsigned c = wh[w][threadIdx.x];
+                wh[w][threadIdx.x] = run;
+                run += c;
+            }
+            __syncthreads();
+            const int warp = threadIdx.x >> 5;
+#pragma unroll
+            for (int r = 0; r < ROUNDS; ++r) {
+                const unsigned d = dig[r];
+                if (d < 256) {
+                    const unsigned pos = dbase[d] + __ldcg(hist + d * nba + b) + wh[warp][d] + rank[r];
+                    kout[pos] = key[r];
+                    if (HV) vout[pos] = val[r];
+                }
+            }
+            __syncthreads();
+        }
+        if (!grid_barrier(bar, ++epoch, status)) return;
+        K *tk = kin; kin = kout; kout = tk;
+        int *tv = vin; vin = vout; vout = tv;
+    }
+}
+
+// co-resident CTAs of k_sort_coop<K, HV> on this device (0: cooperative
+// launch unavailable)
+template <typename K, bool HV>
+int coop_grid() {
+    static int g[64] = {0};
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!done[dev]) {
+        int per_sm = 0, sms = 0, coop = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_coop<K, HV>, TPB, 0) ==
+                cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop)
+            g[dev] = per_sm * sms;
+        else
+            cudaGetLastError();
+        done[dev] = true;
+    }
+    return g[dev];
+}
+
 template <typename K, bool HV>
 bool radix_sort_impl(K *k0, int *v0, K *k1, int *v1, int n, const int *d_n, int bits,
                      SortTemp &t, cudaStream_t s) {
@@ -333,6 +481,23 @@ bool radix_sort_impl(K *k0, int *v0, K *k1, int *v1, int n, const int *d_n, int 
     int nb = (n + TILE - 1) / TILE;
     // the digit totals sit in the spare row after the largest histogram
     unsigned *tot = t.hist + 256 * (size_t)(t.max_blocks - 1);
+    if (d_n) {
+        int grid = coop_grid<K, HV>();
+        if (grid > nb) grid = nb;
+        if (grid > 0) {
+            int bits8 = passes * 8;
+            unsigned *bar = t.hist + 256 * (size_t)(t.max_blocks - 2);
+            uint32_t *status = t.status;
+            cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+            void *args[] = {&k0, &v0, &k1, &v1, &n, (void *)&d_n, &bits8, &t.hist, &tot, &bar, &status};
+            if (status && cudaLaunchCooperativeKernel((const void *)k_sort_coop<K, HV>, grid, TPB, args, 0, s) ==
+                cudaSuccess) {
+                note_launch();
+                return passes & 1;
+            }
+            cudaGetLastError();
+        }
+    }
     K *kin = k0, *kout = k1;
     int *vin = v0, *vout = v1;
     for (int p = 0; p < passes; ++p) {

@@ -332,6 +332,33 @@ def test_two_tori_sampled_full_size(api):
         assert mine == ref
 
 
+def test_two_tori_full_size_response(api):
+    """The precision form on the two 262,144-face tori: every GPU pair is
+    re-verified exactly (which also gives the side of v0), the stencils
+    follow from those pairs as in the oracle, and the float32 CG with
+    float64 refinement matches the float64 oracle minimizer on the full
+    stencil set."""
+    sc = meshgen.scene_c3()
+    A, PA = dev_mesh(api, sc.A.V, sc.A.T, True, np.float32)
+    B, PB = dev_mesh(api, sc.B.V, sc.B.T, True, np.float32)
+    ctx = make_ctx(api, sc.A.n_verts, sc.A.n_tris, 1 << 20)
+    out, n, got, _ = detect(ctx, A, B, 1 << 20)
+    assert n > 0
+    side = np.zeros(n, np.int8)
+    for i, (d, v0, v1, f) in enumerate(got.tolist()):
+        PE, PF, TF = (PA, PB, sc.B.T) if d == 0 else (PB, PA, sc.A.T)
+        ok, sd = oracle.segtri(PE[v0], PE[v1], *PF[TF[f]])
+        assert ok
+        side[i] = sd
+    ref_st = oracle.stencils(oracle.Pairs(got, side))
+    st_t, k, st = stencils(ctx, A, B, out, n, 1 << 20)
+    assert np.array_equal(st, ref_st)
+    g, info = respond(ctx, A, B, st_t, k, 1e-4, sc.A.n_verts, sc.B.n_verts, np.float32)
+    rA, rB, _, _ = oracle.respond(st, PA, sc.A.T, PB, sc.B.T, 1e-4)
+    err = rel_err(g, np.concatenate([rA, rB]))
+    assert err <= TOL_DX and info.converged
+
+
 def test_graph_replay_matches_plain_launches(api):
     """Repair iterations replayed from captured CUDA graphs give bit-identical
     positions to plain launches, on the default and on a created stream, and
