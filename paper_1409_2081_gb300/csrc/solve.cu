@@ -427,15 +427,66 @@ __device__ __forceinline__ int uf_find(int *parent, int x) {
     }
 }
 
+// Inputs of up to UF_SMALL stencils: one CTA runs the whole union-find in
+// shared memory (the same hooking rule as below, so the same labels) and
+// writes the zone keys; the global-memory kernels then return at once.
+constexpr int UF_SMALL = 12288;  // 48 KB of parents
+
+__device__ __forceinline__ int uf_find_s(volatile int *par, int x) {
+    while (true) {
+        const int p = par[x];
+        if (p == x) return x;
+        const int gp = par[p];
+        if (gp != p) par[x] = gp;
+        x = p;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_uf_small(const int *d_k, const int *d_U, const int *seg,
+                                                   const int *cval, unsigned *zlab, int *zsrc,
+                                                   uint32_t *status) {
+    __shared__ int par[UF_SMALL];
+    const int k = *d_k;
+    if (k > UF_SMALL) return;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) par[i] = i;
+    __syncthreads();
+    const int U = *d_U;
+    for (int j = threadIdx.x; j < U; j += blockDim.x) {
+        const int e0 = seg[j], e1 = seg[j + 1];
+        const int s0 = cval[e0] >> 2;
+        for (int e = e0 + 1; e < e1; ++e) {
+            int a = s0, b = cval[e] >> 2;
+            int guard = 0;
+            while (true) {
+                a = uf_find_s(par, a);
+                b = uf_find_s(par, b);
+                if (a == b) break;
+                if (a < b) { int t = a; a = b; b = t; }
+                const int old = atomicCAS(par + a, a, b);
+                if (old == a) break;
+                a = old;
+                if (++guard > (1 << 24)) { atomicOr(status, ST_TIMEOUT); break; }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        zlab[i] = (unsigned)uf_find_s(par, i);
+        zsrc[i] = i;
+    }
+}
+
 __global__ void k_uf_init(const int *d_k, int *parent) {
     const int k = *d_k;
+    if (k <= UF_SMALL) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
         parent[i] = i;
 }
 
 // unions the stencils of every touched vertex (CSR by vertex)
-__global__ void k_uf_union(const int *d_U, const int *seg, const int *cval, int *parent,
-                           uint32_t *status) {
+__global__ void k_uf_union(const int *d_k, const int *d_U, const int *seg, const int *cval,
+                           int *parent, uint32_t *status) {
+    if (*d_k <= UF_SMALL) return;
     const int U = *d_U;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < U; j += gridDim.x * blockDim.x) {
         const int e0 = seg[j], e1 = seg[j + 1];
@@ -462,6 +513,7 @@ __global__ void k_uf_union(const int *d_U, const int *seg, const int *cval, int 
 // zone label of every stencil (its root = the smallest stencil of its zone)
 __global__ void k_zone_keys(const int *d_k, int *parent, unsigned *zlab, int *zsrc) {
     const int k = *d_k;
+    if (k <= UF_SMALL) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
         zlab[i] = (unsigned)uf_find(parent, i);
         zsrc[i] = i;
@@ -746,9 +798,9 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
         const int e0 = seg_g[j0];
         const int g0 = zg[z], G = zg[z + 1] - g0;
         const long long need = 92ll * k + 24ll * U + 4ll * G + 32;
-        const bool in_smem = need <= smem_bytes;
         double rr = bb;
         int its = 0, rounds = 0;
+        const bool in_smem = need <= smem_bytes;
         // the two paths are instantiated separately so that the shared-memory
         // one sees pointers derived only from the shared array (LDS/STS, not
         // generic loads)
@@ -1035,9 +1087,12 @@ void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers 
     int kb = bits_for((long long)cap + 1);
     unsigned *zlab = (unsigned *)sb.zkey, *zlab_alt = (unsigned *)sb.zkey_alt;
     int *zsrc = (int *)sb.zkey + cap, *zsrc_alt = (int *)sb.zkey_alt + cap;
-    { k_uf_init<<<gb, 256, 0, s>>>(d_k, sb.parent); note_launch(); }
-    { k_uf_union<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(sb.d_U, sb.seg, cv1, sb.parent, d_status); note_launch(); }
-    { k_zone_keys<<<gb, 256, 0, s>>>(d_k, sb.parent, zlab, zsrc); note_launch(); }
+    { k_uf_small<<<1, 1024, 0, s>>>(d_k, sb.d_U, sb.seg, cv1, zlab, zsrc, d_status); note_launch(); }
+    if (cap > UF_SMALL) {
+        { k_uf_init<<<gb, 256, 0, s>>>(d_k, sb.parent); note_launch(); }
+        { k_uf_union<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(d_k, sb.d_U, sb.seg, cv1, sb.parent, d_status); note_launch(); }
+        { k_zone_keys<<<gb, 256, 0, s>>>(d_k, sb.parent, zlab, zsrc); note_launch(); }
+    }
     bool zflip = radix_sort_u32_dev(zlab, zsrc, zlab_alt, zsrc_alt, d_k, cap, kb, t, s);
     unsigned *zl = zflip ? zlab_alt : zlab;
     int *zr = zflip ? zsrc_alt : zsrc;

@@ -355,19 +355,20 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned epoch, uint
     return failed == 0;
 }
 
-// All passes of the multi-CTA sort in one cooperative launch, for sorts
-// whose count is on the device: the grid (at most the co-resident CTAs)
+// All passes of the multi-CTA sort in one cooperative launch (the per-pass
+// kernels below remain the fallback where cooperative launch is refused):
+// the grid (at most the co-resident CTAs)
 // walks the live tiles in each phase, with grid-wide barriers between the
 // histogram, the digit-row scans and the scatter.  When the live count fits
-// the single-CTA kernel every CTA returns at once (every CTA reads the same
-// count before any barrier, so none waits alone).  Data written by other
+// the single-CTA kernel (a count on the device) every CTA returns at once
+// (every CTA reads the same count before any barrier, so none waits alone).  Data written by other
 // CTAs in the same launch (keys, histogram rows, digit totals) is read with
 // L2 loads (__ldcg), never through a possibly stale L1 line.
 template <typename K, bool HV>
 __global__ void __launch_bounds__(TPB) k_sort_coop(K *k0, int *v0, K *k1, int *v1, int n,
                                                    const int *d_n, int bits, unsigned *hist,
                                                    unsigned *tot, unsigned *bar, uint32_t *status) {
-    n = min(n, *d_n);
+    if (d_n) n = min(n, *d_n);
     if (n <= SMALL_N) return;
     unsigned epoch = 0;
     const int nba = (n + TILE - 1) / TILE;
@@ -481,7 +482,7 @@ bool radix_sort_impl(K *k0, int *v0, K *k1, int *v1, int n, const int *d_n, int 
     int nb = (n + TILE - 1) / TILE;
     // the digit totals sit in the spare row after the largest histogram
     unsigned *tot = t.hist + 256 * (size_t)(t.max_blocks - 1);
-    if (d_n) {
+    if (d_n) {  // with a host count the per-pass kernels are as fast and launch no idle work
         int grid = coop_grid<K, HV>();
         if (grid > nb) grid = nb;
         if (grid > 0) {
