@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 1,024-pair batched workload")
-    ap.add_argument("--no-c3", action="store_true", help="skip the two-tori precision form and d-sweep")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the two-spheres and two-tori sections (precision form, d-sweep)")
     ap.add_argument("--frames", type=int, default=300,
                     help="frames of the cloth-over-body sequence (0 to skip)")
     return ap.parse_args()
@@ -332,6 +333,52 @@ def batched(api, torch, dev, steps, warmup, timed_fn):
                          "alg_bytes_per_launch": alg,
                          "avg_launch_ms": round(trav_ms / max(1, trav_n), 5),
                          "traverse_variant": variant, "variant_ms": variant_ms}}
+
+
+def small_form(api, torch, dev, steps, timed_fn):
+    """Two jittered level-3 icospheres offset by 1.5 (642 vertices, 1,280
+    faces each), float64: one repair iteration from the initial state in
+    the plain float64 form and the mixed form, and the whole repair loop
+    (alternating roles) to convergence.  This size is bound by launch
+    latency, so it is reported in microseconds."""
+    import numpy as np
+    import meshgen
+    sc = meshgen.scene_c1()
+
+    def mesh(ctx, m):
+        xyz = [torch.tensor(np.ascontiguousarray(m.V[:, c]), dtype=torch.float64, device=dev) for c in range(3)]
+        tris = torch.tensor(m.T, device=dev)
+        # topology preparation (once per mesh, outside the timed region)
+        e = torch.zeros((3 * m.n_tris, 2), dtype=torch.int32, device=dev)
+        e = e[:ctx.hfcr_build_edges(tris, m.n_verts, e)].contiguous()
+        return api.Mesh(*[t.clone() for t in xyz], tris, True, edges=e), xyz
+
+    out = {"workload": "two icospheres L3 (1,280 faces each), offset 1.5, jitter 0.01, float64"}
+    for name, solver, f32f, graphs in (("fp64_form", api.HFCR_SOLVER_FP64, False, False),
+                                       ("mixed_form", api.HFCR_SOLVER_MIXED, True, True)):
+        ctx = api.Context(solver=solver, f32_filter=f32f, graphs=graphs)
+        ctx.hfcr_reserve(sc.A.n_verts, sc.A.n_tris, 1 << 14)
+        (A, a0), (B, b0) = mesh(ctx, sc.A), mesh(ctx, sc.B)
+
+        def step():
+            for t, t0 in zip((A.x, A.y, A.z, B.x, B.y, B.z), a0 + b0):
+                t.copy_(t0, non_blocking=True)
+            return ctx.hfcr_resolve(A, B, D_POST, 1)
+
+        ms, infos = timed_fn(step, steps, 3)
+        out[name] = {"us_per_iteration": round(1e3 * statistics.median(ms), 1),
+                     "pairs": int(infos[-1].pairs_first)}
+        if solver == api.HFCR_SOLVER_MIXED:
+            def loop():
+                for t, t0 in zip((A.x, A.y, A.z, B.x, B.y, B.z), a0 + b0):
+                    t.copy_(t0, non_blocking=True)
+                return ctx.hfcr_resolve(A, B, D_POST, 64)
+            lms, linfo = timed_fn(loop, max(3, steps // 10), 1)
+            out["repair_loop"] = {"ms": round(statistics.median(lms), 3),
+                                  "detections": int(linfo[-1].iters),
+                                  "converged": bool(linfo[-1].converged)}
+        ctx.close()
+    return out
 
 
 def precision_form(api, torch, dev, steps, timed_fn, d_values=(1e-4, 1e-3, 1e-2), rings=4,
@@ -650,6 +697,7 @@ def main():
 
     frames = frame_sequence(api, torch, dev, args.frames) if args.frames > 0 else None
     c3 = None if args.no_c3 else precision_form(api, torch, dev, max(5, args.steps // 5), timed)
+    c1 = None if args.no_c3 else small_form(api, torch, dev, max(10, args.steps // 2), timed)
     batch = None if args.no_batch else batched(api, torch, dev, max(5, args.steps // 10), 2, timed)
 
     line = None
@@ -689,6 +737,7 @@ def main():
             "e2e": {"value": round(e2e_total / (args.steps * ws), 4), "unit": "ms/frame",
                     "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
             "fp64_form": fp64,
+            "small_form": c1,
             "precision_form": c3,
             "frame_sequence": frames,
             "batch": batch,

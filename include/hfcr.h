@@ -107,7 +107,7 @@ typedef struct {
     int32_t max_refine;     /* MIXED: float32 runs per impact zone, each followed by the zone's
                                float64 residual (default 6) */
     double rel_tol;         /* target |b - A lambda| / |b| (default 1e-12) */
-    double inner_tol;       /* MIXED: residual reduction of one float32 run (default 1e-5) */
+    double inner_tol;       /* MIXED: residual reduction of one float32 run (default 1e-4) */
     int32_t graphs;         /* 1 (default): resolve replays each repair iteration as a captured
                                CUDA graph (re-captured when any argument changes); 0: plain launches.
                                Graphs are not used while the profiler is enabled. */

@@ -190,7 +190,7 @@ class Context:
 
     def __init__(self, solver: int = HFCR_SOLVER_MIXED, f32_filter: bool = True,
                  roles: int = HFCR_ROLES_ALTERNATE, max_cg_iters: int = 500, max_refine: int = 6,
-                 rel_tol: float = 1e-12, inner_tol: float = 1e-5, graphs: bool = True,
+                 rel_tol: float = 1e-12, inner_tol: float = 1e-4, graphs: bool = True,
                  diffuse_rings: int = 0, diffuse_sweeps: int = 0):
         import torch
         if not torch.cuda.is_available():

@@ -673,7 +673,7 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
     c->opt.max_cg_iters = 500;
     c->opt.max_refine = 6;
     c->opt.rel_tol = 1e-12;
-    c->opt.inner_tol = 1e-5;
+    c->opt.inner_tol = 1e-4;
     c->opt.graphs = 1;
     c->opt.diffuse_rings = 0;
     c->opt.diffuse_sweeps = 0;
@@ -682,7 +682,7 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
         if (c->opt.max_cg_iters <= 0) c->opt.max_cg_iters = 500;
         if (c->opt.max_refine <= 0) c->opt.max_refine = 6;
         if (!(c->opt.rel_tol > 0)) c->opt.rel_tol = 1e-12;
-        if (!(c->opt.inner_tol > 0)) c->opt.inner_tol = 1e-5;
+        if (!(c->opt.inner_tol > 0)) c->opt.inner_tol = 1e-4;
         if (c->opt.solver != HFCR_SOLVER_FP64) c->opt.solver = HFCR_SOLVER_MIXED;
         if (c->opt.roles != HFCR_ROLES_BOTH) c->opt.roles = HFCR_ROLES_ALTERNATE;
         if (c->opt.diffuse_rings < 0 || c->opt.diffuse_sweeps < 0 || c->opt.diffuse_rings > 1024 ||
