@@ -56,6 +56,11 @@ struct hfcr_ctx {
     SortTemp sort;
     Bvh bvh[2];                   // [0]: faces of B (direction 0), [1]: faces of A (direction 1)
     int *edges[2] = {nullptr, nullptr};
+    // traversal order of each edge list (a permutation; it only steers
+    // performance, so a stale one for a moved mesh is still correct)
+    int *eorder[2] = {nullptr, nullptr};
+    const int *eorder_src[2] = {nullptr, nullptr};
+    int eorder_n[2] = {0, 0};
     unsigned long long *ekeys = nullptr, *ekeys_alt = nullptr;
     unsigned *eflags = nullptr;
     unsigned long long *pkeys = nullptr, *pkeys_alt = nullptr;
@@ -129,12 +134,15 @@ void free_all(hfcr_ctx *c) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *dp[] = {c->adj_ptr[0], c->adj_ptr[1], c->adj_nbr[0], c->adj_nbr[1], c->adj_cur, c->field,
-                  c->field_alt, c->ring};
+                  c->field_alt, c->ring, c->eorder[0], c->eorder[1]};
     for (void *p : dp)
         if (p) cudaFree(p);
     c->adj_ptr[0] = c->adj_ptr[1] = c->adj_nbr[0] = c->adj_nbr[1] = c->adj_cur = nullptr;
     c->field = c->field_alt = nullptr;
     c->ring = nullptr;
+    c->eorder[0] = c->eorder[1] = nullptr;
+    c->eorder_src[0] = c->eorder_src[1] = nullptr;
+    c->eorder_n[0] = c->eorder_n[1] = 0;
     for (int i = 0; i < 2; ++i) {
         Bvh &b = c->bvh[i];
         void *bp[] = {b.nodes, b.parent, b.flags, b.leaf_face, b.leaf_tri, b.keys, b.keys_alt,
@@ -293,6 +301,19 @@ hfcr_status plan_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, b
     }
     if (dir0 && A->n_tris > 0 && (st = mesh_edges(ctx, A, 0, &pl.edges[0], &pl.ne[0], s))) return st;
     if (dir1 && B->n_tris > 0 && (st = mesh_edges(ctx, B, 1, &pl.edges[1], &pl.ne[1], s))) return st;
+    for (int d = 0; d < 2; ++d) {
+        if (!pl.edges[d] || pl.ne[d] <= 0) continue;
+        if (ctx->eorder_src[d] == pl.edges[d] && ctx->eorder_n[d] == pl.ne[d]) continue;
+        // first use of this edge list: its traversal order from the current
+        // positions (kept for later calls)
+        const hfcr_mesh &E = d == 0 ? *A : *B;
+        edge_order(pl.edges[d], pl.ne[d], E, pl.segs, d == 0 ? 0 : 2, pl.nseg, ctx->eorder[d],
+                   (int *)ctx->eflags, ctx->ekeys, ctx->ekeys_alt, ctx->bvh[d].bounds_part,
+                   ctx->bvh[d].bounds, ctx->sort, ctx->d_status, s);
+        CK(cudaGetLastError());
+        ctx->eorder_src[d] = pl.edges[d];
+        ctx->eorder_n[d] = pl.ne[d];
+    }
     int maxe = pl.ne[0] > pl.ne[1] ? pl.ne[0] : pl.ne[1];
     int maxf = A->n_tris > B->n_tris ? A->n_tris : B->n_tris;
     pl.edge_bits = bits_for(maxe > 1 ? maxe : 2);
@@ -319,6 +340,9 @@ void launch_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d
             a.fcol = d == 0 ? 3 : 1;
             a.edge_mesh = &E;
             a.edges = pl.edges[d];
+            a.order = (ctx->eorder_src[d] == pl.edges[d] && ctx->eorder_n[d] == pl.ne[d])
+                          ? ctx->eorder[d]
+                          : nullptr;
             a.n_edges = pl.ne[d];
             a.bvh = &ctx->bvh[d];
             a.dir = d;
@@ -360,6 +384,8 @@ void launch_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d
         a.fcol = d == 0 ? 3 : 1;
         a.edge_mesh = &E;
         a.edges = pl.edges[d];
+        a.order = (ctx->eorder_src[d] == pl.edges[d] && ctx->eorder_n[d] == pl.ne[d]) ? ctx->eorder[d]
+                                                                                    : nullptr;
         a.n_edges = pl.ne[d];
         a.bvh = &b;
         a.dir = d;
@@ -759,6 +785,7 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
         CK(dalloc(&b.bounds, 8));
         CK(dalloc(&b.bounds_part, 6 * 1024));
         CK(dalloc(&ctx->edges[i], 2 * E3));
+        CK(dalloc(&ctx->eorder[i], E3));
     }
     CK(dalloc(&ctx->ekeys, E3));
     CK(dalloc(&ctx->ekeys_alt, E3));

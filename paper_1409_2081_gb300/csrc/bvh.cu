@@ -201,6 +201,31 @@ __global__ void k_morton(const T *x, const T *y, const T *z, int nv, const int *
     vals[t] = t;
 }
 
+// sort key of an edge: (segment of its first vertex, Morton code of its
+// midpoint); value = the edge's index
+template <typename T>
+__global__ void k_edge_order_keys(const int2 *edges, int ne, const T *x, const T *y, const T *z,
+                                  int nv, const float *bounds, const int *segs, int col, int nseg,
+                                  unsigned long long *keys, int *vals, uint32_t *st) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const int2 ed = edges[e];
+    const int a = chk(ed.x, nv, st), b = chk(ed.y, nv, st);
+    const T pa[3] = {x[a], y[a], z[a]}, pb[3] = {x[b], y[b], z[b]};
+    unsigned q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float m = (float)((pa[k] + pb[k]) / (T)2);
+        const float ext = bounds[3 + k] - bounds[k];
+        float u = ext > 0.f ? (m - bounds[k]) / ext : 0.f;
+        u = fminf(fmaxf(u * 1024.f, 0.f), 1023.f);
+        q[k] = (unsigned)u;
+    }
+    const unsigned long long seg = (unsigned long long)seg_of(segs, col, nseg, a);
+    keys[e] = (seg << 30) | (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+    vals[e] = e;
+}
+
 // common-prefix length of the keys of leaves i and j of one segment (its
 // sorted keys start at K); keys made unique by appending the local index
 __device__ __forceinline__ int kdelta(const unsigned long long *K, int n, int i, int j) {
@@ -242,8 +267,9 @@ __global__ void k_karras(const unsigned long long *keys, int n_total, const int 
     int left = (min(i, j) == gamma) ? ~(t0 + gamma) : t0 + gamma;
     int right = (max(i, j) == gamma + 1) ? ~(t0 + gamma + 1) : t0 + gamma + 1;
     nodes[4 * gi + 3] = make_float4(__int_as_float(left), __int_as_float(right), 0.f, 0.f);
-    if (left < 0) lparent[~left] = gi; else iparent[left] = gi;
-    if (right < 0) lparent[~right] = gi; else iparent[right] = gi;
+    // parent links carry the child's slot: (parent << 1) | (1 for the right child)
+    if (left < 0) lparent[~left] = gi << 1; else iparent[left] = gi << 1;
+    if (right < 0) lparent[~right] = (gi << 1) | 1; else iparent[right] = (gi << 1) | 1;
     if (i == 0) iparent[gi] = -1;
 }
 
@@ -287,32 +313,33 @@ __global__ void k_refit(const T *x, const T *y, const T *z, int nv, const int *t
         lo[k] = lo_f(fmin(fmin(a[k], b[k]), c[k]));
         hi[k] = hi_f(fmax(fmax(a[k], b[k]), c[k]));
     }
-    int node = lparent[j];
-    int child = ~j;
+    int link = lparent[j];  // (parent << 1) | slot, -1 at a root
     // bounded by the tree depth (< 64 for unique 62-bit keys); the guard
     // only keeps a corrupted parent array from looping
-    for (int guard = 0; guard < 128 && node >= 0; ++guard) {
+    for (int guard = 0; guard < 128 && link >= 0; ++guard) {
+        const int node = link >> 1;
+        const int slot = (link & 1) ? 6 : 0;
+        const int up = iparent[node];  // read-only: load it before the handshake
         float *nf = (float *)(nodes + 4 * node);
-        int c0 = __float_as_int(nf[12]);
-        int slot = (c0 == child) ? 0 : 6;
         nf[slot + 0] = lo[0];
         nf[slot + 1] = lo[1];
         nf[slot + 2] = lo[2];
         nf[slot + 3] = hi[0];
         nf[slot + 4] = hi[1];
         nf[slot + 5] = hi[2];
-        __threadfence();
-        unsigned old = atomicAdd(&flags[node], 1u);
+        // the first child to arrive leaves; the second (acquire) sees the
+        // first one's box (release) and carries the union upwards
+        unsigned old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                     : "=r"(old) : "l"(flags + node) : "memory");
         if (old == 0) return;
-        __threadfence();
-        int sib = 6 - slot;
+        const int sib = 6 - slot;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             lo[k] = fminf(lo[k], __ldcg(nf + sib + k));
             hi[k] = fmaxf(hi[k], __ldcg(nf + sib + 3 + k));
         }
-        child = node;
-        node = iparent[node];
+        link = up;
     }
 }
 
@@ -388,6 +415,30 @@ void bvh_build(Bvh &b, const hfcr_mesh &m, const int *segs, int col, int nseg, S
     // leaves of one-face segments keep parent -1
     cudaMemsetAsync(b.parent + b.cap, 0xff, sizeof(int) * n, s);
     { k_karras<<<nb, 256, 0, s>>>(b.keys, n, segs, col, nseg, b.nodes, b.parent, b.parent + b.cap); note_launch(); }
+}
+
+void edge_order(const int *edges, int ne, const hfcr_mesh &m, const int *segs, int col, int nseg,
+                int *order, int *order_alt, unsigned long long *keys, unsigned long long *keys_alt,
+                float *bounds_part, float *bounds, SortTemp &t, uint32_t *d_status, cudaStream_t s) {
+    if (ne <= 0 || m.n_verts <= 0) return;
+    const int nv = m.n_verts, nb = (ne + 255) / 256;
+    int vbk = (nv + 255) / 256;
+    if (vbk > 1024) vbk = 1024;
+    if (m.dtype == HFCR_F32) {
+        const float *x = (const float *)m.x, *y = (const float *)m.y, *z = (const float *)m.z;
+        { k_vertex_bounds<float><<<vbk, 256, 0, s>>>(x, y, z, nv, bounds_part); note_launch(); }
+        { k_bounds_final<<<1, 256, 0, s>>>(bounds_part, vbk, bounds); note_launch(); }
+        { k_edge_order_keys<float><<<nb, 256, 0, s>>>((const int2 *)edges, ne, x, y, z, nv, bounds, segs,
+                                                    col, nseg, keys, order, d_status); note_launch(); }
+    } else {
+        const double *x = (const double *)m.x, *y = (const double *)m.y, *z = (const double *)m.z;
+        { k_vertex_bounds<double><<<vbk, 256, 0, s>>>(x, y, z, nv, bounds_part); note_launch(); }
+        { k_bounds_final<<<1, 256, 0, s>>>(bounds_part, vbk, bounds); note_launch(); }
+        { k_edge_order_keys<double><<<nb, 256, 0, s>>>((const int2 *)edges, ne, x, y, z, nv, bounds, segs,
+                                                     col, nseg, keys, order, d_status); note_launch(); }
+    }
+    if (radix_sort_u64(keys, order, keys_alt, order_alt, ne, 30 + bits_for(nseg + 1), t, s))
+        cudaMemcpyAsync(order, order_alt, sizeof(int) * (size_t)ne, cudaMemcpyDeviceToDevice, s);
 }
 
 void bvh_refit(Bvh &b, const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s) {

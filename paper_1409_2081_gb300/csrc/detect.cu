@@ -89,11 +89,15 @@ __device__ __noinline__ bool leaf_test_call(const T *p, const T *q, const Leaf<T
 // of line.
 template <typename T, bool F32F, int MINB, bool NOINL>
 __global__ void __launch_bounds__(256, MINB) k_traverse(
-    const int2 *edges, int ne, const T *ex, const T *ey, const T *ez, int nv, const float4 *nodes,
-    const void *leaf_tri, int nfaces, const int *segs, int nseg, int ecol, int fcol,
-    unsigned long long dirbit, int face_bits, unsigned long long *out, int *count, int cap,
+    const int2 *edges, const int *order, int ne, const T *ex, const T *ey, const T *ez, int nv,
+    const float4 *nodes, const void *leaf_tri, int nfaces, const int *segs, int nseg, int ecol,
+    int fcol, unsigned long long dirbit, int face_bits, unsigned long long *out, int *count, int cap,
     DevStats *st, uint32_t *status) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    // thread t takes edge order[t] (a spatially coherent permutation of the
+    // edges, when there is one): a warp then walks neighbouring parts of the
+    // tree; the keys carry the edge's own index
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = t >= ne ? ne : (order ? order[t] : t);
     unsigned tests = 0;
     int2 ev = make_int2(0, 0);
     int pair = 0, t0 = 0, nleaf = 0;
@@ -303,7 +307,7 @@ static void launch_traverse(const DetectArgs &a, const T *x, const T *y, const T
                             unsigned long long dirbit, cudaStream_t s, uint32_t *d_status) {
     const hfcr_mesh &m = *a.edge_mesh;
     { k_traverse<T, F32F, MINB, NOINL><<<nb, 256, 0, s>>>(
-          (const int2 *)a.edges, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes, a.bvh->leaf_tri,
+          (const int2 *)a.edges, a.order, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes, a.bvh->leaf_tri,
           a.bvh->n, a.segs, a.nseg, a.ecol, a.fcol, dirbit, a.face_bits, a.keys, a.d_count, a.cap,
           a.stats, d_status); note_launch(); }
 }

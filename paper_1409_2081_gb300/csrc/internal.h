@@ -130,6 +130,12 @@ void bvh_build(Bvh &b, const hfcr_mesh &m, const int *segs, int col, int nseg, S
 void check_segments(const int *segs, int nseg, const hfcr_mesh &A, const hfcr_mesh &B,
                     uint32_t *d_status, cudaStream_t s);
 void bvh_refit(Bvh &b, const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s);
+// a traversal order of an edge list: the edges sorted by (segment, Morton
+// code of the midpoint in the mesh's vertex bounds), stable; order [ne] gets
+// the permutation (order_alt [ne] and the keys [ne] each are scratch)
+void edge_order(const int *edges, int ne, const hfcr_mesh &m, const int *segs, int col, int nseg,
+                int *order, int *order_alt, unsigned long long *keys, unsigned long long *keys_alt,
+                float *bounds_part, float *bounds, SortTemp &t, uint32_t *d_status, cudaStream_t s);
 
 // ---- validation ----
 void validate_positions(const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s);
@@ -141,6 +147,7 @@ struct DetectArgs {
     int ecol, fcol;     // vertex column of the edge mesh, face column of the face mesh
     const hfcr_mesh *edge_mesh;
     const int *edges;   // [n_edges][2]
+    const int *order = nullptr;  // traversal order of the edges (a permutation), or null
     int n_edges;
     const Bvh *bvh;     // over the faces of the other mesh
     int dir;
