@@ -114,6 +114,29 @@ def test_batch_resolve_leaves_no_pair(api):
     assert len(_oracle_union(scenes, segs, fA, fB)) == 0
 
 
+def test_batch_resolve_with_diffusion_deep_overlaps(api):
+    # deeper overlaps (centre distance 1.35..1.6 radii): the diffusion of Sec. 5
+    # spreads each pair's displacement over its own mesh only (the
+    # concatenated meshes have no edge between pairs), and the batched loop
+    # ends with no pair left
+    scenes = meshgen.scene_c4(n_pairs=12, lmax=3, seed=meshgen.BASE_SEED + 34, rho_lo=1.35, rho_hi=1.6)
+    A, PA, TA, B, PB, TB, segs, dsegs = _batch(api, scenes)
+    ctx = api.Context(diffuse_rings=4, diffuse_sweeps=16)
+    ctx.hfcr_reserve(max(len(PA), len(PB)), max(len(TA), len(TB)), 1 << 17)
+    info = ctx.hfcr_resolve_batch(A, B, dsegs, 1e-4, 64)
+    assert info.pairs_first > 0
+    assert info.converged, (info.iters, info.pairs_last)
+    fA, fB = positions(A), positions(B)
+    assert len(_oracle_union(scenes, segs, fA, fB)) == 0
+    # every vertex stayed within its own pair's displacement field: the
+    # vertices of a pair without any intersection did not move
+    for i, sc in enumerate(scenes):
+        a0, a1, b0, b1 = segs[i, 0], segs[i + 1, 0], segs[i, 2], segs[i + 1, 2]
+        hit = len(oracle.detect(PA[a0:a1], sc.A.T, True, PB[b0:b1], sc.B.T, True)) > 0
+        if not hit:
+            assert np.array_equal(fA[a0:a1], PA[a0:a1]) and np.array_equal(fB[b0:b1], PB[b0:b1])
+
+
 def test_full_batch_sampled(api):
     """1,024 pairs, levels 1..5 (the batched workload): every reported pair
     of a sample re-checked exactly, and 12 sampled pairs compared in full."""
