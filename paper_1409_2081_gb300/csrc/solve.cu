@@ -302,6 +302,57 @@ __device__ __forceinline__ void block_sum3(float a, float b, float c, float *red
     sc = __shfl_sync(0xffffffffu, q, 0);
 }
 
+// sum over the block, identical in every thread: each warp folds its values
+// with a butterfly and keeps lane 0's result, and every thread adds the warp
+// results in warp order
+__device__ __forceinline__ double block_sum_uniform(double x, double *redd) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    x = __shfl_sync(0xffffffffu, x, 0);
+    if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = x;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += redd[w];
+    __syncthreads();
+    return s;
+}
+
+// The thread group that solves one zone: a whole CTA (CtaGroup) or one
+// warp (WarpGroup, for small zones; barriers are __syncwarp and every
+// reduction stays in shuffles).  Sums are identical in every lane.
+struct CtaGroup {
+    __device__ static int rank() { return threadIdx.x; }
+    __device__ static int size() { return blockDim.x; }
+    __device__ static void sync() { __syncthreads(); }
+    __device__ static void sum3(float a, float b, float c, float *red, float &sa, float &sb,
+                                float &sc) {
+        block_sum3(a, b, c, red, sa, sb, sc);
+    }
+    __device__ static double sum(double x, double *redd) { return block_sum_uniform(x, redd); }
+};
+
+struct WarpGroup {
+    __device__ static int rank() { return threadIdx.x & 31; }
+    __device__ static int size() { return 32; }
+    __device__ static void sync() { __syncwarp(); }
+    __device__ static void sum3(float a, float b, float c, float *, float &sa, float &sb, float &sc) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        sa = __shfl_sync(0xffffffffu, a, 0);
+        sb = __shfl_sync(0xffffffffu, b, 0);
+        sc = __shfl_sync(0xffffffffu, c, 0);
+    }
+    __device__ static double sum(double x, double *) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        return __shfl_sync(0xffffffffu, x, 0);
+    }
+};
+
 // z = P^-1 r for the rows of one group (block-Jacobi over rows sharing x0)
 __device__ __forceinline__ void cg_precond_group(const CgView &v, int g) {
     const int a = v.gst[g] - v.goff, b = v.gst[g + 1] - v.goff;
@@ -314,9 +365,10 @@ __device__ __forceinline__ void cg_precond_group(const CgView &v, int g) {
     }
 }
 
+template <class Gp>
 __device__ __forceinline__ void cg_matvec_vertex(const CgView &v, int U) {
     const float third = 1.0f / 3.0f;
-    for (int j = threadIdx.x; j < U; j += blockDim.x) {
+    for (int j = Gp::rank(); j < U; j += Gp::size()) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
         const int e1 = v.seg[j + 1] - v.eoff;
         for (int e = v.seg[j] - v.eoff; e < e1; ++e) {
@@ -350,13 +402,14 @@ __device__ __forceinline__ float cg_matvec_stencil(const CgView &v, int s) {
 // iteration): u = P^-1 r, w = A u, s = A p by recurrence.  P is the
 // block-Jacobi preconditioner over the groups.  Stops when |r| <= tol |r0|.
 // Returns the iteration count; x holds the solution of A x = r0.
+template <class Gp>
 __device__ __forceinline__ int cg_cg_loop(const CgView &v, int k, int U, int maxit, float tol,
                                           float *red) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = Gp::rank(), nt = Gp::size();
     for (int g = tid; g < v.G; g += nt) cg_precond_group(v, g);
-    __syncthreads();
-    cg_matvec_vertex(v, U);
-    __syncthreads();
+    Gp::sync();
+    cg_matvec_vertex<Gp>(v, U);
+    Gp::sync();
     float ga = 0.f, de = 0.f, rh = 0.f;
     for (int s = tid; s < k; s += nt) {
         float ws = cg_matvec_stencil(v, s);
@@ -367,7 +420,7 @@ __device__ __forceinline__ int cg_cg_loop(const CgView &v, int k, int U, int max
         rh += rs * rs;
     }
     float gamma, delta, rho;
-    block_sum3(ga, de, rh, red, gamma, delta, rho);
+    Gp::sum3(ga, de, rh, red, gamma, delta, rho);
     const float stop = tol * tol * rho;
     float alpha = gamma / delta, beta = 0.f;
     int it = 0;
@@ -384,9 +437,9 @@ __device__ __forceinline__ int cg_cg_loop(const CgView &v, int k, int U, int max
             }
             cg_precond_group(v, g);
         }
-        __syncthreads();
-        cg_matvec_vertex(v, U);
-        __syncthreads();
+        Gp::sync();
+        cg_matvec_vertex<Gp>(v, U);
+        Gp::sync();
         ga = 0.f;
         de = 0.f;
         rh = 0.f;
@@ -399,7 +452,7 @@ __device__ __forceinline__ int cg_cg_loop(const CgView &v, int k, int U, int max
             rh += rs * rs;
         }
         float gn, dn, rn;
-        block_sum3(ga, de, rh, red, gn, dn, rn);
+        Gp::sum3(ga, de, rh, red, gn, dn, rn);
         beta = gn / gamma;
         alpha = gn / (dn - beta * gn / alpha);
         gamma = gn;
@@ -701,29 +754,15 @@ __global__ void k_group_inverse(const int *d_ng, const int *gst, const int4 *vid
     }
 }
 
-// sum over the block, identical in every thread: each warp folds its values
-// with a butterfly and keeps lane 0's result, and every thread adds the warp
-// results in warp order
-__device__ __forceinline__ double block_sum_uniform(double x, double *redd) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    x = __shfl_sync(0xffffffffu, x, 0);
-    if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = x;
-    __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += redd[w];
-    __syncthreads();
-    return s;
-}
-
 // float64 residual r = b - J M^-1 J^T lam of one zone (the float64 normals;
 // Eq. 7), written to v.r in float32 as the next right-hand side.  The
 // vertex half goes through u64 (global scratch, this zone's rows only).
 // Returns |r|^2, identical in every thread.
+template <class Gp>
 __device__ __forceinline__ double zone_residual(const CgView &v, int k, int U, int s0, int j0,
                                                 const double4_32a *n64, const double *b64,
                                                 const double *lam, double *u64, double *redd) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = Gp::rank(), nt = Gp::size();
     const double third = 1.0 / 3.0;
     for (int j = tid; j < U; j += nt) {
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
@@ -743,7 +782,7 @@ __device__ __forceinline__ double zone_residual(const CgView &v, int k, int U, i
         u[1] = w * a1;
         u[2] = w * a2;
     }
-    __syncthreads();
+    Gp::sync();
     double rr = 0.0;
     for (int t = tid; t < k; t += nt) {
         const int4 g = v.vidx[t];
@@ -759,125 +798,197 @@ __device__ __forceinline__ double zone_residual(const CgView &v, int k, int U, i
         v.r[t] = (float)r;
         rr += r * r;
     }
-    return block_sum_uniform(rr, redd);
+    return Gp::sum(rr, redd);
 }
 
-// The mixed solver, one CTA per impact zone (zones with at least `big_min`
-// stencils go to the launch with is_big = 1: 1024 threads and all of shared
-// memory; the others to is_big = 0: 256 threads and a quarter).  Per zone:
-// lam = 0, r = b; then rounds of iterative refinement, each a float32 PCG
-// solve of A x = r (relative tolerance tol), lam += x and the float64
-// residual, until |r|^2 <= rel_tol^2 |b_zone|^2 or max_refine rounds.
-// Meeting that in every zone meets |r| <= rel_tol |b| for the whole
-// system, whose matrix is block-diagonal by zone.  The zone's final |r|^2
-// and |b|^2 go to zres[z] and zbb[z].
+// Arguments of the zone solvers (device pointers of the zone-ordered system).
+struct ZoneArgs {
+    const int *zs, *zv, *zg;       // zone starts of rows, touched vertices, groups
+    const int *seg, *cval;         // vertex CSR (zone-contiguous)
+    const float *winv;
+    const float4 *n32, *pinv;
+    const double4_32a *n64;
+    const int4 *vidx;
+    const int *gst;
+    const double *b64;
+    double *lam, *u64, *zres, *zbb;
+    int maxit, max_refine;
+    double tol, rel_tol;
+    int *ctl;
+};
+
+// |b_zone|^2 with lam = 0 for the zone's rows
+template <class Gp>
+__device__ __forceinline__ double zone_start(const ZoneArgs &a, int s0, int k, double *redd) {
+    double bb = 0.0;
+    for (int t = Gp::rank(); t < k; t += Gp::size()) {
+        const double bv = a.b64[s0 + t];
+        bb += bv * bv;
+        a.lam[s0 + t] = 0.0;
+    }
+    return Gp::sum(bb, redd);
+}
+
+// shared memory a zone needs for the staged solve
+__device__ __forceinline__ long long zone_smem_need(int k, int U, int G) {
+    return 92ll * k + 24ll * U + 4ll * G + 32;
+}
+
+struct ZoneResult {
+    double rr;   // final |r|^2 of the zone
+    int its;     // CG iterations
+    int rounds;  // float32 runs
+};
+
+// Rounds of iterative refinement of zone z, everything the float32 CG
+// touches staged in shared memory at base (zone_smem_need bytes).
+template <class Gp>
+__device__ __forceinline__ ZoneResult solve_zone_smem(const ZoneArgs &a, int z, char *base, double bb,
+                                                      float *red, double *redd) {
+    const int tid = Gp::rank(), nt = Gp::size();
+    const int s0 = a.zs[z], k = a.zs[z + 1] - s0;
+    const int j0 = a.zv[z], U = a.zv[z + 1] - j0;
+    const int g0 = a.zg[z], G = a.zg[z + 1] - g0;
+    const int e0 = a.seg[j0];
+    const double target = a.rel_tol * a.rel_tol * bb;
+    CgView v;
+    // layout: vidx | n4 | pinv | u | r p x sv w z | seg | cval | winv | gst
+    int4 *vidx = (int4 *)base;
+    float4 *n4 = (float4 *)(vidx + k);
+    float4 *pinv = n4 + k;
+    v.u = pinv + k;
+    float *f = (float *)(v.u + U);
+    v.r = f; v.p = f + k; v.x = f + 2 * k; v.sv = f + 3 * k; v.w = f + 4 * k; v.z = f + 5 * k;
+    int *seg = (int *)(f + 6 * k);
+    int *cval = seg + U + 1;
+    float *winv = (float *)(cval + 4 * k);
+    int *gst = (int *)(winv + U);
+    for (int t = tid; t < k; t += nt) {
+        const int4 g = a.vidx[s0 + t];
+        vidx[t] = make_int4(g.x - j0, g.y - j0, g.z - j0, g.w - j0);
+        n4[t] = a.n32[s0 + t];
+        pinv[t] = a.pinv[s0 + t];
+        v.r[t] = (float)a.b64[s0 + t];
+    }
+    for (int g = tid; g <= G; g += nt) gst[g] = a.gst[g0 + g] - s0;
+    v.pinv = pinv; v.gst = gst; v.G = G; v.goff = 0;
+    for (int j = tid; j <= U; j += nt) seg[j] = a.seg[j0 + j] - e0;
+    for (int j = tid; j < U; j += nt) winv[j] = a.winv[j0 + j];
+    for (int e = tid; e < 4 * k; e += nt) cval[e] = a.cval[e0 + e] - 4 * s0;
+    v.n4 = n4;
+    v.vidx = vidx; v.seg = seg; v.cval = cval; v.winv = winv;
+    v.voff = 0; v.coff = 0; v.eoff = 0;
+    double rr = bb;
+    int its = 0, rounds = 0;
+    while (rr > target && rounds < a.max_refine) {
+        for (int t = tid; t < k; t += nt) {
+            v.p[t] = 0.f;
+            v.sv[t] = 0.f;
+            v.x[t] = 0.f;
+        }
+        Gp::sync();
+        its += cg_cg_loop<Gp>(v, k, U, a.maxit, (float)a.tol, red);
+        for (int t = tid; t < k; t += nt) a.lam[s0 + t] += (double)v.x[t];
+        Gp::sync();
+        rr = zone_residual<Gp>(v, k, U, s0, j0, a.n64, a.b64, a.lam, a.u64, redd);
+        ++rounds;
+    }
+    ZoneResult res;
+    res.rr = rr;
+    res.its = its;
+    res.rounds = rounds;
+    return res;
+}
+
+__device__ __forceinline__ void zone_finish(const ZoneArgs &a, int z, double rr, double bb, int its,
+                                            int rounds, bool in_smem) {
+    a.zres[z] = rr;
+    a.zbb[z] = bb;
+    atomicAdd(&a.ctl[1], its);
+    atomicAdd(&a.ctl[2], rounds);
+    atomicMax(&a.ctl[3], rounds);
+    atomicOr(&a.ctl[4], in_smem ? 1 : 2);
+}
+
+// One warp per zone of at most WARP_ZONE stencils (most zones of a batch of
+// small mesh pairs): a 256-thread CTA runs eight of them side by side, each
+// in its own WARP_ZONE_SMEM slice of shared memory.
+constexpr int WARP_ZONE = 32;
+constexpr int WARP_ZONE_SMEM = 6272;  // zone_smem_need(32, 128, 32) rounded up to 16 B
+constexpr int WARP_ZONE_WARPS = 8;
+
+__global__ void __launch_bounds__(256, 4) k_cg_zone_warp(const int *d_nz, ZoneArgs a) {
+    extern __shared__ float4 smem4[];
+    const int nz = *d_nz, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    char *base = (char *)smem4 + (size_t)w * WARP_ZONE_SMEM;
+    const int nwarps = gridDim.x * WARP_ZONE_WARPS;
+    for (int z = blockIdx.x * WARP_ZONE_WARPS + w; z < nz; z += nwarps) {
+        const int s0 = a.zs[z], k = a.zs[z + 1] - s0;
+        if (k > WARP_ZONE) continue;
+        const double bb = zone_start<WarpGroup>(a, s0, k, nullptr);
+        const ZoneResult r = solve_zone_smem<WarpGroup>(a, z, base, bb, nullptr, nullptr);
+        if (lane == 0) zone_finish(a, z, r.rr, bb, r.its, r.rounds, true);
+        __syncwarp();  // the slice is reused by the warp's next zone
+    }
+}
+
+// The mixed solver, one CTA per impact zone of more than warp_max stencils
+// (the zones k_cg_zone_warp took); the 256-thread launch (is_big = 0) takes the zones below
+// big_min, the 1024-thread launch (is_big = 1, all of shared memory) the
+// rest.  A zone whose data do not fit the CTA's shared memory runs the same
+// rounds on global scratch.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
-    const int *d_nz, const int *zs, const int *zv, int big_min, int is_big, const int *seg_g,
-    const int *cval_g, const float *winv_g, const float4 *n32, const double4_32a *n64,
-    const int4 *vidx_g, const float4 *pinv_g, const int *gst_g, const int *zg, const double *b64,
-    double *lam, double *u64, double *zres, double *zbb, float *x_g, float *r_g, float *p_g,
-    float *s_g, float *w_g, float *z_g, float *u_g, int maxit, int max_refine, double tol,
-    double rel_tol, int *ctl, int smem_bytes) {
+    const int *d_nz, ZoneArgs a, int warp_max, int big_min, int is_big, float *x_g, float *r_g,
+    float *p_g, float *s_g, float *w_g, float *z_g, float *u_g, int smem_bytes) {
     extern __shared__ float4 smem4[];
     __shared__ float red[96];
     __shared__ double redd[THREADS / 32];
     const int nz = *d_nz, tid = threadIdx.x, nt = blockDim.x;
     for (int z = blockIdx.x; z < nz; z += gridDim.x) {
-        const int s0 = zs[z], k = zs[z + 1] - s0;
-        const int j0 = zv[z], U = zv[z + 1] - j0;
-        if ((k >= big_min) != (is_big != 0)) continue;
-        double bb = 0.0;
-        for (int t = tid; t < k; t += nt) {
-            const double bv = b64[s0 + t];
-            bb += bv * bv;
-            lam[s0 + t] = 0.0;
-        }
-        bb = block_sum_uniform(bb, redd);
-        const double target = rel_tol * rel_tol * bb;
-        const int e0 = seg_g[j0];
-        const int g0 = zg[z], G = zg[z + 1] - g0;
-        const long long need = 92ll * k + 24ll * U + 4ll * G + 32;
-        double rr = bb;
+        const int s0 = a.zs[z], k = a.zs[z + 1] - s0;
+        const int j0 = a.zv[z], U = a.zv[z + 1] - j0;
+        if (k <= warp_max || (k >= big_min) != (is_big != 0)) continue;
+        const double bb = zone_start<CtaGroup>(a, s0, k, redd);
+        const int g0 = a.zg[z], G = a.zg[z + 1] - g0;
+        const bool in_smem = zone_smem_need(k, U, G) <= smem_bytes;
         int its = 0, rounds = 0;
-        const bool in_smem = need <= smem_bytes;
+        double rr;
         // the two paths are instantiated separately so that the shared-memory
         // one sees pointers derived only from the shared array (LDS/STS, not
         // generic loads)
         if (in_smem) {
-            CgView v;
-            // layout: vidx | n4 | pinv | u | r p x sv w z | seg | cval | winv | gst
-            char *base = (char *)smem4;
-            int4 *vidx = (int4 *)base;
-            float4 *n4 = (float4 *)(vidx + k);
-            float4 *pinv = n4 + k;
-            v.u = pinv + k;
-            float *f = (float *)(v.u + U);
-            v.r = f; v.p = f + k; v.x = f + 2 * k; v.sv = f + 3 * k; v.w = f + 4 * k; v.z = f + 5 * k;
-            int *seg = (int *)(f + 6 * k);
-            int *cval = seg + U + 1;
-            float *winv = (float *)(cval + 4 * k);
-            int *gst = (int *)(winv + U);
-            for (int t = tid; t < k; t += nt) {
-                int4 g = vidx_g[s0 + t];
-                vidx[t] = make_int4(g.x - j0, g.y - j0, g.z - j0, g.w - j0);
-                n4[t] = n32[s0 + t];
-                pinv[t] = pinv_g[s0 + t];
-                v.r[t] = (float)b64[s0 + t];
-            }
-            for (int g = tid; g <= G; g += nt) gst[g] = gst_g[g0 + g] - s0;
-            v.pinv = pinv; v.gst = gst; v.G = G; v.goff = 0;
-            for (int j = tid; j <= U; j += nt) seg[j] = seg_g[j0 + j] - e0;
-            for (int j = tid; j < U; j += nt) winv[j] = winv_g[j0 + j];
-            for (int e = tid; e < 4 * k; e += nt) cval[e] = cval_g[e0 + e] - 4 * s0;
-            v.n4 = n4;
-            v.vidx = vidx; v.seg = seg; v.cval = cval; v.winv = winv;
-            v.voff = 0; v.coff = 0; v.eoff = 0;
-            while (rr > target && rounds < max_refine) {
-                for (int t = tid; t < k; t += nt) {
-                    v.p[t] = 0.f;
-                    v.sv[t] = 0.f;
-                    v.x[t] = 0.f;
-                }
-                __syncthreads();
-                its += cg_cg_loop(v, k, U, maxit, (float)tol, red);
-                for (int t = tid; t < k; t += nt) lam[s0 + t] += (double)v.x[t];
-                __syncthreads();
-                rr = zone_residual(v, k, U, s0, j0, n64, b64, lam, u64, redd);
-                ++rounds;
-            }
+            const ZoneResult r = solve_zone_smem<CtaGroup>(a, z, (char *)smem4, bb, red, redd);
+            rr = r.rr;
+            its = r.its;
+            rounds = r.rounds;
         } else {
+            const double target = a.rel_tol * a.rel_tol * bb;
             CgView v;
             v.r = r_g + s0; v.p = p_g + s0; v.x = x_g + s0; v.sv = s_g + s0; v.w = w_g + s0;
             v.z = z_g + s0;
             v.u = (float4 *)u_g + j0;
-            v.n4 = n32 + s0;
-            v.pinv = pinv_g + s0; v.gst = gst_g + g0; v.G = G; v.goff = s0;
-            v.vidx = vidx_g + s0; v.seg = seg_g + j0; v.cval = cval_g; v.winv = winv_g + j0;
+            v.n4 = a.n32 + s0;
+            v.pinv = a.pinv + s0; v.gst = a.gst + g0; v.G = G; v.goff = s0;
+            v.vidx = a.vidx + s0; v.seg = a.seg + j0; v.cval = a.cval; v.winv = a.winv + j0;
             v.voff = j0; v.coff = 4 * s0; v.eoff = 0;
-            for (int t = tid; t < k; t += nt) v.r[t] = (float)b64[s0 + t];
-            while (rr > target && rounds < max_refine) {
+            for (int t = tid; t < k; t += nt) v.r[t] = (float)a.b64[s0 + t];
+            rr = bb;
+            while (rr > target && rounds < a.max_refine) {
                 for (int t = tid; t < k; t += nt) {
                     v.p[t] = 0.f;
                     v.sv[t] = 0.f;
                     v.x[t] = 0.f;
                 }
                 __syncthreads();
-                its += cg_cg_loop(v, k, U, maxit, (float)tol, red);
-                for (int t = tid; t < k; t += nt) lam[s0 + t] += (double)v.x[t];
+                its += cg_cg_loop<CtaGroup>(v, k, U, a.maxit, (float)a.tol, red);
+                for (int t = tid; t < k; t += nt) a.lam[s0 + t] += (double)v.x[t];
                 __syncthreads();
-                rr = zone_residual(v, k, U, s0, j0, n64, b64, lam, u64, redd);
+                rr = zone_residual<CtaGroup>(v, k, U, s0, j0, a.n64, a.b64, a.lam, a.u64, redd);
                 ++rounds;
             }
         }
-        if (tid == 0) {
-            zres[z] = rr;
-            zbb[z] = bb;
-            atomicAdd(&ctl[1], its);
-            atomicAdd(&ctl[2], rounds);
-            atomicMax(&ctl[3], rounds);
-            atomicOr(&ctl[4], in_smem ? 1 : 2);
-        }
+        if (tid == 0) zone_finish(a, z, rr, bb, its, rounds, in_smem);
         __syncthreads();  // shared memory is reused by the next zone
     }
 }
@@ -1051,7 +1162,7 @@ void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int ca
 
 // dynamic shared memory granted to the zone CG kernels (0: the global-memory
 // path runs); set once per process, outside any stream capture
-static int g_fast_smem = -1, g_zone_small_smem = 0;
+static int g_fast_smem = -1, g_zone_small_smem = 0, g_warp_zone_smem = 0;
 
 void solver_init() {
     if (g_fast_smem >= 0) return;
@@ -1061,6 +1172,10 @@ void solver_init() {
     g_zone_small_smem = cudaFuncSetAttribute(k_cg_zone<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              ZONE_SMALL_SMEM) == cudaSuccess ? ZONE_SMALL_SMEM : 0;
     if (!g_zone_small_smem) cudaGetLastError();
+    const int wz = WARP_ZONE_WARPS * WARP_ZONE_SMEM;
+    g_warp_zone_smem = cudaFuncSetAttribute(k_cg_zone_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            wz) == cudaSuccess ? wz : 0;
+    if (!g_warp_zone_smem) cudaGetLastError();
 }
 
 void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers &sb, SortTemp &t,
@@ -1148,20 +1263,29 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
     // MIXED: float32 PCG with float64 refinement, each zone to convergence
     // in its own CTA.  r64 and q64 (float64 scratch of the FP64 solver) hold
     // the zones' final |r|^2 and |b|^2.
+    ZoneArgs za;
+    za.zs = sb.zs; za.zv = sb.zv; za.zg = sb.zg;
+    za.seg = sb.seg; za.cval = sb.cval_s; za.winv = sb.winv;
+    za.n32 = sb.n32; za.pinv = sb.pinv; za.n64 = sb.n64; za.vidx = sb.vidx; za.gst = sb.gst;
+    za.b64 = sb.b; za.lam = sb.lam; za.u64 = sb.u64; za.zres = sb.r64; za.zbb = sb.q64;
+    za.maxit = p.max_cg_iters; za.max_refine = p.max_refine;
+    za.tol = p.inner_tol; za.rel_tol = p.rel_tol; za.ctl = sb.iwork;
+    const int warp_max = g_warp_zone_smem ? WARP_ZONE : 0;
+    if (warp_max) {
+        int zw = (cap + WARP_ZONE_WARPS - 1) / WARP_ZONE_WARPS;  // CTAs of the warp launch
+        if (zw > 4 * 152) zw = 4 * 152;
+        { k_cg_zone_warp<<<zw, 32 * WARP_ZONE_WARPS, g_warp_zone_smem, s>>>(sb.d_nz, za); note_launch(); }
+    }
     int zsmall = (cap + 1023) / 1024 * 4;  // blocks of the small-zone launch (grid-stride over zones)
     if (zsmall > 2048) zsmall = 2048;
     int zbig = (cap + ZONE_BIG - 1) / ZONE_BIG;
     if (zbig > 152) zbig = 152;
     { k_cg_zone<256><<<zsmall, 256, zone_small_smem, s>>>(
-          sb.d_nz, sb.zs, sb.zv, ZONE_BIG, 0, sb.seg, sb.cval_s, sb.winv, sb.n32, sb.n64, sb.vidx,
-          sb.pinv, sb.gst, sb.zg, sb.b, sb.lam, sb.u64, sb.r64, sb.q64, sb.x32, sb.r32, sb.p32,
-          sb.q32, sb.w32, sb.z32, sb.u32, p.max_cg_iters, p.max_refine, p.inner_tol, p.rel_tol,
-          sb.iwork, zone_small_smem); note_launch(); }
+          sb.d_nz, za, warp_max, ZONE_BIG, 0, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.z32, sb.u32,
+          zone_small_smem); note_launch(); }
     { k_cg_zone<CG_THREADS><<<zbig, CG_THREADS, fast_smem, s>>>(
-          sb.d_nz, sb.zs, sb.zv, ZONE_BIG, 1, sb.seg, sb.cval_s, sb.winv, sb.n32, sb.n64, sb.vidx,
-          sb.pinv, sb.gst, sb.zg, sb.b, sb.lam, sb.u64, sb.r64, sb.q64, sb.x32, sb.r32, sb.p32,
-          sb.q32, sb.w32, sb.z32, sb.u32, p.max_cg_iters, p.max_refine, p.inner_tol, p.rel_tol,
-          sb.iwork, fast_smem); note_launch(); }
+          sb.d_nz, za, warp_max, ZONE_BIG, 1, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.z32, sb.u32,
+          fast_smem); note_launch(); }
     { k_zone_final<<<1, 256, 0, s>>>(sb.d_nz, sb.r64, sb.q64, p.rel_tol, sb.dwork, sb.iwork); note_launch(); }
 }
 
