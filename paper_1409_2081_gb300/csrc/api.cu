@@ -146,7 +146,7 @@ void free_all(hfcr_ctx *c) {
     for (int i = 0; i < 2; ++i) {
         Bvh &b = c->bvh[i];
         void *bp[] = {b.nodes, b.parent, b.flags, b.leaf_face, b.leaf_tri, b.keys, b.keys_alt,
-                      b.vals_alt, b.bounds, b.bounds_part};
+                      b.vals_alt, b.bounds, b.bounds_part, b.d_rest};
         for (void *p : bp)
             if (p) cudaFree(p);
         b = Bvh();
@@ -784,6 +784,7 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
         CK(dalloc(&b.vals_alt, T));
         CK(dalloc(&b.bounds, 8));
         CK(dalloc(&b.bounds_part, 6 * 1024));
+        CK(dalloc(&b.d_rest, 1));
         CK(dalloc(&ctx->edges[i], 2 * E3));
         CK(dalloc(&ctx->eorder[i], E3));
     }

@@ -406,8 +406,14 @@ void bvh_build(Bvh &b, const hfcr_mesh &m, const int *segs, int col, int nseg, S
         { k_morton<double><<<nb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds, segs, col, nseg, b.keys,
                                             b.leaf_face, d_status); note_launch(); }
     }
-    bool flip = radix_sort_u64(b.keys, b.leaf_face, b.keys_alt, b.vals_alt, n, 30 + bits_for(nseg + 1),
-                               t, s);
+    // a batch sorts each pair's faces in its own CTA (the segment bits above
+    // the 30 Morton bits are constant within a pair); one mesh globally
+    bool flip = nseg > 1
+                    ? radix_sort_u64v_segments(b.keys, b.leaf_face, b.keys_alt, b.vals_alt, n,
+                                               30 + bits_for(nseg + 1), segs, col, nseg, 30, b.d_rest,
+                                               t, s)
+                    : radix_sort_u64(b.keys, b.leaf_face, b.keys_alt, b.vals_alt, n,
+                                     30 + bits_for(nseg + 1), t, s);
     if (flip) {
         cudaMemcpyAsync(b.keys, b.keys_alt, sizeof(unsigned long long) * n, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(b.leaf_face, b.vals_alt, sizeof(int) * n, cudaMemcpyDeviceToDevice, s);

@@ -81,6 +81,7 @@ struct Bvh {
     int *vals_alt = nullptr;
     float *bounds = nullptr;    // [6] scene bounds of the centroids
     float *bounds_part = nullptr;  // per-block partial bounds
+    int *d_rest = nullptr;      // [1] the segmented sort's request for the global sort
     int dtype = 0;
     // one tree per segment: segment i owns faces [segs[4 i + col], segs[4 (i + 1) + col])
     const int *segs = nullptr;
@@ -108,6 +109,14 @@ bool radix_sort_u32_dev(unsigned *k0, int *v0, unsigned *k1, int *v1, const int 
                         int bits, SortTemp &t, cudaStream_t s);
 bool radix_sort_u64v_dev(unsigned long long *k0, int *v0, unsigned long long *k1, int *v1,
                          const int *d_n, int cap, int bits, SortTemp &t, cudaStream_t s);
+// keys of a batch grouped by segment (segment number in the bits above
+// seg_bits): one CTA sorts each segment over its low seg_bits bits; if a
+// segment is longer than one CTA sorts, *d_rest (scratch) routes the whole
+// input through the global sort over all `bits` bits.  Same result and
+// buffer as radix_sort_u64 with values.
+bool radix_sort_u64v_segments(unsigned long long *k0, int *v0, unsigned long long *k1, int *v1,
+                              int n, int bits, const int *segs, int col, int nseg, int seg_bits,
+                              int *d_rest, SortTemp &t, cudaStream_t s);
 int sort_blocks_for(int n);
 
 // Exclusive scan of n unsigned flags (in place), total written to *d_total.

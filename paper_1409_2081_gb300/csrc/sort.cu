@@ -252,10 +252,48 @@ __global__ void __launch_bounds__(TPB) k_scatter(const K *kin, const int *vin, K
 // One CTA sorts all passes.  Returns (via *d_flip) nothing: the caller
 // knows the pass count and hence the buffer holding the result.
 template <typename K, bool HV>
+__device__ __forceinline__ void sort_small_body(K *k0, int *v0, K *k1, int *v1, int n, int bits);
+
+template <typename K, bool HV>
 __global__ void __launch_bounds__(TPB) k_sort_small(K *k0, int *v0, K *k1, int *v1, int n,
                                                     const int *d_n, int bits) {
     if (d_n) n = min(n, *d_n);
     if (n > SMALL_N) return;  // the multi-CTA kernels sort it
+    sort_small_body<K, HV>(k0, v0, k1, v1, n, bits);
+}
+
+// Each segment of a batch (CTA i: the keys of segment i, rows i and i + 1 of
+// the segment table, column col) sorted on its own by the single-CTA body,
+// in place at its offset, over the low `bits` bits (the higher bits are the
+// segment number, constant within a segment).  A segment longer than
+// SMALL_N is left alone and *d_rest gets n_total: the caller's global sort
+// then sorts everything.
+template <typename K, bool HV>
+__global__ void __launch_bounds__(TPB) k_sort_segments(K *k0, int *v0, K *k1, int *v1, int n_total,
+                                                       const int *segs, int col, int nseg, int bits,
+                                                       int *d_rest) {
+    const int i = blockIdx.x;
+    if (i >= nseg) return;
+    const int a = min(max(segs[4 * i + col], 0), n_total);
+    const int b = min(max(segs[4 * (i + 1) + col], a), n_total);
+    const int n = b - a;
+    if (n > SMALL_N) {
+        if (threadIdx.x == 0) *d_rest = n_total;
+        return;
+    }
+    if (n <= 1) {
+        // a sort of one key still ends in the buffer the passes would use
+        if (n == 1 && threadIdx.x == 0 && (((bits + 7) / 8) & 1)) {
+            k1[a] = k0[a];
+            if (HV) v1[a] = v0[a];
+        }
+        return;
+    }
+    sort_small_body<K, HV>(k0 + a, HV ? v0 + a : v0, k1 + a, HV ? v1 + a : v1, n, bits);
+}
+
+template <typename K, bool HV>
+__device__ __forceinline__ void sort_small_body(K *k0, int *v0, K *k1, int *v1, int n, int bits) {
     __shared__ unsigned wh[TPB / 32][256];
     __shared__ unsigned off[256];
     __shared__ unsigned cnt[256];
@@ -515,6 +553,22 @@ bool radix_sort_impl(K *k0, int *v0, K *k1, int *v1, int n, const int *d_n, int 
 }  // namespace
 
 int sort_blocks_for(int n) { return (n + TILE - 1) / TILE; }
+
+bool radix_sort_u64v_segments(unsigned long long *k0, int *v0, unsigned long long *k1, int *v1,
+                              int n, int bits, const int *segs, int col, int nseg, int seg_bits,
+                              int *d_rest, SortTemp &t, cudaStream_t s) {
+    const int passes = (bits + 7) / 8;
+    if (n <= 0 || passes == 0) return false;
+    // the segment sorts take as many passes as the global sort, or one more
+    // (a copy over constant bits) so that both leave the result in one buffer
+    int sp = (seg_bits + 7) / 8;
+    if ((sp & 1) != (passes & 1)) ++sp;
+    cudaMemsetAsync(d_rest, 0, sizeof(int), s);
+    { k_sort_segments<unsigned long long, true><<<nseg, TPB, 0, s>>>(k0, v0, k1, v1, n, segs, col, nseg,
+                                                                     sp * 8, d_rest); note_launch(); }
+    // everything again, globally, only if a segment was too long for one CTA
+    return radix_sort_impl<unsigned long long, true>(k0, v0, k1, v1, n, d_rest, bits, t, s);
+}
 
 bool radix_sort_u32(unsigned *k0, int *v0, unsigned *k1, int *v1, int n, int bits, SortTemp &t,
                     cudaStream_t s) {
