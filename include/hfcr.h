@@ -114,6 +114,8 @@ typedef struct {
     int32_t diffuse_rings;  /* Sec. 5 diffusion in hfcr_resolve (see hfcr_diffuse): rings R of the */
     int32_t diffuse_sweeps; /* band and Jacobi sweeps S; 0 (default) in either: no diffusion, the
                                minimizer's displacement is applied as it is */
+    int32_t traverse_variant; /* traversal kernel variant 0..4 used until hfcr_autotune picks one
+                                 (default 0; every variant finds the same pairs) */
 } hfcr_options;
 
 typedef struct {
@@ -281,8 +283,9 @@ hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, in
  * when segs is given, one pair when segs is NULL and n_pairs is ignored),
  * times every traversal variant (register
  * budget for 2, 3 or 4 CTAs of 256 threads per SM, exact narrow phase
- * inline or out of line) three times on this scene, and makes the fastest
- * the context's choice for every later call.  *chosen (host, may be NULL)
+ * inline or out of line, one walk per edge or one per warp of edges of the
+ * same mesh pair) three times on this scene, and makes the fastest the
+ * context's choice for every later call.  *chosen (host, may be NULL)
  * gets its index; ms (host [n_ms], may be NULL) the best time of each
  * variant.  Synchronises. */
 hfcr_status hfcr_autotune(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, int32_t n_pairs,

@@ -55,7 +55,8 @@ class hfcr_options(ctypes.Structure):
                 ("roles", ctypes.c_int32), ("max_cg_iters", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("rel_tol", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("graphs", ctypes.c_int32),
-                ("diffuse_rings", ctypes.c_int32), ("diffuse_sweeps", ctypes.c_int32)]
+                ("diffuse_rings", ctypes.c_int32), ("diffuse_sweeps", ctypes.c_int32),
+                ("traverse_variant", ctypes.c_int32)]
 
 
 class hfcr_solve_info(ctypes.Structure):
@@ -191,14 +192,17 @@ class Context:
     def __init__(self, solver: int = HFCR_SOLVER_MIXED, f32_filter: bool = True,
                  roles: int = HFCR_ROLES_ALTERNATE, max_cg_iters: int = 500, max_refine: int = 6,
                  rel_tol: float = 1e-12, inner_tol: float = 1e-4, graphs: bool = True,
-                 diffuse_rings: int = 0, diffuse_sweeps: int = 0):
+                 diffuse_rings: int = 0, diffuse_sweeps: int = 0, traverse_variant: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("hfcr needs a CUDA device")
         opt = hfcr_options(solver, int(f32_filter), roles, max_cg_iters, max_refine, rel_tol, inner_tol,
-                           int(graphs), diffuse_rings, diffuse_sweeps)
+                           int(graphs), diffuse_rings, diffuse_sweeps, traverse_variant)
         h = ctypes.c_void_p()
-        self._check(lib().hfcr_create(ctypes.byref(h), ctypes.byref(opt)), None)
+        self.handle = None
+        # a refused create has no context: its message is the thread's
+        # context-free one (hfcr_last_error(NULL))
+        self._check(lib().hfcr_create(ctypes.byref(h), ctypes.byref(opt)))
         self.handle = h
 
     def _check(self, status: int, h=None, allow=()):
@@ -227,7 +231,7 @@ class Context:
         self._check(lib().hfcr_autotune(self.handle, ctypes.byref(A.c), ctypes.byref(B.c), n_pairs,
                                         _ptr(segs), ctypes.byref(chosen), ms, 8,
                                         _stream_ptr(stream)))
-        return int(chosen.value), [round(ms[i], 5) for i in range(3)]
+        return int(chosen.value), [round(ms[i], 5) for i in range(5)]
 
     def hfcr_profile_enable(self, on: bool = True):
         self._check(lib().hfcr_profile_enable(self.handle, int(on)))

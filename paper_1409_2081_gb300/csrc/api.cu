@@ -703,6 +703,7 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
     c->opt.graphs = 1;
     c->opt.diffuse_rings = 0;
     c->opt.diffuse_sweeps = 0;
+    c->opt.traverse_variant = 0;
     if (opt) {
         c->opt = *opt;
         if (c->opt.max_cg_iters <= 0) c->opt.max_cg_iters = 500;
@@ -711,6 +712,11 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
         if (!(c->opt.inner_tol > 0)) c->opt.inner_tol = 1e-4;
         if (c->opt.solver != HFCR_SOLVER_FP64) c->opt.solver = HFCR_SOLVER_MIXED;
         if (c->opt.roles != HFCR_ROLES_BOTH) c->opt.roles = HFCR_ROLES_ALTERNATE;
+        if (c->opt.traverse_variant < 0 || c->opt.traverse_variant >= N_TRAVERSE_VARIANTS) {
+            delete c;
+            set_noctx_error("hfcr_create: traverse_variant out of range");
+            return HFCR_ERR_ARG;
+        }
         if (c->opt.diffuse_rings < 0 || c->opt.diffuse_sweeps < 0 || c->opt.diffuse_rings > 1024 ||
             c->opt.diffuse_sweeps > 100000) {
             delete c;
@@ -718,6 +724,7 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
             return HFCR_ERR_ARG;
         }
     }
+    c->trav_variant = c->opt.traverse_variant;
     cudaGetDevice(&c->device);
     *out = c;
     return HFCR_OK;

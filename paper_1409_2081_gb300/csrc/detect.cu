@@ -86,8 +86,13 @@ __device__ __noinline__ bool leaf_test_call(const T *p, const T *q, const Leaf<T
 
 // Traversal variants (picked by hfcr_autotune): MINB = CTAs of 256 threads
 // the compiler must fit per SM (register budget), NOINL = narrow phase out
-// of line.
-template <typename T, bool F32F, int MINB, bool NOINL>
+// of line, PACKET = a warp whose edges all belong to one mesh pair walks
+// that pair's tree together (one broadcast load per node, a node entered
+// when any lane's box overlaps it, a shared stack per warp); each lane still
+// tests exactly the leaves its own box overlaps, because every box of the
+// tree contains its children's, so the tests and pairs are those of the
+// per-thread walk.  Warps that span two pairs walk per thread.
+template <typename T, bool F32F, int MINB, bool NOINL, bool PACKET>
 __global__ void __launch_bounds__(256, MINB) k_traverse(
     const int2 *edges, const int *order, int ne, const T *ex, const T *ey, const T *ez, int nv,
     const float4 *nodes, const void *leaf_tri, int nfaces, const int *segs, int nseg, int ecol,
@@ -107,7 +112,97 @@ __global__ void __launch_bounds__(256, MINB) k_traverse(
         pair = seg_of(segs, ecol, nseg, ev.x);
         seg_range(segs, fcol, pair, nfaces, t0, nleaf);
     }
-    if (e < ne && nleaf > 0) {
+    const bool active = e < ne && nleaf > 0;
+    bool walked = false;  // by the warp's packet walk
+    if constexpr (PACKET) {
+        const unsigned full = 0xffffffffu;
+        const unsigned act = __ballot_sync(full, active);
+        const int leader = act ? __ffs(act) - 1 : 0;
+        const int lt0 = __shfl_sync(full, t0, leader), lnl = __shfl_sync(full, nleaf, leader);
+        if (act && __all_sync(full, !active || (t0 == lt0 && nleaf == lnl))) {
+            walked = true;
+            __shared__ int pstack[256 / 32][STACK];
+            int *stk = pstack[threadIdx.x >> 5];
+            const int lane = threadIdx.x & 31;
+            T p[3] = {0, 0, 0}, q[3] = {0, 0, 0};
+            float lo[3] = {1.f, 1.f, 1.f}, hi[3] = {0.f, 0.f, 0.f};  // empty for idle lanes
+            if (active) {
+                const int i0 = chk(ev.x, nv, status), i1 = chk(ev.y, nv, status);
+                p[0] = ex[i0]; p[1] = ey[i0]; p[2] = ez[i0];
+                q[0] = ex[i1]; q[1] = ey[i1]; q[2] = ez[i1];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    lo[k] = lo_f(p[k] < q[k] ? p[k] : q[k]);
+                    hi[k] = hi_f(p[k] < q[k] ? q[k] : p[k]);
+                }
+            }
+            const unsigned long long ebits = ((unsigned long long)e) << face_bits;
+            int sp = 0;
+            int node = lnl == 1 ? ~lt0 : lt0;
+            int visits = 0;
+            const int max_visits = 2 * lnl + 8;
+            while (true) {
+                if (++visits > max_visits) {
+                    if (lane == 0) atomicOr(status, ST_BAD_INDEX);
+                    break;
+                }
+                int leaf0 = -1, leaf1 = -1, next = -1, push = -1;
+                bool m0 = false, m1 = false;
+                if (node < 0) {
+                    leaf0 = ~node;
+                    m0 = active;
+                } else {
+                    const float4 *nd = nodes + 4 * node;
+                    const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+                    const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+                    const bool h0 = active && overlap(lo, hi, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
+                    const bool h1 = active && overlap(lo, hi, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
+                    const bool a0 = __any_sync(full, h0), a1 = __any_sync(full, h1);
+                    if (a0) {
+                        if (c0 < 0) { leaf0 = ~c0; m0 = h0; } else next = c0;
+                    }
+                    if (a1) {
+                        if (c1 < 0) { leaf1 = ~c1; m1 = h1; }
+                        else if (next < 0) next = c1;
+                        else push = c1;
+                    }
+                }
+#pragma unroll
+                for (int w = 0; w < 2; ++w) {
+                    const int lf = w ? leaf1 : leaf0;
+                    if (lf >= 0 && (w ? m1 : m0)) {
+                        Leaf<T> L;
+                        L.load(leaf_tri, lf);
+                        ++tests;
+                        bool hit;
+                        if constexpr (NOINL) hit = leaf_test_call<T, F32F>(p, q, L, st);
+                        else hit = leaf_test_body<T, F32F>(p, q, L, st);
+                        if (hit) {
+                            int pos = atomicAdd(count, 1);
+                            if (pos < cap) out[pos] = dirbit | ebits | (unsigned)L.face;
+                        }
+                    }
+                }
+                __syncwarp();
+                if (push >= 0) {
+                    if (sp < STACK) {
+                        if (lane == 0) stk[sp] = push;
+                        ++sp;
+                        __syncwarp();
+                    } else if (lane == 0) {
+                        atomicOr(status, ST_BAD_INDEX);  // unreachable: depth < 64
+                    }
+                }
+                if (next >= 0) {
+                    node = next;
+                    continue;
+                }
+                if (sp == 0) break;
+                node = stk[--sp];
+            }
+        }
+    }
+    if (active && !walked) {
         int i0 = chk(ev.x, nv, status), i1 = chk(ev.y, nv, status);
         T p[3] = {ex[i0], ey[i0], ez[i0]}, q[3] = {ex[i1], ey[i1], ez[i1]};
         float lo[3], hi[3];
@@ -302,11 +397,11 @@ void clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *d_status, cudaSt
     { k_clamp_count<<<1, 1, 0, s>>>(d_n, cap, d_eff, d_status); note_launch(); }
 }
 
-template <typename T, bool F32F, int MINB, bool NOINL>
+template <typename T, bool F32F, int MINB, bool NOINL, bool PACKET>
 static void launch_traverse(const DetectArgs &a, const T *x, const T *y, const T *z, int nb,
                             unsigned long long dirbit, cudaStream_t s, uint32_t *d_status) {
     const hfcr_mesh &m = *a.edge_mesh;
-    { k_traverse<T, F32F, MINB, NOINL><<<nb, 256, 0, s>>>(
+    { k_traverse<T, F32F, MINB, NOINL, PACKET><<<nb, 256, 0, s>>>(
           (const int2 *)a.edges, a.order, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes, a.bvh->leaf_tri,
           a.bvh->n, a.segs, a.nseg, a.ecol, a.fcol, dirbit, a.face_bits, a.keys, a.d_count, a.cap,
           a.stats, d_status); note_launch(); }
@@ -316,9 +411,11 @@ template <typename T, bool F32F>
 static void launch_variant(const DetectArgs &a, const T *x, const T *y, const T *z, int nb,
                            unsigned long long dirbit, cudaStream_t s, uint32_t *d_status) {
     switch (a.variant) {
-        case 1: launch_traverse<T, F32F, 4, true>(a, x, y, z, nb, dirbit, s, d_status); break;
-        case 2: launch_traverse<T, F32F, 3, true>(a, x, y, z, nb, dirbit, s, d_status); break;
-        default: launch_traverse<T, F32F, 2, false>(a, x, y, z, nb, dirbit, s, d_status); break;
+        case 1: launch_traverse<T, F32F, 4, true, false>(a, x, y, z, nb, dirbit, s, d_status); break;
+        case 2: launch_traverse<T, F32F, 3, true, false>(a, x, y, z, nb, dirbit, s, d_status); break;
+        case 3: launch_traverse<T, F32F, 2, false, true>(a, x, y, z, nb, dirbit, s, d_status); break;
+        case 4: launch_traverse<T, F32F, 4, true, true>(a, x, y, z, nb, dirbit, s, d_status); break;
+        default: launch_traverse<T, F32F, 2, false, false>(a, x, y, z, nb, dirbit, s, d_status); break;
     }
 }
 

@@ -70,6 +70,14 @@ def test_batch_pairs_equal_per_pair_oracle(api):
     g, info = respond(ctx, A, B, st_t, k, 1e-4, len(PA), len(PB), np.float32)
     rA, rB, _, _ = oracle.respond(stc, PA, TA, PB, TB, 1e-4)
     assert rel_err(g, np.concatenate([rA, rB])) <= 1e-6
+    # every traversal variant, the per-warp packet walks included (warps of
+    # these small pairs often span two pairs and fall back to per-edge walks)
+    for v in range(1, 5):
+        cv = api.Context(traverse_variant=v)
+        cv.hfcr_reserve(max(len(PA), len(PB)), max(len(TA), len(TB)), 1 << 17)
+        nv = cv.hfcr_detect_batch(A, B, dsegs, out)
+        assert nv == n and np.array_equal(out[:nv].cpu().numpy().astype(np.uint32), ref), v
+        cv.close()
 
 
 def _sides(rec, PA, TA, PB, TB):
