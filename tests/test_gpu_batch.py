@@ -145,6 +145,30 @@ def test_batch_resolve_with_diffusion_deep_overlaps(api):
             assert np.array_equal(fA[a0:a1], PA[a0:a1]) and np.array_equal(fB[b0:b1], PB[b0:b1])
 
 
+def test_batch_with_a_long_pair_takes_the_global_sort(api):
+    # a pair whose mesh has more faces than one CTA sorts (36,000 > 32,768):
+    # the per-pair BVH sort hands the whole batch to the global sort, and
+    # the pairs still equal the per-pair oracle's
+    import torch
+    rng = np.random.default_rng(41)
+    VT, TT = meshgen.torus(200, 90, 1.0, 0.3)
+    VS, TS = meshgen.icosphere(2, 0.5)
+    scenes = []
+    for k in range(3):
+        VA = VS + np.array([1.0, 0.0, 0.25]) + rng.uniform(-0.05, 0.05, 3)
+        VB, TB = (VT, TT) if k == 1 else meshgen.icosphere(2, 0.6)
+        scenes.append(meshgen.Scene(meshgen.Mesh(VA, TS, True), meshgen.Mesh(VB, TB, True), np.float32))
+    A, PA, TA, B, PB, TB, segs, dsegs = _batch(api, scenes)
+    assert segs[2, 3] - segs[1, 3] > 32768
+    ctx = api.Context()
+    ctx.hfcr_reserve(max(len(PA), len(PB)), max(len(TA), len(TB)), 1 << 17)
+    out = torch.zeros((1 << 17, 4), dtype=torch.int32, device="cuda:0")
+    n = ctx.hfcr_detect_batch(A, B, dsegs, out)
+    got = out[:n].cpu().numpy().astype(np.uint32)
+    ref = _oracle_union(scenes, segs, PA, PB)
+    assert n > 0 and n == len(ref) and np.array_equal(got, ref)
+
+
 def test_full_batch_sampled(api):
     """1,024 pairs, levels 1..5 (the batched workload): every reported pair
     of a sample re-checked exactly, and 12 sampled pairs compared in full."""
