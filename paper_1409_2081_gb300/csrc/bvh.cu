@@ -21,6 +21,7 @@ namespace {
 // the mesh sizes (the concatenated A and B)
 __global__ void k_check_segs(const int *segs, int nseg, int nva, int nta, int nvb, int ntb,
                              uint32_t *st) {
+    HFCR_PDL_WAIT();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i > nseg) return;
     const int tot[4] = {nva, nta, nvb, ntb};
@@ -41,6 +42,7 @@ __device__ __forceinline__ int chk(int i, int n, uint32_t *st) {
 
 template <typename T>
 __global__ void k_validate(const T *x, const T *y, const T *z, int n, uint32_t *status) {
+    HFCR_PDL_WAIT();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t bad = 0;
     if (i < n) {
@@ -63,6 +65,7 @@ __global__ void k_validate(const T *x, const T *y, const T *z, int n, uint32_t *
 
 __global__ void k_edge_keys(const int *tris, int nt, int vb, unsigned long long *keys,
                             uint32_t *status, int nv) {
+    HFCR_PDL_WAIT();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
@@ -79,12 +82,14 @@ __global__ void k_edge_keys(const int *tris, int nt, int vb, unsigned long long 
 }
 
 __global__ void k_unique_flags(const unsigned long long *keys, int n, unsigned *flags) {
+    HFCR_PDL_WAIT();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
 }
 
 __global__ void k_write_edges(const unsigned long long *keys, const unsigned *pos, int n, int vb,
                               int *edges) {
+    HFCR_PDL_WAIT();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (i == 0 || keys[i] != keys[i - 1]) {
@@ -112,6 +117,7 @@ __device__ __forceinline__ float hi_f(double v) { return __double2float_ru(v); }
 // the leaves)
 template <typename T>
 __global__ void k_vertex_bounds(const T *x, const T *y, const T *z, int nv, float *part) {
+    HFCR_PDL_WAIT();
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
         const float c[3] = {(float)x[v], (float)y[v], (float)z[v]};
@@ -143,6 +149,7 @@ __global__ void k_vertex_bounds(const T *x, const T *y, const T *z, int nv, floa
 
 // the nb per-block partials folded by one CTA of 256 threads
 __global__ void __launch_bounds__(256) k_bounds_final(const float *part, int nb, float *bounds) {
+    HFCR_PDL_WAIT();
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
     for (int i = threadIdx.x; i < nb; i += blockDim.x)
 #pragma unroll
@@ -181,6 +188,7 @@ template <typename T>
 __global__ void k_morton(const T *x, const T *y, const T *z, int nv, const int *tris, int nt,
                          const float *bounds, const int *segs, int col, int nseg,
                          unsigned long long *keys, int *vals, uint32_t *st) {
+    HFCR_PDL_WAIT();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     T a[3], b[3], c[3];
@@ -207,6 +215,7 @@ template <typename T>
 __global__ void k_edge_order_keys(const int2 *edges, int ne, const T *x, const T *y, const T *z,
                                   int nv, const float *bounds, const int *segs, int col, int nseg,
                                   unsigned long long *keys, int *vals, uint32_t *st) {
+    HFCR_PDL_WAIT();
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
     const int2 ed = edges[e];
@@ -241,6 +250,7 @@ __device__ __forceinline__ int kdelta(const unsigned long long *K, int n, int i,
 // t0 + c (encoded ~(t0 + c)); each segment's root (l = 0) has parent -1.
 __global__ void k_karras(const unsigned long long *keys, int n_total, const int *segs, int col,
                          int nseg, float4 *nodes, int *iparent, int *lparent) {
+    HFCR_PDL_WAIT();
     int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= n_total) return;
     const int sgi = seg_of(segs, col, nseg, gi);
@@ -299,6 +309,7 @@ template <typename T>
 __global__ void k_refit(const T *x, const T *y, const T *z, int nv, const int *tris,
                         const int *leaf_face, int n, float4 *nodes, const int *iparent,
                         const int *lparent, unsigned *flags, void *leaf_tri, uint32_t *st) {
+    HFCR_PDL_WAIT();
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     int f = leaf_face[j];
@@ -349,10 +360,10 @@ void validate_positions(const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s) 
     if (m.n_verts <= 0) return;
     int nb = (m.n_verts + 255) / 256;
     if (m.dtype == HFCR_F32)
-        { k_validate<float><<<nb, 256, 0, s>>>((const float *)m.x, (const float *)m.y,
+        { launch_pdl(k_validate<float>, nb, 256, 0, s, (const float *)m.x, (const float *)m.y,
                                              (const float *)m.z, m.n_verts, d_status); note_launch(); }
     else
-        { k_validate<double><<<nb, 256, 0, s>>>((const double *)m.x, (const double *)m.y,
+        { launch_pdl(k_validate<double>, nb, 256, 0, s, (const double *)m.x, (const double *)m.y,
                                               (const double *)m.z, m.n_verts, d_status); note_launch(); }
 }
 
@@ -365,17 +376,20 @@ void build_edges(const int *tris, int n_tris, int n_verts, int *edges_out, int *
         return;
     }
     int vb = bits_for(n_verts > 1 ? n_verts : 2);
-    { k_edge_keys<<<(n_tris + 255) / 256, 256, 0, s>>>(tris, n_tris, vb, keys, d_status, n_verts); note_launch(); }
+    { launch_pdl(k_edge_keys, (n_tris + 255) / 256, 256, 0, s, tris, n_tris, vb, keys, d_status,
+                 n_verts); note_launch(); }
     bool flip = radix_sort_u64(keys, nullptr, keys_alt, nullptr, n, 2 * vb, t, s);
     unsigned long long *sorted = flip ? keys_alt : keys;
-    { k_unique_flags<<<(n + 255) / 256, 256, 0, s>>>(sorted, n, flags); note_launch(); }
+    { launch_pdl(k_unique_flags, (n + 255) / 256, 256, 0, s, sorted, n, flags); note_launch(); }
     scan_flags_dev(flags, nullptr, n, d_count, t, s);
-    { k_write_edges<<<(n + 255) / 256, 256, 0, s>>>(sorted, flags, n, vb, edges_out); note_launch(); }
+    { launch_pdl(k_write_edges, (n + 255) / 256, 256, 0, s, sorted, flags, n, vb,
+                 edges_out); note_launch(); }
 }
 
 void check_segments(const int *segs, int nseg, const hfcr_mesh &A, const hfcr_mesh &B,
                     uint32_t *d_status, cudaStream_t s) {
-    { k_check_segs<<<(nseg + 1 + 127) / 128, 128, 0, s>>>(segs, nseg, A.n_verts, A.n_tris, B.n_verts,
+    { launch_pdl(k_check_segs, (nseg + 1 + 127) / 128, 128, 0, s, segs, nseg, A.n_verts, A.n_tris,
+                 B.n_verts,
                                                         B.n_tris, d_status); note_launch(); }
 }
 
@@ -395,15 +409,19 @@ void bvh_build(Bvh &b, const hfcr_mesh &m, const int *segs, int col, int nseg, S
     if (vbk < 1) vbk = 1;
     if (m.dtype == HFCR_F32) {
         const float *x = (const float *)m.x, *y = (const float *)m.y, *z = (const float *)m.z;
-        { k_vertex_bounds<float><<<vbk, 256, 0, s>>>(x, y, z, nv, b.bounds_part); note_launch(); }
-        { k_bounds_final<<<1, 256, 0, s>>>(b.bounds_part, vbk, b.bounds); note_launch(); }
-        { k_morton<float><<<nb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds, segs, col, nseg, b.keys,
+        { launch_pdl(k_vertex_bounds<float>, vbk, 256, 0, s, x, y, z, nv,
+                     b.bounds_part); note_launch(); }
+        { launch_pdl(k_bounds_final, 1, 256, 0, s, b.bounds_part, vbk, b.bounds); note_launch(); }
+        { launch_pdl(k_morton<float>, nb, 256, 0, s, x, y, z, nv, m.tris, n, b.bounds, segs, col,
+                     nseg, b.keys,
                                            b.leaf_face, d_status); note_launch(); }
     } else {
         const double *x = (const double *)m.x, *y = (const double *)m.y, *z = (const double *)m.z;
-        { k_vertex_bounds<double><<<vbk, 256, 0, s>>>(x, y, z, nv, b.bounds_part); note_launch(); }
-        { k_bounds_final<<<1, 256, 0, s>>>(b.bounds_part, vbk, b.bounds); note_launch(); }
-        { k_morton<double><<<nb, 256, 0, s>>>(x, y, z, nv, m.tris, n, b.bounds, segs, col, nseg, b.keys,
+        { launch_pdl(k_vertex_bounds<double>, vbk, 256, 0, s, x, y, z, nv,
+                     b.bounds_part); note_launch(); }
+        { launch_pdl(k_bounds_final, 1, 256, 0, s, b.bounds_part, vbk, b.bounds); note_launch(); }
+        { launch_pdl(k_morton<double>, nb, 256, 0, s, x, y, z, nv, m.tris, n, b.bounds, segs, col,
+                     nseg, b.keys,
                                             b.leaf_face, d_status); note_launch(); }
     }
     // a batch sorts each pair's faces in its own CTA (the segment bits above
@@ -420,7 +438,8 @@ void bvh_build(Bvh &b, const hfcr_mesh &m, const int *segs, int col, int nseg, S
     }
     // leaves of one-face segments keep parent -1
     cudaMemsetAsync(b.parent + b.cap, 0xff, sizeof(int) * n, s);
-    { k_karras<<<nb, 256, 0, s>>>(b.keys, n, segs, col, nseg, b.nodes, b.parent, b.parent + b.cap); note_launch(); }
+    { launch_pdl(k_karras, nb, 256, 0, s, b.keys, n, segs, col, nseg, b.nodes, b.parent,
+                 b.parent + b.cap); note_launch(); }
 }
 
 void edge_order(const int *edges, int ne, const hfcr_mesh &m, const int *segs, int col, int nseg,
@@ -432,15 +451,19 @@ void edge_order(const int *edges, int ne, const hfcr_mesh &m, const int *segs, i
     if (vbk > 1024) vbk = 1024;
     if (m.dtype == HFCR_F32) {
         const float *x = (const float *)m.x, *y = (const float *)m.y, *z = (const float *)m.z;
-        { k_vertex_bounds<float><<<vbk, 256, 0, s>>>(x, y, z, nv, bounds_part); note_launch(); }
-        { k_bounds_final<<<1, 256, 0, s>>>(bounds_part, vbk, bounds); note_launch(); }
-        { k_edge_order_keys<float><<<nb, 256, 0, s>>>((const int2 *)edges, ne, x, y, z, nv, bounds, segs,
+        { launch_pdl(k_vertex_bounds<float>, vbk, 256, 0, s, x, y, z, nv,
+                     bounds_part); note_launch(); }
+        { launch_pdl(k_bounds_final, 1, 256, 0, s, bounds_part, vbk, bounds); note_launch(); }
+        { launch_pdl(k_edge_order_keys<float>, nb, 256, 0, s, (const int2 *)edges, ne, x, y, z,
+                     nv, bounds, segs,
                                                     col, nseg, keys, order, d_status); note_launch(); }
     } else {
         const double *x = (const double *)m.x, *y = (const double *)m.y, *z = (const double *)m.z;
-        { k_vertex_bounds<double><<<vbk, 256, 0, s>>>(x, y, z, nv, bounds_part); note_launch(); }
-        { k_bounds_final<<<1, 256, 0, s>>>(bounds_part, vbk, bounds); note_launch(); }
-        { k_edge_order_keys<double><<<nb, 256, 0, s>>>((const int2 *)edges, ne, x, y, z, nv, bounds, segs,
+        { launch_pdl(k_vertex_bounds<double>, vbk, 256, 0, s, x, y, z, nv,
+                     bounds_part); note_launch(); }
+        { launch_pdl(k_bounds_final, 1, 256, 0, s, bounds_part, vbk, bounds); note_launch(); }
+        { launch_pdl(k_edge_order_keys<double>, nb, 256, 0, s, (const int2 *)edges, ne, x, y, z,
+                     nv, bounds, segs,
                                                      col, nseg, keys, order, d_status); note_launch(); }
     }
     if (radix_sort_u64(keys, order, keys_alt, order_alt, ne, 30 + bits_for(nseg + 1), t, s))
@@ -453,11 +476,12 @@ void bvh_refit(Bvh &b, const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s) {
     cudaMemsetAsync(b.flags, 0, sizeof(unsigned) * n, s);
     int nb = (n + 255) / 256;
     if (m.dtype == HFCR_F32)
-        { k_refit<float><<<nb, 256, 0, s>>>((const float *)m.x, (const float *)m.y, (const float *)m.z,
+        { launch_pdl(k_refit<float>, nb, 256, 0, s, (const float *)m.x, (const float *)m.y,
+                     (const float *)m.z,
                                           m.n_verts, m.tris, b.leaf_face, n, b.nodes, b.parent,
                                           b.parent + b.cap, b.flags, b.leaf_tri, d_status); note_launch(); }
     else
-        { k_refit<double><<<nb, 256, 0, s>>>((const double *)m.x, (const double *)m.y,
+        { launch_pdl(k_refit<double>, nb, 256, 0, s, (const double *)m.x, (const double *)m.y,
                                            (const double *)m.z, m.n_verts, m.tris, b.leaf_face, n,
                                            b.nodes, b.parent, b.parent + b.cap, b.flags, b.leaf_tri,
                                            d_status); note_launch(); }

@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(256, MINB) k_traverse(
     const float4 *nodes, const void *leaf_tri, int nfaces, const int *segs, int nseg, int ecol,
     int fcol, unsigned long long dirbit, int face_bits, unsigned long long *out, int *count, int cap,
     DevStats *st, uint32_t *status) {
+    HFCR_PDL_WAIT();
     // thread t takes edge order[t] (a spatially coherent permutation of the
     // edges, when there is one): a warp then walks neighbouring parts of the
     // tree; the keys carry the edge's own index
@@ -276,6 +277,7 @@ __global__ void __launch_bounds__(256, MINB) k_traverse(
 __global__ void k_keys_to_pairs(const unsigned long long *keys, const int *d_n, int cap,
                                 const int2 *edgesA, const int2 *edgesB, int edge_bits,
                                 int face_bits, hfcr_pair *out) {
+    HFCR_PDL_WAIT();
     int n = min(*d_n, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -299,6 +301,7 @@ template <typename T>
 __global__ void k_stencil_keys(hfcr_mesh A, hfcr_mesh B, const hfcr_pair *pairs, const int *d_n,
                                int cap, int vert_bits, int face_bits, int f32_filter,
                                unsigned long long *keys, DevStats *st, uint32_t *status) {
+    HFCR_PDL_WAIT();
     int n = min(*d_n, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -326,6 +329,7 @@ __global__ void k_stencil_keys(hfcr_mesh A, hfcr_mesh B, const hfcr_pair *pairs,
 
 __global__ void k_stencil_flags(const unsigned long long *keys, const int *d_n, int cap,
                                 unsigned *flags) {
+    HFCR_PDL_WAIT();
     int n = min(*d_n, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
@@ -334,6 +338,7 @@ __global__ void k_stencil_flags(const unsigned long long *keys, const int *d_n, 
 __global__ void k_stencil_write(const unsigned long long *keys, const unsigned *pos,
                                 const int *d_n, int cap, int vert_bits, int face_bits,
                                 hfcr_stencil *out) {
+    HFCR_PDL_WAIT();
     int n = min(*d_n, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -351,6 +356,7 @@ __global__ void k_stencil_write(const unsigned long long *keys, const unsigned *
 // effective count = count when it fits the capacity, else 0 with
 // ST_CAPACITY raised (so nothing downstream runs on a truncated set)
 __global__ void k_clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *status) {
+    HFCR_PDL_WAIT();
     int n = *d_n;
     if (n > cap) {
         atomicOr(status, ST_CAPACITY);
@@ -370,6 +376,7 @@ __device__ __forceinline__ int first_edge_from(const int2 *E, int ne, int v) {
 
 __global__ void k_pair_products(const int2 *E, int ne, const int *segs, int nseg, int ecol, int fcol,
                                 int nfaces, DevStats *st) {
+    HFCR_PDL_WAIT();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long v = 0;
     if (i < nseg) {
@@ -389,20 +396,21 @@ __global__ void k_pair_products(const int2 *E, int ne, const int *segs, int nseg
 void pair_products(const int *edges, int ne, const int *segs, int nseg, int ecol, int fcol,
                    int nfaces, DevStats *stats, cudaStream_t s) {
     if (ne <= 0 || nseg <= 0) return;
-    { k_pair_products<<<(nseg + 255) / 256, 256, 0, s>>>((const int2 *)edges, ne, segs, nseg, ecol,
+    { launch_pdl(k_pair_products, (nseg + 255) / 256, 256, 0, s, (const int2 *)edges, ne, segs,
+                 nseg, ecol,
                                                         fcol, nfaces, stats); note_launch(); }
 }
 
 void clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *d_status, cudaStream_t s) {
-    { k_clamp_count<<<1, 1, 0, s>>>(d_n, cap, d_eff, d_status); note_launch(); }
+    { launch_pdl(k_clamp_count, 1, 1, 0, s, d_n, cap, d_eff, d_status); note_launch(); }
 }
 
 template <typename T, bool F32F, int MINB, bool NOINL, bool PACKET>
 static void launch_traverse(const DetectArgs &a, const T *x, const T *y, const T *z, int nb,
                             unsigned long long dirbit, cudaStream_t s, uint32_t *d_status) {
     const hfcr_mesh &m = *a.edge_mesh;
-    { k_traverse<T, F32F, MINB, NOINL, PACKET><<<nb, 256, 0, s>>>(
-          (const int2 *)a.edges, a.order, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes, a.bvh->leaf_tri,
+    { launch_pdl(k_traverse<T, F32F, MINB, NOINL, PACKET>, nb, 256, 0, s, (const int2 *)a.edges,
+                 a.order, a.n_edges, x, y, z, m.n_verts, a.bvh->nodes, a.bvh->leaf_tri,
           a.bvh->n, a.segs, a.nseg, a.ecol, a.fcol, dirbit, a.face_bits, a.keys, a.d_count, a.cap,
           a.stats, d_status); note_launch(); }
 }
@@ -437,7 +445,8 @@ void detect_launch(const DetectArgs &a, cudaStream_t s, uint32_t *d_status) {
 void keys_to_pairs(const unsigned long long *keys, const int *d_n, int cap, const int *edgesA,
                    const int *edgesB, int edge_bits, int face_bits, hfcr_pair *out, cudaStream_t s) {
     if (cap <= 0) return;
-    { k_keys_to_pairs<<<(cap + 255) / 256, 256, 0, s>>>(keys, d_n, cap, (const int2 *)edgesA,
+    { launch_pdl(k_keys_to_pairs, (cap + 255) / 256, 256, 0, s, keys, d_n, cap,
+                 (const int2 *)edgesA,
                                                       (const int2 *)edgesB, edge_bits, face_bits, out); note_launch(); }
 }
 
@@ -447,10 +456,12 @@ void stencil_keys(const MeshPair &mp, const hfcr_pair *pairs, const int *d_n, in
     if (cap <= 0) return;
     int nb = (cap + 255) / 256;
     if (mp.A.dtype == HFCR_F32)
-        { k_stencil_keys<float><<<nb, 256, 0, s>>>(mp.A, mp.B, pairs, d_n, cap, vert_bits, face_bits,
+        { launch_pdl(k_stencil_keys<float>, nb, 256, 0, s, mp.A, mp.B, pairs, d_n, cap, vert_bits,
+                     face_bits,
                                                  f32_filter, keys, stats, d_status); note_launch(); }
     else
-        { k_stencil_keys<double><<<nb, 256, 0, s>>>(mp.A, mp.B, pairs, d_n, cap, vert_bits, face_bits,
+        { launch_pdl(k_stencil_keys<double>, nb, 256, 0, s, mp.A, mp.B, pairs, d_n, cap,
+                     vert_bits, face_bits,
                                                   f32_filter, keys, stats, d_status); note_launch(); }
 }
 
@@ -459,9 +470,10 @@ void stencil_unique(const unsigned long long *keys, const int *d_n, int cap, int
                     cudaStream_t s) {
     if (cap <= 0) return;
     int nb = (cap + 255) / 256;
-    { k_stencil_flags<<<nb, 256, 0, s>>>(keys, d_n, cap, flags); note_launch(); }
+    { launch_pdl(k_stencil_flags, nb, 256, 0, s, keys, d_n, cap, flags); note_launch(); }
     scan_flags_dev(flags, d_n, cap, d_k, t, s);
-    { k_stencil_write<<<nb, 256, 0, s>>>(keys, flags, d_n, cap, vert_bits, face_bits, out); note_launch(); }
+    { launch_pdl(k_stencil_write, nb, 256, 0, s, keys, flags, d_n, cap, vert_bits, face_bits,
+                 out); note_launch(); }
 }
 
 }  // namespace hfcr

@@ -23,6 +23,7 @@ namespace hfcr {
 namespace {
 
 __global__ void k_adj_count(const int2 *edges, int ne, int nv, int *deg, uint32_t *st) {
+    HFCR_PDL_WAIT();
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
     const int2 ed = edges[e];
@@ -35,6 +36,7 @@ __global__ void k_adj_count(const int2 *edges, int ne, int nv, int *deg, uint32_
 }
 
 __global__ void k_adj_fill(const int2 *edges, int ne, int nv, const int *ptr, int *cur, int *nbr) {
+    HFCR_PDL_WAIT();
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
     const int2 ed = edges[e];
@@ -45,6 +47,7 @@ __global__ void k_adj_fill(const int2 *edges, int ne, int nv, const int *ptr, in
 
 // ascending order within each vertex's list (the fill order is arbitrary)
 __global__ void k_adj_sort(const int *ptr, int nv, int *nbr) {
+    HFCR_PDL_WAIT();
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     const int a = ptr[v], b = ptr[v + 1];
@@ -71,6 +74,7 @@ struct DPair {
 };
 
 __global__ void k_ring_init(DPair P, const double *u, int *ring, int far) {
+    HFCR_PDL_WAIT();
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= P.ntot) return;
     const double *x = u + 3 * (size_t)g;
@@ -80,6 +84,7 @@ __global__ void k_ring_init(DPair P, const double *u, int *ring, int far) {
 // breadth-first level r: a vertex not reached yet joins when a neighbour
 // sits at level r - 1 (levels r - 1 and below no longer change)
 __global__ void k_ring_step(DPair P, int *ring, int r, int far) {
+    HFCR_PDL_WAIT();
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= P.ntot || ring[g] != far) return;
     const DMesh &M = P.of(g);
@@ -94,6 +99,7 @@ __global__ void k_ring_step(DPair P, int *ring, int r, int far) {
 // one Jacobi sweep: band vertices (1 <= ring <= R, not kinematic) take the
 // neighbour mean; every other vertex keeps its value
 __global__ void k_sweep(DPair P, const int *ring, int R, const double *uin, double *uout) {
+    HFCR_PDL_WAIT();
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= P.ntot) return;
     const DMesh &M = P.of(g);
@@ -135,6 +141,7 @@ __device__ __forceinline__ void add_to(void *p, int i, double d) {
 // x' = x + u on the vertices within R rings (u is zero elsewhere)
 __global__ void k_apply_field(hfcr_mesh A, hfcr_mesh B, const int *ring, int R, const double *u,
                               int ntot) {
+    HFCR_PDL_WAIT();
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ntot) return;
     const int rg = ring[g];
@@ -155,6 +162,7 @@ __global__ void k_apply_field(hfcr_mesh A, hfcr_mesh B, const int *ring, int R, 
 }
 
 __global__ void k_soa_to_aos(const double *x, const double *y, const double *z, int n, double *u) {
+    HFCR_PDL_WAIT();
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     u[3 * (size_t)v] = x[v];
@@ -163,6 +171,7 @@ __global__ void k_soa_to_aos(const double *x, const double *y, const double *z, 
 }
 
 __global__ void k_aos_to_soa(const double *u, int n, double *x, double *y, double *z) {
+    HFCR_PDL_WAIT();
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     x[v] = u[3 * (size_t)v];
@@ -187,11 +196,13 @@ void build_adjacency(const int *edges, int ne, int nv, int *ptr, int *nbr, int *
     if (nv <= 0) return;
     cudaMemsetAsync(ptr, 0, sizeof(int) * (size_t)(nv + 1), s);
     cudaMemsetAsync(cur, 0, sizeof(int) * (size_t)nv, s);
-    if (ne > 0) { k_adj_count<<<blocks(ne), 256, 0, s>>>((const int2 *)edges, ne, nv, ptr, d_status); note_launch(); }
+    if (ne > 0) { launch_pdl(k_adj_count, blocks(ne), 256, 0, s, (const int2 *)edges, ne, nv, ptr,
+                             d_status); note_launch(); }
     // degrees -> exclusive offsets in place, total (2 x valid edges) to ptr[nv]
     scan_flags_dev((unsigned *)ptr, nullptr, nv, ptr + nv, t, s);
-    if (ne > 0) { k_adj_fill<<<blocks(ne), 256, 0, s>>>((const int2 *)edges, ne, nv, ptr, cur, nbr); note_launch(); }
-    { k_adj_sort<<<blocks(nv), 256, 0, s>>>(ptr, nv, nbr); note_launch(); }
+    if (ne > 0) { launch_pdl(k_adj_fill, blocks(ne), 256, 0, s, (const int2 *)edges, ne, nv, ptr,
+                             cur, nbr); note_launch(); }
+    { launch_pdl(k_adj_sort, blocks(nv), 256, 0, s, ptr, nv, nbr); note_launch(); }
 }
 
 const double *diffuse_field(const DiffMeshArgs &a, const DiffMeshArgs &b, double *u, double *u_alt,
@@ -199,11 +210,12 @@ const double *diffuse_field(const DiffMeshArgs &a, const DiffMeshArgs &b, double
     DPair P = make_pair(a, b);
     if (P.ntot <= 0) return u;
     const int far = rings + 1, nb = blocks(P.ntot);
-    { k_ring_init<<<nb, 256, 0, s>>>(P, u, ring, far); note_launch(); }
-    for (int r = 1; r <= rings; ++r) { k_ring_step<<<nb, 256, 0, s>>>(P, ring, r, far); note_launch(); }
+    { launch_pdl(k_ring_init, nb, 256, 0, s, P, u, ring, far); note_launch(); }
+    for (int r = 1; r <= rings; ++r) { launch_pdl(k_ring_step, nb, 256, 0, s, P, ring, r,
+                                                  far); note_launch(); }
     double *in = u, *out = u_alt;
     for (int q = 0; q < sweeps; ++q) {
-        { k_sweep<<<nb, 256, 0, s>>>(P, ring, rings, in, out); note_launch(); }
+        { launch_pdl(k_sweep, nb, 256, 0, s, P, ring, rings, in, out); note_launch(); }
         double *tmp = in; in = out; out = tmp;
     }
     return in;
@@ -213,16 +225,17 @@ void apply_field(const hfcr_mesh &A, const hfcr_mesh &B, const int *ring, int ri
                  const double *u, cudaStream_t s) {
     const int ntot = A.n_verts + B.n_verts;
     if (ntot <= 0) return;
-    { k_apply_field<<<blocks(ntot), 256, 0, s>>>(A, B, ring, rings, u, ntot); note_launch(); }
+    { launch_pdl(k_apply_field, blocks(ntot), 256, 0, s, A, B, ring, rings, u,
+                 ntot); note_launch(); }
 }
 
 void field_from_soa(const double *x, const double *y, const double *z, int n, double *u,
                     cudaStream_t s) {
-    if (n > 0) { k_soa_to_aos<<<blocks(n), 256, 0, s>>>(x, y, z, n, u); note_launch(); }
+    if (n > 0) { launch_pdl(k_soa_to_aos, blocks(n), 256, 0, s, x, y, z, n, u); note_launch(); }
 }
 
 void field_to_soa(const double *u, int n, double *x, double *y, double *z, cudaStream_t s) {
-    if (n > 0) { k_aos_to_soa<<<blocks(n), 256, 0, s>>>(u, n, x, y, z); note_launch(); }
+    if (n > 0) { launch_pdl(k_aos_to_soa, blocks(n), 256, 0, s, u, n, x, y, z); note_launch(); }
 }
 
 }  // namespace hfcr

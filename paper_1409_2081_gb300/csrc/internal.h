@@ -16,6 +16,31 @@ namespace hfcr {
 extern std::atomic<long long> g_launches;
 inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// Every kernel of the library starts with HFCR_PDL_WAIT.  Launched by
+// launch_pdl, a kernel is the programmatic dependent of the previous kernel
+// in its stream: it may be scheduled while that kernel still runs, and the
+// wait holds each thread until that kernel has completed and its writes
+// are visible (no kernel triggers its dependents early), so the order is
+// that of a plain launch and only the launch latency overlaps.  Launched
+// any other way, the wait returns at once.
+#define HFCR_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
+
 // Device-side status bits (one 32-bit word per context, OR-ed by kernels).
 enum : uint32_t {
     ST_NONFINITE = 1u << 0,

@@ -49,6 +49,7 @@ __device__ __forceinline__ void ld_pos(const hfcr_mesh &m, int i, double *o) {
 __global__ void k_assemble(hfcr_mesh A, hfcr_mesh B, const hfcr_stencil *st, const int *d_k,
                            int cap, double d, int4 *ids, double4_32a *n64, float4 *n32, double *b,
                            uint32_t *status) {
+    HFCR_PDL_WAIT();
     int k = min(*d_k, cap);
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= k) return;
@@ -89,6 +90,7 @@ __global__ void k_assemble(hfcr_mesh A, hfcr_mesh B, const hfcr_stencil *st, con
 }
 
 __global__ void k_csr_entries(const int4 *ids, const int *d_k, int cap, unsigned *key, int *val) {
+    HFCR_PDL_WAIT();
     int k = min(*d_k, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 4 * k) return;
@@ -99,6 +101,7 @@ __global__ void k_csr_entries(const int4 *ids, const int *d_k, int cap, unsigned
 
 __global__ void k_csr_flags(const unsigned *key, const int *d_k, int cap, unsigned *flag,
                             int *d_n4) {
+    HFCR_PDL_WAIT();
     int n = 4 * min(*d_k, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *d_n4 = n;
@@ -108,6 +111,7 @@ __global__ void k_csr_flags(const unsigned *key, const int *d_k, int cap, unsign
 __global__ void k_csr_build(const unsigned *key, const int *val, const unsigned *excl,
                             const int *d_k, int cap, int nA, const float *wA, const float *wB,
                             int4 *vidx, int *seg, int *gvert, float *winv) {
+    HFCR_PDL_WAIT();
     int n = 4 * min(*d_k, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -159,6 +163,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg(
     int mode, const int *d_k, const int *d_U, const int *seg, const int *cval, const float *winv,
     const typename NrmT<T>::type *nrm, const int4 *vidx, const double *rhs64, double *lam, T *x,
     T *r, T *p, T *q, T *u, int maxit, double tol, int *ctl) {
+    HFCR_PDL_WAIT();
     __shared__ T sh[33];
     if (mode == 0 && ctl[0]) return;
     const int k = *d_k, U = *d_U, tid = threadIdx.x;
@@ -498,6 +503,7 @@ __device__ __forceinline__ int uf_find_s(volatile int *par, int x) {
 __global__ void __launch_bounds__(1024) k_uf_small(const int *d_k, const int *d_U, const int *seg,
                                                    const int *cval, unsigned *zlab, int *zsrc,
                                                    uint32_t *status) {
+    HFCR_PDL_WAIT();
     __shared__ int par[UF_SMALL];
     const int k = *d_k;
     if (k > UF_SMALL) return;
@@ -530,6 +536,7 @@ __global__ void __launch_bounds__(1024) k_uf_small(const int *d_k, const int *d_
 }
 
 __global__ void k_uf_init(const int *d_k, int *parent) {
+    HFCR_PDL_WAIT();
     const int k = *d_k;
     if (k <= UF_SMALL) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
@@ -539,6 +546,7 @@ __global__ void k_uf_init(const int *d_k, int *parent) {
 // unions the stencils of every touched vertex (CSR by vertex)
 __global__ void k_uf_union(const int *d_k, const int *d_U, const int *seg, const int *cval,
                            int *parent, uint32_t *status) {
+    HFCR_PDL_WAIT();
     if (*d_k <= UF_SMALL) return;
     const int U = *d_U;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < U; j += gridDim.x * blockDim.x) {
@@ -565,6 +573,7 @@ __global__ void k_uf_union(const int *d_k, const int *d_U, const int *seg, const
 
 // zone label of every stencil (its root = the smallest stencil of its zone)
 __global__ void k_zone_keys(const int *d_k, int *parent, unsigned *zlab, int *zsrc) {
+    HFCR_PDL_WAIT();
     const int k = *d_k;
     if (k <= UF_SMALL) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
@@ -574,6 +583,7 @@ __global__ void k_zone_keys(const int *d_k, int *parent, unsigned *zlab, int *zs
 }
 
 __global__ void k_zone_flags(const int *d_k, const unsigned *zlab, unsigned *flags) {
+    HFCR_PDL_WAIT();
     const int k = *d_k;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x)
         flags[t] = (t == 0 || zlab[t] != zlab[t - 1]) ? 1u : 0u;
@@ -586,6 +596,7 @@ __global__ void k_zone_gather(const int *d_k, const unsigned *zlab, const int *z
                               const double4_32a *n64_raw, const float4 *n32_raw,
                               const double *b_raw, int4 *ids, double4_32a *n64, float4 *n32,
                               double *b, int *szone, int *zs, int *pos_of) {
+    HFCR_PDL_WAIT();
     const int k = *d_k;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
         int src = zsrc[t];
@@ -607,6 +618,7 @@ __global__ void k_zone_gather(const int *d_k, const unsigned *zlab, const int *z
 // (vertex order kept inside a zone) and entries renumbered to zone order.
 __global__ void k_csr2_entries(const int *cv1, const int *pos_of, const int *szone,
                                const int *d_k, int cap, unsigned *key, int *val) {
+    HFCR_PDL_WAIT();
     int k = min(*d_k, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 4 * k) return;
@@ -618,6 +630,7 @@ __global__ void k_csr2_entries(const int *cv1, const int *pos_of, const int *szo
 
 __global__ void k_csr2_flags(const int *val, const int4 *ids, const int *d_k, int cap,
                              unsigned *flag) {
+    HFCR_PDL_WAIT();
     int n = 4 * min(*d_k, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n)
@@ -628,6 +641,7 @@ __global__ void k_csr2_build(const unsigned *zkey, const int *val, const unsigne
                              const int4 *ids, const int *d_k, int cap, int nA, const float *wA,
                              const float *wB, int4 *vidx, int *seg, int *gvert, float *winv,
                              int *zv, const int *d_nz) {
+    HFCR_PDL_WAIT();
     int n = 4 * min(*d_k, cap);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -668,6 +682,7 @@ __device__ __forceinline__ bool group_start(const int4 *ids, const int *szone, c
 
 __global__ void k_group_flags(const int *d_k, const int4 *ids, const int *szone, const int *zs,
                               unsigned *flags) {
+    HFCR_PDL_WAIT();
     const int k = *d_k;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x)
         flags[t] = group_start(ids, szone, zs, t) ? 1u : 0u;
@@ -675,6 +690,7 @@ __global__ void k_group_flags(const int *d_k, const int4 *ids, const int *szone,
 
 __global__ void k_group_build(const int *d_k, const int4 *ids, const int *szone, const int *zs,
                               const unsigned *excl, const int *d_nz, int *gst, int *zg) {
+    HFCR_PDL_WAIT();
     const int k = *d_k;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
         const bool st = group_start(ids, szone, zs, t);
@@ -696,6 +712,7 @@ __global__ void k_group_build(const int *d_k, const int4 *ids, const int *szone,
 // A_ab = (n_a . n_b) (w(x0) + 1/9 sum of w over the face vertices shared by a and b)
 __global__ void k_group_inverse(const int *d_ng, const int *gst, const int4 *vidx,
                                 const double4_32a *n64, const float *winv, float4 *pinv) {
+    HFCR_PDL_WAIT();
     const int ng = *d_ng;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
         const int a0 = gst[g], m = gst[g + 1] - a0;
@@ -918,6 +935,7 @@ constexpr int WARP_ZONE_SMEM = 6272;  // zone_smem_need(32, 128, 32) rounded up 
 constexpr int WARP_ZONE_WARPS = 8;
 
 __global__ void __launch_bounds__(256, 4) k_cg_zone_warp(const int *d_nz, ZoneArgs a) {
+    HFCR_PDL_WAIT();
     extern __shared__ float4 smem4[];
     const int nz = *d_nz, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     char *base = (char *)smem4 + (size_t)w * WARP_ZONE_SMEM;
@@ -941,6 +959,7 @@ template <int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
     const int *d_nz, ZoneArgs a, int warp_max, int big_min, int is_big, float *x_g, float *r_g,
     float *p_g, float *s_g, float *w_g, float *z_g, float *u_g, int smem_bytes) {
+    HFCR_PDL_WAIT();
     extern __shared__ float4 smem4[];
     __shared__ float red[96];
     __shared__ double redd[THREADS / 32];
@@ -998,6 +1017,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
 __global__ void __launch_bounds__(256) k_zone_final(const int *d_nz, const double *zres,
                                                     const double *zbb, double rel_tol,
                                                     double *dres, int *ctl) {
+    HFCR_PDL_WAIT();
     __shared__ double redd[8];
     const int nz = *d_nz;
     double R = 0.0, Bn = 0.0;
@@ -1018,6 +1038,7 @@ __global__ void __launch_bounds__(256) k_zone_final(const int *d_nz, const doubl
 // float64 residual, vertex half: u = M^-1 J^T lam
 __global__ void k_res_vertex(const int *d_U, const int *seg, const int *cval, const float *winv,
                              const double4_32a *n64, const double *lam, double *u, const int *ctl) {
+    HFCR_PDL_WAIT();
     if (ctl[0]) return;
     const int U = *d_U;
     const double third = 1.0 / 3.0;
@@ -1048,6 +1069,7 @@ __global__ void k_res_stencil(const int *d_k, const int4 *vidx, const double4_32
                               const double *b, const double *u, double *r, double *red,
                               int *ctl, unsigned *ticket, double rel_tol, double *dres,
                               int count_round) {
+    HFCR_PDL_WAIT();
     __shared__ double sh[33];
     __shared__ bool last;
     if (ctl[0]) return;
@@ -1090,6 +1112,7 @@ __global__ void k_res_stencil(const int *d_k, const int4 *vidx, const double4_32
 }
 
 __global__ void k_init_lam(const int *d_k, const double *b, double *lam, double *r) {
+    HFCR_PDL_WAIT();
     const int k = *d_k;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < k; s += gridDim.x * blockDim.x) {
         lam[s] = 0.0;
@@ -1104,6 +1127,7 @@ __global__ void k_displace(const int *d_U, const int *seg, const int *cval, cons
                            const double4_32a *n64, const double *lam, const int *gvert, hfcr_mesh A,
                            hfcr_mesh B, int apply, void *dA0, void *dA1, void *dA2, void *dB0,
                            void *dB1, void *dB2) {
+    HFCR_PDL_WAIT();
     const int U = *d_U;
     const double third = 1.0 / 3.0;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < U; j += gridDim.x * blockDim.x) {
@@ -1156,7 +1180,7 @@ __global__ void k_displace(const int *d_U, const int *seg, const int *cval, cons
 void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int cap, double d,
               SolveBuffers &sb, uint32_t *d_status, cudaStream_t s) {
     if (cap <= 0) return;
-    { k_assemble<<<(cap + 255) / 256, 256, 0, s>>>(mp.A, mp.B, st, d_k, cap, d, sb.ids_raw,
+    { launch_pdl(k_assemble, (cap + 255) / 256, 256, 0, s, mp.A, mp.B, st, d_k, cap, d, sb.ids_raw,
                                                  sb.n64_raw, sb.n32_raw, sb.b_raw, d_status); note_launch(); }
 }
 
@@ -1186,15 +1210,18 @@ void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers 
     int gb = (cap + 255) / 256;
     if (gb > 1024) gb = 1024;
     // vertex -> stencils of the rows as assembled (for the impact zones)
-    { k_csr_entries<<<nb, 256, 0, s>>>(sb.ids_raw, d_k, cap, sb.ckey, sb.cval); note_launch(); }
-    { k_csr_flags<<<1, 1, 0, s>>>(sb.ckey, d_k, cap, sb.cflag, d_n4); note_launch(); }  // count only
+    { launch_pdl(k_csr_entries, nb, 256, 0, s, sb.ids_raw, d_k, cap, sb.ckey,
+                 sb.cval); note_launch(); }
+    { launch_pdl(k_csr_flags, 1, 1, 0, s, sb.ckey, d_k, cap, sb.cflag,
+                 d_n4); note_launch(); }  // count only
     int vb = bits_for((long long)mp.A.n_verts + mp.B.n_verts);
     bool flip = radix_sort_u32_dev(sb.ckey, sb.cval, sb.ckey_alt, sb.cval_alt, d_n4, n4, vb, t, s);
     unsigned *ck1 = flip ? sb.ckey_alt : sb.ckey;
     int *cv1 = flip ? sb.cval_alt : sb.cval;
-    { k_csr_flags<<<nb, 256, 0, s>>>(ck1, d_k, cap, sb.cflag, d_n4); note_launch(); }
+    { launch_pdl(k_csr_flags, nb, 256, 0, s, ck1, d_k, cap, sb.cflag, d_n4); note_launch(); }
     scan_flags_dev(sb.cflag, d_n4, n4, sb.d_U, t, s);
-    { k_csr_build<<<nb, 256, 0, s>>>(ck1, cv1, sb.cflag, d_k, cap, mp.A.n_verts, mp.A.inv_mass,
+    { launch_pdl(k_csr_build, nb, 256, 0, s, ck1, cv1, sb.cflag, d_k, cap, mp.A.n_verts,
+                 mp.A.inv_mass,
                                    mp.B.inv_mass, sb.vidx, sb.seg, sb.gvert, sb.winv); note_launch(); }
     // impact zones and the zone-ordered rows.  The 64-bit scratch arrays
     // are used as pairs of 32-bit arrays: (label, stencil) for the zone sort,
@@ -1202,39 +1229,48 @@ void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers 
     int kb = bits_for((long long)cap + 1);
     unsigned *zlab = (unsigned *)sb.zkey, *zlab_alt = (unsigned *)sb.zkey_alt;
     int *zsrc = (int *)sb.zkey + cap, *zsrc_alt = (int *)sb.zkey_alt + cap;
-    { k_uf_small<<<1, 1024, 0, s>>>(d_k, sb.d_U, sb.seg, cv1, zlab, zsrc, d_status); note_launch(); }
+    { launch_pdl(k_uf_small, 1, 1024, 0, s, d_k, sb.d_U, sb.seg, cv1, zlab, zsrc,
+                 d_status); note_launch(); }
     if (cap > UF_SMALL) {
-        { k_uf_init<<<gb, 256, 0, s>>>(d_k, sb.parent); note_launch(); }
-        { k_uf_union<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(d_k, sb.d_U, sb.seg, cv1, sb.parent, d_status); note_launch(); }
-        { k_zone_keys<<<gb, 256, 0, s>>>(d_k, sb.parent, zlab, zsrc); note_launch(); }
+        { launch_pdl(k_uf_init, gb, 256, 0, s, d_k, sb.parent); note_launch(); }
+        { launch_pdl(k_uf_union, nb < 1024 ? nb : 1024, 256, 0, s, d_k, sb.d_U, sb.seg, cv1,
+                     sb.parent, d_status); note_launch(); }
+        { launch_pdl(k_zone_keys, gb, 256, 0, s, d_k, sb.parent, zlab, zsrc); note_launch(); }
     }
     bool zflip = radix_sort_u32_dev(zlab, zsrc, zlab_alt, zsrc_alt, d_k, cap, kb, t, s);
     unsigned *zl = zflip ? zlab_alt : zlab;
     int *zr = zflip ? zsrc_alt : zsrc;
-    { k_zone_flags<<<gb, 256, 0, s>>>(d_k, zl, sb.cflag); note_launch(); }
+    { launch_pdl(k_zone_flags, gb, 256, 0, s, d_k, zl, sb.cflag); note_launch(); }
     scan_flags_dev(sb.cflag, d_k, cap, sb.d_nz, t, s);
     int *pos_of = sb.parent;  // the forest is no longer needed
-    { k_zone_gather<<<gb, 256, 0, s>>>(d_k, zl, zr, sb.cflag, sb.ids_raw, sb.n64_raw, sb.n32_raw,
+    { launch_pdl(k_zone_gather, gb, 256, 0, s, d_k, zl, zr, sb.cflag, sb.ids_raw, sb.n64_raw,
+                 sb.n32_raw,
                                      sb.b_raw, sb.ids, sb.n64, sb.n32, sb.b, sb.szone, sb.zs,
                                      pos_of); note_launch(); }
     // vertex-ordered entries re-sorted stably by zone: zone-contiguous numbering
     unsigned *k2 = (unsigned *)sb.ck64, *k2_alt = (unsigned *)sb.ck64_alt;
     int *v2 = (int *)sb.ck64 + n4, *v2_alt = (int *)sb.ck64_alt + n4;
-    { k_csr2_entries<<<nb, 256, 0, s>>>(cv1, pos_of, sb.szone, d_k, cap, k2, v2); note_launch(); }
+    { launch_pdl(k_csr2_entries, nb, 256, 0, s, cv1, pos_of, sb.szone, d_k, cap, k2,
+                 v2); note_launch(); }
     bool flip2 = radix_sort_u32_dev(k2, v2, k2_alt, v2_alt, d_n4, n4, kb, t, s);
     unsigned *zk2 = flip2 ? k2_alt : k2;
     sb.cval_s = flip2 ? v2_alt : v2;
-    { k_csr2_flags<<<nb, 256, 0, s>>>(sb.cval_s, sb.ids, d_k, cap, sb.cflag); note_launch(); }
+    { launch_pdl(k_csr2_flags, nb, 256, 0, s, sb.cval_s, sb.ids, d_k, cap,
+                 sb.cflag); note_launch(); }
     scan_flags_dev(sb.cflag, d_n4, n4, sb.d_U, t, s);
-    { k_csr2_build<<<nb, 256, 0, s>>>(zk2, sb.cval_s, sb.cflag, sb.ids, d_k, cap, mp.A.n_verts,
+    { launch_pdl(k_csr2_build, nb, 256, 0, s, zk2, sb.cval_s, sb.cflag, sb.ids, d_k, cap,
+                 mp.A.n_verts,
                                     mp.A.inv_mass, mp.B.inv_mass, sb.vidx, sb.seg, sb.gvert, sb.winv,
                                     sb.zv, sb.d_nz); note_launch(); }
     // groups of rows sharing x0 and the inverses of their blocks
-    { k_group_flags<<<gb, 256, 0, s>>>(d_k, sb.ids, sb.szone, sb.zs, sb.cflag); note_launch(); }
+    { launch_pdl(k_group_flags, gb, 256, 0, s, d_k, sb.ids, sb.szone, sb.zs,
+                 sb.cflag); note_launch(); }
     scan_flags_dev(sb.cflag, d_k, cap, sb.d_ng, t, s);
-    { k_group_build<<<gb, 256, 0, s>>>(d_k, sb.ids, sb.szone, sb.zs, sb.cflag, sb.d_nz, sb.gst,
+    { launch_pdl(k_group_build, gb, 256, 0, s, d_k, sb.ids, sb.szone, sb.zs, sb.cflag, sb.d_nz,
+                 sb.gst,
                                      sb.zg); note_launch(); }
-    { k_group_inverse<<<gb, 128, 0, s>>>(sb.d_ng, sb.gst, sb.vidx, sb.n64, sb.winv, sb.pinv); note_launch(); }
+    { launch_pdl(k_group_inverse, gb, 128, 0, s, sb.d_ng, sb.gst, sb.vidx, sb.n64, sb.winv,
+                 sb.pinv); note_launch(); }
 }
 
 void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint32_t *d_status,
@@ -1248,14 +1284,17 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
     cudaMemsetAsync(sb.iwork, 0, sizeof(int) * 16, s);
     if (p.solver == HFCR_SOLVER_FP64) {
         // one float64 run with the whole iteration budget of the mixed solver
-        { k_init_lam<<<rb, 256, 0, s>>>(d_k, sb.b, sb.lam, sb.r64); note_launch(); }
-        { k_cg<double><<<1, CG_THREADS, 0, s>>>(1, d_k, sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64,
+        { launch_pdl(k_init_lam, rb, 256, 0, s, d_k, sb.b, sb.lam, sb.r64); note_launch(); }
+        { launch_pdl(k_cg<double>, 1, CG_THREADS, 0, s, 1, d_k, sb.d_U, sb.seg, sb.cval_s,
+                     sb.winv, sb.n64,
                                               sb.vidx, sb.b, sb.lam, sb.p64 + 0, sb.r64, sb.p64 + cap,
                                               sb.q64, sb.u64, p.max_cg_iters * p.max_refine,
                                               p.rel_tol, sb.iwork); note_launch(); }
-        { k_res_vertex<<<rb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64, sb.lam, sb.u64,
+        { launch_pdl(k_res_vertex, rb, 256, 0, s, sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64,
+                     sb.lam, sb.u64,
                                          sb.iwork); note_launch(); }
-        { k_res_stencil<<<rb, 256, 0, s>>>(d_k, sb.vidx, sb.n64, sb.b, sb.u64, sb.r64, sb.red,
+        { launch_pdl(k_res_stencil, rb, 256, 0, s, d_k, sb.vidx, sb.n64, sb.b, sb.u64, sb.r64,
+                     sb.red,
                                           sb.iwork, (unsigned *)(sb.iwork + 12), p.rel_tol,
                                           sb.dwork, 0); note_launch(); }
         return;
@@ -1274,19 +1313,21 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
     if (warp_max) {
         int zw = (cap + WARP_ZONE_WARPS - 1) / WARP_ZONE_WARPS;  // CTAs of the warp launch
         if (zw > 4 * 152) zw = 4 * 152;
-        { k_cg_zone_warp<<<zw, 32 * WARP_ZONE_WARPS, g_warp_zone_smem, s>>>(sb.d_nz, za); note_launch(); }
+        { launch_pdl(k_cg_zone_warp, zw, 32 * WARP_ZONE_WARPS, g_warp_zone_smem, s, sb.d_nz,
+                     za); note_launch(); }
     }
     int zsmall = (cap + 1023) / 1024 * 4;  // blocks of the small-zone launch (grid-stride over zones)
     if (zsmall > 2048) zsmall = 2048;
     int zbig = (cap + ZONE_BIG - 1) / ZONE_BIG;
     if (zbig > 152) zbig = 152;
-    { k_cg_zone<256><<<zsmall, 256, zone_small_smem, s>>>(
-          sb.d_nz, za, warp_max, ZONE_BIG, 0, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.z32, sb.u32,
+    { launch_pdl(k_cg_zone<256>, zsmall, 256, zone_small_smem, s, sb.d_nz, za, warp_max, ZONE_BIG,
+                 0, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.z32, sb.u32,
           zone_small_smem); note_launch(); }
-    { k_cg_zone<CG_THREADS><<<zbig, CG_THREADS, fast_smem, s>>>(
-          sb.d_nz, za, warp_max, ZONE_BIG, 1, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.z32, sb.u32,
+    { launch_pdl(k_cg_zone<CG_THREADS>, zbig, CG_THREADS, fast_smem, s, sb.d_nz, za, warp_max,
+                 ZONE_BIG, 1, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.z32, sb.u32,
           fast_smem); note_launch(); }
-    { k_zone_final<<<1, 256, 0, s>>>(sb.d_nz, sb.r64, sb.q64, p.rel_tol, sb.dwork, sb.iwork); note_launch(); }
+    { launch_pdl(k_zone_final, 1, 256, 0, s, sb.d_nz, sb.r64, sb.q64, p.rel_tol, sb.dwork,
+                 sb.iwork); note_launch(); }
 }
 
 void displacement(const MeshPair &mp, int cap, SolveBuffers &sb, int apply, void *const *dxA,
@@ -1296,7 +1337,8 @@ void displacement(const MeshPair &mp, int cap, SolveBuffers &sb, int apply, void
     if (nb > 1024) nb = 1024;
     void *a0 = dxA ? dxA[0] : nullptr, *a1 = dxA ? dxA[1] : nullptr, *a2 = dxA ? dxA[2] : nullptr;
     void *b0 = dxB ? dxB[0] : nullptr, *b1 = dxB ? dxB[1] : nullptr, *b2 = dxB ? dxB[2] : nullptr;
-    { k_displace<<<nb, 256, 0, s>>>(sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64, sb.lam, sb.gvert, mp.A,
+    { launch_pdl(k_displace, nb, 256, 0, s, sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64, sb.lam,
+                 sb.gvert, mp.A,
                                   mp.B, apply, a0, a1, a2, b0, b1, b2); note_launch(); }
 }
 

@@ -71,6 +71,7 @@ __device__ __forceinline__ int live_tiles(int n, const int *d_n) {
 template <typename K>
 __global__ void __launch_bounds__(TPB) k_hist(const K *keys, int n, const int *d_n, int shift,
                                               unsigned *hist) {
+    HFCR_PDL_WAIT();
     const int nba = live_tiles(n, d_n);
     if ((int)blockIdx.x >= nba) return;
     if (d_n) n = min(n, *d_n);
@@ -134,6 +135,7 @@ __device__ __forceinline__ unsigned block_scan_excl(unsigned *a, int m, unsigned
 
 // exclusive scan of a[0..m) (m clamped to *d_m) by one CTA; total to *d_total
 __global__ void __launch_bounds__(1024) k_scan1(unsigned *a, int m, const int *d_m, int *d_total) {
+    HFCR_PDL_WAIT();
     if (d_m) m = min(m, *d_m);
     unsigned total = block_scan_excl<1024>(a, m);
     if (threadIdx.x == 0 && d_total) *d_total = (int)total;
@@ -143,6 +145,7 @@ __global__ void __launch_bounds__(1024) k_scan1(unsigned *a, int m, const int *d
 // in place and writes the digit's total to tot[d]
 __global__ void __launch_bounds__(TPB) k_scan_rows(unsigned *hist, int n, const int *d_n,
                                                    unsigned *tot) {
+    HFCR_PDL_WAIT();
     const int nba = live_tiles(n, d_n);
     if (!nba) return;
     unsigned total = block_scan_excl<TPB>(hist + blockIdx.x * nba, nba);
@@ -157,6 +160,7 @@ constexpr int SCAN_CHUNK = 4096;
 
 __global__ void __launch_bounds__(TPB) k_scan_reduce(const unsigned *a, int m, const int *d_m,
                                                      unsigned *part) {
+    HFCR_PDL_WAIT();
     __shared__ unsigned ws[TPB / 32];
     if (d_m) m = min(m, *d_m);
     const int base = blockIdx.x * SCAN_CHUNK;
@@ -177,6 +181,7 @@ __global__ void __launch_bounds__(TPB) k_scan_reduce(const unsigned *a, int m, c
 
 __global__ void __launch_bounds__(TPB) k_scan_down(unsigned *a, int m, const int *d_m,
                                                    const unsigned *part, int *d_total) {
+    HFCR_PDL_WAIT();
     __shared__ unsigned ws[TPB / 32];
     if (d_m) m = min(m, *d_m);
     const int base = blockIdx.x * SCAN_CHUNK;
@@ -201,6 +206,7 @@ template <typename K, bool HV>
 __global__ void __launch_bounds__(TPB) k_scatter(const K *kin, const int *vin, K *kout, int *vout,
                                                  int n, const int *d_n, int shift,
                                                  const unsigned *hist, const unsigned *tot) {
+    HFCR_PDL_WAIT();
     const int nba = live_tiles(n, d_n);
     if ((int)blockIdx.x >= nba) return;
     if (d_n) n = min(n, *d_n);
@@ -257,6 +263,7 @@ __device__ __forceinline__ void sort_small_body(K *k0, int *v0, K *k1, int *v1, 
 template <typename K, bool HV>
 __global__ void __launch_bounds__(TPB) k_sort_small(K *k0, int *v0, K *k1, int *v1, int n,
                                                     const int *d_n, int bits) {
+    HFCR_PDL_WAIT();
     if (d_n) n = min(n, *d_n);
     if (n > SMALL_N) return;  // the multi-CTA kernels sort it
     sort_small_body<K, HV>(k0, v0, k1, v1, n, bits);
@@ -272,6 +279,7 @@ template <typename K, bool HV>
 __global__ void __launch_bounds__(TPB) k_sort_segments(K *k0, int *v0, K *k1, int *v1, int n_total,
                                                        const int *segs, int col, int nseg, int bits,
                                                        int *d_rest) {
+    HFCR_PDL_WAIT();
     const int i = blockIdx.x;
     if (i >= nseg) return;
     const int a = min(max(segs[4 * i + col], 0), n_total);
@@ -406,6 +414,7 @@ template <typename K, bool HV>
 __global__ void __launch_bounds__(TPB) k_sort_coop(K *k0, int *v0, K *k1, int *v1, int n,
                                                    const int *d_n, int bits, unsigned *hist,
                                                    unsigned *tot, unsigned *bar, uint32_t *status) {
+    HFCR_PDL_WAIT();
     if (d_n) n = min(n, *d_n);
     if (n <= SMALL_N) return;
     unsigned epoch = 0;
@@ -514,7 +523,8 @@ bool radix_sort_impl(K *k0, int *v0, K *k1, int *v1, int n, const int *d_n, int 
     if (n <= SMALL_N || d_n) {
         // with a device count the single CTA sorts whenever *d_n <= SMALL_N
         // and the multi-CTA kernels below return at once; otherwise the reverse
-        { k_sort_small<K, HV><<<1, TPB, 0, s>>>(k0, v0, k1, v1, n, d_n, passes * 8); note_launch(); }
+        { launch_pdl(k_sort_small<K, HV>, 1, TPB, 0, s, k0, v0, k1, v1, n, d_n,
+                     passes * 8); note_launch(); }
         if (n <= SMALL_N) return passes & 1;
     }
     int nb = (n + TILE - 1) / TILE;
@@ -541,9 +551,10 @@ bool radix_sort_impl(K *k0, int *v0, K *k1, int *v1, int n, const int *d_n, int 
     int *vin = v0, *vout = v1;
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
-        { k_hist<K><<<nb, TPB, 0, s>>>(kin, n, d_n, shift, t.hist); note_launch(); }
-        { k_scan_rows<<<256, TPB, 0, s>>>(t.hist, n, d_n, tot); note_launch(); }
-        { k_scatter<K, HV><<<nb, TPB, 0, s>>>(kin, vin, kout, vout, n, d_n, shift, t.hist, tot); note_launch(); }
+        { launch_pdl(k_hist<K>, nb, TPB, 0, s, kin, n, d_n, shift, t.hist); note_launch(); }
+        { launch_pdl(k_scan_rows, 256, TPB, 0, s, t.hist, n, d_n, tot); note_launch(); }
+        { launch_pdl(k_scatter<K, HV>, nb, TPB, 0, s, kin, vin, kout, vout, n, d_n, shift, t.hist,
+                     tot); note_launch(); }
         K *tk = kin; kin = kout; kout = tk;
         int *tv = vin; vin = vout; vout = tv;
     }
@@ -564,7 +575,8 @@ bool radix_sort_u64v_segments(unsigned long long *k0, int *v0, unsigned long lon
     int sp = (seg_bits + 7) / 8;
     if ((sp & 1) != (passes & 1)) ++sp;
     cudaMemsetAsync(d_rest, 0, sizeof(int), s);
-    { k_sort_segments<unsigned long long, true><<<nseg, TPB, 0, s>>>(k0, v0, k1, v1, n, segs, col, nseg,
+    { launch_pdl(k_sort_segments<unsigned long long, true>, nseg, TPB, 0, s, k0, v0, k1, v1, n,
+                 segs, col, nseg,
                                                                      sp * 8, d_rest); note_launch(); }
     // everything again, globally, only if a segment was too long for one CTA
     return radix_sort_impl<unsigned long long, true>(k0, v0, k1, v1, n, d_rest, bits, t, s);
@@ -598,12 +610,12 @@ bool radix_sort_u32_dev(unsigned *k0, int *v0, unsigned *k1, int *v1, const int 
 void scan_flags_dev(unsigned *flags, const int *d_n, int cap, int *d_total, SortTemp &t,
                     cudaStream_t s) {
     if (cap <= SCAN_CHUNK) {
-        { k_scan1<<<1, 1024, 0, s>>>(flags, cap, d_n, d_total); note_launch(); }
+        { launch_pdl(k_scan1, 1, 1024, 0, s, flags, cap, d_n, d_total); note_launch(); }
         return;
     }
     const int nc = (cap + SCAN_CHUNK - 1) / SCAN_CHUNK;
-    { k_scan_reduce<<<nc, TPB, 0, s>>>(flags, cap, d_n, t.hist); note_launch(); }
-    { k_scan_down<<<nc, TPB, 0, s>>>(flags, cap, d_n, t.hist, d_total); note_launch(); }
+    { launch_pdl(k_scan_reduce, nc, TPB, 0, s, flags, cap, d_n, t.hist); note_launch(); }
+    { launch_pdl(k_scan_down, nc, TPB, 0, s, flags, cap, d_n, t.hist, d_total); note_launch(); }
 }
 
 int bits_for(long long n) {
