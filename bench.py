@@ -121,9 +121,15 @@ PROFILES = {"k_traverse": "k_traverse_cloth_torus.md", "k_cg_zone": "k_cg_zone_c
 
 
 def kernel_source_hash(kernel: str = "k_traverse") -> str:
+    """First 16 hex digits of the SHA-256 of the kernel's source files, code
+    lines only (lines that are blank or hold only a // comment are left out,
+    so a comment edit keeps a profile valid)."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[kernel]:
-        h.update(open(os.path.join(ROOT, "paper_1409_2081_gb300", "csrc", f), "rb").read())
+        for line in open(os.path.join(ROOT, "paper_1409_2081_gb300", "csrc", f), "rb"):
+            t = line.strip()
+            if t and not t.startswith(b"//"):
+                h.update(t + b"\n")
     return h.hexdigest()[:16]
 
 

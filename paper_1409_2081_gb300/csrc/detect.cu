@@ -4,6 +4,9 @@
 // One thread per edge of the edge mesh walks the BVH of the oriented mesh's
 // faces with the edge's box, testing both children of a node with one
 // 64-byte node load; at a leaf the exact segment-triangle test decides.
+// Threads take the edges in the Morton order of their midpoints (a cached
+// permutation), so that a warp walks one region of the tree; the packet
+// variants walk a warp's edges together.
 // Hits are appended (one atomic per hit) as 64-bit keys
 // (dir | edge | face), which a radix sort turns into the lexicographic
 // (dir, v0, v1, face) order because the edges are sorted by (v0, v1).

@@ -1,6 +1,6 @@
-// Internal declarations shared by the translation units of libhfcr.
-// Host-side launch wrappers only; every device function a kernel needs is
-// defined in the translation unit (or the .cuh header) that launches it.
+// Internal declarations shared by the translation units of libhfcr: the
+// host-side wrappers of each translation unit's kernels, the launch helper
+// and the few device helpers (segment lookup) more than one unit needs.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -11,10 +11,15 @@
 //   q = grad(D) u          (per stencil: gather of four vertices).
 // Displacement x' - x = -M^-1 grad(D)^T lambda (Eq. 5).
 //
-// MIXED: conjugate gradients in float32 on float32 normals solve for a
-// correction of lambda; the residual b - A lambda is recomputed in float64
-// with the float64 normals after every run (iterative refinement), until
-// |r| <= rel_tol |b|.  FP64: conjugate gradients in float64.
+// The matrix is block-diagonal by impact zone (stencils that share a vertex,
+// found by union-find); every zone is solved on its own.
+// MIXED: per zone (one warp for zones of at most 32 stencils, one CTA for
+// the others, staged in shared memory), conjugate gradients in float32 on
+// float32 normals, preconditioned by the inverses of the blocks of rows that
+// share x0, solve for a correction of lambda; the zone's residual
+// b - A lambda is recomputed in float64 with the float64 normals after every
+// run (iterative refinement), until |r_zone| <= rel_tol |b_zone|.
+// FP64: conjugate gradients in float64 on the whole system.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

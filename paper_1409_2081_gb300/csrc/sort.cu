@@ -8,7 +8,10 @@
 // warp counts are then prefix-summed across the 8 warps, and a tile's
 // global offset for a digit comes from the digit-major scan of all tiles'
 // histograms.  Inputs of up to SMALL_N keys are sorted by one CTA that
-// walks its tiles in order (one launch for all passes).
+// walks its tiles in order (one launch for all passes).  A sort whose count
+// only the device knows launches that CTA and one cooperative kernel that
+// runs every multi-CTA pass when the count is larger; the segments of a
+// batch can be sorted one CTA each.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
