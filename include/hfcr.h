@@ -116,6 +116,9 @@ typedef struct {
                                minimizer's displacement is applied as it is */
     int32_t traverse_variant; /* traversal kernel variant 0..4 used until hfcr_autotune picks one
                                  (default 0; every variant finds the same pairs) */
+    int32_t setup_path;     /* response setup (vertex CSR, impact zones, preconditioner groups):
+                               0 (default) one cooperative launch, 1 a sequence of about 25
+                               kernels; both build the same arrays, so the results are identical */
 } hfcr_options;
 
 typedef struct {

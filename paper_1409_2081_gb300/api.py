@@ -56,7 +56,7 @@ class hfcr_options(ctypes.Structure):
                 ("max_refine", ctypes.c_int32), ("rel_tol", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("graphs", ctypes.c_int32),
                 ("diffuse_rings", ctypes.c_int32), ("diffuse_sweeps", ctypes.c_int32),
-                ("traverse_variant", ctypes.c_int32)]
+                ("traverse_variant", ctypes.c_int32), ("setup_path", ctypes.c_int32)]
 
 
 class hfcr_solve_info(ctypes.Structure):
@@ -192,12 +192,13 @@ class Context:
     def __init__(self, solver: int = HFCR_SOLVER_MIXED, f32_filter: bool = True,
                  roles: int = HFCR_ROLES_ALTERNATE, max_cg_iters: int = 500, max_refine: int = 6,
                  rel_tol: float = 1e-12, inner_tol: float = 1e-4, graphs: bool = True,
-                 diffuse_rings: int = 0, diffuse_sweeps: int = 0, traverse_variant: int = 0):
+                 diffuse_rings: int = 0, diffuse_sweeps: int = 0, traverse_variant: int = 0,
+                 setup_path: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("hfcr needs a CUDA device")
         opt = hfcr_options(solver, int(f32_filter), roles, max_cg_iters, max_refine, rel_tol, inner_tol,
-                           int(graphs), diffuse_rings, diffuse_sweeps, traverse_variant)
+                           int(graphs), diffuse_rings, diffuse_sweeps, traverse_variant, setup_path)
         h = ctypes.c_void_p()
         self.handle = None
         # a refused create has no context: its message is the thread's

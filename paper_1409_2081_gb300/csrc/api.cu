@@ -480,7 +480,7 @@ hfcr_status run_response(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     prof_begin(ctx, HFCR_STAGE_ASSEMBLE, s);
     assemble(mp, st, ctx->d_cnt + C_STENCILS, k, d, ctx->sb, ctx->d_status, s);
     build_vertex_csr(mp, ctx->d_cnt + C_STENCILS, k, ctx->sb, ctx->sort, ctx->d_cnt + C_N4,
-                     ctx->d_status, s);
+                     ctx->d_status, ctx->opt.setup_path, s);
     prof_end(ctx, HFCR_STAGE_ASSEMBLE, s);
     prof_begin(ctx, HFCR_STAGE_SOLVE, s);
     solve(params_of(ctx->opt), ctx->d_cnt + C_STENCILS, k, ctx->sb, ctx->d_status, s);
@@ -704,6 +704,7 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
     c->opt.diffuse_rings = 0;
     c->opt.diffuse_sweeps = 0;
     c->opt.traverse_variant = 0;
+    c->opt.setup_path = 0;
     if (opt) {
         c->opt = *opt;
         if (c->opt.max_cg_iters <= 0) c->opt.max_cg_iters = 500;
@@ -715,6 +716,11 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
         if (c->opt.traverse_variant < 0 || c->opt.traverse_variant >= N_TRAVERSE_VARIANTS) {
             delete c;
             set_noctx_error("hfcr_create: traverse_variant out of range");
+            return HFCR_ERR_ARG;
+        }
+        if (c->opt.setup_path != 0 && c->opt.setup_path != 1) {
+            delete c;
+            set_noctx_error("hfcr_create: setup_path must be 0 or 1");
             return HFCR_ERR_ARG;
         }
         if (c->opt.diffuse_rings < 0 || c->opt.diffuse_sweeps < 0 || c->opt.diffuse_rings > 1024 ||

@@ -276,8 +276,10 @@ struct SolveParams {
 void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int cap, double d,
               SolveBuffers &sb, uint32_t *d_status, cudaStream_t s);
 // d_n4: device word receiving 4k (the CSR entry count)
+// path 0: one cooperative launch (the multi-kernel sequence where that
+// launch is refused); 1: the multi-kernel sequence
 void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers &sb, SortTemp &t,
-                      int *d_n4, uint32_t *d_status, cudaStream_t s);
+                      int *d_n4, uint32_t *d_status, int path, cudaStream_t s);
 // One-time kernel attributes (shared-memory opt-in); call outside stream capture.
 void solver_init();
 // Solves and leaves lambda in sb.lam; results (iters, residual) in sb.iwork / sb.dwork.

@@ -24,12 +24,35 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "sortdev.cuh"
 
 namespace hfcr {
 
 namespace {
 
 constexpr int CG_THREADS = 1024;
+
+// Loads of data written earlier in the same launch: plain where only the
+// loading CTA wrote it (PlainLd), through L2 where another CTA may have
+// (L2Ld), never through a possibly stale L1 line.
+struct PlainLd {
+    static constexpr bool L2 = false;
+    template <class T> __device__ static T ld(const T *p) { return *p; }
+};
+struct L2Ld {
+    static constexpr bool L2 = true;
+    template <class T> __device__ static T ld(const T *p) { return __ldcg(p); }
+};
+
+template <class G>
+__device__ __forceinline__ double4_32a ld_n64(const double4_32a *p) {
+    if (!G::L2) return *p;
+    const double2 lo = __ldcg((const double2 *)p), hi = __ldcg((const double2 *)p + 1);
+    double4_32a r;
+    r.x = lo.x; r.y = lo.y; r.z = hi.x; r.w = hi.y;
+    return r;
+}
+
 constexpr int RES_BLOCKS = 512;
 
 __device__ __forceinline__ int chk(int i, int n, uint32_t *st) {
@@ -713,26 +736,33 @@ __global__ void k_group_build(const int *d_k, const int4 *ids, const int *szone,
     }
 }
 
+// inverse mass of global vertex g (1 where the mesh gives none)
+__device__ __forceinline__ double inv_mass_of(int g, int nA, const float *wA, const float *wB) {
+    const float *w = g < nA ? wA : wB;
+    return w ? (double)w[g < nA ? g : g - nA] : 1.0;
+}
+
 // inverse of each group's block of A = J M^-1 J^T (float64, stored float32):
-// A_ab = (n_a . n_b) (w(x0) + 1/9 sum of w over the face vertices shared by a and b)
-__global__ void k_group_inverse(const int *d_ng, const int *gst, const int4 *vidx,
-                                const double4_32a *n64, const float *winv, float4 *pinv) {
-    HFCR_PDL_WAIT();
-    const int ng = *d_ng;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
-        const int a0 = gst[g], m = gst[g + 1] - a0;
+// A_ab = (n_a . n_b) (w(x0) + 1/9 sum of w over the face vertices shared by
+// a and b); ids are the global vertex ids (x0, face) of the zone-ordered rows
+template <class G>
+__device__ __forceinline__ void group_inverse_one(int g, const int *gst, const int4 *ids,
+                                                  const double4_32a *n64, int nA, const float *wA,
+                                                  const float *wB, float4 *pinv) {
+    {
+        const int a0 = G::ld(gst + g), m = G::ld(gst + g + 1) - a0;
         double A[GMAX][2 * GMAX];
         for (int a = 0; a < m; ++a) {
-            const int4 va = vidx[a0 + a];
-            const double4_32a na = n64[a0 + a];
+            const int4 va = G::ld(ids + a0 + a);
+            const double4_32a na = ld_n64<G>(n64 + a0 + a);
             for (int b = 0; b < m; ++b) {
-                const int4 vb = vidx[a0 + b];
-                const double4_32a nb = n64[a0 + b];
-                double w = winv[va.x];
+                const int4 vb = G::ld(ids + a0 + b);
+                const double4_32a nb = ld_n64<G>(n64 + a0 + b);
+                double w = inv_mass_of(va.x, nA, wA, wB);
                 const int fa[3] = {va.y, va.z, va.w}, fb[3] = {vb.y, vb.z, vb.w};
                 for (int p = 0; p < 3; ++p)
                     for (int q = 0; q < 3; ++q)
-                        if (fa[p] == fb[q]) w += winv[fa[p]] / 9.0;
+                        if (fa[p] == fb[q]) w += inv_mass_of(fa[p], nA, wA, wB) / 9.0;
                 A[a][b] = (na.x * nb.x + na.y * nb.y + na.z * nb.z) * w;
                 A[a][GMAX + b] = a == b ? 1.0 : 0.0;
             }
@@ -767,13 +797,24 @@ __global__ void k_group_inverse(const int *d_ng, const int *gst, const int4 *vid
                 for (int b = 0; b < m; ++b) row[b] = (float)A[a][GMAX + b];
             } else {
                 // diagonal fallback computed from the untouched inputs
-                const int4 va = vidx[a0 + a];
-                double w = winv[va.x] + (winv[va.y] + winv[va.z] + winv[va.w]) / 9.0;
+                const int4 va = G::ld(ids + a0 + a);
+                double w = inv_mass_of(va.x, nA, wA, wB) +
+                           (inv_mass_of(va.y, nA, wA, wB) + inv_mass_of(va.z, nA, wA, wB) +
+                            inv_mass_of(va.w, nA, wA, wB)) / 9.0;
                 row[a] = w > 0.0 ? (float)(1.0 / w) : 0.f;
             }
             pinv[a0 + a] = make_float4(row[0], row[1], row[2], row[3]);
         }
     }
+}
+
+__global__ void k_group_inverse(const int *d_ng, const int *gst, const int4 *ids,
+                                const double4_32a *n64, int nA, const float *wA, const float *wB,
+                                float4 *pinv) {
+    HFCR_PDL_WAIT();
+    const int ng = *d_ng;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        group_inverse_one<PlainLd>(g, gst, ids, n64, nA, wA, wB, pinv);
 }
 
 // float64 residual r = b - J M^-1 J^T lam of one zone (the float64 normals;
@@ -1180,6 +1221,438 @@ __global__ void k_displace(const int *d_U, const int *seg, const int *cval, cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// The response setup in one cooperative launch: vertex CSR of the stencil
+// entries, impact zones, zone-ordered rows, zone-ordered CSR, the groups of
+// rows sharing x0 and the inverses of their blocks.  It computes exactly
+// what the multi-kernel sequence of build_vertex_csr computes (the same
+// stable sorts, the same union-find roots, hence the same arrays), in one
+// launch instead of about twenty-five.  The elementwise phases run on every
+// CTA taking part, separated by bounded grid-wide barriers, and data
+// written by another CTA is read through L2.  Up to SETUP_SMALL_K stencils
+// few CTAs take part (one per 1,024 entries) and the first CTA alone runs
+// the sorts, the union-find (in shared memory) and the scans between two
+// barriers; above, every CTA takes part in those too (the multi-CTA sort,
+// union-find in global memory, the two-level scan).
+// ---------------------------------------------------------------------------
+constexpr int SETUP_SMALL_K = 8192;  // 4k <= SMALL_N sort keys, 32 KB of parents
+constexpr int SETUP_SCAN_CHUNK = 4096;
+constexpr int SETUP_ENTRIES_PER_CTA = 1024;
+
+struct SetupArgs {
+    const int *d_k;
+    int cap, vbits, nA;
+    const float *wA, *wB;
+    const int4 *ids_raw;
+    const double4_32a *n64_raw;
+    const float4 *n32_raw;
+    const double *b_raw;
+    unsigned *ckey, *ckey_alt, *cflag;
+    int *cval, *cval_alt;
+    unsigned *zlab, *zlab_alt;
+    int *zsrc, *zsrc_alt;
+    unsigned *k2, *k2_alt;
+    int *v2, *v2_alt;
+    int *parent;  // union-find forest above SETUP_SMALL_K, then the position of each stencil
+    int4 *ids;
+    double4_32a *n64;
+    float4 *n32;
+    double *b;
+    int *szone, *zs, *zv, *gst, *zg, *seg, *gvert;
+    int4 *vidx;
+    float *winv;
+    float4 *pinv;
+    int *d_n4, *d_U, *d_nz, *d_ng;
+    unsigned *hist, *tot, *bar;
+    uint32_t *status;
+};
+
+// the CTAs taking part (blockIdx.x < parts) and their barrier
+struct SetupSync {
+    unsigned *bar;
+    unsigned epoch;
+    uint32_t *status;
+    unsigned parts;
+    __device__ bool sync() {
+        if (parts == 1) {
+            __syncthreads();
+            return true;
+        }
+        return grid_barrier(bar, ++epoch, status, parts);
+    }
+};
+
+__device__ __forceinline__ unsigned cta_sum_u(unsigned v) {
+    __shared__ unsigned ws[TPB / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();  // ws is free of its previous use
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    unsigned t = 0;
+#pragma unroll
+    for (int q = 0; q < TPB / 32; ++q) t += ws[q];
+    return t;
+}
+
+// exclusive scan of a[0..m) in place, the sum to *d_total; on return the
+// scanned values and the sum are visible to every CTA taking part.  Small:
+// the first CTA scans alone.  Otherwise chunks of SETUP_SCAN_CHUNK: chunk
+// sums, a barrier, each chunk scanned from the sum of the chunks before it.
+__device__ __forceinline__ bool setup_scan(SetupSync &g, bool small, unsigned *a, int m,
+                                           unsigned *part, int *d_total, unsigned &total) {
+    if (small) {
+        if (blockIdx.x == 0) {
+            const unsigned t = block_scan_excl<TPB, true>(a, m);
+            if (threadIdx.x == 0) *d_total = (int)t;
+        }
+        if (!g.sync()) return false;
+        total = (unsigned)__ldcg(d_total);
+        return true;
+    }
+    const int nc = (m + SETUP_SCAN_CHUNK - 1) / SETUP_SCAN_CHUNK;
+    for (int c = blockIdx.x; c < nc; c += g.parts) {
+        const int base = c * SETUP_SCAN_CHUNK, end = min(m, base + SETUP_SCAN_CHUNK);
+        unsigned x = 0;
+        for (int i = base + threadIdx.x; i < end; i += TPB) x += __ldcg(a + i);
+        x = cta_sum_u(x);
+        if (threadIdx.x == 0) part[c] = x;
+    }
+    if (!g.sync()) return false;
+    for (int c = blockIdx.x; c < nc; c += g.parts) {
+        unsigned x = 0;
+        for (int i = threadIdx.x; i < c; i += TPB) x += __ldcg(part + i);
+        const unsigned off = cta_sum_u(x);
+        const int base = c * SETUP_SCAN_CHUNK;
+        block_scan_excl<TPB, true>(a + base, min(m - base, SETUP_SCAN_CHUNK), off);
+    }
+    unsigned x = 0;
+    for (int i = threadIdx.x; i < nc; i += TPB) x += __ldcg(part + i);
+    total = cta_sum_u(x);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_total = (int)total;
+    return g.sync();
+}
+
+// stable sort of (key, val) pairs over `bits` bits (a multiple of 8); the
+// result is in (k1, v1) after an odd number of passes.  Small: the first
+// CTA alone, then a barrier.
+__device__ __forceinline__ bool setup_sort(SetupSync &g, bool small, unsigned *k0, int *v0,
+                                           unsigned *k1, int *v1, int n, int bits,
+                                           const SetupArgs &a, SortSmem &sm) {
+    if (small) {
+        if (blockIdx.x == 0) sort_small_body<unsigned, true, true>(k0, v0, k1, v1, n, bits, sm);
+        return g.sync();
+    }
+    return sort_grid_body<unsigned, true>(k0, v0, k1, v1, n, bits, a.hist, a.tot, g.bar, g.epoch,
+                                          g.status, sm, g.parts);
+}
+
+__device__ __forceinline__ int setup_bits(int n) {  // 8 x the passes for keys < n (n >= 1)
+    int b = 1;
+    while ((1 << b) < n) ++b;
+    return 8 * ((b + 7) / 8);
+}
+
+__device__ __forceinline__ bool group_start_l2(const int4 *ids, const int *szone, const int *zs,
+                                               int t) {
+    const int zs0 = __ldcg(zs + __ldcg(szone + t)), x0 = __ldcg(&ids[t].x);
+    int rs = t;
+    while (rs > zs0 && __ldcg(&ids[rs - 1].x) == x0) --rs;
+    return ((t - rs) % GMAX) == 0;
+}
+
+// unites the zones of stencils s0 and s1 (the smaller root becomes the
+// root); SH: parents in shared memory
+template <bool SH>
+__device__ __forceinline__ void setup_unite(int *par, int s0, int s1, uint32_t *status) {
+    int a = s0, b = s1, guard = 0;
+    while (true) {
+        if constexpr (SH) {
+            a = uf_find_s(par, a);
+            b = uf_find_s(par, b);
+        } else {
+            a = uf_find(par, a);
+            b = uf_find(par, b);
+        }
+        if (a == b) break;
+        if (a < b) { int t = a; a = b; b = t; }
+        const int old = atomicCAS(par + a, a, b);
+        if (old == a) break;
+        a = old;
+        if (++guard > (1 << 24)) { atomicOr(status, ST_TIMEOUT); break; }
+    }
+}
+
+// Impact zones of up to SETUP_SMALL_K stencils by one CTA, in shared
+// memory: connected components of the stencils, two stencils being
+// adjacent when consecutive entries of the vertex-sorted list (ck1, cv1)
+// share a vertex.  Min-label hooking with shortcutting (the FastSV scheme of
+// Zhang, Azad and Hu, 2020): every sweep hooks the parent of each end of an
+// edge, and each end itself, under the smaller of their grandparents
+// (atomicMin), then every stencil jumps to its grandparent; labels only
+// fall and stay inside their component, so at the first sweep that changes
+// nothing every stencil points straight at the smallest stencil of its
+// zone (the root the lock-free union-find gives too).  After SV_SWEEPS
+// sweeps without convergence the forest (every parent smaller than its
+// child, inside the same zone) is finished by the union-find.
+constexpr int SV_SWEEPS = 64;
+
+__device__ void zones_min_label(int *f, int k, const unsigned *ck1, const int *cv1, int n4,
+                                uint32_t *status) {
+    __shared__ int changed;
+    for (int s = threadIdx.x; s < k; s += TPB) f[s] = s;
+    if (threadIdx.x == 0) changed = 0;
+    __syncthreads();
+    int again = 1;
+    for (int sweep = 0; sweep < SV_SWEEPS; ++sweep) {
+        bool ch = false;
+        for (int i = threadIdx.x + 1; i < n4; i += TPB) {
+            if (ck1[i] != ck1[i - 1]) continue;
+            const int u = cv1[i] >> 2, v = cv1[i - 1] >> 2;
+            const int fu = f[u], fv = f[v];
+            const int m = min(f[fu], f[fv]);
+            ch |= atomicMin(f + fu, m) > m;
+            ch |= atomicMin(f + fv, m) > m;
+            ch |= atomicMin(f + u, m) > m;
+            ch |= atomicMin(f + v, m) > m;
+        }
+        __syncthreads();
+        for (int s = threadIdx.x; s < k; s += TPB) {
+            const int gp = f[f[s]];
+            ch |= atomicMin(f + s, gp) > gp;
+        }
+        if (ch) changed = 1;
+        __syncthreads();
+        again = changed;
+        __syncthreads();
+        if (!again) break;
+        if (threadIdx.x == 0) changed = 0;  // written again only after the next sweep's barrier
+    }
+    if (again) {
+        for (int i = threadIdx.x + 1; i < n4; i += TPB)
+            if (ck1[i] == ck1[i - 1]) setup_unite<true>(f, cv1[i] >> 2, cv1[i - 1] >> 2, status);
+        __syncthreads();
+    }
+}
+
+// word of the barrier row raised when the groups are built (zeroed with
+// the barrier counter before the launch)
+constexpr int SETUP_READY = 1;
+
+// the inverse blocks of CTAs first .. first + n - 1 (consecutive groups on
+// different CTAs)
+__device__ __forceinline__ void setup_inverses(const SetupArgs &a, int first, int n) {
+    const int ng = __ldcg(a.d_ng);
+    for (int gi = threadIdx.x * n + (blockIdx.x - first); gi < ng; gi += n * TPB)
+        group_inverse_one<L2Ld>(gi, a.gst, a.ids, a.n64, a.nA, a.wA, a.wB, a.pinv);
+}
+
+// a CTA not taking part in the phases (first = the first such CTA): waits
+// (bounded, like the barrier) for the groups, then computes its share of
+// the inverse blocks
+__device__ void setup_helper(const SetupArgs &a, int first) {
+    __shared__ int go;
+    if (threadIdx.x == 0) {
+        go = 0;
+        long long spins = 0;
+        while (true) {
+            unsigned seen;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen)
+                         : "l"(a.bar + SETUP_READY) : "memory");
+            if (seen) { go = 1; break; }
+            if (*(volatile uint32_t *)a.status & ST_TIMEOUT) break;
+            if (++spins > BARRIER_SPIN_LIMIT) {
+                atomicOr(a.status, ST_TIMEOUT);
+                break;
+            }
+            __nanosleep(100);
+        }
+    }
+    __syncthreads();
+    if (go) setup_inverses(a, first, (int)gridDim.x - first);
+}
+
+__device__ bool setup_phases(SetupSync &g, const SetupArgs &a, int k, SortSmem &sm, int *par_s) {
+    const bool small = k <= SETUP_SMALL_K;
+    const int tid = blockIdx.x * TPB + threadIdx.x, nt = (int)g.parts * TPB, n4 = 4 * k;
+    if (tid == 0) *a.d_n4 = n4;
+    if (k == 0) {
+        if (tid == 0) { *a.d_U = 0; *a.d_nz = 0; *a.d_ng = 0; }
+        return true;
+    }
+    // vertex CSR: entries (vertex, 4 s + role) sorted by vertex
+    for (int i = tid; i < n4; i += nt) {
+        a.ckey[i] = (unsigned)((const int *)a.ids_raw)[i];
+        a.cval[i] = i;
+    }
+    if (!g.sync()) return false;
+    const bool f1 = (a.vbits / 8) & 1;
+    const unsigned *ck1 = f1 ? a.ckey_alt : a.ckey;
+    const int *cv1 = f1 ? a.cval_alt : a.cval;
+    // impact zones: stencils of consecutive entries on the same vertex are
+    // united; every zone's root is its smallest stencil.  Then the rows
+    // regrouped zone by zone (zones in the order of their root).
+    const int zbits = setup_bits(k);
+    const bool f2 = (zbits / 8) & 1;
+    const unsigned *zl = f2 ? a.zlab_alt : a.zlab;
+    const int *zr = f2 ? a.zsrc_alt : a.zsrc;
+    if (small) {
+        if (blockIdx.x == 0) {  // sort, union-find, labels and their sort in this CTA
+            sort_small_body<unsigned, true, true>(a.ckey, a.cval, a.ckey_alt, a.cval_alt, n4,
+                                                  a.vbits, sm);
+            int *par = par_s;  // overlays the sort's shared memory (the sort is done)
+            zones_min_label(par, k, ck1, cv1, n4, a.status);
+            for (int s = threadIdx.x; s < k; s += TPB) {
+                a.zlab[s] = (unsigned)uf_find_s(par, s);
+                a.zsrc[s] = s;
+            }
+            __syncthreads();
+            sort_small_body<unsigned, true>(a.zlab, a.zsrc, a.zlab_alt, a.zsrc_alt, k, zbits, sm);
+            for (int t = threadIdx.x; t < k; t += TPB)
+                a.cflag[t] = (t == 0 || zl[t] != zl[t - 1]) ? 1u : 0u;
+            __syncthreads();
+        }
+    } else {
+        if (!setup_sort(g, false, a.ckey, a.cval, a.ckey_alt, a.cval_alt, n4, a.vbits, a, sm))
+            return false;
+        int *par = a.parent;
+        for (int s = tid; s < k; s += nt) par[s] = s;
+        if (!g.sync()) return false;
+        for (int i = tid + 1; i < n4; i += nt)
+            if (__ldcg(ck1 + i) == __ldcg(ck1 + i - 1))
+                setup_unite<false>(par, __ldcg(cv1 + i) >> 2, __ldcg(cv1 + i - 1) >> 2, a.status);
+        if (!g.sync()) return false;
+        for (int s = tid; s < k; s += nt) {
+            a.zlab[s] = (unsigned)uf_find(par, s);
+            a.zsrc[s] = s;
+        }
+        if (!g.sync()) return false;
+        if (!setup_sort(g, false, a.zlab, a.zsrc, a.zlab_alt, a.zsrc_alt, k, zbits, a, sm))
+            return false;
+        for (int t = tid; t < k; t += nt)
+            a.cflag[t] = (t == 0 || __ldcg(zl + t) != __ldcg(zl + t - 1)) ? 1u : 0u;
+        if (!g.sync()) return false;
+    }
+    unsigned nz;
+    if (!setup_scan(g, small, a.cflag, k, a.hist, a.d_nz, nz)) return false;
+    int *pos_of = a.parent;
+    for (int t = tid; t < k; t += nt) {
+        const int src = __ldcg(zr + t);
+        const unsigned f = (t == 0 || __ldcg(zl + t) != __ldcg(zl + t - 1)) ? 1u : 0u;
+        const int z = (int)(__ldcg(a.cflag + t) + f) - 1;
+        a.szone[t] = z;
+        pos_of[src] = t;
+        if (f) a.zs[z] = t;
+        if (t == k - 1) a.zs[z + 1] = k;
+        a.ids[t] = a.ids_raw[src];
+        a.n64[t] = a.n64_raw[src];
+        a.n32[t] = a.n32_raw[src];
+        a.b[t] = a.b_raw[src];
+    }
+    if (!g.sync()) return false;
+    // groups of rows sharing x0 (at most GMAX rows each)
+    for (int t = tid; t < k; t += nt)
+        a.cflag[t] = group_start_l2(a.ids, a.szone, a.zs, t) ? 1u : 0u;
+    if (!g.sync()) return false;
+    unsigned ng;
+    if (!setup_scan(g, small, a.cflag, k, a.hist, a.d_ng, ng)) return false;
+    for (int t = tid; t < k; t += nt) {
+        const bool st = group_start_l2(a.ids, a.szone, a.zs, t);
+        const int gi = (int)__ldcg(a.cflag + t);
+        if (st) {
+            a.gst[gi] = t;
+            const int z = __ldcg(a.szone + t);
+            if (__ldcg(a.zs + z) == t) a.zg[z] = gi;
+        }
+        if (t == k - 1) {
+            a.gst[ng] = k;
+            a.zg[nz] = (int)ng;
+        }
+    }
+    // the inverse blocks (float64) need only the groups, the zone-ordered
+    // rows and the masses: the CTAs not taking part compute them while the
+    // others build the zone-ordered CSR (they wait for this flag,
+    // SETUP_READY); without such CTAs the others compute them at the end
+    const bool helpers = g.parts < gridDim.x;
+    if (helpers) {
+        __threadfence();  // the groups are written before the flag below
+        if (!g.sync()) return false;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.bar + SETUP_READY, 1u);
+    }
+    // zone-ordered CSR: the vertex-ordered entries re-sorted stably by zone
+    for (int i = tid; i < n4; i += nt) {
+        const int e = __ldcg(cv1 + i);
+        const int t = __ldcg(pos_of + (e >> 2));
+        a.k2[i] = (unsigned)__ldcg(a.szone + t);
+        a.v2[i] = 4 * t + (e & 3);
+    }
+    if (!g.sync()) return false;
+    const int qbits = setup_bits((int)nz);
+    if (!setup_sort(g, small, a.k2, a.v2, a.k2_alt, a.v2_alt, n4, qbits, a, sm)) return false;
+    const unsigned *zk = a.k2;
+    if ((qbits / 8) & 1) {  // the entries end in v2 whatever the pass count
+        zk = a.k2_alt;
+        for (int i = tid; i < n4; i += nt) a.v2[i] = __ldcg(a.v2_alt + i);
+        if (!g.sync()) return false;
+    }
+    const int *val = a.v2;
+    const int *idsi = (const int *)a.ids;
+    for (int i = tid; i < n4; i += nt)
+        a.cflag[i] = (i == 0 || __ldcg(idsi + __ldcg(val + i)) != __ldcg(idsi + __ldcg(val + i - 1)))
+                         ? 1u : 0u;
+    if (!g.sync()) return false;
+    unsigned U;
+    if (!setup_scan(g, small, a.cflag, n4, a.hist, a.d_U, U)) return false;
+    for (int i = tid; i < n4; i += nt) {
+        const int vi = __ldcg(val + i);
+        const int gv = __ldcg(idsi + vi);
+        const unsigned f = (i == 0 || gv != __ldcg(idsi + __ldcg(val + i - 1))) ? 1u : 0u;
+        const int j = (int)(__ldcg(a.cflag + i) + f) - 1;
+        ((int *)a.vidx)[vi] = j;
+        if (f) {
+            a.seg[j] = i;
+            a.gvert[j] = gv;
+            const float *w = gv < a.nA ? a.wA : a.wB;
+            const int lv = gv < a.nA ? gv : gv - a.nA;
+            a.winv[j] = w ? w[lv] : 1.0f;
+            const unsigned zi = __ldcg(zk + i);
+            if (i == 0 || zi != __ldcg(zk + i - 1)) a.zv[zi] = j;
+        }
+        if (i == n4 - 1) {
+            a.seg[j + 1] = n4;
+            a.zv[nz] = j + 1;
+        }
+    }
+    if (!g.sync()) return false;
+    if (!helpers) setup_inverses(a, 0, (int)g.parts);
+    return true;
+}
+
+union SetupSmem {
+    SortSmem sort;
+    int par[SETUP_SMALL_K];
+};
+
+__global__ void __launch_bounds__(TPB) k_setup(SetupArgs a) {
+    HFCR_PDL_WAIT();
+    const int k = max(0, min(*a.d_k, a.cap));
+    // CTAs taking part: every CTA on large inputs, one per 1,024 entries on
+    // small ones (the others leave at once; every CTA reads the same count)
+    unsigned parts = gridDim.x;
+    if (k <= SETUP_SMALL_K) {
+        const unsigned want = (unsigned)max(1, (4 * k + SETUP_ENTRIES_PER_CTA - 1) / SETUP_ENTRIES_PER_CTA);
+        if (want < parts) parts = want;
+    }
+    if (blockIdx.x >= parts) {
+        if (k > 0) setup_helper(a, (int)parts);
+        return;
+    }
+    __shared__ SetupSmem sh;
+    SetupSync g{a.bar, 0u, a.status, parts};
+    setup_phases(g, a, k, sh.sort, sh.par);
+}
+
 }  // namespace
 
 void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int cap, double d,
@@ -1207,9 +1680,98 @@ void solver_init() {
     if (!g_warp_zone_smem) cudaGetLastError();
 }
 
+// co-resident CTAs of k_setup on this device (0: cooperative launch unavailable)
+static int setup_grid_max() {
+    static int g[64] = {0};
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!done[dev]) {
+        int per_sm = 0, sms = 0, coop = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_setup, TPB, 0) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop)
+            // two CTAs per SM at most: the grid-wide phases are short and
+            // every barrier costs one arrival per CTA
+            g[dev] = (per_sm < 2 ? per_sm : 2) * sms;
+        else
+            cudaGetLastError();
+        done[dev] = true;
+    }
+    return g[dev];
+}
+
+// the whole setup as one cooperative launch; false when it cannot be launched
+static bool build_setup_fused(const MeshPair &mp, const int *d_k, int cap, SolveBuffers &sb,
+                              SortTemp &t, int *d_n4, uint32_t *d_status, cudaStream_t s) {
+    int grid = setup_grid_max();
+    if (grid <= 0 || !d_status || t.max_blocks < 3) return false;
+    const int tiles = (4 * cap + TILE - 1) / TILE;
+    if (grid > tiles) grid = tiles > 0 ? tiles : 1;
+    SetupArgs a;
+    const int vb = bits_for((long long)mp.A.n_verts + mp.B.n_verts);
+    a.d_k = d_k;
+    a.cap = cap;
+    a.vbits = 8 * ((vb + 7) / 8);
+    a.nA = mp.A.n_verts;
+    a.wA = mp.A.inv_mass;
+    a.wB = mp.B.inv_mass;
+    a.ids_raw = sb.ids_raw;
+    a.n64_raw = sb.n64_raw;
+    a.n32_raw = sb.n32_raw;
+    a.b_raw = sb.b_raw;
+    a.ckey = sb.ckey;
+    a.ckey_alt = sb.ckey_alt;
+    a.cflag = sb.cflag;
+    a.cval = sb.cval;
+    a.cval_alt = sb.cval_alt;
+    a.zlab = (unsigned *)sb.zkey;
+    a.zlab_alt = (unsigned *)sb.zkey_alt;
+    a.zsrc = (int *)sb.zkey + cap;
+    a.zsrc_alt = (int *)sb.zkey_alt + cap;
+    a.k2 = (unsigned *)sb.ck64;
+    a.k2_alt = (unsigned *)sb.ck64_alt;
+    a.v2 = (int *)sb.ck64 + 4 * (size_t)cap;
+    a.v2_alt = (int *)sb.ck64_alt + 4 * (size_t)cap;
+    a.parent = sb.parent;
+    a.ids = sb.ids;
+    a.n64 = sb.n64;
+    a.n32 = sb.n32;
+    a.b = sb.b;
+    a.szone = sb.szone;
+    a.zs = sb.zs;
+    a.zv = sb.zv;
+    a.gst = sb.gst;
+    a.zg = sb.zg;
+    a.seg = sb.seg;
+    a.gvert = sb.gvert;
+    a.vidx = sb.vidx;
+    a.winv = sb.winv;
+    a.pinv = sb.pinv;
+    a.d_n4 = d_n4;
+    a.d_U = sb.d_U;
+    a.d_nz = sb.d_nz;
+    a.d_ng = sb.d_ng;
+    a.hist = t.hist;
+    a.tot = t.hist + 256 * (size_t)(t.max_blocks - 1);
+    a.bar = t.hist + 256 * (size_t)(t.max_blocks - 2);
+    a.status = d_status;
+    cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), s);  // barrier counter, ready flag
+    void *args[] = {&a};
+    if (cudaLaunchCooperativeKernel((const void *)k_setup, grid, TPB, args, 0, s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    note_launch();
+    sb.cval_s = a.v2;
+    return true;
+}
+
 void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers &sb, SortTemp &t,
-                      int *d_n4, uint32_t *d_status, cudaStream_t s) {
+                      int *d_n4, uint32_t *d_status, int path, cudaStream_t s) {
     if (cap <= 0) return;
+    if (path == 0 && build_setup_fused(mp, d_k, cap, sb, t, d_n4, d_status, s)) return;
+    // the same setup as a sequence of kernels
     int n4 = 4 * cap;
     int nb = (n4 + 255) / 256;
     int gb = (cap + 255) / 256;
@@ -1274,8 +1836,8 @@ void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers 
     { launch_pdl(k_group_build, gb, 256, 0, s, d_k, sb.ids, sb.szone, sb.zs, sb.cflag, sb.d_nz,
                  sb.gst,
                                      sb.zg); note_launch(); }
-    { launch_pdl(k_group_inverse, gb, 128, 0, s, sb.d_ng, sb.gst, sb.vidx, sb.n64, sb.winv,
-                 sb.pinv); note_launch(); }
+    { launch_pdl(k_group_inverse, gb, 128, 0, s, sb.d_ng, sb.gst, sb.ids, sb.n64, mp.A.n_verts,
+                 mp.A.inv_mass, mp.B.inv_mass, sb.pinv); note_launch(); }
 }
 
 void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint32_t *d_status,
