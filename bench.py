@@ -628,8 +628,9 @@ def main():
     dominant = max(stage_ms, key=stage_ms.get)
     # rooflines of the two kernels that own a stage each: the traversal +
     # exact narrow phase, and the per-zone solver (the solve stage is
-    # k_cg_zone<256>, the 1024-thread launch, empty on this frame, and the
-    # one-CTA k_zone_final); algorithmic bytes = compulsory reads + writes
+    # k_cg_zone<256>, the one-warp-per-zone and 1024-thread launches, both
+    # nearly empty on this frame, and the one-CTA k_zone_final);
+    # algorithmic bytes = compulsory reads + writes
     trav_ms, trav_n = prof["traverse"]
     trav_avg_ms = trav_ms / max(1, trav_n)
     alg_trav = (sc.A.n_verts * 12 + ne * 8 + sc.B.n_verts * 12 + sc.B.n_tris * 12 + P * 8)

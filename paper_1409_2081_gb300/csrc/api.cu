@@ -400,8 +400,20 @@ void launch_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d
         prof_begin(ctx, HFCR_STAGE_TRAVERSE, s);
         detect_launch(a, s, ctx->d_status);
         prof_end(ctx, HFCR_STAGE_TRAVERSE, s);
-        pair_products(a.edges, a.n_edges, pl.segs, pl.nseg, a.ecol, a.fcol, F.n_tris, ctx->d_stats, s);
+        // a single pair's count is |edges| x |faces|, added on the host
+        // (single_pair_bf); a batch counts per pair on the device
+        if (pl.nseg > 1)
+            pair_products(a.edges, a.n_edges, pl.segs, pl.nseg, a.ecol, a.fcol, F.n_tris,
+                          ctx->d_stats, s);
     }
+}
+
+// brute-force-equivalent E-F tests of one detection of a single mesh pair
+// (a batch counts its pairs on the device)
+int64_t single_pair_bf(const DetectPlan &pl, bool d0, bool d1, const hfcr_mesh *A,
+                       const hfcr_mesh *B) {
+    if (pl.nseg > 1) return 0;
+    return (d0 ? (int64_t)pl.ne[0] * B->n_tris : 0) + (d1 ? (int64_t)pl.ne[1] * A->n_tris : 0);
 }
 
 hfcr_status read_back(hfcr_ctx *ctx, cudaStream_t s) {
@@ -517,28 +529,27 @@ hfcr_status prepare_diffusion(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh
 }
 
 // One repair iteration enqueued on device counts only: detection, clamped
-// pair count, pair sort and records, stencils, assembly, solve, applied
+// pair count, pair records, stencils, assembly, solve, applied
 // displacement.  Grids are sized by the reserved capacity; kernels read
-// the live counts.  Nothing is read back.
+// the live counts.  Nothing is read back.  The pairs stay in the order the
+// traversal appended them: the stencils are sorted and deduplicated on
+// their own keys, so their list does not depend on that order.
 void enqueue_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d0, bool d1,
                        const DetectPlan &pl, bool *built, double d, cudaStream_t s) {
     const int cap = (int)ctx->max_pairs;
     launch_detect(ctx, A, B, d0, d1, pl, built, s);
     prof_begin(ctx, HFCR_STAGE_STENCILS, s);
     clamp_count(ctx->d_cnt + C_PAIRS, cap, ctx->d_cnt + C_PEFF, ctx->d_status, s);
-    int bits = 1 + pl.edge_bits + pl.face_bits;
-    bool flip = radix_sort_u64_dev(ctx->pkeys, ctx->pkeys_alt, ctx->d_cnt + C_PEFF, cap, bits,
-                                   ctx->sort, s);
-    keys_to_pairs(flip ? ctx->pkeys_alt : ctx->pkeys, ctx->d_cnt + C_PEFF, cap, pl.edges[0],
-                  pl.edges[1], pl.edge_bits, pl.face_bits, ctx->pairs, s);
+    keys_to_pairs(ctx->pkeys, ctx->d_cnt + C_PEFF, cap, pl.edges[0], pl.edges[1], pl.edge_bits,
+                  pl.face_bits, ctx->pairs, s);
     MeshPair mp{*A, *B};
     int maxv = A->n_verts > B->n_verts ? A->n_verts : B->n_verts;
     int maxf = A->n_tris > B->n_tris ? A->n_tris : B->n_tris;
     int vb = bits_for(maxv > 1 ? maxv : 2), fb = bits_for(maxf > 1 ? maxf : 2);
     stencil_keys(mp, ctx->pairs, ctx->d_cnt + C_PEFF, cap, vb, fb, ctx->opt.f32_filter, ctx->skeys,
                  ctx->d_stats, ctx->d_status, s);
-    flip = radix_sort_u64_dev(ctx->skeys, ctx->skeys_alt, ctx->d_cnt + C_PEFF, cap, 1 + vb + fb,
-                              ctx->sort, s);
+    const bool flip = radix_sort_u64_dev(ctx->skeys, ctx->skeys_alt, ctx->d_cnt + C_PEFF, cap,
+                                         1 + vb + fb, ctx->sort, s);
     stencil_unique(flip ? ctx->skeys_alt : ctx->skeys, ctx->d_cnt + C_PEFF, cap, vb, fb, ctx->sflags,
                    ctx->stencils, ctx->d_cnt + C_STENCILS, ctx->sort, s);
     prof_end(ctx, HFCR_STAGE_STENCILS, s);
@@ -916,7 +927,10 @@ static hfcr_status detect_impl(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mes
     if ((st = read_back(ctx, s))) return st;
     int P = ctx->h_cnt[C_PAIRS];
     *n_out = P;
-    if (stats) add_stats(stats, *ctx->h_stats);
+    if (stats) {
+        add_stats(stats, *ctx->h_stats);
+        stats->brute_force_equiv += single_pair_bf(pl, dir0, dir1, A, B);
+    }
     if (P > ctx->max_pairs)
         return fail(ctx, HFCR_ERR_CAPACITY, "%d pairs exceed the reserved %lld", P,
                     (long long)ctx->max_pairs);
@@ -1077,6 +1091,7 @@ static hfcr_status resolve_impl(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, const
             return st;
         }
         add_stats(&loc.stats, *ctx->h_stats);
+        loc.stats.brute_force_equiv += single_pair_bf(pl, d0, d1, A, B);
         if (it == 0) loc.pairs_first = P;
         loc.pairs_last = P;
         loc.total_pairs += P;
