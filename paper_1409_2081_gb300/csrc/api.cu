@@ -37,22 +37,39 @@ struct GraphEntry {
     unsigned long long last_use = 0;
 };
 
+// The small device words of one call (status, statistics, counters, solver
+// control words and scalars, the touched-vertex count): one allocation, so
+// that a call clears them with one memset and reads them back with one
+// copy into the pinned mirror of the same layout.
+struct DevWords {
+    uint32_t status;
+    uint32_t pad0;
+    DevStats stats;
+    int cnt[16];
+    int iwork[16];
+    double dwork[16];
+    int touched;
+    int pad1[3];
+};
+
 struct hfcr_ctx {
     hfcr_options opt;
     std::string err;
     int64_t max_verts = 0, max_tris = 0, max_pairs = 0;
     int device = 0;
+    DevWords *d_words = nullptr;  // the words below point into these two
+    DevWords *h_words = nullptr;  // pinned mirror
     uint32_t *d_status = nullptr;
     DevStats *d_stats = nullptr;
     int *d_cnt = nullptr;         // [16] device counters
-    uint32_t *h_status = nullptr; // pinned
-    int *h_cnt = nullptr;         // pinned [16]
-    DevStats *h_stats = nullptr;  // pinned
-    double *h_dw = nullptr;       // pinned [4] solver words
+    uint32_t *h_status = nullptr;
+    int *h_cnt = nullptr;         // [16]
+    DevStats *h_stats = nullptr;
+    double *h_dw = nullptr;       // solver scalars
     int trav_variant = 0;         // traversal variant (hfcr_autotune)
     int *d_segs = nullptr;        // [8] segment table of a single mesh pair
     int *h_segs = nullptr;        // pinned [8]
-    int *h_iw = nullptr;          // pinned [8] solver control words
+    int *h_iw = nullptr;          // solver control words
     SortTemp sort;
     Bvh bvh[2];                   // [0]: faces of B (direction 0), [1]: faces of A (direction 1)
     int *edges[2] = {nullptr, nullptr};
@@ -119,7 +136,7 @@ cudaError_t dalloc(T **p, size_t n) {
 }
 
 void free_all(hfcr_ctx *c) {
-    void *ptrs[] = {c->d_status, c->d_stats, c->d_cnt, c->sort.hist, c->edges[0], c->edges[1],
+    void *ptrs[] = {c->d_words, c->sort.hist, c->edges[0], c->edges[1],
                     c->ekeys, c->ekeys_alt, c->eflags, c->pkeys, c->pkeys_alt, c->pairs,
                     c->skeys, c->skeys_alt, c->sflags, c->stencils,
                     c->sb.ids_raw, c->sb.n64_raw, c->sb.n32_raw, c->sb.b_raw, c->sb.parent,
@@ -129,8 +146,7 @@ void free_all(hfcr_ctx *c) {
                     c->sb.ids, c->sb.n64, c->sb.n32, c->sb.b, c->sb.lam, c->sb.r64, c->sb.r32,
                     c->sb.x32, c->sb.p32, c->sb.q32, c->sb.w32, c->sb.p64, c->sb.q64, c->sb.vidx, c->sb.ckey,
                     c->sb.ckey_alt, c->sb.cval, c->sb.cval_alt, c->sb.cflag, c->sb.seg, c->sb.gvert,
-                    c->sb.winv, c->sb.u64, c->sb.u32, c->sb.red, c->sb.d_U, c->sb.iwork,
-                    c->sb.dwork};
+                    c->sb.winv, c->sb.u64, c->sb.u32, c->sb.red};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *dp[] = {c->adj_ptr[0], c->adj_ptr[1], c->adj_nbr[0], c->adj_nbr[1], c->adj_cur, c->field,
@@ -151,13 +167,10 @@ void free_all(hfcr_ctx *c) {
             if (p) cudaFree(p);
         b = Bvh();
     }
-    if (c->h_status) cudaFreeHost(c->h_status);
-    if (c->h_cnt) cudaFreeHost(c->h_cnt);
-    if (c->h_stats) cudaFreeHost(c->h_stats);
-    if (c->h_dw) cudaFreeHost(c->h_dw);
+    if (c->h_words) cudaFreeHost(c->h_words);
     if (c->h_segs) cudaFreeHost(c->h_segs);
     if (c->d_segs) cudaFree(c->d_segs);
-    if (c->h_iw) cudaFreeHost(c->h_iw);
+    c->d_words = nullptr; c->h_words = nullptr;
     c->d_status = nullptr; c->d_stats = nullptr; c->d_cnt = nullptr; c->sort = SortTemp();
     c->edges[0] = c->edges[1] = nullptr;
     c->ekeys = c->ekeys_alt = nullptr; c->eflags = nullptr;
@@ -359,8 +372,7 @@ void launch_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d
         return;
     }
     prof_begin(ctx, HFCR_STAGE_VALIDATE, s);
-    validate_positions(*A, ctx->d_status, s);
-    validate_positions(*B, ctx->d_status, s);
+    validate_pair(*A, *B, ctx->d_status, s);
     check_segments(pl.segs, pl.nseg, *A, *B, ctx->d_status, s);
     prof_end(ctx, HFCR_STAGE_VALIDATE, s);
     for (int d = 0; d < 2; ++d) {
@@ -417,9 +429,7 @@ int64_t single_pair_bf(const DetectPlan &pl, bool d0, bool d1, const hfcr_mesh *
 }
 
 hfcr_status read_back(hfcr_ctx *ctx, cudaStream_t s) {
-    CK(cudaMemcpyAsync(ctx->h_cnt, ctx->d_cnt, sizeof(int) * 16, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_words, ctx->d_words, sizeof(DevWords), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
     prof_collect(ctx);
@@ -574,13 +584,8 @@ void enqueue_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bo
 }
 
 // Reads the counters, status, statistics and solver words of the last
-// iteration in one batch and synchronises.
-hfcr_status read_iteration(hfcr_ctx *ctx, cudaStream_t s) {
-    CK(cudaMemcpyAsync(ctx->h_iw, ctx->sb.iwork, sizeof(int) * 6, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(ctx->h_iw + 6, ctx->sb.d_U, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(ctx->h_dw, ctx->sb.dwork, sizeof(double), cudaMemcpyDeviceToHost, s));
-    return read_back(ctx, s);
-}
+// iteration (one copy) and synchronises.
+hfcr_status read_iteration(hfcr_ctx *ctx, cudaStream_t s) { return read_back(ctx, s); }
 
 hfcr_status reset_words(hfcr_ctx *ctx, cudaStream_t s);
 
@@ -600,11 +605,8 @@ void key_add(std::string &k, const T &v) {
 hfcr_status run_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d0, bool d1,
                           const DetectPlan &pl, bool *built, double d, cudaStream_t s) {
     auto body = [&]() -> hfcr_status {
-        hfcr_status st = reset_words(ctx, s);
+        hfcr_status st = reset_words(ctx, s);  // the solver words too
         if (st) return st;
-        CK(cudaMemsetAsync(ctx->sb.iwork, 0, sizeof(int) * 16, s));
-        CK(cudaMemsetAsync(ctx->sb.dwork, 0, sizeof(double) * 2, s));
-        CK(cudaMemsetAsync(ctx->sb.d_U, 0, sizeof(int), s));
         enqueue_iteration(ctx, A, B, d0, d1, pl, built, d, s);
         return HFCR_OK;
     };
@@ -672,27 +674,21 @@ hfcr_status run_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
 }
 
 hfcr_status solve_info(hfcr_ctx *ctx, int k, hfcr_solve_info *info, cudaStream_t s) {
-    int iw[16] = {0};
-    double dw[1] = {0};
-    if (k > 0) {
-        CK(cudaMemcpyAsync(iw, ctx->sb.iwork, sizeof(int) * 16, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(dw, ctx->sb.dwork, sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(ctx->h_cnt + 8, ctx->sb.d_U, sizeof(int), cudaMemcpyDeviceToHost, s));
-    }
+    if (k > 0)
+        CK(cudaMemcpyAsync(ctx->h_words, ctx->d_words, sizeof(DevWords), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    info->cg_iters = iw[1];
-    info->refine_rounds = iw[3];
-    info->rel_residual = dw[0];
-    info->converged = k == 0 || dw[0] <= ctx->opt.rel_tol;
+    const DevWords &w = *ctx->h_words;
+    info->cg_iters = k > 0 ? w.iwork[1] : 0;
+    info->refine_rounds = k > 0 ? w.iwork[3] : 0;
+    info->rel_residual = k > 0 ? w.dwork[0] : 0.0;
+    info->converged = k == 0 || w.dwork[0] <= ctx->opt.rel_tol;
     info->n_stencils = k;
-    info->n_touched = k > 0 ? ctx->h_cnt[8] : 0;
+    info->n_touched = k > 0 ? w.touched : 0;
     return HFCR_OK;
 }
 
 hfcr_status reset_words(hfcr_ctx *ctx, cudaStream_t s) {
-    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s));
-    CK(cudaMemsetAsync(ctx->d_stats, 0, sizeof(DevStats), s));
-    CK(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(int) * 16, s));
+    CK(cudaMemsetAsync(ctx->d_words, 0, sizeof(DevWords), s));
     return HFCR_OK;
 }
 
@@ -781,14 +777,18 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     if (max_tris < 1) max_tris = 1;
     if (max_pairs < 1) max_pairs = 1;
     const size_t T = (size_t)max_tris, P = (size_t)max_pairs, E3 = 3 * T;
-    CK(dalloc(&ctx->d_status, 1));
-    CK(dalloc(&ctx->d_stats, 1));
-    CK(dalloc(&ctx->d_cnt, 16));
-    CK(cudaMallocHost((void **)&ctx->h_status, sizeof(uint32_t)));
-    CK(cudaMallocHost((void **)&ctx->h_cnt, sizeof(int) * 16));
-    CK(cudaMallocHost((void **)&ctx->h_stats, sizeof(DevStats)));
-    CK(cudaMallocHost((void **)&ctx->h_dw, sizeof(double) * 4));
-    CK(cudaMallocHost((void **)&ctx->h_iw, sizeof(int) * 8));
+    CK(dalloc(&ctx->d_words, 1));
+    CK(cudaMemset(ctx->d_words, 0, sizeof(DevWords)));
+    CK(cudaMallocHost((void **)&ctx->h_words, sizeof(DevWords)));
+    memset(ctx->h_words, 0, sizeof(DevWords));
+    ctx->d_status = &ctx->d_words->status;
+    ctx->d_stats = &ctx->d_words->stats;
+    ctx->d_cnt = ctx->d_words->cnt;
+    ctx->h_status = &ctx->h_words->status;
+    ctx->h_stats = &ctx->h_words->stats;
+    ctx->h_cnt = ctx->h_words->cnt;
+    ctx->h_dw = ctx->h_words->dwork;
+    ctx->h_iw = ctx->h_words->iwork;
     CK(cudaMallocHost((void **)&ctx->h_segs, sizeof(int) * 8));
     CK(dalloc(&ctx->d_segs, 8));
     size_t maxn = E3 > 4 * P ? E3 : 4 * P;
@@ -878,9 +878,9 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(dalloc(&sb.u64, 12 * P));
     CK(dalloc(&sb.u32, 16 * P));
     CK(dalloc(&sb.red, 1024));
-    CK(dalloc(&sb.d_U, 1));
-    CK(dalloc(&sb.iwork, 16));
-    CK(dalloc(&sb.dwork, 16));
+    sb.d_U = &ctx->d_words->touched;
+    sb.iwork = ctx->d_words->iwork;
+    sb.dwork = ctx->d_words->dwork;
     ctx->max_verts = max_verts;
     ctx->max_tris = max_tris;
     ctx->max_pairs = max_pairs;
@@ -969,8 +969,7 @@ hfcr_status hfcr_build_stencils(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_me
     ctx->h_cnt[C_NPAIRS_IN] = (int)n_pairs;
     CK(cudaMemcpyAsync(ctx->d_cnt + C_NPAIRS_IN, ctx->h_cnt + C_NPAIRS_IN, sizeof(int),
                        cudaMemcpyHostToDevice, s));
-    validate_positions(*A, ctx->d_status, s);
-    validate_positions(*B, ctx->d_status, s);
+    validate_pair(*A, *B, ctx->d_status, s);
     int64_t k = 0;
     if ((st = make_stencils(ctx, A, B, pairs, (int)n_pairs, C_NPAIRS_IN, ctx->stencils, &k, s)))
         return st;
@@ -1005,8 +1004,7 @@ hfcr_status hfcr_respond(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     ctx->h_cnt[C_STENCILS] = (int)k;
     CK(cudaMemcpyAsync(ctx->d_cnt + C_STENCILS, ctx->h_cnt + C_STENCILS, sizeof(int),
                        cudaMemcpyHostToDevice, s));
-    validate_positions(*A, ctx->d_status, s);
-    validate_positions(*B, ctx->d_status, s);
+    validate_pair(*A, *B, ctx->d_status, s);
     if ((st = run_response(ctx, A, B, st_in, (int)k, d, 0, dxA, dxB, s))) return st;
     if (info) {
         memset(info, 0, sizeof *info);

@@ -63,6 +63,33 @@ __global__ void k_validate(const T *x, const T *y, const T *z, int n, uint32_t *
     if (bad && (threadIdx.x & 31) == 0) atomicOr(status, bad);
 }
 
+// both meshes of a pair in one launch: vertex i < nA of A, else i - nA of B
+template <typename T>
+__global__ void k_validate_pair(const T *ax, const T *ay, const T *az, int nA, const T *bx,
+                                const T *by, const T *bz, int nB, uint32_t *status) {
+    HFCR_PDL_WAIT();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t bad = 0;
+    if (i < nA + nB) {
+        const bool inA = i < nA;
+        const int j = inA ? i : i - nA;
+        T c[3] = {inA ? ax[j] : bx[j], inA ? ay[j] : by[j], inA ? az[j] : bz[j]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T v = c[k];
+            if (!isfinite(v)) {
+                bad |= ST_NONFINITE;
+            } else {
+                T a = fabs(v);
+                if (a > (T)0x1p38) bad |= ST_RANGE;
+                if (sizeof(T) == 8 && a != (T)0 && a < (T)0x1p-200) bad |= ST_RANGE;
+            }
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (bad && (threadIdx.x & 31) == 0) atomicOr(status, bad);
+}
+
 __global__ void k_edge_keys(const int *tris, int nt, int vb, unsigned long long *keys,
                             uint32_t *status, int nv) {
     HFCR_PDL_WAIT();
@@ -365,6 +392,25 @@ void validate_positions(const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s) 
     else
         { launch_pdl(k_validate<double>, nb, 256, 0, s, (const double *)m.x, (const double *)m.y,
                                               (const double *)m.z, m.n_verts, d_status); note_launch(); }
+}
+
+void validate_pair(const hfcr_mesh &A, const hfcr_mesh &B, uint32_t *d_status, cudaStream_t s) {
+    if (A.dtype != B.dtype) {
+        validate_positions(A, d_status, s);
+        validate_positions(B, d_status, s);
+        return;
+    }
+    const int nA = A.n_verts > 0 ? A.n_verts : 0, nB = B.n_verts > 0 ? B.n_verts : 0;
+    if (nA + nB <= 0) return;
+    const int nb = (nA + nB + 255) / 256;
+    if (A.dtype == HFCR_F32)
+        { launch_pdl(k_validate_pair<float>, nb, 256, 0, s, (const float *)A.x, (const float *)A.y,
+                     (const float *)A.z, nA, (const float *)B.x, (const float *)B.y,
+                     (const float *)B.z, nB, d_status); note_launch(); }
+    else
+        { launch_pdl(k_validate_pair<double>, nb, 256, 0, s, (const double *)A.x,
+                     (const double *)A.y, (const double *)A.z, nA, (const double *)B.x,
+                     (const double *)B.y, (const double *)B.z, nB, d_status); note_launch(); }
 }
 
 void build_edges(const int *tris, int n_tris, int n_verts, int *edges_out, int *d_count,

@@ -173,6 +173,8 @@ void edge_order(const int *edges, int ne, const hfcr_mesh &m, const int *segs, i
 
 // ---- validation ----
 void validate_positions(const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s);
+// both meshes of a pair (one launch when they share a dtype)
+void validate_pair(const hfcr_mesh &A, const hfcr_mesh &B, uint32_t *d_status, cudaStream_t s);
 
 // ---- detection ----
 struct DetectArgs {
@@ -261,7 +263,7 @@ struct SolveBuffers {
     float *u32 = nullptr;        // [4 * 4 cap_k] (float4 per touched vertex)
     double *red = nullptr;       // reduction partials [1024]
     int *d_U = nullptr;          // touched vertex count (device)
-    int *iwork = nullptr;        // [16] solver control words
+    int *iwork = nullptr;        // [16] solver control words (zeroed by the caller before a solve)
     double *dwork = nullptr;     // [16]
 };
 

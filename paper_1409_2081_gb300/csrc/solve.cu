@@ -1848,7 +1848,7 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
     const int fast_smem = g_fast_smem, zone_small_smem = g_zone_small_smem;
     int rb = (cap + 255) / 256;
     if (rb > RES_BLOCKS) rb = RES_BLOCKS;
-    cudaMemsetAsync(sb.iwork, 0, sizeof(int) * 16, s);
+    // sb.iwork and sb.dwork were zeroed with the call's other device words
     if (p.solver == HFCR_SOLVER_FP64) {
         // one float64 run with the whole iteration budget of the mixed solver
         { launch_pdl(k_init_lam, rb, 256, 0, s, d_k, sb.b, sb.lam, sb.r64); note_launch(); }
