@@ -168,6 +168,18 @@ def whole_job(local_total_ms: float, steps: int, dist=None, device=None):
     return t, t / (steps * ws)
 
 
+def packed(torch, xs):
+    """One buffer holding the coordinate arrays xs back to back, views into
+    it (in order) and a copy of its initial state: a step restores, uploads
+    or downloads every array of both meshes with one copy."""
+    pos = torch.cat([t.reshape(-1) for t in xs])
+    views, o = [], 0
+    for t in xs:
+        views.append(pos[o:o + t.numel()])
+        o += t.numel()
+    return pos, pos.clone(), views
+
+
 def scene():
     import meshgen
     return meshgen.scene_c2()
@@ -301,13 +313,13 @@ def batched(api, torch, dev, steps, warmup, timed_fn):
     ea = ea[:ctx.hfcr_build_edges(ta, len(VA), ea)].contiguous()
     eb = torch.zeros((3 * len(TB), 2), dtype=torch.int32, device=dev)
     eb = eb[:ctx.hfcr_build_edges(tb, len(VB), eb)].contiguous()
-    A = api.Mesh(*[t.clone() for t in xa], ta, True, edges=ea)
-    B = api.Mesh(*[t.clone() for t in xb], tb, True, edges=eb)
+    pos, pos0, v = packed(torch, xa + xb)
+    A = api.Mesh(*v[:3], ta, True, edges=ea)
+    B = api.Mesh(*v[3:], tb, True, edges=eb)
     dsegs = torch.tensor(segs, device=dev)
 
     def step():
-        for t, t0 in zip((A.x, A.y, A.z, B.x, B.y, B.z), xa + xb):
-            t.copy_(t0, non_blocking=True)
+        pos.copy_(pos0, non_blocking=True)
         return ctx.hfcr_resolve_batch(A, B, dsegs, D_POST, 1)
 
     variant, variant_ms = ctx.hfcr_autotune(A, B, dsegs)
@@ -355,18 +367,20 @@ def small_form(api, torch, dev, steps, timed_fn):
         # topology preparation (once per mesh, outside the timed region)
         e = torch.zeros((3 * m.n_tris, 2), dtype=torch.int32, device=dev)
         e = e[:ctx.hfcr_build_edges(tris, m.n_verts, e)].contiguous()
-        return api.Mesh(*[t.clone() for t in xyz], tris, True, edges=e), xyz
+        return tris, e, xyz
 
     out = {"workload": "two icospheres L3 (1,280 faces each), offset 1.5, jitter 0.01, float64"}
     for name, solver, f32f, graphs in (("fp64_form", api.HFCR_SOLVER_FP64, False, False),
                                        ("mixed_form", api.HFCR_SOLVER_MIXED, True, True)):
         ctx = api.Context(solver=solver, f32_filter=f32f, graphs=graphs)
         ctx.hfcr_reserve(sc.A.n_verts, sc.A.n_tris, 1 << 14)
-        (A, a0), (B, b0) = mesh(ctx, sc.A), mesh(ctx, sc.B)
+        (ta, ea, a0), (tb, eb, b0) = mesh(ctx, sc.A), mesh(ctx, sc.B)
+        pos, pos0, v = packed(torch, a0 + b0)
+        A = api.Mesh(*v[:3], ta, True, edges=ea)
+        B = api.Mesh(*v[3:], tb, True, edges=eb)
 
         def step():
-            for t, t0 in zip((A.x, A.y, A.z, B.x, B.y, B.z), a0 + b0):
-                t.copy_(t0, non_blocking=True)
+            pos.copy_(pos0, non_blocking=True)
             return ctx.hfcr_resolve(A, B, D_POST, 1)
 
         ms, infos = timed_fn(step, steps, 3)
@@ -374,8 +388,7 @@ def small_form(api, torch, dev, steps, timed_fn):
                      "pairs": int(infos[-1].pairs_first)}
         if solver == api.HFCR_SOLVER_MIXED:
             def loop():
-                for t, t0 in zip((A.x, A.y, A.z, B.x, B.y, B.z), a0 + b0):
-                    t.copy_(t0, non_blocking=True)
+                pos.copy_(pos0, non_blocking=True)
                 return ctx.hfcr_resolve(A, B, D_POST, 64)
             lms, linfo = timed_fn(loop, max(3, steps // 10), 1)
             out["repair_loop"] = {"ms": round(statistics.median(lms), 3),
@@ -399,17 +412,18 @@ def precision_form(api, torch, dev, steps, timed_fn, d_values=(1e-4, 1e-3, 1e-2)
     import meshgen
     sc = meshgen.scene_c3()
 
-    def mesh(m):
-        xyz = [torch.tensor(np.ascontiguousarray(m.V[:, c].astype(np.float32)), device=dev) for c in range(3)]
-        return api.Mesh(*xyz, torch.tensor(m.T, device=dev), True), [t.clone() for t in xyz]
-
     def fresh():
-        (A, a0), (B, b0) = mesh(sc.A), mesh(sc.B)
-        return A, B, a0 + b0
+        # the six coordinate arrays are views of one buffer (one restore copy);
+        # init = (buffer, its initial copy, the six initial arrays)
+        xyz = [torch.tensor(np.ascontiguousarray(m.V[:, c].astype(np.float32)), device=dev)
+               for m in (sc.A, sc.B) for c in range(3)]
+        pos, pos0, views = packed(torch, xyz)
+        A = api.Mesh(*views[:3], torch.tensor(sc.A.T, device=dev), True)
+        B = api.Mesh(*views[3:], torch.tensor(sc.B.T, device=dev), True)
+        return A, B, (pos, pos0, xyz)
 
     def restore(A, B, init):
-        for t, t0 in zip((A.x, A.y, A.z, B.x, B.y, B.z), init):
-            t.copy_(t0, non_blocking=True)
+        init[0].copy_(init[1], non_blocking=True)  # all six coordinate arrays
 
     cap = 1 << 20
     ctx = api.Context()
@@ -431,8 +445,8 @@ def precision_form(api, torch, dev, steps, timed_fn, d_values=(1e-4, 1e-3, 1e-2)
     k = ctx.hfcr_build_stencils(A, B, pairs, n, st)
     ctx64 = api.Context(solver=api.HFCR_SOLVER_FP64)
     ctx64.hfcr_reserve(sc.A.n_verts, sc.A.n_tris, cap)
-    A64 = api.Mesh(*[t.double() for t in init[:3]], A.tris, True)
-    B64 = api.Mesh(*[t.double() for t in init[3:]], B.tris, True)
+    A64 = api.Mesh(*[t.double() for t in init[2][:3]], A.tris, True)
+    B64 = api.Mesh(*[t.double() for t in init[2][3:]], B.tris, True)
     dx = {}
     for name, c, MA, MB in (("mixed", ctx, A64, B64), ("fp64", ctx64, A64, B64)):
         da = [torch.zeros(sc.A.n_verts, dtype=torch.float64, device=dev) for _ in range(3)]
@@ -561,16 +575,17 @@ def main():
         ea = torch.zeros((3 * sc.A.n_tris, 2), dtype=torch.int32, device=dev)
         ne = ctx.hfcr_build_edges(ta, sc.A.n_verts, ea)
         ea = ea[:ne].contiguous()
-        A = api.Mesh(*[t.clone() for t in xa], ta, False, edges=ea)
-        B = api.Mesh(*[t.clone() for t in xb], tb, True)
-        init = xa + xb
-        return ctx, A, B, init, ne
+        # the six coordinate arrays are views of one buffer, so that a frame
+        # restores (or uploads, or downloads) the positions in one copy
+        pos, pos0, views = packed(torch, xa + xb)
+        A = api.Mesh(*views[:3], ta, False, edges=ea)
+        B = api.Mesh(*views[3:], tb, True)
+        return ctx, A, B, (pos, pos0), ne
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def restore(A, B, init):
-        for t, t0 in zip((A.x, A.y, A.z, B.x, B.y, B.z), init):
-            t.copy_(t0, non_blocking=True)
+        init[0].copy_(init[1], non_blocking=True)  # all six coordinate arrays
 
     def frame(ctx, A, B, init):
         restore(A, B, init)
@@ -672,20 +687,19 @@ def main():
                     chosen_by="the larger of the solve and traverse stages in the profiled pass")
 
     # ---- end to end through the C ABI with host buffers ----
-    host_in = [t.detach().cpu().pin_memory() for t in init]
-    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    # both meshes' coordinates, one pinned host buffer each way
+    host_in = init[1].detach().cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
 
     def e2e_frame():
-        for t, h in zip((A.x, A.y, A.z, B.x, B.y, B.z), host_in):
-            t.copy_(h, non_blocking=True)
+        init[0].copy_(host_in, non_blocking=True)
         info = ctx.hfcr_resolve(A, B, D_POST, 1)
-        for t, h in zip((A.x, A.y, A.z, B.x, B.y, B.z), host_out):
-            h.copy_(t, non_blocking=True)
+        host_out.copy_(init[0], non_blocking=True)
         return info
 
     e2e_ms, _ = timed(e2e_frame, args.steps, 2)
     e2e_total, _ = whole_job(sum(e2e_ms), args.steps, pg, dev)
-    io_bytes = sum(h.numel() * h.element_size() for h in host_in)
+    io_bytes = host_in.numel() * host_in.element_size()
 
     # ---- the plain float64 GPU form on the same frame ----
     fp64 = None
