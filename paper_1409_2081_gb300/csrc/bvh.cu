@@ -211,9 +211,11 @@ __device__ __forceinline__ unsigned spread10(unsigned v) {
     return v;
 }
 
+// Morton code of each face's centroid, quantised to `cells` per axis in the
+// scene bounds (cells <= 1024), above it the face's segment
 template <typename T>
 __global__ void k_morton(const T *x, const T *y, const T *z, int nv, const int *tris, int nt,
-                         const float *bounds, const int *segs, int col, int nseg,
+                         const float *bounds, const int *segs, int col, int nseg, float cells,
                          unsigned long long *keys, int *vals, uint32_t *st) {
     HFCR_PDL_WAIT();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -228,7 +230,7 @@ __global__ void k_morton(const T *x, const T *y, const T *z, int nv, const int *
         float m = (float)((a[k] + b[k] + c[k]) / (T)3);
         float ext = bounds[3 + k] - bounds[k];
         float u = ext > 0.f ? (m - bounds[k]) / ext : 0.f;
-        u = fminf(fmaxf(u * 1024.f, 0.f), 1023.f);
+        u = fminf(fmaxf(u * cells, 0.f), cells - 1.f);
         q[k] = (unsigned)u;
     }
     const unsigned long long seg = (unsigned long long)seg_of(segs, col, nseg, t);
@@ -450,6 +452,18 @@ void bvh_build(Bvh &b, const hfcr_mesh &m, const int *segs, int col, int nseg, S
     b.nseg = nseg;
     if (n <= 0) return;
     int nb = (n + 255) / 256;
+    // one mesh: 8 bits per axis (24-bit codes, three radix passes; at the
+    // face counts here a cell holds about one or two centroids, and equal
+    // codes are ordered by face index); a batch: 10 bits per axis below the
+    // segment number, each pair's faces sorted by their own CTA
+    const bool single = nseg <= 1;
+    const float cells = single ? 256.f : 1024.f;
+    const int kbits = single ? 24 : 30 + bits_for(nseg + 1);
+    // an odd pass count of the one-mesh sort starts from the spare buffers,
+    // so that the sorted keys and faces end in the tree's own
+    const bool odd = single && (((kbits + 7) / 8) & 1);
+    unsigned long long *kin = odd ? b.keys_alt : b.keys, *kout = odd ? b.keys : b.keys_alt;
+    int *vin = odd ? b.vals_alt : b.leaf_face, *vout = odd ? b.leaf_face : b.vals_alt;
     int vbk = (nv + 255) / 256;
     if (vbk > 1024) vbk = 1024;
     if (vbk < 1) vbk = 1;
@@ -459,25 +473,21 @@ void bvh_build(Bvh &b, const hfcr_mesh &m, const int *segs, int col, int nseg, S
                      b.bounds_part); note_launch(); }
         { launch_pdl(k_bounds_final, 1, 256, 0, s, b.bounds_part, vbk, b.bounds); note_launch(); }
         { launch_pdl(k_morton<float>, nb, 256, 0, s, x, y, z, nv, m.tris, n, b.bounds, segs, col,
-                     nseg, b.keys,
-                                           b.leaf_face, d_status); note_launch(); }
+                     nseg, cells, kin, vin, d_status); note_launch(); }
     } else {
         const double *x = (const double *)m.x, *y = (const double *)m.y, *z = (const double *)m.z;
         { launch_pdl(k_vertex_bounds<double>, vbk, 256, 0, s, x, y, z, nv,
                      b.bounds_part); note_launch(); }
         { launch_pdl(k_bounds_final, 1, 256, 0, s, b.bounds_part, vbk, b.bounds); note_launch(); }
         { launch_pdl(k_morton<double>, nb, 256, 0, s, x, y, z, nv, m.tris, n, b.bounds, segs, col,
-                     nseg, b.keys,
-                                            b.leaf_face, d_status); note_launch(); }
+                     nseg, cells, kin, vin, d_status); note_launch(); }
     }
     // a batch sorts each pair's faces in its own CTA (the segment bits above
     // the 30 Morton bits are constant within a pair); one mesh globally
-    bool flip = nseg > 1
+    bool flip = !single
                     ? radix_sort_u64v_segments(b.keys, b.leaf_face, b.keys_alt, b.vals_alt, n,
-                                               30 + bits_for(nseg + 1), segs, col, nseg, 30, b.d_rest,
-                                               t, s)
-                    : radix_sort_u64(b.keys, b.leaf_face, b.keys_alt, b.vals_alt, n,
-                                     30 + bits_for(nseg + 1), t, s);
+                                               kbits, segs, col, nseg, 30, b.d_rest, t, s)
+                    : radix_sort_u64(kin, vin, kout, vout, n, kbits, t, s) != (kin == b.keys_alt);
     if (flip) {
         cudaMemcpyAsync(b.keys, b.keys_alt, sizeof(unsigned long long) * n, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(b.leaf_face, b.vals_alt, sizeof(int) * n, cudaMemcpyDeviceToDevice, s);
