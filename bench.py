@@ -116,8 +116,8 @@ def measured_peak_hbm():
     return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = {"k_traverse": ("detect.cu", "predicates.cuh"), "k_cg_zone": ("solve.cu",)}
-PROFILES = {"k_traverse": "k_traverse_cloth_torus.md", "k_cg_zone": "k_cg_zone_cloth_torus.md"}
+KERNEL_SOURCES = {"k_traverse": ("detect.cu", "predicates.cuh"), "k_cg_zone_pair": ("solve.cu",)}
+PROFILES = {"k_traverse": "k_traverse_cloth_torus.md", "k_cg_zone_pair": "k_cg_zone_pair_cloth_torus.md"}
 
 
 def kernel_source_hash(kernel: str = "k_traverse") -> str:
@@ -643,9 +643,10 @@ def main():
     dominant = max(stage_ms, key=stage_ms.get)
     # rooflines of the two kernels that own a stage each: the traversal +
     # exact narrow phase, and the per-zone solver (the solve stage is
-    # k_cg_zone<256>, the one-warp-per-zone and 1024-thread launches, both
-    # nearly empty on this frame, and the one-CTA k_zone_final);
-    # algorithmic bytes = compulsory reads + writes
+    # k_cg_zone_pair, which solves this frame's ten zones, the
+    # one-warp-per-zone and 1024-thread launches, both nearly empty here,
+    # and the one-CTA k_zone_final); algorithmic bytes = compulsory reads +
+    # writes
     trav_ms, trav_n = prof["traverse"]
     trav_avg_ms = trav_ms / max(1, trav_n)
     alg_trav = (sc.A.n_verts * 12 + ne * 8 + sc.B.n_verts * 12 + sc.B.n_tris * 12 + P * 8)
@@ -674,15 +675,15 @@ def main():
                        "traffic": profiled_traffic("k_traverse"), "alg_bytes_per_launch": alg_trav,
                        "avg_launch_ms": round(trav_avg_ms, 5), "launches_timed": trav_n,
                        "traverse_variant": variant, "variant_ms": variant_ms},
-        "k_cg_zone": {"kernel": "k_cg_zone<256> (float32 PCG per impact zone, float64 refinement in "
-                                "the kernel)", "bound": "hbm",
+        "k_cg_zone_pair": {"kernel": "k_cg_zone_pair (float32 PCG per impact zone, float64 "
+                                     "refinement in the kernel)", "bound": "hbm",
                       "achieved": round(ach_cg, 3), "peak": peak, "peak_kind": peak_kind,
                       "unit": "GB/s", "frac": round(ach_cg / peak, 6),
-                      "traffic": profiled_traffic("k_cg_zone"), "alg_bytes_per_launch": alg_cg,
+                      "traffic": profiled_traffic("k_cg_zone_pair"), "alg_bytes_per_launch": alg_cg,
                       "avg_launch_ms": round(solve_avg_ms, 5), "launches_timed": solve_n,
                       "stencils": k_st, "touched_vertices": int(si.n_touched)},
     }
-    dom_kernel = "k_cg_zone" if stage_ms["solve"] >= stage_ms["traverse"] else "k_traverse"
+    dom_kernel = "k_cg_zone_pair" if stage_ms["solve"] >= stage_ms["traverse"] else "k_traverse"
     roofline = dict(roof[dom_kernel], dominant_stage=dominant,
                     chosen_by="the larger of the solve and traverse stages in the profiled pass")
 

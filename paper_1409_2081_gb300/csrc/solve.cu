@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg(
 // ---------------------------------------------------------------------------
 
 constexpr int FAST_SMEM = 231424;  // 226 KB dynamic (+256 B static) under the 227 KB per-CTA limit
-constexpr int ZONE_SMALL_SMEM = 56 * 1024;  // small zones: up to 4 CTAs per SM
+constexpr int ZONE_MID = 256;   // zones with at least this many stencils get all 512 threads
+constexpr int ZONE_PAIR_SMEM = 112 * 1024;  // k_cg_zone_pair: 2 CTAs per SM, 56 KB per half
 constexpr int ZONE_BIG = 1024;  // zones with at least this many stencils get a 1024-thread CTA
 
 struct CgView {
@@ -383,6 +384,57 @@ struct WarpGroup {
 #pragma unroll
         for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         return __shfl_sync(0xffffffffu, x, 0);
+    }
+};
+
+// One 256-thread half H of a 512-thread CTA (threads 256 H .. 256 H + 255)
+// solving a zone of its own: its barrier is the named barrier 1 + H, its
+// reductions run over its 8 warps through its own red / redd slices (24
+// floats, 8 doubles; each slot is rewritten only after another of the
+// half's barriers).  Sums are identical in every thread of the half.
+template <int H>
+struct HalfGroup {
+    __device__ static int rank() { return threadIdx.x - 256 * H; }
+    __device__ static int size() { return 256; }
+    __device__ static void sync() { asm volatile("bar.sync %0, 256;" ::"n"(1 + H) : "memory"); }
+    __device__ static void sum3(float a, float b, float c, float *red, float &sa, float &sb,
+                                float &sc) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 7;
+        if (lane == 0) {
+            red[3 * w] = a;
+            red[3 * w + 1] = b;
+            red[3 * w + 2] = c;
+        }
+        sync();
+        float x = lane < 8 ? red[3 * lane] : 0.f;
+        float y = lane < 8 ? red[3 * lane + 1] : 0.f;
+        float q = lane < 8 ? red[3 * lane + 2] : 0.f;
+#pragma unroll
+        for (int o = 4; o; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+            q += __shfl_xor_sync(0xffffffffu, q, o);
+        }
+        sa = __shfl_sync(0xffffffffu, x, 0);
+        sb = __shfl_sync(0xffffffffu, y, 0);
+        sc = __shfl_sync(0xffffffffu, q, 0);
+    }
+    __device__ static double sum(double x, double *redd) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        x = __shfl_sync(0xffffffffu, x, 0);
+        if ((threadIdx.x & 31) == 0) redd[(threadIdx.x >> 5) & 7] = x;
+        sync();
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += redd[w];
+        sync();
+        return s;
     }
 };
 
@@ -878,6 +930,7 @@ struct ZoneArgs {
     int maxit, max_refine;
     double tol, rel_tol;
     int *ctl;
+    unsigned *ticket;  // [2] zone counters of the pair launch (zero before a solve)
 };
 
 // |b_zone|^2 with lam = 0 for the zone's rows
@@ -996,65 +1049,139 @@ __global__ void __launch_bounds__(256, 4) k_cg_zone_warp(const int *d_nz, ZoneAr
     }
 }
 
-// The mixed solver, one CTA per impact zone of more than warp_max stencils
-// (the zones k_cg_zone_warp took); the 256-thread launch (is_big = 0) takes the zones below
-// big_min, the 1024-thread launch (is_big = 1, all of shared memory) the
-// rest.  A zone whose data do not fit the CTA's shared memory runs the same
-// rounds on global scratch.
+// Zone z solved by the thread group Gp: staged in shared memory at base
+// when its data fit smem_bytes, else the same rounds on global scratch.
+// The two paths are instantiated separately so that the shared-memory one
+// sees pointers derived only from the shared array (LDS/STS, not generic
+// loads).
+struct ZoneScratch {
+    float *x, *r, *p, *s, *w, *z, *u;
+};
+
+template <class Gp>
+__device__ __forceinline__ void solve_zone(const ZoneArgs &a, int z, char *base, int smem_bytes,
+                                           float *red, double *redd, const ZoneScratch &g) {
+    const int tid = Gp::rank(), nt = Gp::size();
+    const int s0 = a.zs[z], k = a.zs[z + 1] - s0;
+    const int j0 = a.zv[z], U = a.zv[z + 1] - j0;
+    const double bb = zone_start<Gp>(a, s0, k, redd);
+    const int g0 = a.zg[z], G = a.zg[z + 1] - g0;
+    const bool in_smem = zone_smem_need(k, U, G) <= smem_bytes;
+    int its = 0, rounds = 0;
+    double rr;
+    if (in_smem) {
+        const ZoneResult r = solve_zone_smem<Gp>(a, z, base, bb, red, redd);
+        rr = r.rr;
+        its = r.its;
+        rounds = r.rounds;
+    } else {
+        const double target = a.rel_tol * a.rel_tol * bb;
+        CgView v;
+        v.r = g.r + s0; v.p = g.p + s0; v.x = g.x + s0; v.sv = g.s + s0; v.w = g.w + s0;
+        v.z = g.z + s0;
+        v.u = (float4 *)g.u + j0;
+        v.n4 = a.n32 + s0;
+        v.pinv = a.pinv + s0; v.gst = a.gst + g0; v.G = G; v.goff = s0;
+        v.vidx = a.vidx + s0; v.seg = a.seg + j0; v.cval = a.cval; v.winv = a.winv + j0;
+        v.voff = j0; v.coff = 4 * s0; v.eoff = 0;
+        for (int t = tid; t < k; t += nt) v.r[t] = (float)a.b64[s0 + t];
+        rr = bb;
+        while (rr > target && rounds < a.max_refine) {
+            for (int t = tid; t < k; t += nt) {
+                v.p[t] = 0.f;
+                v.sv[t] = 0.f;
+                v.x[t] = 0.f;
+            }
+            Gp::sync();
+            its += cg_cg_loop<Gp>(v, k, U, a.maxit, (float)a.tol, red);
+            for (int t = tid; t < k; t += nt) a.lam[s0 + t] += (double)v.x[t];
+            Gp::sync();
+            rr = zone_residual<Gp>(v, k, U, s0, j0, a.n64, a.b64, a.lam, a.u64, redd);
+            ++rounds;
+        }
+    }
+    if (tid == 0) zone_finish(a, z, rr, bb, its, rounds, in_smem);
+    Gp::sync();  // shared memory is reused by the group's next zone
+}
+
+// The mixed solver's CTA launches (k_cg_zone_warp takes the zones of at
+// most WARP_ZONE stencils).  k_cg_zone_pair: the zones of ZONE_MID to
+// ZONE_BIG - 1 stencils one at a time on all 512 threads, then the smaller
+// ones two at a time, one per 256-thread half (its own named barrier, half
+// the shared memory), so that a zone gets about one to four rows per
+// thread.  k_cg_zone<1024>: the
+// rest, one 1,024-thread CTA with all of shared memory each.  (solve_zone
+// ends with its group's barrier, so the halves may reuse the shared memory
+// of the CTA's last whole-CTA zone.)
+// Zone assignment of the pair launch: a solver's first zone is fixed (so
+// that while there are fewer zones than solvers each zone has an SM to
+// itself), the following ones are taken from a counter in turn (zones
+// differ widely in size; the counter balances them).  stride = the
+// solvers; the counter counts the zones taken beyond the fixed ones.
+// Returns the group's next zone, identical in every thread of the group
+// (slot: the group's shared word).
+template <class Gp>
+__device__ __forceinline__ int next_zone(unsigned *counter, int stride, int *slot) {
+    if (Gp::rank() == 0) *slot = stride + (int)atomicAdd(counter, 1u);
+    Gp::sync();
+    const int z = *slot;
+    Gp::sync();  // the slot is rewritten by the next call
+    return z;
+}
+
+// the zones of small_lo < k < ZONE_MID stencils on half H (first fixed
+// zone: blockIdx.x + H gridDim.x)
+template <int H>
+__device__ __forceinline__ void half_zones(const ZoneArgs &a, int nz, int small_lo, char *base,
+                                           int bytes, float *red, double *redd,
+                                           const ZoneScratch &g, int *slot) {
+    const bool more = nz > 2 * (int)gridDim.x;  // zones beyond the fixed ones
+    for (int z = blockIdx.x + H * gridDim.x; z < nz;
+         z = more ? next_zone<HalfGroup<H>>(a.ticket + 1, 2 * gridDim.x, slot) : nz) {
+        const int k = a.zs[z + 1] - a.zs[z];
+        if (k <= small_lo || k >= ZONE_MID) continue;
+        solve_zone<HalfGroup<H>>(a, z, base, bytes, red, redd, g);
+    }
+}
+
+__global__ void __launch_bounds__(512, 2) k_cg_zone_pair(const int *d_nz, ZoneArgs a, int small_lo,
+                                                         ZoneScratch g, int smem_bytes) {
+    HFCR_PDL_WAIT();
+    extern __shared__ float4 smem4[];
+    __shared__ float red[96];     // halves: 24 floats each; the whole CTA: 48
+    __shared__ double redd[16];   // halves: 8 each; the whole CTA: 16
+    __shared__ int slot[3];
+    const int nz = *d_nz;
+    // the larger zones first, on all 512 threads
+    const bool more = nz > (int)gridDim.x;  // zones beyond the fixed ones
+    for (int z = blockIdx.x; z < nz;
+         z = more ? next_zone<CtaGroup>(a.ticket, gridDim.x, slot + 2) : nz) {
+        const int k = a.zs[z + 1] - a.zs[z];
+        if (k < ZONE_MID || k >= ZONE_BIG) continue;
+        solve_zone<CtaGroup>(a, z, (char *)smem4, smem_bytes, red, redd, g);
+    }
+    // then the smaller ones, two at a time (a whole-CTA zone ends with a
+    // barrier of the whole CTA, so the halves may reuse the shared memory)
+    const int half_bytes = (smem_bytes / 2) & ~15;
+    if (threadIdx.x < 256)
+        half_zones<0>(a, nz, small_lo, (char *)smem4, half_bytes, red, redd, g, slot);
+    else
+        half_zones<1>(a, nz, small_lo, (char *)smem4 + half_bytes, half_bytes, red + 24, redd + 8,
+                      g, slot + 1);
+}
+
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 4 : 1) k_cg_zone(
-    const int *d_nz, ZoneArgs a, int warp_max, int big_min, int is_big, float *x_g, float *r_g,
-    float *p_g, float *s_g, float *w_g, float *z_g, float *u_g, int smem_bytes) {
+__global__ void __launch_bounds__(THREADS, 1) k_cg_zone(const int *d_nz, ZoneArgs a, int k_lo,
+                                                        ZoneScratch g, int smem_bytes) {
     HFCR_PDL_WAIT();
     extern __shared__ float4 smem4[];
     __shared__ float red[96];
     __shared__ double redd[THREADS / 32];
-    const int nz = *d_nz, tid = threadIdx.x, nt = blockDim.x;
+    const int nz = *d_nz;
     for (int z = blockIdx.x; z < nz; z += gridDim.x) {
-        const int s0 = a.zs[z], k = a.zs[z + 1] - s0;
-        const int j0 = a.zv[z], U = a.zv[z + 1] - j0;
-        if (k <= warp_max || (k >= big_min) != (is_big != 0)) continue;
-        const double bb = zone_start<CtaGroup>(a, s0, k, redd);
-        const int g0 = a.zg[z], G = a.zg[z + 1] - g0;
-        const bool in_smem = zone_smem_need(k, U, G) <= smem_bytes;
-        int its = 0, rounds = 0;
-        double rr;
-        // the two paths are instantiated separately so that the shared-memory
-        // one sees pointers derived only from the shared array (LDS/STS, not
-        // generic loads)
-        if (in_smem) {
-            const ZoneResult r = solve_zone_smem<CtaGroup>(a, z, (char *)smem4, bb, red, redd);
-            rr = r.rr;
-            its = r.its;
-            rounds = r.rounds;
-        } else {
-            const double target = a.rel_tol * a.rel_tol * bb;
-            CgView v;
-            v.r = r_g + s0; v.p = p_g + s0; v.x = x_g + s0; v.sv = s_g + s0; v.w = w_g + s0;
-            v.z = z_g + s0;
-            v.u = (float4 *)u_g + j0;
-            v.n4 = a.n32 + s0;
-            v.pinv = a.pinv + s0; v.gst = a.gst + g0; v.G = G; v.goff = s0;
-            v.vidx = a.vidx + s0; v.seg = a.seg + j0; v.cval = a.cval; v.winv = a.winv + j0;
-            v.voff = j0; v.coff = 4 * s0; v.eoff = 0;
-            for (int t = tid; t < k; t += nt) v.r[t] = (float)a.b64[s0 + t];
-            rr = bb;
-            while (rr > target && rounds < a.max_refine) {
-                for (int t = tid; t < k; t += nt) {
-                    v.p[t] = 0.f;
-                    v.sv[t] = 0.f;
-                    v.x[t] = 0.f;
-                }
-                __syncthreads();
-                its += cg_cg_loop<CtaGroup>(v, k, U, a.maxit, (float)a.tol, red);
-                for (int t = tid; t < k; t += nt) a.lam[s0 + t] += (double)v.x[t];
-                __syncthreads();
-                rr = zone_residual<CtaGroup>(v, k, U, s0, j0, a.n64, a.b64, a.lam, a.u64, redd);
-                ++rounds;
-            }
-        }
-        if (tid == 0) zone_finish(a, z, rr, bb, its, rounds, in_smem);
-        __syncthreads();  // shared memory is reused by the next zone
+        const int k = a.zs[z + 1] - a.zs[z];
+        if (k <= k_lo) continue;
+        solve_zone<CtaGroup>(a, z, (char *)smem4, smem_bytes, red, redd, g);
     }
 }
 
@@ -1664,16 +1791,16 @@ void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int ca
 
 // dynamic shared memory granted to the zone CG kernels (0: the global-memory
 // path runs); set once per process, outside any stream capture
-static int g_fast_smem = -1, g_zone_small_smem = 0, g_warp_zone_smem = 0;
+static int g_fast_smem = -1, g_zone_pair_smem = 0, g_warp_zone_smem = 0;
 
 void solver_init() {
     if (g_fast_smem >= 0) return;
     g_fast_smem = cudaFuncSetAttribute(k_cg_zone<CG_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        FAST_SMEM) == cudaSuccess ? FAST_SMEM : 0;
     if (!g_fast_smem) cudaGetLastError();
-    g_zone_small_smem = cudaFuncSetAttribute(k_cg_zone<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             ZONE_SMALL_SMEM) == cudaSuccess ? ZONE_SMALL_SMEM : 0;
-    if (!g_zone_small_smem) cudaGetLastError();
+    g_zone_pair_smem = cudaFuncSetAttribute(k_cg_zone_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            ZONE_PAIR_SMEM) == cudaSuccess ? ZONE_PAIR_SMEM : 0;
+    if (!g_zone_pair_smem) cudaGetLastError();
     const int wz = WARP_ZONE_WARPS * WARP_ZONE_SMEM;
     g_warp_zone_smem = cudaFuncSetAttribute(k_cg_zone_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             wz) == cudaSuccess ? wz : 0;
@@ -1845,7 +1972,7 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
     (void)d_status;
     if (cap <= 0) return;
     solver_init();
-    const int fast_smem = g_fast_smem, zone_small_smem = g_zone_small_smem;
+    const int fast_smem = g_fast_smem;
     int rb = (cap + 255) / 256;
     if (rb > RES_BLOCKS) rb = RES_BLOCKS;
     // sb.iwork and sb.dwork were zeroed with the call's other device words
@@ -1876,6 +2003,7 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
     za.b64 = sb.b; za.lam = sb.lam; za.u64 = sb.u64; za.zres = sb.r64; za.zbb = sb.q64;
     za.maxit = p.max_cg_iters; za.max_refine = p.max_refine;
     za.tol = p.inner_tol; za.rel_tol = p.rel_tol; za.ctl = sb.iwork;
+    za.ticket = (unsigned *)(sb.iwork + 13);  // iwork is zeroed before every solve
     const int warp_max = g_warp_zone_smem ? WARP_ZONE : 0;
     if (warp_max) {
         int zw = (cap + WARP_ZONE_WARPS - 1) / WARP_ZONE_WARPS;  // CTAs of the warp launch
@@ -1883,16 +2011,20 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
         { launch_pdl(k_cg_zone_warp, zw, 32 * WARP_ZONE_WARPS, g_warp_zone_smem, s, sb.d_nz,
                      za); note_launch(); }
     }
-    int zsmall = (cap + 1023) / 1024 * 4;  // blocks of the small-zone launch (grid-stride over zones)
-    if (zsmall > 2048) zsmall = 2048;
+    ZoneScratch gs;
+    gs.x = sb.x32; gs.r = sb.r32; gs.p = sb.p32; gs.s = sb.q32; gs.w = sb.w32; gs.z = sb.z32;
+    gs.u = sb.u32;
+    // CTAs of the pair launch: two zones of more than warp_max stencils at
+    // a time (at most 2 CTAs per SM); of the 1024-thread launch: one zone
+    // of ZONE_BIG or more stencils each
+    int zpair = (cap / (WARP_ZONE + 1) + 1) / 2 + 1;
+    if (zpair > 2 * 152) zpair = 2 * 152;
     int zbig = (cap + ZONE_BIG - 1) / ZONE_BIG;
     if (zbig > 152) zbig = 152;
-    { launch_pdl(k_cg_zone<256>, zsmall, 256, zone_small_smem, s, sb.d_nz, za, warp_max, ZONE_BIG,
-                 0, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.z32, sb.u32,
-          zone_small_smem); note_launch(); }
-    { launch_pdl(k_cg_zone<CG_THREADS>, zbig, CG_THREADS, fast_smem, s, sb.d_nz, za, warp_max,
-                 ZONE_BIG, 1, sb.x32, sb.r32, sb.p32, sb.q32, sb.w32, sb.z32, sb.u32,
-          fast_smem); note_launch(); }
+    { launch_pdl(k_cg_zone_pair, zpair, 512, g_zone_pair_smem, s, sb.d_nz, za, warp_max, gs,
+                 g_zone_pair_smem); note_launch(); }
+    { launch_pdl(k_cg_zone<CG_THREADS>, zbig, CG_THREADS, fast_smem, s, sb.d_nz, za, ZONE_BIG - 1,
+                 gs, fast_smem); note_launch(); }
     { launch_pdl(k_zone_final, 1, 256, 0, s, sb.d_nz, sb.r64, sb.q64, p.rel_tol, sb.dwork,
                  sb.iwork); note_launch(); }
 }
