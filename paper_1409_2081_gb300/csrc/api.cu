@@ -553,13 +553,20 @@ void enqueue_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bo
     keys_to_pairs(ctx->pkeys, ctx->d_cnt + C_PEFF, cap, pl.edges[0], pl.edges[1], pl.edge_bits,
                   pl.face_bits, ctx->pairs, s);
     MeshPair mp{*A, *B};
-    int maxv = A->n_verts > B->n_verts ? A->n_verts : B->n_verts;
-    int maxf = A->n_tris > B->n_tris ? A->n_tris : B->n_tris;
+    // stencil keys (dir, x0, face): x0 and face fields sized to the meshes
+    // of the directions this iteration runs, the direction bit sorted only
+    // when both run (otherwise it is the same in every key)
+    int maxv = 0, maxf = 0;
+    if (d0) { maxv = A->n_verts; maxf = B->n_tris; }
+    if (d1) {
+        if (B->n_verts > maxv) maxv = B->n_verts;
+        if (A->n_tris > maxf) maxf = A->n_tris;
+    }
     int vb = bits_for(maxv > 1 ? maxv : 2), fb = bits_for(maxf > 1 ? maxf : 2);
     stencil_keys(mp, ctx->pairs, ctx->d_cnt + C_PEFF, cap, vb, fb, ctx->opt.f32_filter, ctx->skeys,
                  ctx->d_stats, ctx->d_status, s);
     const bool flip = radix_sort_u64_dev(ctx->skeys, ctx->skeys_alt, ctx->d_cnt + C_PEFF, cap,
-                                         1 + vb + fb, ctx->sort, s);
+                                         (d0 && d1 ? 1 : 0) + vb + fb, ctx->sort, s);
     stencil_unique(flip ? ctx->skeys_alt : ctx->skeys, ctx->d_cnt + C_PEFF, cap, vb, fb, ctx->sflags,
                    ctx->stencils, ctx->d_cnt + C_STENCILS, ctx->sort, s);
     prof_end(ctx, HFCR_STAGE_STENCILS, s);
