@@ -1462,13 +1462,14 @@ __device__ __forceinline__ bool setup_scan(SetupSync &g, bool small, unsigned *a
 }
 
 // stable sort of (key, val) pairs over `bits` bits (a multiple of 8); the
-// result is in (k1, v1) after an odd number of passes.  Small: the first
-// CTA alone, then a barrier.
+// result is in (k1, v1) after an odd number of passes.  One CTA taking
+// part: the single-CTA sort; otherwise every CTA taking part (at most one
+// tile each on small inputs: no scan phase).
 __device__ __forceinline__ bool setup_sort(SetupSync &g, bool small, unsigned *k0, int *v0,
                                            unsigned *k1, int *v1, int n, int bits,
                                            const SetupArgs &a, SortSmem &sm) {
-    if (small) {
-        if (blockIdx.x == 0) sort_small_body<unsigned, true, true>(k0, v0, k1, v1, n, bits, sm);
+    if (small && g.parts == 1) {
+        sort_small_body<unsigned, true, true>(k0, v0, k1, v1, n, bits, sm);
         return g.sync();
     }
     return sort_grid_body<unsigned, true>(k0, v0, k1, v1, n, bits, a.hist, a.tot, g.bar, g.epoch,
@@ -1525,8 +1526,11 @@ __device__ __forceinline__ void setup_unite(int *par, int s0, int s1, uint32_t *
 // child, inside the same zone) is finished by the union-find.
 constexpr int SV_SWEEPS = 64;
 
-__device__ void zones_min_label(int *f, int k, const unsigned *ck1, const int *cv1, int n4,
-                                uint32_t *status) {
+// edge[i] (i < n4): the stencils (u << 16 | v) of entries i and i - 1 of the
+// vertex-sorted list when they share a vertex, NO_EDGE otherwise
+constexpr unsigned NO_EDGE = 0xffffffffu;
+
+__device__ void zones_min_label(int *f, int k, const unsigned *edge, int n4, uint32_t *status) {
     __shared__ int changed;
     for (int s = threadIdx.x; s < k; s += TPB) f[s] = s;
     if (threadIdx.x == 0) changed = 0;
@@ -1535,8 +1539,9 @@ __device__ void zones_min_label(int *f, int k, const unsigned *ck1, const int *c
     for (int sweep = 0; sweep < SV_SWEEPS; ++sweep) {
         bool ch = false;
         for (int i = threadIdx.x + 1; i < n4; i += TPB) {
-            if (ck1[i] != ck1[i - 1]) continue;
-            const int u = cv1[i] >> 2, v = cv1[i - 1] >> 2;
+            const unsigned e = edge[i];
+            if (e == NO_EDGE) continue;
+            const int u = (int)(e >> 16), v = (int)(e & 0xffffu);
             const int fu = f[u], fv = f[v];
             const int m = min(f[fu], f[fv]);
             ch |= atomicMin(f + fu, m) > m;
@@ -1557,8 +1562,10 @@ __device__ void zones_min_label(int *f, int k, const unsigned *ck1, const int *c
         if (threadIdx.x == 0) changed = 0;  // written again only after the next sweep's barrier
     }
     if (again) {
-        for (int i = threadIdx.x + 1; i < n4; i += TPB)
-            if (ck1[i] == ck1[i - 1]) setup_unite<true>(f, cv1[i] >> 2, cv1[i - 1] >> 2, status);
+        for (int i = threadIdx.x + 1; i < n4; i += TPB) {
+            const unsigned e = edge[i];
+            if (e != NO_EDGE) setup_unite<true>(f, (int)(e >> 16), (int)(e & 0xffffu), status);
+        }
         __syncthreads();
     }
 }
@@ -1625,11 +1632,43 @@ __device__ bool setup_phases(SetupSync &g, const SetupArgs &a, int k, SortSmem &
     const unsigned *zl = f2 ? a.zlab_alt : a.zlab;
     const int *zr = f2 ? a.zsrc_alt : a.zsrc;
     if (small) {
-        if (blockIdx.x == 0) {  // sort, union-find, labels and their sort in this CTA
-            sort_small_body<unsigned, true, true>(a.ckey, a.cval, a.ckey_alt, a.cval_alt, n4,
-                                                  a.vbits, sm);
+        // the entries sorted by every CTA taking part (one CTA: by itself),
+        // then the zones, the labels and their sort in the first CTA
+        if (g.parts > 1 &&
+            !sort_grid_body<unsigned, true>(a.ckey, a.cval, a.ckey_alt, a.cval_alt, n4, a.vbits,
+                                            a.hist, a.tot, g.bar, g.epoch, g.status, sm, g.parts))
+            return false;
+        if (blockIdx.x == 0) {
+            if (g.parts == 1)
+                sort_small_body<unsigned, true, true>(a.ckey, a.cval, a.ckey_alt, a.cval_alt, n4,
+                                                      a.vbits, sm);
             int *par = par_s;  // overlays the sort's shared memory (the sort is done)
-            zones_min_label(par, k, ck1, cv1, n4, a.status);
+            // the adjacent pairs of sorted entries, read once through L2
+            // (other CTAs wrote them; eight entries' loads in flight per
+            // thread) and packed into cflag (free here)
+            for (int i0 = 0; i0 < n4; i0 += 8 * TPB) {
+                unsigned kc[8], kb[8];
+                int vc[8], vb[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int i = i0 + q * TPB + threadIdx.x;
+                    const bool ok = i > 0 && i < n4;
+                    kc[q] = ok ? __ldcg(ck1 + i) : 0u;
+                    kb[q] = ok ? __ldcg(ck1 + i - 1) : 1u;
+                    vc[q] = ok ? __ldcg(cv1 + i) : 0;
+                    vb[q] = ok ? __ldcg(cv1 + i - 1) : 0;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int i = i0 + q * TPB + threadIdx.x;
+                    if (i < n4)
+                        a.cflag[i] = kc[q] == kb[q]
+                                         ? (unsigned)(vc[q] >> 2) << 16 | (unsigned)(vb[q] >> 2)
+                                         : NO_EDGE;
+                }
+            }
+            __syncthreads();
+            zones_min_label(par, k, a.cflag, n4, a.status);
             for (int s = threadIdx.x; s < k; s += TPB) {
                 a.zlab[s] = (unsigned)uf_find_s(par, s);
                 a.zsrc[s] = s;

@@ -26,6 +26,7 @@ constexpr int ROUNDS = 8;
 constexpr int TILE = TPB * ROUNDS;  // 2048
 constexpr int SMALL_N = 16 * TILE;  // single-CTA sort up to 32768 keys
 constexpr int HIST_BATCH = 8;       // keys a thread loads at once for a digit count
+constexpr int FEW_TILES = 16;       // grid sorts of at most this many tiles skip the scan phase
 
 // shared memory of one sorting CTA (the kernel declares it once, so that a
 // kernel holding several sorts, or a sort and other phases, can overlay it)
@@ -240,7 +241,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned epoch, uint
 
 // All passes of the multi-CTA sort by every CTA of a cooperative launch:
 // the grid walks the tiles in each phase, with grid-wide barriers between
-// the histogram, the digit-row scans and the scatter.  hist holds 256 rows
+// the histogram, the digit-row scans and the scatter (with at most
+// FEW_TILES tiles and a CTA per tile, each CTA derives its offsets itself
+// and the scan phase and its barrier drop out).  hist holds 256 rows
 // of ceil(n / TILE) tile counts, tot 256 digit totals.  Data written by
 // other CTAs (keys, histogram rows, digit totals) is read with L2 loads
 // (__ldcg), never through a possibly stale L1 line.  parts: the CTAs taking
@@ -276,6 +279,59 @@ __device__ __forceinline__ bool sort_grid_body(K *k0, int *v0, K *k1, int *v1, i
             __syncthreads();
         }
         if (!grid_barrier(bar, ++epoch, status, P)) return false;
+        if (nba <= P && nba <= FEW_TILES) {
+            // one tile per CTA: each CTA with a tile derives its digit offsets
+            // itself (thread d: digit d's count over all tiles and over the
+            // tiles before its own), so the pass needs no scan phase
+            const int b = blockIdx.x;
+            if (b < nba) {
+                const int d = threadIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+                unsigned total = 0, before = 0;
+                for (int q = 0; q < nba; ++q) {
+                    const unsigned c = __ldcg(hist + d * nba + q);
+                    total += c;
+                    if (q < b) before += c;
+                }
+                unsigned x = total;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (lane == 31) wsum[w] = x;
+                __syncthreads();
+                unsigned pre = 0;
+                for (int q = 0; q < w; ++q) pre += wsum[q];
+                dbase[d] = pre + x - total + before;
+                for (int i = threadIdx.x; i < (TPB / 32) * 256; i += TPB) (&wh[0][0])[i] = 0;
+                __syncthreads();
+                K key[ROUNDS];
+                int val[ROUNDS];
+                unsigned dig[ROUNDS], rank[ROUNDS];
+                rank_tile<K, HV, true>(kin, vin, n, b * TILE, wh, key, val, dig, rank, shift);
+                __syncthreads();
+                unsigned run = 0;
+                for (int q = 0; q < TPB / 32; ++q) {
+                    unsigned c = wh[q][threadIdx.x];
+                    wh[q][threadIdx.x] = run;
+                    run += c;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < ROUNDS; ++r) {
+                    const unsigned dg = dig[r];
+                    if (dg < 256) {
+                        const unsigned pos = dbase[dg] + wh[w][dg] + rank[r];
+                        kout[pos] = key[r];
+                        if (HV) vout[pos] = val[r];
+                    }
+                }
+            }
+            if (!grid_barrier(bar, ++epoch, status, P)) return false;
+            K *tk = kin; kin = kout; kout = tk;
+            int *tv = vin; vin = vout; vout = tv;
+            continue;
+        }
         for (int d = blockIdx.x; d < 256; d += P) {
             const unsigned total = block_scan_excl<TPB, true>(hist + d * nba, nba);
             if (threadIdx.x == 0) tot[d] = total;
