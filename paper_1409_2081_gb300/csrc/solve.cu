@@ -11,10 +11,15 @@
 //   q = grad(D) u          (per stencil: gather of four vertices).
 // Displacement x' - x = -M^-1 grad(D)^T lambda (Eq. 5).
 //
-// The matrix is block-diagonal by impact zone (stencils that share a vertex,
-// found by union-find); every zone is solved on its own.
-// MIXED: per zone (one warp for zones of at most 32 stencils, one CTA for
-// the others, staged in shared memory), conjugate gradients in float32 on
+// The matrix is block-diagonal by impact zone (stencils that share a vertex:
+// connected components by min-label hooking or a lock-free union-find, both
+// giving each zone its smallest stencil as label); every zone is solved on
+// its own.  The response setup (vertex CSR, zones, zone-ordered rows and
+// CSR, preconditioner groups) runs in one cooperative launch (k_setup), or
+// as a sequence of kernels.
+// MIXED: per zone (a thread group sized to the zone: one warp up to 32
+// stencils, a 256-thread half CTA up to 255, a 512-thread CTA up to 1,023,
+// a 1,024-thread CTA above; staged in shared memory), conjugate gradients in float32 on
 // float32 normals, preconditioned by the inverses of the blocks of rows that
 // share x0, solve for a correction of lambda; the zone's residual
 // b - A lambda is recomputed in float64 with the float64 normals after every
