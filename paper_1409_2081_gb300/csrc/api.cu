@@ -81,7 +81,6 @@ struct hfcr_ctx {
     unsigned long long *ekeys = nullptr, *ekeys_alt = nullptr;
     unsigned *eflags = nullptr;
     unsigned long long *pkeys = nullptr, *pkeys_alt = nullptr;
-    hfcr_pair *pairs = nullptr;
     unsigned long long *skeys = nullptr, *skeys_alt = nullptr;
     unsigned *sflags = nullptr;
     hfcr_stencil *stencils = nullptr;
@@ -137,7 +136,7 @@ cudaError_t dalloc(T **p, size_t n) {
 
 void free_all(hfcr_ctx *c) {
     void *ptrs[] = {c->d_words, c->sort.hist, c->edges[0], c->edges[1],
-                    c->ekeys, c->ekeys_alt, c->eflags, c->pkeys, c->pkeys_alt, c->pairs,
+                    c->ekeys, c->ekeys_alt, c->eflags, c->pkeys, c->pkeys_alt,
                     c->skeys, c->skeys_alt, c->sflags, c->stencils,
                     c->sb.ids_raw, c->sb.n64_raw, c->sb.n32_raw, c->sb.b_raw, c->sb.parent,
                     c->sb.zkey, c->sb.zkey_alt, c->sb.szone, c->sb.zs, c->sb.zv, c->sb.d_nz,
@@ -174,7 +173,7 @@ void free_all(hfcr_ctx *c) {
     c->d_status = nullptr; c->d_stats = nullptr; c->d_cnt = nullptr; c->sort = SortTemp();
     c->edges[0] = c->edges[1] = nullptr;
     c->ekeys = c->ekeys_alt = nullptr; c->eflags = nullptr;
-    c->pkeys = c->pkeys_alt = nullptr; c->pairs = nullptr;
+    c->pkeys = c->pkeys_alt = nullptr;
     c->skeys = c->skeys_alt = nullptr; c->sflags = nullptr; c->stencils = nullptr;
     c->sb = SolveBuffers();
     c->h_status = nullptr; c->h_cnt = nullptr; c->h_stats = nullptr; c->h_dw = nullptr; c->h_iw = nullptr;
@@ -539,19 +538,16 @@ hfcr_status prepare_diffusion(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh
 }
 
 // One repair iteration enqueued on device counts only: detection, clamped
-// pair count, pair records, stencils, assembly, solve, applied
-// displacement.  Grids are sized by the reserved capacity; kernels read
-// the live counts.  Nothing is read back.  The pairs stay in the order the
-// traversal appended them: the stencils are sorted and deduplicated on
-// their own keys, so their list does not depend on that order.
+// pair count, stencils, assembly, solve, applied displacement.  Grids are
+// sized by the reserved capacity; kernels read the live counts.  Nothing is
+// read back.  The pair keys stay in the order the traversal appended them:
+// the stencils are sorted and deduplicated on their own keys, so their list
+// does not depend on that order.
 void enqueue_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d0, bool d1,
                        const DetectPlan &pl, bool *built, double d, cudaStream_t s) {
     const int cap = (int)ctx->max_pairs;
     launch_detect(ctx, A, B, d0, d1, pl, built, s);
     prof_begin(ctx, HFCR_STAGE_STENCILS, s);
-    clamp_count(ctx->d_cnt + C_PAIRS, cap, ctx->d_cnt + C_PEFF, ctx->d_status, s);
-    keys_to_pairs(ctx->pkeys, ctx->d_cnt + C_PEFF, cap, pl.edges[0], pl.edges[1], pl.edge_bits,
-                  pl.face_bits, ctx->pairs, s);
     MeshPair mp{*A, *B};
     // stencil keys (dir, x0, face): x0 and face fields sized to the meshes
     // of the directions this iteration runs, the direction bit sorted only
@@ -563,8 +559,11 @@ void enqueue_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bo
         if (A->n_tris > maxf) maxf = A->n_tris;
     }
     int vb = bits_for(maxv > 1 ? maxv : 2), fb = bits_for(maxf > 1 ? maxf : 2);
-    stencil_keys(mp, ctx->pairs, ctx->d_cnt + C_PEFF, cap, vb, fb, ctx->opt.f32_filter, ctx->skeys,
-                 ctx->d_stats, ctx->d_status, s);
+    // the pair keys as appended, decoded straight into stencil keys (the
+    // clamped pair count to C_PEFF)
+    stencil_keys_from_pair_keys(mp, ctx->pkeys, ctx->d_cnt + C_PAIRS, cap, pl.edges[0], pl.edges[1],
+                                pl.edge_bits, pl.face_bits, vb, fb, ctx->opt.f32_filter,
+                                ctx->skeys, ctx->d_cnt + C_PEFF, ctx->d_stats, ctx->d_status, s);
     const bool flip = radix_sort_u64_dev(ctx->skeys, ctx->skeys_alt, ctx->d_cnt + C_PEFF, cap,
                                          (d0 && d1 ? 1 : 0) + vb + fb, ctx->sort, s);
     stencil_unique(flip ? ctx->skeys_alt : ctx->skeys, ctx->d_cnt + C_PEFF, cap, vb, fb, ctx->sflags,
@@ -824,7 +823,6 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(dalloc(&ctx->eflags, E3));
     CK(dalloc(&ctx->pkeys, P));
     CK(dalloc(&ctx->pkeys_alt, P));
-    CK(dalloc(&ctx->pairs, P));
     CK(dalloc(&ctx->skeys, P));
     CK(dalloc(&ctx->skeys_alt, P));
     CK(dalloc(&ctx->sflags, P));

@@ -300,21 +300,18 @@ __device__ __forceinline__ void ld3(const hfcr_mesh &m, int i, T *o) {
 }
 
 // x0 = the endpoint of the pair's edge on the back side of its face
+// stencil key of the pair (dir, v0, v1, f): x0 = the endpoint of the edge on
+// the back side of its face
 template <typename T>
-__global__ void k_stencil_keys(hfcr_mesh A, hfcr_mesh B, const hfcr_pair *pairs, const int *d_n,
-                               int cap, int vert_bits, int face_bits, int f32_filter,
-                               unsigned long long *keys, DevStats *st, uint32_t *status) {
-    HFCR_PDL_WAIT();
-    int n = min(*d_n, cap);
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    hfcr_pair pr = pairs[i];
-    unsigned dir = pr.dir ? 1u : 0u;
-    if (pr.dir > 1u) atomicOr(status, ST_BAD_INDEX);
+__device__ __forceinline__ unsigned long long stencil_key_of(const hfcr_mesh &A, const hfcr_mesh &B,
+                                                             unsigned dir, unsigned pv0, unsigned pv1,
+                                                             unsigned pf, int vert_bits, int face_bits,
+                                                             int f32_filter, DevStats *st,
+                                                             uint32_t *status) {
     const hfcr_mesh &E = dir ? B : A;
     const hfcr_mesh &F = dir ? A : B;
-    int v0 = chk((int)pr.v0, E.n_verts, status), v1 = chk((int)pr.v1, E.n_verts, status);
-    int f = chk((int)pr.face, F.n_tris, status);
+    int v0 = chk((int)pv0, E.n_verts, status), v1 = chk((int)pv1, E.n_verts, status);
+    int f = chk((int)pf, F.n_tris, status);
     int ia = chk(F.tris[3 * f], F.n_verts, status), ib = chk(F.tris[3 * f + 1], F.n_verts, status),
         ic = chk(F.tris[3 * f + 2], F.n_verts, status);
     T a[3], b[3], c[3], p[3];
@@ -326,8 +323,52 @@ __global__ void k_stencil_keys(hfcr_mesh A, hfcr_mesh B, const hfcr_pair *pairs,
     // a crossing pair has s != 0; a pair given by the caller with the first
     // endpoint on the plane keeps v1 (the crossing test would reject it)
     unsigned x0 = s < 0 ? (unsigned)v0 : (unsigned)v1;
-    keys[i] = ((unsigned long long)dir << (vert_bits + face_bits)) |
-              ((unsigned long long)x0 << face_bits) | (unsigned long long)(unsigned)f;
+    return ((unsigned long long)dir << (vert_bits + face_bits)) |
+           ((unsigned long long)x0 << face_bits) | (unsigned long long)(unsigned)f;
+}
+
+template <typename T>
+__global__ void k_stencil_keys(hfcr_mesh A, hfcr_mesh B, const hfcr_pair *pairs, const int *d_n,
+                               int cap, int vert_bits, int face_bits, int f32_filter,
+                               unsigned long long *keys, DevStats *st, uint32_t *status) {
+    HFCR_PDL_WAIT();
+    int n = min(*d_n, cap);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    hfcr_pair pr = pairs[i];
+    unsigned dir = pr.dir ? 1u : 0u;
+    if (pr.dir > 1u) atomicOr(status, ST_BAD_INDEX);
+    keys[i] = stencil_key_of<T>(A, B, dir, pr.v0, pr.v1, pr.face, vert_bits, face_bits, f32_filter,
+                                st, status);
+}
+
+// The same from the traversal's pair keys (dir | edge | face) as appended:
+// the pair count is clamped here (more than cap: ST_CAPACITY and no pair;
+// the clamped count to *d_eff for the kernels that follow)
+template <typename T>
+__global__ void k_stencil_keys_from_pair_keys(hfcr_mesh A, hfcr_mesh B,
+                                              const unsigned long long *pkeys, const int *d_n,
+                                              int cap, const int2 *edgesA, const int2 *edgesB,
+                                              int edge_bits, int pface_bits, int vert_bits,
+                                              int face_bits, int f32_filter,
+                                              unsigned long long *keys, int *d_eff, DevStats *st,
+                                              uint32_t *status) {
+    HFCR_PDL_WAIT();
+    int n = *d_n;
+    if (n > cap) n = 0;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        if (*d_n > cap) atomicOr(status, ST_CAPACITY);
+        *d_eff = n;
+    }
+    if (i >= n) return;
+    const unsigned long long k = pkeys[i];
+    const unsigned dir = (unsigned)(k >> (edge_bits + pface_bits));
+    const int e = (int)((k >> pface_bits) & ((1ull << edge_bits) - 1));
+    const unsigned f = (unsigned)(k & ((1ull << pface_bits) - 1));
+    const int2 ev = dir ? edgesB[e] : edgesA[e];
+    keys[i] = stencil_key_of<T>(A, B, dir, (unsigned)ev.x, (unsigned)ev.y, f, vert_bits, face_bits,
+                                f32_filter, st, status);
 }
 
 __global__ void k_stencil_flags(const unsigned long long *keys, const int *d_n, int cap,
@@ -358,16 +399,6 @@ __global__ void k_stencil_write(const unsigned long long *keys, const unsigned *
 
 // effective count = count when it fits the capacity, else 0 with
 // ST_CAPACITY raised (so nothing downstream runs on a truncated set)
-__global__ void k_clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *status) {
-    HFCR_PDL_WAIT();
-    int n = *d_n;
-    if (n > cap) {
-        atomicOr(status, ST_CAPACITY);
-        n = 0;
-    }
-    *d_eff = n;
-}
-
 __device__ __forceinline__ int first_edge_from(const int2 *E, int ne, int v) {
     int lo = 0, hi = ne;  // first edge whose first vertex is >= v
     while (lo < hi) {
@@ -402,10 +433,6 @@ void pair_products(const int *edges, int ne, const int *segs, int nseg, int ecol
     { launch_pdl(k_pair_products, (nseg + 255) / 256, 256, 0, s, (const int2 *)edges, ne, segs,
                  nseg, ecol,
                                                         fcol, nfaces, stats); note_launch(); }
-}
-
-void clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *d_status, cudaStream_t s) {
-    { launch_pdl(k_clamp_count, 1, 1, 0, s, d_n, cap, d_eff, d_status); note_launch(); }
 }
 
 template <typename T, bool F32F, int MINB, bool NOINL, bool PACKET>
@@ -466,6 +493,24 @@ void stencil_keys(const MeshPair &mp, const hfcr_pair *pairs, const int *d_n, in
         { launch_pdl(k_stencil_keys<double>, nb, 256, 0, s, mp.A, mp.B, pairs, d_n, cap,
                      vert_bits, face_bits,
                                                   f32_filter, keys, stats, d_status); note_launch(); }
+}
+
+void stencil_keys_from_pair_keys(const MeshPair &mp, const unsigned long long *pkeys, const int *d_n,
+                                 int cap, const int *edgesA, const int *edgesB, int edge_bits,
+                                 int pface_bits, int vert_bits, int face_bits, int f32_filter,
+                                 unsigned long long *keys, int *d_eff, DevStats *stats,
+                                 uint32_t *d_status, cudaStream_t s) {
+    if (cap <= 0) return;
+    const int nb = (cap + 255) / 256;
+    if (mp.A.dtype == HFCR_F32)
+        launch_pdl(k_stencil_keys_from_pair_keys<float>, nb, 256, 0, s, mp.A, mp.B, pkeys, d_n, cap,
+                   (const int2 *)edgesA, (const int2 *)edgesB, edge_bits, pface_bits, vert_bits,
+                   face_bits, f32_filter, keys, d_eff, stats, d_status);
+    else
+        launch_pdl(k_stencil_keys_from_pair_keys<double>, nb, 256, 0, s, mp.A, mp.B, pkeys, d_n, cap,
+                   (const int2 *)edgesA, (const int2 *)edgesB, edge_bits, pface_bits, vert_bits,
+                   face_bits, f32_filter, keys, d_eff, stats, d_status);
+    note_launch();
 }
 
 void stencil_unique(const unsigned long long *keys, const int *d_n, int cap, int vert_bits,

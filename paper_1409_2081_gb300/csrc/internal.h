@@ -201,8 +201,6 @@ void detect_launch(const DetectArgs &a, cudaStream_t s, uint32_t *d_status);
 // sorted by first vertex, so each pair's edges are contiguous)
 void pair_products(const int *edges, int ne, const int *segs, int nseg, int ecol, int fcol,
                    int nfaces, DevStats *stats, cudaStream_t s);
-// d_eff = *d_n if it is at most cap, else 0 and ST_CAPACITY
-void clamp_count(const int *d_n, int cap, int *d_eff, uint32_t *d_status, cudaStream_t s);
 // keys (sorted) -> hfcr_pair records
 void keys_to_pairs(const unsigned long long *keys, const int *d_n, int cap, const int *edgesA,
                    const int *edgesB, int edge_bits, int face_bits, hfcr_pair *out, cudaStream_t s);
@@ -211,6 +209,14 @@ void keys_to_pairs(const unsigned long long *keys, const int *d_n, int cap, cons
 struct MeshPair {
     hfcr_mesh A, B;
 };
+// one stencil key per pair of the traversal's pair keys (dir | edge | face,
+// in append order); the pair count *d_n is clamped to cap into *d_eff (more
+// than cap: ST_CAPACITY and none)
+void stencil_keys_from_pair_keys(const MeshPair &mp, const unsigned long long *pkeys, const int *d_n,
+                                 int cap, const int *edgesA, const int *edgesB, int edge_bits,
+                                 int pface_bits, int vert_bits, int face_bits, int f32_filter,
+                                 unsigned long long *keys, int *d_eff, DevStats *stats,
+                                 uint32_t *d_status, cudaStream_t s);
 // one stencil key per pair (dir | x0 | face); n pairs from host count
 void stencil_keys(const MeshPair &mp, const hfcr_pair *pairs, const int *d_n, int cap,
                   int vert_bits, int face_bits, int f32_filter, unsigned long long *keys,

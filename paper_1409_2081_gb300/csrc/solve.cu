@@ -1752,21 +1752,21 @@ __device__ bool setup_phases(SetupSync &g, const SetupArgs &a, int k, SortSmem &
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.bar + SETUP_READY, 1u);
     }
     // zone-ordered CSR: the vertex-ordered entries re-sorted stably by zone
+    // (an odd pass count starts from the spare buffers, so that the sorted
+    // entries end in v2, where the solver reads them)
+    const int qbits = setup_bits((int)nz);
+    const bool qodd = (qbits / 8) & 1;
+    unsigned *k2in = qodd ? a.k2_alt : a.k2, *k2out = qodd ? a.k2 : a.k2_alt;
+    int *v2in = qodd ? a.v2_alt : a.v2, *v2out = qodd ? a.v2 : a.v2_alt;
     for (int i = tid; i < n4; i += nt) {
         const int e = __ldcg(cv1 + i);
         const int t = __ldcg(pos_of + (e >> 2));
-        a.k2[i] = (unsigned)__ldcg(a.szone + t);
-        a.v2[i] = 4 * t + (e & 3);
+        k2in[i] = (unsigned)__ldcg(a.szone + t);
+        v2in[i] = 4 * t + (e & 3);
     }
     if (!g.sync()) return false;
-    const int qbits = setup_bits((int)nz);
-    if (!setup_sort(g, small, a.k2, a.v2, a.k2_alt, a.v2_alt, n4, qbits, a, sm)) return false;
+    if (!setup_sort(g, small, k2in, v2in, k2out, v2out, n4, qbits, a, sm)) return false;
     const unsigned *zk = a.k2;
-    if ((qbits / 8) & 1) {  // the entries end in v2 whatever the pass count
-        zk = a.k2_alt;
-        for (int i = tid; i < n4; i += nt) a.v2[i] = __ldcg(a.v2_alt + i);
-        if (!g.sync()) return false;
-    }
     const int *val = a.v2;
     const int *idsi = (const int *)a.ids;
     for (int i = tid; i < n4; i += nt)
