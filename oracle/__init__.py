@@ -410,26 +410,14 @@ def vertex_adjacency(E: np.ndarray, n_verts: int):
     return np.cumsum(indptr), dst
 
 
-def diffuse(dx: np.ndarray, E: np.ndarray, rings: int, sweeps: int,
-            fixed: Optional[np.ndarray] = None) -> np.ndarray:
-    """Spreads the displacement of the vertices the minimizer moved to their
-    vicinity as a discrete harmonic field (Sec. 5 names constrained
-    diffusion without equations; this is the reading used here): the moved
-    vertices (nonzero dx) keep their displacement (Dirichlet), vertices more
-    than `rings` edges away and `fixed` (kinematic) vertices keep zero, and
-    each vertex in between takes the mean of its neighbours, `sweeps` Jacobi
-    sweeps starting from zero.  The ring distance is the edge-count distance
-    to the nearest moved vertex over the whole mesh.  dx: [n, 3]."""
-    n = dx.shape[0]
-    C = np.any(dx != 0.0, axis=1)
-    if rings <= 0 or sweeps <= 0 or not C.any():
-        return dx.copy()
-    indptr, nbr = vertex_adjacency(E, n)
-    deg = np.diff(indptr)
-    # ring distance from the moved vertices (breadth-first, `rings` levels)
+def ring_distance(moved: np.ndarray, indptr, nbr, rings: int) -> np.ndarray:
+    """Edge-count distance of every vertex to the nearest moved vertex,
+    found breadth-first over `rings` levels; vertices farther away get
+    rings + 1."""
+    n = len(moved)
     dist = np.full(n, rings + 1, np.int64)
-    dist[C] = 0
-    frontier = np.nonzero(C)[0]
+    dist[moved] = 0
+    frontier = np.nonzero(moved)[0]
     for r in range(1, rings + 1):
         nxt = []
         for v in frontier:
@@ -438,19 +426,77 @@ def diffuse(dx: np.ndarray, E: np.ndarray, rings: int, sweeps: int,
                     dist[w] = r
                     nxt.append(w)
         frontier = np.array(sorted(set(nxt)), np.int64)
+    return dist
+
+
+def diffuse(dx: np.ndarray, E: np.ndarray, rings: int, sweeps: int = 0,
+            fixed: Optional[np.ndarray] = None) -> np.ndarray:
+    """Spreads the displacement of the vertices the minimizer moved over
+    their vicinity as a harmonic vector field (Sec. 5 names constrained
+    diffusion to a harmonic field and gives no equations; this is the
+    reading used here).  On the mesh graph (vertices, edges E):
+
+      * the moved vertices (nonzero dx) keep their displacement: Dirichlet
+        values;
+      * the band = the vertices 1 .. `rings` edges from the nearest moved
+        vertex, except `fixed` (kinematic) ones: the unknowns;
+      * every other vertex is held at zero: Dirichlet values too.
+
+    sweeps == 0: the harmonic field itself, i.e. each band vertex equals
+    the mean of its neighbours: deg(v) u_v - sum of u_w over the band
+    neighbours w = sum of the Dirichlet values of its other neighbours,
+    one sparse linear system per coordinate (the graph Laplacian of the
+    band), solved directly.  Every band vertex is joined to a Dirichlet
+    vertex by a path of band vertices (its ring number falls along a
+    shortest path to the moved set), so the system is positive definite.
+
+    sweeps > 0: the named approximation instead: `sweeps` Jacobi sweeps of
+    the neighbour mean over the band, starting from zero (the harmonic
+    field is their limit).  dx: [n, 3]."""
+    n = dx.shape[0]
+    C = np.any(dx != 0.0, axis=1)
+    if rings <= 0 or not C.any():
+        return dx.copy()
+    indptr, nbr = vertex_adjacency(E, n)
+    deg = np.diff(indptr)
+    dist = ring_distance(C, indptr, nbr, rings)
     free = (dist >= 1) & (dist <= rings)
     if fixed is not None:
         free &= ~np.asarray(fixed, bool)
     u = np.where(C[:, None], dx, 0.0)
     fv = np.nonzero(free)[0]
-    for _ in range(sweeps):
-        new = u.copy()
-        for v in fv:
-            acc = np.zeros(3)
-            for w in nbr[indptr[v]:indptr[v + 1]]:
-                acc += u[w]
-            new[v] = acc / deg[v]
-        u = new
+    if sweeps > 0:
+        for _ in range(sweeps):
+            new = u.copy()
+            for v in fv:
+                acc = np.zeros(3)
+                for w in nbr[indptr[v]:indptr[v + 1]]:
+                    acc += u[w]
+                new[v] = acc / deg[v]
+            u = new
+        return u
+    if len(fv) == 0:
+        return u
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+    col = np.full(n, -1, np.int64)
+    col[fv] = np.arange(len(fv))
+    rows, cols, vals = [], [], []
+    rhs = np.zeros((len(fv), 3))
+    for i, v in enumerate(fv):
+        rows.append(i)
+        cols.append(i)
+        vals.append(float(deg[v]))
+        for w in nbr[indptr[v]:indptr[v + 1]]:
+            if free[w]:
+                rows.append(i)
+                cols.append(col[w])
+                vals.append(-1.0)
+            else:
+                rhs[i] += u[w]       # Dirichlet neighbour (moved: dx, else 0)
+    L = sp.csc_matrix((vals, (rows, cols)), shape=(len(fv), len(fv)))
+    for c in range(3):
+        u[fv, c] = sla.spsolve(L, rhs[:, c])
     return u
 
 
@@ -486,9 +532,10 @@ def resolve(PA, TA, orientedA, PB, TB, orientedB, d: float = 1e-4, max_iters: in
     when the most recent detections covering every active direction found
     no pair, or after `max_iters` detections.  Positions are rounded to
     `store_dtype` after each displacement (the storage type of the scene).
-    With diffuse_rings and diffuse_sweeps > 0, each mesh's displacement is
-    spread by `diffuse` (Sec. 5) before it is applied; vertices of inverse
-    mass 0 are held fixed."""
+    With diffuse_rings > 0, each mesh's displacement is spread by `diffuse`
+    (Sec. 5) before it is applied: the harmonic field when diffuse_sweeps is
+    0, else that many Jacobi sweeps; vertices of inverse mass 0 are held
+    fixed."""
     if mode not in ("alternate", "both"):
         raise ValueError(mode)
     PA = np.asarray(PA, np.float64).astype(store_dtype).astype(np.float64)
@@ -513,7 +560,7 @@ def resolve(PA, TA, orientedA, PB, TB, orientedB, d: float = 1e-4, max_iters: in
         st = stencils(pr)
         sc.append(len(st))
         dA, dB, _, _ = respond(st, PA, TA, PB, TB, d, inv_mass)
-        if diffuse_rings > 0 and diffuse_sweeps > 0:
+        if diffuse_rings > 0:
             nA = PA.shape[0]
             fx = None if inv_mass is None else np.asarray(inv_mass) == 0.0
             dA = diffuse(dA, EA, diffuse_rings, diffuse_sweeps, None if fx is None else fx[:nA])
