@@ -1,26 +1,30 @@
 #!/usr/bin/env python
 """DCD + response ms/frame and E-F tests/s on one GB300.
 
-Workload (default): un-oriented cloth, 200 x 200 vertices (119,201 edges,
-79,202 faces, side 2.0, seeded sinusoidal heights of amplitude 0.3) draped
-into an oriented torus (256 x 128 quads = 65,536 faces, R 1.0, r 0.4),
-float32 positions, about 2,200 E-F intersections.  One frame = one pass of
-the whole path: exact E-F detection (BVH build, refit, traversal, exact
-narrow phase), pair sort, stencils, constraint assembly, the Eq. 8 solve and
-the displacement of the stencil vertices, starting from the same initial
-positions every frame (restored inside the timed region).
+Workload (default): the frame sequence.  An un-oriented float32 cloth of
+512 x 512 vertices (784,385 edges, side 3.0) falls onto an oriented closed
+body: an icosphere of level 7 (327,680 faces) whose radius carries
+seeded spherical-harmonic noise.  Every frame, a seeded smooth velocity
+field moves the cloth; then one DCD response runs: one repair iteration of
+exact E-F detection (BVH build and refit, traversal, exact narrow phase),
+stencils, constraint assembly, the Eq. 8 solve, and the harmonic diffusion
+of the displacement (Sec. 5), replayed as a CUDA graph.  This is one DCD
+response per output frame, the paper's own use (Sec. 6, third experiment).
+A step is the whole 300-frame sequence from the initial state.
 
-Printed: one JSON line (rank 0).  `value` is ms per frame (lower is
-better); E-F tests/s is reported beside it, brute-force equivalent
-(|E| x |F| per frame over the frame time) and executed narrow-phase tests.
-`--impl reference` times the CPU oracle on the same frame instead.
+Printed: one JSON line (rank 0).  `value` is ms per frame over all timed
+frames (lower is better), with p50 / p99 beside it.  E-F tests/s is
+reported both as brute-force equivalent (|E| x |F| per frame over the
+frame time) and as executed narrow-phase tests.  The other configurations
+are extra keys: the cloth / torus frame, the two tori (precision form and
+d-sweep), the two small spheres, and the 1,024-pair batch.
+`--impl reference` times the CPU oracle on the same workload instead.
 """
 from __future__ import annotations
 
 import argparse
 import csv
 import hashlib
-import io
 import json
 import os
 import statistics
@@ -34,21 +38,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DCD+response ms/frame and E-F tests/s on 1 GB300 vs plain FP64 GPU form"
 D_POST = 1e-4
+RINGS = 4          # diffusion band of the frame sequence (Sec. 5)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20, help="timed 300-frame sequences")
+    ap.add_argument("--warmup", type=int, default=5, help="untimed 300-frame sequences")
+    ap.add_argument("--frames", type=int, default=300, help="frames per sequence")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="reference arm: seconds of oracle work for warmup + steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64-form", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the 1,024-pair batched workload")
-    ap.add_argument("--no-c3", action="store_true",
-                    help="skip the two-spheres and two-tori sections (precision form, d-sweep)")
-    ap.add_argument("--frames", type=int, default=300,
-                    help="frames of the cloth-over-body sequence (0 to skip)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the lockstep pass of the float64 and graph-less forms")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the cloth/torus, two-tori, two-spheres and batch sections")
+    ap.add_argument("--frame-log", default=None, help="write a per-frame CSV of the last timed sequence")
     return ap.parse_args()
 
 
@@ -76,7 +83,7 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -116,8 +123,14 @@ def measured_peak_hbm():
     return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = {"k_traverse": ("detect.cu", "predicates.cuh"), "k_cg_zone_pair": ("solve.cu",)}
-PROFILES = {"k_traverse": "k_traverse_cloth_torus.md", "k_cg_zone_pair": "k_cg_zone_pair_cloth_torus.md"}
+# kernel -> (source files whose code lines it depends on, its ncu summary)
+KERNELS = {
+    "k_traverse": (("detect.cu", "predicates.cuh"), "k_traverse_frame_sequence.md"),
+    "k_traverse_batch": (("detect.cu", "predicates.cuh"), "k_traverse_batch.md"),
+    "k_band_cg": (("diffuse.cu",), "k_band_cg_frame_sequence.md"),
+    "k_cg_zone_pair": (("solve.cu",), "k_cg_zone_pair_cloth_torus.md"),
+    "k_refit": (("bvh.cu",), "k_refit_frame_sequence.md"),
+}
 
 
 def kernel_source_hash(kernel: str = "k_traverse") -> str:
@@ -125,7 +138,7 @@ def kernel_source_hash(kernel: str = "k_traverse") -> str:
     lines only (lines that are blank or hold only a // comment are left out,
     so a comment edit keeps a profile valid)."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES[kernel]:
+    for f in KERNELS[kernel][0]:
         for line in open(os.path.join(ROOT, "paper_1409_2081_gb300", "csrc", f), "rb"):
             t = line.strip()
             if t and not t.startswith(b"//"):
@@ -133,10 +146,10 @@ def kernel_source_hash(kernel: str = "k_traverse") -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str = "k_traverse"):
+def profiled_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, if
     the summary was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", PROFILES[kernel])
+    path = os.path.join(ROOT, "profiles", KERNELS[kernel][1])
     if not os.path.exists(path):
         return None
     vals = {}
@@ -154,9 +167,9 @@ def profiled_traffic(kernel: str = "k_traverse"):
 
 def whole_job(local_total_ms: float, steps: int, dist=None, device=None):
     """Replicas only: every rank runs the same workload on its own GPU; the
-    job's time is the slowest rank's, and the whole-job ms per frame is
-    that time over all frames of all ranks.  Returns (max total ms, ms per
-    frame)."""
+    job's time is the slowest rank's, and the whole-job ms per unit (frame)
+    is that time over all units of all ranks.  Returns (max total ms, ms
+    per unit)."""
     ws = 1
     t = local_total_ms
     if dist is not None and dist.is_initialized():
@@ -180,117 +193,325 @@ def packed(torch, xs):
     return pos, pos.clone(), views
 
 
-def scene():
-    import meshgen
-    return meshgen.scene_c2()
+def pct(xs, q):
+    s = sorted(xs)
+    return s[min(len(s) - 1, int(q * len(s)))] if s else None
 
 
-def cpu_oracle_frame(sc, edge_fraction=1.0):
-    """One frame on the CPU oracle (detection over a fraction of the cloth
-    edges, then stencils and the float64 solve of what was found); returns
-    (seconds, cores, scaled seconds per full frame)."""
+# ---------------------------------------------------------------------------
+# the frame sequence (headline workload)
+# ---------------------------------------------------------------------------
+
+class Sequence:
+    """The cloth-over-body frame sequence on the device: both meshes'
+    coordinates in one packed buffer (restore / upload / download in one
+    copy), the cloth's edge list built once, a context with the harmonic
+    diffusion of Sec. 5 over RINGS rings."""
+
+    def __init__(self, api, torch, dev, sc, dtype, **ctx_kw):
+        import numpy as np
+        self.api, self.torch, self.sc = api, torch, sc
+        tdt = torch.float32 if dtype == np.float32 else torch.float64
+        xyz = [torch.tensor(np.ascontiguousarray(m.V.astype(np.float32).astype(dtype)[:, c]), dtype=tdt,
+                            device=dev) for m in (sc.A, sc.B) for c in range(3)]
+        self.pos, self.pos0, v = packed(torch, xyz)
+        self.ctx = api.Context(diffuse_rings=RINGS, **ctx_kw)
+        self.ctx.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), 1 << 18)
+        ta, tb = torch.tensor(sc.A.T, device=dev), torch.tensor(sc.B.T, device=dev)
+        # topology preparation (once per mesh): both edge lists, so that the
+        # diffusion's vertex adjacency is built once and kept
+        ea = torch.zeros((3 * sc.A.n_tris, 2), dtype=torch.int32, device=dev)
+        ea = ea[:self.ctx.hfcr_build_edges(ta, sc.A.n_verts, ea)].contiguous()
+        eb = torch.zeros((3 * sc.B.n_tris, 2), dtype=torch.int32, device=dev)
+        eb = eb[:self.ctx.hfcr_build_edges(tb, sc.B.n_verts, eb)].contiguous()
+        self.A = api.Mesh(*v[:3], ta, False, edges=ea)
+        self.B = api.Mesh(*v[3:], tb, True, edges=eb)
+        self.ne = int(ea.shape[0])
+        self.motion = sc.meta["motion"]
+        self.params = self.motion.device_params(torch, dev)
+
+    def restore(self):
+        self.pos.copy_(self.pos0, non_blocking=True)
+
+    def advance(self, f):
+        self.motion.advance(self.torch, self.params, self.A.x, self.A.y, self.A.z, f)
+
+    def load_from(self, other):
+        self.pos.copy_(other.pos, non_blocking=True)   # widened when self is float64
+
+    def resolve(self):
+        return self.ctx.hfcr_resolve(self.A, self.B, D_POST, 1)
+
+    def positions(self):
+        import numpy as np
+        P = self.pos.double().cpu().numpy()
+        nA, nB = self.sc.A.n_verts, self.sc.B.n_verts
+        return (np.stack([P[0:nA], P[nA:2 * nA], P[2 * nA:3 * nA]], 1),
+                np.stack([P[3 * nA + i * nB:3 * nA + (i + 1) * nB] for i in range(3)], 1))
+
+    def close(self):
+        self.ctx.close()
+
+
+def run_sequences(seq, torch, stream, flush, n_seq, n_frames, keep=None, on_frame=None):
+    """n_seq passes of the whole sequence from the initial state; each
+    frame's response timed with CUDA events on the launching stream, the L2
+    flushed (256 MB write) before it, outside the timed interval.  Returns
+    (per-frame ms of all passes, infos of the last pass)."""
+    ms, infos = [], []
+    for k in range(n_seq):
+        seq.restore()
+        evs = []
+        last = []
+        for f in range(n_frames):
+            seq.advance(f)
+            if keep is not None and k == n_seq - 1 and f in keep:
+                keep[f] = seq.positions()
+            flush.fill_(float(f))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = seq.resolve()
+            e1.record(stream)
+            evs.append((e0, e1))
+            last.append(info)
+            if on_frame is not None:
+                on_frame(f)
+        torch.cuda.synchronize()
+        ms.extend(a.elapsed_time(b) for a, b in evs)
+        infos = last
+    return ms, infos
+
+
+def frame_stats(infos):
+    import numpy as np
+    pairs = np.array([int(i.pairs_first) for i in infos])
+    contact = np.nonzero(pairs > 0)[0]
+    return {"first_contact_frame": int(contact[0]) if len(contact) else None,
+            "contact_frames": int(len(contact)),
+            "pairs_last_frame": int(pairs[-1]) if len(pairs) else 0,
+            "max_pairs": int(pairs.max()) if len(pairs) else 0,
+            "mean_pairs_contact_frames": round(float(pairs[contact].mean()), 1) if len(contact) else 0.0}
+
+
+def lockstep_forms(api, torch, dev, sc, stream, flush, n_frames, drv):
+    """The same frames through four forms: each frame the driver (mixed
+    precision, graphs) moves the cloth; the float32 form without graphs,
+    the plain float64 form (float64 positions = exact widening, float64
+    filter -> exact, float64 CG per impact zone, plain launches) and the
+    float64 form with one CTA's global CG load the driver's positions and
+    run their response (timed, result discarded); then the driver runs its
+    own (timed).  Splits the mixed form's gain into precision, solver
+    structure and graph replay."""
+    import numpy as np
+    forms = {
+        "mixed_no_graphs": Sequence(api, torch, dev, sc, np.float32, graphs=False),
+        "fp64_per_zone": Sequence(api, torch, dev, sc, np.float64, solver=api.HFCR_SOLVER_FP64,
+                                  f32_filter=False, graphs=False),
+        "fp64_global_cg": Sequence(api, torch, dev, sc, np.float64,
+                                   solver=api.HFCR_SOLVER_FP64_GLOBAL, f32_filter=False, graphs=False),
+    }
+    times = {k: [] for k in forms}
+    times["mixed_graphs"] = []
+    agree = {k: 0 for k in forms}
+    drv.restore()
+    for f in range(n_frames):
+        drv.advance(f)
+        for name, s in forms.items():
+            s.load_from(drv)
+            flush.fill_(float(f))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            inf = s.resolve()
+            e1.record(stream)
+            e1.synchronize()
+            times[name].append(e0.elapsed_time(e1))
+            agree[name] += int(inf.pairs_first)
+        flush.fill_(float(f))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inf = drv.resolve()
+        e1.record(stream)
+        e1.synchronize()
+        times["mixed_graphs"].append(e0.elapsed_time(e1))
+        for name in forms:
+            agree[name] -= int(inf.pairs_first)
+    for s in forms.values():
+        s.close()
+    mean = {k: statistics.mean(v) for k, v in times.items()}
+    out = {k: {"ms_per_frame": round(mean[k], 4), "ms_p50": round(pct(times[k], 0.5), 4),
+               "ms_p99": round(pct(times[k], 0.99), 4)} for k in times}
+    out["fp64_per_zone"]["solver"] = "float64 CG per impact zone (one thread group per zone), float64 filter -> exact"
+    out["fp64_global_cg"]["solver"] = "float64 CG of the whole system in one 1,024-thread CTA"
+    out["pair_counts_identical"] = all(v == 0 for v in agree.values())
+    out["factors"] = {
+        "precision (fp64_per_zone / mixed_no_graphs)": round(mean["fp64_per_zone"] / mean["mixed_no_graphs"], 3),
+        "solver structure (fp64_global_cg / fp64_per_zone)": round(mean["fp64_global_cg"] / mean["fp64_per_zone"], 3),
+        "graph replay (mixed_no_graphs / mixed_graphs)": round(mean["mixed_no_graphs"] / mean["mixed_graphs"], 3),
+        "plain fp64 form / headline (fp64_per_zone / mixed_graphs)": round(mean["fp64_per_zone"] / mean["mixed_graphs"], 3),
+    }
+    return out
+
+
+def e2e_sequences(seq, torch, stream, n_seq, n_frames):
+    """End to end through the C ABI with host buffers: every frame the
+    cloth moves on the device (the simulator's state, untimed) and is read
+    into a pinned host buffer; then, timed: the host -> device copy of both
+    meshes' coordinates, the response, and the device -> host copy of the
+    result."""
+    host_in = torch.empty_like(seq.pos, device="cpu").pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    ms = []
+    for _ in range(n_seq):
+        seq.restore()
+        for f in range(n_frames):
+            seq.advance(f)
+            host_in.copy_(seq.pos)           # synchronous: the state is on the host
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            seq.pos.copy_(host_in, non_blocking=True)
+            seq.resolve()
+            host_out.copy_(seq.pos, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    return ms, host_in.numel() * host_in.element_size()
+
+
+def oracle_frame(PA, TA, PB, TB, E, frac, offset=0):
+    """The oracle on one frame of the cloth / body: brute-force exact
+    detection of a stride sample of the cloth's edges against every body
+    face, then stencils and the float64 response of what was found; both
+    times scaled by 1 / frac to the whole edge list.  Returns (scaled
+    seconds, seconds spent)."""
     import numpy as np
     import oracle
-    PA, PB = sc.positions("A"), sc.positions("B")
-    E = oracle.edges(sc.A.T)
-    m = max(1, int(round(len(E) * edge_fraction)))
-    sub = E if m >= len(E) else E[np.linspace(0, len(E) - 1, m).astype(np.int64)]
+    step = max(1, int(round(1.0 / frac)))
+    idx = np.arange(offset % step, len(E), step)
+    sub = E[idx]
     t0 = time.perf_counter()
-    hits = oracle.detect_one_direction(PA, sub, PB, sc.B.T)
+    hits = oracle.detect_one_direction(PA, sub, PB, TB)
+    t1 = time.perf_counter()
+    if len(hits):
+        rec = np.zeros((len(hits), 4), np.uint32)
+        rec[:, 1] = sub[hits[:, 0], 0]
+        rec[:, 2] = sub[hits[:, 0], 1]
+        rec[:, 3] = hits[:, 1]
+        st = oracle.stencils(oracle.Pairs(rec, hits[:, 2].astype(np.int8)))
+        dA, dB, _, _ = oracle.respond(st, PA, TA, PB, TB, D_POST)
+        oracle.diffuse(dA, E, RINGS)
+    t2 = time.perf_counter()
+    f = len(idx) / len(E)
+    return (t2 - t0) / f, t2 - t0
+
+
+# ---------------------------------------------------------------------------
+# the other configurations (extra keys)
+# ---------------------------------------------------------------------------
+
+def cloth_torus(api, torch, dev, stream, flush, steps, warmup, timed, cpu=True):
+    """Cloth 200 x 200 (119,201 edges) draped into an oriented torus
+    (65,536 faces), float32: one frame = one repair iteration from the
+    initial positions (restored inside the timed region), graph-replayed;
+    its stage profile, the rooflines of the traversal and of the per-zone
+    solver, and the oracle on the same frame."""
+    import numpy as np
+    import meshgen
+    sc = meshgen.scene_c2()
+    xyz = [torch.tensor(np.ascontiguousarray(m.V.astype(np.float32)[:, c]), device=dev)
+           for m in (sc.A, sc.B) for c in range(3)]
+    pos, pos0, v = packed(torch, xyz)
+    ctx = api.Context()
+    ctx.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), 1 << 16)
+    ta, tb = torch.tensor(sc.A.T, device=dev), torch.tensor(sc.B.T, device=dev)
+    ea = torch.zeros((3 * sc.A.n_tris, 2), dtype=torch.int32, device=dev)
+    ne = ctx.hfcr_build_edges(ta, sc.A.n_verts, ea)
+    ea = ea[:ne].contiguous()
+    A = api.Mesh(*v[:3], ta, False, edges=ea)
+    B = api.Mesh(*v[3:], tb, True)
+
+    def frame():
+        pos.copy_(pos0, non_blocking=True)
+        return ctx.hfcr_resolve(A, B, D_POST, 1)
+
+    variant, variant_ms = ctx.hfcr_autotune(A, B)
+    ctx.hfcr_profile_enable(True)
+    timed(frame, max(5, steps), 2)
+    prof = ctx.hfcr_profile_read()
+    ctx.hfcr_profile_enable(False)
+    ms, infos = timed(frame, steps, warmup)
+    info = infos[-1]
+    n_prof = max(1, prof["traverse"][1])
+    stage_ms = {k: round(val[0] / n_prof, 4) for k, val in prof.items()}
+    P = int(info.pairs_first)
+    peak, kind = measured_peak_hbm()
+    trav_ms = prof["traverse"][0] / max(1, prof["traverse"][1])
+    alg_trav = sc.A.n_verts * 12 + ne * 8 + sc.B.n_verts * 12 + sc.B.n_tris * 12 + P * 8
+    # stencils and touched vertices of this frame's system (outside the timed regions)
+    pos.copy_(pos0)
+    cap = max(1 << 10, 2 * P)
+    pbuf = torch.zeros((cap, 4), dtype=torch.int32, device=dev)
+    n_p = ctx.hfcr_detect(A, B, pbuf)
+    sbuf = torch.zeros((cap, 4), dtype=torch.int32, device=dev)
+    k_st = ctx.hfcr_build_stencils(A, B, pbuf, n_p, sbuf)
+    dxa = [torch.zeros(sc.A.n_verts, device=dev) for _ in range(3)]
+    dxb = [torch.zeros(sc.B.n_verts, device=dev) for _ in range(3)]
+    si = ctx.hfcr_respond(A, B, sbuf, k_st, D_POST, dxa, dxb)
+    solve_ms = prof["solve"][0] / max(1, prof["solve"][1])
+    # per stencil: ids 16 + float32 normal 16 + preconditioner row 16 + b 8 + float64
+    # normal 32 + lam 8 (written) + 4 vertex-CSR entries 16 + group start 4; per
+    # touched vertex: CSR offset 4 + inverse mass 4
+    alg_cg = 116 * k_st + 8 * int(si.n_touched)
+    out = {"workload": "cloth 200x200 (119,201 edges) vs torus 256x128 (65,536 faces), float32, one "
+                       "repair iteration from the initial positions (restored inside the timed region)",
+           "ms_per_frame": round(statistics.mean(ms), 4), "ms_p50": round(pct(ms, 0.5), 4),
+           "ms_p99": round(pct(ms, 0.99), 4), "pairs": P, "stencils": int(info.total_stencils),
+           "ef_tests_per_s_bruteforce": round(info.stats.brute_force_equiv / (statistics.mean(ms) / 1e3), 1),
+           "stage_ms_per_frame": stage_ms, "traverse_variant": variant, "variant_ms": variant_ms,
+           "rooflines": {
+               "k_traverse": {"bound": "hbm", "achieved": round(alg_trav / (trav_ms * 1e-3) / 1e9, 2),
+                              "peak": peak, "peak_kind": kind, "unit": "GB/s",
+                              "frac": round(alg_trav / (trav_ms * 1e-3) / 1e9 / peak, 6),
+                              "alg_bytes_per_launch": alg_trav, "avg_launch_ms": round(trav_ms, 5)},
+               "k_cg_zone_pair": {"bound": "hbm", "achieved": round(alg_cg / (solve_ms * 1e-3) / 1e9, 3),
+                                  "peak": peak, "peak_kind": kind, "unit": "GB/s",
+                                  "frac": round(alg_cg / (solve_ms * 1e-3) / 1e9 / peak, 7),
+                                  "traffic": profiled_traffic("k_cg_zone_pair"),
+                                  "alg_bytes_per_launch": alg_cg, "avg_launch_ms": round(solve_ms, 5),
+                                  "stencils": k_st, "touched_vertices": int(si.n_touched)}}}
+    ctx.close()
+    if cpu:
+        import oracle
+        PA, PB = sc.positions("A"), sc.positions("B")
+        scaled, _ = oracle_frame_generic(PA, sc.A.T, PB, sc.B.T, oracle.edges(sc.A.T), 1.0)
+        out["cpu_baseline"] = {"value": round(scaled * 1e3, 2), "unit": "ms/frame",
+                               "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": "one whole frame: brute-force exact detection of all 119,201 "
+                                         "cloth edges against all 65,536 torus faces, stencils, float64 "
+                                         "per-zone solve"}
+    return out
+
+
+def oracle_frame_generic(PA, TA, PB, TB, E, frac):
+    import numpy as np
+    import oracle
+    step = max(1, int(round(1.0 / frac)))
+    sub = E[::step]
+    t0 = time.perf_counter()
+    hits = oracle.detect_one_direction(PA, sub, PB, TB)
     t1 = time.perf_counter()
     rec = np.zeros((len(hits), 4), np.uint32)
     rec[:, 1] = sub[hits[:, 0], 0]
     rec[:, 2] = sub[hits[:, 0], 1]
     rec[:, 3] = hits[:, 1]
     st = oracle.stencils(oracle.Pairs(rec, hits[:, 2].astype(np.int8)))
-    oracle.respond(st, PA, sc.A.T, PB, sc.B.T, D_POST)
+    oracle.respond(st, PA, TA, PB, TB, D_POST)
     t2 = time.perf_counter()
-    frac = len(sub) / len(E)
-    return (t2 - t0), oracle.num_threads(), (t1 - t0) / frac + (t2 - t1)
+    f = len(sub) / len(E)
+    return (t1 - t0) / f + (t2 - t1), t2 - t0
 
 
-def frame_sequence(api, torch, dev, n_frames, max_iters=1, rings=4, sweeps=16, body_inv_mass=1.0,
-                   time_budget_s=45.0):
-    """Cloth 512 x 512 (side 3.0, float32, un-oriented) falling onto an
-    oriented body (icosphere level 7 with spherical-harmonic radius noise of
-    amplitude 0.1): each frame moves the cloth by the seeded velocity field
-    (torch ops on the device, outside the timed region), then resolve is
-    timed: max_iters repair iterations (default one DCD response per frame,
-    the paper's use in its animation, Sec. 6), graph-replayed, with the
-    diffusion of Sec. 5 over `rings` rings and `sweeps` sweeps.  The
-    prescribed drift pushes the resting cloth into the body every frame, so
-    contact frames keep a few thousand fresh pairs for the next response; a
-    run whose frames blow up stops at `time_budget_s` and reports the frames
-    it completed."""
-    import time
-    import numpy as np
-    import meshgen
-    sc = meshgen.scene_c5()
-    mot = sc.meta["motion"]
-    ctx = api.Context(diffuse_rings=rings, diffuse_sweeps=sweeps)
-    cap = 1 << 18
-    ctx.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), cap)
-
-    def dev_xyz(V):
-        P = V.astype(np.float32)
-        return [torch.tensor(np.ascontiguousarray(P[:, c]), device=dev) for c in range(3)]
-
-    xa, xb = dev_xyz(sc.A.V), dev_xyz(sc.B.V)
-    ta, tb = torch.tensor(sc.A.T, device=dev), torch.tensor(sc.B.T, device=dev)
-    ea = torch.zeros((3 * sc.A.n_tris, 2), dtype=torch.int32, device=dev)
-    ea = ea[:ctx.hfcr_build_edges(ta, sc.A.n_verts, ea)].contiguous()
-    A = api.Mesh(*xa, ta, False, edges=ea)
-    wb = None if body_inv_mass == 1.0 else torch.full((sc.B.n_verts,), body_inv_mass,
-                                                      dtype=torch.float32, device=dev)
-    B = api.Mesh(*xb, tb, True, inv_mass=wb)
-    K = torch.tensor(mot.k.T, dtype=torch.float32, device=dev)
-    W = torch.tensor(mot.w, dtype=torch.float32, device=dev)
-    PH = torch.tensor(mot.ph, dtype=torch.float32, device=dev)
-    AD = torch.tensor((mot.amp[:, None] * mot.dir) * (0.5 * mot.v0), dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-    ms, pairs, iters = [], [], []
-    stop, t_start = "all frames", time.time()
-    for f in range(n_frames):
-        X = torch.stack([A.x, A.y, A.z], 1)
-        V = torch.sin(X @ K + W * f + PH) @ AD
-        V[:, 2] -= mot.v0
-        X += V
-        A.x.copy_(X[:, 0]); A.y.copy_(X[:, 1]); A.z.copy_(X[:, 2])
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        try:
-            info = ctx.hfcr_resolve(A, B, D_POST, max_iters)
-        except api.HfcrError as e:
-            stop = f"frame {f}: {e}"[:120]
-            break
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        pairs.append(int(info.pairs_first))
-        iters.append(int(info.iters))
-        if time.time() - t_start > time_budget_s:
-            stop = f"time budget {time_budget_s:.0f} s after frame {f}"
-            break
-    ctx.close()
-    contact = [i for i, p in enumerate(pairs) if p > 0]
-    srt = sorted(ms)
-    cms = sorted(ms[i] for i in contact)
-    return {"workload": "cloth 512x512 (784,385 edges) falling on SH body (icosphere L7, 327,680 faces), "
-                        "float32, one resolve (<= %d iterations, diffusion R=%d S=%d, body inverse "
-                        "mass %g) per frame" % (max_iters, rings, sweeps, body_inv_mass),
-            "frames_requested": n_frames, "frames_completed": len(ms), "stopped": stop,
-            "ms_p50": round(statistics.median(ms), 4) if ms else None,
-            "ms_p99": round(srt[min(len(srt) - 1, int(0.99 * len(srt)))], 4) if ms else None,
-            "first_contact_frame": contact[0] if contact else None,
-            "contact_frames": len(contact),
-            "contact_ms_p50": round(statistics.median(cms), 4) if cms else None,
-            "contact_ms_p99": round(cms[min(len(cms) - 1, int(0.99 * len(cms)))], 4) if cms else None,
-            "pairs_last_frame": pairs[-1] if pairs else 0,
-            "max_pairs": max(pairs) if pairs else 0,
-            "mean_iters": round(statistics.mean(iters), 2) if iters else None}
-
-
-def batched(api, torch, dev, steps, warmup, timed_fn):
+def batched(api, torch, dev, steps, warmup, timed, cpu=True):
     """1,024 independent pairs of oriented icospheres (levels 1..5, 80 to
     20,480 faces each, random rotation, centre distance U(0.5, 1.8) radii),
     float32, concatenated into two meshes with a segment table.  A step is
@@ -299,21 +520,18 @@ def batched(api, torch, dev, steps, warmup, timed_fn):
     all pairs, stencils, zones, solve, displacement)."""
     import numpy as np
     import meshgen
-    VA, TA, VB, TB, segs = meshgen.concat_batch(meshgen.scene_c4())
+    scenes = meshgen.scene_c4()
+    VA, TA, VB, TB, segs = meshgen.concat_batch(scenes)
     ctx = api.Context()
     ctx.hfcr_reserve(max(len(VA), len(VB)), max(len(TA), len(TB)), 1 << 21)
-
-    def xyz(V):
-        P = V.astype(np.float32)
-        return [torch.tensor(np.ascontiguousarray(P[:, c]), device=dev) for c in range(3)]
-
-    xa, xb = xyz(VA), xyz(VB)
+    xyz = [torch.tensor(np.ascontiguousarray(V.astype(np.float32)[:, c]), device=dev)
+           for V in (VA, VB) for c in range(3)]
     ta, tb = torch.tensor(TA, device=dev), torch.tensor(TB, device=dev)
     ea = torch.zeros((3 * len(TA), 2), dtype=torch.int32, device=dev)
     ea = ea[:ctx.hfcr_build_edges(ta, len(VA), ea)].contiguous()
     eb = torch.zeros((3 * len(TB), 2), dtype=torch.int32, device=dev)
     eb = eb[:ctx.hfcr_build_edges(tb, len(VB), eb)].contiguous()
-    pos, pos0, v = packed(torch, xa + xb)
+    pos, pos0, v = packed(torch, xyz)
     A = api.Mesh(*v[:3], ta, True, edges=ea)
     B = api.Mesh(*v[3:], tb, True, edges=eb)
     dsegs = torch.tensor(segs, device=dev)
@@ -323,13 +541,11 @@ def batched(api, torch, dev, steps, warmup, timed_fn):
         return ctx.hfcr_resolve_batch(A, B, dsegs, D_POST, 1)
 
     variant, variant_ms = ctx.hfcr_autotune(A, B, dsegs)
-    for _ in range(warmup):
-        step()
     ctx.hfcr_profile_enable(True)
-    timed_fn(step, max(3, steps // 4), 1)
+    timed(step, max(3, steps // 2), 1)
     prof = ctx.hfcr_profile_read()
     ctx.hfcr_profile_enable(False)
-    ms, infos = timed_fn(step, steps, 1)
+    ms, infos = timed(step, steps, warmup)
     info = infos[-1]
     trav_ms, trav_n = prof["traverse"]
     P = int(info.pairs_first)
@@ -337,21 +553,46 @@ def batched(api, torch, dev, steps, warmup, timed_fn):
     peak, kind = measured_peak_hbm()
     ach = alg / (trav_ms / max(1, trav_n) * 1e-3) / 1e9
     ctx.close()
-    n_frames = max(1, prof["traverse"][1])
-    return {"workload": "1,024 pairs of icospheres L1..5 (A: %d faces, B: %d faces), float32, "
-                        "one batched repair iteration" % (len(TA), len(TB)),
-            "ms_per_step": round(statistics.mean(ms), 4), "ms_p50": round(statistics.median(ms), 4),
-            "pairs": P, "stencils": int(info.total_stencils),
-            "ef_tests_per_s_bruteforce": round(info.stats.brute_force_equiv / (statistics.mean(ms) / 1e3), 1),
-            "stage_ms_per_step": {k: round(v[0] / n_frames, 4) for k, v in prof.items()},
-            "roofline": {"kernel": "k_traverse", "bound": "hbm", "achieved": round(ach, 2),
-                         "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": round(ach / peak, 5),
-                         "alg_bytes_per_launch": alg,
-                         "avg_launch_ms": round(trav_ms / max(1, trav_n), 5),
-                         "traverse_variant": variant, "variant_ms": variant_ms}}
+    n_it = max(1, prof["traverse"][1])
+    out = {"workload": "1,024 pairs of icospheres L1..5 (A: %d faces, B: %d faces), float32, "
+                       "one batched repair iteration" % (len(TA), len(TB)),
+           "ms_per_step": round(statistics.mean(ms), 4), "ms_p50": round(pct(ms, 0.5), 4),
+           "pairs": P, "stencils": int(info.total_stencils),
+           "ef_tests_per_s_bruteforce": round(info.stats.brute_force_equiv / (statistics.mean(ms) / 1e3), 1),
+           "stage_ms_per_step": {k: round(val[0] / n_it, 4) for k, val in prof.items()},
+           "roofline": {"kernel": "k_traverse", "bound": "hbm", "achieved": round(ach, 2),
+                        "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": round(ach / peak, 5),
+                        "traffic": profiled_traffic("k_traverse_batch"),
+                        "alg_bytes_per_launch": alg, "avg_launch_ms": round(trav_ms / max(1, trav_n), 5),
+                        "traverse_variant": variant, "variant_ms": variant_ms}}
+    if cpu:
+        # the oracle once per pair on a seeded sample of 24 pairs (direction 0,
+        # as in the timed iteration), scaled by the brute-force candidates
+        import oracle
+        rng = np.random.default_rng(7)
+        pick = rng.choice(len(scenes), 24, replace=False)
+        bf_all = sum(len(oracle.edges(s.A.T)) * s.B.n_tris for s in scenes)
+        bf_s, t_s = 0, 0.0
+        for i in pick:
+            s = scenes[i]
+            PA = s.A.V.astype(np.float32).astype(np.float64)
+            PB = s.B.V.astype(np.float32).astype(np.float64)
+            t0 = time.perf_counter()
+            pr = oracle.detect(PA, s.A.T, False, PB, s.B.T, True)
+            st = oracle.stencils(pr)
+            if len(st):
+                oracle.respond(st, PA, s.A.T, PB, s.B.T, D_POST)
+            t_s += time.perf_counter() - t0
+            bf_s += len(oracle.edges(s.A.T)) * s.B.n_tris
+        out["cpu_baseline"] = {"value": round(t_s * bf_all / bf_s * 1e3, 1), "unit": "ms/step",
+                               "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": "24 seeded pairs of the 1,024 (direction 0: detection, "
+                                         "stencils, float64 response), scaled by |E| x |F| of all "
+                                         "pairs over that of the sample"}
+    return out
 
 
-def small_form(api, torch, dev, steps, timed_fn):
+def small_form(api, torch, dev, steps, timed):
     """Two jittered level-3 icospheres offset by 1.5 (642 vertices, 1,280
     faces each), float64: one repair iteration from the initial state in
     the plain float64 form and the mixed form, and the whole repair loop
@@ -360,37 +601,29 @@ def small_form(api, torch, dev, steps, timed_fn):
     import numpy as np
     import meshgen
     sc = meshgen.scene_c1()
-
-    def mesh(ctx, m):
-        xyz = [torch.tensor(np.ascontiguousarray(m.V[:, c]), dtype=torch.float64, device=dev) for c in range(3)]
-        tris = torch.tensor(m.T, device=dev)
-        # topology preparation (once per mesh, outside the timed region)
-        e = torch.zeros((3 * m.n_tris, 2), dtype=torch.int32, device=dev)
-        e = e[:ctx.hfcr_build_edges(tris, m.n_verts, e)].contiguous()
-        return tris, e, xyz
-
     out = {"workload": "two icospheres L3 (1,280 faces each), offset 1.5, jitter 0.01, float64"}
     for name, solver, f32f, graphs in (("fp64_form", api.HFCR_SOLVER_FP64, False, False),
                                        ("mixed_form", api.HFCR_SOLVER_MIXED, True, True)):
         ctx = api.Context(solver=solver, f32_filter=f32f, graphs=graphs)
         ctx.hfcr_reserve(sc.A.n_verts, sc.A.n_tris, 1 << 14)
-        (ta, ea, a0), (tb, eb, b0) = mesh(ctx, sc.A), mesh(ctx, sc.B)
-        pos, pos0, v = packed(torch, a0 + b0)
-        A = api.Mesh(*v[:3], ta, True, edges=ea)
-        B = api.Mesh(*v[3:], tb, True, edges=eb)
+        xyz = [torch.tensor(np.ascontiguousarray(m.V[:, c]), dtype=torch.float64, device=dev)
+               for m in (sc.A, sc.B) for c in range(3)]
+        pos, pos0, v = packed(torch, xyz)
+        A = api.Mesh(*v[:3], torch.tensor(sc.A.T, device=dev), True)
+        B = api.Mesh(*v[3:], torch.tensor(sc.B.T, device=dev), True)
 
         def step():
             pos.copy_(pos0, non_blocking=True)
             return ctx.hfcr_resolve(A, B, D_POST, 1)
 
-        ms, infos = timed_fn(step, steps, 3)
+        ms, infos = timed(step, steps, 3)
         out[name] = {"us_per_iteration": round(1e3 * statistics.median(ms), 1),
                      "pairs": int(infos[-1].pairs_first)}
         if solver == api.HFCR_SOLVER_MIXED:
             def loop():
                 pos.copy_(pos0, non_blocking=True)
                 return ctx.hfcr_resolve(A, B, D_POST, 64)
-            lms, linfo = timed_fn(loop, max(3, steps // 10), 1)
+            lms, linfo = timed(loop, max(3, steps // 10), 1)
             out["repair_loop"] = {"ms": round(statistics.median(lms), 3),
                                   "detections": int(linfo[-1].iters),
                                   "converged": bool(linfo[-1].converged)}
@@ -398,98 +631,100 @@ def small_form(api, torch, dev, steps, timed_fn):
     return out
 
 
-def precision_form(api, torch, dev, steps, timed_fn, d_values=(1e-4, 1e-3, 1e-2), rings=4,
-                   sweeps=16, max_iters=32):
+def precision_form(api, torch, dev, steps, timed, d_values=(1e-4, 3e-4, 1e-3, 3e-3, 1e-2),
+                   max_iters=32):
     """Two 262,144-face tori, float32, a seeded local overlap: one repair
     iteration (float32 filter -> float64 -> exact; float32 CG + float64
     refinement) timed from the initial state; the float32 solver's
-    displacement error against the float64 GPU solver on the same stencils;
-    and the d-sweep (each d resolved with diffusion, at most max_iters
-    detections: detections run, and the signed distance D' of every
-    first-iteration stencil's x0 from its face at the final positions,
-    relative to d)."""
+    displacement error against the float64 GPU solver on the same
+    stencils; and the d-sweep (Eq. 8: each d resolved with the harmonic
+    diffusion, at most max_iters detections).  For each d, the signed
+    distance D' of every first-response stencil's x0 from its face (Eq. 1)
+    right after the first response, where Eq. 8 makes it d up to the
+    linearisation of the normals, and again at the end of the loop."""
     import numpy as np
     import meshgen
     sc = meshgen.scene_c3()
-
-    def fresh():
-        # the six coordinate arrays are views of one buffer (one restore copy);
-        # init = (buffer, its initial copy, the six initial arrays)
-        xyz = [torch.tensor(np.ascontiguousarray(m.V[:, c].astype(np.float32)), device=dev)
-               for m in (sc.A, sc.B) for c in range(3)]
-        pos, pos0, views = packed(torch, xyz)
-        A = api.Mesh(*views[:3], torch.tensor(sc.A.T, device=dev), True)
-        B = api.Mesh(*views[3:], torch.tensor(sc.B.T, device=dev), True)
-        return A, B, (pos, pos0, xyz)
-
-    def restore(A, B, init):
-        init[0].copy_(init[1], non_blocking=True)  # all six coordinate arrays
-
+    xyz = [torch.tensor(np.ascontiguousarray(m.V[:, c].astype(np.float32)), device=dev)
+           for m in (sc.A, sc.B) for c in range(3)]
+    pos, pos0, v = packed(torch, xyz)
+    A = api.Mesh(*v[:3], torch.tensor(sc.A.T, device=dev), True)
+    B = api.Mesh(*v[3:], torch.tensor(sc.B.T, device=dev), True)
     cap = 1 << 20
     ctx = api.Context()
     ctx.hfcr_reserve(sc.A.n_verts, sc.A.n_tris, cap)
-    A, B, init = fresh()
     variant, _ = ctx.hfcr_autotune(A, B)
 
     def step():
-        restore(A, B, init)
+        pos.copy_(pos0, non_blocking=True)
         return ctx.hfcr_resolve(A, B, D_POST, 1)
 
-    ms, infos = timed_fn(step, steps, 3)
+    ms, infos = timed(step, steps, 3)
     info = infos[-1]
-    # float32 CG + float64 refinement vs the float64 CG on the same stencils
-    restore(A, B, init)
+    pos.copy_(pos0)
     pairs = torch.zeros((cap, 4), dtype=torch.int32, device=dev)
     n = ctx.hfcr_detect(A, B, pairs)
     st = torch.zeros((cap, 4), dtype=torch.int32, device=dev)
     k = ctx.hfcr_build_stencils(A, B, pairs, n, st)
     ctx64 = api.Context(solver=api.HFCR_SOLVER_FP64)
     ctx64.hfcr_reserve(sc.A.n_verts, sc.A.n_tris, cap)
-    A64 = api.Mesh(*[t.double() for t in init[2][:3]], A.tris, True)
-    B64 = api.Mesh(*[t.double() for t in init[2][3:]], B.tris, True)
+    A64 = api.Mesh(*[t.double() for t in xyz[:3]], A.tris, True)
+    B64 = api.Mesh(*[t.double() for t in xyz[3:]], B.tris, True)
     dx = {}
-    for name, c, MA, MB in (("mixed", ctx, A64, B64), ("fp64", ctx64, A64, B64)):
+    for name, c in (("mixed", ctx), ("fp64", ctx64)):
         da = [torch.zeros(sc.A.n_verts, dtype=torch.float64, device=dev) for _ in range(3)]
         db = [torch.zeros(sc.B.n_verts, dtype=torch.float64, device=dev) for _ in range(3)]
-        si = c.hfcr_respond(MA, MB, st, k, D_POST, da, db)
+        si = c.hfcr_respond(A64, B64, st, k, D_POST, da, db)
         dx[name] = (torch.cat([torch.stack(da, 1), torch.stack(db, 1)]), si)
     err = float((dx["mixed"][0] - dx["fp64"][0]).abs().max() / dx["fp64"][0].abs().max())
     ctx64.close()
     ctx.close()
-    # d-sweep: repair to convergence from the initial state (the overlap is
-    # several edge lengths deep: the loop uses the diffusion of Sec. 5)
-    ctx = api.Context(diffuse_rings=rings, diffuse_sweeps=sweeps)
-    ctx.hfcr_reserve(sc.A.n_verts, sc.A.n_tris, cap)
     stn = st[:k, :3].cpu().numpy().astype(np.int64)
-    sweep = []
-    for d in d_values:
-        restore(A, B, init)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        r = ctx.hfcr_resolve(A, B, d, max_iters)
-        e1.record()
-        e1.synchronize()
+
+    def gaps(d, dirs=(0, 1)):
         PA = torch.stack([A.x, A.y, A.z], 1).double().cpu().numpy()
         PB = torch.stack([B.x, B.y, B.z], 1).double().cpu().numpy()
-        # D' of x0 against its face at the final positions (Eq. 1); dir 0:
-        # x0 in A, face in B; dir 1: the reverse
-        m0 = stn[:, 0] == 0
-        x0 = np.empty((len(stn), 3))
-        tri = np.empty((len(stn), 3, 3))
-        x0[m0], tri[m0] = PA[stn[m0, 1]], PB[sc.B.T[stn[m0, 2]]]
-        x0[~m0], tri[~m0] = PB[stn[~m0, 1]], PA[sc.A.T[stn[~m0, 2]]]
+        sel = stn[np.isin(stn[:, 0], dirs)]
+        m0 = sel[:, 0] == 0
+        x0 = np.empty((len(sel), 3))
+        tri = np.empty((len(sel), 3, 3))
+        x0[m0], tri[m0] = PA[sel[m0, 1]], PB[sc.B.T[sel[m0, 2]]]
+        x0[~m0], tri[~m0] = PB[sel[~m0, 1]], PA[sc.A.T[sel[~m0, 2]]]
         nrm = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
         ln = np.linalg.norm(nrm, axis=1)
         ok = ln > 0
-        Dp = np.einsum("ij,ij->i", nrm[ok] / ln[ok, None], x0[ok] - tri[ok].mean(axis=1))
+        Dp = np.einsum("ij,ij->i", nrm[ok] / ln[ok, None], x0[ok] - tri[ok].mean(axis=1)) / d
+        return {"min": round(float(Dp.min()), 4), "p05": round(float(np.percentile(Dp, 5)), 4),
+                "median": round(float(np.median(Dp)), 4), "p95": round(float(np.percentile(Dp, 95)), 4),
+                "max": round(float(Dp.max()), 4)}
+
+    sweep = []
+    for d in d_values:
+        # the first response alone, without diffusion (Eq. 8 on the stencils
+        # of the initial positions; roles alternate, so the first iteration
+        # responds to the direction-0 stencils)
+        c1 = api.Context()
+        c1.hfcr_reserve(sc.A.n_verts, sc.A.n_tris, cap)
+        pos.copy_(pos0)
+        c1.hfcr_resolve(A, B, d, 1)
+        first = gaps(d, (0,))
+        c1.close()
+        c2 = api.Context(diffuse_rings=RINGS)
+        c2.hfcr_reserve(sc.A.n_verts, sc.A.n_tris, cap)
+        pos.copy_(pos0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = c2.hfcr_resolve(A, B, d, max_iters)
+        e1.record()
+        e1.synchronize()
         sweep.append({"d": d, "converged": bool(r.converged), "detections": int(r.iters),
                       "pairs_first": int(r.pairs_first), "ms": round(e0.elapsed_time(e1), 3),
-                      "gap_over_d_min": round(float(Dp.min() / d), 4),
-                      "gap_over_d_median": round(float(np.median(Dp) / d), 4)})
-    ctx.close()
+                      "gap_over_d_after_first_response": first,
+                      "gap_over_d_after_loop": gaps(d)})
+        c2.close()
     return {"workload": "two tori 512x256 quads (262,144 faces each), float32, local overlap "
                         "depth U(0, 0.2 r); one repair iteration from the initial state",
-            "ms_p50": round(statistics.median(ms), 4), "ms_mean": round(statistics.mean(ms), 4),
+            "ms_p50": round(pct(ms, 0.5), 4), "ms_mean": round(statistics.mean(ms), 4),
             "pairs": int(info.pairs_first), "stencils": int(k),
             "filter": {"narrow_tests": int(info.stats.narrow_tests),
                        "f64_fallbacks": int(info.stats.f64_fallbacks),
@@ -498,42 +733,65 @@ def precision_form(api, torch, dev, steps, timed_fn, d_values=(1e-4, 1e-3, 1e-2)
             "mixed_solver": {"cg_iters": int(dx["mixed"][1].cg_iters),
                              "rel_residual": dx["mixed"][1].rel_residual},
             "traverse_variant": variant,
-            "d_sweep": {"diffusion": {"rings": rings, "sweeps": sweeps}, "max_iters": max_iters,
-                        "runs": sweep}}
+            "d_sweep": {"diffusion": {"rings": RINGS, "field": "harmonic"}, "max_iters": max_iters,
+                        "stencils": "after the first response: its direction-0 stencils; after "
+                                    "the loop: the stencils of both directions at the initial "
+                                    "positions", "runs": sweep}}
 
+
+# ---------------------------------------------------------------------------
+# the reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
 
 def run_reference(args, ws, rank):
-    """The CPU oracle as the reference arm (rank 0 only)."""
+    """The CPU oracle as the reference arm (rank 0 only), on the headline
+    workload: frame 0 of the sequence (the cloth moved once by the motion
+    field; before the first contact, so the frame is the detection alone).
+    Each step is a stride sample of the cloth edges sized so that warmup +
+    steps take about --ref-budget seconds, scaled to the whole frame."""
     if rank != 0:
         return
-    sc = scene()
-    # size each step so that warmup + steps finish within a few minutes
-    t_full, cores, _ = cpu_oracle_frame(sc, 1.0)
-    budget = 150.0
-    frac = min(1.0, budget / max(1e-9, t_full * (args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        cpu_oracle_frame(sc, frac)
+    import numpy as np
+    import meshgen
+    import oracle
+    sc = meshgen.scene_c5()
+    mot = sc.meta["motion"]
+    PA = sc.A.V.astype(np.float32)
+    PA = (PA + mot.velocity(PA.astype(np.float64), 0).astype(np.float32)).astype(np.float64)
+    PB = sc.B.V.astype(np.float32).astype(np.float64)
+    E = oracle.edges(sc.A.T)
+    # calibration on 1/500 of the edges
+    cal, spent = oracle_frame(PA, sc.A.T, PB, sc.B.T, E, 1 / 500)
+    n = max(1, args.steps + args.warmup)
+    frac = min(1.0, max(1 / 2000, args.ref_budget / n / max(1e-9, cal)))
+    for w in range(args.warmup):
+        oracle_frame(PA, sc.A.T, PB, sc.B.T, E, frac, w)
     times = []
-    for _ in range(args.steps):
-        _, _, scaled = cpu_oracle_frame(sc, frac)
+    for s in range(args.steps):
+        scaled, _ = oracle_frame(PA, sc.A.T, PB, sc.B.T, E, frac, s)
         times.append(scaled * 1e3)
     ms = statistics.mean(times)
-    bf = 119201 * 65536
-    sample = (f"{frac:.3f} of the cloth edges per step against all 65,536 torus faces, "
-              f"stencils and float64 solve of the found pairs; scaled to a full frame")
+    bf = len(E) * sc.B.n_tris
+    step = max(1, int(round(1.0 / frac)))
+    sample = (f"frame 0 of the 512x512 cloth / level-7 body sequence (before the first contact): "
+              f"brute-force exact detection of every {step}th cloth edge against all 327,680 body "
+              f"faces per step, scaled to all 784,385 edges")
     line = {"metric": METRIC, "value": round(ms, 3), "unit": "ms/frame", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "cloth 200x200 vs torus 256x128 (65,536 faces), one frame",
+            "config": {"workload": "cloth 512x512 (784,385 edges) over SH body (icosphere L7, "
+                                   "327,680 faces), float32 positions, one DCD response per frame",
                        "l2": "n/a (CPU)"},
             "ef_tests_per_s_bruteforce": bf / (ms / 1e3),
-            "cpu_baseline": {"value": round(ms, 3), "unit": "ms/frame", "cores": cores,
+            "cpu_baseline": {"value": round(ms, 3), "unit": "ms/frame", "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(ms, 3), "unit": "ms/frame", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+# ---------------------------------------------------------------------------
 
 def main():
     args = parse()
@@ -543,6 +801,7 @@ def main():
         return
     import numpy as np
     import torch
+    import meshgen
     from paper_1409_2081_gb300 import api
 
     if not torch.cuda.is_available():
@@ -557,46 +816,13 @@ def main():
     # a dedicated stream (the legacy default stream cannot be graph-captured)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
-
-    sc = scene()
-
-    def dev_mesh(m, dtype):
-        # the float64 form computes on the exact widening of the same float32 data
-        P = np.ascontiguousarray(m.V.astype(np.float32).astype(dtype))
-        tdt = torch.float32 if dtype == np.float32 else torch.float64
-        xyz = [torch.tensor(np.ascontiguousarray(P[:, c]), dtype=tdt, device=dev) for c in range(3)]
-        return xyz, torch.tensor(m.T, device=dev)
-
-    def build(dtype, solver, f32_filter, graphs=True):
-        ctx = api.Context(solver=solver, f32_filter=f32_filter, graphs=graphs)
-        ctx.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), 1 << 16)
-        (xa, ta), (xb, tb) = dev_mesh(sc.A, dtype), dev_mesh(sc.B, dtype)
-        # topology preparation (once per mesh, outside every timed region)
-        ea = torch.zeros((3 * sc.A.n_tris, 2), dtype=torch.int32, device=dev)
-        ne = ctx.hfcr_build_edges(ta, sc.A.n_verts, ea)
-        ea = ea[:ne].contiguous()
-        # the six coordinate arrays are views of one buffer, so that a frame
-        # restores (or uploads, or downloads) the positions in one copy
-        pos, pos0, views = packed(torch, xa + xb)
-        A = api.Mesh(*views[:3], ta, False, edges=ea)
-        B = api.Mesh(*views[3:], tb, True)
-        return ctx, A, B, (pos, pos0), ne
-
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def restore(A, B, init):
-        init[0].copy_(init[1], non_blocking=True)  # all six coordinate arrays
-
-    def frame(ctx, A, B, init):
-        restore(A, B, init)
-        return ctx.hfcr_resolve(A, B, D_POST, 1)
+    F = args.frames
 
     def timed(fn, K, W):
         for _ in range(W):
             fn()
         torch.cuda.synchronize()
-        if pg:
-            pg.barrier()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(K)]
         infos = []
@@ -606,167 +832,153 @@ def main():
             infos.append(fn())
             evs[i][1].record(stream)
         torch.cuda.synchronize()
-        if pg:
-            pg.barrier()
-        ms = [a.elapsed_time(b) for a, b in evs]
-        return ms, infos
+        return [a.elapsed_time(b) for a, b in evs], infos
 
-    # ---- optimized form: float32 filter, mixed-precision solver ----
-    ctx, A, B, init, ne = build(np.float32, api.HFCR_SOLVER_MIXED, True)
-    # traversal variant chosen by the library's autotuner on this scene
-    variant, variant_ms = ctx.hfcr_autotune(A, B)
-    for _ in range(args.warmup):
-        frame(ctx, A, B, init)
-    # profiled pass: CUDA events around every stage on the launching stream
-    # (the library launches the stages directly while profiling)
-    k_prof = max(5, min(args.steps, 50))
-    ctx.hfcr_profile_enable(True)
-    prof_ms, _ = timed(lambda: frame(ctx, A, B, init), k_prof, 2)
-    prof = ctx.hfcr_profile_read()
-    ctx.hfcr_profile_enable(False)
-    # headline pass: each repair iteration replayed as a CUDA graph
+    # ---- headline: the frame sequence, mixed form, graphs ----
+    sc = meshgen.scene_c5()
+    seq = Sequence(api, torch, dev, sc, np.float32)
+    variant, variant_ms = seq.ctx.hfcr_autotune(seq.A, seq.B)
+    keep = {0: None, F // 2 - 1: None, F - 1: None}
+    run_sequences(seq, torch, stream, flush, max(1, args.warmup), F, keep=keep)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
     launches0 = api.hfcr_launch_count()
     sampler = ClockSampler(local)
     sampler.start()
-    ms, infos = timed(lambda: frame(ctx, A, B, init), args.steps, 2)
+    t_wall = time.perf_counter()
+    ms, infos = run_sequences(seq, torch, stream, flush, args.steps, F)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     launches = api.hfcr_launch_count() - launches0
-    total_ms, per_frame = whole_job(sum(ms), args.steps, pg, dev)
-    info = infos[-1]
-    bf = int(info.stats.brute_force_equiv)
-    narrow = int(info.stats.narrow_tests)
+    if pg:
+        pg.barrier()
+    total_ms, per_frame = whole_job(sum(ms), args.steps * F, pg, dev)
+    fstats = frame_stats(infos)
+    bf_frame = seq.ne * sc.B.n_tris
+    narrow = statistics.mean(int(i.stats.narrow_tests) for i in infos)
+    # per-frame record of the last timed sequence: the slowest frames and why
+    last = ms[-F:]
+    order = sorted(range(F), key=lambda f: -last[f])
+    slow = [{"frame": f, "ms": round(last[f], 4), "pairs": int(infos[f].pairs_first),
+             "stencils": int(infos[f].total_stencils), "cg_iters": int(infos[f].cg_iters),
+             "solver_path": int(infos[f].solver_path),
+             "diffuse_cg_iters": int(infos[f].diffuse_cg_iters)} for f in order[:6]]
+    if args.frame_log:
+        with open(args.frame_log, "w") as fh:
+            fh.write("frame,ms,pairs,stencils,cg_iters,solver_path,diffuse_cg_iters\n")
+            for f in range(F):
+                i = infos[f]
+                fh.write(f"{f},{last[f]:.5f},{i.pairs_first},{i.total_stencils},{i.cg_iters},"
+                         f"{i.solver_path},{i.diffuse_cg_iters}\n")
 
-    P = int(info.pairs_first)
+    # profiled pass: CUDA events around every stage (plain launches)
+    seq.ctx.hfcr_profile_enable(True)
+    pms, _ = run_sequences(seq, torch, stream, flush, 1, F)
+    prof = seq.ctx.hfcr_profile_read()
+    seq.ctx.hfcr_profile_enable(False)
+    stage_ms = {k: round(v[0] / F, 4) for k, v in prof.items()}
     peak, peak_kind = measured_peak_hbm()
-    n_prof_frames = max(1, prof["traverse"][1])
-    stage_ms = {k: round(v[0] / n_prof_frames, 4) for k, v in prof.items()}
-    dominant = max(stage_ms, key=stage_ms.get)
-    # rooflines of the two kernels that own a stage each: the traversal +
-    # exact narrow phase, and the per-zone solver (the solve stage is
-    # k_cg_zone_pair, which solves this frame's ten zones, the
-    # one-warp-per-zone and 1024-thread launches, both nearly empty here,
-    # and the one-CTA k_zone_final); algorithmic bytes = compulsory reads +
-    # writes
-    trav_ms, trav_n = prof["traverse"]
-    trav_avg_ms = trav_ms / max(1, trav_n)
-    alg_trav = (sc.A.n_verts * 12 + ne * 8 + sc.B.n_verts * 12 + sc.B.n_tris * 12 + P * 8)
-    ach_trav = alg_trav / (trav_avg_ms * 1e-3) / 1e9
-    solve_ms, solve_n = prof["solve"]
-    solve_avg_ms = solve_ms / max(1, solve_n)
-    # stencil count and touched vertices of this frame's system (outside the
-    # timed regions)
-    restore(A, B, init)
-    pbuf = torch.zeros((1 << 16, 4), dtype=torch.int32, device=dev)
-    n_p = ctx.hfcr_detect(A, B, pbuf)
-    sbuf = torch.zeros((1 << 16, 4), dtype=torch.int32, device=dev)
-    k_st = ctx.hfcr_build_stencils(A, B, pbuf, n_p, sbuf)
-    dxa = [torch.zeros(sc.A.n_verts, device=dev) for _ in range(3)]
-    dxb = [torch.zeros(sc.B.n_verts, device=dev) for _ in range(3)]
-    si = ctx.hfcr_respond(A, B, sbuf, k_st, D_POST, dxa, dxb)
-    # per stencil: ids 16 + float32 normal 16 + preconditioner row 16 + b 8
-    # + float64 normal 32 + lam 8 (written) + 4 vertex-CSR entries 16 + group
-    # start 4; per touched vertex: CSR offset 4 + inverse mass 4
-    alg_cg = 116 * k_st + 8 * int(si.n_touched)
-    ach_cg = alg_cg / (solve_avg_ms * 1e-3) / 1e9
+    # rooflines: the traversal (one launch per frame) and the harmonic
+    # diffusion's band CG; algorithmic bytes = compulsory reads + writes
+    trav_ms = prof["traverse"][0] / max(1, prof["traverse"][1])
+    P_mean = statistics.mean(int(i.pairs_first) for i in infos)
+    alg_trav = int(sc.A.n_verts * 12 + seq.ne * 8 + sc.B.n_verts * 12 + sc.B.n_tris * 12 + P_mean * 8)
+    ach_trav = alg_trav / (trav_ms * 1e-3) / 1e9
+    frame_bytes = (sc.A.n_verts + sc.B.n_verts) * 12 * 2 + seq.ne * 8 + sc.B.n_tris * 12
     roof = {
         "k_traverse": {"kernel": "k_traverse (BVH traversal + exact narrow phase)", "bound": "hbm",
                        "achieved": round(ach_trav, 2), "peak": peak, "peak_kind": peak_kind,
                        "unit": "GB/s", "frac": round(ach_trav / peak, 5),
                        "traffic": profiled_traffic("k_traverse"), "alg_bytes_per_launch": alg_trav,
-                       "avg_launch_ms": round(trav_avg_ms, 5), "launches_timed": trav_n,
-                       "traverse_variant": variant, "variant_ms": variant_ms},
-        "k_cg_zone_pair": {"kernel": "k_cg_zone_pair (float32 PCG per impact zone, float64 "
-                                     "refinement in the kernel)", "bound": "hbm",
-                      "achieved": round(ach_cg, 3), "peak": peak, "peak_kind": peak_kind,
-                      "unit": "GB/s", "frac": round(ach_cg / peak, 6),
-                      "traffic": profiled_traffic("k_cg_zone_pair"), "alg_bytes_per_launch": alg_cg,
-                      "avg_launch_ms": round(solve_avg_ms, 5), "launches_timed": solve_n,
-                      "stencils": k_st, "touched_vertices": int(si.n_touched)},
+                       "avg_launch_ms": round(trav_ms, 5), "launches_timed": prof["traverse"][1]},
+        "whole_frame": {"bound": "hbm", "alg_bytes_per_frame": frame_bytes,
+                        "achieved": round(frame_bytes / (per_frame * 1e-3) / 1e9, 2), "peak": peak,
+                        "unit": "GB/s", "frac": round(frame_bytes / (per_frame * 1e-3) / 1e9 / peak, 5),
+                        "note": "positions of both meshes read and written, cloth edges, body faces"},
     }
-    dom_kernel = "k_cg_zone_pair" if stage_ms["solve"] >= stage_ms["traverse"] else "k_traverse"
-    roofline = dict(roof[dom_kernel], dominant_stage=dominant,
-                    chosen_by="the larger of the solve and traverse stages in the profiled pass")
+    dominant = max(("traverse", "bvh", "solve", "diffuse"), key=lambda k: stage_ms[k])
+    roofline = dict(roof["k_traverse"], dominant_stage=dominant,
+                    chosen_by="the traversal kernel; the stage times of the profiled pass are in "
+                              "stage_ms_per_frame")
+
+    # ---- the same frames through the other forms ----
+    forms = None if args.no_forms else lockstep_forms(api, torch, dev, sc, stream, flush, F, seq)
 
     # ---- end to end through the C ABI with host buffers ----
-    # both meshes' coordinates, one pinned host buffer each way
-    host_in = init[1].detach().cpu().pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
+    n_e2e = max(2, args.steps // 4)
+    e2e_ms, io_bytes = e2e_sequences(seq, torch, stream, n_e2e, F)
+    e2e_total, e2e_per_frame = whole_job(sum(e2e_ms), n_e2e * F, pg, dev)
+    seq.close()
 
-    def e2e_frame():
-        init[0].copy_(host_in, non_blocking=True)
-        info = ctx.hfcr_resolve(A, B, D_POST, 1)
-        host_out.copy_(init[0], non_blocking=True)
-        return info
+    extra = {}
+    if not args.no_extra:
+        extra["cloth_torus"] = cloth_torus(api, torch, dev, stream, flush, 20, 5, timed,
+                                           cpu=rank == 0 and not args.no_cpu_baseline)
+        extra["precision_form"] = precision_form(api, torch, dev, 5, timed)
+        extra["small_form"] = small_form(api, torch, dev, 10, timed)
+        extra["batch"] = batched(api, torch, dev, 5, 2, timed,
+                                 cpu=rank == 0 and not args.no_cpu_baseline)
 
-    e2e_ms, _ = timed(e2e_frame, args.steps, 2)
-    e2e_total, _ = whole_job(sum(e2e_ms), args.steps, pg, dev)
-    io_bytes = host_in.numel() * host_in.element_size()
-
-    # ---- the plain float64 GPU form on the same frame ----
-    fp64 = None
-    if not args.no_fp64_form:
-        # the plain float64 form: float64 positions, float64 filter -> exact,
-        # float64 CG, plain launches (no graphs)
-        ctx64, A64, B64, init64, _ = build(np.float64, api.HFCR_SOLVER_FP64, False, graphs=False)
-        k64 = max(3, args.steps // 3)
-        ms64, inf64 = timed(lambda: frame(ctx64, A64, B64, init64), k64, 2)
-        fp64 = {"ms_per_frame": round(statistics.mean(ms64), 4), "steps": k64,
-                "pairs": int(inf64[-1].pairs_first),
-                "speedup_of_f32_form": round(statistics.mean(ms64) / statistics.mean(ms), 2)}
-        ctx64.close()
-
-    frames = frame_sequence(api, torch, dev, args.frames) if args.frames > 0 else None
-    c3 = None if args.no_c3 else precision_form(api, torch, dev, max(5, args.steps // 5), timed)
-    c1 = None if args.no_c3 else small_form(api, torch, dev, max(10, args.steps // 2), timed)
-    batch = None if args.no_batch else batched(api, torch, dev, max(5, args.steps // 10), 2, timed)
-
-    line = None
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            sec, cores, scaled = cpu_oracle_frame(sc, 1.0)
-            cpu = {"value": round(scaled * 1e3, 2), "unit": "ms/frame", "cores": cores, "kind": "oracle",
-                   "sample": "one full frame: brute-force exact detection of all 119,201 cloth edges "
-                             "against all 65,536 torus faces, stencils, float64 per-zone solve"}
+            import oracle
+            E = oracle.edges(sc.A.T)
+            vals, spent = [], 0.0
+            for i, f in enumerate(sorted(keep)):
+                PA, PB = keep[f]
+                scaled, s_ = oracle_frame(PA, sc.A.T, PB, sc.B.T, E, 1 / 3, i)
+                vals.append(scaled)
+                spent += s_
+            cpu = {"value": round(1e3 * statistics.mean(vals), 1), "unit": "ms/frame",
+                   "cores": oracle.num_threads(), "kind": "oracle",
+                   "sample": "frames %s of the sequence (the GPU's positions before each frame's "
+                             "response): brute-force exact detection of every third cloth edge "
+                             "against all 327,680 body faces, stencils, float64 response and "
+                             "harmonic diffusion of what was found, scaled by 3; %.1f s of CPU "
+                             "work" % (sorted(keep), spent),
+                   "per_frame_ms": [round(1e3 * v, 1) for v in vals]}
         line = {
             "metric": METRIC, "value": round(per_frame, 4), "unit": "ms/frame",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "cloth 200x200 (119,201 edges) vs torus 256x128 (65,536 faces), "
-                                   "float32, one DCD+response frame from the initial state",
-                       "pairs": P, "stencils": int(info.total_stencils),
+            "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "frame sequence: cloth 512x512 (784,385 edges, float32, "
+                                   "un-oriented) over an oriented SH body (icosphere L7, 327,680 "
+                                   "faces); %d frames per step, one DCD response per frame "
+                                   "(detection, stencils, Eq. 8 solve, harmonic diffusion R=%d), "
+                                   "CUDA-graph replay" % (F, RINGS),
+                       "frames_per_step": F,
                        "predicates": "float32 semi-static filter -> float64 filter -> exact integers",
-                       "solver": "float32 CG + float64 iterative refinement to 1e-12",
-                       "l2": "flushed between steps (256 MB write)",
+                       "solver": "float32 CG + float64 iterative refinement to 1e-12 per impact zone",
+                       "diffusion": "harmonic field: float64 CG on the band Laplacian to 1e-10",
+                       "l2": "flushed before every frame (256 MB write, outside the timed interval)",
                        "parallelism": f"replicas x{ws}"},
-            "ms_p50": round(statistics.median(ms), 4),
-            "ms_p99": round(sorted(ms)[min(len(ms) - 1, int(0.99 * len(ms)))], 4),
-            "ef_tests_per_s_bruteforce": round(bf / (per_frame / 1e3), 1),
+            "ms_p50": round(pct(ms, 0.5), 4), "ms_p99": round(pct(ms, 0.99), 4),
+            "frames": fstats,
+            "slowest_frames": slow,
+            "ef_tests_per_s_bruteforce": round(bf_frame / (per_frame / 1e3), 1),
             "ef_tests_per_s_executed": round(narrow / (per_frame / 1e3), 1),
-            "filter": {"narrow_tests": narrow, "f64_fallbacks": int(info.stats.f64_fallbacks),
-                       "exact_fallbacks": int(info.stats.exact_fallbacks)},
-            "solver": {"cg_iters": int(info.cg_iters), "rel_residual": info.worst_rel_residual,
-                       "float32_cg_in_shared_memory": bool(info.solver_path & 1)},
             "stage_ms_per_frame": stage_ms,
-            "profiled_ms_per_frame": round(statistics.mean(prof_ms), 4),
+            "profiled_ms_per_frame": round(statistics.mean(pms), 4),
+            "traverse_variant": variant, "variant_ms": variant_ms,
             "graphs": True,
             "roofline": roofline,
             "rooflines": roof,
-            "e2e": {"value": round(e2e_total / (args.steps * ws), 4), "unit": "ms/frame",
-                    "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
-            "fp64_form": fp64,
-            "small_form": c1,
-            "precision_form": c3,
-            "frame_sequence": frames,
-            "batch": batch,
+            "e2e": {"value": round(e2e_per_frame, 4), "unit": "ms/frame",
+                    "h2d_bytes_per_step": io_bytes * F, "d2h_bytes_per_step": io_bytes * F,
+                    "h2d_bytes_per_frame": io_bytes, "d2h_bytes_per_frame": io_bytes,
+                    "steps": n_e2e},
+            "forms_same_frames": forms,
             "gpu_launches": launches,
+            "timed_wall_s": round(t_wall, 2),
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
-    ctx.close()
     if pg:
         pg.barrier()
         pg.destroy_process_group()

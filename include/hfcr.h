@@ -66,10 +66,15 @@ typedef enum {
 
 typedef enum { HFCR_F32 = 0, HFCR_F64 = 1 } hfcr_dtype;
 
-/* Solver of Eq. 7/8.  MIXED: conjugate gradients in float32 with float64
- * iterative refinement of the residual against the float64 constraint
- * gradients; FP64: conjugate gradients in float64 throughout. */
-typedef enum { HFCR_SOLVER_MIXED = 0, HFCR_SOLVER_FP64 = 1 } hfcr_solver;
+/* Solver of Eq. 7/8, one linear system per impact zone (Sec. 4).  MIXED:
+ * conjugate gradients in float32 with float64 iterative refinement of the
+ * residual against the float64 constraint gradients, each zone staged in
+ * shared memory by a thread group sized to it; FP64: conjugate gradients
+ * in float64 throughout, each zone by one CTA on global memory (with
+ * float64 meshes and f32_filter 0 this is the plain float64 form);
+ * FP64_GLOBAL: float64 conjugate gradients over the whole system in one
+ * CTA (the same x', a different solver structure). */
+typedef enum { HFCR_SOLVER_MIXED = 0, HFCR_SOLVER_FP64 = 1, HFCR_SOLVER_FP64_GLOBAL = 2 } hfcr_solver;
 
 /* Role schedule of the repair loop when both meshes are oriented (Sec. 4:
  * "one is regarded as oriented and the other as un-oriented" in the
@@ -111,14 +116,19 @@ typedef struct {
     int32_t graphs;         /* 1 (default): resolve replays each repair iteration as a captured
                                CUDA graph (re-captured when any argument changes); 0: plain launches.
                                Graphs are not used while the profiler is enabled. */
-    int32_t diffuse_rings;  /* Sec. 5 diffusion in hfcr_resolve (see hfcr_diffuse): rings R of the */
-    int32_t diffuse_sweeps; /* band and Jacobi sweeps S; 0 (default) in either: no diffusion, the
-                               minimizer's displacement is applied as it is */
+    int32_t diffuse_rings;  /* Sec. 5 diffusion in hfcr_resolve (see hfcr_diffuse): rings R of the
+                               band; 0 (default): no diffusion, the minimizer's displacement is
+                               applied as it is */
+    int32_t diffuse_sweeps; /* 0 (default): the harmonic field (conjugate gradients to diffuse_tol);
+                               S > 0: the fixed-sweep approximation, S Jacobi sweeps from zero */
     int32_t traverse_variant; /* traversal kernel variant 0..4 used until hfcr_autotune picks one
                                  (default 0; every variant finds the same pairs) */
     int32_t setup_path;     /* response setup (vertex CSR, impact zones, preconditioner groups):
                                0 (default) one cooperative launch, 1 a sequence of about 25
                                kernels; both build the same arrays, so the results are identical */
+    int32_t diffuse_max_iters; /* harmonic diffusion: iteration limit (0: default 1000) */
+    double diffuse_tol;     /* harmonic diffusion: stop at |r| <= diffuse_tol |b| per coordinate,
+                               0 < tol < 1 (0: default 1e-10) */
 } hfcr_options;
 
 typedef struct {
@@ -148,7 +158,10 @@ typedef struct {
     int32_t cg_iters;              /* all solves */
     double worst_rel_residual;     /* largest solver residual over the iterations */
     hfcr_detect_stats stats;       /* summed over the detections */
-    int32_t solver_path;           /* bit 0: the float32 CG ran in shared memory, bit 1: in global memory */
+    int32_t solver_path;           /* bit 0: the float32 CG ran in shared memory, bit 1: in global
+                                      memory; bit 2: the float64 per-zone CG ran */
+    int32_t diffuse_cg_iters;      /* harmonic diffusion: CG iterations over all iterations */
+    int32_t diffuse_unconverged;   /* iterations whose harmonic diffusion stopped at diffuse_max_iters */
 } hfcr_resolve_info;
 
 /* Stages timed by the optional profiler (instrumentation; the paper has no
@@ -161,7 +174,8 @@ typedef enum {
     HFCR_STAGE_ASSEMBLE = 4,  /* constraint rows and the vertex CSR */
     HFCR_STAGE_SOLVE = 5,     /* Eq. 7 / Eq. 8 solve */
     HFCR_STAGE_DISPLACE = 6,  /* x' - x and its application */
-    HFCR_N_STAGES = 7
+    HFCR_STAGE_DIFFUSE = 7,   /* diffusion of the displacement (Sec. 5) and its application */
+    HFCR_N_STAGES = 8
 } hfcr_stage;
 
 typedef struct {
@@ -259,24 +273,29 @@ hfcr_status hfcr_respond(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
 /* Diffusion of a displacement field over one mesh (Sec. 5: the
  * correction is propagated from the penetrating vertices to their vicinity
  * as a harmonic vector field; the paper gives no equations, this is the
- * reading implemented): vertices with a nonzero displacement keep it,
+ * reading implemented).  On the graph of M's edges (M.edges, or derived
+ * from the triangles): vertices with a nonzero displacement keep it,
  * vertices more than `rings` edges from all of them, and kinematic
- * vertices (M.inv_mass 0), get 0, and every vertex in between takes
- * `sweeps` Jacobi sweeps of the mean of its neighbours, starting from 0.
- * The neighbours come from M's edge list (M.edges, or derived from the
- * triangles); each mean sums them in ascending vertex order in float64.
+ * vertices (M.inv_mass 0), get 0 (Dirichlet values), and every vertex in
+ * between (the band) gets the value that makes it the mean of its
+ * neighbours.  sweeps == 0: that harmonic field, solved per coordinate by
+ * Jacobi-preconditioned conjugate gradients on the band's graph Laplacian
+ * to |r| <= diffuse_tol |b| (options), HFCR_ERR_NOT_CONVERGED when
+ * diffuse_max_iters iterations do not reach it; sweeps > 0: the fixed-sweep
+ * approximation instead, `sweeps` Jacobi sweeps of the neighbour mean
+ * starting from 0 (each mean summed in ascending vertex order in float64).
  * dx, dy, dz: device float64 [M.n_verts], read and overwritten.  rings in
- * [0, 1024], sweeps in [0, 100000]; either 0 leaves the field as it is.
+ * [0, 1024] (0 leaves the field as it is), sweeps in [0, 100000].
  * Synchronises. */
 hfcr_status hfcr_diffuse(hfcr_ctx *ctx, const hfcr_mesh *M, double *dx, double *dy, double *dz,
                          int32_t rings, int32_t sweeps, void *stream);
 
 /* The repair loop (Sec. 3): detect, build stencils, displace, repeated
  * until no E-F intersection remains or max_iters detections ran.  Updates
- * A and B's positions in place.  With options diffuse_rings and
- * diffuse_sweeps > 0, each iteration's displacement is first spread over
- * both meshes as by hfcr_diffuse (Sec. 5), then applied.  info (host) may
- * be NULL.  Returns HFCR_ERR_NOT_CONVERGED when the loop stopped at
+ * A and B's positions in place.  With option diffuse_rings > 0, each
+ * iteration's displacement is first spread over both meshes as by
+ * hfcr_diffuse (Sec. 5; the harmonic field unless diffuse_sweeps > 0), then
+ * applied.  info (host) may be NULL.  Returns HFCR_ERR_NOT_CONVERGED when the loop stopped at
  * max_iters.  Synchronises. */
 hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, int32_t max_iters,
                          hfcr_resolve_info *info, void *stream);

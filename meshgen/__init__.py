@@ -382,6 +382,27 @@ class ClothMotion:
         v[:, 2] -= self.v0
         return v
 
+    def device_params(self, torch, dev):
+        """The field's parameters as float32 tensors on `dev` (for advance)."""
+        f32 = torch.float32
+        return (torch.tensor(self.k.T, dtype=f32, device=dev),
+                torch.tensor(self.w, dtype=f32, device=dev),
+                torch.tensor(self.ph, dtype=f32, device=dev),
+                torch.tensor((self.amp[:, None] * self.dir) * (0.5 * self.v0), dtype=f32, device=dev))
+
+    def advance(self, torch, params, x, y, z, frame: int):
+        """Moves the cloth by one frame in place: x, y, z are float32 device
+        tensors, params from device_params (the same field as velocity,
+        evaluated in float32 on the device)."""
+        K, W, PH, AD = params
+        X = torch.stack([x, y, z], 1)
+        V = torch.sin(X @ K + W * frame + PH) @ AD
+        V[:, 2] -= self.v0
+        X += V
+        x.copy_(X[:, 0])
+        y.copy_(X[:, 1])
+        z.copy_(X[:, 2])
+
 
 def scene_c5(seed: int = BASE_SEED + 4, n: int = 512, side: float = 3.0,
              z_start: float = 1.15, body_level: int = 7) -> Scene:

@@ -28,6 +28,7 @@ HFCR_F32 = 0
 HFCR_F64 = 1
 HFCR_SOLVER_MIXED = 0
 HFCR_SOLVER_FP64 = 1
+HFCR_SOLVER_FP64_GLOBAL = 2
 HFCR_ROLES_ALTERNATE = 0
 HFCR_ROLES_BOTH = 1
 
@@ -56,7 +57,8 @@ class hfcr_options(ctypes.Structure):
                 ("max_refine", ctypes.c_int32), ("rel_tol", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("graphs", ctypes.c_int32),
                 ("diffuse_rings", ctypes.c_int32), ("diffuse_sweeps", ctypes.c_int32),
-                ("traverse_variant", ctypes.c_int32), ("setup_path", ctypes.c_int32)]
+                ("traverse_variant", ctypes.c_int32), ("setup_path", ctypes.c_int32),
+                ("diffuse_max_iters", ctypes.c_int32), ("diffuse_tol", ctypes.c_double)]
 
 
 class hfcr_solve_info(ctypes.Structure):
@@ -75,11 +77,12 @@ class hfcr_resolve_info(ctypes.Structure):
                 ("pairs_first", ctypes.c_int64), ("pairs_last", ctypes.c_int64),
                 ("total_pairs", ctypes.c_int64), ("total_stencils", ctypes.c_int64),
                 ("cg_iters", ctypes.c_int32), ("worst_rel_residual", ctypes.c_double),
-                ("stats", hfcr_detect_stats), ("solver_path", ctypes.c_int32)]
+                ("stats", hfcr_detect_stats), ("solver_path", ctypes.c_int32),
+                ("diffuse_cg_iters", ctypes.c_int32), ("diffuse_unconverged", ctypes.c_int32)]
 
 
-HFCR_N_STAGES = 7
-STAGES = ("validate", "bvh", "traverse", "stencils", "assemble", "solve", "displace")
+HFCR_N_STAGES = 8
+STAGES = ("validate", "bvh", "traverse", "stencils", "assemble", "solve", "displace", "diffuse")
 
 
 class hfcr_profile(ctypes.Structure):
@@ -193,12 +196,13 @@ class Context:
                  roles: int = HFCR_ROLES_ALTERNATE, max_cg_iters: int = 500, max_refine: int = 6,
                  rel_tol: float = 1e-12, inner_tol: float = 1e-4, graphs: bool = True,
                  diffuse_rings: int = 0, diffuse_sweeps: int = 0, traverse_variant: int = 0,
-                 setup_path: int = 0):
+                 setup_path: int = 0, diffuse_max_iters: int = 1000, diffuse_tol: float = 1e-10):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("hfcr needs a CUDA device")
         opt = hfcr_options(solver, int(f32_filter), roles, max_cg_iters, max_refine, rel_tol, inner_tol,
-                           int(graphs), diffuse_rings, diffuse_sweeps, traverse_variant, setup_path)
+                           int(graphs), diffuse_rings, diffuse_sweeps, traverse_variant, setup_path,
+                           diffuse_max_iters, diffuse_tol)
         h = ctypes.c_void_p()
         self.handle = None
         # a refused create has no context: its message is the thread's
@@ -296,8 +300,9 @@ class Context:
                                        ctypes.byref(si) if info else None, _stream_ptr(stream)))
         return si
 
-    def hfcr_diffuse(self, M: "Mesh", dx, rings: int, sweeps: int, stream=None):
-        """dx: three float64 CUDA tensors [n] (x, y, z), overwritten."""
+    def hfcr_diffuse(self, M: "Mesh", dx, rings: int, sweeps: int = 0, stream=None):
+        """dx: three float64 CUDA tensors [n] (x, y, z), overwritten; sweeps
+        0: the harmonic field, > 0: that many Jacobi sweeps."""
         self._check(lib().hfcr_diffuse(self.handle, ctypes.byref(M.c), _ptr(dx[0]), _ptr(dx[1]),
                                        _ptr(dx[2]), rings, sweeps, _stream_ptr(stream)))
 

@@ -88,8 +88,11 @@ struct hfcr_ctx {
     // diffusion (Sec. 5): vertex adjacency per mesh, float64 field ping-pong
     // over both meshes' vertices (AoS), ring distances
     int *adj_ptr[2] = {nullptr, nullptr}, *adj_nbr[2] = {nullptr, nullptr}, *adj_cur = nullptr;
+    const int *adj_src[2] = {nullptr, nullptr};  // caller edge list behind adj_ptr / adj_nbr
+    int adj_ne[2] = {0, 0}, adj_nv[2] = {0, 0};
     double *field = nullptr, *field_alt = nullptr;
     int *ring = nullptr;
+    DiffScratch dscr;             // the harmonic diffusion's band and CG state
     // profiler
     bool prof_on = false;
     double prof_ms[HFCR_N_STAGES] = {0};
@@ -104,7 +107,8 @@ struct hfcr_ctx {
 };
 
 // device counter slots
-enum { C_PAIRS = 0, C_STENCILS = 1, C_EDGES_A = 2, C_EDGES_B = 3, C_N4 = 4, C_NPAIRS_IN = 5, C_PEFF = 6 };
+enum { C_PAIRS = 0, C_STENCILS = 1, C_EDGES_A = 2, C_EDGES_B = 3, C_N4 = 4, C_NPAIRS_IN = 5, C_PEFF = 6,
+       C_DIFF_ITERS = 7, C_DIFF_FAIL = 8, C_NFREE = 9 };
 
 namespace {
 
@@ -143,18 +147,22 @@ void free_all(hfcr_ctx *c) {
                     c->sb.ck64, c->sb.ck64_alt, c->sb.gst, c->sb.zg, c->sb.d_ng, c->sb.pinv,
                     c->sb.z32,
                     c->sb.ids, c->sb.n64, c->sb.n32, c->sb.b, c->sb.lam, c->sb.r64, c->sb.r32,
-                    c->sb.x32, c->sb.p32, c->sb.q32, c->sb.w32, c->sb.p64, c->sb.q64, c->sb.vidx, c->sb.ckey,
+                    c->sb.x32, c->sb.p32, c->sb.q32, c->sb.w32, c->sb.p64, c->sb.q64, c->sb.cg64, c->sb.vidx, c->sb.ckey,
                     c->sb.ckey_alt, c->sb.cval, c->sb.cval_alt, c->sb.cflag, c->sb.seg, c->sb.gvert,
                     c->sb.winv, c->sb.u64, c->sb.u32, c->sb.red};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *dp[] = {c->adj_ptr[0], c->adj_ptr[1], c->adj_nbr[0], c->adj_nbr[1], c->adj_cur, c->field,
-                  c->field_alt, c->ring, c->eorder[0], c->eorder[1]};
+                  c->field_alt, c->ring, c->eorder[0], c->eorder[1], c->dscr.flags, c->dscr.cidx,
+                  c->dscr.fv, c->dscr.b64, c->dscr.u64, c->dscr.x32, c->dscr.p32, c->dscr.rec,
+                  c->dscr.cnbr, c->dscr.part, c->dscr.bar};
     for (void *p : dp)
         if (p) cudaFree(p);
     c->adj_ptr[0] = c->adj_ptr[1] = c->adj_nbr[0] = c->adj_nbr[1] = c->adj_cur = nullptr;
     c->field = c->field_alt = nullptr;
     c->ring = nullptr;
+    c->dscr = DiffScratch();
+    c->adj_src[0] = c->adj_src[1] = nullptr;
     c->eorder[0] = c->eorder[1] = nullptr;
     c->eorder_src[0] = c->eorder_src[1] = nullptr;
     c->eorder_n[0] = c->eorder_n[1] = 0;
@@ -513,9 +521,7 @@ hfcr_status run_response(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     return HFCR_OK;
 }
 
-bool diffusing(const hfcr_ctx *ctx) {
-    return ctx->opt.diffuse_rings > 0 && ctx->opt.diffuse_sweeps > 0;
-}
+bool diffusing(const hfcr_ctx *ctx) { return ctx->opt.diffuse_rings > 0; }
 
 // vertex adjacency of both meshes for the diffusion, from their edge lists
 // (the plan's, or derived from the triangles)
@@ -524,6 +530,11 @@ hfcr_status prepare_diffusion(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh
     const hfcr_mesh *M[2] = {A, B};
     for (int i = 0; i < 2; ++i) {
         if (M[i]->n_verts <= 0) continue;
+        // a caller's edge list is taken to stay the same while its buffer
+        // and counts do (as for the traversal order): its adjacency is kept
+        if (M[i]->edges && ctx->adj_src[i] == M[i]->edges && ctx->adj_ne[i] == M[i]->n_edges &&
+            ctx->adj_nv[i] == M[i]->n_verts)
+            continue;
         const int *e = pl.edges[i];
         int ne = pl.ne[i];
         if (!e && M[i]->n_tris > 0) {
@@ -532,6 +543,9 @@ hfcr_status prepare_diffusion(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh
         }
         build_adjacency(e, e ? ne : 0, M[i]->n_verts, ctx->adj_ptr[i], ctx->adj_nbr[i], ctx->adj_cur,
                         ctx->sort, ctx->d_status, s);
+        ctx->adj_src[i] = M[i]->edges;
+        ctx->adj_ne[i] = M[i]->n_edges;
+        ctx->adj_nv[i] = M[i]->n_verts;
     }
     CK(cudaGetLastError());
     return HFCR_OK;
@@ -579,14 +593,16 @@ void enqueue_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bo
     cudaMemsetAsync(ctx->field, 0, sizeof(double) * 3 * (size_t)ntot, s);
     void *fld[3] = {ctx->field, nullptr, nullptr};
     run_response(ctx, A, B, ctx->stencils, cap, d, 2, fld, nullptr, s);
-    prof_begin(ctx, HFCR_STAGE_DISPLACE, s);
+    prof_begin(ctx, HFCR_STAGE_DIFFUSE, s);
     DiffMeshArgs da, db;
     da.ptr = ctx->adj_ptr[0]; da.nbr = ctx->adj_nbr[0]; da.inv_mass = A->inv_mass; da.n = A->n_verts;
     db.ptr = ctx->adj_ptr[1]; db.nbr = ctx->adj_nbr[1]; db.inv_mass = B->inv_mass; db.n = B->n_verts;
     const double *u = diffuse_field(da, db, ctx->field, ctx->field_alt, ctx->ring,
-                                    ctx->opt.diffuse_rings, ctx->opt.diffuse_sweeps, s);
+                                    ctx->opt.diffuse_rings, ctx->opt.diffuse_sweeps,
+                                    ctx->opt.diffuse_tol, ctx->opt.diffuse_max_iters, ctx->dscr,
+                                    ctx->sort, ctx->d_status, s);
     apply_field(*A, *B, ctx->ring, ctx->opt.diffuse_rings, u, s);
-    prof_end(ctx, HFCR_STAGE_DISPLACE, s);
+    prof_end(ctx, HFCR_STAGE_DIFFUSE, s);
 }
 
 // Reads the counters, status, statistics and solver words of the last
@@ -718,13 +734,16 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
     c->opt.diffuse_sweeps = 0;
     c->opt.traverse_variant = 0;
     c->opt.setup_path = 0;
+    c->opt.diffuse_max_iters = 1000;
+    c->opt.diffuse_tol = 1e-10;
     if (opt) {
         c->opt = *opt;
         if (c->opt.max_cg_iters <= 0) c->opt.max_cg_iters = 500;
         if (c->opt.max_refine <= 0) c->opt.max_refine = 6;
         if (!(c->opt.rel_tol > 0)) c->opt.rel_tol = 1e-12;
         if (!(c->opt.inner_tol > 0)) c->opt.inner_tol = 1e-4;
-        if (c->opt.solver != HFCR_SOLVER_FP64) c->opt.solver = HFCR_SOLVER_MIXED;
+        if (c->opt.solver != HFCR_SOLVER_FP64 && c->opt.solver != HFCR_SOLVER_FP64_GLOBAL)
+            c->opt.solver = HFCR_SOLVER_MIXED;
         if (c->opt.roles != HFCR_ROLES_BOTH) c->opt.roles = HFCR_ROLES_ALTERNATE;
         if (c->opt.traverse_variant < 0 || c->opt.traverse_variant >= N_TRAVERSE_VARIANTS) {
             delete c;
@@ -734,6 +753,14 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
         if (c->opt.setup_path != 0 && c->opt.setup_path != 1) {
             delete c;
             set_noctx_error("hfcr_create: setup_path must be 0 or 1");
+            return HFCR_ERR_ARG;
+        }
+        if (c->opt.diffuse_max_iters == 0) c->opt.diffuse_max_iters = 1000;
+        if (c->opt.diffuse_tol == 0.0) c->opt.diffuse_tol = 1e-10;
+        if (!(c->opt.diffuse_tol > 0.0 && c->opt.diffuse_tol < 1.0) || c->opt.diffuse_max_iters < 0 ||
+            c->opt.diffuse_max_iters > 100000) {
+            delete c;
+            set_noctx_error("hfcr_create: diffuse_tol must be in (0, 1) and diffuse_max_iters in [0, 100000]");
             return HFCR_ERR_ARG;
         }
         if (c->opt.diffuse_rings < 0 || c->opt.diffuse_sweeps < 0 || c->opt.diffuse_rings > 1024 ||
@@ -780,6 +807,7 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     clear_graphs(ctx);
     free_all(ctx);
     solver_init();
+    diffusion_init();
     if (max_tris < 1) max_tris = 1;
     if (max_pairs < 1) max_pairs = 1;
     const size_t T = (size_t)max_tris, P = (size_t)max_pairs, E3 = 3 * T;
@@ -837,6 +865,22 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
         CK(dalloc(&ctx->field, 6 * V));
         CK(dalloc(&ctx->field_alt, 6 * V));
         CK(dalloc(&ctx->ring, 2 * V));
+        DiffScratch &ds = ctx->dscr;
+        ds.cap = (int)(2 * V);
+        CK(dalloc(&ds.flags, 2 * V));
+        CK(dalloc(&ds.cidx, 2 * V));
+        CK(dalloc(&ds.fv, 2 * V));
+        CK(dalloc(&ds.b64, 6 * V));
+        CK(dalloc(&ds.u64, 12 * V));
+        CK(dalloc(&ds.x32, 6 * V));
+        CK(dalloc(&ds.p32, 6 * V));
+        CK(dalloc(&ds.rec, 48 * V));
+        CK(dalloc(&ds.cnbr, 4 * E3));   // the capacity of both adjacency arrays
+        ds.eoffB = (int)(2 * E3);
+        CK(dalloc(&ds.part, 2 * 9 * 1024));
+        CK(dalloc(&ds.bar, 1));
+        ds.d_nfree = ctx->d_cnt + C_NFREE;
+        ds.ctl = ctx->d_cnt + C_DIFF_ITERS;
     }
     SolveBuffers &sb = ctx->sb;
     sb.cap_k = (int)P;
@@ -870,6 +914,7 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(dalloc(&sb.q32, P));
     CK(dalloc(&sb.w32, P));
     CK(dalloc(&sb.p64, 2 * P));
+    CK(dalloc(&sb.cg64, 5 * P));
     CK(dalloc(&sb.q64, P));
     CK(dalloc(&sb.vidx, P));
     CK(dalloc(&sb.ckey, 4 * P));
@@ -1030,7 +1075,9 @@ hfcr_status hfcr_diffuse(hfcr_ctx *ctx, const hfcr_mesh *M, double *dx, double *
         return fail(ctx, HFCR_ERR_ARG, "hfcr_diffuse: rings must be in [0, 1024], sweeps in [0, 100000]");
     if (M->n_verts > 0 && (!dx || !dy || !dz))
         return fail(ctx, HFCR_ERR_ARG, "hfcr_diffuse: NULL displacement array");
-    if (M->n_verts == 0 || rings == 0 || sweeps == 0) return HFCR_OK;
+    if (M->n_verts == 0 || rings == 0) return HFCR_OK;
+    if (M->n_verts > ctx->dscr.cap)
+        return fail(ctx, HFCR_ERR_CAPACITY, "hfcr_diffuse: mesh exceeds the reserved vertices");
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = reset_words(ctx, s))) return st;
     const int *e = M->edges;
@@ -1038,15 +1085,21 @@ hfcr_status hfcr_diffuse(hfcr_ctx *ctx, const hfcr_mesh *M, double *dx, double *
     if (!e && M->n_tris > 0 && (st = mesh_edges(ctx, M, 0, &e, &ne, s))) return st;
     build_adjacency(e, e ? ne : 0, M->n_verts, ctx->adj_ptr[0], ctx->adj_nbr[0], ctx->adj_cur,
                     ctx->sort, ctx->d_status, s);
+    ctx->adj_src[0] = nullptr;  // slot 0 no longer holds a resolve call's adjacency
     field_from_soa(dx, dy, dz, M->n_verts, ctx->field, s);
     DiffMeshArgs a, none;
     a.ptr = ctx->adj_ptr[0]; a.nbr = ctx->adj_nbr[0]; a.inv_mass = M->inv_mass; a.n = M->n_verts;
-    const double *u = diffuse_field(a, none, ctx->field, ctx->field_alt, ctx->ring, rings, sweeps, s);
+    const double *u = diffuse_field(a, none, ctx->field, ctx->field_alt, ctx->ring, rings, sweeps,
+                                    ctx->opt.diffuse_tol, ctx->opt.diffuse_max_iters, ctx->dscr,
+                                    ctx->sort, ctx->d_status, s);
     field_to_soa(u, M->n_verts, dx, dy, dz, s);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    return device_status(ctx, *ctx->h_status);
+    if ((st = read_back(ctx, s))) return st;
+    if (sweeps == 0 && ctx->h_cnt[C_DIFF_FAIL])
+        return fail(ctx, HFCR_ERR_NOT_CONVERGED,
+                    "hfcr_diffuse: the harmonic solve stopped after %d iterations above tol %g",
+                    ctx->h_cnt[C_DIFF_ITERS], ctx->opt.diffuse_tol);
+    return HFCR_OK;
 }
 
 static hfcr_status resolve_impl(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, const int *segs,
@@ -1095,6 +1148,8 @@ static hfcr_status resolve_impl(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, const
         }
         add_stats(&loc.stats, *ctx->h_stats);
         loc.stats.brute_force_equiv += single_pair_bf(pl, d0, d1, A, B);
+        loc.diffuse_cg_iters += ctx->h_cnt[C_DIFF_ITERS];
+        if (ctx->h_cnt[C_DIFF_FAIL]) loc.diffuse_unconverged += 1;
         if (it == 0) loc.pairs_first = P;
         loc.pairs_last = P;
         loc.total_pairs += P;

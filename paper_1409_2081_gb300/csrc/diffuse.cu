@@ -2,21 +2,32 @@
 // gives the stencil vertices is spread over their vicinity as a harmonic
 // vector field, so that the mesh moves smoothly instead of only at the
 // penetrating vertices.  The paper names constrained diffusion without
-// equations; the reading implemented here: vertices with a nonzero
-// displacement keep it (Dirichlet values), vertices more than R edges away
-// and kinematic vertices (inverse mass 0) keep zero, and every vertex in
-// between takes the mean of its neighbours, S Jacobi sweeps from zero.
+// equations; the reading implemented here, per mesh: vertices with a
+// nonzero displacement keep it (Dirichlet values), vertices more than R
+// edges away and kinematic vertices (inverse mass 0) keep zero, and every
+// vertex in between (the band) is the mean of its neighbours, i.e. the
+// band's graph Laplacian system
+//     deg(v) u_v - sum of u_w over band neighbours w
+//         = sum of the Dirichlet values of v's other neighbours
+// is solved for each coordinate, by Jacobi-preconditioned conjugate
+// gradients to a relative residual `tol` (k_band_cg, one cooperative launch
+// over the band's vertices).  The older fixed-sweep form (S Jacobi sweeps of
+// the neighbour mean from zero, whose limit is that field) stays available
+// as a named approximation.
 //
 // Layout: the field u is float64 AoS (x, y, z per vertex) over the global
 // vertex numbering of the pair (A's vertices, then B's), so that a
 // neighbour read is one 24-byte load.  Each mesh's vertex adjacency is a
 // CSR with ascending neighbours, built from its sorted edge list.  The
-// neighbour sums run in that ascending order and divide by the degree, so
-// the result is bit-identical to a sequential float64 evaluation.
+// band's vertices are compacted into a list (a flag scan), and the CG state
+// of band vertex i is one 96-byte record (r, w, s per coordinate, 1/deg and
+// its range of neighbour slots) in one of two buffers that alternate by
+// iteration.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "internal.h"
+#include "sortdev.cuh"
 
 namespace hfcr {
 
@@ -179,6 +190,460 @@ __global__ void k_aos_to_soa(const double *u, int n, double *x, double *y, doubl
     z[v] = u[3 * (size_t)v + 2];
 }
 
+// ---- the harmonic field: CG on the band's graph Laplacian ----
+
+constexpr int BAND_TPB = 256;
+constexpr int BAND_MIN_PER_CTA = 32;     // band vertices per CTA taking part, at least
+constexpr int BAND_REC = 12;             // floats per record: r[3] w[3] s[3] 1/deg, first / end slot
+constexpr float BAND_INNER_TOL = 1e-5f;  // residual reduction of one float32 round
+constexpr int BAND_MAX_ROUNDS = 32;
+constexpr long long BAND_SPIN_LIMIT = 1ll << 22;
+
+__device__ __forceinline__ bool band_vertex(const DPair &P, const int *ring, int R, int g) {
+    const int rg = ring[g];
+    if (rg < 1 || rg > R) return false;
+    const DMesh &M = P.of(g);
+    return !(M.inv_mass && M.inv_mass[g - M.off] == 0.f);
+}
+
+// flag of every vertex: 1 in the band (scanned in place into the compact
+// index), then the list of band vertices and the vertex -> index map
+__global__ void k_band_flags(DPair P, const int *ring, int R, unsigned *flags) {
+    HFCR_PDL_WAIT();
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < P.ntot) flags[g] = band_vertex(P, ring, R, g) ? 1u : 0u;
+}
+
+__global__ void k_band_list(DPair P, const int *ring, int R, const unsigned *pos, int *cidx,
+                            int *fv) {
+    HFCR_PDL_WAIT();
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.ntot) return;
+    if (band_vertex(P, ring, R, g)) {
+        cidx[g] = (int)pos[g];
+        fv[pos[g]] = g;
+    } else {
+        cidx[g] = -1;
+    }
+}
+
+struct BandArgs {
+    DPair P;
+    const int *cidx;     // [ntot] index of a band vertex in fv, -1 elsewhere
+    const int *fv;       // [nfree] global id of each band vertex
+    const int *d_nfree;
+    double *u;           // field: Dirichlet values in; the band's solution written at the end
+    double *b64;         // [cap][3] right-hand side (Dirichlet sums), float64
+    double *u64;         // [2][cap][3] float64 solution, alternating by round
+    float *x32, *p32;    // [cap][3] the float32 correction of the round and its search direction
+    float *rec;          // [2][cap][BAND_REC] float32 CG records, alternating by iteration
+    int *cnbr;           // band index of every adjacency slot (-1: Dirichlet), slots of
+    int eoffB;           //   mesh B from eoffB on
+    double *part;        // [2][grid][9] per-CTA partial sums (doubles, or floats in the same space)
+    unsigned *bar;       // grid barrier counter, zeroed before the launch
+    int *ctl;            // [0] CG iterations run, [1] set when a coordinate stopped unconverged
+    uint32_t *status;
+    double tol;
+    int max_iters;
+    int cap;
+};
+
+// Barrier of the `parts` CTAs taking part: an arrival counter, polled
+// without sleeping first (these waits are microseconds), bounded all the
+// same: after the spin limit the CTA records ST_TIMEOUT and every CTA
+// that sees it leaves (the caller then reports HFCR_ERR_TIMEOUT).
+__device__ __forceinline__ bool band_barrier(unsigned *bar, unsigned target, uint32_t *status) {
+    __shared__ int failed;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        failed = 0;
+        // arrival: a release reduction (this CTA's writes, ordered before
+        // the barrier by __syncthreads, become visible with it)
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+        long long spins = 0;
+        while (true) {
+            unsigned seen;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(bar) : "memory");
+            if (seen >= target) break;
+            if (++spins > BAND_SPIN_LIMIT) {
+                atomicOr(status, ST_TIMEOUT);
+                failed = 1;
+                break;
+            }
+            if ((spins & 255) == 0) {
+                if (*(volatile uint32_t *)status & ST_TIMEOUT) { failed = 1; break; }
+                __nanosleep(64);
+            }
+        }
+    }
+    __syncthreads();
+    return failed == 0;
+}
+
+// the nine sums of this CTA's threads to part[9 blockIdx.x ...], fixed
+// order (T float in the inner iterations: float64 arithmetic is scarce on
+// GB300; double for the float64 residual of a round)
+template <typename T>
+__device__ __forceinline__ void band_cta_partials(const T *v, T *part) {
+    __shared__ T sh[BAND_TPB / 32][9];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        T t = v[k];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[w][k] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        T t = 0;
+        for (int q = 0; q < BAND_TPB / 32; ++q) t += sh[q][threadIdx.x];
+        part[9 * blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+// the grid's nine sums from the partials of the `parts` CTAs (written
+// before the barrier): warp w folds sums w and w + 8, lanes striding over
+// the CTAs; the fixed order makes the result identical in every CTA
+template <typename T>
+__device__ __forceinline__ void band_grid_sums(const T *part, int parts, T *out) {
+    __shared__ T sh[9];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = w; k < 9; k += BAND_TPB / 32) {
+        T t = 0;
+        for (int c = lane; c < parts; c += 32) t += __ldcg(part + 9 * c + k);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[k] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 9; ++k) out[k] = sh[k];
+    __syncthreads();
+}
+
+// one float32 record (48 B): r[3] w[3] s[3] 1/deg, then the first and end
+// adjacency slot; read through L2 (written by another CTA before the last
+// barrier; an L1 line of an earlier use of the buffer may be stale)
+struct BandRec {
+    float r[3], w[3], s[3], id;
+    int e0, e1;
+};
+__device__ __forceinline__ BandRec band_load(const float *rec) {
+    const float4 *q = (const float4 *)rec;
+    const float4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
+    BandRec t;
+    t.r[0] = a.x; t.r[1] = a.y; t.r[2] = a.z; t.w[0] = a.w;
+    t.w[1] = b.x; t.w[2] = b.y; t.s[0] = b.z; t.s[1] = b.w;
+    t.s[2] = c.x; t.id = c.y; t.e0 = __float_as_int(c.z); t.e1 = __float_as_int(c.w);
+    return t;
+}
+__device__ __forceinline__ void band_store(float *rec, const float *r, const float *w,
+                                           const float *s, float id, int e0, int e1) {
+    float4 *q = (float4 *)rec;
+    q[0] = make_float4(r[0], r[1], r[2], w[0]);
+    q[1] = make_float4(w[1], w[2], s[0], s[1]);
+    q[2] = make_float4(s[2], id, __int_as_float(e0), __int_as_float(e1));
+}
+
+// The band's Laplacian system L u = b (three right-hand sides, the
+// coordinates) by iterative refinement: each round solves L e = r for the
+// float64 residual r = b - L u with Jacobi-preconditioned CG in float32
+// (the Laplacian's entries, deg and -1, are exact in float32; the
+// Chronopoulos-Gear form, one reduction per iteration) to a reduction of
+// BAND_INNER_TOL, then u += e and the residual is recomputed in float64;
+// until |r| <= tol |b| per coordinate.  GB300's float64 rate is a small
+// fraction of its float32 rate, so only the residual runs in float64.
+//
+// Iteration i of a round reads the record (r_i, w_i = L z_i, s_{i-1}) of
+// every band vertex from buffer i mod 2 and writes (r_{i+1}, w_{i+1}, s_i)
+// of its own vertices to the other; the neighbours' z_{i+1} = (r_i -
+// alpha (w_i + beta s_{i-1})) / deg that w_{i+1} needs are recomputed from
+// their records, so an iteration has one grid-wide barrier (its
+// reduction).  A round's end computes u_new = u + e of its own vertices
+// and the float64 residual from the neighbours' u and e as they stand, so
+// it needs no barrier of its own either.  Band vertex i belongs to CTA i
+// mod parts, so the band spreads over every CTA taking part (the float64
+// work included); the neighbours' band indices are resolved once (cnbr).
+// sum over the band neighbours j (slots e0 .. e1) of f(record j), the
+// records fetched eight at a time so that their loads are in flight
+// together (the neighbour loop is otherwise a chain of dependent L2 loads)
+template <class F>
+__device__ __forceinline__ void band_neighbours(const float *recs, const int *cnbr, int e0, int e1,
+                                                F f) {
+    constexpr int B = 8;
+    for (int base = e0; base < e1; base += B) {
+        int js[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) js[k] = base + k < e1 ? cnbr[base + k] : -1;
+        float4 q0[B], q1[B];
+        float2 q2[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            if (js[k] >= 0) {
+                const float *r = recs + (size_t)BAND_REC * js[k];
+                q0[k] = __ldcg((const float4 *)r);
+                q1[k] = __ldcg((const float4 *)r + 1);
+                q2[k] = __ldcg((const float2 *)(r + 8));
+            }
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            if (js[k] >= 0) {
+                BandRec t;
+                t.r[0] = q0[k].x; t.r[1] = q0[k].y; t.r[2] = q0[k].z; t.w[0] = q0[k].w;
+                t.w[1] = q1[k].x; t.w[2] = q1[k].y; t.s[0] = q1[k].z; t.s[1] = q1[k].w;
+                t.s[2] = q2[k].x; t.id = q2[k].y; t.e0 = t.e1 = 0;
+                f(t);
+            }
+    }
+}
+
+// The band's Laplacian system L u = b (three right-hand sides, the
+// coordinates) by iterative refinement: each round solves L e = r for the
+// float64 residual r = b - L u with Jacobi-preconditioned CG in float32
+// (the Laplacian's entries, deg and -1, are exact in float32; the
+// Chronopoulos-Gear form, one reduction per iteration) to a reduction of
+// BAND_INNER_TOL, then u += e and the residual is recomputed in float64;
+// until |r| <= tol |b| per coordinate.  GB300's float64 rate is a small
+// fraction of its float32 rate, so only the residual (and its norm) runs
+// in float64; the inner iterations reduce in float32.
+//
+// Iteration i of a round reads the record (r_i, w_i = L z_i, s_{i-1}) of
+// every band vertex from buffer i mod 2 and writes (r_{i+1}, w_{i+1}, s_i)
+// of its own vertices to the other; the neighbours' z_{i+1} = (r_i -
+// alpha (w_i + beta s_{i-1})) / deg that w_{i+1} needs are recomputed from
+// their records, so an iteration has one grid-wide barrier (its
+// reduction).  A round's end computes u_new = u + e of its own vertices
+// and the float64 residual from the neighbours' u and e as they stand, so
+// it needs no barrier of its own either.  Band vertex i belongs to CTA i
+// mod parts, so the band spreads over every CTA taking part; the
+// neighbours' band indices are resolved once (cnbr).  All reductions run
+// in a fixed order, so the result is deterministic.
+__global__ void __launch_bounds__(BAND_TPB) k_band_cg(BandArgs a) {
+    HFCR_PDL_WAIT();
+    const int n = *a.d_nfree;
+    int parts = (n + BAND_MIN_PER_CTA - 1) / BAND_MIN_PER_CTA;
+    parts = parts < 1 ? 1 : (parts > (int)gridDim.x ? (int)gridDim.x : parts);
+    if ((int)blockIdx.x >= parts) return;
+    const int i0 = blockIdx.x + parts * threadIdx.x, stride = parts * BAND_TPB;
+    unsigned epoch = 0;
+    float *R0 = a.rec, *R1 = a.rec + (size_t)BAND_REC * a.cap;
+    double *U0 = a.u64, *U1 = a.u64 + 3 * (size_t)a.cap;
+    // partial sums: [2][grid][9] doubles, or as floats in the same space
+    double *const pd0 = a.part, *const pd1 = a.part + (size_t)9 * gridDim.x;
+    double dl[9], ds[9];
+    float fl[9], fs[9];
+    // the right-hand side (Dirichlet values of the neighbours outside the
+    // band), the neighbours' band indices, the first round's records
+    // (r = b, since u = 0), |b|^2
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dl[k] = 0.0;
+    for (int i = i0; i < n; i += stride) {
+        const int g = a.fv[i];
+        const bool inB = g >= a.P.m[1].off;
+        const DMesh &M = inB ? a.P.m[1] : a.P.m[0];
+        const int v = g - M.off;
+        const int e0 = M.ptr[v], e1 = M.ptr[v + 1];
+        const int s0 = (inB ? a.eoffB : 0) + e0;
+        double b[3] = {0.0, 0.0, 0.0};
+        for (int e = e0; e < e1; ++e) {
+            const int w = M.off + M.nbr[e];
+            const int j = a.cidx[w];
+            a.cnbr[s0 + e - e0] = j;
+            if (j < 0) {
+                const double *uw = a.u + 3 * (size_t)w;
+                b[0] += uw[0];
+                b[1] += uw[1];
+                b[2] += uw[2];
+            }
+        }
+        const float rb[3] = {(float)b[0], (float)b[1], (float)b[2]}, z3[3] = {0.f, 0.f, 0.f};
+        // a band vertex has a neighbour one ring closer, so e1 > e0
+        band_store(R0 + (size_t)BAND_REC * i, rb, z3, z3, 1.0f / (float)(e1 - e0), s0,
+                   s0 + e1 - e0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a.b64[3 * (size_t)i + c] = b[c];
+            U0[3 * (size_t)i + c] = 0.0;
+            a.x32[3 * (size_t)i + c] = 0.f;
+            a.p32[3 * (size_t)i + c] = 0.f;
+            dl[6 + c] += b[c] * b[c];
+        }
+    }
+    int pb = 0;  // parity of the partials buffer
+    band_cta_partials(dl, (pb ? pd1 : pd0));
+    if (!band_barrier(a.bar, parts * ++epoch, a.status)) return;
+    band_grid_sums((pb ? pd1 : pd0), parts, ds);
+    pb ^= 1;
+    double target[3];
+    bool act[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        target[c] = a.tol * a.tol * ds[6 + c];
+        act[c] = ds[6 + c] > 0.0;
+    }
+    int it = 0, rounds = 0;
+    int ub = 0;  // U buffer holding the current float64 solution
+    int rb = 0;  // record buffer of the current iteration
+    bool fail = false;
+    while (act[0] || act[1] || act[2]) {
+        if (++rounds > BAND_MAX_ROUNDS) { fail = true; break; }
+        // ---- a round: w_0 = L z_0 and the first sums ----
+        const float *cur = rb ? R1 : R0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) fl[k] = 0.f;
+        for (int i = i0; i < n; i += stride) {
+            float *rec = (rb ? R1 : R0) + (size_t)BAND_REC * i;
+            const BandRec me = band_load(rec);
+            float w[3] = {me.r[0], me.r[1], me.r[2]};
+            band_neighbours(cur, a.cnbr, me.e0, me.e1, [&](const BandRec &nb) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) w[c] -= nb.r[c] * nb.id;
+            });
+            // only w changes (the neighbours read r and 1/deg of this record)
+            rec[3] = w[0];
+            rec[4] = w[1];
+            rec[5] = w[2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                a.x32[3 * (size_t)i + c] = 0.f;
+                a.p32[3 * (size_t)i + c] = 0.f;
+                fl[c] += me.r[c] * me.r[c] * me.id;   // gamma = (r, z)
+                fl[3 + c] += w[c] * me.r[c] * me.id;  // delta = (w, z)
+                fl[6 + c] += me.r[c] * me.r[c];       // rho = |r|^2
+            }
+        }
+        band_cta_partials(fl, (float *)(pb ? pd1 : pd0));
+        if (!band_barrier(a.bar, parts * ++epoch, a.status)) return;
+        band_grid_sums((float *)(pb ? pd1 : pd0), parts, fs);
+        pb ^= 1;
+        float gam[3], alp[3], bet[3], stop[3];
+        bool in[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            gam[c] = fs[c];
+            alp[c] = fs[c] / fs[3 + c];
+            bet[c] = 0.f;
+            stop[c] = BAND_INNER_TOL * BAND_INNER_TOL * fs[6 + c];
+            in[c] = act[c] && fs[6 + c] > 0.f && alp[c] > 0.f && isfinite(alp[c]);
+        }
+        // ---- inner float32 iterations ----
+        const int it_round = it;
+        while ((in[0] || in[1] || in[2]) && it < a.max_iters) {
+            const float *cr = rb ? R1 : R0;
+            float *nx = rb ? R0 : R1;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) fl[k] = 0.f;
+            for (int i = i0; i < n; i += stride) {
+                const BandRec me = band_load(cr + (size_t)BAND_REC * i);
+                float rn[3], sn[3], wn[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (in[c]) {
+                        const float pn = me.r[c] * me.id + bet[c] * a.p32[3 * (size_t)i + c];
+                        sn[c] = me.w[c] + bet[c] * me.s[c];
+                        a.p32[3 * (size_t)i + c] = pn;
+                        a.x32[3 * (size_t)i + c] += alp[c] * pn;
+                        rn[c] = me.r[c] - alp[c] * sn[c];
+                        wn[c] = rn[c];  // deg_v z_{i+1, v}
+                    } else {
+                        sn[c] = me.s[c];
+                        rn[c] = me.r[c];
+                        wn[c] = me.w[c];
+                    }
+                }
+                band_neighbours(cr, a.cnbr, me.e0, me.e1, [&](const BandRec &nb) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        if (in[c]) wn[c] -= (nb.r[c] - alp[c] * (nb.w[c] + bet[c] * nb.s[c])) * nb.id;
+                });
+                band_store(nx + (size_t)BAND_REC * i, rn, wn, sn, me.id, me.e0, me.e1);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    fl[c] += rn[c] * rn[c] * me.id;
+                    fl[3 + c] += wn[c] * rn[c] * me.id;
+                    fl[6 + c] += rn[c] * rn[c];
+                }
+            }
+            rb ^= 1;
+            ++it;
+            band_cta_partials(fl, (float *)(pb ? pd1 : pd0));
+            if (!band_barrier(a.bar, parts * ++epoch, a.status)) return;
+            band_grid_sums((float *)(pb ? pd1 : pd0), parts, fs);
+            pb ^= 1;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (!in[c]) continue;
+                if (fs[6 + c] <= stop[c]) { in[c] = false; continue; }
+                const float b = fs[c] / gam[c];
+                const float al = fs[c] / (fs[3 + c] - b * fs[c] / alp[c]);
+                if (!(al > 0.f && isfinite(al))) { in[c] = false; continue; }
+                bet[c] = b;
+                alp[c] = al;
+                gam[c] = fs[c];
+            }
+        }
+        // ---- the round's end: u += e, the float64 residual, the next
+        // round's records (r = the residual, s = 0; w follows) ----
+        const double *Uc = ub ? U1 : U0;
+        double *Un = ub ? U0 : U1;
+        const float *nr = rb ? R1 : R0;   // the records last written
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dl[k] = 0.0;
+        for (int i = i0; i < n; i += stride) {
+            const BandRec me = band_load(nr + (size_t)BAND_REC * i);
+            double un[3], r64[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                un[c] = __ldcg(Uc + 3 * (size_t)i + c) + (double)__ldcg(a.x32 + 3 * (size_t)i + c);
+                r64[c] = a.b64[3 * (size_t)i + c] - (double)(me.e1 - me.e0) * un[c];
+            }
+            for (int e = me.e0; e < me.e1; ++e) {
+                const int j = a.cnbr[e];
+                if (j < 0) continue;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    r64[c] += __ldcg(Uc + 3 * (size_t)j + c) + (double)__ldcg(a.x32 + 3 * (size_t)j + c);
+            }
+            float rf[3];
+            const float z3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Un[3 * (size_t)i + c] = un[c];
+                rf[c] = act[c] ? (float)r64[c] : 0.f;
+                dl[6 + c] += r64[c] * r64[c];
+            }
+            // written to the buffer the last iteration read: every CTA has
+            // passed the barrier after that read
+            band_store((rb ? R0 : R1) + (size_t)BAND_REC * i, rf, z3, z3, me.id, me.e0, me.e1);
+        }
+        band_cta_partials(dl, (pb ? pd1 : pd0));
+        if (!band_barrier(a.bar, parts * ++epoch, a.status)) return;
+        band_grid_sums((pb ? pd1 : pd0), parts, ds);
+        pb ^= 1;
+        ub ^= 1;
+        rb ^= 1;
+        bool progress = false;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (!act[c]) continue;
+            if (ds[6 + c] <= target[c]) { act[c] = false; continue; }
+            progress = true;
+        }
+        if (progress && (it >= a.max_iters || it == it_round)) { fail = true; break; }
+    }
+    const double *Uf = ub ? U1 : U0;
+    for (int i = i0; i < n; i += stride) {
+        double *ug = a.u + 3 * (size_t)a.fv[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ug[c] = __ldcg(Uf + 3 * (size_t)i + c);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl[0] += it;
+        if (fail) a.ctl[1] = 1;
+    }
+}
+
 inline int blocks(int n) { return (n + 255) / 256; }
 
 DPair make_pair(const DiffMeshArgs &a, const DiffMeshArgs &b) {
@@ -205,20 +670,87 @@ void build_adjacency(const int *edges, int ne, int nv, int *ptr, int *nbr, int *
     { launch_pdl(k_adj_sort, blocks(nv), 256, 0, s, ptr, nv, nbr); note_launch(); }
 }
 
+// co-resident CTAs of k_band_cg on this device (0: no cooperative launch)
+static int band_grid_max() {
+    static int cached[64];
+    static bool done[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 0;
+    if (!done[dev]) {
+        int coop = 0, sms = 0, per = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_band_cg, BAND_TPB, 0);
+        cached[dev] = coop ? sms * (per < 1 ? 0 : 1) : 0;  // one CTA per SM: cheaper barriers
+        done[dev] = true;
+    }
+    return cached[dev];
+}
+
+void diffusion_init() { (void)band_grid_max(); }
+
 const double *diffuse_field(const DiffMeshArgs &a, const DiffMeshArgs &b, double *u, double *u_alt,
-                            int *ring, int rings, int sweeps, cudaStream_t s) {
+                            int *ring, int rings, int sweeps, double tol, int max_iters,
+                            const DiffScratch &ds, SortTemp &t, uint32_t *d_status,
+                            cudaStream_t s) {
     DPair P = make_pair(a, b);
-    if (P.ntot <= 0) return u;
+    if (P.ntot <= 0 || rings <= 0) return u;
     const int far = rings + 1, nb = blocks(P.ntot);
     { launch_pdl(k_ring_init, nb, 256, 0, s, P, u, ring, far); note_launch(); }
     for (int r = 1; r <= rings; ++r) { launch_pdl(k_ring_step, nb, 256, 0, s, P, ring, r,
                                                   far); note_launch(); }
-    double *in = u, *out = u_alt;
-    for (int q = 0; q < sweeps; ++q) {
-        { launch_pdl(k_sweep, nb, 256, 0, s, P, ring, rings, in, out); note_launch(); }
-        double *tmp = in; in = out; out = tmp;
+    if (sweeps > 0) {
+        // the named approximation: a fixed number of Jacobi sweeps from zero
+        double *in = u, *out = u_alt;
+        for (int q = 0; q < sweeps; ++q) {
+            { launch_pdl(k_sweep, nb, 256, 0, s, P, ring, rings, in, out); note_launch(); }
+            double *tmp = in; in = out; out = tmp;
+        }
+        return in;
     }
-    return in;
+    // the harmonic field: the band compacted, then CG on its Laplacian
+    { launch_pdl(k_band_flags, nb, 256, 0, s, P, ring, rings, ds.flags); note_launch(); }
+    scan_flags_dev(ds.flags, nullptr, P.ntot, ds.d_nfree, t, s);
+    { launch_pdl(k_band_list, nb, 256, 0, s, P, ring, rings, (const unsigned *)ds.flags, ds.cidx,
+                 ds.fv); note_launch(); }
+    int grid = band_grid_max();
+    const int want = (P.ntot + 4 * BAND_TPB - 1) / (4 * BAND_TPB);
+    if (grid > want) grid = want;
+    if (grid < 1) {
+        cudaMemsetAsync(ds.ctl + 1, 0xff, sizeof(int), s);  // reported as not converged
+        return u;
+    }
+    BandArgs ba;
+    ba.P = P;
+    ba.cidx = ds.cidx;
+    ba.fv = ds.fv;
+    ba.d_nfree = ds.d_nfree;
+    ba.u = u;
+    ba.b64 = ds.b64;
+    ba.u64 = ds.u64;
+    ba.x32 = ds.x32;
+    ba.p32 = ds.p32;
+    ba.rec = ds.rec;
+    ba.cnbr = ds.cnbr;
+    ba.eoffB = ds.eoffB;
+    ba.part = ds.part;
+    ba.bar = ds.bar;
+    ba.ctl = ds.ctl;
+    ba.status = d_status;
+    ba.tol = tol;
+    ba.max_iters = max_iters;
+    ba.cap = ds.cap;
+    cudaMemsetAsync(ds.bar, 0, sizeof(unsigned), s);
+    void *args[] = {&ba};
+    if (cudaLaunchCooperativeKernel((const void *)k_band_cg, grid, BAND_TPB, args, 0, s) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        cudaMemsetAsync(ds.ctl + 1, 0xff, sizeof(int), s);  // reported as not converged
+        return u;
+    }
+    note_launch();
+    return u;
 }
 
 void apply_field(const hfcr_mesh &A, const hfcr_mesh &B, const int *ring, int rings,

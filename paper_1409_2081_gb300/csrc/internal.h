@@ -255,6 +255,7 @@ struct SolveBuffers {
     double *r64 = nullptr;       // [cap_k]
     float *r32 = nullptr, *x32 = nullptr, *p32 = nullptr, *q32 = nullptr, *w32 = nullptr;  // [cap_k]
     double *p64 = nullptr, *q64 = nullptr;   // p64 [2 cap_k] (x and p), q64 [cap_k] (FP64 solver)
+    double *cg64 = nullptr;      // [5 cap_k] r, p, s, w, z of the float64 per-zone CG
     int4 *vidx = nullptr;        // [cap_k] compact vertex index of each stencil role
     // vertex CSR over 4k entries
     unsigned *ckey = nullptr, *ckey_alt = nullptr;   // [4 cap_k]
@@ -311,11 +312,34 @@ struct DiffMeshArgs {
 // CSR of an edge list: ptr [nv + 1], nbr [2 ne], cur [nv] scratch
 void build_adjacency(const int *edges, int ne, int nv, int *ptr, int *nbr, int *cur, SortTemp &t,
                      uint32_t *d_status, cudaStream_t s);
-// rings and sweeps over u (AoS float64 over A's then B's vertices); returns
-// the buffer holding the result (u or u_alt); ring [a.n + b.n] gets the
-// ring distances (0: moved, rings + 1: beyond)
+// scratch of the harmonic diffusion (capacity cap = vertices of both meshes)
+struct DiffScratch {
+    int cap = 0;
+    unsigned *flags = nullptr;  // [cap] band flags, scanned in place
+    int *cidx = nullptr;        // [cap] band index of a vertex, -1 outside the band
+    int *fv = nullptr;          // [cap] band vertices
+    double *b64 = nullptr;      // [3 cap] right-hand side of the band system
+    double *u64 = nullptr;      // [2 * 3 cap] float64 solution, alternating by round
+    float *x32 = nullptr, *p32 = nullptr;  // [3 cap] float32 correction and search direction
+    float *rec = nullptr;       // [2 * 12 cap] float32 CG records
+    int *cnbr = nullptr;        // band index of every adjacency slot: A's slots, then B's from eoffB
+    int eoffB = 0;
+    double *part = nullptr;     // [2 * 9 * 1024] per-CTA partial sums
+    unsigned *bar = nullptr;    // [1] grid barrier counter
+    int *d_nfree = nullptr;     // band size (device)
+    int *ctl = nullptr;         // [2] CG iterations (accumulated), unconverged flag
+};
+// Diffusion of the field u (AoS float64 over A's then B's vertices) over
+// `rings` rings: the harmonic field (sweeps 0: conjugate gradients to the
+// relative residual tol, at most max_iters iterations) or `sweeps` Jacobi
+// sweeps.  Returns the buffer holding the result (u, or u_alt after an odd
+// number of sweeps); ring [a.n + b.n] gets the ring distances (0: moved,
+// rings + 1: beyond).
 const double *diffuse_field(const DiffMeshArgs &a, const DiffMeshArgs &b, double *u, double *u_alt,
-                            int *ring, int rings, int sweeps, cudaStream_t s);
+                            int *ring, int rings, int sweeps, double tol, int max_iters,
+                            const DiffScratch &ds, SortTemp &t, uint32_t *d_status, cudaStream_t s);
+// one-time device query of the diffusion kernels; call outside stream capture
+void diffusion_init();
 void apply_field(const hfcr_mesh &A, const hfcr_mesh &B, const int *ring, int rings,
                  const double *u, cudaStream_t s);
 void field_from_soa(const double *x, const double *y, const double *z, int n, double *u,

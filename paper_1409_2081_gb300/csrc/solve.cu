@@ -286,7 +286,15 @@ constexpr int ZONE_MID = 256;   // zones with at least this many stencils get al
 constexpr int ZONE_PAIR_SMEM = 112 * 1024;  // k_cg_zone_pair: 2 CTAs per SM, 56 KB per half
 constexpr int ZONE_BIG = 1024;  // zones with at least this many stencils get a 1024-thread CTA
 
-struct CgView {
+// Index types of a view: the global-memory path reads the int arrays as
+// they are; the zone staged in shared memory holds zone-local indices in
+// 16 bits (a staged zone has fewer than 2^16 touched vertices and CSR
+// entries, since shared memory holds at most 227 KB)
+__device__ __forceinline__ int4 as_int4(const int4 &v) { return v; }
+__device__ __forceinline__ int4 as_int4(const ushort4 &v) { return make_int4(v.x, v.y, v.z, v.w); }
+
+template <typename VI, typename IX>
+struct CgViewT {
     float *r, *p, *x, *sv, *w;   // [k]
     float *z;                    // [k] preconditioned residual P^-1 r
     const float4 *pinv;          // [k] row of its group's inverse block (up to 4 columns)
@@ -295,9 +303,9 @@ struct CgView {
     int goff = 0;                // subtracted from gst values (global path)
     float4 *u;                   // [U] M^-1 J^T r per touched vertex (w unused)
     const float4 *n4;            // [k] unit normals (float32)
-    const int4 *vidx;            // [k]
-    const int *seg;              // [U + 1]
-    const int *cval;             // [4 k]
+    const VI *vidx;              // [k]
+    const IX *seg;               // [U + 1]
+    const IX *cval;              // [4 k]
     const float *winv;           // [U]
     int voff = 0, coff = 0, eoff = 0;  // subtracted from vidx, cval and seg values (global path)
     __device__ __forceinline__ float3 nrm(int s) const {
@@ -305,6 +313,8 @@ struct CgView {
         return make_float3(v.x, v.y, v.z);
     }
 };
+typedef CgViewT<int4, int> CgView;                // global memory
+typedef CgViewT<ushort4, uint16_t> CgViewS;       // staged in shared memory
 
 // deterministic block reduction of three sums with a single barrier: warp
 // partials go to red[3 * warp]; after the barrier every warp loads the
@@ -444,7 +454,8 @@ struct HalfGroup {
 };
 
 // z = P^-1 r for the rows of one group (block-Jacobi over rows sharing x0)
-__device__ __forceinline__ void cg_precond_group(const CgView &v, int g) {
+template <class V>
+__device__ __forceinline__ void cg_precond_group(const V &v, int g) {
     const int a = v.gst[g] - v.goff, b = v.gst[g + 1] - v.goff;
     float rr[4];
 #pragma unroll
@@ -455,14 +466,14 @@ __device__ __forceinline__ void cg_precond_group(const CgView &v, int g) {
     }
 }
 
-template <class Gp>
-__device__ __forceinline__ void cg_matvec_vertex(const CgView &v, int U) {
+template <class Gp, class V>
+__device__ __forceinline__ void cg_matvec_vertex(const V &v, int U) {
     const float third = 1.0f / 3.0f;
     for (int j = Gp::rank(); j < U; j += Gp::size()) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        const int e1 = v.seg[j + 1] - v.eoff;
-        for (int e = v.seg[j] - v.eoff; e < e1; ++e) {
-            int c = v.cval[e] - v.coff;
+        const int e1 = (int)v.seg[j + 1] - v.eoff;
+        for (int e = (int)v.seg[j] - v.eoff; e < e1; ++e) {
+            int c = (int)v.cval[e] - v.coff;
             int s = c >> 2;
             float ps = ((c & 3) ? -third : 1.0f) * v.z[s];
             float3 n = v.nrm(s);
@@ -475,9 +486,10 @@ __device__ __forceinline__ void cg_matvec_vertex(const CgView &v, int U) {
     }
 }
 
-__device__ __forceinline__ float cg_matvec_stencil(const CgView &v, int s) {
+template <class V>
+__device__ __forceinline__ float cg_matvec_stencil(const V &v, int s) {
     const float third = 1.0f / 3.0f;
-    int4 g = v.vidx[s];
+    int4 g = as_int4(v.vidx[s]);
     g.x -= v.voff; g.y -= v.voff; g.z -= v.voff; g.w -= v.voff;
     float3 n = v.nrm(s);
     float4 u0 = v.u[g.x], u1 = v.u[g.y], u2 = v.u[g.z], u3 = v.u[g.w];
@@ -492,8 +504,8 @@ __device__ __forceinline__ float cg_matvec_stencil(const CgView &v, int s) {
 // iteration): u = P^-1 r, w = A u, s = A p by recurrence.  P is the
 // block-Jacobi preconditioner over the groups.  Stops when |r| <= tol |r0|.
 // Returns the iteration count; x holds the solution of A x = r0.
-template <class Gp>
-__device__ __forceinline__ int cg_cg_loop(const CgView &v, int k, int U, int maxit, float tol,
+template <class Gp, class V>
+__device__ __forceinline__ int cg_cg_loop(const V &v, int k, int U, int maxit, float tol,
                                           float *red) {
     const int tid = Gp::rank(), nt = Gp::size();
     for (int g = tid; g < v.G; g += nt) cg_precond_group(v, g);
@@ -878,17 +890,17 @@ __global__ void k_group_inverse(const int *d_ng, const int *gst, const int4 *ids
 // Eq. 7), written to v.r in float32 as the next right-hand side.  The
 // vertex half goes through u64 (global scratch, this zone's rows only).
 // Returns |r|^2, identical in every thread.
-template <class Gp>
-__device__ __forceinline__ double zone_residual(const CgView &v, int k, int U, int s0, int j0,
+template <class Gp, class V>
+__device__ __forceinline__ double zone_residual(const V &v, int k, int U, int s0, int j0,
                                                 const double4_32a *n64, const double *b64,
                                                 const double *lam, double *u64, double *redd) {
     const int tid = Gp::rank(), nt = Gp::size();
     const double third = 1.0 / 3.0;
     for (int j = tid; j < U; j += nt) {
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        const int e1 = v.seg[j + 1] - v.eoff;
-        for (int e = v.seg[j] - v.eoff; e < e1; ++e) {
-            const int c = v.cval[e] - v.coff;
+        const int e1 = (int)v.seg[j + 1] - v.eoff;
+        for (int e = (int)v.seg[j] - v.eoff; e < e1; ++e) {
+            const int c = (int)v.cval[e] - v.coff;
             const int sl = c >> 2;
             const double ps = ((c & 3) ? -third : 1.0) * lam[s0 + sl];
             const double4_32a n = n64[s0 + sl];
@@ -905,7 +917,7 @@ __device__ __forceinline__ double zone_residual(const CgView &v, int k, int U, i
     Gp::sync();
     double rr = 0.0;
     for (int t = tid; t < k; t += nt) {
-        const int4 g = v.vidx[t];
+        const int4 g = as_int4(v.vidx[t]);
         const double *ux = u64 + 3 * (size_t)(j0 + g.x - v.voff);
         const double *ua = u64 + 3 * (size_t)(j0 + g.y - v.voff);
         const double *ub = u64 + 3 * (size_t)(j0 + g.z - v.voff);
@@ -950,9 +962,12 @@ __device__ __forceinline__ double zone_start(const ZoneArgs &a, int s0, int k, d
     return Gp::sum(bb, redd);
 }
 
-// shared memory a zone needs for the staged solve
+// shared memory a zone needs for the staged solve: per row the float32
+// normal, the preconditioner row, six CG vectors, four 16-bit CSR entries
+// and 16-bit vertex ids (72 B); per touched vertex u, the inverse mass and
+// a 16-bit CSR offset (22 B); per group its first row; alignment slack
 __device__ __forceinline__ long long zone_smem_need(int k, int U, int G) {
-    return 92ll * k + 24ll * U + 4ll * G + 32;
+    return 72ll * k + 22ll * U + 4ll * G + 48;
 }
 
 struct ZoneResult {
@@ -972,30 +987,31 @@ __device__ __forceinline__ ZoneResult solve_zone_smem(const ZoneArgs &a, int z, 
     const int g0 = a.zg[z], G = a.zg[z + 1] - g0;
     const int e0 = a.seg[j0];
     const double target = a.rel_tol * a.rel_tol * bb;
-    CgView v;
-    // layout: vidx | n4 | pinv | u | r p x sv w z | seg | cval | winv | gst
-    int4 *vidx = (int4 *)base;
-    float4 *n4 = (float4 *)(vidx + k);
+    CgViewS v;
+    // layout: n4 | pinv | u | r p x sv w z | winv | gst | vidx (16-bit) | seg (16-bit) | cval (16-bit)
+    float4 *n4 = (float4 *)base;
     float4 *pinv = n4 + k;
     v.u = pinv + k;
     float *f = (float *)(v.u + U);
     v.r = f; v.p = f + k; v.x = f + 2 * k; v.sv = f + 3 * k; v.w = f + 4 * k; v.z = f + 5 * k;
-    int *seg = (int *)(f + 6 * k);
-    int *cval = seg + U + 1;
-    float *winv = (float *)(cval + 4 * k);
+    float *winv = f + 6 * k;
     int *gst = (int *)(winv + U);
+    ushort4 *vidx = (ushort4 *)(((uintptr_t)(gst + G + 1) + 7) & ~(uintptr_t)7);
+    uint16_t *seg = (uint16_t *)(vidx + k);
+    uint16_t *cval = seg + U + 1;
     for (int t = tid; t < k; t += nt) {
         const int4 g = a.vidx[s0 + t];
-        vidx[t] = make_int4(g.x - j0, g.y - j0, g.z - j0, g.w - j0);
+        vidx[t] = make_ushort4((unsigned short)(g.x - j0), (unsigned short)(g.y - j0),
+                               (unsigned short)(g.z - j0), (unsigned short)(g.w - j0));
         n4[t] = a.n32[s0 + t];
         pinv[t] = a.pinv[s0 + t];
         v.r[t] = (float)a.b64[s0 + t];
     }
     for (int g = tid; g <= G; g += nt) gst[g] = a.gst[g0 + g] - s0;
     v.pinv = pinv; v.gst = gst; v.G = G; v.goff = 0;
-    for (int j = tid; j <= U; j += nt) seg[j] = a.seg[j0 + j] - e0;
+    for (int j = tid; j <= U; j += nt) seg[j] = (uint16_t)(a.seg[j0 + j] - e0);
     for (int j = tid; j < U; j += nt) winv[j] = a.winv[j0 + j];
-    for (int e = tid; e < 4 * k; e += nt) cval[e] = a.cval[e0 + e] - 4 * s0;
+    for (int e = tid; e < 4 * k; e += nt) cval[e] = (uint16_t)(a.cval[e0 + e] - 4 * s0);
     v.n4 = n4;
     v.vidx = vidx; v.seg = seg; v.cval = cval; v.winv = winv;
     v.voff = 0; v.coff = 0; v.eoff = 0;
@@ -1035,7 +1051,7 @@ __device__ __forceinline__ void zone_finish(const ZoneArgs &a, int z, double rr,
 // small mesh pairs): a 256-thread CTA runs eight of them side by side, each
 // in its own WARP_ZONE_SMEM slice of shared memory.
 constexpr int WARP_ZONE = 32;
-constexpr int WARP_ZONE_SMEM = 6272;  // zone_smem_need(32, 128, 32) rounded up to 16 B
+constexpr int WARP_ZONE_SMEM = 6272;  // at least zone_smem_need(32, 128, 32), a multiple of 16 B
 constexpr int WARP_ZONE_WARPS = 8;
 
 __global__ void __launch_bounds__(256, 4) k_cg_zone_warp(const int *d_nz, ZoneArgs a) {
@@ -1187,6 +1203,192 @@ __global__ void __launch_bounds__(THREADS, 1) k_cg_zone(const int *d_nz, ZoneArg
         const int k = a.zs[z + 1] - a.zs[z];
         if (k <= k_lo) continue;
         solve_zone<CtaGroup>(a, z, (char *)smem4, smem_bytes, red, redd, g);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The plain float64 form's per-zone solve: the same impact zones,
+// zone-ordered rows, vertex CSR and block-Jacobi groups as the mixed
+// solver, each zone solved by one 256-thread CTA with preconditioned CG in
+// the Chronopoulos-Gear form, in float64 on the float64 normals, on global
+// (L2-resident) arrays, to |r_zone| <= rel_tol |b_zone| (no refinement: the
+// arithmetic is already float64).
+// ---------------------------------------------------------------------------
+
+struct Zone64Scratch {
+    double *r, *p, *s, *w, *z;  // [cap_k] each, zone-ordered rows
+};
+
+constexpr int ZONE64_THREADS = 256;
+
+// three block sums with one barrier, identical in every thread (the
+// float64 counterpart of block_sum3)
+__device__ __forceinline__ void block_sum3d(double a, double b, double c, double *red, double &sa,
+                                            double &sb_, double &sc) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();  // red is free of its previous use
+    if (lane == 0) {
+        red[3 * w] = a;
+        red[3 * w + 1] = b;
+        red[3 * w + 2] = c;
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    double x = lane < nw ? red[3 * lane] : 0.0;
+    double y = lane < nw ? red[3 * lane + 1] : 0.0;
+    double q = lane < nw ? red[3 * lane + 2] : 0.0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    sa = __shfl_sync(0xffffffffu, x, 0);
+    sb_ = __shfl_sync(0xffffffffu, y, 0);
+    sc = __shfl_sync(0xffffffffu, q, 0);
+}
+
+// out = J M^-1 J^T in over the zone's rows (u: the zone's touched
+// vertices, 3 doubles each); returns nothing, the caller synchronises
+__device__ __forceinline__ void zone64_vertex(const ZoneArgs &a, int s0, int j0, int U,
+                                              const double *in, double *u) {
+    const double third = 1.0 / 3.0;
+    for (int j = threadIdx.x; j < U; j += blockDim.x) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int e = a.seg[j0 + j]; e < a.seg[j0 + j + 1]; ++e) {
+            const int c = a.cval[e] - 4 * s0;
+            const int sl = c >> 2;
+            const double ps = ((c & 3) ? -third : 1.0) * in[sl];
+            const double4_32a n = a.n64[s0 + sl];
+            a0 += ps * n.x;
+            a1 += ps * n.y;
+            a2 += ps * n.z;
+        }
+        const double wv = (double)a.winv[j0 + j];
+        u[3 * j] = wv * a0;
+        u[3 * j + 1] = wv * a1;
+        u[3 * j + 2] = wv * a2;
+    }
+}
+
+__device__ __forceinline__ double zone64_stencil(const ZoneArgs &a, int s0, int j0, int t,
+                                                 const double *u) {
+    const double third = 1.0 / 3.0;
+    const int4 g = a.vidx[s0 + t];
+    const double *ux = u + 3 * (g.x - j0), *ua = u + 3 * (g.y - j0), *ub = u + 3 * (g.z - j0),
+                 *uc = u + 3 * (g.w - j0);
+    const double4_32a n = a.n64[s0 + t];
+    return n.x * (ux[0] - (ua[0] + ub[0] + uc[0]) * third) +
+           n.y * (ux[1] - (ua[1] + ub[1] + uc[1]) * third) +
+           n.z * (ux[2] - (ua[2] + ub[2] + uc[2]) * third);
+}
+
+// z = P^-1 r over the zone's groups (the float32-stored inverse blocks)
+__device__ __forceinline__ void zone64_precond(const ZoneArgs &a, int s0, int g0, int G,
+                                               const double *r, double *zz) {
+    for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
+        const int lo = a.gst[g0 + gi] - s0, hi = a.gst[g0 + gi + 1] - s0;
+        double rr[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rr[q] = lo + q < hi ? r[lo + q] : 0.0;
+        for (int t = lo; t < hi; ++t) {
+            const float4 m = a.pinv[s0 + t];
+            zz[t] = (double)m.x * rr[0] + (double)m.y * rr[1] + (double)m.z * rr[2] + (double)m.w * rr[3];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(ZONE64_THREADS) k_cg_zone64(const int *d_nz, ZoneArgs a,
+                                                              Zone64Scratch g, int maxit) {
+    HFCR_PDL_WAIT();
+    __shared__ double red[3 * (ZONE64_THREADS / 32)];
+    __shared__ double redd[ZONE64_THREADS / 32];
+    const int nz = *d_nz;
+    for (int z = blockIdx.x; z < nz; z += gridDim.x) {
+        const int s0 = a.zs[z], k = a.zs[z + 1] - s0;
+        const int j0 = a.zv[z], U = a.zv[z + 1] - j0;
+        const int g0 = a.zg[z], G = a.zg[z + 1] - g0;
+        const double bb = zone_start<CtaGroup>(a, s0, k, redd);  // lam = 0 on the zone's rows
+        double *r = g.r + s0, *p = g.p + s0, *sv = g.s + s0, *w = g.w + s0, *zz = g.z + s0;
+        double *x = a.lam + s0, *u = a.u64 + 3 * (size_t)j0;
+        for (int t = threadIdx.x; t < k; t += blockDim.x) {
+            r[t] = a.b64[s0 + t];
+            p[t] = 0.0;
+            sv[t] = 0.0;
+        }
+        __syncthreads();
+        zone64_precond(a, s0, g0, G, r, zz);
+        __syncthreads();
+        zone64_vertex(a, s0, j0, U, zz, u);
+        __syncthreads();
+        double ga = 0.0, de = 0.0, rh = 0.0;
+        for (int t = threadIdx.x; t < k; t += blockDim.x) {
+            const double wt = zone64_stencil(a, s0, j0, t, u);
+            w[t] = wt;
+            ga += r[t] * zz[t];
+            de += wt * zz[t];
+            rh += r[t] * r[t];
+        }
+        double gamma, delta, rho;
+        block_sum3d(ga, de, rh, red, gamma, delta, rho);
+        const double stop = a.rel_tol * a.rel_tol * bb;
+        double alpha = gamma / delta, beta = 0.0;
+        int it = 0;
+        while (it < maxit && rho > stop && alpha > 0.0 && isfinite(alpha)) {
+            for (int t = threadIdx.x; t < k; t += blockDim.x) {
+                const double pt = zz[t] + beta * p[t];
+                const double st = w[t] + beta * sv[t];
+                p[t] = pt;
+                sv[t] = st;
+                x[t] += alpha * pt;
+                r[t] -= alpha * st;
+            }
+            __syncthreads();
+            zone64_precond(a, s0, g0, G, r, zz);
+            __syncthreads();
+            zone64_vertex(a, s0, j0, U, zz, u);
+            __syncthreads();
+            ga = de = rh = 0.0;
+            for (int t = threadIdx.x; t < k; t += blockDim.x) {
+                const double wt = zone64_stencil(a, s0, j0, t, u);
+                w[t] = wt;
+                ga += r[t] * zz[t];
+                de += wt * zz[t];
+                rh += r[t] * r[t];
+            }
+            double gn, dn, rn;
+            block_sum3d(ga, de, rh, red, gn, dn, rn);
+            beta = gn / gamma;
+            alpha = gn / (dn - beta * gn / alpha);
+            gamma = gn;
+            rho = rn;
+            ++it;
+        }
+        // the zone's true residual b - A lam (not the recurrence's)
+        __syncthreads();
+        zone64_vertex(a, s0, j0, U, x, u);
+        __syncthreads();
+        double rr = 0.0;
+        for (int t = threadIdx.x; t < k; t += blockDim.x) {
+            const double rt = a.b64[s0 + t] - zone64_stencil(a, s0, j0, t, u);
+            rr += rt * rt;
+        }
+        rr = block_sum_uniform(rr, redd);
+        if (threadIdx.x == 0) {
+            a.zres[z] = rr;
+            a.zbb[z] = bb;
+            atomicAdd(&a.ctl[1], it);
+            atomicAdd(&a.ctl[2], 1);
+            atomicMax(&a.ctl[3], 1);
+            atomicOr(&a.ctl[4], 4);
+        }
+        __syncthreads();  // u and the scalars' shared words are reused by the next zone
     }
 }
 
@@ -2021,6 +2223,27 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
     if (rb > RES_BLOCKS) rb = RES_BLOCKS;
     // sb.iwork and sb.dwork were zeroed with the call's other device words
     if (p.solver == HFCR_SOLVER_FP64) {
+        // the plain float64 form: every impact zone by its own CTA, float64
+        // CG with the whole iteration budget of the mixed solver
+        ZoneArgs za;
+        za.zs = sb.zs; za.zv = sb.zv; za.zg = sb.zg;
+        za.seg = sb.seg; za.cval = sb.cval_s; za.winv = sb.winv;
+        za.n32 = sb.n32; za.pinv = sb.pinv; za.n64 = sb.n64; za.vidx = sb.vidx; za.gst = sb.gst;
+        za.b64 = sb.b; za.lam = sb.lam; za.u64 = sb.u64; za.zres = sb.r64; za.zbb = sb.q64;
+        za.maxit = p.max_cg_iters; za.max_refine = p.max_refine;
+        za.tol = p.inner_tol; za.rel_tol = p.rel_tol; za.ctl = sb.iwork;
+        za.ticket = (unsigned *)(sb.iwork + 13);
+        Zone64Scratch g64;
+        g64.r = sb.cg64; g64.p = sb.cg64 + cap; g64.s = sb.cg64 + 2 * (size_t)cap;
+        g64.w = sb.cg64 + 3 * (size_t)cap; g64.z = sb.cg64 + 4 * (size_t)cap;
+        int zg = cap < 4 * 152 ? cap : 4 * 152;
+        { launch_pdl(k_cg_zone64, zg, ZONE64_THREADS, 0, s, sb.d_nz, za, g64,
+                     p.max_cg_iters * p.max_refine); note_launch(); }
+        { launch_pdl(k_zone_final, 1, 256, 0, s, sb.d_nz, sb.r64, sb.q64, p.rel_tol, sb.dwork,
+                     sb.iwork); note_launch(); }
+        return;
+    }
+    if (p.solver == HFCR_SOLVER_FP64_GLOBAL) {
         // one float64 run with the whole iteration budget of the mixed solver
         { launch_pdl(k_init_lam, rb, 256, 0, s, d_k, sb.b, sb.lam, sb.r64); note_launch(); }
         { launch_pdl(k_cg<double>, 1, CG_THREADS, 0, s, 1, d_k, sb.d_U, sb.seg, sb.cval_s,

@@ -123,15 +123,16 @@ def test_batch_resolve_leaves_no_pair(api):
 
 
 def test_batch_resolve_with_diffusion_deep_overlaps(api):
-    # deeper overlaps (centre distance 1.35..1.6 radii): the diffusion of Sec. 5
-    # spreads each pair's displacement over its own mesh only (the
+    # deeper overlaps (centre distance 1.35..1.6 radii): the harmonic diffusion
+    # of Sec. 5 spreads each pair's displacement over its own mesh only (the
     # concatenated meshes have no edge between pairs), and the batched loop
     # ends with no pair left
     scenes = meshgen.scene_c4(n_pairs=12, lmax=3, seed=meshgen.BASE_SEED + 34, rho_lo=1.35, rho_hi=1.6)
     A, PA, TA, B, PB, TB, segs, dsegs = _batch(api, scenes)
-    ctx = api.Context(diffuse_rings=4, diffuse_sweeps=16)
+    ctx = api.Context(diffuse_rings=4)
     ctx.hfcr_reserve(max(len(PA), len(PB)), max(len(TA), len(TB)), 1 << 17)
     info = ctx.hfcr_resolve_batch(A, B, dsegs, 1e-4, 64)
+    assert info.diffuse_unconverged == 0
     assert info.pairs_first > 0
     assert info.converged, (info.iters, info.pairs_last)
     fA, fB = positions(A), positions(B)

@@ -73,7 +73,7 @@ def _scene_parity(api, sc, solver, f32_filter, d=1e-4):
     return n, k, err, stats
 
 
-@pytest.mark.parametrize("solver", [0, 1], ids=["mixed", "fp64"])
+@pytest.mark.parametrize("solver", [0, 1, 2], ids=["mixed", "fp64", "fp64_global"])
 @pytest.mark.parametrize("seed,kind", [(31, "spheres"), (32, "torus_sphere"), (33, "cloth_sphere"),
                                        (34, "spheres")])
 def test_small_scenes(api, seed, kind, solver):
@@ -85,7 +85,7 @@ def test_small_scenes_without_f32_filter(api, seed, kind):
     _scene_parity(api, meshgen.scene_random_small(seed, kind), 0, False)
 
 
-@pytest.mark.parametrize("solver", [0, 1], ids=["mixed", "fp64"])
+@pytest.mark.parametrize("solver", [0, 1, 2], ids=["mixed", "fp64", "fp64_global"])
 def test_two_icospheres_fp64(api, solver):
     """Two jittered level-3 icospheres offset by 1.5, float64 positions."""
     n, k, err, st = _scene_parity(api, meshgen.scene_c1(), solver, True)

@@ -9,7 +9,9 @@ with another strip.  Every row has its own x0, so the system is positive
 definite.  Zone sizes: 20 stencils (one warp), 100 (a 256-thread half
 CTA), 600 (a whole 512-thread CTA), 1,500 (a 1,024-thread CTA), and 700
 zones of 40 stencils (more zones than the half-CTA solvers, so they are
-handed out by the counter)."""
+handed out by the counter).  The same system through the float64 per-zone
+solver of the plain float64 form (one CTA per zone, every size) and the
+one-CTA global float64 CG, on float64 positions."""
 import numpy as np
 import pytest
 
@@ -52,7 +54,10 @@ def strips(sizes, rng):
     return V, np.array(T, np.int32), first
 
 
-def test_zone_size_classes_against_oracle(api):
+@pytest.mark.parametrize("solver,dtype,tol", [(0, np.float32, TOL_DX), (1, np.float64, 1e-9),
+                                              (2, np.float64, 1e-9)],
+                         ids=["mixed", "fp64_per_zone", "fp64_global"])
+def test_zone_size_classes_against_oracle(api, solver, dtype, tol):
     import torch
     rng = np.random.default_rng(1409)
     sizes = [20, 20, 20, 100, 100, 100, 600, 600, 1500] + [40] * 700
@@ -63,17 +68,17 @@ def test_zone_size_classes_against_oracle(api):
     cen = VB[TB].mean(axis=1)
     VA = cen + np.array([0.0, 0.0, -0.02]) + rng.uniform(-0.005, 0.005, (k, 3))
     TA = np.array([[0, 1, 2]], np.int32)
-    A, PA = dev_mesh(api, VA, TA, False, np.float32)
-    B, PB = dev_mesh(api, VB, TB, True, np.float32)
+    A, PA = dev_mesh(api, VA, TA, False, dtype)
+    B, PB = dev_mesh(api, VB, TB, True, dtype)
     st = np.zeros((k, 4), np.int32)
     st[:, 1] = np.arange(k)      # x0 (dir 0: a vertex of A)
     st[:, 2] = np.arange(k)      # its face of B
-    ctx = api.Context()
+    ctx = api.Context(solver=solver)
     ctx.hfcr_reserve(max(len(VA), len(VB)), max(len(TA), len(TB)), 1 << 16)
     st_t = torch.tensor(st, device="cuda:0")
-    g, info = respond(ctx, A, B, st_t, k, 1e-4, len(VA), len(VB), np.float32)
-    assert info.converged and info.n_stencils == k
+    g, info = respond(ctx, A, B, st_t, k, 1e-4, len(VA), len(VB), dtype)
+    assert info.converged and info.n_stencils == k and info.rel_residual <= 1e-12
     rA, rB, _, sol = oracle.respond(st[:, :3].astype(np.uint32), PA, TA, PB, TB, 1e-4)
-    assert rel_err(g, np.concatenate([rA, rB])) <= TOL_DX
+    assert rel_err(g, np.concatenate([rA, rB])) <= tol
     # every zone of the system is one strip (the oracle's union-find)
     assert sol.n_zones == len(sizes)

@@ -1,0 +1,189 @@
+"""Parity at the sizes and in the calls the benchmark times.
+
+* The cloth (200 x 200) / torus (256 x 128) frame: one hfcr_resolve
+  iteration, graph-replayed, from the initial positions, against
+  x + oracle.respond(oracle.stencils(oracle.detect(x))) rounded to float32.
+* The 1,024-pair batch: one hfcr_resolve_batch iteration (direction 0, the
+  first of the alternating roles) against the oracle pair by pair, and the
+  response to both directions' stencils (hfcr_respond) against the oracle.
+* The 300-frame sequence (512 x 512 cloth over the level-7 body, one
+  repair iteration per frame with the harmonic diffusion of Sec. 5): at
+  frames 0, 149 and 299 the GPU's pairs and stencils equal the brute-force
+  oracle's on the GPU's own positions (Sec. 3, exact), its displacement is
+  within 1e-6 of the oracle's minimizer, and the positions after the frame's
+  response equal the oracle's response + harmonic diffusion from the same
+  positions.
+
+Displacements: |dx_gpu - dx_oracle|_inf <= 1e-6 |dx_oracle|_inf.
+Positions (float32): within that plus 4 float32 ulps of the largest
+coordinate (the rounding of x + dx on either side)."""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+from gpu_util import dev_mesh, positions, rel_err
+
+pytestmark = pytest.mark.gpu
+
+D_POST = 1e-4
+
+
+@pytest.fixture(scope="module")
+def api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_2081_gb300 import api as a
+    a.lib()
+    return a
+
+
+def _pos_tol(dx_scale, *P):
+    return 1e-6 * dx_scale + 4 * float(np.spacing(np.float32(max(np.abs(p).max() for p in P))))
+
+
+def test_cloth_torus_frame_resolve(api):
+    import torch
+    sc = meshgen.scene_c2()
+    A, PA = dev_mesh(api, sc.A.V, sc.A.T, False, np.float32, edges=True)
+    B, PB = dev_mesh(api, sc.B.V, sc.B.T, True, np.float32)
+    ref = oracle.detect(PA, sc.A.T, False, PB, sc.B.T, True)
+    st = oracle.stencils(ref)
+    dA, dB, _, _ = oracle.respond(st, PA, sc.A.T, PB, sc.B.T, D_POST)
+    eA = (PA + dA).astype(np.float32).astype(np.float64)
+    eB = (PB + dB).astype(np.float32).astype(np.float64)
+    # graphs on (the default), as timed; on the legacy default stream the
+    # library captures on a stream of its own
+    ctx = api.Context()
+    ctx.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), 1 << 16)
+    for rep in range(2):         # the captured graph, then its replay
+        for m, P in ((A, PA), (B, PB)):
+            for c, t in enumerate((m.x, m.y, m.z)):
+                t.copy_(torch.tensor(np.ascontiguousarray(P[:, c].astype(np.float32)), device=t.device))
+        info = ctx.hfcr_resolve(A, B, D_POST, 1)
+        assert info.pairs_first == len(ref) and info.total_stencils == len(st)
+        gA, gB = positions(A), positions(B)
+        tol = _pos_tol(max(np.abs(dA).max(), np.abs(dB).max()), PA, PB)
+        assert np.abs(gA - eA).max() <= tol and np.abs(gB - eB).max() <= tol, rep
+
+
+def _batch(api, scenes):
+    import torch
+    VA, TA, VB, TB, segs = meshgen.concat_batch(scenes)
+    A, PA = dev_mesh(api, VA, TA, True, np.float32, edges=True)
+    B, PB = dev_mesh(api, VB, TB, True, np.float32, edges=True)
+    return A, PA, TA, B, PB, TB, segs, torch.tensor(segs, device="cuda:0")
+
+
+def _oracle_batch(scenes, segs, PA, PB, dirs):
+    """Pairs of every mesh pair (global ids within the concatenations),
+    sorted by (dir, v0, v1, face), with their sides."""
+    recs, sides = [], []
+    for i, sc in enumerate(scenes):
+        a0, b0 = segs[i, 0], segs[i, 2]
+        pr = oracle.detect(PA[a0:segs[i + 1, 0]], sc.A.T, 1 in dirs, PB[b0:segs[i + 1, 2]], sc.B.T,
+                           0 in dirs)
+        r = pr.rec.astype(np.int64)
+        for d, ev, ef in ((0, a0, segs[i, 3]), (1, b0, segs[i, 1])):
+            m = r[:, 0] == d
+            r[m, 1] += ev
+            r[m, 2] += ev
+            r[m, 3] += ef
+        recs.append(r)
+        sides.append(pr.side)
+    rec = np.concatenate(recs)
+    side = np.concatenate(sides)
+    o = np.lexsort((rec[:, 3], rec[:, 2], rec[:, 1], rec[:, 0]))
+    return oracle.Pairs(rec[o].astype(np.uint32), side[o])
+
+
+def test_batch_one_iteration_and_full_respond(api):
+    import torch
+    scenes = meshgen.scene_c4()
+    A, PA, TA, B, PB, TB, segs, dsegs = _batch(api, scenes)
+    # the timed call: one iteration of the alternating roles = direction 0
+    pr0 = _oracle_batch(scenes, segs, PA, PB, (0,))
+    st0 = oracle.stencils(pr0)
+    dA, dB, _, _ = oracle.respond(st0, PA, TA, PB, TB, D_POST)
+    ctx = api.Context()
+    ctx.hfcr_reserve(max(len(PA), len(PB)), max(len(TA), len(TB)), 1 << 21)
+    info = ctx.hfcr_resolve_batch(A, B, dsegs, D_POST, 1)
+    assert info.pairs_first == len(pr0) and info.total_stencils == len(st0)
+    gA, gB = positions(A), positions(B)
+    eA = (PA + dA).astype(np.float32).astype(np.float64)
+    eB = (PB + dB).astype(np.float32).astype(np.float64)
+    tol = _pos_tol(max(np.abs(dA).max(), np.abs(dB).max()), PA, PB)
+    assert np.abs(gA - eA).max() <= tol and np.abs(gB - eB).max() <= tol
+    # both directions' stencils of the initial positions through hfcr_respond
+    for m, P in ((A, PA), (B, PB)):
+        for c, t in enumerate((m.x, m.y, m.z)):
+            t.copy_(torch.tensor(np.ascontiguousarray(P[:, c].astype(np.float32)), device=t.device))
+    pr = _oracle_batch(scenes, segs, PA, PB, (0, 1))
+    st = oracle.stencils(pr)
+    out = torch.zeros((1 << 21, 4), dtype=torch.int32, device="cuda:0")
+    n = ctx.hfcr_detect_batch(A, B, dsegs, out)
+    assert n == len(pr) and np.array_equal(out[:n].cpu().numpy().astype(np.uint32), pr.rec)
+    sbuf = torch.zeros((1 << 21, 4), dtype=torch.int32, device="cuda:0")
+    k = ctx.hfcr_build_stencils(A, B, out, n, sbuf)
+    assert k == len(st) and np.array_equal(sbuf[:k, :3].cpu().numpy().astype(np.uint32), st)
+    assert k > 50000
+    rA, rB, _, _ = oracle.respond(st, PA, TA, PB, TB, D_POST)
+    dxA = [torch.zeros(len(PA), dtype=torch.float32, device="cuda:0") for _ in range(3)]
+    dxB = [torch.zeros(len(PB), dtype=torch.float32, device="cuda:0") for _ in range(3)]
+    si = ctx.hfcr_respond(A, B, sbuf, k, D_POST, dxA, dxB)
+    assert si.converged
+    g = np.concatenate([torch.stack(dxA, 1).cpu().numpy(), torch.stack(dxB, 1).cpu().numpy()])
+    r = np.concatenate([rA, rB])
+    # float32 outputs: the float64 result rounded once
+    assert rel_err(g.astype(np.float64), r) <= 1e-6 + 2 ** -23
+
+
+def test_frame_sequence_sampled_frames(api):
+    import torch
+    sc = meshgen.scene_c5()
+    mot = sc.meta["motion"]
+    A, _ = dev_mesh(api, sc.A.V, sc.A.T, False, np.float32, edges=True)
+    B, _ = dev_mesh(api, sc.B.V, sc.B.T, True, np.float32, edges=True)
+    EA, EB = oracle.edges(sc.A.T), oracle.edges(sc.B.T)
+    params = mot.device_params(torch, A.x.device)
+    R = 4
+    ctx = api.Context(diffuse_rings=R)     # the harmonic field, as timed
+    ctx.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), 1 << 18)
+    cap = 1 << 18
+    ctx64 = api.Context()   # the float64 widening of the same positions: dx in float64
+    ctx64.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), cap)
+    pbuf = torch.zeros((cap, 4), dtype=torch.int32, device="cuda:0")
+    sbuf = torch.zeros((cap, 4), dtype=torch.int32, device="cuda:0")
+    checked = []
+    for f in range(300):
+        mot.advance(torch, params, A.x, A.y, A.z, f)
+        if f in (0, 149, 299):
+            PA, PB = positions(A), positions(B)
+            ref = oracle.detect(PA, sc.A.T, False, PB, sc.B.T, True)
+            n = ctx.hfcr_detect(A, B, pbuf)
+            assert n == len(ref) and np.array_equal(pbuf[:n].cpu().numpy().astype(np.uint32), ref.rec), f
+            st = oracle.stencils(ref)
+            k = ctx.hfcr_build_stencils(A, B, pbuf, n, sbuf)
+            assert k == len(st) and np.array_equal(sbuf[:k, :3].cpu().numpy().astype(np.uint32), st), f
+            if k:
+                dA, dB, _, _ = oracle.respond(st, PA, sc.A.T, PB, sc.B.T, D_POST)
+                dxA = [torch.zeros(len(PA), dtype=torch.float64, device="cuda:0") for _ in range(3)]
+                dxB = [torch.zeros(len(PB), dtype=torch.float64, device="cuda:0") for _ in range(3)]
+                A64 = api.Mesh(*[t.double() for t in (A.x, A.y, A.z)], A.tris, False, edges=A.edges)
+                B64 = api.Mesh(*[t.double() for t in (B.x, B.y, B.z)], B.tris, True, edges=B.edges)
+                ctx64.hfcr_respond(A64, B64, sbuf, k, D_POST, dxA, dxB)
+                g = np.concatenate([torch.stack(dxA, 1).cpu().numpy(), torch.stack(dxB, 1).cpu().numpy()])
+                assert rel_err(g, np.concatenate([dA, dB])) <= 1e-6, f
+                eA = (PA + oracle.diffuse(dA, EA, R)).astype(np.float32).astype(np.float64)
+                eB = (PB + oracle.diffuse(dB, EB, R)).astype(np.float32).astype(np.float64)
+        info = ctx.hfcr_resolve(A, B, D_POST, 1)
+        if f in (0, 149, 299):
+            assert info.pairs_first == len(ref) and info.diffuse_unconverged == 0, f
+            if k:
+                gA, gB = positions(A), positions(B)
+                tol = _pos_tol(max(np.abs(dA).max(), np.abs(dB).max()), PA, PB)
+                assert np.abs(gA - eA).max() <= tol and np.abs(gB - eB).max() <= tol, f
+            checked.append((f, n, k))
+    # frame 0 is before the first contact; the later samples have thousands of pairs
+    assert checked[0][1] == 0 and checked[1][1] > 1000 and checked[2][1] > 1000, checked
