@@ -129,6 +129,8 @@ typedef struct {
     int32_t diffuse_max_iters; /* harmonic diffusion: iteration limit (0: default 1000) */
     double diffuse_tol;     /* harmonic diffusion: stop at |r| <= diffuse_tol |b| per coordinate,
                                0 < tol < 1 (0: default 1e-10) */
+    double amplification_limit; /* hfcr_resolve counts the responses whose max_dx / max_rhs
+                                   exceeds it (0: default 1000) */
 } hfcr_options;
 
 typedef struct {
@@ -139,6 +141,11 @@ typedef struct {
     int32_t converged;       /* rel_residual <= rel_tol */
     int32_t n_stencils;
     int32_t n_touched;       /* distinct vertices in the stencils */
+    double max_rhs;          /* largest |D - d| of the stencils (Eq. 8) */
+    double max_dx;           /* largest displacement component |dx|; max_dx / max_rhs is the
+                                response's amplification: below ~10 for a well-posed system,
+                                far above when Eq. 7 is nearly singular (e.g. a stencil whose
+                                face is kinematic and whose x0 crosses near-parallel faces) */
 } hfcr_solve_info;
 
 typedef struct {
@@ -162,6 +169,10 @@ typedef struct {
                                       memory; bit 2: the float64 per-zone CG ran */
     int32_t diffuse_cg_iters;      /* harmonic diffusion: CG iterations over all iterations */
     int32_t diffuse_unconverged;   /* iterations whose harmonic diffusion stopped at diffuse_max_iters */
+    double worst_amplification;    /* largest max_dx / max_rhs of a response (see hfcr_solve_info) */
+    int32_t amplified_iters;       /* responses whose amplification exceeded the option
+                                      amplification_limit: an ill-conditioned system moved
+                                      vertices far more than the penetration depths */
 } hfcr_resolve_info;
 
 /* Stages timed by the optional profiler (instrumentation; the paper has no
@@ -218,14 +229,17 @@ hfcr_status hfcr_build_edges(hfcr_ctx *ctx, const int32_t *tris, int32_t n_tris,
  * enough for n_tris <= 65,536), which every GPU that loads the library
  * holds until the process exits.  Larger inputs return HFCR_ERR_CAPACITY
  * (message in hfcr_last_error(NULL)), as does cap < 3 * n_tris: out must
- * have room for the largest possible edge count.  The first call on a
- * device looks up that device's address of the array (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the one
- * array: calls that overlap on the GPU (different streams, or different
- * host threads) race and give undefined results; calls in sequence are
- * fine, since each call clears the words it needs cleared.
- * tris, out: device; *n_out (host) gets the edge count.  Synchronises
- * `stream`. */
+ * have room for the largest possible edge count; a vertex index outside
+ * [0, n_verts) returns HFCR_ERR_ARG.  The first call on a device looks up
+ * that device's address of the array (cudaGetSymbolAddress) and keeps it
+ * for the process; make that first call before any stream capture.  After
+ * cudaDeviceReset the kept address is no longer valid: do not call this
+ * entry point again in that process.  All calls share the one array:
+ * calls that overlap on the GPU (different streams, or different host
+ * threads) race and give undefined results; calls in sequence are fine,
+ * since each call clears the words it needs cleared.
+ * tris, out: device; *n_out (host) gets the edge count.  The call
+ * synchronises `stream` before it returns (it reads the count back). */
 hfcr_status hfcr_build_edges_noalloc(const int32_t *tris, int32_t n_tris, int32_t n_verts,
                                      int32_t *out, int64_t cap, int64_t *n_out, void *stream);
 

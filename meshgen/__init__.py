@@ -321,7 +321,8 @@ def scene_c3(seed: int = BASE_SEED + 2, nu: int = 512, nv: int = 256,
     VB = VB @ Rm.T + centre
     return Scene(Mesh(VA, TA, True, "torusA"), Mesh(VB, TB, True, "torusB"),
                  np.float32, name=f"two tori {nu}x{nv}, r {r}, delta {delta:.4f}, fp32",
-                 meta={"delta": float(delta)})
+                 meta={"delta": float(delta), "R": R, "r": r,
+                       "frame_B": (Rm, centre)})    # world = local @ Rm.T + centre
 
 
 def scene_c4(seed: int = BASE_SEED + 3, n_pairs: int = 1024, lmin: int = 1,

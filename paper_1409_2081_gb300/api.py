@@ -58,13 +58,15 @@ class hfcr_options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("graphs", ctypes.c_int32),
                 ("diffuse_rings", ctypes.c_int32), ("diffuse_sweeps", ctypes.c_int32),
                 ("traverse_variant", ctypes.c_int32), ("setup_path", ctypes.c_int32),
-                ("diffuse_max_iters", ctypes.c_int32), ("diffuse_tol", ctypes.c_double)]
+                ("diffuse_max_iters", ctypes.c_int32), ("diffuse_tol", ctypes.c_double),
+                ("amplification_limit", ctypes.c_double)]
 
 
 class hfcr_solve_info(ctypes.Structure):
     _fields_ = [("cg_iters", ctypes.c_int32), ("refine_rounds", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("converged", ctypes.c_int32),
-                ("n_stencils", ctypes.c_int32), ("n_touched", ctypes.c_int32)]
+                ("n_stencils", ctypes.c_int32), ("n_touched", ctypes.c_int32),
+                ("max_rhs", ctypes.c_double), ("max_dx", ctypes.c_double)]
 
 
 class hfcr_detect_stats(ctypes.Structure):
@@ -78,7 +80,8 @@ class hfcr_resolve_info(ctypes.Structure):
                 ("total_pairs", ctypes.c_int64), ("total_stencils", ctypes.c_int64),
                 ("cg_iters", ctypes.c_int32), ("worst_rel_residual", ctypes.c_double),
                 ("stats", hfcr_detect_stats), ("solver_path", ctypes.c_int32),
-                ("diffuse_cg_iters", ctypes.c_int32), ("diffuse_unconverged", ctypes.c_int32)]
+                ("diffuse_cg_iters", ctypes.c_int32), ("diffuse_unconverged", ctypes.c_int32),
+                ("worst_amplification", ctypes.c_double), ("amplified_iters", ctypes.c_int32)]
 
 
 HFCR_N_STAGES = 8
@@ -196,13 +199,14 @@ class Context:
                  roles: int = HFCR_ROLES_ALTERNATE, max_cg_iters: int = 500, max_refine: int = 6,
                  rel_tol: float = 1e-12, inner_tol: float = 1e-4, graphs: bool = True,
                  diffuse_rings: int = 0, diffuse_sweeps: int = 0, traverse_variant: int = 0,
-                 setup_path: int = 0, diffuse_max_iters: int = 1000, diffuse_tol: float = 1e-10):
+                 setup_path: int = 0, diffuse_max_iters: int = 1000, diffuse_tol: float = 1e-10,
+                 amplification_limit: float = 1000.0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("hfcr needs a CUDA device")
         opt = hfcr_options(solver, int(f32_filter), roles, max_cg_iters, max_refine, rel_tol, inner_tol,
                            int(graphs), diffuse_rings, diffuse_sweeps, traverse_variant, setup_path,
-                           diffuse_max_iters, diffuse_tol)
+                           diffuse_max_iters, diffuse_tol, amplification_limit)
         h = ctypes.c_void_p()
         self.handle = None
         # a refused create has no context: its message is the thread's

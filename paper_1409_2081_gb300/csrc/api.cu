@@ -147,7 +147,7 @@ void free_all(hfcr_ctx *c) {
                     c->sb.ck64, c->sb.ck64_alt, c->sb.gst, c->sb.zg, c->sb.d_ng, c->sb.pinv,
                     c->sb.z32,
                     c->sb.ids, c->sb.n64, c->sb.n32, c->sb.b, c->sb.lam, c->sb.r64, c->sb.r32,
-                    c->sb.x32, c->sb.p32, c->sb.q32, c->sb.w32, c->sb.p64, c->sb.q64, c->sb.cg64, c->sb.vidx, c->sb.ckey,
+                    c->sb.x32, c->sb.p32, c->sb.q32, c->sb.w32, c->sb.p64, c->sb.q64, c->sb.cg64, c->sb.pinv64, c->sb.vidx, c->sb.ckey,
                     c->sb.ckey_alt, c->sb.cval, c->sb.cval_alt, c->sb.cflag, c->sb.seg, c->sb.gvert,
                     c->sb.winv, c->sb.u64, c->sb.u32, c->sb.red};
     for (void *p : ptrs)
@@ -512,7 +512,7 @@ hfcr_status run_response(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
                      ctx->d_status, ctx->opt.setup_path, s);
     prof_end(ctx, HFCR_STAGE_ASSEMBLE, s);
     prof_begin(ctx, HFCR_STAGE_SOLVE, s);
-    solve(params_of(ctx->opt), ctx->d_cnt + C_STENCILS, k, ctx->sb, ctx->d_status, s);
+    solve(params_of(ctx->opt), mp, ctx->d_cnt + C_STENCILS, k, ctx->sb, ctx->d_status, s);
     prof_end(ctx, HFCR_STAGE_SOLVE, s);
     prof_begin(ctx, HFCR_STAGE_DISPLACE, s);
     displacement(mp, k, ctx->sb, apply, dxA, dxB, s);
@@ -706,6 +706,8 @@ hfcr_status solve_info(hfcr_ctx *ctx, int k, hfcr_solve_info *info, cudaStream_t
     info->converged = k == 0 || w.dwork[0] <= ctx->opt.rel_tol;
     info->n_stencils = k;
     info->n_touched = k > 0 ? w.touched : 0;
+    info->max_rhs = k > 0 ? w.dwork[8] : 0.0;
+    info->max_dx = k > 0 ? w.dwork[9] : 0.0;
     return HFCR_OK;
 }
 
@@ -736,6 +738,7 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
     c->opt.setup_path = 0;
     c->opt.diffuse_max_iters = 1000;
     c->opt.diffuse_tol = 1e-10;
+    c->opt.amplification_limit = 1000.0;
     if (opt) {
         c->opt = *opt;
         if (c->opt.max_cg_iters <= 0) c->opt.max_cg_iters = 500;
@@ -757,6 +760,7 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
         }
         if (c->opt.diffuse_max_iters == 0) c->opt.diffuse_max_iters = 1000;
         if (c->opt.diffuse_tol == 0.0) c->opt.diffuse_tol = 1e-10;
+        if (!(c->opt.amplification_limit > 0.0)) c->opt.amplification_limit = 1000.0;
         if (!(c->opt.diffuse_tol > 0.0 && c->opt.diffuse_tol < 1.0) || c->opt.diffuse_max_iters < 0 ||
             c->opt.diffuse_max_iters > 100000) {
             delete c;
@@ -915,6 +919,7 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(dalloc(&sb.w32, P));
     CK(dalloc(&sb.p64, 2 * P));
     CK(dalloc(&sb.cg64, 5 * P));
+    CK(dalloc(&sb.pinv64, P));
     CK(dalloc(&sb.q64, P));
     CK(dalloc(&sb.vidx, P));
     CK(dalloc(&sb.ckey, 4 * P));
@@ -1161,6 +1166,13 @@ static hfcr_status resolve_impl(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, const
         quiet = 0;
         loc.cg_iters += ctx->h_iw[1];
         loc.solver_path |= ctx->h_iw[4];
+        if (ctx->h_dw[8] > 0.0) {
+            // the minimizer's own displacement (before any diffusion) against
+            // the largest penetration it answers
+            const double amp = ctx->h_dw[9] / ctx->h_dw[8];
+            if (amp > loc.worst_amplification) loc.worst_amplification = amp;
+            if (amp > ctx->opt.amplification_limit) loc.amplified_iters += 1;
+        }
         if (ctx->h_dw[0] > loc.worst_rel_residual) loc.worst_rel_residual = ctx->h_dw[0];
     }
     if (info) *info = loc;

@@ -256,6 +256,7 @@ struct SolveBuffers {
     float *r32 = nullptr, *x32 = nullptr, *p32 = nullptr, *q32 = nullptr, *w32 = nullptr;  // [cap_k]
     double *p64 = nullptr, *q64 = nullptr;   // p64 [2 cap_k] (x and p), q64 [cap_k] (FP64 solver)
     double *cg64 = nullptr;      // [5 cap_k] r, p, s, w, z of the float64 per-zone CG
+    double4_32a *pinv64 = nullptr;  // [cap_k] float64 inverse-block rows of that CG
     int4 *vidx = nullptr;        // [cap_k] compact vertex index of each stencil role
     // vertex CSR over 4k entries
     unsigned *ckey = nullptr, *ckey_alt = nullptr;   // [4 cap_k]
@@ -292,8 +293,8 @@ void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers 
 // One-time kernel attributes (shared-memory opt-in); call outside stream capture.
 void solver_init();
 // Solves and leaves lambda in sb.lam; results (iters, residual) in sb.iwork / sb.dwork.
-void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint32_t *d_status,
-           cudaStream_t s);
+void solve(const SolveParams &p, const MeshPair &mp, const int *d_k, int cap, SolveBuffers &sb,
+           uint32_t *d_status, cudaStream_t s);
 // dx = -M^-1 J^T lambda for the touched vertices; apply to positions (apply=1)
 // or write full dx arrays (zeroed first).
 // apply 1: x += dx; 0: dx to dxA / dxB (three arrays each, mesh dtype);

@@ -1,4 +1,5 @@
-// Edge extraction for callers that cannot allocate device memory.
+// Edge extraction for callers that cannot allocate device memory.  The
+// paper has no counterpart.
 //
 // Same computation as hfcr_build_edges (sorted unique undirected edges of a
 // triangle list), but every scratch buffer lives in one file-scope device
@@ -19,6 +20,13 @@ void set_noctx_error(const std::string &msg);
 }
 
 namespace {
+
+// HFCR_ERR_CUDA with the failing call's message for hfcr_last_error(NULL)
+hfcr_status cuda_fail(const char *what, cudaError_t e) {
+    hfcr::set_noctx_error(std::string("hfcr_build_edges_noalloc: ") + what + " failed: " +
+                          cudaGetErrorString(e));
+    return HFCR_ERR_CUDA;
+}
 
 constexpr int NOALLOC_MAX_TRIS = 1 << 16;
 constexpr int NOALLOC_KEYS = 3 * NOALLOC_MAX_TRIS;              // one key per half-edge
@@ -59,7 +67,12 @@ extern "C" hfcr_status hfcr_build_edges_noalloc(const int32_t *tris, int32_t n_t
     }
     if (n_tris == 0) return HFCR_OK;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HFCR_ERR_CUDA;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail("cudaGetDevice", ce);
+    if (dev < 0 || dev >= 64) {
+        hfcr::set_noctx_error("hfcr_build_edges_noalloc: device ordinal beyond 63");
+        return HFCR_ERR_CUDA;
+    }
     void *base = nullptr;
     {
         // the host-side name of a __device__ array is not a device address:
@@ -68,11 +81,7 @@ extern "C" hfcr_status hfcr_build_edges_noalloc(const int32_t *tris, int32_t n_t
         if (!g_base[dev]) {
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p) {
-                hfcr::set_noctx_error(std::string("cudaGetSymbolAddress failed: ") +
-                                      cudaGetErrorString(e));
-                return HFCR_ERR_CUDA;
-            }
+            if (e != cudaSuccess || !p) return cuda_fail("cudaGetSymbolAddress", e);
             g_base[dev] = p;
         }
         base = g_base[dev];
@@ -86,15 +95,19 @@ extern "C" hfcr_status hfcr_build_edges_noalloc(const int32_t *tris, int32_t n_t
     t.max_blocks = NOALLOC_HIST_BLOCKS;
     t.status = d_status;
     // the count and the status word carry over from the previous call
-    if (cudaMemsetAsync(d_count, 0, 8, s) != cudaSuccess) return HFCR_ERR_CUDA;
+    if ((ce = cudaMemsetAsync(d_count, 0, 8, s)) != cudaSuccess)
+        return cuda_fail("cudaMemsetAsync", ce);
     hfcr::build_edges(tris, n_tris, n_verts, out, d_count, (unsigned long long *)(b + OFF_KEYS),
                       (unsigned long long *)(b + OFF_KEYS_ALT), (unsigned *)(b + OFF_FLAGS), t,
                       d_status, s);
+    // a launch error of this call's kernels, peeked rather than fetched: an
+    // error state the caller's own earlier work left behind is not cleared
+    // here (it is reported like a failure of this call)
+    if ((ce = cudaPeekAtLastError()) != cudaSuccess) return cuda_fail("a kernel launch", ce);
     int words[2] = {0, 0};
-    if (cudaMemcpyAsync(words, d_count, sizeof words, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return HFCR_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
-        return HFCR_ERR_CUDA;
+    if ((ce = cudaMemcpyAsync(words, d_count, sizeof words, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail("cudaMemcpyAsync", ce);
+    if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail("cudaStreamSynchronize", ce);
     if (words[1] & hfcr::ST_BAD_INDEX) {
         hfcr::set_noctx_error("hfcr_build_edges_noalloc: a vertex index is out of range");
         return HFCR_ERR_ARG;

@@ -79,13 +79,20 @@ __device__ __forceinline__ void ld_pos(const hfcr_mesh &m, int i, double *o) {
     }
 }
 
-__global__ void k_assemble(hfcr_mesh A, hfcr_mesh B, const hfcr_stencil *st, const int *d_k,
-                           int cap, double d, int4 *ids, double4_32a *n64, float4 *n32, double *b,
-                           uint32_t *status) {
-    HFCR_PDL_WAIT();
-    int k = min(*d_k, cap);
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= k) return;
+// the largest of a non-negative double over the warp into *dst: the bit
+// patterns of non-negative doubles order like the unsigned integers
+__device__ __forceinline__ void warp_max_to(double v, unsigned long long *dst) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(v));
+}
+
+// row s of the constraints (Eq. 1, Eq. 2) and its right-hand side (Eq. 8);
+// returns |b_s|
+__device__ __forceinline__ double assemble_row(const hfcr_mesh &A, const hfcr_mesh &B,
+                                               const hfcr_stencil *st, int s, double d, int4 *ids,
+                                               double4_32a *n64, float4 *n32, double *b,
+                                               uint32_t *status) {
     hfcr_stencil S = st[s];
     const int nA = A.n_verts;
     const hfcr_mesh &E = S.dir ? B : A;  // mesh of x0
@@ -119,7 +126,20 @@ __global__ void k_assemble(hfcr_mesh A, hfcr_mesh B, const hfcr_stencil *st, con
     ids[s] = make_int4(g0, o + v1, o + v2, o + v3);
     n64[s] = make_double4_32a(n[0], n[1], n[2], 0.0);
     n32[s] = make_float4((float)n[0], (float)n[1], (float)n[2], 0.f);
-    b[s] = nn > 0.0 ? D - d : 0.0;
+    const double bs = nn > 0.0 ? D - d : 0.0;
+    b[s] = bs;
+    return fabs(bs);
+}
+
+// the rows, and the largest |b| of the call into *max_rhs
+__global__ void k_assemble(hfcr_mesh A, hfcr_mesh B, const hfcr_stencil *st, const int *d_k,
+                           int cap, double d, int4 *ids, double4_32a *n64, float4 *n32, double *b,
+                           unsigned long long *max_rhs, uint32_t *status) {
+    HFCR_PDL_WAIT();
+    const int k = min(*d_k, cap);
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const double mb = s < k ? assemble_row(A, B, st, s, d, ids, n64, n32, b, status) : 0.0;
+    warp_max_to(mb, max_rhs);
 }
 
 __global__ void k_csr_entries(const int4 *ids, const int *d_k, int cap, unsigned *key, int *val) {
@@ -814,10 +834,18 @@ __device__ __forceinline__ double inv_mass_of(int g, int nA, const float *wA, co
 // inverse of each group's block of A = J M^-1 J^T (float64, stored float32):
 // A_ab = (n_a . n_b) (w(x0) + 1/9 sum of w over the face vertices shared by
 // a and b); ids are the global vertex ids (x0, face) of the zone-ordered rows
-template <class G>
+__device__ __forceinline__ void store_inv_row(float4 *p, const double *row) {
+    *p = make_float4((float)row[0], (float)row[1], (float)row[2], (float)row[3]);
+}
+__device__ __forceinline__ void store_inv_row(double4_32a *p, const double *row) {
+    *p = make_double4_32a(row[0], row[1], row[2], row[3]);
+}
+
+// R: float4 rows for the mixed solver, double4_32a rows for the float64 one
+template <class G, typename R>
 __device__ __forceinline__ void group_inverse_one(int g, const int *gst, const int4 *ids,
                                                   const double4_32a *n64, int nA, const float *wA,
-                                                  const float *wB, float4 *pinv) {
+                                                  const float *wB, R *pinv) {
     {
         const int a0 = G::ld(gst + g), m = G::ld(gst + g + 1) - a0;
         double A[GMAX][2 * GMAX];
@@ -861,18 +889,18 @@ __device__ __forceinline__ void group_inverse_one(int g, const int *gst, const i
                 }
         }
         for (int a = 0; a < m; ++a) {
-            float row[GMAX] = {0.f, 0.f, 0.f, 0.f};
+            double row[GMAX] = {0.0, 0.0, 0.0, 0.0};
             if (ok) {
-                for (int b = 0; b < m; ++b) row[b] = (float)A[a][GMAX + b];
+                for (int b = 0; b < m; ++b) row[b] = A[a][GMAX + b];
             } else {
                 // diagonal fallback computed from the untouched inputs
                 const int4 va = G::ld(ids + a0 + a);
                 double w = inv_mass_of(va.x, nA, wA, wB) +
                            (inv_mass_of(va.y, nA, wA, wB) + inv_mass_of(va.z, nA, wA, wB) +
                             inv_mass_of(va.w, nA, wA, wB)) / 9.0;
-                row[a] = w > 0.0 ? (float)(1.0 / w) : 0.f;
+                row[a] = w > 0.0 ? 1.0 / w : 0.0;
             }
-            pinv[a0 + a] = make_float4(row[0], row[1], row[2], row[3]);
+            store_inv_row(pinv + a0 + a, row);
         }
     }
 }
@@ -948,6 +976,12 @@ struct ZoneArgs {
     double tol, rel_tol;
     int *ctl;
     unsigned *ticket;  // [2] zone counters of the pair launch (zero before a solve)
+    // float64 per-zone solve: rows' global vertex ids, inverse masses, and the
+    // float64 inverse blocks it computes
+    const int4 *ids;
+    int nA;
+    const float *wA, *wB;
+    double4_32a *pinv64;  // [cap_k]
 };
 
 // |b_zone|^2 with lam = 0 for the zone's rows
@@ -1289,7 +1323,7 @@ __device__ __forceinline__ double zone64_stencil(const ZoneArgs &a, int s0, int 
            n.z * (ux[2] - (ua[2] + ub[2] + uc[2]) * third);
 }
 
-// z = P^-1 r over the zone's groups (the float32-stored inverse blocks)
+// z = P^-1 r over the zone's groups (the float64 inverse blocks)
 __device__ __forceinline__ void zone64_precond(const ZoneArgs &a, int s0, int g0, int G,
                                                const double *r, double *zz) {
     for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
@@ -1298,8 +1332,8 @@ __device__ __forceinline__ void zone64_precond(const ZoneArgs &a, int s0, int g0
 #pragma unroll
         for (int q = 0; q < 4; ++q) rr[q] = lo + q < hi ? r[lo + q] : 0.0;
         for (int t = lo; t < hi; ++t) {
-            const float4 m = a.pinv[s0 + t];
-            zz[t] = (double)m.x * rr[0] + (double)m.y * rr[1] + (double)m.z * rr[2] + (double)m.w * rr[3];
+            const double4_32a m = a.pinv64[s0 + t];
+            zz[t] = m.x * rr[0] + m.y * rr[1] + m.z * rr[2] + m.w * rr[3];
         }
     }
 }
@@ -1315,6 +1349,10 @@ __global__ void __launch_bounds__(ZONE64_THREADS) k_cg_zone64(const int *d_nz, Z
         const int j0 = a.zv[z], U = a.zv[z + 1] - j0;
         const int g0 = a.zg[z], G = a.zg[z + 1] - g0;
         const double bb = zone_start<CtaGroup>(a, s0, k, redd);  // lam = 0 on the zone's rows
+        // the zone's block-Jacobi inverses in float64 (a block of nearly
+        // dependent rows has a large inverse that float32 would not hold)
+        for (int gi = threadIdx.x; gi < G; gi += blockDim.x)
+            group_inverse_one<PlainLd>(g0 + gi, a.gst, a.ids, a.n64, a.nA, a.wA, a.wB, a.pinv64);
         double *r = g.r + s0, *p = g.p + s0, *sv = g.s + s0, *w = g.w + s0, *zz = g.z + s0;
         double *x = a.lam + s0, *u = a.u64 + 3 * (size_t)j0;
         for (int t = threadIdx.x; t < k; t += blockDim.x) {
@@ -1506,11 +1544,15 @@ __global__ void k_init_lam(const int *d_k, const double *b, double *lam, double 
 __global__ void k_displace(const int *d_U, const int *seg, const int *cval, const float *winv,
                            const double4_32a *n64, const double *lam, const int *gvert, hfcr_mesh A,
                            hfcr_mesh B, int apply, void *dA0, void *dA1, void *dA2, void *dB0,
-                           void *dB1, void *dB2) {
+                           void *dB1, void *dB2, unsigned long long *max_dx) {
     HFCR_PDL_WAIT();
     const int U = *d_U;
     const double third = 1.0 / 3.0;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < U; j += gridDim.x * blockDim.x) {
+    double biggest = 0.0;  // the largest displacement component of this thread's vertices
+    const int j_end = (U + (int)(gridDim.x * blockDim.x) - 1) / (int)(gridDim.x * blockDim.x) *
+                      (int)(gridDim.x * blockDim.x);  // every thread of a warp runs the same trips
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < j_end; j += gridDim.x * blockDim.x) {
+        if (j >= U) continue;
         double a0 = 0, a1 = 0, a2 = 0;
         for (int e = seg[j]; e < seg[j + 1]; ++e) {
             int v = cval[e];
@@ -1523,6 +1565,7 @@ __global__ void k_displace(const int *d_U, const int *seg, const int *cval, cons
         }
         double w = (double)winv[j];
         double dx[3] = {-w * a0, -w * a1, -w * a2};
+        biggest = fmax(biggest, fmax(fabs(dx[0]), fmax(fabs(dx[1]), fabs(dx[2]))));
         int g = gvert[j];
         if (apply == 2) {  // into the float64 field of the diffusion (AoS, global ids)
             double *f = (double *)dA0 + 3 * (size_t)g;
@@ -1553,6 +1596,7 @@ __global__ void k_displace(const int *d_U, const int *seg, const int *cval, cons
             }
         }
     }
+    warp_max_to(biggest, max_dx);
 }
 
 // ---------------------------------------------------------------------------
@@ -2031,8 +2075,11 @@ __global__ void __launch_bounds__(TPB) k_setup(SetupArgs a) {
 void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int cap, double d,
               SolveBuffers &sb, uint32_t *d_status, cudaStream_t s) {
     if (cap <= 0) return;
+    // dwork[8] / dwork[9]: the largest |b| and |dx| of the call, as the
+    // bits of non-negative doubles
     { launch_pdl(k_assemble, (cap + 255) / 256, 256, 0, s, mp.A, mp.B, st, d_k, cap, d, sb.ids_raw,
-                                                 sb.n64_raw, sb.n32_raw, sb.b_raw, d_status); note_launch(); }
+                 sb.n64_raw, sb.n32_raw, sb.b_raw, (unsigned long long *)(sb.dwork + 8),
+                 d_status); note_launch(); }
 }
 
 // dynamic shared memory granted to the zone CG kernels (0: the global-memory
@@ -2213,8 +2260,8 @@ void build_vertex_csr(const MeshPair &mp, const int *d_k, int cap, SolveBuffers 
                  mp.A.inv_mass, mp.B.inv_mass, sb.pinv); note_launch(); }
 }
 
-void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint32_t *d_status,
-           cudaStream_t s) {
+void solve(const SolveParams &p, const MeshPair &mp, const int *d_k, int cap, SolveBuffers &sb,
+           uint32_t *d_status, cudaStream_t s) {
     (void)d_status;
     if (cap <= 0) return;
     solver_init();
@@ -2233,6 +2280,11 @@ void solve(const SolveParams &p, const int *d_k, int cap, SolveBuffers &sb, uint
         za.maxit = p.max_cg_iters; za.max_refine = p.max_refine;
         za.tol = p.inner_tol; za.rel_tol = p.rel_tol; za.ctl = sb.iwork;
         za.ticket = (unsigned *)(sb.iwork + 13);
+        za.ids = sb.ids;
+        za.nA = mp.A.n_verts;
+        za.wA = mp.A.inv_mass;
+        za.wB = mp.B.inv_mass;
+        za.pinv64 = sb.pinv64;
         Zone64Scratch g64;
         g64.r = sb.cg64; g64.p = sb.cg64 + cap; g64.s = sb.cg64 + 2 * (size_t)cap;
         g64.w = sb.cg64 + 3 * (size_t)cap; g64.z = sb.cg64 + 4 * (size_t)cap;
@@ -2304,8 +2356,8 @@ void displacement(const MeshPair &mp, int cap, SolveBuffers &sb, int apply, void
     void *a0 = dxA ? dxA[0] : nullptr, *a1 = dxA ? dxA[1] : nullptr, *a2 = dxA ? dxA[2] : nullptr;
     void *b0 = dxB ? dxB[0] : nullptr, *b1 = dxB ? dxB[1] : nullptr, *b2 = dxB ? dxB[2] : nullptr;
     { launch_pdl(k_displace, nb, 256, 0, s, sb.d_U, sb.seg, sb.cval_s, sb.winv, sb.n64, sb.lam,
-                 sb.gvert, mp.A,
-                                  mp.B, apply, a0, a1, a2, b0, b1, b2); note_launch(); }
+                 sb.gvert, mp.A, mp.B, apply, a0, a1, a2, b0, b1, b2,
+                 (unsigned long long *)(sb.dwork + 9)); note_launch(); }
 }
 
 }  // namespace hfcr
