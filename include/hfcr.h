@@ -121,7 +121,7 @@ typedef struct {
                                applied as it is */
     int32_t diffuse_sweeps; /* 0 (default): the harmonic field (conjugate gradients to diffuse_tol);
                                S > 0: the fixed-sweep approximation, S Jacobi sweeps from zero */
-    int32_t traverse_variant; /* traversal kernel variant 0..4 used until hfcr_autotune picks one
+    int32_t traverse_variant; /* traversal kernel variant 0..8 used until hfcr_autotune picks one
                                  (default 0; every variant finds the same pairs) */
     int32_t setup_path;     /* response setup (vertex CSR, impact zones, preconditioner groups):
                                0 (default) one cooperative launch, 1 a sequence of about 25
@@ -317,13 +317,18 @@ hfcr_status hfcr_resolve(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, double d, in
 /* Autotuner of the traversal kernel (no counterpart in the paper): builds
  * the hierarchies for A and B (a batch laid out as in hfcr_detect_batch
  * when segs is given, one pair when segs is NULL and n_pairs is ignored),
- * times every traversal variant (register
- * budget for 2, 3 or 4 CTAs of 256 threads per SM, exact narrow phase
- * inline or out of line, one walk per edge or one per warp of edges of the
- * same mesh pair) three times on this scene, and makes the fastest the
- * context's choice for every later call.  *chosen (host, may be NULL)
- * gets its index; ms (host [n_ms], may be NULL) the best time of each
- * variant.  Synchronises. */
+ * times every traversal variant three times on this scene and makes the
+ * fastest the context's choice for every later call.  The variants span:
+ * the register budget (2, 3 or 4 CTAs of 256 threads per SM), the exact
+ * narrow phase inline or out of line, one walk per edge or one per warp of
+ * edges of the same mesh pair (0 to 4), and persistent walks fed by a
+ * device work queue of edges, with 3 or 4 CTAs per SM and a warp refilling
+ * its idle lanes once 8 or 16 are idle (5 to 8).  The stack depth is not
+ * tuned: it is set by the deepest tree the build makes.  *chosen (host,
+ * may be NULL) gets the chosen index; ms (host [n_ms], may be NULL) the
+ * best time of each variant per traversal launch (one launch per direction
+ * with edges, as a repair iteration of that direction runs it).
+ * Synchronises. */
 hfcr_status hfcr_autotune(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, int32_t n_pairs,
                           const int32_t *segs, int32_t *chosen, double *ms, int32_t n_ms,
                           void *stream);

@@ -29,6 +29,7 @@ HFCR_F64 = 1
 HFCR_SOLVER_MIXED = 0
 HFCR_SOLVER_FP64 = 1
 HFCR_SOLVER_FP64_GLOBAL = 2
+N_TRAVERSE_VARIANTS = 9
 HFCR_ROLES_ALTERNATE = 0
 HFCR_ROLES_BOTH = 1
 
@@ -235,12 +236,12 @@ class Context:
         """Times the traversal variants on this scene (a batch when segs is
         given) and keeps the fastest; returns (chosen index, [ms per variant])."""
         chosen = ctypes.c_int32()
-        ms = (ctypes.c_double * 8)()
+        ms = (ctypes.c_double * N_TRAVERSE_VARIANTS)()
         n_pairs = 0 if segs is None else int(segs.shape[0]) - 1
         self._check(lib().hfcr_autotune(self.handle, ctypes.byref(A.c), ctypes.byref(B.c), n_pairs,
-                                        _ptr(segs), ctypes.byref(chosen), ms, 8,
+                                        _ptr(segs), ctypes.byref(chosen), ms, N_TRAVERSE_VARIANTS,
                                         _stream_ptr(stream)))
-        return int(chosen.value), [round(ms[i], 5) for i in range(5)]
+        return int(chosen.value), [round(ms[i], 5) for i in range(N_TRAVERSE_VARIANTS)]
 
     def hfcr_profile_enable(self, on: bool = True):
         self._check(lib().hfcr_profile_enable(self.handle, int(on)))

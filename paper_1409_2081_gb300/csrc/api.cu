@@ -108,7 +108,7 @@ struct hfcr_ctx {
 
 // device counter slots
 enum { C_PAIRS = 0, C_STENCILS = 1, C_EDGES_A = 2, C_EDGES_B = 3, C_N4 = 4, C_NPAIRS_IN = 5, C_PEFF = 6,
-       C_DIFF_ITERS = 7, C_DIFF_FAIL = 8, C_NFREE = 9 };
+       C_DIFF_ITERS = 7, C_DIFF_FAIL = 8, C_NFREE = 9, C_QUEUE = 10 };
 
 namespace {
 
@@ -374,6 +374,7 @@ void launch_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d
             a.cap = (int)ctx->max_pairs;
             a.stats = ctx->d_stats;
             a.variant = variant;
+            a.queue = ctx->d_cnt + C_QUEUE;
             detect_launch(a, s, ctx->d_status);
         }
         return;
@@ -416,6 +417,7 @@ void launch_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bool d
         a.cap = (int)ctx->max_pairs;
         a.stats = ctx->d_stats;
         a.variant = ctx->trav_variant;
+        a.queue = ctx->d_cnt + C_QUEUE;
         prof_begin(ctx, HFCR_STAGE_TRAVERSE, s);
         detect_launch(a, s, ctx->d_status);
         prof_end(ctx, HFCR_STAGE_TRAVERSE, s);
@@ -1212,6 +1214,13 @@ hfcr_status hfcr_autotune(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     bool built[2] = {false, false};
     launch_detect(ctx, A, B, dir0, dir1, pl, built, s);  // builds and refits the hierarchies
     if ((st = read_back(ctx, s))) return st;
+    // traversal launches per timed call (one per active direction with
+    // work): the times below are per launch, as a repair iteration of one
+    // direction runs it
+    int nl = 0;
+    if (dir0 && B->n_tris > 0 && pl.ne[0] > 0) ++nl;
+    if (dir1 && A->n_tris > 0 && pl.ne[1] > 0) ++nl;
+    if (nl == 0) nl = 1;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1227,7 +1236,7 @@ hfcr_status hfcr_autotune(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
             CK(cudaEventSynchronize(e1));
             float t = 0.f;
             CK(cudaEventElapsedTime(&t, e0, e1));
-            if (t < vbest) vbest = t;
+            if (t / nl < vbest) vbest = t / nl;
         }
         if (ms && v < n_ms) ms[v] = vbest;
         if (vbest < best_ms) {

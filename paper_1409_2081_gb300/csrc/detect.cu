@@ -277,6 +277,126 @@ __global__ void __launch_bounds__(256, MINB) k_traverse(
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&st->narrow_tests, (unsigned long long)tot);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent traversal with a device work queue (variants 5 to 8): a grid
+// of as many CTAs as fit on the GPU at once; every warp keeps its lanes
+// busy by handing each lane whose walk has ended the next edge of the
+// traversal order from one global counter (one atomic per refill, once at
+// least FETCH lanes are idle).  Every lane then takes one node per step,
+// so short walks (edges that leave at the root of their pair's tree) no
+// longer idle their warp until its longest walk ends, and no CTA outlives
+// the others with a few long walks.  Edges are handed out in the Morton
+// order of their midpoints, so a warp still walks one region of a tree.
+// The pairs and tests are exactly those of the per-edge walk.
+// ---------------------------------------------------------------------------
+template <typename T, bool F32F, int MINB, int FETCH>
+__global__ void __launch_bounds__(256, MINB) k_traverse_q(
+    const int2 *edges, const int *order, int ne, const T *ex, const T *ey, const T *ez, int nv,
+    const float4 *nodes, const void *leaf_tri, int nfaces, const int *segs, int nseg, int ecol,
+    int fcol, unsigned long long dirbit, int face_bits, unsigned long long *out, int *count, int cap,
+    int *queue, DevStats *st, uint32_t *status) {
+    HFCR_PDL_WAIT();
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    bool active = false, drained = false;
+    int e = 0, node = 0, sp = 0, visits = 0, max_visits = 0;
+    T p[3] = {0, 0, 0}, q[3] = {0, 0, 0};
+    float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f};
+    unsigned long long ebits = 0;
+    int stack[STACK];
+    unsigned tests = 0;
+    while (true) {
+        // refill the idle lanes from the queue (warp-uniform decision)
+        const unsigned idle = __ballot_sync(full, !active);
+        if (!drained && __popc(idle) >= (idle == full ? 1 : FETCH)) {
+            const int leader = __ffs(idle) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(queue, __popc(idle));
+            base = __shfl_sync(full, base, leader);
+            if (base + __popc(idle) >= ne) drained = true;
+            if (!active) {
+                const int t = base + __popc(idle & below);
+                if (t < ne) {
+                    e = order ? order[t] : t;
+                    const int2 ev = edges[e];
+                    const int pair = seg_of(segs, ecol, nseg, ev.x);
+                    int t0, nleaf;
+                    seg_range(segs, fcol, pair, nfaces, t0, nleaf);
+                    if (nleaf > 0) {
+                        const int i0 = chk(ev.x, nv, status), i1 = chk(ev.y, nv, status);
+                        p[0] = ex[i0]; p[1] = ey[i0]; p[2] = ez[i0];
+                        q[0] = ex[i1]; q[1] = ey[i1]; q[2] = ez[i1];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            lo[k] = lo_f(p[k] < q[k] ? p[k] : q[k]);
+                            hi[k] = hi_f(p[k] < q[k] ? q[k] : p[k]);
+                        }
+                        ebits = ((unsigned long long)e) << face_bits;
+                        node = nleaf == 1 ? ~t0 : t0;
+                        sp = 0;
+                        visits = 0;
+                        // a tree of nleaf leaves has 2 nleaf - 1 nodes, each
+                        // visited at most once per edge: the bound only guards
+                        // a corrupted tree
+                        max_visits = 2 * nleaf + 8;
+                        active = true;
+                    }
+                }
+            }
+        }
+        if (!__any_sync(full, active)) {
+            if (drained) break;
+            continue;  // every fetched edge had an empty pair; fetch again
+        }
+        if (!active) continue;
+        // one step of this lane's walk
+        if (++visits > max_visits) {
+            atomicOr(status, ST_BAD_INDEX);
+            active = false;
+            continue;
+        }
+        int leaf0 = -1, leaf1 = -1, next = -1, push = -1;
+        if (node < 0) {
+            leaf0 = ~node;
+        } else {
+            const float4 *nd = nodes + 4 * node;
+            const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+            const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+            const bool h0 = overlap(lo, hi, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
+            const bool h1 = overlap(lo, hi, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
+            if (h0) { if (c0 < 0) leaf0 = ~c0; else next = c0; }
+            if (h1) {
+                if (c1 < 0) leaf1 = ~c1;
+                else if (next < 0) next = c1;
+                else push = c1;
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            const int lf = w ? leaf1 : leaf0;
+            if (lf >= 0) {
+                Leaf<T> L;
+                L.load(leaf_tri, lf);
+                ++tests;
+                if (leaf_test_call<T, F32F>(p, q, L, st)) {
+                    const int pos = atomicAdd(count, 1);
+                    if (pos < cap) out[pos] = dirbit | ebits | (unsigned)L.face;
+                }
+            }
+        }
+        if (push >= 0) {
+            if (sp < STACK) stack[sp++] = push;
+            else atomicOr(status, ST_BAD_INDEX);  // unreachable: depth < 64
+        }
+        if (next >= 0) node = next;
+        else if (sp > 0) node = stack[--sp];
+        else active = false;
+    }
+    unsigned tot = __reduce_add_sync(full, tests);
+    if (lane == 0 && tot) atomicAdd(&st->narrow_tests, (unsigned long long)tot);
+}
+
 __global__ void k_keys_to_pairs(const unsigned long long *keys, const int *d_n, int cap,
                                 const int2 *edgesA, const int2 *edgesB, int edge_bits,
                                 int face_bits, hfcr_pair *out) {
@@ -445,9 +565,49 @@ static void launch_traverse(const DetectArgs &a, const T *x, const T *y, const T
           a.stats, d_status); note_launch(); }
 }
 
+// resident CTAs of a persistent traversal kernel on this device (cached)
+template <typename K>
+static int resident_ctas(K kern) {
+    static int dev_cache[64];
+    static bool done[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 152;
+    if (!done[dev]) {
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0);
+        dev_cache[dev] = sms * (per > 0 ? per : 1);
+        done[dev] = true;
+    }
+    return dev_cache[dev];
+}
+
+template <typename T, bool F32F, int MINB, int FETCH>
+static void launch_queue(const DetectArgs &a, const T *x, const T *y, const T *z,
+                         unsigned long long dirbit, cudaStream_t s, uint32_t *d_status) {
+    const hfcr_mesh &m = *a.edge_mesh;
+    auto kern = k_traverse_q<T, F32F, MINB, FETCH>;
+    int grid = resident_ctas(kern);
+    const int need = (a.n_edges + 255) / 256;
+    if (grid > need) grid = need;
+    cudaMemsetAsync(a.queue, 0, sizeof(int), s);
+    { launch_pdl(kern, grid, 256, 0, s, (const int2 *)a.edges, a.order, a.n_edges, x, y, z,
+                 m.n_verts, a.bvh->nodes, a.bvh->leaf_tri, a.bvh->n, a.segs, a.nseg, a.ecol, a.fcol,
+                 dirbit, a.face_bits, a.keys, a.d_count, a.cap, a.queue, a.stats, d_status);
+      note_launch(); }
+}
+
 template <typename T, bool F32F>
 static void launch_variant(const DetectArgs &a, const T *x, const T *y, const T *z, int nb,
                            unsigned long long dirbit, cudaStream_t s, uint32_t *d_status) {
+    switch (a.variant) {
+        case 5: launch_queue<T, F32F, 3, 8>(a, x, y, z, dirbit, s, d_status); return;
+        case 6: launch_queue<T, F32F, 4, 8>(a, x, y, z, dirbit, s, d_status); return;
+        case 7: launch_queue<T, F32F, 3, 16>(a, x, y, z, dirbit, s, d_status); return;
+        case 8: launch_queue<T, F32F, 4, 16>(a, x, y, z, dirbit, s, d_status); return;
+        default: break;
+    }
     switch (a.variant) {
         case 1: launch_traverse<T, F32F, 4, true, false>(a, x, y, z, nb, dirbit, s, d_status); break;
         case 2: launch_traverse<T, F32F, 3, true, false>(a, x, y, z, nb, dirbit, s, d_status); break;

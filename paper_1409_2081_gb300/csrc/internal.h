@@ -193,9 +193,10 @@ struct DetectArgs {
     int *d_count;
     int cap;
     DevStats *stats;
-    int variant = 0;  // traversal variant (0 to 4; see detect.cu)
+    int variant = 0;  // traversal variant (0 to 8; see detect.cu)
+    int *queue = nullptr;  // work counter of the persistent variants (zeroed by the launch)
 };
-constexpr int N_TRAVERSE_VARIANTS = 5;
+constexpr int N_TRAVERSE_VARIANTS = 9;
 void detect_launch(const DetectArgs &a, cudaStream_t s, uint32_t *d_status);
 // adds sum_i |edges of pair i| x |faces of pair i| to stats->bf (edges are
 // sorted by first vertex, so each pair's edges are contiguous)

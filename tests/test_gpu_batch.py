@@ -72,7 +72,9 @@ def test_batch_pairs_equal_per_pair_oracle(api):
     assert rel_err(g, np.concatenate([rA, rB])) <= 1e-6
     # every traversal variant, the per-warp packet walks included (warps of
     # these small pairs often span two pairs and fall back to per-edge walks)
-    for v in range(1, 5):
+    # and the persistent walks fed by a work queue (lanes of one warp walk
+    # edges of different pairs)
+    for v in range(1, api.N_TRAVERSE_VARIANTS):
         cv = api.Context(traverse_variant=v)
         cv.hfcr_reserve(max(len(PA), len(PB)), max(len(TA), len(TB)), 1 << 17)
         nv = cv.hfcr_detect_batch(A, B, dsegs, out)

@@ -382,24 +382,31 @@ def test_graph_replay_matches_plain_launches(api):
 
 
 def test_autotuned_variants_give_identical_pairs(api):
-    """Every traversal variant (per-edge walks, per-warp packet walks) finds
-    the same exact pair set, and the autotuner picks one of them."""
+    """Every traversal variant (per-edge walks, per-warp packet walks, the
+    persistent walks fed by a work queue) finds the same exact pair set,
+    and the autotuner picks one of them."""
     sc = meshgen.scene_c2()
     A, PA = dev_mesh(api, sc.A.V, sc.A.T, False, np.float32)
     B, PB = dev_mesh(api, sc.B.V, sc.B.T, True, np.float32)
     ref = oracle.detect(PA, sc.A.T, False, PB, sc.B.T, True)
-    for v in range(5):
+    nvar = api.N_TRAVERSE_VARIANTS
+    for v in range(nvar):
         ctx = make_ctx(api, sc.A.n_verts, sc.A.n_tris, traverse_variant=v)
         _, n, got, st = detect(ctx, A, B)
         assert np.array_equal(got, ref.rec), v
+        # the same narrow-phase tests as the per-edge walk
+        if v == 0:
+            tests0 = st.narrow_tests
+        elif v not in (3, 4):   # the packet walks test the same leaves too
+            assert st.narrow_tests == tests0, v
         ctx.close()
     ctx = make_ctx(api, sc.A.n_verts, sc.A.n_tris)
     chosen, ms = ctx.hfcr_autotune(A, B)
-    assert 0 <= chosen < 5 and len(ms) == 5 and all(t > 0 for t in ms)
+    assert 0 <= chosen < nvar and len(ms) == nvar and all(t > 0 for t in ms)
     _, n, got, _ = detect(ctx, A, B)
     assert np.array_equal(got, ref.rec)
     with pytest.raises(api.HfcrError):
-        api.Context(traverse_variant=5)
+        api.Context(traverse_variant=nvar)
 
 
 def test_kinematic_body_respond(api):
