@@ -28,6 +28,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
 #include "sortdev.cuh"
 
@@ -1225,9 +1227,11 @@ __global__ void __launch_bounds__(512, 2) k_cg_zone_pair(const int *d_nz, ZoneAr
                       g, slot + 1);
 }
 
+// leave_big: zones that do not fit smem_bytes are left to the cluster
+// solver (k_cg_zone_cl) instead of the global-memory path
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) k_cg_zone(const int *d_nz, ZoneArgs a, int k_lo,
-                                                        ZoneScratch g, int smem_bytes) {
+                                                        ZoneScratch g, int smem_bytes, int leave_big) {
     HFCR_PDL_WAIT();
     extern __shared__ float4 smem4[];
     __shared__ float red[96];
@@ -1236,6 +1240,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_cg_zone(const int *d_nz, ZoneArg
     for (int z = blockIdx.x; z < nz; z += gridDim.x) {
         const int k = a.zs[z + 1] - a.zs[z];
         if (k <= k_lo) continue;
+        if (leave_big && zone_smem_need(k, a.zv[z + 1] - a.zv[z], a.zg[z + 1] - a.zg[z]) > smem_bytes)
+            continue;
         solve_zone<CtaGroup>(a, z, (char *)smem4, smem_bytes, red, redd, g);
     }
 }
@@ -1428,6 +1434,325 @@ __global__ void __launch_bounds__(ZONE64_THREADS) k_cg_zone64(const int *d_nz, Z
         }
         __syncthreads();  // u and the scalars' shared words are reused by the next zone
     }
+}
+
+// ---------------------------------------------------------------------------
+// Large impact zones on a thread-block cluster: the zone's rows and touched
+// vertices are split over the CL CTAs of a cluster (CL SMs), each CTA
+// stages its share in its own shared memory, and the products that cross
+// shares read the other CTAs' shared memory directly (distributed shared
+// memory) between hardware cluster barriers.  The arithmetic is that of the
+// one-CTA staged solve (float32 Chronopoulos-Gear PCG on the float32
+// normals, block-Jacobi groups, float64 residual rounds, the same stopping
+// rules); zones too large for one SM's shared memory (which would
+// otherwise iterate on global memory) stay in shared memory, up to CL times
+// larger.  (Measured: a zone that fits one SM iterates no faster on a
+// cluster: an iteration is a chain of barriers and dependent loads either
+// way, so such zones stay on one CTA.)  Rows are split at group boundaries, so
+// the preconditioner stays local to a CTA.  Every CTA uses one layout,
+// sized for the largest share of the zone, so another CTA's array is this
+// CTA's array mapped to that rank.  Reductions: each CTA writes its
+// partial sums into every CTA's slot for it, and after the barrier each
+// CTA adds the CL slots in rank order (identical sums everywhere).
+// ---------------------------------------------------------------------------
+
+constexpr int CL = 8;               // CTAs per cluster (portable cluster size)
+constexpr int CL_THREADS = 512;
+constexpr int CL_SMEM = 200 * 1024; // dynamic shared memory per CTA
+constexpr int ZONE_CL_MIN = ZONE_BIG;  // zones of at least this many rows
+
+namespace cgx = cooperative_groups;
+
+struct ClLayout {
+    int Kc, Uc, Ec, Gc;       // capacities: rows, vertices, CSR entries, groups per CTA
+    int o_n4, o_pinv, o_vidx, o_u, o_f, o_winv, o_seg, o_ent, o_gst;
+    int bytes;
+};
+
+__device__ __forceinline__ ClLayout cl_layout(int Kc, int Uc, int Ec, int Gc) {
+    ClLayout L;
+    L.Kc = Kc; L.Uc = Uc; L.Ec = Ec; L.Gc = Gc;
+    int o = 0;
+    L.o_n4 = o;   o += 16 * Kc;
+    L.o_pinv = o; o += 16 * Kc;
+    L.o_vidx = o; o += 16 * Kc;
+    L.o_u = o;    o += 16 * Uc;
+    L.o_f = o;    o += 4 * 6 * Kc;          // r p x sv w z
+    L.o_winv = o; o += 4 * Uc;
+    L.o_seg = o;  o += 4 * (Uc + 1);
+    L.o_ent = o;  o += 4 * Ec;
+    L.o_gst = o;  o += 4 * (Gc + 1);
+    L.bytes = o;
+    return L;
+}
+
+// the partial sums of this CTA (nv values, the same in every thread) into
+// slot `rank` of every CTA's red, then after the barrier the sums over the
+// CL slots in rank order
+template <typename T, int NV>
+__device__ __forceinline__ void cl_reduce(cgx::cluster_group &cl, const T *part, T *red, T *out) {
+    if (threadIdx.x < CL * NV) {
+        const int dst = threadIdx.x / NV, v = threadIdx.x % NV;
+        T *r = cl.map_shared_rank(red, dst);
+        r[cl.block_rank() * NV + v] = part[v];
+    }
+    cl.sync();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        T t = 0;
+        for (int c = 0; c < CL; ++c) t += red[c * NV + v];
+        out[v] = t;
+    }
+}
+
+// CTA-wide float sums of three values (identical in every thread)
+__device__ __forceinline__ void cl_block3(float a, float b, float c, float *red, float *out) {
+    float sa, sb, sc;
+    block_sum3(a, b, c, red, sa, sb, sc);
+    __syncthreads();  // red is rewritten by the next call
+    out[0] = sa; out[1] = sb; out[2] = sc;
+}
+
+// one_cta_smem: the shared memory of the one-CTA solver (k_cg_zone): the
+// zones that fit it are its, this kernel takes the larger ones
+__global__ void __launch_bounds__(CL_THREADS, 1) k_cg_zone_cl(const int *d_nz, ZoneArgs a,
+                                                              ZoneScratch gs, int one_cta_smem) {
+    HFCR_PDL_WAIT();
+    cgx::cluster_group cl = cgx::this_cluster();
+    extern __shared__ float4 smem4[];
+    char *base = (char *)smem4;
+    __shared__ float redf[CL * 3];          // cluster partials (float)
+    __shared__ double redd[CL * 2];         // cluster partials (double)
+    __shared__ float bred[96];              // block reductions
+    __shared__ double bredd[CL_THREADS / 32];
+    __shared__ int rb[CL + 1], gb[CL + 1], vb[CL + 1], eb[CL + 1];
+    const int rank = cl.block_rank();
+    const int tid = threadIdx.x, nt = CL_THREADS;
+    const int nz = *d_nz;
+    const int ncl = gridDim.x / CL;
+    const int ci = blockIdx.x / CL;
+    for (int z = ci; z < nz; z += ncl) {
+        const int s0 = a.zs[z], k = a.zs[z + 1] - s0;
+        if (k < ZONE_CL_MIN) continue;
+        const int j0 = a.zv[z], U = a.zv[z + 1] - j0;
+        const int g0 = a.zg[z], G = a.zg[z + 1] - g0;
+        if (zone_smem_need(k, U, G) <= one_cta_smem) continue;   // the one-CTA solver's
+        const int e0 = a.seg[j0];
+        // shares: rows split at group boundaries (CL nearly equal group
+        // counts), vertex j in CTA j / Ucap; every CTA computes all
+        // boundaries, so every CTA derives the same layout
+        const int Ucap = (U + CL - 1) / CL;
+        if (tid <= CL) {
+            const int gc = (int)(((long long)G * tid) / CL);
+            gb[tid] = gc;
+            rb[tid] = tid == CL ? k : a.gst[g0 + gc] - s0;
+            const int vc = min(U, tid * Ucap);
+            vb[tid] = vc;
+            eb[tid] = a.seg[j0 + vc] - e0;
+        }
+        __syncthreads();
+        int Kc = 0, Ec = 0, Gc = 0;
+        for (int c = 0; c < CL; ++c) {
+            Kc = max(Kc, rb[c + 1] - rb[c]);
+            Ec = max(Ec, eb[c + 1] - eb[c]);
+            Gc = max(Gc, gb[c + 1] - gb[c]);
+        }
+        const ClLayout L = cl_layout(Kc, Ucap, Ec, Gc);
+        const double bb = [&] {
+            double t = 0.0;
+            for (int q = tid; q < k; q += nt) {
+                const double bv = a.b64[s0 + q];
+                t += bv * bv;
+            }
+            return block_sum_uniform(t, bredd);
+        }();
+        if (L.bytes > CL_SMEM) {
+            // too large for the cluster's shared memory: the first CTA solves
+            // it on global memory (the one-CTA path), the others go on
+            if (rank == 0) solve_zone<CtaGroup>(a, z, base, 0, bred, bredd, gs);
+            continue;
+        }
+        const int r0 = rb[rank], kr = rb[rank + 1] - r0;            // own rows
+        const int v0 = vb[rank], ur = vb[rank + 1] - v0;            // own vertices
+        const int gg0 = gb[rank], gr = gb[rank + 1] - gg0;          // own groups
+        const int ee0 = eb[rank], er = eb[rank + 1] - ee0;          // own CSR entries
+        float4 *n4 = (float4 *)(base + L.o_n4);
+        float4 *pinv = (float4 *)(base + L.o_pinv);
+        int4 *vidx = (int4 *)(base + L.o_vidx);
+        float4 *u = (float4 *)(base + L.o_u);
+        float *f = (float *)(base + L.o_f);
+        float *r = f, *p = f + Kc, *x = f + 2 * Kc, *sv = f + 3 * Kc, *w = f + 4 * Kc, *zz = f + 5 * Kc;
+        float *winv = (float *)(base + L.o_winv);
+        int *seg = (int *)(base + L.o_seg);
+        int *ent = (int *)(base + L.o_ent);
+        int *gst = (int *)(base + L.o_gst);
+        // stage the own share
+        for (int t = tid; t < kr; t += nt) {
+            const int4 g = a.vidx[s0 + r0 + t];
+            vidx[t] = make_int4(g.x - j0, g.y - j0, g.z - j0, g.w - j0);
+            n4[t] = a.n32[s0 + r0 + t];
+            pinv[t] = a.pinv[s0 + r0 + t];
+            a.lam[s0 + r0 + t] = 0.0;
+        }
+        for (int q = tid; q <= gr; q += nt) gst[q] = a.gst[g0 + gg0 + q] - s0 - r0;
+        for (int j = tid; j <= ur; j += nt) seg[j] = a.seg[j0 + v0 + j] - e0 - ee0;
+        for (int j = tid; j < ur; j += nt) winv[j] = a.winv[j0 + v0 + j];
+        for (int e = tid; e < er; e += nt) ent[e] = a.cval[e0 + ee0 + e] - 4 * s0;
+        // the CTA that owns row s (rows split at rb)
+        auto row_owner = [&](int sl) {
+            int c = 0;
+#pragma unroll
+            for (int q = 1; q < CL; ++q) c += sl >= rb[q];
+            return c;
+        };
+        const double target = a.rel_tol * a.rel_tol * bb;
+        const float third = 1.0f / 3.0f;
+        double rr = bb;
+        int its = 0, rounds = 0;
+        // the first round's right-hand side: b (lam = 0)
+        for (int t = tid; t < kr; t += nt) r[t] = (float)a.b64[s0 + r0 + t];
+        cl.sync();
+        while (rr > target && rounds < a.max_refine) {
+            for (int t = tid; t < kr; t += nt) { p[t] = 0.f; sv[t] = 0.f; x[t] = 0.f; }
+            // ---- float32 PCG (Chronopoulos-Gear) on the float32 normals ----
+            auto precond = [&]() {
+                for (int g = tid; g < gr; g += nt) {
+                    const int lo = gst[g], hi = gst[g + 1];
+                    float rq[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) rq[q] = lo + q < hi ? r[lo + q] : 0.f;
+                    for (int t = lo; t < hi; ++t) {
+                        const float4 m = pinv[t];
+                        zz[t] = m.x * rq[0] + m.y * rq[1] + m.z * rq[2] + m.w * rq[3];
+                    }
+                }
+            };
+            auto matvec_vertex = [&]() {   // u = M^-1 J^T z over the own vertices
+                for (int j = tid; j < ur; j += nt) {
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+                    for (int e = seg[j]; e < seg[j + 1]; ++e) {
+                        const int c = ent[e];
+                        const int sl = c >> 2;
+                        const int ow = row_owner(sl);
+                        const int li = sl - rb[ow];
+                        const float zs = *cl.map_shared_rank(zz + li, ow);
+                        const float4 nn = *cl.map_shared_rank(n4 + li, ow);
+                        const float ps = ((c & 3) ? -third : 1.0f) * zs;
+                        a0 += ps * nn.x;
+                        a1 += ps * nn.y;
+                        a2 += ps * nn.z;
+                    }
+                    const float wv = winv[j];
+                    u[j] = make_float4(wv * a0, wv * a1, wv * a2, 0.f);
+                }
+            };
+            auto matvec_rows = [&](float *ga, float *de, float *rh) {   // w = J u, partial sums
+                for (int t = tid; t < kr; t += nt) {
+                    const int4 g = vidx[t];
+                    const float4 u0 = *cl.map_shared_rank(u + g.x % Ucap, g.x / Ucap);
+                    const float4 u1 = *cl.map_shared_rank(u + g.y % Ucap, g.y / Ucap);
+                    const float4 u2 = *cl.map_shared_rank(u + g.z % Ucap, g.z / Ucap);
+                    const float4 u3 = *cl.map_shared_rank(u + g.w % Ucap, g.w / Ucap);
+                    const float4 nn = n4[t];
+                    const float ws = nn.x * (u0.x - (u1.x + u2.x + u3.x) * third) +
+                                     nn.y * (u0.y - (u1.y + u2.y + u3.y) * third) +
+                                     nn.z * (u0.z - (u1.z + u2.z + u3.z) * third);
+                    w[t] = ws;
+                    *ga += r[t] * zz[t];
+                    *de += ws * zz[t];
+                    *rh += r[t] * r[t];
+                }
+            };
+            precond();
+            cl.sync();
+            matvec_vertex();
+            cl.sync();
+            float ga = 0.f, de = 0.f, rh = 0.f;
+            matvec_rows(&ga, &de, &rh);
+            float part[3], sums[3];
+            cl_block3(ga, de, rh, bred, part);
+            cl_reduce<float, 3>(cl, part, redf, sums);
+            float gamma = sums[0], delta = sums[1], rho = sums[2];
+            const float stop = (float)a.tol * (float)a.tol * rho;
+            float alpha = gamma / delta, beta = 0.f;
+            int it = 0;
+            while (it < a.maxit && rho > stop && rho > 0.f && alpha > 0.f && isfinite(alpha)) {
+                for (int g = tid; g < gr; g += nt) {
+                    const int lo = gst[g], hi = gst[g + 1];
+                    for (int t = lo; t < hi; ++t) {
+                        const float ps = zz[t] + beta * p[t];
+                        const float ss = w[t] + beta * sv[t];
+                        p[t] = ps;
+                        sv[t] = ss;
+                        x[t] += alpha * ps;
+                        r[t] -= alpha * ss;
+                    }
+                }
+                __syncthreads();
+                precond();
+                cl.sync();
+                matvec_vertex();
+                cl.sync();
+                ga = de = rh = 0.f;
+                matvec_rows(&ga, &de, &rh);
+                cl_block3(ga, de, rh, bred, part);
+                cl_reduce<float, 3>(cl, part, redf, sums);
+                beta = sums[0] / gamma;
+                alpha = sums[0] / (sums[1] - beta * sums[0] / alpha);
+                gamma = sums[0];
+                rho = sums[2];
+                ++it;
+            }
+            its += it;
+            // ---- lam += x, then the zone's float64 residual b - A lam ----
+            for (int t = tid; t < kr; t += nt) a.lam[s0 + r0 + t] += (double)x[t];
+            __threadfence();
+            cl.sync();
+            const double third64 = 1.0 / 3.0;
+            for (int j = tid; j < ur; j += nt) {
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+                for (int e = seg[j]; e < seg[j + 1]; ++e) {
+                    const int c = ent[e];
+                    const int sl = c >> 2;
+                    const double ps = ((c & 3) ? -third64 : 1.0) * __ldcg(a.lam + s0 + sl);
+                    const double4_32a nn = a.n64[s0 + sl];
+                    a0 += ps * nn.x;
+                    a1 += ps * nn.y;
+                    a2 += ps * nn.z;
+                }
+                const double wv = (double)winv[j];
+                double *uo = a.u64 + 3 * (size_t)(j0 + v0 + j);
+                uo[0] = wv * a0;
+                uo[1] = wv * a1;
+                uo[2] = wv * a2;
+            }
+            __threadfence();
+            cl.sync();
+            double rrl = 0.0;
+            for (int t = tid; t < kr; t += nt) {
+                const int4 g = vidx[t];
+                const double *ux = a.u64 + 3 * (size_t)(j0 + g.x), *ua = a.u64 + 3 * (size_t)(j0 + g.y);
+                const double *ub = a.u64 + 3 * (size_t)(j0 + g.z), *uc = a.u64 + 3 * (size_t)(j0 + g.w);
+                double d[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    d[c] = __ldcg(ux + c) - (__ldcg(ua + c) + __ldcg(ub + c) + __ldcg(uc + c)) * third64;
+                const double4_32a nn = a.n64[s0 + r0 + t];
+                const double rv = a.b64[s0 + r0 + t] - (nn.x * d[0] + nn.y * d[1] + nn.z * d[2]);
+                r[t] = (float)rv;
+                rrl += rv * rv;
+            }
+            double pd[2] = {block_sum_uniform(rrl, bredd), 0.0}, sd[2];
+            cl_reduce<double, 2>(cl, pd, redd, sd);
+            rr = sd[0];
+            ++rounds;
+        }
+        if (rank == 0 && tid == 0) zone_finish(a, z, rr, bb, its, rounds, true);
+        // the shares (shared memory) of this zone are read by other CTAs until
+        // every CTA has passed this barrier
+        cl.sync();
+    }
+    cl.sync();
 }
 
 // |r| / |b| of the whole system from the zones' |r|^2 and |b|^2 (fixed
@@ -2085,6 +2410,7 @@ void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int ca
 // dynamic shared memory granted to the zone CG kernels (0: the global-memory
 // path runs); set once per process, outside any stream capture
 static int g_fast_smem = -1, g_zone_pair_smem = 0, g_warp_zone_smem = 0;
+static bool g_cluster_ok = false;  // k_cg_zone_cl can be launched on this device
 
 void solver_init() {
     if (g_fast_smem >= 0) return;
@@ -2098,6 +2424,27 @@ void solver_init() {
     g_warp_zone_smem = cudaFuncSetAttribute(k_cg_zone_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             wz) == cudaSuccess ? wz : 0;
     if (!g_warp_zone_smem) cudaGetLastError();
+    // the cluster solver of large zones: its shared memory, and whether a
+    // cluster of CL such CTAs fits on this device at all
+    g_cluster_ok = false;
+    if (cudaFuncSetAttribute(k_cg_zone_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, CL_SMEM) ==
+        cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(CL);
+        cfg.blockDim = dim3(CL_THREADS);
+        cfg.dynamicSmemBytes = CL_SMEM;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        g_cluster_ok = cudaOccupancyMaxActiveClusters(&ncl, (const void *)k_cg_zone_cl, &cfg) ==
+                           cudaSuccess && ncl > 0;
+    }
+    cudaGetLastError();
 }
 
 // co-resident CTAs of k_setup on this device (0: cooperative launch unavailable)
@@ -2342,8 +2689,31 @@ void solve(const SolveParams &p, const MeshPair &mp, const int *d_k, int cap, So
     if (zbig > 152) zbig = 152;
     { launch_pdl(k_cg_zone_pair, zpair, 512, g_zone_pair_smem, s, sb.d_nz, za, warp_max, gs,
                  g_zone_pair_smem); note_launch(); }
+    // zones of ZONE_BIG rows or more: one 1,024-thread CTA each when they fit
+    // its shared memory; larger ones on a cluster of CL CTAs (or, without
+    // clusters, on global memory)
     { launch_pdl(k_cg_zone<CG_THREADS>, zbig, CG_THREADS, fast_smem, s, sb.d_nz, za, ZONE_BIG - 1,
-                 gs, fast_smem); note_launch(); }
+                 gs, fast_smem, g_cluster_ok ? 1 : 0); note_launch(); }
+    if (g_cluster_ok) {
+        int ncl = (cap + ZONE_CL_MIN - 1) / ZONE_CL_MIN;
+        if (ncl > 152 / CL) ncl = 152 / CL;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(ncl * CL);
+        cfg.blockDim = dim3(CL_THREADS);
+        cfg.dynamicSmemBytes = CL_SMEM;
+        cfg.stream = s;
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 2;
+        cudaLaunchKernelEx(&cfg, k_cg_zone_cl, (const int *)sb.d_nz, za, gs, fast_smem);
+        note_launch();
+    }
     { launch_pdl(k_zone_final, 1, 256, 0, s, sb.d_nz, sb.r64, sb.q64, p.rel_tol, sb.dwork,
                  sb.iwork); note_launch(); }
 }

@@ -7,9 +7,10 @@ pairs face j with its own edge-mesh vertex x0, so a strip's stencils share
 face vertices with their neighbours (one zone per strip) and no vertex
 with another strip.  Every row has its own x0, so the system is positive
 definite.  Zone sizes: 20 stencils (one warp), 100 (a 256-thread half
-CTA), 600 (a whole 512-thread CTA), 1,500 (a 1,024-thread CTA), and 700
-zones of 40 stencils (more zones than the half-CTA solvers, so they are
-handed out by the counter).  The same system through the float64 per-zone
+CTA), 600 (a whole 512-thread CTA), 1,500 (a 1,024-thread CTA), 3,000 (too
+large for one CTA's shared memory: a cluster of CTAs sharing theirs), and
+700 zones of 40 stencils (more zones than the half-CTA solvers, so they
+are handed out by the counter).  The same system through the float64 per-zone
 solver of the plain float64 form (one CTA per zone, every size) and the
 one-CTA global float64 CG, on float64 positions."""
 import numpy as np
@@ -60,7 +61,7 @@ def strips(sizes, rng):
 def test_zone_size_classes_against_oracle(api, solver, dtype, tol):
     import torch
     rng = np.random.default_rng(1409)
-    sizes = [20, 20, 20, 100, 100, 100, 600, 600, 1500] + [40] * 700
+    sizes = [20, 20, 20, 100, 100, 100, 600, 600, 1500, 3000] + [40] * 700
     VB, TB, _ = strips(sizes, rng)
     k = sum(sizes)
     assert len(TB) == k
