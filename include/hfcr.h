@@ -30,6 +30,15 @@
  *  - Vertex and face ids in pairs and stencils are local to their mesh.
  *  - Errors are returned as hfcr_status; no C++ exception crosses the ABI.
  *    hfcr_last_error(ctx) gives a human-readable message.
+ *  - A context keeps, between calls, data derived from the caller's
+ *    buffers, keyed by their addresses and sizes: the traversal order and
+ *    the vertex adjacency of a caller's edge list, and the hierarchy over a
+ *    face mesh (refitted to the current positions on every call, rebuilt
+ *    every bvh_rebuild_interval calls).  The positions may change freely.
+ *    An edge list or a batch's segment table whose contents change while
+ *    the same buffer is passed again must come with a new reservation
+ *    (hfcr_reserve with larger sizes frees everything kept), or set
+ *    bvh_rebuild_interval to 1 and pass the edges in a fresh buffer.
  *
  * Readings of the paper fixed by this interface:
  *  - An E-F intersection is a strict crossing of the face's plane by the
@@ -131,6 +140,11 @@ typedef struct {
                                0 < tol < 1 (0: default 1e-10) */
     double amplification_limit; /* hfcr_resolve counts the responses whose max_dx / max_rhs
                                    exceeds it (0: default 1000) */
+    int32_t bvh_rebuild_interval; /* a hierarchy built over the same face mesh (triangle buffer,
+                                     counts, batch table) by an earlier call is refitted to the
+                                     current positions (exact boxes) instead of rebuilt, up to this
+                                     many calls in a row (0: default 8; 1: rebuild every call).
+                                     Only the traversal's speed depends on it, never the pairs. */
 } hfcr_options;
 
 typedef struct {

@@ -72,6 +72,15 @@ struct hfcr_ctx {
     int *h_iw = nullptr;          // solver control words
     SortTemp sort;
     Bvh bvh[2];                   // [0]: faces of B (direction 0), [1]: faces of A (direction 1)
+    // what each hierarchy was last built over, and the calls since: a later
+    // call over the same faces refits it (exact boxes) and rebuilds it only
+    // every opt.bvh_rebuild_interval calls
+    struct BvhKey {
+        const void *tris = nullptr;
+        const int *segs = nullptr;
+        int n_tris = -1, n_verts = -1, nseg = -1, dtype = -1;
+    } bvh_key[2];
+    int bvh_age[2] = {0, 0};
     int *edges[2] = {nullptr, nullptr};
     // traversal order of each edge list (a permutation; it only steers
     // performance, so a stale one for a moved mesh is still correct)
@@ -162,6 +171,10 @@ void free_all(hfcr_ctx *c) {
     c->field = c->field_alt = nullptr;
     c->ring = nullptr;
     c->dscr = DiffScratch();
+    for (int i = 0; i < 2; ++i) {
+        c->bvh_key[i] = hfcr_ctx::BvhKey();
+        c->bvh_age[i] = 0;
+    }
     c->adj_src[0] = c->adj_src[1] = nullptr;
     c->eorder[0] = c->eorder[1] = nullptr;
     c->eorder_src[0] = c->eorder_src[1] = nullptr;
@@ -339,6 +352,51 @@ hfcr_status plan_detect(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, b
     pl.edge_bits = bits_for(maxe > 1 ? maxe : 2);
     pl.face_bits = bits_for(maxf > 1 ? maxf : 2);
     return HFCR_OK;
+}
+
+// Whether the hierarchy of direction d can be refitted instead of rebuilt
+// for faces F: it was built over the same triangle buffer, counts and
+// segment table, fewer than bvh_rebuild_interval calls ago.
+bool bvh_reusable(const hfcr_ctx *ctx, int d, const hfcr_mesh &F, const DetectPlan &pl) {
+    const hfcr_ctx::BvhKey &k = ctx->bvh_key[d];
+    return ctx->opt.bvh_rebuild_interval > 1 && k.tris == F.tris && k.n_tris == F.n_tris &&
+           k.n_verts == F.n_verts && k.segs == pl.segs && k.nseg == pl.nseg && k.dtype == F.dtype &&
+           ctx->bvh_age[d] < ctx->opt.bvh_rebuild_interval - 1 && ctx->bvh[d].n == F.n_tris;
+}
+
+// The hierarchies a call may keep (built[d] true: refit only)
+void bvh_start(const hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, const DetectPlan &pl,
+               bool *built) {
+    built[0] = bvh_reusable(ctx, 0, *B, pl);
+    built[1] = bvh_reusable(ctx, 1, *A, pl);
+}
+
+void bvh_note(hfcr_ctx *ctx, int d, const hfcr_mesh &F, const DetectPlan &pl, bool rebuilt);
+
+// After a call that started from kept[]: record the hierarchies it built
+// and age the ones it kept
+void bvh_finish(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, const DetectPlan &pl,
+                const bool *kept, const bool *built) {
+    for (int d = 0; d < 2; ++d) {
+        if (kept[d]) bvh_note(ctx, d, d == 0 ? *B : *A, pl, false);
+        else if (built[d]) bvh_note(ctx, d, d == 0 ? *B : *A, pl, true);
+    }
+}
+
+// After a call: record a fresh build of direction d, or age the kept one.
+void bvh_note(hfcr_ctx *ctx, int d, const hfcr_mesh &F, const DetectPlan &pl, bool rebuilt) {
+    if (rebuilt) {
+        hfcr_ctx::BvhKey &k = ctx->bvh_key[d];
+        k.tris = F.tris;
+        k.n_tris = F.n_tris;
+        k.n_verts = F.n_verts;
+        k.segs = pl.segs;
+        k.nseg = pl.nseg;
+        k.dtype = F.dtype;
+        ctx->bvh_age[d] = 0;
+    } else {
+        ++ctx->bvh_age[d];
+    }
 }
 
 // Launches the traversal of the active directions; positions validated and
@@ -741,6 +799,7 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
     c->opt.diffuse_max_iters = 1000;
     c->opt.diffuse_tol = 1e-10;
     c->opt.amplification_limit = 1000.0;
+    c->opt.bvh_rebuild_interval = 8;
     if (opt) {
         c->opt = *opt;
         if (c->opt.max_cg_iters <= 0) c->opt.max_cg_iters = 500;
@@ -763,6 +822,7 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
         if (c->opt.diffuse_max_iters == 0) c->opt.diffuse_max_iters = 1000;
         if (c->opt.diffuse_tol == 0.0) c->opt.diffuse_tol = 1e-10;
         if (!(c->opt.amplification_limit > 0.0)) c->opt.amplification_limit = 1000.0;
+        if (c->opt.bvh_rebuild_interval <= 0) c->opt.bvh_rebuild_interval = 8;
         if (!(c->opt.diffuse_tol > 0.0 && c->opt.diffuse_tol < 1.0) || c->opt.diffuse_max_iters < 0 ||
             c->opt.diffuse_max_iters > 100000) {
             delete c;
@@ -979,8 +1039,11 @@ static hfcr_status detect_impl(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mes
     bool dir0 = B->oriented != 0, dir1 = A->oriented != 0;
     DetectPlan pl;
     if ((st = plan_detect(ctx, A, B, dir0, dir1, pl, s, segs, nseg))) return st;
-    bool built[2] = {false, false};
+    bool built[2];
+    bvh_start(ctx, A, B, pl, built);
+    const bool kept[2] = {built[0], built[1]};
     launch_detect(ctx, A, B, dir0, dir1, pl, built, s);
+    bvh_finish(ctx, A, B, pl, kept, built);
     if ((st = read_back(ctx, s))) return st;
     int P = ctx->h_cnt[C_PAIRS];
     *n_out = P;
@@ -1138,7 +1201,9 @@ static hfcr_status resolve_impl(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, const
     DetectPlan pl;
     if ((st = plan_detect(ctx, A, B, has0, has1, pl, s, segs, nseg))) return st;
     if (diffusing(ctx) && (st = prepare_diffusion(ctx, A, B, pl, s))) return st;
-    bool built[2] = {false, false};
+    bool built[2];
+    bvh_start(ctx, A, B, pl, built);
+    const bool kept[2] = {built[0], built[1]};
     int quiet = 0;
     for (int it = 0; it < max_iters; ++it) {
         bool d0 = has0, d1 = has1;
@@ -1178,6 +1243,8 @@ static hfcr_status resolve_impl(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, const
         if (ctx->h_dw[0] > loc.worst_rel_residual) loc.worst_rel_residual = ctx->h_dw[0];
     }
     if (info) *info = loc;
+    // the hierarchies built by this call, or kept, for the next call
+    bvh_finish(ctx, A, B, pl, kept, built);
     CK(cudaStreamSynchronize(s));
     if (s != user) {
         CK(cudaEventRecord(ctx->ev_out, s));
@@ -1213,6 +1280,8 @@ hfcr_status hfcr_autotune(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
     if ((st = plan_detect(ctx, A, B, dir0, dir1, pl, s, segs, segs ? n_pairs : 1))) return st;
     bool built[2] = {false, false};
     launch_detect(ctx, A, B, dir0, dir1, pl, built, s);  // builds and refits the hierarchies
+    const bool none[2] = {false, false};
+    bvh_finish(ctx, A, B, pl, none, built);
     if ((st = read_back(ctx, s))) return st;
     // traversal launches per timed call (one per active direction with
     // work): the times below are per launch, as a repair iteration of one
