@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the cloth/torus, two-tori, two-spheres and batch sections")
     ap.add_argument("--frame-log", default=None, help="write a per-frame CSV of the last timed sequence")
+    ap.add_argument("--profile", default=None, metavar="CASE",
+                    help="profiling run instead of the bench: 'frame:N' (the frame sequence up to "
+                         "frame N), 'cloth_torus' or 'batch' (one iteration after three); the "
+                         "profiled call runs inside the NVTX range 'profile'")
     return ap.parse_args()
 
 
@@ -227,6 +231,7 @@ class Sequence:
         self.A = api.Mesh(*v[:3], ta, False, edges=ea)
         self.B = api.Mesh(*v[3:], tb, True, edges=eb)
         self.ne = int(ea.shape[0])
+        self.ne_b = int(eb.shape[0])
         self.motion = sc.meta["motion"]
         self.params = self.motion.device_params(torch, dev)
 
@@ -792,6 +797,78 @@ def run_reference(args, ws, rank):
 
 
 # ---------------------------------------------------------------------------
+# profiling runs (for ncu: --nvtx --nvtx-include "profile/")
+# ---------------------------------------------------------------------------
+
+def run_profile(case, api, torch, dev, stream):
+    """One call of a bench workload inside the NVTX range 'profile', after
+    the same warm-up the bench gives it (autotuner, earlier frames); prints
+    one JSON line describing the profiled call."""
+    import numpy as np
+    import meshgen
+    out = {"profile": case}
+    if case.startswith("frame:"):
+        target = int(case.split(":", 1)[1])
+        sc = meshgen.scene_c5()
+        seq = Sequence(api, torch, dev, sc, np.float32)
+        out["traverse_variant"], _ = seq.ctx.hfcr_autotune(seq.A, seq.B)
+        seq.restore()
+        for f in range(target + 1):
+            seq.advance(f)
+            if f == target:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_push("profile")
+            info = seq.resolve()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        seq.close()
+    elif case in ("cloth_torus", "batch"):
+        if case == "cloth_torus":
+            sc = meshgen.scene_c2()
+            VA, TA, VB, TB, segs = sc.A.V, sc.A.T, sc.B.V, sc.B.T, None
+            oriented_a = False
+        else:
+            VA, TA, VB, TB, segs = meshgen.concat_batch(meshgen.scene_c4())
+            oriented_a = True
+        ctx = api.Context()
+        ctx.hfcr_reserve(max(len(VA), len(VB)), max(len(TA), len(TB)), 1 << (21 if segs is not None else 16))
+        xyz = [torch.tensor(np.ascontiguousarray(V.astype(np.float32)[:, c]), device=dev)
+               for V in (VA, VB) for c in range(3)]
+        ta, tb = torch.tensor(TA, device=dev), torch.tensor(TB, device=dev)
+        ea = torch.zeros((3 * len(TA), 2), dtype=torch.int32, device=dev)
+        ea = ea[:ctx.hfcr_build_edges(ta, len(VA), ea)].contiguous()
+        pos, pos0, v = packed(torch, xyz)
+        A = api.Mesh(*v[:3], ta, oriented_a, edges=ea)
+        if segs is not None:
+            eb = torch.zeros((3 * len(TB), 2), dtype=torch.int32, device=dev)
+            eb = eb[:ctx.hfcr_build_edges(tb, len(VB), eb)].contiguous()
+            B = api.Mesh(*v[3:], tb, True, edges=eb)
+            dsegs = torch.tensor(segs, device=dev)
+            out["traverse_variant"], _ = ctx.hfcr_autotune(A, B, dsegs)
+            call = lambda: ctx.hfcr_resolve_batch(A, B, dsegs, D_POST, 1)
+        else:
+            B = api.Mesh(*v[3:], tb, True)
+            out["traverse_variant"], _ = ctx.hfcr_autotune(A, B)
+            call = lambda: ctx.hfcr_resolve(A, B, D_POST, 1)
+        for _ in range(3):
+            pos.copy_(pos0, non_blocking=True)
+            call()
+        pos.copy_(pos0, non_blocking=True)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profile")
+        info = call()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        ctx.close()
+    else:
+        raise SystemExit(f"unknown profile case {case!r}")
+    out.update(pairs=int(info.pairs_first), stencils=int(info.total_stencils),
+               cg_iters=int(info.cg_iters), solver_path=int(info.solver_path),
+               diffuse_cg_iters=int(info.diffuse_cg_iters))
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
 
 def main():
     args = parse()
@@ -816,6 +893,9 @@ def main():
     # a dedicated stream (the legacy default stream cannot be graph-captured)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
+    if args.profile:
+        run_profile(args.profile, api, torch, dev, stream)
+        return
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     F = args.frames
 
@@ -887,12 +967,30 @@ def main():
     alg_trav = int(sc.A.n_verts * 12 + seq.ne * 8 + sc.B.n_verts * 12 + sc.B.n_tris * 12 + P_mean * 8)
     ach_trav = alg_trav / (trav_ms * 1e-3) / 1e9
     frame_bytes = (sc.A.n_verts + sc.B.n_verts) * 12 * 2 + seq.ne * 8 + sc.B.n_tris * 12
+    # the band CG (one launch per frame): compulsory bytes per free band
+    # vertex = its index 4 + CSR offsets 8 + neighbour ids 4 x degree + the
+    # field read 24 and written 24 (float64 xyz); the iterations' records
+    # stay on chip / in L2 and are not compulsory
+    band_ms = prof["band_cg"][0] / max(1, prof["band_cg"][1])
+    nb_mean = statistics.mean(int(i.band_vertices) for i in infos)
+    deg = 2.0 * (seq.ne + seq.ne_b) / (sc.A.n_verts + sc.B.n_verts)
+    alg_band = int(nb_mean * (60 + 4 * deg))
+    band_iters = statistics.mean(int(i.diffuse_cg_iters) for i in infos)
+    ach_band = alg_band / (band_ms * 1e-3) / 1e9
     roof = {
         "k_traverse": {"kernel": "k_traverse (BVH traversal + exact narrow phase)", "bound": "hbm",
                        "achieved": round(ach_trav, 2), "peak": peak, "peak_kind": peak_kind,
                        "unit": "GB/s", "frac": round(ach_trav / peak, 5),
                        "traffic": profiled_traffic("k_traverse"), "alg_bytes_per_launch": alg_trav,
                        "avg_launch_ms": round(trav_ms, 5), "launches_timed": prof["traverse"][1]},
+        "k_band_cg": {"kernel": "k_band_cg (harmonic diffusion: CG on the band Laplacian, one "
+                                "cooperative launch)", "bound": "hbm",
+                      "achieved": round(ach_band, 3), "peak": peak, "peak_kind": peak_kind,
+                      "unit": "GB/s", "frac": round(ach_band / peak, 7),
+                      "traffic": profiled_traffic("k_band_cg"), "alg_bytes_per_launch": alg_band,
+                      "avg_launch_ms": round(band_ms, 5), "launches_timed": prof["band_cg"][1],
+                      "band_vertices_mean": round(nb_mean, 1), "cg_iters_mean": round(band_iters, 2),
+                      "us_per_cg_iter": round(1e3 * band_ms / band_iters, 3) if band_iters else None},
         "whole_frame": {"bound": "hbm", "alg_bytes_per_frame": frame_bytes,
                         "achieved": round(frame_bytes / (per_frame * 1e-3) / 1e9, 2), "peak": peak,
                         "unit": "GB/s", "frac": round(frame_bytes / (per_frame * 1e-3) / 1e9 / peak, 5),

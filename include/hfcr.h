@@ -187,6 +187,8 @@ typedef struct {
     int32_t amplified_iters;       /* responses whose amplification exceeded the option
                                       amplification_limit: an ill-conditioned system moved
                                       vertices far more than the penetration depths */
+    int64_t band_vertices;         /* harmonic diffusion: free band vertices (the unknowns of
+                                      the band's Dirichlet problem), summed over the iterations */
 } hfcr_resolve_info;
 
 /* Stages timed by the optional profiler (instrumentation; the paper has no
@@ -200,7 +202,9 @@ typedef enum {
     HFCR_STAGE_SOLVE = 5,     /* Eq. 7 / Eq. 8 solve */
     HFCR_STAGE_DISPLACE = 6,  /* x' - x and its application */
     HFCR_STAGE_DIFFUSE = 7,   /* diffusion of the displacement (Sec. 5) and its application */
-    HFCR_N_STAGES = 8
+    HFCR_STAGE_BAND_CG = 8,   /* the band CG kernel alone: its intervals lie inside DIFFUSE's,
+                                 so it is not added to the other stages */
+    HFCR_N_STAGES = 9
 } hfcr_stage;
 
 typedef struct {

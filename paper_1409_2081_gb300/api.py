@@ -82,11 +82,13 @@ class hfcr_resolve_info(ctypes.Structure):
                 ("cg_iters", ctypes.c_int32), ("worst_rel_residual", ctypes.c_double),
                 ("stats", hfcr_detect_stats), ("solver_path", ctypes.c_int32),
                 ("diffuse_cg_iters", ctypes.c_int32), ("diffuse_unconverged", ctypes.c_int32),
-                ("worst_amplification", ctypes.c_double), ("amplified_iters", ctypes.c_int32)]
+                ("worst_amplification", ctypes.c_double), ("amplified_iters", ctypes.c_int32),
+                ("band_vertices", ctypes.c_int64)]
 
 
-HFCR_N_STAGES = 8
-STAGES = ("validate", "bvh", "traverse", "stencils", "assemble", "solve", "displace", "diffuse")
+HFCR_N_STAGES = 9
+STAGES = ("validate", "bvh", "traverse", "stencils", "assemble", "solve", "displace", "diffuse",
+          "band_cg")
 
 
 class hfcr_profile(ctypes.Structure):

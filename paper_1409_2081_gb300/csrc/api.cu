@@ -230,6 +230,14 @@ void prof_end(hfcr_ctx *c, int stage, cudaStream_t s) {
         }
 }
 
+// the band CG's own interval, nested inside the diffusion stage's
+void band_mark(void *c, int begin, cudaStream_t s) {
+    if (begin)
+        prof_begin((hfcr_ctx *)c, HFCR_STAGE_BAND_CG, s);
+    else
+        prof_end((hfcr_ctx *)c, HFCR_STAGE_BAND_CG, s);
+}
+
 // accumulates every closed interval (waits for its end event)
 void prof_collect(hfcr_ctx *c) {
     std::vector<ProfInterval> keep;
@@ -657,10 +665,15 @@ void enqueue_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bo
     DiffMeshArgs da, db;
     da.ptr = ctx->adj_ptr[0]; da.nbr = ctx->adj_nbr[0]; da.inv_mass = A->inv_mass; da.n = A->n_verts;
     db.ptr = ctx->adj_ptr[1]; db.nbr = ctx->adj_nbr[1]; db.inv_mass = B->inv_mass; db.n = B->n_verts;
+    StageMark mark;
+    if (ctx->prof_on) {
+        mark.fn = band_mark;
+        mark.arg = ctx;
+    }
     const double *u = diffuse_field(da, db, ctx->field, ctx->field_alt, ctx->ring,
                                     ctx->opt.diffuse_rings, ctx->opt.diffuse_sweeps,
                                     ctx->opt.diffuse_tol, ctx->opt.diffuse_max_iters, ctx->dscr,
-                                    ctx->sort, ctx->d_status, s);
+                                    ctx->sort, ctx->d_status, s, mark);
     apply_field(*A, *B, ctx->ring, ctx->opt.diffuse_rings, u, s);
     prof_end(ctx, HFCR_STAGE_DIFFUSE, s);
 }
@@ -1221,6 +1234,7 @@ static hfcr_status resolve_impl(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, const
         add_stats(&loc.stats, *ctx->h_stats);
         loc.stats.brute_force_equiv += single_pair_bf(pl, d0, d1, A, B);
         loc.diffuse_cg_iters += ctx->h_cnt[C_DIFF_ITERS];
+        if (diffusing(ctx) && ctx->opt.diffuse_sweeps <= 0) loc.band_vertices += ctx->h_cnt[C_NFREE];
         if (ctx->h_cnt[C_DIFF_FAIL]) loc.diffuse_unconverged += 1;
         if (it == 0) loc.pairs_first = P;
         loc.pairs_last = P;

@@ -693,7 +693,7 @@ void diffusion_init() { (void)band_grid_max(); }
 const double *diffuse_field(const DiffMeshArgs &a, const DiffMeshArgs &b, double *u, double *u_alt,
                             int *ring, int rings, int sweeps, double tol, int max_iters,
                             const DiffScratch &ds, SortTemp &t, uint32_t *d_status,
-                            cudaStream_t s) {
+                            cudaStream_t s, const StageMark &mark) {
     DPair P = make_pair(a, b);
     if (P.ntot <= 0 || rings <= 0) return u;
     const int far = rings + 1, nb = blocks(P.ntot);
@@ -743,8 +743,10 @@ const double *diffuse_field(const DiffMeshArgs &a, const DiffMeshArgs &b, double
     ba.cap = ds.cap;
     cudaMemsetAsync(ds.bar, 0, sizeof(unsigned), s);
     void *args[] = {&ba};
-    if (cudaLaunchCooperativeKernel((const void *)k_band_cg, grid, BAND_TPB, args, 0, s) !=
-        cudaSuccess) {
+    mark(1, s);
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_band_cg, grid, BAND_TPB, args, 0, s);
+    mark(0, s);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         cudaMemsetAsync(ds.ctl + 1, 0xff, sizeof(int), s);  // reported as not converged
         return u;
