@@ -131,7 +131,7 @@ def measured_peak_hbm():
 KERNELS = {
     "k_traverse": (("detect.cu", "predicates.cuh"), "k_traverse_frame_sequence.md"),
     "k_traverse_batch": (("detect.cu", "predicates.cuh"), "k_traverse_batch.md"),
-    "k_band_cg": (("diffuse.cu",), "k_band_cg_frame_sequence.md"),
+    "k_band_cl": (("diffuse.cu",), "k_band_cl_frame_sequence.md"),
     "k_cg_zone_pair": (("solve.cu",), "k_cg_zone_pair_cloth_torus.md"),
     "k_refit": (("bvh.cu",), "k_refit_frame_sequence.md"),
 }
@@ -944,14 +944,15 @@ def main():
     slow = [{"frame": f, "ms": round(last[f], 4), "pairs": int(infos[f].pairs_first),
              "stencils": int(infos[f].total_stencils), "cg_iters": int(infos[f].cg_iters),
              "solver_path": int(infos[f].solver_path),
-             "diffuse_cg_iters": int(infos[f].diffuse_cg_iters)} for f in order[:6]]
+             "diffuse_cg_iters": int(infos[f].diffuse_cg_iters),
+             "band_vertices": int(infos[f].band_vertices)} for f in order[:6]]
     if args.frame_log:
         with open(args.frame_log, "w") as fh:
-            fh.write("frame,ms,pairs,stencils,cg_iters,solver_path,diffuse_cg_iters\n")
+            fh.write("frame,ms,pairs,stencils,cg_iters,solver_path,diffuse_cg_iters,band_vertices\n")
             for f in range(F):
                 i = infos[f]
                 fh.write(f"{f},{last[f]:.5f},{i.pairs_first},{i.total_stencils},{i.cg_iters},"
-                         f"{i.solver_path},{i.diffuse_cg_iters}\n")
+                         f"{i.solver_path},{i.diffuse_cg_iters},{i.band_vertices}\n")
 
     # profiled pass: CUDA events around every stage (plain launches)
     seq.ctx.hfcr_profile_enable(True)
@@ -967,7 +968,7 @@ def main():
     alg_trav = int(sc.A.n_verts * 12 + seq.ne * 8 + sc.B.n_verts * 12 + sc.B.n_tris * 12 + P_mean * 8)
     ach_trav = alg_trav / (trav_ms * 1e-3) / 1e9
     frame_bytes = (sc.A.n_verts + sc.B.n_verts) * 12 * 2 + seq.ne * 8 + sc.B.n_tris * 12
-    # the band CG (one launch per frame): compulsory bytes per free band
+    # the band CG (one cluster launch per frame): compulsory bytes per free band
     # vertex = its index 4 + CSR offsets 8 + neighbour ids 4 x degree + the
     # field read 24 and written 24 (float64 xyz); the iterations' records
     # stay on chip / in L2 and are not compulsory
@@ -983,11 +984,12 @@ def main():
                        "unit": "GB/s", "frac": round(ach_trav / peak, 5),
                        "traffic": profiled_traffic("k_traverse"), "alg_bytes_per_launch": alg_trav,
                        "avg_launch_ms": round(trav_ms, 5), "launches_timed": prof["traverse"][1]},
-        "k_band_cg": {"kernel": "k_band_cg (harmonic diffusion: CG on the band Laplacian, one "
-                                "cooperative launch)", "bound": "hbm",
+        "k_band_cl": {"kernel": "k_band_cl (harmonic diffusion: CG on the band Laplacian on one "
+                                "thread-block cluster; k_band_cg, the grid-wide form, takes bands "
+                                "beyond the cluster's capacity)", "bound": "hbm",
                       "achieved": round(ach_band, 3), "peak": peak, "peak_kind": peak_kind,
                       "unit": "GB/s", "frac": round(ach_band / peak, 7),
-                      "traffic": profiled_traffic("k_band_cg"), "alg_bytes_per_launch": alg_band,
+                      "traffic": profiled_traffic("k_band_cl"), "alg_bytes_per_launch": alg_band,
                       "avg_launch_ms": round(band_ms, 5), "launches_timed": prof["band_cg"][1],
                       "band_vertices_mean": round(nb_mean, 1), "cg_iters_mean": round(band_iters, 2),
                       "us_per_cg_iter": round(1e3 * band_ms / band_iters, 3) if band_iters else None},

@@ -10,8 +10,9 @@
 //     deg(v) u_v - sum of u_w over band neighbours w
 //         = sum of the Dirichlet values of v's other neighbours
 // is solved for each coordinate, by Jacobi-preconditioned conjugate
-// gradients to a relative residual `tol` (k_band_cg, one cooperative launch
-// over the band's vertices).  The older fixed-sweep form (S Jacobi sweeps of
+// gradients to a relative residual `tol` (k_band_cl on one thread-block
+// cluster for bands of up to some 27,000 vertices, k_band_cg over the whole
+// grid beyond).  The older fixed-sweep form (S Jacobi sweeps of
 // the neighbour mean from zero, whose limit is that field) stays available
 // as a named approximation.
 //
@@ -25,6 +26,8 @@
 // iteration.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <cooperative_groups.h>
 
 #include "internal.h"
 #include "sortdev.cuh"
@@ -418,10 +421,12 @@ __device__ __forceinline__ void band_neighbours(const float *recs, const int *cn
 // it needs no barrier of its own either.  Band vertex i belongs to CTA i
 // mod parts, so the band spreads over every CTA taking part; the
 // neighbours' band indices are resolved once (cnbr).  All reductions run
-// in a fixed order, so the result is deterministic.
-__global__ void __launch_bounds__(BAND_TPB) k_band_cg(BandArgs a) {
+// in a fixed order, so the result is deterministic.  This kernel takes the
+// bands larger than the cluster kernel (k_band_cl) holds.
+__global__ void __launch_bounds__(BAND_TPB) k_band_cg(BandArgs a, int limit) {
     HFCR_PDL_WAIT();
     const int n = *a.d_nfree;
+    if (n <= limit) return;  // the cluster kernel's band
     int parts = (n + BAND_MIN_PER_CTA - 1) / BAND_MIN_PER_CTA;
     parts = parts < 1 ? 1 : (parts > (int)gridDim.x ? (int)gridDim.x : parts);
     if ((int)blockIdx.x >= parts) return;
@@ -644,6 +649,340 @@ __global__ void __launch_bounds__(BAND_TPB) k_band_cg(BandArgs a) {
     }
 }
 
+// ---- the band on one thread-block cluster ----
+//
+// The same refinement rounds and Chronopoulos-Gear iterations as k_band_cg
+// on one cluster of BCL_THREADS-thread CTAs, for bands of up to `limit`
+// vertices (the bands of a frame sequence are a few thousand to a few tens
+// of thousands of vertices: one grid-wide barrier per iteration over every
+// SM costs more than the iteration's work).  Band vertex i belongs to CTA
+// i / chunk and keeps its CG state in that CTA's shared memory: a 48-byte
+// record (r with 1/deg, and the float64 u of the rounds' residuals: the
+// part other CTAs read, a neighbour's z being r / deg), and p, s, x, w.
+// Each neighbour slot of cnbr holds -2 - (local index) for a neighbour of
+// the same CTA (read from shared memory), the band index for one of
+// another CTA, -1 for a Dirichlet neighbour.  Other CTAs' values are read
+// from global copies (r as float4 in rec, u in u64) that every vertex
+// writes beside its record, through L2: random reads of other SMs' shared
+// memory serialise on the SM-to-SM network, L2 serves them in parallel.
+// An iteration has two cluster barriers (the neighbours' r, then
+// the sums); every CTA stores its sums into every CTA's receive slots
+// before the second, and each folds them in rank order after it, so every
+// CTA takes the same decisions from the same values.  Hardware cluster
+// barriers: nothing here spins.
+namespace cgx = cooperative_groups;
+
+constexpr int BCL_THREADS = 1024;
+constexpr int BCL_MAX = 16;                  // CTAs per cluster at most
+constexpr int BCL_SMEM = 200 * 1024;         // dynamic shared memory per CTA
+constexpr int BCL_VBYTES = 48 + 4 * 16 + 8;  // record, p s x w (float4), slot range
+
+struct __align__(16) BclRec {
+    float4 r;     // r (x, y, z) and 1 / deg
+    double u[3];  // the float64 solution of the rounds
+    double pad;
+};
+
+struct BclState {
+    float recv[2][BCL_MAX][9];    // the CTAs' float sums, by parity and sender
+    double recvd[2][BCL_MAX][3];  // their float64 sums
+    float sums[9];
+    double sumsd[3];
+    float scr[32 * 9];
+    double scrd[32 * 3];
+    float *recv_of[BCL_MAX];
+    double *recvd_of[BCL_MAX];
+};
+
+// K warp butterflies side by side (level by level, so the shuffles of the
+// K values overlap); every lane ends with lane 0's sums
+template <typename T, int K>
+__device__ __forceinline__ void warp_sums(T (&t)[K]) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = __shfl_sync(0xffffffffu, t[k], 0);
+}
+
+// the K sums of v over the cluster into out (shared, identical in every
+// CTA): warp sums, warp 0 folds the warps' values into this CTA's sums and
+// stores them into every CTA's receive slots (recv[par][rank], remote
+// stores: no round trip), a cluster barrier, then warp 0 folds the
+// received sums in rank order (lane q holds CTA q's).  A parity's slots are
+// rewritten two calls later, after every CTA has passed the barrier that
+// follows its reads.
+template <typename T, int K>
+__device__ __forceinline__ void bcl_sums(cgx::cluster_group &cl, const T (&v)[K], T *scr, T *recv,
+                                         T *const *recv_of, int par, int rank, int ncta, T *out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = v[k];
+    warp_sums<T, K>(t);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) scr[w * K + k] = t[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) t[k] = lane < BCL_THREADS / 32 ? scr[lane * K + k] : (T)0;
+        warp_sums<T, K>(t);
+        if (lane < ncta) {
+            T *dst = recv_of[lane] + (par * BCL_MAX + rank) * K;
+#pragma unroll
+            for (int k = 0; k < K; ++k) dst[k] = t[k];
+        }
+    }
+    cl.sync();  // every CTA's sums received
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) t[k] = lane < ncta ? recv[(par * BCL_MAX + lane) * K + k] : (T)0;
+        warp_sums<T, K>(t);
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) out[k] = t[k];
+        }
+    }
+    __syncthreads();
+}
+
+constexpr int BCL_GATHER = 8;  // neighbour values in flight per vertex
+
+__global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limit, int vcap) {
+    HFCR_PDL_WAIT();
+    cgx::cluster_group cl = cgx::this_cluster();
+    const int n = *a.d_nfree;
+    if (n > limit) return;  // the grid kernel's band (the same n in every CTA)
+    extern __shared__ float4 bsm[];
+    __shared__ BclState st;
+    const int ncta = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int chunk = n > 0 ? (n + ncta - 1) / ncta : 1;
+    const int lo = rank * chunk;
+    const int cnt = n - lo < chunk ? (n - lo > 0 ? n - lo : 0) : chunk;
+    BclRec *rec = (BclRec *)bsm;
+    float4 *gr = (float4 *)a.rec;  // r of every band vertex, for the other CTAs
+    double *gu = a.u64;            // u of every band vertex
+    float4 *pq = (float4 *)(rec + vcap), *sq = pq + vcap, *xq = sq + vcap, *wq = xq + vcap;
+    int2 *ed = (int2 *)(wq + vcap);
+    if ((int)threadIdx.x < ncta) {
+        st.recv_of[threadIdx.x] = cl.map_shared_rank(&st.recv[0][0][0], threadIdx.x);
+        st.recvd_of[threadIdx.x] = cl.map_shared_rank(&st.recvd[0][0][0], threadIdx.x);
+    }
+    // the right-hand side (Dirichlet values of the neighbours outside the
+    // band), the neighbours' record addresses, the first round's state
+    // (r = b, u = 0)
+    double dl[3] = {0.0, 0.0, 0.0};
+    for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
+        const int i = lo + li;
+        const int g = a.fv[i];
+        const bool inB = g >= a.P.m[1].off;
+        const DMesh &M = inB ? a.P.m[1] : a.P.m[0];
+        const int v = g - M.off;
+        const int e0 = M.ptr[v], e1 = M.ptr[v + 1];
+        const int s0 = (inB ? a.eoffB : 0) + e0;
+        double b[3] = {0.0, 0.0, 0.0};
+        for (int e = e0; e < e1; ++e) {
+            const int w = M.off + M.nbr[e];
+            const int j = a.cidx[w];
+            int code = -1;
+            if (j >= 0) {
+                code = j / chunk == rank ? -2 - (j - lo) : j;
+            } else {
+                const double *uw = a.u + 3 * (size_t)w;
+                b[0] += uw[0];
+                b[1] += uw[1];
+                b[2] += uw[2];
+            }
+            a.cnbr[s0 + e - e0] = code;
+        }
+        // a band vertex has a neighbour one ring closer, so e1 > e0
+        ed[li] = make_int2(s0, e1 - e0);
+        BclRec &R = rec[li];
+        R.r = make_float4((float)b[0], (float)b[1], (float)b[2], 1.0f / (float)(e1 - e0));
+        gr[i] = R.r;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        pq[li] = z4;
+        sq[li] = z4;
+        xq[li] = z4;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a.b64[3 * (size_t)i + c] = b[c];
+            R.u[c] = 0.0;
+            gu[3 * (size_t)i + c] = 0.0;
+            dl[c] += b[c] * b[c];
+        }
+    }
+    int pf = 0, pd = 0;  // parities of the float and float64 receive slots
+    bcl_sums<double, 3>(cl, dl, st.scrd, &st.recvd[0][0][0], st.recvd_of, pd, rank, ncta, st.sumsd);
+    pd ^= 1;
+    double target[3];
+    bool act[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        target[c] = a.tol * a.tol * st.sumsd[c];
+        act[c] = st.sumsd[c] > 0.0;
+    }
+    int it = 0, rounds = 0;
+    bool fail = false;
+    while (act[0] || act[1] || act[2]) {
+        if (++rounds > BAND_MAX_ROUNDS) { fail = true; break; }
+        float gam[3], alp[3], bet[3], stop[3];
+        bool in[3];
+        const int it_round = it;
+        bool first = true;
+        while (true) {
+            cl.sync();  // every band vertex's r visible
+            // w = L z (deg_v z_v = r_v), and the sums (r, z), (w, z), |r|^2
+            float fl[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) fl[k] = 0.f;
+            for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
+                const float4 me = rec[li].r;
+                const int2 e = ed[li];
+                float w0 = me.x, w1 = me.y, w2 = me.z;
+                for (int base = 0; base < e.y; base += BCL_GATHER) {
+                    int cd[BCL_GATHER];
+#pragma unroll
+                    for (int k = 0; k < BCL_GATHER; ++k) cd[k] = base + k < e.y ? a.cnbr[e.x + base + k] : -1;
+                    float4 nb[BCL_GATHER];
+#pragma unroll
+                    for (int k = 0; k < BCL_GATHER; ++k)
+                        nb[k] = cd[k] >= 0 ? __ldcg(gr + cd[k])
+                                           : (cd[k] <= -2 ? rec[-2 - cd[k]].r : make_float4(0.f, 0.f, 0.f, 0.f));
+#pragma unroll
+                    for (int k = 0; k < BCL_GATHER; ++k) {
+                        w0 -= nb[k].x * nb[k].w;
+                        w1 -= nb[k].y * nb[k].w;
+                        w2 -= nb[k].z * nb[k].w;
+                    }
+                }
+                wq[li] = make_float4(w0, w1, w2, 0.f);
+                const float z0 = me.x * me.w, z1 = me.y * me.w, z2 = me.z * me.w;
+                fl[0] += me.x * z0; fl[1] += me.y * z1; fl[2] += me.z * z2;
+                fl[3] += w0 * z0;   fl[4] += w1 * z1;   fl[5] += w2 * z2;
+                fl[6] += me.x * me.x; fl[7] += me.y * me.y; fl[8] += me.z * me.z;
+            }
+            bcl_sums<float, 9>(cl, fl, st.scr, &st.recv[0][0][0], st.recv_of, pf, rank, ncta, st.sums);
+            pf ^= 1;
+            float fs[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) fs[k] = st.sums[k];
+            if (first) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    gam[c] = fs[c];
+                    alp[c] = __fdividef(fs[c], fs[3 + c]);
+                    bet[c] = 0.f;
+                    stop[c] = BAND_INNER_TOL * BAND_INNER_TOL * fs[6 + c];
+                    in[c] = act[c] && fs[6 + c] > 0.f && alp[c] > 0.f && isfinite(alp[c]);
+                }
+                first = false;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float b = __fdividef(fs[c], gam[c]);
+                    const float al = __fdividef(fs[c], fs[3 + c] - b * __fdividef(fs[c], alp[c]));
+                    const bool go = in[c] && fs[6 + c] > stop[c] && al > 0.f && isfinite(al);
+                    if (go) {
+                        bet[c] = b;
+                        alp[c] = al;
+                        gam[c] = fs[c];
+                    }
+                    in[c] = go;
+                }
+            }
+            if (!(in[0] || in[1] || in[2]) || it >= a.max_iters) break;
+            // p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s
+            for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
+                float4 r4 = rec[li].r, p4 = pq[li], s4 = sq[li], x4 = xq[li];
+                const float4 w4 = wq[li];
+                float *r = &r4.x, *p = &p4.x, *sv = &s4.x, *x = &x4.x;
+                const float *w = &w4.x;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (!in[c]) continue;
+                    p[c] = r[c] * r4.w + bet[c] * p[c];
+                    sv[c] = w[c] + bet[c] * sv[c];
+                    x[c] += alp[c] * p[c];
+                    r[c] -= alp[c] * sv[c];
+                }
+                rec[li].r = r4;
+                gr[lo + li] = r4;
+                pq[li] = p4;
+                sq[li] = s4;
+                xq[li] = x4;
+            }
+            ++it;
+        }
+        // the round's end: u += x, then the float64 residual b - L u from
+        // the neighbours' u; the next round starts from it (x = p = s = 0)
+        for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
+            const float4 x4 = xq[li];
+            BclRec &R = rec[li];
+            R.u[0] += (double)x4.x;
+            R.u[1] += (double)x4.y;
+            R.u[2] += (double)x4.z;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gu[3 * (size_t)(lo + li) + c] = R.u[c];
+        }
+        cl.sync();  // every band vertex's u visible
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dl[c] = 0.0;
+        for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
+            const int i = lo + li;
+            const int2 e = ed[li];
+            BclRec &R = rec[li];
+            double r64[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r64[c] = a.b64[3 * (size_t)i + c] - (double)e.y * R.u[c];
+            for (int k = 0; k < e.y; ++k) {
+                const int cd = a.cnbr[e.x + k];
+                if (cd == -1) continue;
+                if (cd >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) r64[c] += __ldcg(gu + 3 * (size_t)cd + c);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) r64[c] += rec[-2 - cd].u[c];
+                }
+            }
+            R.r = make_float4(act[0] ? (float)r64[0] : 0.f, act[1] ? (float)r64[1] : 0.f,
+                              act[2] ? (float)r64[2] : 0.f, R.r.w);
+            gr[i] = R.r;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            pq[li] = z4;
+            sq[li] = z4;
+            xq[li] = z4;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dl[c] += r64[c] * r64[c];
+        }
+        bcl_sums<double, 3>(cl, dl, st.scrd, &st.recvd[0][0][0], st.recvd_of, pd, rank, ncta, st.sumsd);
+        pd ^= 1;
+        bool progress = false;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (!act[c]) continue;
+            if (st.sumsd[c] <= target[c]) { act[c] = false; continue; }
+            progress = true;
+        }
+        if (progress && (it >= a.max_iters || it == it_round)) { fail = true; break; }
+    }
+    for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
+        double *ug = a.u + 3 * (size_t)a.fv[lo + li];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ug[c] = rec[li].u[c];
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        a.ctl[0] += it;
+        if (fail) a.ctl[1] = 1;
+    }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 inline int blocks(int n) { return (n + 255) / 256; }
 
 DPair make_pair(const DiffMeshArgs &a, const DiffMeshArgs &b) {
@@ -688,7 +1027,56 @@ static int band_grid_max() {
     return cached[dev];
 }
 
-void diffusion_init() { (void)band_grid_max(); }
+// the cluster of k_band_cl on this device: the most CTAs (16, 8, 4, 2)
+// whose cluster fits, and the band vertices one CTA holds
+struct BclConfig {
+    bool ok = false;
+    int ncta = 0, vcap = 0;
+};
+static BclConfig band_cl_config() {
+    static BclConfig cached[64];
+    static bool done[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BclConfig();
+    if (!done[dev]) {
+        BclConfig c;
+        if (cudaFuncSetAttribute(k_band_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, BCL_SMEM) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_band_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess) {
+            for (int n = BCL_MAX; n >= 2 && !c.ok; n /= 2) {
+                cudaLaunchConfig_t lc = {};
+                lc.gridDim = dim3(n);
+                lc.blockDim = dim3(BCL_THREADS);
+                lc.dynamicSmemBytes = BCL_SMEM;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = n;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                lc.attrs = at;
+                lc.numAttrs = 1;
+                int ncl = 0;
+                if (cudaOccupancyMaxActiveClusters(&ncl, (const void *)k_band_cl, &lc) == cudaSuccess &&
+                    ncl > 0) {
+                    c.ok = true;
+                    c.ncta = n;
+                }
+                cudaGetLastError();
+            }
+        }
+        cudaGetLastError();
+        c.vcap = BCL_SMEM / BCL_VBYTES;
+        cached[dev] = c;
+        done[dev] = true;
+    }
+    return cached[dev];
+}
+
+void diffusion_init() {
+    (void)band_grid_max();
+    (void)band_cl_config();
+}
 
 const double *diffuse_field(const DiffMeshArgs &a, const DiffMeshArgs &b, double *u, double *u_alt,
                             int *ring, int rings, int sweeps, double tol, int max_iters,
@@ -742,8 +1130,34 @@ const double *diffuse_field(const DiffMeshArgs &a, const DiffMeshArgs &b, double
     ba.max_iters = max_iters;
     ba.cap = ds.cap;
     cudaMemsetAsync(ds.bar, 0, sizeof(unsigned), s);
-    void *args[] = {&ba};
+    // bands of up to `limit` vertices on one cluster, larger ones on the
+    // grid (each kernel returns at once when the band is the other's)
+    const BclConfig bc = band_cl_config();
+    int limit = bc.ok ? bc.ncta * bc.vcap : -1;
     mark(1, s);
+    if (bc.ok) {
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(bc.ncta);
+        lc.blockDim = dim3(BCL_THREADS);
+        lc.dynamicSmemBytes = BCL_SMEM;
+        lc.stream = s;
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = bc.ncta;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = 1;
+        lc.attrs = at;
+        lc.numAttrs = 2;
+        if (cudaLaunchKernelEx(&lc, k_band_cl, ba, limit, bc.vcap) == cudaSuccess) {
+            note_launch();
+        } else {
+            cudaGetLastError();
+            limit = -1;
+        }
+    }
+    void *args[] = {&ba, &limit};
     const cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_band_cg, grid, BAND_TPB, args, 0, s);
     mark(0, s);
     if (e != cudaSuccess) {

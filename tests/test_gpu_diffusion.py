@@ -96,6 +96,25 @@ def test_diffuse_harmonic_full_size_cloth_field(api):
         assert err <= FIELD_TOL, err
 
 
+def test_diffuse_harmonic_band_beyond_one_cluster(api):
+    # 600 scattered moved vertices of a 400 x 400 cloth over R = 8 rings: a
+    # band of tens of thousands of vertices, more than one thread-block
+    # cluster holds, so the grid-wide kernel solves it
+    rng = np.random.default_rng(12)
+    V, T = meshgen.cloth(400, 2.0)
+    n = len(V)
+    ctx = api.Context()
+    ctx.hfcr_reserve(n, len(T), 16)
+    M, _ = dev_mesh(api, V, T, False, np.float32)
+    dx = _field(n, rng.choice(n, 600, replace=False), rng)
+    got = _gpu_diffuse(api, ctx, M, dx, 8)
+    ref = oracle.diffuse(dx, oracle.edges(T), 8)
+    band = int(np.count_nonzero(np.any(ref != 0, axis=1) & ~np.any(dx != 0, axis=1)))
+    assert band > 40000, band
+    err = np.abs(got - ref).max() / np.abs(dx).max()
+    assert err <= FIELD_TOL, err
+
+
 @pytest.mark.parametrize("kind", ["cloth", "sphere", "torus"])
 def test_diffuse_jacobi_sweeps_bit_exact(api, kind):
     # the fixed-sweep approximation
