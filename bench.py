@@ -134,6 +134,7 @@ KERNELS = {
     "k_band_cl": (("diffuse.cu",), "k_band_cl_frame_sequence.md"),
     "k_cg_zone_pair": (("solve.cu",), "k_cg_zone_pair_cloth_torus.md"),
     "k_refit": (("bvh.cu",), "k_refit_frame_sequence.md"),
+    "k_cg_zone_big": (("solve.cu",), "k_cg_zone_1024_frame_sequence.md"),
 }
 
 
@@ -978,6 +979,15 @@ def main():
     alg_band = int(nb_mean * (60 + 4 * deg))
     band_iters = statistics.mean(int(i.diffuse_cg_iters) for i in infos)
     ach_band = alg_band / (band_ms * 1e-3) / 1e9
+    # the solver launches of the large impact zones (1,024 rows or more; the
+    # frame's one big contact zone): per row 116 B (ids, float32 and float64
+    # normals, block-Jacobi row, b, lambda written, four CSR entries, group
+    # start), per touched vertex 8 B
+    zb_ms = prof["zone_big"][0] / max(1, prof["zone_big"][1])
+    zb_rows = statistics.mean(int(i.big_zone_rows) for i in infos)
+    zb_verts = statistics.mean(int(i.big_zone_vertices) for i in infos)
+    alg_zb = int(116 * zb_rows + 8 * zb_verts)
+    ach_zb = alg_zb / (zb_ms * 1e-3) / 1e9
     roof = {
         "k_traverse": {"kernel": "k_traverse (BVH traversal + exact narrow phase)", "bound": "hbm",
                        "achieved": round(ach_trav, 2), "peak": peak, "peak_kind": peak_kind,
@@ -993,15 +1003,28 @@ def main():
                       "avg_launch_ms": round(band_ms, 5), "launches_timed": prof["band_cg"][1],
                       "band_vertices_mean": round(nb_mean, 1), "cg_iters_mean": round(band_iters, 2),
                       "us_per_cg_iter": round(1e3 * band_ms / band_iters, 3) if band_iters else None},
+        "k_cg_zone_big": {"kernel": "k_cg_zone<1024> (+ k_cg_zone_cl): float32 PCG with float64 "
+                                    "refinement of the impact zones of 1,024 rows or more, one CTA "
+                                    "(or cluster) per zone", "bound": "hbm",
+                          "achieved": round(ach_zb, 3), "peak": peak, "peak_kind": peak_kind,
+                          "unit": "GB/s", "frac": round(ach_zb / peak, 7),
+                          "traffic": profiled_traffic("k_cg_zone_big"), "alg_bytes_per_launch": alg_zb,
+                          "avg_launch_ms": round(zb_ms, 5), "launches_timed": prof["zone_big"][1],
+                          "rows_mean": round(zb_rows, 1), "vertices_mean": round(zb_verts, 1)},
         "whole_frame": {"bound": "hbm", "alg_bytes_per_frame": frame_bytes,
                         "achieved": round(frame_bytes / (per_frame * 1e-3) / 1e9, 2), "peak": peak,
                         "unit": "GB/s", "frac": round(frame_bytes / (per_frame * 1e-3) / 1e9 / peak, 5),
                         "note": "positions of both meshes read and written, cloth edges, body faces"},
     }
-    dominant = max(("traverse", "bvh", "solve", "diffuse"), key=lambda k: stage_ms[k])
-    roofline = dict(roof["k_traverse"], dominant_stage=dominant,
-                    chosen_by="the traversal kernel; the stage times of the profiled pass are in "
-                              "stage_ms_per_frame")
+    # the headline roofline: the single kernel with the most time per frame
+    # in the profiled pass (the traversal, the band CG, the large-zone solver)
+    kernel_ms = {"k_traverse": prof["traverse"][0] / F, "k_band_cl": prof["band_cg"][0] / F,
+                 "k_cg_zone_big": prof["zone_big"][0] / F}
+    top = max(kernel_ms, key=kernel_ms.get)
+    roofline = dict(roof[top], ms_per_frame=round(kernel_ms[top], 4),
+                    chosen_by="the kernel with the most time per frame of %s (profiled pass, "
+                              "ms/frame %s)" % (sorted(kernel_ms),
+                                                {k: round(v, 4) for k, v in kernel_ms.items()}))
 
     # ---- the same frames through the other forms ----
     forms = None if args.no_forms else lockstep_forms(api, torch, dev, sc, stream, flush, F, seq)

@@ -189,6 +189,10 @@ typedef struct {
                                       vertices far more than the penetration depths */
     int64_t band_vertices;         /* harmonic diffusion: free band vertices (the unknowns of
                                       the band's Dirichlet problem), summed over the iterations */
+    int64_t big_zone_rows;         /* MIXED: rows of the impact zones of 1,024 rows or more
+                                      (one CTA or one cluster per zone), summed over the
+                                      iterations */
+    int64_t big_zone_vertices;     /* and the vertices those zones touch */
 } hfcr_resolve_info;
 
 /* Stages timed by the optional profiler (instrumentation; the paper has no
@@ -202,9 +206,11 @@ typedef enum {
     HFCR_STAGE_SOLVE = 5,     /* Eq. 7 / Eq. 8 solve */
     HFCR_STAGE_DISPLACE = 6,  /* x' - x and its application */
     HFCR_STAGE_DIFFUSE = 7,   /* diffusion of the displacement (Sec. 5) and its application */
-    HFCR_STAGE_BAND_CG = 8,   /* the band CG kernel alone: its intervals lie inside DIFFUSE's,
-                                 so it is not added to the other stages */
-    HFCR_N_STAGES = 9
+    HFCR_STAGE_BAND_CG = 8,   /* the band CG kernels alone: their intervals lie inside DIFFUSE's,
+                                 so they are not added to the other stages */
+    HFCR_STAGE_ZONE_BIG = 9,  /* the solver launches of the impact zones of 1,024 rows or more
+                                 (MIXED), inside SOLVE's intervals */
+    HFCR_N_STAGES = 10
 } hfcr_stage;
 
 typedef struct {

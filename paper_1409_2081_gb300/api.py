@@ -83,12 +83,13 @@ class hfcr_resolve_info(ctypes.Structure):
                 ("stats", hfcr_detect_stats), ("solver_path", ctypes.c_int32),
                 ("diffuse_cg_iters", ctypes.c_int32), ("diffuse_unconverged", ctypes.c_int32),
                 ("worst_amplification", ctypes.c_double), ("amplified_iters", ctypes.c_int32),
-                ("band_vertices", ctypes.c_int64)]
+                ("band_vertices", ctypes.c_int64), ("big_zone_rows", ctypes.c_int64),
+                ("big_zone_vertices", ctypes.c_int64)]
 
 
-HFCR_N_STAGES = 9
+HFCR_N_STAGES = 10
 STAGES = ("validate", "bvh", "traverse", "stencils", "assemble", "solve", "displace", "diffuse",
-          "band_cg")
+          "band_cg", "zone_big")
 
 
 class hfcr_profile(ctypes.Structure):

@@ -238,6 +238,14 @@ void band_mark(void *c, int begin, cudaStream_t s) {
         prof_end((hfcr_ctx *)c, HFCR_STAGE_BAND_CG, s);
 }
 
+// the large zones' solver launches, nested inside the solve stage
+void zone_big_mark(void *c, int begin, cudaStream_t s) {
+    if (begin)
+        prof_begin((hfcr_ctx *)c, HFCR_STAGE_ZONE_BIG, s);
+    else
+        prof_end((hfcr_ctx *)c, HFCR_STAGE_ZONE_BIG, s);
+}
+
 // accumulates every closed interval (waits for its end event)
 void prof_collect(hfcr_ctx *c) {
     std::vector<ProfInterval> keep;
@@ -580,7 +588,12 @@ hfcr_status run_response(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B,
                      ctx->d_status, ctx->opt.setup_path, s);
     prof_end(ctx, HFCR_STAGE_ASSEMBLE, s);
     prof_begin(ctx, HFCR_STAGE_SOLVE, s);
-    solve(params_of(ctx->opt), mp, ctx->d_cnt + C_STENCILS, k, ctx->sb, ctx->d_status, s);
+    SolveParams sp = params_of(ctx->opt);
+    if (ctx->prof_on) {
+        sp.big_mark.fn = zone_big_mark;
+        sp.big_mark.arg = ctx;
+    }
+    solve(sp, mp, ctx->d_cnt + C_STENCILS, k, ctx->sb, ctx->d_status, s);
     prof_end(ctx, HFCR_STAGE_SOLVE, s);
     prof_begin(ctx, HFCR_STAGE_DISPLACE, s);
     displacement(mp, k, ctx->sb, apply, dxA, dxB, s);
@@ -1235,6 +1248,10 @@ static hfcr_status resolve_impl(hfcr_ctx *ctx, hfcr_mesh *A, hfcr_mesh *B, const
         loc.stats.brute_force_equiv += single_pair_bf(pl, d0, d1, A, B);
         loc.diffuse_cg_iters += ctx->h_cnt[C_DIFF_ITERS];
         if (diffusing(ctx) && ctx->opt.diffuse_sweeps <= 0) loc.band_vertices += ctx->h_cnt[C_NFREE];
+        if (P > 0) {
+            loc.big_zone_rows += ctx->h_iw[5];
+            loc.big_zone_vertices += ctx->h_iw[6];
+        }
         if (ctx->h_cnt[C_DIFF_FAIL]) loc.diffuse_unconverged += 1;
         if (it == 0) loc.pairs_first = P;
         loc.pairs_last = P;

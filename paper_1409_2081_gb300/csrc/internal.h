@@ -276,12 +276,22 @@ struct SolveBuffers {
     double *dwork = nullptr;     // [16]
 };
 
+// StageMark brackets a launch for the caller's stage profiler (fn(arg, 1, s)
+// before it, fn(arg, 0, s) after; no-op when fn is null).
+struct StageMark {
+    void (*fn)(void *arg, int begin, cudaStream_t s) = nullptr;
+    void *arg = nullptr;
+    void operator()(int begin, cudaStream_t s) const {
+        if (fn) fn(arg, begin, s);
+    }
+};
 struct SolveParams {
     int solver;
     int max_cg_iters;
     int max_refine;
     double rel_tol;
     double inner_tol;
+    StageMark big_mark;  // brackets the launches of the zones of ZONE_BIG rows or more
 };
 
 void assemble(const MeshPair &mp, const hfcr_stencil *st, const int *d_k, int cap, double d,
@@ -337,15 +347,7 @@ struct DiffScratch {
 // sweeps.  Returns the buffer holding the result (u, or u_alt after an odd
 // number of sweeps); ring [a.n + b.n] gets the ring distances (0: moved,
 // rings + 1: beyond).
-// StageMark brackets the band CG launch for the caller's stage profiler
-// (fn(arg, 1, s) before it, fn(arg, 0, s) after; no-op when fn is null).
-struct StageMark {
-    void (*fn)(void *arg, int begin, cudaStream_t s) = nullptr;
-    void *arg = nullptr;
-    void operator()(int begin, cudaStream_t s) const {
-        if (fn) fn(arg, begin, s);
-    }
-};
+
 const double *diffuse_field(const DiffMeshArgs &a, const DiffMeshArgs &b, double *u, double *u_alt,
                             int *ring, int rings, int sweeps, double tol, int max_iters,
                             const DiffScratch &ds, SortTemp &t, uint32_t *d_status, cudaStream_t s,

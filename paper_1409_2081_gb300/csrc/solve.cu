@@ -1243,6 +1243,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_cg_zone(const int *d_nz, ZoneArg
         if (leave_big && zone_smem_need(k, a.zv[z + 1] - a.zv[z], a.zg[z + 1] - a.zg[z]) > smem_bytes)
             continue;
         solve_zone<CtaGroup>(a, z, (char *)smem4, smem_bytes, red, redd, g);
+        if (threadIdx.x == 0) {  // rows and touched vertices of the large zones
+            atomicAdd(&a.ctl[5], k);
+            atomicAdd(&a.ctl[6], a.zv[z + 1] - a.zv[z]);
+        }
     }
 }
 
@@ -1747,7 +1751,11 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_cg_zone_cl(const int *d_nz, Z
             rr = sd[0];
             ++rounds;
         }
-        if (rank == 0 && tid == 0) zone_finish(a, z, rr, bb, its, rounds, true);
+        if (rank == 0 && tid == 0) {
+            zone_finish(a, z, rr, bb, its, rounds, true);
+            atomicAdd(&a.ctl[5], k);
+            atomicAdd(&a.ctl[6], U);
+        }
         // the shares (shared memory) of this zone are read by other CTAs until
         // every CTA has passed this barrier
         cl.sync();
@@ -2692,6 +2700,7 @@ void solve(const SolveParams &p, const MeshPair &mp, const int *d_k, int cap, So
     // zones of ZONE_BIG rows or more: one 1,024-thread CTA each when they fit
     // its shared memory; larger ones on a cluster of CL CTAs (or, without
     // clusters, on global memory)
+    p.big_mark(1, s);
     { launch_pdl(k_cg_zone<CG_THREADS>, zbig, CG_THREADS, fast_smem, s, sb.d_nz, za, ZONE_BIG - 1,
                  gs, fast_smem, g_cluster_ok ? 1 : 0); note_launch(); }
     if (g_cluster_ok) {
@@ -2714,6 +2723,7 @@ void solve(const SolveParams &p, const MeshPair &mp, const int *d_k, int cap, So
         cudaLaunchKernelEx(&cfg, k_cg_zone_cl, (const int *)sb.d_nz, za, gs, fast_smem);
         note_launch();
     }
+    p.big_mark(0, s);
     { launch_pdl(k_zone_final, 1, 256, 0, s, sb.d_nz, sb.r64, sb.q64, p.rel_tol, sb.dwork,
                  sb.iwork); note_launch(); }
 }
