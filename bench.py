@@ -1003,7 +1003,7 @@ def main():
                       "avg_launch_ms": round(band_ms, 5), "launches_timed": prof["band_cg"][1],
                       "band_vertices_mean": round(nb_mean, 1), "cg_iters_mean": round(band_iters, 2),
                       "us_per_cg_iter": round(1e3 * band_ms / band_iters, 3) if band_iters else None},
-        "k_cg_zone_big": {"kernel": "k_cg_zone<1024> (+ k_cg_zone_cl): float32 PCG with float64 "
+        "k_cg_zone_big": {"kernel": "k_cg_zone<512> (+ k_cg_zone_cl): float32 PCG with float64 "
                                     "refinement of the impact zones of 1,024 rows or more, one CTA "
                                     "(or cluster) per zone", "bound": "hbm",
                           "achieved": round(ach_zb, 3), "peak": peak, "peak_kind": peak_kind,

@@ -97,6 +97,8 @@ struct hfcr_ctx {
     // diffusion (Sec. 5): vertex adjacency per mesh, float64 field ping-pong
     // over both meshes' vertices (AoS), ring distances
     int *adj_ptr[2] = {nullptr, nullptr}, *adj_nbr[2] = {nullptr, nullptr}, *adj_cur = nullptr;
+    int *adj_rank[2] = {nullptr, nullptr};  // Morton rank of each vertex (cached adjacencies)
+    bool adj_ranked[2] = {false, false};
     const int *adj_src[2] = {nullptr, nullptr};  // caller edge list behind adj_ptr / adj_nbr
     int adj_ne[2] = {0, 0}, adj_nv[2] = {0, 0};
     double *field = nullptr, *field_alt = nullptr;
@@ -161,13 +163,16 @@ void free_all(hfcr_ctx *c) {
                     c->sb.winv, c->sb.u64, c->sb.u32, c->sb.red};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    void *dp[] = {c->adj_ptr[0], c->adj_ptr[1], c->adj_nbr[0], c->adj_nbr[1], c->adj_cur, c->field,
+    void *dp[] = {c->adj_ptr[0], c->adj_ptr[1], c->adj_nbr[0], c->adj_nbr[1], c->adj_cur,
+                  c->adj_rank[0], c->adj_rank[1], c->field,
                   c->field_alt, c->ring, c->eorder[0], c->eorder[1], c->dscr.flags, c->dscr.cidx,
                   c->dscr.fv, c->dscr.b64, c->dscr.u64, c->dscr.x32, c->dscr.p32, c->dscr.rec,
                   c->dscr.cnbr, c->dscr.part, c->dscr.bar};
     for (void *p : dp)
         if (p) cudaFree(p);
     c->adj_ptr[0] = c->adj_ptr[1] = c->adj_nbr[0] = c->adj_nbr[1] = c->adj_cur = nullptr;
+    c->adj_rank[0] = c->adj_rank[1] = nullptr;
+    c->adj_ranked[0] = c->adj_ranked[1] = false;
     c->field = c->field_alt = nullptr;
     c->ring = nullptr;
     c->dscr = DiffScratch();
@@ -624,6 +629,9 @@ hfcr_status prepare_diffusion(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh
         }
         build_adjacency(e, e ? ne : 0, M[i]->n_verts, ctx->adj_ptr[i], ctx->adj_nbr[i], ctx->adj_cur,
                         ctx->sort, ctx->d_status, s);
+        // a kept adjacency also gets the Morton order of the band list (once)
+        ctx->adj_ranked[i] = M[i]->edges != nullptr;
+        if (ctx->adj_ranked[i]) vertex_rank(*M[i], ctx->adj_rank[i], ctx->dscr, ctx->sort, s);
         ctx->adj_src[i] = M[i]->edges;
         ctx->adj_ne[i] = M[i]->n_edges;
         ctx->adj_nv[i] = M[i]->n_verts;
@@ -678,6 +686,8 @@ void enqueue_iteration(hfcr_ctx *ctx, const hfcr_mesh *A, const hfcr_mesh *B, bo
     DiffMeshArgs da, db;
     da.ptr = ctx->adj_ptr[0]; da.nbr = ctx->adj_nbr[0]; da.inv_mass = A->inv_mass; da.n = A->n_verts;
     db.ptr = ctx->adj_ptr[1]; db.nbr = ctx->adj_nbr[1]; db.inv_mass = B->inv_mass; db.n = B->n_verts;
+    da.rank = ctx->adj_ranked[0] ? ctx->adj_rank[0] : nullptr;
+    db.rank = ctx->adj_ranked[1] ? ctx->adj_rank[1] : nullptr;
     StageMark mark;
     if (ctx->prof_on) {
         mark.fn = band_mark;
@@ -952,6 +962,7 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
         for (int i = 0; i < 2; ++i) {
             CK(dalloc(&ctx->adj_ptr[i], V + 1));
             CK(dalloc(&ctx->adj_nbr[i], 2 * E3));
+            CK(dalloc(&ctx->adj_rank[i], V));
         }
         CK(dalloc(&ctx->adj_cur, V));
         CK(dalloc(&ctx->field, 6 * V));
@@ -1182,6 +1193,7 @@ hfcr_status hfcr_diffuse(hfcr_ctx *ctx, const hfcr_mesh *M, double *dx, double *
     build_adjacency(e, e ? ne : 0, M->n_verts, ctx->adj_ptr[0], ctx->adj_nbr[0], ctx->adj_cur,
                     ctx->sort, ctx->d_status, s);
     ctx->adj_src[0] = nullptr;  // slot 0 no longer holds a resolve call's adjacency
+    ctx->adj_ranked[0] = false;
     field_from_soa(dx, dy, dz, M->n_verts, ctx->field, s);
     DiffMeshArgs a, none;
     a.ptr = ctx->adj_ptr[0]; a.nbr = ctx->adj_nbr[0]; a.inv_mass = M->inv_mass; a.n = M->n_verts;

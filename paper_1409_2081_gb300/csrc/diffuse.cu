@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cfloat>
+
 #include <cooperative_groups.h>
 
 #include "internal.h"
@@ -79,6 +81,7 @@ __global__ void k_adj_sort(const int *ptr, int nv, int *nbr) {
 struct DMesh {
     const int *ptr = nullptr, *nbr = nullptr;
     const float *inv_mass = nullptr;
+    const int *rank = nullptr;  // place of each vertex in the band list's order (null: identity)
     int n = 0, off = 0;
 };
 struct DPair {
@@ -209,12 +212,19 @@ __device__ __forceinline__ bool band_vertex(const DPair &P, const int *ring, int
     return !(M.inv_mass && M.inv_mass[g - M.off] == 0.f);
 }
 
-// flag of every vertex: 1 in the band (scanned in place into the compact
-// index), then the list of band vertices and the vertex -> index map
+// place of global vertex g in the band list's order: its mesh's offset
+// plus its rank there (the Morton order of the positions, where given)
+__device__ __forceinline__ int band_slot(const DPair &P, int g) {
+    const DMesh &M = P.of(g);
+    return M.rank ? M.off + M.rank[g - M.off] : g;
+}
+
+// flag of every vertex at its slot: 1 in the band (scanned in place into the
+// compact index), then the list of band vertices and the vertex -> index map
 __global__ void k_band_flags(DPair P, const int *ring, int R, unsigned *flags) {
     HFCR_PDL_WAIT();
     int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < P.ntot) flags[g] = band_vertex(P, ring, R, g) ? 1u : 0u;
+    if (g < P.ntot) flags[band_slot(P, g)] = band_vertex(P, ring, R, g) ? 1u : 0u;
 }
 
 __global__ void k_band_list(DPair P, const int *ring, int R, const unsigned *pos, int *cidx,
@@ -223,11 +233,90 @@ __global__ void k_band_list(DPair P, const int *ring, int R, const unsigned *pos
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= P.ntot) return;
     if (band_vertex(P, ring, R, g)) {
-        cidx[g] = (int)pos[g];
-        fv[pos[g]] = g;
+        const unsigned i = pos[band_slot(P, g)];
+        cidx[g] = (int)i;
+        fv[i] = g;
     } else {
         cidx[g] = -1;
     }
+}
+
+// ---- the Morton rank of a mesh's vertices (once per kept adjacency) ----
+
+// float -> int with the same order (for atomicMin / atomicMax)
+__device__ __forceinline__ int ordered_int(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ordered_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+template <typename T>
+__global__ void k_rank_bounds(const T *x, const T *y, const T *z, int n, int *box) {
+    HFCR_PDL_WAIT();
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const float c[3] = {(float)x[v], (float)y[v], (float)z[v]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(lo[k], c[k]);
+            hi[k] = fmaxf(hi[k], c[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(box + k, ordered_int(lo[k]));
+            atomicMax(box + 3 + k, ordered_int(hi[k]));
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned spread3(unsigned v) {  // 10 bits -> every third of 30
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+template <typename T>
+__global__ void k_rank_keys(const T *x, const T *y, const T *z, int n, const int *box,
+                            unsigned long long *keys, int *vals) {
+    HFCR_PDL_WAIT();
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const float c[3] = {(float)x[v], (float)y[v], (float)z[v]};
+    unsigned q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = ordered_float(box[k]), hi = ordered_float(box[3 + k]);
+        const float ext = hi - lo;
+        float t = ext > 0.f ? (c[k] - lo) / ext : 0.f;  // NaN coordinates fall to cell 0
+        t = t > 0.f ? (t < 1.f ? t : 1.f) : 0.f;
+        const unsigned cell = (unsigned)(t * 1023.f);
+        q[k] = cell > 1023u ? 1023u : cell;
+    }
+    keys[v] = (unsigned long long)(spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2));
+    vals[v] = v;
+}
+
+__global__ void k_rank_box_init(int *box) {
+    HFCR_PDL_WAIT();
+    if (threadIdx.x < 6) box[threadIdx.x] = threadIdx.x < 3 ? 0x7fffffff : (int)0x80000000;
+}
+
+__global__ void k_rank_scatter(const int *vals, int n, int *rank) {
+    HFCR_PDL_WAIT();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rank[vals[i]] = i;
 }
 
 struct BandArgs {
@@ -989,6 +1078,8 @@ DPair make_pair(const DiffMeshArgs &a, const DiffMeshArgs &b) {
     DPair P;
     P.m[0].ptr = a.ptr; P.m[0].nbr = a.nbr; P.m[0].inv_mass = a.inv_mass; P.m[0].n = a.n; P.m[0].off = 0;
     P.m[1].ptr = b.ptr; P.m[1].nbr = b.nbr; P.m[1].inv_mass = b.inv_mass; P.m[1].n = b.n; P.m[1].off = a.n;
+    P.m[0].rank = a.rank;
+    P.m[1].rank = b.rank;
     P.ntot = a.n + b.n;
     return P;
 }
@@ -1071,6 +1162,30 @@ static BclConfig band_cl_config() {
         done[dev] = true;
     }
     return cached[dev];
+}
+
+void vertex_rank(const hfcr_mesh &m, int *rank, const DiffScratch &ds, SortTemp &t, cudaStream_t s) {
+    const int n = m.n_verts;
+    if (n <= 0) return;
+    // scratch: keys and values in the grid kernel's record buffer (48 floats
+    // per vertex of capacity; the sort needs 24 bytes), the box in `part`
+    unsigned long long *k0 = (unsigned long long *)ds.rec, *k1 = k0 + n;
+    int *v0 = (int *)(k1 + n), *v1 = v0 + n;
+    int *box = (int *)ds.part;
+    { launch_pdl(k_rank_box_init, 1, 32, 0, s, box); note_launch(); }
+    int nb = blocks(n);
+    const int nbb = nb > 1024 ? 1024 : nb;
+    if (m.dtype == HFCR_F32) {
+        const float *x = (const float *)m.x, *y = (const float *)m.y, *z = (const float *)m.z;
+        { launch_pdl(k_rank_bounds<float>, nbb, 256, 0, s, x, y, z, n, box); note_launch(); }
+        { launch_pdl(k_rank_keys<float>, nb, 256, 0, s, x, y, z, n, (const int *)box, k0, v0); note_launch(); }
+    } else {
+        const double *x = (const double *)m.x, *y = (const double *)m.y, *z = (const double *)m.z;
+        { launch_pdl(k_rank_bounds<double>, nbb, 256, 0, s, x, y, z, n, box); note_launch(); }
+        { launch_pdl(k_rank_keys<double>, nb, 256, 0, s, x, y, z, n, (const int *)box, k0, v0); note_launch(); }
+    }
+    const bool flip = radix_sort_u64(k0, v0, k1, v1, n, 30, t, s);
+    { launch_pdl(k_rank_scatter, nb, 256, 0, s, (const int *)(flip ? v1 : v0), n, rank); note_launch(); }
 }
 
 void diffusion_init() {

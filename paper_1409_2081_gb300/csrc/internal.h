@@ -319,8 +319,16 @@ int bits_for(long long n);  // smallest b with n <= 2^b (at least 1)
 struct DiffMeshArgs {
     const int *ptr = nullptr, *nbr = nullptr;  // vertex adjacency CSR, ascending neighbours
     const float *inv_mass = nullptr;           // null: no kinematic vertices
+    const int *rank = nullptr;                 // order of the band list (null: vertex order)
     int n = 0;                                 // vertices
 };
+// rank[v] = place of vertex v in the Morton order of the mesh's positions
+// (30-bit codes in its bounding box, ties by index): the band list follows it,
+// so that neighbouring band vertices sit close in the list.  Scratch: the
+// diffusion's record buffer and partial-sum buffer (nothing kept there
+// between calls).
+void vertex_rank(const hfcr_mesh &m, int *rank, const struct DiffScratch &ds, SortTemp &t,
+                 cudaStream_t s);
 // CSR of an edge list: ptr [nv + 1], nbr [2 ne], cur [nv] scratch
 void build_adjacency(const int *edges, int ne, int nv, int *ptr, int *nbr, int *cur, SortTemp &t,
                      uint32_t *d_status, cudaStream_t s);

@@ -19,7 +19,8 @@
 // as a sequence of kernels.
 // MIXED: per zone (a thread group sized to the zone: one warp up to 32
 // stencils, a 256-thread half CTA up to 255, a 512-thread CTA up to 1,023,
-// a 1,024-thread CTA above; staged in shared memory), conjugate gradients in float32 on
+// a 512-thread CTA with all of an SM's shared memory above, an 8-CTA
+// cluster beyond that; staged in shared memory), conjugate gradients in float32 on
 // float32 normals, preconditioned by the inverses of the blocks of rows that
 // share x0, solve for a correction of lambda; the zone's residual
 // b - A lambda is recomputed in float64 with the float64 normals after every
@@ -38,6 +39,7 @@ namespace hfcr {
 namespace {
 
 constexpr int CG_THREADS = 1024;
+constexpr int BIG_ZONE_THREADS = 512;  // threads of the solver of the zones of ZONE_BIG rows or more
 
 // Loads of data written earlier in the same launch: plain where only the
 // loading CTA wrote it (PlainLd), through L2 where another CTA may have
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg(
 constexpr int FAST_SMEM = 231424;  // 226 KB dynamic (+256 B static) under the 227 KB per-CTA limit
 constexpr int ZONE_MID = 256;   // zones with at least this many stencils get all 512 threads
 constexpr int ZONE_PAIR_SMEM = 112 * 1024;  // k_cg_zone_pair: 2 CTAs per SM, 56 KB per half
-constexpr int ZONE_BIG = 1024;  // zones with at least this many stencils get a 1024-thread CTA
+constexpr int ZONE_BIG = 1024;  // zones with at least this many stencils get a CTA of their own
 
 // Index types of a view: the global-memory path reads the int arrays as
 // they are; the zone staged in shared memory holds zone-local indices in
@@ -1166,8 +1168,10 @@ __device__ __forceinline__ void solve_zone(const ZoneArgs &a, int z, char *base,
 // ZONE_BIG - 1 stencils one at a time on all 512 threads, then the smaller
 // ones two at a time, one per 256-thread half (its own named barrier, half
 // the shared memory), so that a zone gets about one to four rows per
-// thread.  k_cg_zone<1024>: the
-// rest, one 1,024-thread CTA with all of shared memory each.  (solve_zone
+// thread.  k_cg_zone<BIG_ZONE_THREADS>: the rest, one CTA with all of
+// shared memory each (512 threads: measured a little faster than 1,024 on
+// the frame sequence's large zones, 0.546 against 0.566 ms per frame, and
+// cheaper barriers and reductions).  (solve_zone
 // ends with its group's barrier, so the halves may reuse the shared memory
 // of the CTA's last whole-CTA zone.)
 // Zone assignment of the pair launch: a solver's first zone is fixed (so
@@ -2422,7 +2426,7 @@ static bool g_cluster_ok = false;  // k_cg_zone_cl can be launched on this devic
 
 void solver_init() {
     if (g_fast_smem >= 0) return;
-    g_fast_smem = cudaFuncSetAttribute(k_cg_zone<CG_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    g_fast_smem = cudaFuncSetAttribute(k_cg_zone<BIG_ZONE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        FAST_SMEM) == cudaSuccess ? FAST_SMEM : 0;
     if (!g_fast_smem) cudaGetLastError();
     g_zone_pair_smem = cudaFuncSetAttribute(k_cg_zone_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2689,7 +2693,7 @@ void solve(const SolveParams &p, const MeshPair &mp, const int *d_k, int cap, So
     gs.x = sb.x32; gs.r = sb.r32; gs.p = sb.p32; gs.s = sb.q32; gs.w = sb.w32; gs.z = sb.z32;
     gs.u = sb.u32;
     // CTAs of the pair launch: two zones of more than warp_max stencils at
-    // a time (at most 2 CTAs per SM); of the 1024-thread launch: one zone
+    // a time (at most 2 CTAs per SM); of the large-zone launch: one zone
     // of ZONE_BIG or more stencils each
     int zpair = (cap / (WARP_ZONE + 1) + 1) / 2 + 1;
     if (zpair > 2 * 152) zpair = 2 * 152;
@@ -2697,11 +2701,11 @@ void solve(const SolveParams &p, const MeshPair &mp, const int *d_k, int cap, So
     if (zbig > 152) zbig = 152;
     { launch_pdl(k_cg_zone_pair, zpair, 512, g_zone_pair_smem, s, sb.d_nz, za, warp_max, gs,
                  g_zone_pair_smem); note_launch(); }
-    // zones of ZONE_BIG rows or more: one 1,024-thread CTA each when they fit
-    // its shared memory; larger ones on a cluster of CL CTAs (or, without
+    // zones of ZONE_BIG rows or more: one CTA each when they fit its shared
+    // memory; larger ones on a cluster of CL CTAs (or, without
     // clusters, on global memory)
     p.big_mark(1, s);
-    { launch_pdl(k_cg_zone<CG_THREADS>, zbig, CG_THREADS, fast_smem, s, sb.d_nz, za, ZONE_BIG - 1,
+    { launch_pdl(k_cg_zone<BIG_ZONE_THREADS>, zbig, BIG_ZONE_THREADS, fast_smem, s, sb.d_nz, za, ZONE_BIG - 1,
                  gs, fast_smem, g_cluster_ok ? 1 : 0); note_launch(); }
     if (g_cluster_ok) {
         int ncl = (cap + ZONE_CL_MIN - 1) / ZONE_CL_MIN;
