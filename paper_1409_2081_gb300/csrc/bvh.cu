@@ -305,7 +305,10 @@ __global__ void k_karras(const unsigned long long *keys, int n_total, const int 
     int gamma = i + s * d + min(d, 0);
     int left = (min(i, j) == gamma) ? ~(t0 + gamma) : t0 + gamma;
     int right = (max(i, j) == gamma + 1) ? ~(t0 + gamma + 1) : t0 + gamma + 1;
-    nodes[4 * gi + 3] = make_float4(__int_as_float(left), __int_as_float(right), 0.f, 0.f);
+    // child ids, then the node's leaf range (first, last; one end is gi), which
+    // the refit uses to keep a warp's own subtrees in shared memory
+    nodes[4 * gi + 3] = make_float4(__int_as_float(left), __int_as_float(right),
+                                    __int_as_float(t0 + min(i, j)), __int_as_float(t0 + max(i, j)));
     // parent links carry the child's slot: (parent << 1) | (1 for the right child)
     if (left < 0) lparent[~left] = gi << 1; else iparent[left] = gi << 1;
     if (right < 0) lparent[~right] = (gi << 1) | 1; else iparent[right] = (gi << 1) | 1;
@@ -334,12 +337,29 @@ __device__ __forceinline__ void pack_leaf<double>(void *leaf_tri, int j, const d
     L[4] = make_double2(c[2], __longlong_as_double((long long)f));
 }
 
+// Bottom-up refit, one thread per leaf, warp by warp: warp w owns leaves
+// [32 w, 32 w + 32).  A node whose leaf range lies in its warp's block (its
+// whole subtree does) is met by two lanes of that warp: they hand over
+// through shared memory (box slots and an arrival counter, block-scope
+// fences), and the second writes both child boxes of the node.  Above the
+// block, the second child to arrive at a node (an acquire-release atomic
+// counter in global memory) merges the two boxes.  Min and max are exact,
+// so the boxes do not depend on the arrival order.
+constexpr int REFIT_WARPS = 8;
+
 template <typename T>
-__global__ void k_refit(const T *x, const T *y, const T *z, int nv, const int *tris,
-                        const int *leaf_face, int n, float4 *nodes, const int *iparent,
-                        const int *lparent, unsigned *flags, void *leaf_tri, uint32_t *st) {
+__global__ void __launch_bounds__(32 * REFIT_WARPS) k_refit(
+    const T *x, const T *y, const T *z, int nv, const int *tris, const int *leaf_face, int n,
+    float4 *nodes, const int *iparent, const int *lparent, unsigned *flags, void *leaf_tri,
+    uint32_t *st) {
     HFCR_PDL_WAIT();
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ unsigned cnt[REFIT_WARPS][32];
+    __shared__ float sbox[REFIT_WARPS][32][12];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int base = (blockIdx.x * REFIT_WARPS + w) * 32;
+    cnt[w][lane] = 0u;
+    __syncwarp();
+    const int j = base + lane;
     if (j >= n) return;
     int f = leaf_face[j];
     T a[3], b[3], c[3];
@@ -358,26 +378,58 @@ __global__ void k_refit(const T *x, const T *y, const T *z, int nv, const int *t
     // only keeps a corrupted parent array from looping
     for (int guard = 0; guard < 128 && link >= 0; ++guard) {
         const int node = link >> 1;
-        const int slot = (link & 1) ? 6 : 0;
+        const int side = link & 1;
         const int up = iparent[node];  // read-only: load it before the handshake
         float *nf = (float *)(nodes + 4 * node);
-        nf[slot + 0] = lo[0];
-        nf[slot + 1] = lo[1];
-        nf[slot + 2] = lo[2];
-        nf[slot + 3] = hi[0];
-        nf[slot + 4] = hi[1];
-        nf[slot + 5] = hi[2];
-        // the first child to arrive leaves; the second (acquire) sees the
-        // first one's box (release) and carries the union upwards
-        unsigned old;
-        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
-                     : "=r"(old) : "l"(flags + node) : "memory");
-        if (old == 0) return;
-        const int sib = 6 - slot;
+        const float4 n3 = nodes[4 * node + 3];  // ids and leaf range: not written here
+        const int first = __float_as_int(n3.z), last = __float_as_int(n3.w);
+        // both children's lanes are in this warp when the range is: the
+        // node's slot q (one end of its range is the node's own index)
+        const int q = node - base;
+        if (first >= base && last < base + 32 && q >= 0 && q < 32) {
+            float *mine = sbox[w][q] + 6 * side;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            lo[k] = fminf(lo[k], __ldcg(nf + sib + k));
-            hi[k] = fmaxf(hi[k], __ldcg(nf + sib + 3 + k));
+            for (int k = 0; k < 3; ++k) {
+                mine[k] = lo[k];
+                mine[3 + k] = hi[k];
+            }
+            __threadfence_block();
+            if (atomicAdd(&cnt[w][q], 1u) == 0u) return;
+            __threadfence_block();
+            const volatile float *sb = sbox[w][q];
+            float bx[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) bx[k] = sb[k];
+            float4 *nd = nodes + 4 * node;
+            nd[0] = make_float4(bx[0], bx[1], bx[2], bx[3]);
+            nd[1] = make_float4(bx[4], bx[5], bx[6], bx[7]);
+            nd[2] = make_float4(bx[8], bx[9], bx[10], bx[11]);
+            const int o = 6 * (1 - side);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = fminf(lo[k], bx[o + k]);
+                hi[k] = fmaxf(hi[k], bx[o + 3 + k]);
+            }
+        } else {
+            const int slot = 6 * side;
+            nf[slot + 0] = lo[0];
+            nf[slot + 1] = lo[1];
+            nf[slot + 2] = lo[2];
+            nf[slot + 3] = hi[0];
+            nf[slot + 4] = hi[1];
+            nf[slot + 5] = hi[2];
+            // the first child to arrive leaves; the second (acquire) sees the
+            // first one's box (release) and carries the union upwards
+            unsigned old;
+            asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                         : "=r"(old) : "l"(flags + node) : "memory");
+            if (old == 0) return;
+            const int sib = 6 - slot;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = fminf(lo[k], __ldcg(nf + sib + k));
+                hi[k] = fmaxf(hi[k], __ldcg(nf + sib + 3 + k));
+            }
         }
         link = up;
     }
@@ -530,14 +582,14 @@ void bvh_refit(Bvh &b, const hfcr_mesh &m, uint32_t *d_status, cudaStream_t s) {
     int n = b.n;
     if (n <= 0) return;
     cudaMemsetAsync(b.flags, 0, sizeof(unsigned) * n, s);
-    int nb = (n + 255) / 256;
+    int nb = (n + 32 * REFIT_WARPS - 1) / (32 * REFIT_WARPS);
     if (m.dtype == HFCR_F32)
-        { launch_pdl(k_refit<float>, nb, 256, 0, s, (const float *)m.x, (const float *)m.y,
+        { launch_pdl(k_refit<float>, nb, 32 * REFIT_WARPS, 0, s, (const float *)m.x, (const float *)m.y,
                      (const float *)m.z,
                                           m.n_verts, m.tris, b.leaf_face, n, b.nodes, b.parent,
                                           b.parent + b.cap, b.flags, b.leaf_tri, d_status); note_launch(); }
     else
-        { launch_pdl(k_refit<double>, nb, 256, 0, s, (const double *)m.x, (const double *)m.y,
+        { launch_pdl(k_refit<double>, nb, 32 * REFIT_WARPS, 0, s, (const double *)m.x, (const double *)m.y,
                                            (const double *)m.z, m.n_verts, m.tris, b.leaf_face, n,
                                            b.nodes, b.parent, b.parent + b.cap, b.flags, b.leaf_tri,
                                            d_status); note_launch(); }
