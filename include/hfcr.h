@@ -145,6 +145,11 @@ typedef struct {
                                      current positions (exact boxes) instead of rebuilt, up to this
                                      many calls in a row (0: default 8; 1: rebuild every call).
                                      Only the traversal's speed depends on it, never the pairs. */
+    int32_t block_switch_iters; /* MIXED, impact zones of 1,024 rows or more: a float32 run that
+                                   reaches this many iterations ends there, and the zone's later
+                                   runs are preconditioned by blocks of up to 16 rows that share
+                                   x0 or a face (ill-conditioned zones) instead of the groups of
+                                   rows sharing x0 (0: default 48; -1: never) */
 } hfcr_options;
 
 typedef struct {

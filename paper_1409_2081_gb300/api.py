@@ -60,7 +60,8 @@ class hfcr_options(ctypes.Structure):
                 ("diffuse_rings", ctypes.c_int32), ("diffuse_sweeps", ctypes.c_int32),
                 ("traverse_variant", ctypes.c_int32), ("setup_path", ctypes.c_int32),
                 ("diffuse_max_iters", ctypes.c_int32), ("diffuse_tol", ctypes.c_double),
-                ("amplification_limit", ctypes.c_double), ("bvh_rebuild_interval", ctypes.c_int32)]
+                ("amplification_limit", ctypes.c_double), ("bvh_rebuild_interval", ctypes.c_int32),
+                ("block_switch_iters", ctypes.c_int32)]
 
 
 class hfcr_solve_info(ctypes.Structure):
@@ -204,13 +205,15 @@ class Context:
                  rel_tol: float = 1e-12, inner_tol: float = 1e-4, graphs: bool = True,
                  diffuse_rings: int = 0, diffuse_sweeps: int = 0, traverse_variant: int = 0,
                  setup_path: int = 0, diffuse_max_iters: int = 1000, diffuse_tol: float = 1e-10,
-                 amplification_limit: float = 1000.0, bvh_rebuild_interval: int = 8):
+                 amplification_limit: float = 1000.0, bvh_rebuild_interval: int = 8,
+                 block_switch_iters: int = 48):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("hfcr needs a CUDA device")
         opt = hfcr_options(solver, int(f32_filter), roles, max_cg_iters, max_refine, rel_tol, inner_tol,
                            int(graphs), diffuse_rings, diffuse_sweeps, traverse_variant, setup_path,
-                           diffuse_max_iters, diffuse_tol, amplification_limit, bvh_rebuild_interval)
+                           diffuse_max_iters, diffuse_tol, amplification_limit, bvh_rebuild_interval,
+                           block_switch_iters)
         h = ctypes.c_void_p()
         self.handle = None
         # a refused create has no context: its message is the thread's

@@ -158,7 +158,7 @@ void free_all(hfcr_ctx *c) {
                     c->sb.ck64, c->sb.ck64_alt, c->sb.gst, c->sb.zg, c->sb.d_ng, c->sb.pinv,
                     c->sb.z32,
                     c->sb.ids, c->sb.n64, c->sb.n32, c->sb.b, c->sb.lam, c->sb.r64, c->sb.r32,
-                    c->sb.x32, c->sb.p32, c->sb.q32, c->sb.w32, c->sb.p64, c->sb.q64, c->sb.cg64, c->sb.pinv64, c->sb.vidx, c->sb.ckey,
+                    c->sb.x32, c->sb.p32, c->sb.q32, c->sb.w32, c->sb.p64, c->sb.q64, c->sb.cg64, c->sb.pinv64, c->sb.binv, c->sb.vidx, c->sb.ckey,
                     c->sb.ckey_alt, c->sb.cval, c->sb.cval_alt, c->sb.cflag, c->sb.seg, c->sb.gvert,
                     c->sb.winv, c->sb.u64, c->sb.u32, c->sb.red};
     for (void *p : ptrs)
@@ -578,6 +578,7 @@ SolveParams params_of(const hfcr_options &o) {
     p.max_refine = o.max_refine;
     p.rel_tol = o.rel_tol;
     p.inner_tol = o.inner_tol;
+    p.block_switch = o.block_switch_iters;
     return p;
 }
 
@@ -836,6 +837,7 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
     c->opt.diffuse_tol = 1e-10;
     c->opt.amplification_limit = 1000.0;
     c->opt.bvh_rebuild_interval = 8;
+    c->opt.block_switch_iters = 48;
     if (opt) {
         c->opt = *opt;
         if (c->opt.max_cg_iters <= 0) c->opt.max_cg_iters = 500;
@@ -858,6 +860,8 @@ hfcr_status hfcr_create(hfcr_ctx **out, const hfcr_options *opt) {
         if (c->opt.diffuse_max_iters == 0) c->opt.diffuse_max_iters = 1000;
         if (c->opt.diffuse_tol == 0.0) c->opt.diffuse_tol = 1e-10;
         if (!(c->opt.amplification_limit > 0.0)) c->opt.amplification_limit = 1000.0;
+        if (c->opt.block_switch_iters == 0) c->opt.block_switch_iters = 48;
+        if (c->opt.block_switch_iters < 0) c->opt.block_switch_iters = -1;
         if (c->opt.bvh_rebuild_interval <= 0) c->opt.bvh_rebuild_interval = 8;
         if (!(c->opt.diffuse_tol > 0.0 && c->opt.diffuse_tol < 1.0) || c->opt.diffuse_max_iters < 0 ||
             c->opt.diffuse_max_iters > 100000) {
@@ -1019,6 +1023,7 @@ hfcr_status hfcr_reserve(hfcr_ctx *ctx, int64_t max_verts, int64_t max_tris, int
     CK(dalloc(&sb.p64, 2 * P));
     CK(dalloc(&sb.cg64, 5 * P));
     CK(dalloc(&sb.pinv64, P));
+    CK(dalloc(&sb.binv, 16 * P));
     CK(dalloc(&sb.q64, P));
     CK(dalloc(&sb.vidx, P));
     CK(dalloc(&sb.ckey, 4 * P));

@@ -258,6 +258,7 @@ struct SolveBuffers {
     double *p64 = nullptr, *q64 = nullptr;   // p64 [2 cap_k] (x and p), q64 [cap_k] (FP64 solver)
     double *cg64 = nullptr;      // [5 cap_k] r, p, s, w, z of the float64 per-zone CG
     double4_32a *pinv64 = nullptr;  // [cap_k] float64 inverse-block rows of that CG
+    float *binv = nullptr;          // [16 cap_k] rows of the large zones' block inverses (mixed)
     int4 *vidx = nullptr;        // [cap_k] compact vertex index of each stencil role
     // vertex CSR over 4k entries
     unsigned *ckey = nullptr, *ckey_alt = nullptr;   // [4 cap_k]
@@ -291,6 +292,7 @@ struct SolveParams {
     int max_refine;
     double rel_tol;
     double inner_tol;
+    int block_switch = 48;  // iterations of a large zone's run before the blocks (-1: never)
     StageMark big_mark;  // brackets the launches of the zones of ZONE_BIG rows or more
 };
 

@@ -332,6 +332,14 @@ struct CgViewT {
     const IX *cval;              // [4 k]
     const float *winv;           // [U]
     int voff = 0, coff = 0, eoff = 0;  // subtracted from vidx, cval and seg values (global path)
+    // the large zones' preconditioner (null bperm: the groups' inverse rows):
+    // blocks of rows sharing x0 or a face; place q of the block order holds
+    // row bperm[q], its block starts at place binfo[q] >> 5 and has
+    // binfo[q] & 31 rows, and binv + 16 q holds its row of the block's
+    // inverse (columns in block order)
+    const uint16_t *bperm = nullptr;
+    const int *binfo = nullptr;
+    const float *binv = nullptr;
     __device__ __forceinline__ float3 nrm(int s) const {
         float4 v = n4[s];
         return make_float3(v.x, v.y, v.z);
@@ -490,6 +498,36 @@ __device__ __forceinline__ void cg_precond_group(const V &v, int g) {
     }
 }
 
+// z = P^-1 r with P the blocks of rows sharing x0 or a face: one place of
+// the block order per thread, its row of the block's inverse (four float4
+// loads) against the block's residuals, summed in column order
+constexpr int BLOCK_MAX = 16;
+
+__host__ __device__ constexpr int tri(int i) { return i * (i + 1) / 2; }
+
+template <class Gp, class V>
+__device__ __forceinline__ void cg_precond_blocks(const V &v, int k) {
+    for (int q = Gp::rank(); q < k; q += Gp::size()) {
+        const int info = v.binfo[q];
+        const int r0 = info >> 5, m = info & 31;
+        const float4 *row = (const float4 *)(v.binv + 16 * (size_t)q);
+        float c[BLOCK_MAX];
+#pragma unroll
+        for (int t = 0; t < BLOCK_MAX / 4; ++t) {
+            const float4 x = t * 4 < m ? row[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+            c[4 * t] = x.x;
+            c[4 * t + 1] = x.y;
+            c[4 * t + 2] = x.z;
+            c[4 * t + 3] = x.w;
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int t = 0; t < BLOCK_MAX; ++t)
+            if (t < m) acc += c[t] * v.r[v.bperm[r0 + t]];
+        v.z[v.bperm[q]] = acc;
+    }
+}
+
 template <class Gp, class V>
 __device__ __forceinline__ void cg_matvec_vertex(const V &v, int U) {
     const float third = 1.0f / 3.0f;
@@ -532,7 +570,11 @@ template <class Gp, class V>
 __device__ __forceinline__ int cg_cg_loop(const V &v, int k, int U, int maxit, float tol,
                                           float *red) {
     const int tid = Gp::rank(), nt = Gp::size();
-    for (int g = tid; g < v.G; g += nt) cg_precond_group(v, g);
+    if (v.bperm) {
+        cg_precond_blocks<Gp>(v, k);
+    } else {
+        for (int g = tid; g < v.G; g += nt) cg_precond_group(v, g);
+    }
     Gp::sync();
     cg_matvec_vertex<Gp>(v, U);
     Gp::sync();
@@ -551,17 +593,32 @@ __device__ __forceinline__ int cg_cg_loop(const V &v, int k, int U, int maxit, f
     float alpha = gamma / delta, beta = 0.f;
     int it = 0;
     while (it < maxit && rho > stop && rho > 0.f && alpha > 0.f && isfinite(alpha)) {
-        for (int g = tid; g < v.G; g += nt) {
-            const int a = v.gst[g] - v.goff, b = v.gst[g + 1] - v.goff;
-            for (int s = a; s < b; ++s) {
-                float ps = v.z[s] + beta * v.p[s];
-                float ss = v.w[s] + beta * v.sv[s];
+        if (v.bperm) {
+            // the blocks span rows of other threads: the update, a barrier,
+            // then the blocks
+            for (int s = tid; s < k; s += nt) {
+                const float ps = v.z[s] + beta * v.p[s];
+                const float ss = v.w[s] + beta * v.sv[s];
                 v.p[s] = ps;
                 v.sv[s] = ss;
                 v.x[s] += alpha * ps;
                 v.r[s] -= alpha * ss;
             }
-            cg_precond_group(v, g);
+            Gp::sync();
+            cg_precond_blocks<Gp>(v, k);
+        } else {
+            for (int g = tid; g < v.G; g += nt) {
+                const int a = v.gst[g] - v.goff, b = v.gst[g + 1] - v.goff;
+                for (int s = a; s < b; ++s) {
+                    float ps = v.z[s] + beta * v.p[s];
+                    float ss = v.w[s] + beta * v.sv[s];
+                    v.p[s] = ps;
+                    v.sv[s] = ss;
+                    v.x[s] += alpha * ps;
+                    v.r[s] -= alpha * ss;
+                }
+                cg_precond_group(v, g);
+            }
         }
         Gp::sync();
         cg_matvec_vertex<Gp>(v, U);
@@ -986,6 +1043,8 @@ struct ZoneArgs {
     int nA;
     const float *wA, *wB;
     double4_32a *pinv64;  // [cap_k]
+    float *binv;          // [16 cap_k] rows of the large zones' block inverses (mixed solver)
+    int block_switch;     // iterations of a large zone's run before its blocks (-1: never)
 };
 
 // |b_zone|^2 with lam = 0 for the zone's rows
@@ -1014,9 +1073,292 @@ struct ZoneResult {
     int rounds;  // float32 runs
 };
 
-// Rounds of iterative refinement of zone z, everything the float32 CG
-// touches staged in shared memory at base (zone_smem_need bytes).
+// exclusive prefix sums of a[0 .. n) in place over the whole group (each
+// thread a contiguous run, warp and group scans of the runs' totals);
+// returns the total.  ws: 32 ints of scratch.
 template <class Gp>
+__device__ __forceinline__ int group_scan_excl(int *a, int n, int *ws) {
+    const int tid = Gp::rank(), nt = Gp::size();
+    const int lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+    const int per = (n + nt - 1) / nt, lo = tid * per, hi = lo + per < n ? lo + per : n;
+    int sum = 0;
+    for (int i = lo; i < hi; ++i) sum += a[i];
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    Gp::sync();
+    if (w == 0) {
+        int t = lane < nw ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) ws[lane] = t;
+    }
+    Gp::sync();
+    int run = (w > 0 ? ws[w - 1] : 0) + x - sum;
+    const int total = ws[nw - 1];
+    for (int i = lo; i < hi; ++i) {
+        const int t = a[i];
+        a[i] = run;
+        run += t;
+    }
+    Gp::sync();
+    return total;
+}
+
+// one union of the shared-memory union-find: the larger root is hooked
+// under the smaller (so every zone's blocks are the same whatever the
+// order of the unions); a lost race retries, at most a bounded number of
+// times (a skipped union leaves two blocks where one would do: still a
+// valid block preconditioner)
+__device__ __forceinline__ void uf_union_s(int *par, int a, int b) {
+    volatile int *vp = par;
+    for (int tries = 0; tries < 4096; ++tries) {
+        a = uf_find_s(vp, a);
+        b = uf_find_s(vp, b);
+        if (a == b) return;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(par + b, b, a) == b) return;
+    }
+}
+
+// The inverse of one block of m <= N rows (rows[0 .. m)), in float64 (a
+// block of nearly dependent rows has a large condition number, and its
+// float32 inverse can come out indefinite): the matrix from the float32
+// normals (products exact in float64), factored L L^T (the diagonal kept as
+// 1 / L_ii; a pivot below 1e-12 of its diagonal entry makes the block its
+// diagonal), L^-1, then L^-T L^-1, symmetric by construction, rounded to
+// float32; row i to out + 16 i.  N fixes the unrolled bounds (a block pays
+// for the size class it falls in).
+template <int N, class V>
+__device__ __forceinline__ void block_inverse(const V &v, const uint16_t *rows, int m, float *out) {
+    const double third = 1.0 / 3.0;
+    double Lr[tri(N)];
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (i >= m) continue;
+        const int si = rows[i];
+        const ushort4 gi = v.vidx[si];
+        const float3 ni = v.nrm(si);
+        const int vi[4] = {gi.x, gi.y, gi.z, gi.w};
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            const int sj = rows[j];
+            const ushort4 gj = v.vidx[sj];
+            const float3 nj = v.nrm(sj);
+            const int vj[4] = {gj.x, gj.y, gj.z, gj.w};
+            double wsh = 0.0;
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (vi[p] == vj[q]) wsh += (p ? -third : 1.0) * (q ? -third : 1.0) * (double)v.winv[vi[p]];
+            const double dot = (double)ni.x * nj.x + (double)ni.y * nj.y + (double)ni.z * nj.z;
+            double a_ij = dot * wsh;
+            const double a_ii = a_ij;
+#pragma unroll
+            for (int q = 0; q < j; ++q) a_ij -= Lr[tri(i) + q] * Lr[tri(j) + q];
+            if (j < i) {
+                Lr[tri(i) + j] = a_ij * Lr[tri(j) + j];
+            } else if (ok && a_ij > 1e-12 * a_ii && isfinite(a_ij)) {
+                Lr[tri(i) + i] = rsqrt(a_ij);
+            } else {
+                ok = false;
+            }
+        }
+    }
+    if (!ok) {
+        // the block's diagonal alone
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            if (i >= m) continue;
+            const int si = rows[i];
+            const ushort4 gi = v.vidx[si];
+            const float3 ni = v.nrm(si);
+            const int vi[4] = {gi.x, gi.y, gi.z, gi.w};
+            double wsh = 0.0;
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (vi[p] == vi[q]) wsh += (p ? -third : 1.0) * (q ? -third : 1.0) * (double)v.winv[vi[p]];
+            const double d = ((double)ni.x * ni.x + (double)ni.y * ni.y + (double)ni.z * ni.z) * wsh;
+#pragma unroll
+            for (int q = 0; q < i; ++q) Lr[tri(i) + q] = 0.0;
+            Lr[tri(i) + i] = d > 0.0 && isfinite(d) ? rsqrt(d) : 1.0;
+        }
+    }
+    double Li[tri(N)];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        if (j >= m) continue;
+        Li[tri(j) + j] = Lr[tri(j) + j];
+#pragma unroll
+        for (int i = j + 1; i < N; ++i) {
+            if (i >= m) continue;
+            double t = 0.0;
+#pragma unroll
+            for (int q = j; q < i; ++q) t += Lr[tri(i) + q] * Li[tri(q) + j];
+            Li[tri(i) + j] = -t * Lr[tri(i) + i];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (i >= m) continue;
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            double t = 0.0;
+#pragma unroll
+            for (int q = i; q < N; ++q)
+                if (q < m) t += Li[tri(q) + i] * Li[tri(q) + j];
+            out[16 * i + j] = (float)t;
+            out[16 * j + i] = (float)t;
+        }
+    }
+}
+
+// The preconditioner blocks of a staged large zone (Sec. 4's rows of one
+// impact zone): rows joined when they share x0 or the face (their nearly
+// parallel rows make the zone's system ill-conditioned, and a block that
+// holds them all captures that); a component of at most BLOCK_MAX rows is
+// one block, a larger one is cut into runs of whole x0 groups of at most
+// BLOCK_MAX rows, in row order.  Rows are ordered by block
+// (ascending within a block), and every block's matrix, entry (s, t) =
+// (n_s . n_t) sum over the vertices v the two rows share of c_s(v) c_t(v)
+// w(v) (c = 1 at x0, -1/3 at a face vertex), is factored L L^T in float32
+// (a pivot that is not positive makes the block its diagonal) and inverted
+// as L^-T L^-1, which is symmetric by construction; place q of the block
+// order gets its row bperm[q], its block's start and size binfo[q] and its
+// row of the inverse at binv + 16 q.  Called between rounds; scratch: the
+// CG vectors p, sv, w, z and x (dead between rounds), bst (k + 1 ints) and
+// 96 ints at ws.  Returns the block count.  Not inlined: its register
+// needs (the unrolled factorisations) stay out of the CG loop's allocation.
+template <class Gp>
+__device__ __noinline__ int zone_blocks(const CgViewS &v, int k, int U, const int *gst, int G,
+                                           uint16_t *bperm, int *binfo, int *bst, float *binv,
+                                           int *ws) {
+    const int tid = Gp::rank(), nt = Gp::size();
+    int *par = (int *)v.p;   // [k] union-find parents, then each row's block key
+    int *cnt = (int *)v.sv;  // [k] component sizes, then block numbers of the keys
+    int *hist = (int *)v.w;  // [k + 1] rows per key (w and z are contiguous)
+    for (int t = tid; t < k; t += nt) {
+        par[t] = t;
+        cnt[t] = 0;
+    }
+    for (int t = tid; t <= k; t += nt) hist[t] = 0;
+    Gp::sync();
+    // rows with the same x0 are neighbours in the zone's order (dir, x0, face)
+    for (int t = 1 + tid; t < k; t += nt)
+        if (v.vidx[t].x == v.vidx[t - 1].x) uf_union_s(par, t, t - 1);
+    // rows with the same face both list its first vertex in role 1
+    for (int j = tid; j < U; j += nt) {
+        const int e0 = v.seg[j], e1 = v.seg[j + 1];
+        for (int e = e0; e < e1; ++e) {
+            const int c = v.cval[e];
+            if ((c & 3) != 1) continue;
+            const ushort4 gs = v.vidx[c >> 2];
+            for (int f = e + 1; f < e1; ++f) {
+                const int c2 = v.cval[f];
+                if ((c2 & 3) != 1) continue;
+                const ushort4 gt = v.vidx[c2 >> 2];
+                if (gs.z == gt.z && gs.w == gt.w) uf_union_s(par, c >> 2, c2 >> 2);
+            }
+        }
+    }
+    Gp::sync();
+    for (int t = tid; t < k; t += nt) par[t] = uf_find_s((volatile int *)par, t);
+    Gp::sync();
+    for (int t = tid; t < k; t += nt) atomicAdd(&cnt[par[t]], 1);
+    int *keys = (int *)v.x;  // the block key of each row (x is dead between rounds)
+    int *nbig = ws + 32, *big = ws + 33;
+    if (tid == 0) *nbig = 0;
+    Gp::sync();
+    // the components of more than BLOCK_MAX rows (up to 63 of them)
+    for (int t = tid; t < k; t += nt)
+        if (par[t] == t && cnt[t] > BLOCK_MAX) {
+            const int i = atomicAdd(nbig, 1);
+            if (i < 63) big[i] = t;
+        }
+    // block key of a row: its component's root; in a larger component the
+    // first row of its x0 group, unless that component is split below
+    for (int g = tid; g < G; g += nt)
+        for (int t = gst[g]; t < gst[g + 1]; ++t) {
+            const int r = par[t];
+            keys[t] = cnt[r] <= BLOCK_MAX ? r : gst[g];
+        }
+    Gp::sync();
+    // a listed large component in runs of whole x0 groups, in row order, of
+    // at most BLOCK_MAX rows (one thread a component; the key of a run is
+    // its first row)
+    const int nb_list = *nbig < 63 ? *nbig : 63;
+    for (int c = tid; c < nb_list; c += nt) {
+        const int r = big[c];
+        int acc = 0, key = -1;
+        for (int g = 0; g < G; ++g) {
+            const int t0 = gst[g];
+            if (par[t0] != r) continue;
+            const int sz = gst[g + 1] - t0;
+            if (key < 0 || acc + sz > BLOCK_MAX) {
+                key = t0;
+                acc = 0;
+            }
+            acc += sz;
+            for (int t = t0; t < t0 + sz; ++t) keys[t] = key;
+        }
+    }
+    Gp::sync();
+    for (int t = tid; t < k; t += nt) atomicAdd(&hist[keys[t]], 1);
+    Gp::sync();
+    group_scan_excl<Gp>(hist, k + 1, ws);  // hist[key]: first place of the key's rows
+    for (int q = tid; q < k; q += nt) cnt[q] = hist[q + 1] > hist[q] ? 1 : 0;
+    Gp::sync();
+    const int NB = group_scan_excl<Gp>(cnt, k, ws);
+    for (int q = tid; q < k; q += nt)
+        if (hist[q + 1] > hist[q]) bst[cnt[q]] = hist[q];
+    if (tid == 0) bst[NB] = k;
+    Gp::sync();
+    for (int t = tid; t < k; t += nt) bperm[atomicAdd(&hist[keys[t]], 1)] = (uint16_t)t;
+    Gp::sync();
+    // one thread per block: its rows in ascending order, then its inverse
+    for (int b = tid; b < NB; b += nt) {
+        const int r0 = bst[b], m = bst[b + 1] - r0;
+        for (int i = 1; i < m; ++i) {
+            const uint16_t x = bperm[r0 + i];
+            int j = i - 1;
+            while (j >= 0 && bperm[r0 + j] > x) {
+                bperm[r0 + j + 1] = bperm[r0 + j];
+                --j;
+            }
+            bperm[r0 + j + 1] = x;
+        }
+        for (int i = 0; i < m; ++i) binfo[r0 + i] = (r0 << 5) | m;
+        float *out = binv + 16 * (size_t)r0;
+        if (m <= 4)
+            block_inverse<4>(v, bperm + r0, m, out);
+        else if (m <= 8)
+            block_inverse<8>(v, bperm + r0, m, out);
+        else
+            block_inverse<BLOCK_MAX>(v, bperm + r0, m, out);
+    }
+    Gp::sync();
+    return NB;
+}
+
+// Rounds of iterative refinement of zone z, everything the float32 CG
+// touches staged in shared memory at base (zone_smem_need bytes); BLK: the
+// large zones' preconditioner blocks (zone_blocks) instead of the groups.
+template <class Gp, bool BLK = false>
 __device__ __forceinline__ ZoneResult solve_zone_smem(const ZoneArgs &a, int z, char *base, double bb,
                                                       float *red, double *redd) {
     const int tid = Gp::rank(), nt = Gp::size();
@@ -1054,19 +1396,50 @@ __device__ __forceinline__ ZoneResult solve_zone_smem(const ZoneArgs &a, int z, 
     v.vidx = vidx; v.seg = seg; v.cval = cval; v.winv = winv;
     v.voff = 0; v.coff = 0; v.eoff = 0;
     double rr = bb;
-    int its = 0, rounds = 0;
-    while (rr > target && rounds < a.max_refine) {
+    int its = 0, rounds = 0, extra = 0;
+    // BLK: a run stops after block_switch iterations; a zone that needs
+    // more (an ill-conditioned one) keeps that run's correction and
+    // continues on the blocks (that run is not counted)
+    bool blocks_on = false;
+    const bool may_switch = BLK && a.block_switch > 0 && a.block_switch < a.maxit;
+    while (rr > target && rounds < a.max_refine + extra) {
         for (int t = tid; t < k; t += nt) {
             v.p[t] = 0.f;
             v.sv[t] = 0.f;
             v.x[t] = 0.f;
         }
         Gp::sync();
-        its += cg_cg_loop<Gp>(v, k, U, a.maxit, (float)a.tol, red);
+        const int cap_it = may_switch && !blocks_on ? a.block_switch : a.maxit;
+        const int n_it = cg_cg_loop<Gp>(v, k, U, cap_it, (float)a.tol, red);
+        its += n_it;
         for (int t = tid; t < k; t += nt) a.lam[s0 + t] += (double)v.x[t];
         Gp::sync();
+        const double rr_prev = rr;
         rr = zone_residual<Gp>(v, k, U, s0, j0, a.n64, a.b64, a.lam, a.u64, redd);
         ++rounds;
+        if (!(rr < rr_prev)) {
+            // the run did not reduce the float64 residual (a stagnating or
+            // failing float32 run): its correction is taken back, the zone
+            // keeps the best lambda found
+            for (int t = tid; t < k; t += nt) a.lam[s0 + t] -= (double)v.x[t];
+            rr = rr_prev;
+            Gp::sync();
+            break;
+        }
+        if (may_switch && !blocks_on && n_it >= cap_it && rr > target) {
+            // the block order, the places' blocks and the block starts in
+            // the groups' inverse rows' slot (16 B a row: 2 + 4 + 4)
+            uint16_t *bperm = (uint16_t *)pinv;
+            int *binfo = (int *)(bperm + ((k + 7) & ~7));
+            int *bst = binfo + k;
+            float *binv = a.binv + 16 * (size_t)s0;
+            zone_blocks<Gp>(v, k, U, gst, G, bperm, binfo, bst, binv, (int *)red);
+            v.bperm = bperm;
+            v.binfo = binfo;
+            v.binv = binv;
+            blocks_on = true;
+            extra = 1;
+        }
     }
     ZoneResult res;
     res.rr = rr;
@@ -1117,7 +1490,7 @@ struct ZoneScratch {
     float *x, *r, *p, *s, *w, *z, *u;
 };
 
-template <class Gp>
+template <class Gp, bool BLK = false>
 __device__ __forceinline__ void solve_zone(const ZoneArgs &a, int z, char *base, int smem_bytes,
                                            float *red, double *redd, const ZoneScratch &g) {
     const int tid = Gp::rank(), nt = Gp::size();
@@ -1129,7 +1502,7 @@ __device__ __forceinline__ void solve_zone(const ZoneArgs &a, int z, char *base,
     int its = 0, rounds = 0;
     double rr;
     if (in_smem) {
-        const ZoneResult r = solve_zone_smem<Gp>(a, z, base, bb, red, redd);
+        const ZoneResult r = solve_zone_smem<Gp, BLK>(a, z, base, bb, red, redd);
         rr = r.rr;
         its = r.its;
         rounds = r.rounds;
@@ -1155,8 +1528,15 @@ __device__ __forceinline__ void solve_zone(const ZoneArgs &a, int z, char *base,
             its += cg_cg_loop<Gp>(v, k, U, a.maxit, (float)a.tol, red);
             for (int t = tid; t < k; t += nt) a.lam[s0 + t] += (double)v.x[t];
             Gp::sync();
+            const double rr_prev = rr;
             rr = zone_residual<Gp>(v, k, U, s0, j0, a.n64, a.b64, a.lam, a.u64, redd);
             ++rounds;
+            if (!(rr < rr_prev)) {  // as in the staged path: the run is taken back
+                for (int t = tid; t < k; t += nt) a.lam[s0 + t] -= (double)v.x[t];
+                rr = rr_prev;
+                Gp::sync();
+                break;
+            }
         }
     }
     if (tid == 0) zone_finish(a, z, rr, bb, its, rounds, in_smem);
@@ -1246,7 +1626,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cg_zone(const int *d_nz, ZoneArg
         if (k <= k_lo) continue;
         if (leave_big && zone_smem_need(k, a.zv[z + 1] - a.zv[z], a.zg[z + 1] - a.zg[z]) > smem_bytes)
             continue;
-        solve_zone<CtaGroup>(a, z, (char *)smem4, smem_bytes, red, redd, g);
+        solve_zone<CtaGroup, true>(a, z, (char *)smem4, smem_bytes, red, redd, g);
         if (threadIdx.x == 0) {  // rows and touched vertices of the large zones
             atomicAdd(&a.ctl[5], k);
             atomicAdd(&a.ctl[6], a.zv[z + 1] - a.zv[z]);
@@ -2682,6 +3062,8 @@ void solve(const SolveParams &p, const MeshPair &mp, const int *d_k, int cap, So
     za.maxit = p.max_cg_iters; za.max_refine = p.max_refine;
     za.tol = p.inner_tol; za.rel_tol = p.rel_tol; za.ctl = sb.iwork;
     za.ticket = (unsigned *)(sb.iwork + 13);  // iwork is zeroed before every solve
+    za.binv = sb.binv;
+    za.block_switch = p.block_switch;
     const int warp_max = g_warp_zone_smem ? WARP_ZONE : 0;
     if (warp_max) {
         int zw = (cap + WARP_ZONE_WARPS - 1) / WARP_ZONE_WARPS;  // CTAs of the warp launch

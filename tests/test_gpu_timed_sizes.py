@@ -153,6 +153,10 @@ def test_frame_sequence_sampled_frames(api):
     cap = 1 << 18
     ctx64 = api.Context()   # the float64 widening of the same positions: dx in float64
     ctx64.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), cap)
+    # the same response with every large zone on the blocks of rows sharing
+    # x0 or a face after its first iteration (the path ill-conditioned zones take)
+    ctxb = api.Context(block_switch_iters=1)
+    ctxb.hfcr_reserve(max(sc.A.n_verts, sc.B.n_verts), max(sc.A.n_tris, sc.B.n_tris), cap)
     pbuf = torch.zeros((cap, 4), dtype=torch.int32, device="cuda:0")
     sbuf = torch.zeros((cap, 4), dtype=torch.int32, device="cuda:0")
     checked = []
@@ -175,6 +179,12 @@ def test_frame_sequence_sampled_frames(api):
                 ctx64.hfcr_respond(A64, B64, sbuf, k, D_POST, dxA, dxB)
                 g = np.concatenate([torch.stack(dxA, 1).cpu().numpy(), torch.stack(dxB, 1).cpu().numpy()])
                 assert rel_err(g, np.concatenate([dA, dB])) <= 1e-6, f
+                for t in dxA + dxB:
+                    t.zero_()
+                si = ctxb.hfcr_respond(A64, B64, sbuf, k, D_POST, dxA, dxB)
+                g = np.concatenate([torch.stack(dxA, 1).cpu().numpy(), torch.stack(dxB, 1).cpu().numpy()])
+                assert rel_err(g, np.concatenate([dA, dB])) <= 1e-6, ("blocks", f)
+                assert si.rel_residual <= 1e-12, ("blocks", f, si.rel_residual)
                 eA = (PA + oracle.diffuse(dA, EA, R)).astype(np.float32).astype(np.float64)
                 eB = (PB + oracle.diffuse(dB, EB, R)).astype(np.float32).astype(np.float64)
         info = ctx.hfcr_resolve(A, B, D_POST, 1)
