@@ -1228,6 +1228,86 @@ __device__ __forceinline__ void block_inverse(const V &v, const uint16_t *rows, 
     }
 }
 
+// The inverse of one block of 4 < m <= BLOCK_MAX rows by one warp, in
+// float64: lane j < 16 holds column j of the block's matrix, lane 16 + j
+// column j of the identity; Gauss-Jordan elimination without pivoting (the
+// matrix is symmetric positive definite), the pivot column broadcast by
+// shuffles at each step, turns the right half into the inverse, which is
+// written rounded to float32 and made symmetric pairwise; a pivot that is
+// not positive makes the block its diagonal.  Called by every lane.
+template <class V>
+__device__ __forceinline__ void block_inverse_warp(const V &v, const uint16_t *rows, int m, float *out) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, j = lane & 15;
+    const double third = 1.0 / 3.0;
+    double c[BLOCK_MAX];
+#pragma unroll
+    for (int i = 0; i < BLOCK_MAX; ++i) c[i] = 0.0;
+    if (lane < 16 && j < m) {
+        const int sj = rows[j];
+        const ushort4 gj = v.vidx[sj];
+        const float3 nj = v.nrm(sj);
+        const int vj[4] = {gj.x, gj.y, gj.z, gj.w};
+#pragma unroll
+        for (int i = 0; i < BLOCK_MAX; ++i) {
+            if (i >= m) continue;
+            const int si = rows[i];
+            const ushort4 gi = v.vidx[si];
+            const float3 ni = v.nrm(si);
+            const int vi[4] = {gi.x, gi.y, gi.z, gi.w};
+            double wsh = 0.0;
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (vi[p] == vj[q]) wsh += (p ? -third : 1.0) * (q ? -third : 1.0) * (double)v.winv[vi[p]];
+            c[i] = ((double)ni.x * nj.x + (double)ni.y * nj.y + (double)ni.z * nj.z) * wsh;
+        }
+    } else if (lane >= 16 && j < m) {
+#pragma unroll
+        for (int i = 0; i < BLOCK_MAX; ++i)
+            if (i == j) c[i] = 1.0;
+    }
+    double dj = 0.0;  // the block's diagonal entry of lane j (< 16), for the fallback
+#pragma unroll
+    for (int i = 0; i < BLOCK_MAX; ++i)
+        if (i == j) dj = c[i];
+    bool ok = true;
+#pragma unroll
+    for (int kk = 0; kk < BLOCK_MAX; ++kk) {
+        if (kk >= m) break;
+        const double piv = __shfl_sync(full, c[kk], kk);
+        const double d0 = __shfl_sync(full, dj, kk);
+        ok = ok && piv > 1e-12 * d0 && isfinite(piv);
+        c[kk] *= 1.0 / piv;
+#pragma unroll
+        for (int i = 0; i < BLOCK_MAX; ++i) {
+            if (i >= m || i == kk) continue;
+            const double f = __shfl_sync(full, c[i], kk);
+            c[i] -= f * c[kk];
+        }
+    }
+    if (ok) {
+        if (lane >= 16 && j < m) {
+#pragma unroll
+            for (int i = 0; i < BLOCK_MAX; ++i)
+                if (i < m) out[16 * i + j] = (float)c[i];
+        }
+        __syncwarp();
+        // (i, u) and (u, i) to their mean, the pair handled by lane i > u
+        if (lane < m) {
+            for (int u = 0; u < lane; ++u) {
+                const float x = 0.5f * (out[16 * lane + u] + out[16 * u + lane]);
+                out[16 * lane + u] = x;
+                out[16 * u + lane] = x;
+            }
+        }
+    } else if (lane < 16 && j < m) {
+        for (int i = 0; i < m; ++i) out[16 * i + j] = i == j ? (dj > 0.0 && isfinite(dj) ? (float)(1.0 / dj) : 1.f) : 0.f;
+    }
+    __syncwarp();
+}
+
 // The preconditioner blocks of a staged large zone (Sec. 4's rows of one
 // impact zone): rows joined when they share x0 or the face (their nearly
 // parallel rows make the zone's system ill-conditioned, and a block that
@@ -1330,7 +1410,12 @@ __device__ __noinline__ int zone_blocks(const CgViewS &v, int k, int U, const in
     Gp::sync();
     for (int t = tid; t < k; t += nt) bperm[atomicAdd(&hist[keys[t]], 1)] = (uint16_t)t;
     Gp::sync();
-    // one thread per block: its rows in ascending order, then its inverse
+    // one thread per block: its rows in ascending order, then the inverse of
+    // a block of at most 4 rows; the larger ones are listed for the warps
+    int *wlist = cnt;  // the block numbers are no longer needed
+    int *nwl = ws + 32;
+    if (tid == 0) *nwl = 0;
+    Gp::sync();
     for (int b = tid; b < NB; b += nt) {
         const int r0 = bst[b], m = bst[b + 1] - r0;
         for (int i = 1; i < m; ++i) {
@@ -1343,13 +1428,19 @@ __device__ __noinline__ int zone_blocks(const CgViewS &v, int k, int U, const in
             bperm[r0 + j + 1] = x;
         }
         for (int i = 0; i < m; ++i) binfo[r0 + i] = (r0 << 5) | m;
-        float *out = binv + 16 * (size_t)r0;
         if (m <= 4)
-            block_inverse<4>(v, bperm + r0, m, out);
-        else if (m <= 8)
-            block_inverse<8>(v, bperm + r0, m, out);
+            block_inverse<4>(v, bperm + r0, m, binv + 16 * (size_t)r0);
         else
-            block_inverse<BLOCK_MAX>(v, bperm + r0, m, out);
+            wlist[atomicAdd(nwl, 1)] = b;  // for a warp below
+    }
+    Gp::sync();
+    // the larger blocks, one warp each
+    {
+        const int nwarps = nt >> 5, w = tid >> 5, nl = *nwl;
+        for (int i = w; i < nl; i += nwarps) {
+            const int b = wlist[i], r0 = bst[b];
+            block_inverse_warp(v, bperm + r0, bst[b + 1] - r0, binv + 16 * (size_t)r0);
+        }
     }
     Gp::sync();
     return NB;
