@@ -134,7 +134,7 @@ KERNELS = {
     "k_band_cl": (("diffuse.cu",), "k_band_cl_frame_sequence.md"),
     "k_cg_zone_pair": (("solve.cu",), "k_cg_zone_pair_cloth_torus.md"),
     "k_refit": (("bvh.cu",), "k_refit_frame_sequence.md"),
-    "k_cg_zone_big": (("solve.cu",), "k_cg_zone_1024_frame_sequence.md"),
+    "k_cg_zone_big": (("solve.cu",), "k_cg_zone_big_frame_sequence.md"),
 }
 
 
