@@ -98,19 +98,20 @@ __global__ void k_ring_init(DPair P, const double *u, int *ring, int far) {
     ring[g] = (x[0] != 0.0 || x[1] != 0.0 || x[2] != 0.0) ? 0 : far;
 }
 
-// breadth-first level r: a vertex not reached yet joins when a neighbour
-// sits at level r - 1 (levels r - 1 and below no longer change)
+// breadth-first level r: every vertex at level r - 1 gives level r to its
+// neighbours not reached yet (levels r - 1 and below no longer change; all
+// writers of a vertex write the same r, and a vertex reached in this step is
+// not read as a source of it)
 __global__ void k_ring_step(DPair P, int *ring, int r, int far) {
     HFCR_PDL_WAIT();
     int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= P.ntot || ring[g] != far) return;
+    if (g >= P.ntot || ring[g] != r - 1) return;
     const DMesh &M = P.of(g);
     const int v = g - M.off;
-    for (int e = M.ptr[v]; e < M.ptr[v + 1]; ++e)
-        if (ring[M.off + M.nbr[e]] == r - 1) {
-            ring[g] = r;
-            return;
-        }
+    for (int e = M.ptr[v]; e < M.ptr[v + 1]; ++e) {
+        const int w = M.off + M.nbr[e];
+        if (ring[w] == far) ring[w] = r;
+    }
 }
 
 // one Jacobi sweep: band vertices (1 <= ring <= R, not kinematic) take the
