@@ -194,8 +194,10 @@ typedef struct {
                                       vertices far more than the penetration depths */
     int64_t band_vertices;         /* harmonic diffusion: free band vertices (the unknowns of
                                       the band's Dirichlet problem), summed over the iterations */
-    int64_t big_zone_rows;         /* MIXED: rows of the impact zones of 1,024 rows or more
-                                      (one CTA or one cluster per zone), summed over the
+    int64_t big_zone_rows;         /* MIXED: rows of the impact zones solved one CTA or one
+                                      cluster per zone: those of 1,024 rows or more, and
+                                      those of 256 or more when there are at most as many
+                                      of them as the launch's CTAs; summed over the
                                       iterations */
     int64_t big_zone_vertices;     /* and the vertices those zones touch */
 } hfcr_resolve_info;

@@ -1661,6 +1661,40 @@ __device__ __forceinline__ int next_zone(unsigned *counter, int stride, int *slo
     return z;
 }
 
+// The zones of at least ZONE_MID stencils go to the large-zone launch, one
+// CTA each, when there are no more of them than its CTAs: a frame's few
+// large contact zones then run side by side instead of one launch after
+// the other, and each may switch to its blocks.  Otherwise the pair launch
+// takes those below ZONE_BIG as before.  Both launches count them from the
+// zone starts (one barrier per blockDim.x zones), so they take the same
+// decision.  Returns how many zones have at least lo stencils; *pick: the
+// one of rank `rank` among them in zone order, -1 if none (identical in
+// every thread of the CTA).
+__device__ __forceinline__ int zones_at_least(const int *zs, int nz, int lo, int rank, int *pick) {
+    __shared__ int wc[32];
+    __shared__ int found;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) found = -1;
+    int total = 0;
+    for (int base = 0; base < nz; base += blockDim.x) {
+        const int z = base + threadIdx.x;
+        const bool pred = z < nz && zs[z + 1] - zs[z] >= lo;
+        const int c = __syncthreads_count(pred);
+        if (rank >= total && rank < total + c) {  // the same in every thread
+            const unsigned bal = __ballot_sync(0xffffffffu, pred);
+            if (lane == 0) wc[w] = __popc(bal);
+            __syncthreads();
+            int before = total + __popc(bal & ((1u << lane) - 1u));
+            for (int q = 0; q < w; ++q) before += wc[q];
+            if (pred && before == rank) found = z;
+        }
+        total += c;
+    }
+    __syncthreads();
+    *pick = found;
+    return total;
+}
+
 // the zones of small_lo < k < ZONE_MID stencils on half H (first fixed
 // zone: blockIdx.x + H gridDim.x)
 template <int H>
@@ -1677,17 +1711,24 @@ __device__ __forceinline__ void half_zones(const ZoneArgs &a, int nz, int small_
 }
 
 __global__ void __launch_bounds__(512, 2) k_cg_zone_pair(const int *d_nz, ZoneArgs a, int small_lo,
-                                                         ZoneScratch g, int smem_bytes) {
+                                                         ZoneScratch g, int smem_bytes, int big_ctas) {
     HFCR_PDL_WAIT();
     extern __shared__ float4 smem4[];
     __shared__ float red[96];     // halves: 24 floats each; the whole CTA: 48
     __shared__ double redd[16];   // halves: 8 each; the whole CTA: 16
     __shared__ int slot[3];
     const int nz = *d_nz;
-    // the larger zones first, on all 512 threads
+    // the larger zones first, on all 512 threads (unless the large-zone
+    // launch takes them)
+    __shared__ int first;
+    {
+        int unused;
+        const bool to_big = zones_at_least(a.zs, nz, ZONE_MID, -1, &unused) <= big_ctas;
+        if (threadIdx.x == 0) first = to_big ? nz : (int)blockIdx.x;
+        __syncthreads();
+    }
     const bool more = nz > (int)gridDim.x;  // zones beyond the fixed ones
-    for (int z = blockIdx.x; z < nz;
-         z = more ? next_zone<CtaGroup>(a.ticket, gridDim.x, slot + 2) : nz) {
+    for (int z = first; z < nz; z = more ? next_zone<CtaGroup>(a.ticket, gridDim.x, slot + 2) : nz) {
         const int k = a.zs[z + 1] - a.zs[z];
         if (k < ZONE_MID || k >= ZONE_BIG) continue;
         solve_zone<CtaGroup>(a, z, (char *)smem4, smem_bytes, red, redd, g);
@@ -1702,23 +1743,39 @@ __global__ void __launch_bounds__(512, 2) k_cg_zone_pair(const int *d_nz, ZoneAr
                       g, slot + 1);
 }
 
-// leave_big: zones that do not fit smem_bytes are left to the cluster
-// solver (k_cg_zone_cl) instead of the global-memory path
+// The zones of more than k_lo stencils, one CTA each; or, when there are
+// no more zones of at least mid_lo stencils than CTAs (zones_at_least),
+// the zone of rank blockIdx.x among those.  leave_big: zones that do not
+// fit smem_bytes are left to the cluster solver (k_cg_zone_cl) instead of
+// the global-memory path.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) k_cg_zone(const int *d_nz, ZoneArgs a, int k_lo,
-                                                        ZoneScratch g, int smem_bytes, int leave_big) {
+                                                        int mid_lo, ZoneScratch g, int smem_bytes,
+                                                        int leave_big) {
     HFCR_PDL_WAIT();
     extern __shared__ float4 smem4[];
     __shared__ float red[96];
     __shared__ double redd[THREADS / 32];
     const int nz = *d_nz;
-    for (int z = blockIdx.x; z < nz; z += gridDim.x) {
+    // the loop's first zone, its stride, and the zones' smallest size minus one
+    __shared__ int sel[3];
+    {
+        int pick;
+        const bool ranked = zones_at_least(a.zs, nz, mid_lo, blockIdx.x, &pick) <= (int)gridDim.x;
+        if (threadIdx.x == 0) {
+            sel[0] = ranked ? (pick >= 0 ? pick : nz) : (int)blockIdx.x;
+            sel[1] = ranked ? nz : (int)gridDim.x;
+            sel[2] = ranked ? mid_lo - 1 : k_lo;
+        }
+        __syncthreads();
+    }
+    for (int z = sel[0]; z < nz; z += sel[1]) {
         const int k = a.zs[z + 1] - a.zs[z];
-        if (k <= k_lo) continue;
+        if (k <= sel[2]) continue;
         if (leave_big && zone_smem_need(k, a.zv[z + 1] - a.zv[z], a.zg[z + 1] - a.zg[z]) > smem_bytes)
             continue;
         solve_zone<CtaGroup, true>(a, z, (char *)smem4, smem_bytes, red, redd, g);
-        if (threadIdx.x == 0) {  // rows and touched vertices of the large zones
+        if (threadIdx.x == 0) {  // rows and touched vertices of the zones of this launch
             atomicAdd(&a.ctl[5], k);
             atomicAdd(&a.ctl[6], a.zv[z + 1] - a.zv[z]);
         }
@@ -3170,16 +3227,16 @@ void solve(const SolveParams &p, const MeshPair &mp, const int *d_k, int cap, So
     // of ZONE_BIG or more stencils each
     int zpair = (cap / (WARP_ZONE + 1) + 1) / 2 + 1;
     if (zpair > 2 * 152) zpair = 2 * 152;
-    int zbig = (cap + ZONE_BIG - 1) / ZONE_BIG;
+    int zbig = (cap + ZONE_MID - 1) / ZONE_MID;
     if (zbig > 152) zbig = 152;
     { launch_pdl(k_cg_zone_pair, zpair, 512, g_zone_pair_smem, s, sb.d_nz, za, warp_max, gs,
-                 g_zone_pair_smem); note_launch(); }
+                 g_zone_pair_smem, zbig); note_launch(); }
     // zones of ZONE_BIG rows or more: one CTA each when they fit its shared
     // memory; larger ones on a cluster of CL CTAs (or, without
     // clusters, on global memory)
     p.big_mark(1, s);
     { launch_pdl(k_cg_zone<BIG_ZONE_THREADS>, zbig, BIG_ZONE_THREADS, fast_smem, s, sb.d_nz, za, ZONE_BIG - 1,
-                 gs, fast_smem, g_cluster_ok ? 1 : 0); note_launch(); }
+                 ZONE_MID, gs, fast_smem, g_cluster_ok ? 1 : 0); note_launch(); }
     if (g_cluster_ok) {
         int ncl = (cap + ZONE_CL_MIN - 1) / ZONE_CL_MIN;
         if (ncl > 152 / CL) ncl = 152 / CL;
