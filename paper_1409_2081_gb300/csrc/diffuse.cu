@@ -752,20 +752,31 @@ __global__ void __launch_bounds__(BAND_TPB) k_band_cg(BandArgs a, int limit) {
 // Each neighbour slot of cnbr holds -2 - (local index) for a neighbour of
 // the same CTA (read from shared memory), the band index for one of
 // another CTA, -1 for a Dirichlet neighbour.  Other CTAs' values are read
-// from global copies (r as float4 in rec, u in u64) that every vertex
+// from global copies (z as float4 in rec, u in u64) that every vertex
 // writes beside its record, through L2: random reads of other SMs' shared
 // memory serialise on the SM-to-SM network, L2 serves them in parallel.
-// An iteration has two cluster barriers (the neighbours' r, then
-// the sums); every CTA stores its sums into every CTA's receive slots
-// before the second, and each folds them in rank order after it, so every
-// CTA takes the same decisions from the same values.  Hardware cluster
+// The preconditioner is local to each CTA: z_v = (r_v + theta sum r_u /
+// deg_u) / deg_v over v's band neighbours u in the same CTA, that is
+// D^-1 (I + theta N D^-1) with N the adjacency inside the CTAs' blocks: one
+// Jacobi sweep on each CTA's block after the first, symmetric, and
+// positive definite for theta < 1 (the eigenvalues of D^-1/2 N D^-1/2 lie
+// in [-1, 1] since deg counts every neighbour).  It needs only this CTA's
+// r, so it costs a CTA barrier, not a cluster barrier, and takes about a
+// quarter fewer iterations than Jacobi on the bands of a frame sequence.
+// An iteration has two cluster barriers (the neighbours' z, then the
+// sums); every CTA stores its sums into every CTA's receive slots before
+// the second, and each folds them in rank order after it, so every CTA
+// takes the same decisions from the same values.  Hardware cluster
 // barriers: nothing here spins.
 namespace cgx = cooperative_groups;
 
 constexpr int BCL_THREADS = 1024;
 constexpr int BCL_MAX = 16;                  // CTAs per cluster at most
-constexpr int BCL_SMEM = 200 * 1024;         // dynamic shared memory per CTA
-constexpr int BCL_VBYTES = 48 + 4 * 16 + 8;  // record, p s x w (float4), slot range
+constexpr int BCL_SMEM = 220 * 1024;  // dynamic shared memory per CTA
+constexpr int BCL_NB = 8;             // neighbour codes kept in shared memory per vertex
+// record, p s x w z (float4), the neighbour codes, slot range
+constexpr int BCL_VBYTES = 48 + 5 * 16 + 4 * BCL_NB + 8;
+constexpr float BCL_THETA = 0.9f;            // weight of the preconditioner's local sweep
 
 struct __align__(16) BclRec {
     float4 r;     // r (x, y, z) and 1 / deg
@@ -840,7 +851,19 @@ __device__ __forceinline__ void bcl_sums(cgx::cluster_group &cl, const T (&v)[K]
     __syncthreads();
 }
 
-constexpr int BCL_GATHER = 8;  // neighbour values in flight per vertex
+// the codes of neighbours base .. base + BCL_NB - 1 of a vertex (-1 past its
+// degree): from shared memory when they all fit there, else from cnbr
+__device__ __forceinline__ void bcl_codes(const int4 *cq, const int *cnbr, int li, int2 e, int base,
+                                          int (&cd)[BCL_NB]) {
+    if (e.y <= BCL_NB) {
+        const int4 c0 = cq[2 * li], c1 = cq[2 * li + 1];
+        cd[0] = c0.x; cd[1] = c0.y; cd[2] = c0.z; cd[3] = c0.w;
+        cd[4] = c1.x; cd[5] = c1.y; cd[6] = c1.z; cd[7] = c1.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < BCL_NB; ++k) cd[k] = base + k < e.y ? cnbr[e.x + base + k] : -1;
+    }
+}
 
 __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limit, int vcap) {
     HFCR_PDL_WAIT();
@@ -854,10 +877,12 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
     const int lo = rank * chunk;
     const int cnt = n - lo < chunk ? (n - lo > 0 ? n - lo : 0) : chunk;
     BclRec *rec = (BclRec *)bsm;
-    float4 *gr = (float4 *)a.rec;  // r of every band vertex, for the other CTAs
+    float4 *gz = (float4 *)a.rec;  // z of every band vertex, for the other CTAs
     double *gu = a.u64;            // u of every band vertex
     float4 *pq = (float4 *)(rec + vcap), *sq = pq + vcap, *xq = sq + vcap, *wq = xq + vcap;
-    int2 *ed = (int2 *)(wq + vcap);
+    float4 *zq = wq + vcap;
+    int4 *cq = (int4 *)(zq + vcap);  // two int4 (BCL_NB codes) per vertex
+    int2 *ed = (int2 *)(cq + 2 * (size_t)vcap);
     if ((int)threadIdx.x < ncta) {
         st.recv_of[threadIdx.x] = cl.map_shared_rank(&st.recv[0][0][0], threadIdx.x);
         st.recvd_of[threadIdx.x] = cl.map_shared_rank(&st.recvd[0][0][0], threadIdx.x);
@@ -875,6 +900,9 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
         const int e0 = M.ptr[v], e1 = M.ptr[v + 1];
         const int s0 = (inB ? a.eoffB : 0) + e0;
         double b[3] = {0.0, 0.0, 0.0};
+        int cs[BCL_NB];
+#pragma unroll
+        for (int k = 0; k < BCL_NB; ++k) cs[k] = -1;
         for (int e = e0; e < e1; ++e) {
             const int w = M.off + M.nbr[e];
             const int j = a.cidx[w];
@@ -888,12 +916,16 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
                 b[2] += uw[2];
             }
             a.cnbr[s0 + e - e0] = code;
+#pragma unroll
+            for (int k = 0; k < BCL_NB; ++k)
+                if (e - e0 == k) cs[k] = code;
         }
+        cq[2 * li] = make_int4(cs[0], cs[1], cs[2], cs[3]);
+        cq[2 * li + 1] = make_int4(cs[4], cs[5], cs[6], cs[7]);
         // a band vertex has a neighbour one ring closer, so e1 > e0
         ed[li] = make_int2(s0, e1 - e0);
         BclRec &R = rec[li];
         R.r = make_float4((float)b[0], (float)b[1], (float)b[2], 1.0f / (float)(e1 - e0));
-        gr[i] = R.r;
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         pq[li] = z4;
         sq[li] = z4;
@@ -925,35 +957,59 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
         const int it_round = it;
         bool first = true;
         while (true) {
-            cl.sync();  // every band vertex's r visible
-            // w = L z (deg_v z_v = r_v), and the sums (r, z), (w, z), |r|^2
+            __syncthreads();  // this CTA's r visible
+            // z = M^-1 r from this CTA's r
+            for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
+                const float4 me = rec[li].r;
+                const int2 e = ed[li];
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+                for (int base = 0; base < e.y; base += BCL_NB) {
+                    int cd[BCL_NB];
+                    bcl_codes(cq, a.cnbr, li, e, base, cd);
+                    float4 nb[BCL_NB];
+#pragma unroll
+                    for (int k = 0; k < BCL_NB; ++k)
+                        nb[k] = cd[k] <= -2 ? rec[-2 - cd[k]].r : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < BCL_NB; ++k) {
+                        s0 += nb[k].x * nb[k].w;
+                        s1 += nb[k].y * nb[k].w;
+                        s2 += nb[k].z * nb[k].w;
+                    }
+                }
+                const float4 z4 = make_float4((me.x + BCL_THETA * s0) * me.w, (me.y + BCL_THETA * s1) * me.w,
+                                              (me.z + BCL_THETA * s2) * me.w, 0.f);
+                zq[li] = z4;
+                gz[lo + li] = z4;
+            }
+            cl.sync();  // every band vertex's z visible
+            // w = L z, and the sums (r, z), (w, z), |r|^2
             float fl[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) fl[k] = 0.f;
             for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
-                const float4 me = rec[li].r;
+                const float4 me = rec[li].r, zm = zq[li];
                 const int2 e = ed[li];
-                float w0 = me.x, w1 = me.y, w2 = me.z;
-                for (int base = 0; base < e.y; base += BCL_GATHER) {
-                    int cd[BCL_GATHER];
+                const float dg = (float)e.y;
+                float w0 = dg * zm.x, w1 = dg * zm.y, w2 = dg * zm.z;
+                for (int base = 0; base < e.y; base += BCL_NB) {
+                    int cd[BCL_NB];
+                    bcl_codes(cq, a.cnbr, li, e, base, cd);
+                    float4 nb[BCL_NB];
 #pragma unroll
-                    for (int k = 0; k < BCL_GATHER; ++k) cd[k] = base + k < e.y ? a.cnbr[e.x + base + k] : -1;
-                    float4 nb[BCL_GATHER];
+                    for (int k = 0; k < BCL_NB; ++k)
+                        nb[k] = cd[k] >= 0 ? __ldcg(gz + cd[k])
+                                           : (cd[k] <= -2 ? zq[-2 - cd[k]] : make_float4(0.f, 0.f, 0.f, 0.f));
 #pragma unroll
-                    for (int k = 0; k < BCL_GATHER; ++k)
-                        nb[k] = cd[k] >= 0 ? __ldcg(gr + cd[k])
-                                           : (cd[k] <= -2 ? rec[-2 - cd[k]].r : make_float4(0.f, 0.f, 0.f, 0.f));
-#pragma unroll
-                    for (int k = 0; k < BCL_GATHER; ++k) {
-                        w0 -= nb[k].x * nb[k].w;
-                        w1 -= nb[k].y * nb[k].w;
-                        w2 -= nb[k].z * nb[k].w;
+                    for (int k = 0; k < BCL_NB; ++k) {
+                        w0 -= nb[k].x;
+                        w1 -= nb[k].y;
+                        w2 -= nb[k].z;
                     }
                 }
                 wq[li] = make_float4(w0, w1, w2, 0.f);
-                const float z0 = me.x * me.w, z1 = me.y * me.w, z2 = me.z * me.w;
-                fl[0] += me.x * z0; fl[1] += me.y * z1; fl[2] += me.z * z2;
-                fl[3] += w0 * z0;   fl[4] += w1 * z1;   fl[5] += w2 * z2;
+                fl[0] += me.x * zm.x; fl[1] += me.y * zm.y; fl[2] += me.z * zm.z;
+                fl[3] += w0 * zm.x;   fl[4] += w1 * zm.y;   fl[5] += w2 * zm.z;
                 fl[6] += me.x * me.x; fl[7] += me.y * me.y; fl[8] += me.z * me.z;
             }
             bcl_sums<float, 9>(cl, fl, st.scr, &st.recv[0][0][0], st.recv_of, pf, rank, ncta, st.sums);
@@ -989,19 +1045,18 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
             // p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s
             for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
                 float4 r4 = rec[li].r, p4 = pq[li], s4 = sq[li], x4 = xq[li];
-                const float4 w4 = wq[li];
+                const float4 w4 = wq[li], z4 = zq[li];
                 float *r = &r4.x, *p = &p4.x, *sv = &s4.x, *x = &x4.x;
-                const float *w = &w4.x;
+                const float *w = &w4.x, *zz = &z4.x;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (!in[c]) continue;
-                    p[c] = r[c] * r4.w + bet[c] * p[c];
+                    p[c] = zz[c] + bet[c] * p[c];
                     sv[c] = w[c] + bet[c] * sv[c];
                     x[c] += alp[c] * p[c];
                     r[c] -= alp[c] * sv[c];
                 }
                 rec[li].r = r4;
-                gr[lo + li] = r4;
                 pq[li] = p4;
                 sq[li] = s4;
                 xq[li] = x4;
@@ -1042,7 +1097,6 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
             }
             R.r = make_float4(act[0] ? (float)r64[0] : 0.f, act[1] ? (float)r64[1] : 0.f,
                               act[2] ? (float)r64[2] : 0.f, R.r.w);
-            gr[i] = R.r;
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
             pq[li] = z4;
             sq[li] = z4;
