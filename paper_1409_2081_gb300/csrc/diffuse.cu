@@ -746,9 +746,10 @@ __global__ void __launch_bounds__(BAND_TPB) k_band_cg(BandArgs a, int limit) {
 // vertices (the bands of a frame sequence are a few thousand to a few tens
 // of thousands of vertices: one grid-wide barrier per iteration over every
 // SM costs more than the iteration's work).  Band vertex i belongs to CTA
-// i / chunk and keeps its CG state in that CTA's shared memory: a 48-byte
-// record (r with 1/deg, and the float64 u of the rounds' residuals: the
-// part other CTAs read, a neighbour's z being r / deg), and p, s, x, w.
+// i / chunk and keeps its CG state in that CTA's shared memory, one array
+// per field so that a warp's own-vertex accesses are conflict-free: r with
+// 1/deg, p, s, x, w, z (float4), its neighbour codes, the float64 u of the
+// rounds.
 // Each neighbour slot of cnbr holds -2 - (local index) for a neighbour of
 // the same CTA (read from shared memory), the band index for one of
 // another CTA, -1 for a Dirichlet neighbour.  Other CTAs' values are read
@@ -774,21 +775,22 @@ constexpr int BCL_THREADS = 1024;
 constexpr int BCL_MAX = 16;                  // CTAs per cluster at most
 constexpr int BCL_SMEM = 220 * 1024;  // dynamic shared memory per CTA
 constexpr int BCL_NB = 8;             // neighbour codes kept in shared memory per vertex
-// record, p s x w z (float4), the neighbour codes, slot range
-constexpr int BCL_VBYTES = 48 + 5 * 16 + 4 * BCL_NB + 8;
+// r p s x w z (float4), the neighbour codes, the float64 u, slot range
+constexpr int BCL_VBYTES = 6 * 16 + 4 * BCL_NB + 24 + 8;
+constexpr int BCL_VCAP = BCL_SMEM / BCL_VBYTES;  // band vertices per CTA (1,408)
 constexpr float BCL_THETA = 0.9f;            // weight of the preconditioner's local sweep
 
-struct __align__(16) BclRec {
-    float4 r;     // r (x, y, z) and 1 / deg
-    double u[3];  // the float64 solution of the rounds
-    double pad;
-};
 
 struct BclState {
     float recv[2][BCL_MAX][9];    // the CTAs' float sums, by parity and sender
     double recvd[2][BCL_MAX][3];  // their float64 sums
     float sums[9];
     double sumsd[3];
+    // the CG scalars per coordinate (the same for every thread: kept here,
+    // set by thread 0, rather than in every thread's registers)
+    float gam[3], alp[3], bet[3], stop[3];
+    double target[3];
+    int in;  // coordinates whose float32 run goes on (bit c)
     float scr[32 * 9];
     double scrd[32 * 3];
     float *recv_of[BCL_MAX];
@@ -815,7 +817,7 @@ __device__ __forceinline__ void warp_sums(T (&t)[K]) {
 // received sums in rank order (lane q holds CTA q's).  A parity's slots are
 // rewritten two calls later, after every CTA has passed the barrier that
 // follows its reads.
-template <typename T, int K>
+template <typename T, int K, bool SYNC_END = true>
 __device__ __forceinline__ void bcl_sums(cgx::cluster_group &cl, const T (&v)[K], T *scr, T *recv,
                                          T *const *recv_of, int par, int rank, int ncta, T *out) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -848,7 +850,7 @@ __device__ __forceinline__ void bcl_sums(cgx::cluster_group &cl, const T (&v)[K]
             for (int k = 0; k < K; ++k) out[k] = t[k];
         }
     }
-    __syncthreads();
+    if (SYNC_END) __syncthreads();  // otherwise out[] is thread 0's until the caller's barrier
 }
 
 // the codes of neighbours base .. base + BCL_NB - 1 of a vertex (-1 past its
@@ -865,7 +867,8 @@ __device__ __forceinline__ void bcl_codes(const int4 *cq, const int *cnbr, int l
     }
 }
 
-__global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limit, int vcap) {
+__global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limit) {
+    constexpr int vcap = BCL_VCAP;
     HFCR_PDL_WAIT();
     cgx::cluster_group cl = cgx::this_cluster();
     const int n = *a.d_nfree;
@@ -876,13 +879,14 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
     const int chunk = n > 0 ? (n + ncta - 1) / ncta : 1;
     const int lo = rank * chunk;
     const int cnt = n - lo < chunk ? (n - lo > 0 ? n - lo : 0) : chunk;
-    BclRec *rec = (BclRec *)bsm;
+    float4 *rq = bsm;  // r (x, y, z) and 1 / deg
     float4 *gz = (float4 *)a.rec;  // z of every band vertex, for the other CTAs
     double *gu = a.u64;            // u of every band vertex
-    float4 *pq = (float4 *)(rec + vcap), *sq = pq + vcap, *xq = sq + vcap, *wq = xq + vcap;
+    float4 *pq = rq + vcap, *sq = pq + vcap, *xq = sq + vcap, *wq = xq + vcap;
     float4 *zq = wq + vcap;
     int4 *cq = (int4 *)(zq + vcap);  // two int4 (BCL_NB codes) per vertex
-    int2 *ed = (int2 *)(cq + 2 * (size_t)vcap);
+    double *uq = (double *)(cq + 2 * (size_t)vcap);  // u (x, y, z) of the rounds
+    int2 *ed = (int2 *)(uq + 3 * (size_t)vcap);
     if ((int)threadIdx.x < ncta) {
         st.recv_of[threadIdx.x] = cl.map_shared_rank(&st.recv[0][0][0], threadIdx.x);
         st.recvd_of[threadIdx.x] = cl.map_shared_rank(&st.recvd[0][0][0], threadIdx.x);
@@ -924,8 +928,7 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
         cq[2 * li + 1] = make_int4(cs[4], cs[5], cs[6], cs[7]);
         // a band vertex has a neighbour one ring closer, so e1 > e0
         ed[li] = make_int2(s0, e1 - e0);
-        BclRec &R = rec[li];
-        R.r = make_float4((float)b[0], (float)b[1], (float)b[2], 1.0f / (float)(e1 - e0));
+        rq[li] = make_float4((float)b[0], (float)b[1], (float)b[2], 1.0f / (float)(e1 - e0));
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         pq[li] = z4;
         sq[li] = z4;
@@ -933,7 +936,7 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             a.b64[3 * (size_t)i + c] = b[c];
-            R.u[c] = 0.0;
+            uq[3 * li + c] = 0.0;
             gu[3 * (size_t)i + c] = 0.0;
             dl[c] += b[c] * b[c];
         }
@@ -941,26 +944,25 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
     int pf = 0, pd = 0;  // parities of the float and float64 receive slots
     bcl_sums<double, 3>(cl, dl, st.scrd, &st.recvd[0][0][0], st.recvd_of, pd, rank, ncta, st.sumsd);
     pd ^= 1;
-    double target[3];
-    bool act[3];
+    int act = 0;  // coordinates not yet converged (bit c), the same in every thread
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        target[c] = a.tol * a.tol * st.sumsd[c];
-        act[c] = st.sumsd[c] > 0.0;
+    for (int c = 0; c < 3; ++c)
+        if (st.sumsd[c] > 0.0) act |= 1 << c;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st.target[c] = a.tol * a.tol * st.sumsd[c];
     }
     int it = 0, rounds = 0;
     bool fail = false;
-    while (act[0] || act[1] || act[2]) {
+    while (act) {
         if (++rounds > BAND_MAX_ROUNDS) { fail = true; break; }
-        float gam[3], alp[3], bet[3], stop[3];
-        bool in[3];
         const int it_round = it;
         bool first = true;
         while (true) {
             __syncthreads();  // this CTA's r visible
             // z = M^-1 r from this CTA's r
             for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
-                const float4 me = rec[li].r;
+                const float4 me = rq[li];
                 const int2 e = ed[li];
                 float s0 = 0.f, s1 = 0.f, s2 = 0.f;
                 for (int base = 0; base < e.y; base += BCL_NB) {
@@ -969,7 +971,7 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
                     float4 nb[BCL_NB];
 #pragma unroll
                     for (int k = 0; k < BCL_NB; ++k)
-                        nb[k] = cd[k] <= -2 ? rec[-2 - cd[k]].r : make_float4(0.f, 0.f, 0.f, 0.f);
+                        nb[k] = cd[k] <= -2 ? rq[-2 - cd[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                     for (int k = 0; k < BCL_NB; ++k) {
                         s0 += nb[k].x * nb[k].w;
@@ -988,23 +990,27 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
 #pragma unroll
             for (int k = 0; k < 9; ++k) fl[k] = 0.f;
             for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
-                const float4 me = rec[li].r, zm = zq[li];
+                const float4 me = rq[li], zm = zq[li];
                 const int2 e = ed[li];
                 const float dg = (float)e.y;
                 float w0 = dg * zm.x, w1 = dg * zm.y, w2 = dg * zm.z;
                 for (int base = 0; base < e.y; base += BCL_NB) {
                     int cd[BCL_NB];
                     bcl_codes(cq, a.cnbr, li, e, base, cd);
-                    float4 nb[BCL_NB];
 #pragma unroll
-                    for (int k = 0; k < BCL_NB; ++k)
-                        nb[k] = cd[k] >= 0 ? __ldcg(gz + cd[k])
-                                           : (cd[k] <= -2 ? zq[-2 - cd[k]] : make_float4(0.f, 0.f, 0.f, 0.f));
+                    for (int h = 0; h < BCL_NB; h += 4) {
+                        float4 nb[4];
 #pragma unroll
-                    for (int k = 0; k < BCL_NB; ++k) {
-                        w0 -= nb[k].x;
-                        w1 -= nb[k].y;
-                        w2 -= nb[k].z;
+                        for (int k = 0; k < 4; ++k)
+                            nb[k] = cd[h + k] >= 0 ? __ldcg(gz + cd[h + k])
+                                                   : (cd[h + k] <= -2 ? zq[-2 - cd[h + k]]
+                                                                      : make_float4(0.f, 0.f, 0.f, 0.f));
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            w0 -= nb[k].x;
+                            w1 -= nb[k].y;
+                            w2 -= nb[k].z;
+                        }
                     }
                 }
                 wq[li] = make_float4(w0, w1, w2, 0.f);
@@ -1012,51 +1018,55 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
                 fl[3] += w0 * zm.x;   fl[4] += w1 * zm.y;   fl[5] += w2 * zm.z;
                 fl[6] += me.x * me.x; fl[7] += me.y * me.y; fl[8] += me.z * me.z;
             }
-            bcl_sums<float, 9>(cl, fl, st.scr, &st.recv[0][0][0], st.recv_of, pf, rank, ncta, st.sums);
+            bcl_sums<float, 9, false>(cl, fl, st.scr, &st.recv[0][0][0], st.recv_of, pf, rank, ncta,
+                                      st.sums);
             pf ^= 1;
-            float fs[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) fs[k] = st.sums[k];
-            if (first) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    gam[c] = fs[c];
-                    alp[c] = __fdividef(fs[c], fs[3 + c]);
-                    bet[c] = 0.f;
-                    stop[c] = BAND_INNER_TOL * BAND_INNER_TOL * fs[6 + c];
-                    in[c] = act[c] && fs[6 + c] > 0.f && alp[c] > 0.f && isfinite(alp[c]);
-                }
-                first = false;
-            } else {
+            if (threadIdx.x == 0) {  // the scalars, from the sums thread 0 has just folded
+                const float *fs = st.sums;
+                int in = 0;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float b = __fdividef(fs[c], gam[c]);
-                    const float al = __fdividef(fs[c], fs[3 + c] - b * __fdividef(fs[c], alp[c]));
-                    const bool go = in[c] && fs[6 + c] > stop[c] && al > 0.f && isfinite(al);
-                    if (go) {
-                        bet[c] = b;
-                        alp[c] = al;
-                        gam[c] = fs[c];
+                    if (first) {
+                        const float al = __fdividef(fs[c], fs[3 + c]);
+                        st.gam[c] = fs[c];
+                        st.alp[c] = al;
+                        st.bet[c] = 0.f;
+                        st.stop[c] = BAND_INNER_TOL * BAND_INNER_TOL * fs[6 + c];
+                        if ((act >> c & 1) && fs[6 + c] > 0.f && al > 0.f && isfinite(al)) in |= 1 << c;
+                    } else {
+                        const float b = __fdividef(fs[c], st.gam[c]);
+                        const float al = __fdividef(fs[c], fs[3 + c] - b * __fdividef(fs[c], st.alp[c]));
+                        if ((st.in >> c & 1) && fs[6 + c] > st.stop[c] && al > 0.f && isfinite(al)) {
+                            st.bet[c] = b;
+                            st.alp[c] = al;
+                            st.gam[c] = fs[c];
+                            in |= 1 << c;
+                        }
                     }
-                    in[c] = go;
                 }
+                st.in = in;
             }
-            if (!(in[0] || in[1] || in[2]) || it >= a.max_iters) break;
+            __syncthreads();
+            first = false;
+            const int in = st.in;
+            if (!in || it >= a.max_iters) break;
             // p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s
+            const float al[3] = {st.alp[0], st.alp[1], st.alp[2]};
+            const float be[3] = {st.bet[0], st.bet[1], st.bet[2]};
             for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
-                float4 r4 = rec[li].r, p4 = pq[li], s4 = sq[li], x4 = xq[li];
+                float4 r4 = rq[li], p4 = pq[li], s4 = sq[li], x4 = xq[li];
                 const float4 w4 = wq[li], z4 = zq[li];
                 float *r = &r4.x, *p = &p4.x, *sv = &s4.x, *x = &x4.x;
                 const float *w = &w4.x, *zz = &z4.x;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    if (!in[c]) continue;
-                    p[c] = zz[c] + bet[c] * p[c];
-                    sv[c] = w[c] + bet[c] * sv[c];
-                    x[c] += alp[c] * p[c];
-                    r[c] -= alp[c] * sv[c];
+                    if (!(in >> c & 1)) continue;
+                    p[c] = zz[c] + be[c] * p[c];
+                    sv[c] = w[c] + be[c] * sv[c];
+                    x[c] += al[c] * p[c];
+                    r[c] -= al[c] * sv[c];
                 }
-                rec[li].r = r4;
+                rq[li] = r4;
                 pq[li] = p4;
                 sq[li] = s4;
                 xq[li] = x4;
@@ -1067,12 +1077,12 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
         // the neighbours' u; the next round starts from it (x = p = s = 0)
         for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
             const float4 x4 = xq[li];
-            BclRec &R = rec[li];
-            R.u[0] += (double)x4.x;
-            R.u[1] += (double)x4.y;
-            R.u[2] += (double)x4.z;
+            double *u = uq + 3 * li;
+            u[0] += (double)x4.x;
+            u[1] += (double)x4.y;
+            u[2] += (double)x4.z;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) gu[3 * (size_t)(lo + li) + c] = R.u[c];
+            for (int c = 0; c < 3; ++c) gu[3 * (size_t)(lo + li) + c] = u[c];
         }
         cl.sync();  // every band vertex's u visible
 #pragma unroll
@@ -1080,10 +1090,10 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
         for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
             const int i = lo + li;
             const int2 e = ed[li];
-            BclRec &R = rec[li];
+            const double *u = uq + 3 * li;
             double r64[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) r64[c] = a.b64[3 * (size_t)i + c] - (double)e.y * R.u[c];
+            for (int c = 0; c < 3; ++c) r64[c] = a.b64[3 * (size_t)i + c] - (double)e.y * u[c];
             for (int k = 0; k < e.y; ++k) {
                 const int cd = a.cnbr[e.x + k];
                 if (cd == -1) continue;
@@ -1092,11 +1102,11 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
                     for (int c = 0; c < 3; ++c) r64[c] += __ldcg(gu + 3 * (size_t)cd + c);
                 } else {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) r64[c] += rec[-2 - cd].u[c];
+                    for (int c = 0; c < 3; ++c) r64[c] += uq[3 * (-2 - cd) + c];
                 }
             }
-            R.r = make_float4(act[0] ? (float)r64[0] : 0.f, act[1] ? (float)r64[1] : 0.f,
-                              act[2] ? (float)r64[2] : 0.f, R.r.w);
+            rq[li] = make_float4((act & 1) ? (float)r64[0] : 0.f, (act & 2) ? (float)r64[1] : 0.f,
+                                 (act & 4) ? (float)r64[2] : 0.f, rq[li].w);
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
             pq[li] = z4;
             sq[li] = z4;
@@ -1106,19 +1116,15 @@ __global__ void __launch_bounds__(BCL_THREADS, 1) k_band_cl(BandArgs a, int limi
         }
         bcl_sums<double, 3>(cl, dl, st.scrd, &st.recvd[0][0][0], st.recvd_of, pd, rank, ncta, st.sumsd);
         pd ^= 1;
-        bool progress = false;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (!act[c]) continue;
-            if (st.sumsd[c] <= target[c]) { act[c] = false; continue; }
-            progress = true;
-        }
-        if (progress && (it >= a.max_iters || it == it_round)) { fail = true; break; }
+        for (int c = 0; c < 3; ++c)
+            if ((act >> c & 1) && st.sumsd[c] <= st.target[c]) act &= ~(1 << c);
+        if (act && (it >= a.max_iters || it == it_round)) { fail = true; break; }
     }
     for (int li = threadIdx.x; li < cnt; li += BCL_THREADS) {
         double *ug = a.u + 3 * (size_t)a.fv[lo + li];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ug[c] = rec[li].u[c];
+        for (int c = 0; c < 3; ++c) ug[c] = uq[3 * li + c];
     }
     if (rank == 0 && threadIdx.x == 0) {
         a.ctl[0] += it;
@@ -1212,7 +1218,7 @@ static BclConfig band_cl_config() {
             }
         }
         cudaGetLastError();
-        c.vcap = BCL_SMEM / BCL_VBYTES;
+        c.vcap = BCL_VCAP;
         cached[dev] = c;
         done[dev] = true;
     }
@@ -1320,7 +1326,7 @@ const double *diffuse_field(const DiffMeshArgs &a, const DiffMeshArgs &b, double
         at[1].val.programmaticStreamSerializationAllowed = 1;
         lc.attrs = at;
         lc.numAttrs = 2;
-        if (cudaLaunchKernelEx(&lc, k_band_cl, ba, limit, bc.vcap) == cudaSuccess) {
+        if (cudaLaunchKernelEx(&lc, k_band_cl, ba, limit) == cudaSuccess) {
             note_launch();
         } else {
             cudaGetLastError();
