@@ -1662,23 +1662,33 @@ __device__ __forceinline__ int next_zone(unsigned *counter, int stride, int *slo
 }
 
 // The zones of at least ZONE_MID stencils go to the large-zone launch, one
-// CTA each, when there are no more of them than its CTAs: a frame's few
-// large contact zones then run side by side instead of one launch after
-// the other, and each may switch to its blocks.  Otherwise the pair launch
-// takes those below ZONE_BIG as before.  Both launches count them from the
-// zone starts (one barrier per blockDim.x zones), so they take the same
-// decision.  Returns how many zones have at least lo stencils; *pick: the
-// one of rank `rank` among them in zone order, -1 if none (identical in
-// every thread of the CTA).
-__device__ __forceinline__ int zones_at_least(const int *zs, int nz, int lo, int rank, int *pick) {
+// CTA each, when at least one of them has ZONE_BIG stencils or more and
+// there are at most ROUTE_MAX of them (and no more than its CTAs): a
+// frame's large contact zone and the few medium ones beside it then run
+// side by side instead of one launch after the other, and each may switch
+// to its blocks.  Otherwise the pair launch takes those below ZONE_BIG:
+// alone, a medium zone is faster there (measured: a 538-row zone of the
+// two-tori scene, 0.26 against 0.37 ms; the large-zone CTA's shared memory
+// leaves little L1 for the float64 rounds), and many of them (a batch)
+// share its two CTAs per SM.  Both launches count the zones from the zone
+// starts (one barrier per blockDim.x zones), so they take the same
+// decision.  Returns how many zones have at least lo stencils, *n_big how
+// many at least ZONE_BIG; *pick: the zone of rank `rank` among the first
+// ones in zone order, -1 if none (all identical in every thread of the CTA).
+constexpr int ROUTE_MAX = 8;
+
+__device__ __forceinline__ int zones_at_least(const int *zs, int nz, int lo, int rank, int *pick,
+                                              int *n_big) {
     __shared__ int wc[32];
     __shared__ int found;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) found = -1;
-    int total = 0;
+    int total = 0, big = 0;
     for (int base = 0; base < nz; base += blockDim.x) {
         const int z = base + threadIdx.x;
-        const bool pred = z < nz && zs[z + 1] - zs[z] >= lo;
+        const int kz = z < nz ? zs[z + 1] - zs[z] : 0;
+        const bool pred = kz >= lo;
+        big += __syncthreads_count(kz >= ZONE_BIG);
         const int c = __syncthreads_count(pred);
         if (rank >= total && rank < total + c) {  // the same in every thread
             const unsigned bal = __ballot_sync(0xffffffffu, pred);
@@ -1692,6 +1702,7 @@ __device__ __forceinline__ int zones_at_least(const int *zs, int nz, int lo, int
     }
     __syncthreads();
     *pick = found;
+    *n_big = big;
     return total;
 }
 
@@ -1722,8 +1733,9 @@ __global__ void __launch_bounds__(512, 2) k_cg_zone_pair(const int *d_nz, ZoneAr
     // launch takes them)
     __shared__ int first;
     {
-        int unused;
-        const bool to_big = zones_at_least(a.zs, nz, ZONE_MID, -1, &unused) <= big_ctas;
+        int unused, n_big;
+        const int n_mid = zones_at_least(a.zs, nz, ZONE_MID, -1, &unused, &n_big);
+        const bool to_big = n_big > 0 && n_mid <= ROUTE_MAX && n_mid <= big_ctas;
         if (threadIdx.x == 0) first = to_big ? nz : (int)blockIdx.x;
         __syncthreads();
     }
@@ -1743,9 +1755,9 @@ __global__ void __launch_bounds__(512, 2) k_cg_zone_pair(const int *d_nz, ZoneAr
                       g, slot + 1);
 }
 
-// The zones of more than k_lo stencils, one CTA each; or, when there are
-// no more zones of at least mid_lo stencils than CTAs (zones_at_least),
-// the zone of rank blockIdx.x among those.  leave_big: zones that do not
+// The zones of more than k_lo stencils, one CTA each; or, when the zones
+// of at least mid_lo stencils come to this launch (zones_at_least), the
+// zone of rank blockIdx.x among those.  leave_big: zones that do not
 // fit smem_bytes are left to the cluster solver (k_cg_zone_cl) instead of
 // the global-memory path.
 template <int THREADS>
@@ -1760,8 +1772,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_cg_zone(const int *d_nz, ZoneArg
     // the loop's first zone, its stride, and the zones' smallest size minus one
     __shared__ int sel[3];
     {
-        int pick;
-        const bool ranked = zones_at_least(a.zs, nz, mid_lo, blockIdx.x, &pick) <= (int)gridDim.x;
+        int pick, n_big;
+        const int n_mid = zones_at_least(a.zs, nz, mid_lo, blockIdx.x, &pick, &n_big);
+        const bool ranked = n_big > 0 && n_mid <= ROUTE_MAX && n_mid <= (int)gridDim.x;
         if (threadIdx.x == 0) {
             sel[0] = ranked ? (pick >= 0 ? pick : nz) : (int)blockIdx.x;
             sel[1] = ranked ? nz : (int)gridDim.x;
