@@ -979,10 +979,10 @@ def main():
     alg_band = int(nb_mean * (60 + 4 * deg))
     band_iters = statistics.mean(int(i.diffuse_cg_iters) for i in infos)
     ach_band = alg_band / (band_ms * 1e-3) / 1e9
-    # the solver launches of the large impact zones (1,024 rows or more; the
-    # frame's one big contact zone): per row 116 B (ids, float32 and float64
-    # normals, block-Jacobi row, b, lambda written, four CSR entries, group
-    # start), per touched vertex 8 B
+    # the solver launches of the large impact zones (1,024 rows or more: the
+    # frame's big contact zone, and the few medium zones beside it): per row
+    # 116 B (ids, float32 and float64 normals, block-Jacobi row, b, lambda
+    # written, four CSR entries, group start), per touched vertex 8 B
     zb_ms = prof["zone_big"][0] / max(1, prof["zone_big"][1])
     zb_rows = statistics.mean(int(i.big_zone_rows) for i in infos)
     zb_verts = statistics.mean(int(i.big_zone_vertices) for i in infos)
@@ -1004,8 +1004,9 @@ def main():
                       "band_vertices_mean": round(nb_mean, 1), "cg_iters_mean": round(band_iters, 2),
                       "us_per_cg_iter": round(1e3 * band_ms / band_iters, 3) if band_iters else None},
         "k_cg_zone_big": {"kernel": "k_cg_zone<512> (+ k_cg_zone_cl): float32 PCG with float64 "
-                                    "refinement of the impact zones of 1,024 rows or more, one CTA "
-                                    "(or cluster) per zone", "bound": "hbm",
+                                    "refinement of the impact zones of 1,024 rows or more (and of at "
+                                    "most eight medium zones beside them), one CTA (or cluster) "
+                                    "per zone", "bound": "hbm",
                           "achieved": round(ach_zb, 3), "peak": peak, "peak_kind": peak_kind,
                           "unit": "GB/s", "frac": round(ach_zb / peak, 7),
                           "traffic": profiled_traffic("k_cg_zone_big"), "alg_bytes_per_launch": alg_zb,
