@@ -779,7 +779,7 @@ def run_reference(args, ws, rank):
     ms = statistics.mean(times)
     bf = len(E) * sc.B.n_tris
     step = max(1, int(round(1.0 / frac)))
-    which = "every" if step == 1 else f"one in {step} of the"
+    which = "all" if step == 1 else f"one in {step} of the"
     sample = (f"frame 0 of the 512x512 cloth / level-7 body sequence (before the first contact): "
               f"brute-force exact detection of {which} cloth edges against all 327,680 body "
               f"faces per step, scaled to all 784,385 edges")
