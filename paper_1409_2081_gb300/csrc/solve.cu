@@ -1893,13 +1893,17 @@ __device__ __forceinline__ void zone64_precond(const ZoneArgs &a, int s0, int g0
     }
 }
 
+// rescue: only the zones whose recorded |r|^2 (the mixed solver's) misses
+// the target, solved again from lam = 0 (zones on which the float32 runs
+// stopped reducing the float64 residual)
 __global__ void __launch_bounds__(ZONE64_THREADS) k_cg_zone64(const int *d_nz, ZoneArgs a,
-                                                              Zone64Scratch g, int maxit) {
+                                                              Zone64Scratch g, int maxit, int rescue) {
     HFCR_PDL_WAIT();
     __shared__ double red[3 * (ZONE64_THREADS / 32)];
     __shared__ double redd[ZONE64_THREADS / 32];
     const int nz = *d_nz;
     for (int z = blockIdx.x; z < nz; z += gridDim.x) {
+        if (rescue && a.zres[z] <= a.rel_tol * a.rel_tol * a.zbb[z]) continue;
         const int s0 = a.zs[z], k = a.zs[z + 1] - s0;
         const int j0 = a.zv[z], U = a.zv[z + 1] - j0;
         const int g0 = a.zg[z], G = a.zg[z + 1] - g0;
@@ -3190,7 +3194,7 @@ void solve(const SolveParams &p, const MeshPair &mp, const int *d_k, int cap, So
         g64.w = sb.cg64 + 3 * (size_t)cap; g64.z = sb.cg64 + 4 * (size_t)cap;
         int zg = cap < 4 * 152 ? cap : 4 * 152;
         { launch_pdl(k_cg_zone64, zg, ZONE64_THREADS, 0, s, sb.d_nz, za, g64,
-                     p.max_cg_iters * p.max_refine); note_launch(); }
+                     p.max_cg_iters * p.max_refine, 0); note_launch(); }
         { launch_pdl(k_zone_final, 1, 256, 0, s, sb.d_nz, sb.r64, sb.q64, p.rel_tol, sb.dwork,
                      sb.iwork); note_launch(); }
         return;
@@ -3271,6 +3275,22 @@ void solve(const SolveParams &p, const MeshPair &mp, const int *d_k, int cap, So
         note_launch();
     }
     p.big_mark(0, s);
+    // a zone whose float32 runs stopped reducing its float64 residual before
+    // the target (the residual guard) is solved again by the float64 per-zone
+    // CG; every other zone is skipped at once
+    za.ids = sb.ids;
+    za.nA = mp.A.n_verts;
+    za.wA = mp.A.inv_mass;
+    za.wB = mp.B.inv_mass;
+    za.pinv64 = sb.pinv64;
+    {
+        Zone64Scratch g64;
+        g64.r = sb.cg64; g64.p = sb.cg64 + cap; g64.s = sb.cg64 + 2 * (size_t)cap;
+        g64.w = sb.cg64 + 3 * (size_t)cap; g64.z = sb.cg64 + 4 * (size_t)cap;
+        int zr = cap < 152 ? cap : 152;
+        { launch_pdl(k_cg_zone64, zr, ZONE64_THREADS, 0, s, sb.d_nz, za, g64,
+                     p.max_cg_iters * p.max_refine, 1); note_launch(); }
+    }
     { launch_pdl(k_zone_final, 1, 256, 0, s, sb.d_nz, sb.r64, sb.q64, p.rel_tol, sb.dwork,
                  sb.iwork); note_launch(); }
 }
