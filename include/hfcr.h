@@ -185,7 +185,9 @@ typedef struct {
     double worst_rel_residual;     /* largest solver residual over the iterations */
     hfcr_detect_stats stats;       /* summed over the detections */
     int32_t solver_path;           /* bit 0: the float32 CG ran in shared memory, bit 1: in global
-                                      memory; bit 2: the float64 per-zone CG ran */
+                                      memory; bit 2: the float64 per-zone CG ran (the float64
+                                      form, or in the mixed form for a zone whose float32 runs
+                                      stopped reducing its residual before rel_tol) */
     int32_t diffuse_cg_iters;      /* harmonic diffusion: CG iterations over all iterations */
     int32_t diffuse_unconverged;   /* iterations whose harmonic diffusion stopped at diffuse_max_iters */
     double worst_amplification;    /* largest max_dx / max_rhs of a response (see hfcr_solve_info) */
